@@ -1,0 +1,199 @@
+/*
+ * tks.h -- C ABI of the GB300 (sm_103a) library for sketched recompression of
+ * sums of Tucker tensors (R. Smith et al., "Efficient Sketching-Based Summation
+ * of Tucker Tensors", arXiv 2603.13532).
+ *
+ * A problem is a sum of K Tucker terms X = sum_k alpha_k G_k x_1 U_k^(1) ... x_d U_k^(d)
+ * (Eq. TuckerDecompositionModeProd; term weights as in TuckerAxby, Alg. 1).  The
+ * library recompresses X without forming it (KronSum-Tucker, Alg. 3; KRPSum-Tucker,
+ * Alg. 4):
+ *   stage (a)  M_kj = U_k^(j)^T Omega_j with Gaussian Omega_j (Sec. 3.1, factor reuse)
+ *   stage (b)  Y_n = sum_k U_k^(n) V_kn with the Khatri-Rao or Kronecker core sketch
+ *              V_kn (Eqs. KRP_sketch_unfolding / Kron_sketch_unfolding), Q_n = qr(Y_n)
+ *   stage (c)  H = sum_k G_k x_1 (Q_1^T U_k^(1)) ... x_d (Q_d^T U_k^(d)) (Sec. 3.3)
+ *   final      ST-HOSVD truncation of H (Alg. 2 phase 2), U~_n = Q_n P_n.
+ * Many independent problems of different sizes go into one plan and run in grouped
+ * launches.
+ *
+ * Conventions for every entry point
+ *   - Matrices are column-major.  Tensors are stored with mode 1 fastest, which is
+ *     the unfolding order of Eq. unfolding_index.
+ *   - "device" pointers are CUDA global-memory addresses on the plan's device, "host"
+ *     pointers are ordinary CPU memory.  The caller owns every buffer it passes; the
+ *     library allocates device memory only inside tks_plan_create (descriptor tables
+ *     and a status word) and frees it in tks_plan_destroy.
+ *   - stream is a cudaStream_t (NULL = legacy default stream).  Execute calls only
+ *     enqueue work and return; results and the device status word are valid after the
+ *     stream completes.  tks_sync_status synchronizes and reports device-side errors.
+ *   - Errors are returned as tks_status (never exceptions); tks_last_error() gives a
+ *     thread-local message for the last failing call on that thread.
+ *   - Calls on the same plan must not run concurrently on different streams: they
+ *     share the plan's status word (and the workspace, if the same one is passed).
+ */
+#ifndef TKS_H
+#define TKS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define TKS_API __attribute__((visibility("default")))
+#else
+#define TKS_API
+#endif
+
+#define TKS_MAX_ORDER 6      /* tensor order d: 2 <= d <= TKS_MAX_ORDER */
+#define TKS_MAX_RANK 64      /* per-term rank r_km: 1 <= r_km <= min(n_m, TKS_MAX_RANK) */
+#define TKS_MAX_BASIS 96     /* columns of Q_n, b_n = min(n_n, S_n) <= TKS_MAX_BASIS */
+
+typedef enum {
+  TKS_OK = 0,
+  TKS_EINVAL = 1,        /* invalid argument; nothing was enqueued */
+  TKS_ENOMEM = 2,        /* a device allocation inside tks_plan_create failed */
+  TKS_ECUDA = 3,         /* a CUDA runtime call failed (message in tks_last_error) */
+  TKS_ETIMEOUT = 4,      /* a bounded device-side wait ran out (kernel returned early) */
+  TKS_ENONFINITE = 5,    /* a NaN or Inf reached the sketch or the projected core */
+  TKS_ENOCONV = 6,       /* the small symmetric eigensolver hit its sweep limit */
+  TKS_EUNSUPPORTED = 7   /* valid input outside what this build supports */
+} tks_status;
+
+typedef enum { TKS_SKETCH_KRON = 0, TKS_SKETCH_KRP = 1 } tks_sketch;
+
+typedef enum {
+  TKS_FP64 = 0,   /* every stage in float64 on CUDA cores (the plain FP64 GPU path) */
+  TKS_MIXED = 1   /* contractions on tcgen05 tensor cores with bfloat16 operands (a float32
+                     operand is split into bfloat16 planes) and float32 accumulation; QR and
+                     ST-HOSVD as in TKS_FP64 */
+} tks_precision;
+
+typedef enum { TKS_DT_F64 = 0, TKS_DT_BF16 = 1 } tks_dtype;
+
+/* One Tucker sum.  All arrays described as host are read during tks_plan_create only;
+ * the device pointers are remembered by the plan and read by every execute call. */
+typedef struct {
+  int32_t order;                /* d */
+  const int64_t* dims;          /* host [d]: n_1..n_d, each >= 1 */
+  int32_t num_terms;            /* K >= 1 */
+  const int32_t* ranks;         /* host [K*d]: ranks[k*d + m] = r_km */
+  const int32_t* target_ranks;  /* host [d]: target rank per mode, >= 1 */
+  const int32_t* oversampling;  /* host [d]: oversampling p_n >= 0; ell_n = target_n + p_n */
+  const double* alpha;          /* host [K] term weights, or NULL for all ones */
+  const void* cores;            /* device: the K cores packed back to back, term k's core
+                                   (r_k1 x ... x r_kd, mode 1 fastest) starting at element
+                                   sum_{k'<k} prod_m r_k'm; element type = params dtype */
+  const void* const* factors;   /* host [d] of device pointers: factors[m] is the
+                                   concatenated factor Ucat_m = [U_1^(m) ... U_K^(m)],
+                                   n_m x R_m column-major (ld = n_m), R_m = sum_k r_km
+                                   (the TuckerAxby layout, Alg. 1) */
+} tks_problem;
+
+typedef struct {
+  tks_sketch sketch;            /* Kronecker (Alg. 3) or Khatri-Rao (Alg. 4) */
+  tks_precision precision;      /* TKS_FP64 needs dtype F64; TKS_MIXED needs dtype BF16 */
+  tks_dtype dtype;              /* element type of cores and factors */
+  uint64_t seed;                /* key of the Gaussian draws (Philox4x64-10) */
+  double trunc_tol;             /* 0: keep min(target_n, b_n) columns per mode; > 0: the
+                                   relative tolerance rule of Alg. 2, capped by the target */
+} tks_params;
+
+typedef struct tks_plan tks_plan;
+
+typedef struct {
+  size_t workspace_bytes;       /* device scratch each execute call needs (256-byte aligned) */
+  int64_t omega_elems;          /* float64 elements of the Omega buffer (tks_generate_omega) */
+  int64_t sketch_elems;         /* float64 elements of the Y buffer (tucker_sum_sketch) */
+  int64_t basis_elems;          /* float64 elements of a Q buffer (tks_project_core input) */
+  int64_t core_elems;           /* float64 elements of an H buffer (tks_project_core output) */
+  int64_t output_elems;         /* float64 elements of the recompression output buffer */
+  int32_t num_problems;
+  int32_t launches_recompress;  /* kernel launches one tucker_sum_recompress enqueues */
+  double flops_lowprec;         /* algorithmic flops of the contraction stages, all problems */
+  double flops_fp64;            /* algorithmic flops of QR and ST-HOSVD, all problems */
+} tks_plan_info_t;
+
+typedef struct {
+  int32_t order;
+  int32_t R[TKS_MAX_ORDER];              /* sum of term ranks per mode */
+  int32_t omega_cols[TKS_MAX_ORDER];     /* s_m: columns of Omega_m */
+  int32_t sketch_cols[TKS_MAX_ORDER];    /* S_n: columns of Y_n */
+  int32_t basis_cols[TKS_MAX_ORDER];     /* b_n = min(n_n, S_n): columns of Q_n, H's dims */
+  int32_t max_ranks[TKS_MAX_ORDER];      /* rmax_n = min(target_n, b_n) */
+  int64_t omega_off[TKS_MAX_ORDER];      /* element offsets of Omega_m (n_m x s_m) */
+  int64_t sketch_off[TKS_MAX_ORDER];     /* element offsets of Y_n (n_n x S_n) */
+  int64_t basis_off[TKS_MAX_ORDER];      /* element offsets of Q_n (n_n x b_n) */
+  int64_t core_off;                      /* element offset of H (b_1 x ... x b_d) */
+  int64_t out_core_off;                  /* element offset of the output core (rmax_1 x ... ) */
+  int64_t out_factor_off[TKS_MAX_ORDER]; /* element offsets of U~_n (n_n x rmax_n) */
+} tks_problem_info_t;
+
+/* Validates the problems, computes sketch sizes (Sec. 3.2: s = max_n ell_n for Khatri-Rao,
+ * Eq. heuristic_formula in exact integer form for Kronecker), workspace layout and launch
+ * tables, and copies the tables to the current CUDA device.  Host-only apart from those
+ * allocations and copies; synchronous.  On error *plan is set to NULL. */
+TKS_API tks_status tks_plan_create(tks_plan** plan, const tks_problem* problems, int32_t num_problems,
+                           const tks_params* params);
+TKS_API void tks_plan_destroy(tks_plan* plan);
+TKS_API tks_status tks_plan_info(const tks_plan* plan, tks_plan_info_t* info);
+TKS_API tks_status tks_problem_info(const tks_plan* plan, int32_t problem, tks_problem_info_t* info);
+
+/* Writes every Omega_m (n_m x s_m, float64, column-major) of every problem into the device
+ * buffer omega_out at the offsets of tks_problem_info.  Draw e = i + n_m c of problem p, mode m
+ * is Philox4x64-10 block e/4 under key (seed, 0) and counter (e/4, m, p, 0), turned into normals
+ * by Box-Muller (lane e%4).  In TKS_MIXED the values are rounded to float32 then bfloat16.
+ * This is the exact Omega every other entry point uses. */
+TKS_API tks_status tks_generate_omega(tks_plan* plan, void* workspace, double* omega_out, void* stream);
+
+/* Stages (a) and (b) without the QR: Y_n = sum_k U_k^(n) V_kn (Eqs. KRP_sketch_unfolding /
+ * Kron_sketch_unfolding) for every problem and mode, float64, into the device buffer Y_out
+ * (layout: tks_problem_info sketch_off; Kronecker column order = first remaining mode fastest). */
+TKS_API tks_status tucker_sum_sketch(tks_plan* plan, void* workspace, double* Y_out, void* stream);
+
+/* Stage (c) for given bases: H = sum_k alpha_k G_k x_1 (Q_1^T U_k^(1)) ... x_d (Q_d^T U_k^(d))
+ * (Sec. 3.3).  Q_in (device, float64, n_n x b_n per mode at basis_off) is read, H_out (device,
+ * float64, b_1 x ... x b_d at core_off) is written. */
+TKS_API tks_status tks_project_core(tks_plan* plan, void* workspace, const double* Q_in, double* H_out,
+                            void* stream);
+
+/* The whole method: stages (a)-(c) and the ST-HOSVD truncation.  out (device, float64,
+ * output_elems) receives per problem the core G~ (rmax_1 x ... x rmax_d at out_core_off) and
+ * the factors U~_n = Q_n P_n (n_n x rmax_n at out_factor_off[n]).  ranks_out (device, int32,
+ * [num_problems * TKS_MAX_ORDER], entry p*TKS_MAX_ORDER + n) receives the kept ranks r_n <= rmax_n
+ * (unused entries 0); entries of the core and
+ * columns of U~_n beyond them are zero, so the padded arrays are the same Tucker tensor. */
+TKS_API tks_status tucker_sum_recompress(tks_plan* plan, void* workspace, double* out, int32_t* ranks_out,
+                                 void* stream);
+
+/* Synchronizes stream, then returns and clears the first error a kernel of this plan recorded
+ * since the previous call (TKS_ENONFINITE, TKS_ENOCONV, TKS_ETIMEOUT), else TKS_OK. */
+TKS_API tks_status tks_sync_status(tks_plan* plan, void* stream);
+
+/* Per-stage timing of tucker_sum_recompress with CUDA events recorded on the caller's stream
+ * between the plan's launches (no synchronization is added).  tks_profile_begin arms it for
+ * the next max_calls calls; tks_profile_end synchronizes on the last recorded event, fills up
+ * to cap entries (one per launch of the plan's launch list, in launch order) and disarms it.
+ * flops and bytes are the stage's algorithmic counts for one call (all problems): every real
+ * multiply-add counts 2 flops; bytes count each operand read once and each result written
+ * once (float64 or the operand's own element size). */
+typedef struct {
+  char name[32];          /* stage, e.g. "b2:Y=UcatVcat" */
+  int32_t kind;           /* 0 Omega, 1 GEMM, 2 split-K reduction, 3 core sketch, 4 QR, 5 eig */
+  int32_t calls;          /* recompress calls timed */
+  double ms;              /* summed duration over those calls */
+  double flops;           /* algorithmic flops of one call */
+  double bytes;           /* algorithmic bytes of one call */
+} tks_step_profile_t;
+
+TKS_API tks_status tks_profile_begin(tks_plan* plan, int32_t max_calls);
+TKS_API tks_status tks_profile_end(tks_plan* plan, tks_step_profile_t* out, int32_t cap, int32_t* nsteps);
+
+TKS_API const char* tks_last_error(void);
+TKS_API const char* tks_status_string(tks_status status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TKS_H */

@@ -1,0 +1,268 @@
+"""Python binding of the C ABI in include/tks.h (ctypes; argument marshalling only).
+
+Every step of the method runs in the CUDA kernels of libtks.so; this module only
+packs tensors into the documented layouts, passes device pointers and the current
+torch CUDA stream, and unpacks results.  There is no fallback: if the library has
+not been built, :func:`load` raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+from .build import LIB_PATH
+
+MAX_ORDER = 6
+SKETCH = {"kron": 0, "krp": 1}
+PRECISION = {"fp64": 0, "mixed": 1}
+DTYPE = {"fp64": 0, "bf16": 1}
+STATUS = {0: "TKS_OK", 1: "TKS_EINVAL", 2: "TKS_ENOMEM", 3: "TKS_ECUDA", 4: "TKS_ETIMEOUT",
+          5: "TKS_ENONFINITE", 6: "TKS_ENOCONV", 7: "TKS_EUNSUPPORTED"}
+
+STEP_KINDS = {0: "omega", 1: "gemm", 2: "reduce", 3: "core_sketch", 4: "qr", 5: "eig"}
+
+
+class TksError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Problem_t(ctypes.Structure):
+    _fields_ = [("order", ctypes.c_int32), ("dims", ctypes.POINTER(ctypes.c_int64)),
+                ("num_terms", ctypes.c_int32), ("ranks", ctypes.POINTER(ctypes.c_int32)),
+                ("target_ranks", ctypes.POINTER(ctypes.c_int32)),
+                ("oversampling", ctypes.POINTER(ctypes.c_int32)),
+                ("alpha", ctypes.POINTER(ctypes.c_double)), ("cores", ctypes.c_void_p),
+                ("factors", ctypes.POINTER(ctypes.c_void_p))]
+
+
+class Params_t(ctypes.Structure):
+    _fields_ = [("sketch", ctypes.c_int), ("precision", ctypes.c_int), ("dtype", ctypes.c_int),
+                ("seed", ctypes.c_uint64), ("trunc_tol", ctypes.c_double)]
+
+
+class PlanInfo_t(ctypes.Structure):
+    _fields_ = [("workspace_bytes", ctypes.c_size_t), ("omega_elems", ctypes.c_int64),
+                ("sketch_elems", ctypes.c_int64), ("basis_elems", ctypes.c_int64),
+                ("core_elems", ctypes.c_int64), ("output_elems", ctypes.c_int64),
+                ("num_problems", ctypes.c_int32), ("launches_recompress", ctypes.c_int32),
+                ("flops_lowprec", ctypes.c_double), ("flops_fp64", ctypes.c_double)]
+
+
+I32x6 = ctypes.c_int32 * MAX_ORDER
+I64x6 = ctypes.c_int64 * MAX_ORDER
+
+
+class ProblemInfo_t(ctypes.Structure):
+    _fields_ = [("order", ctypes.c_int32), ("R", I32x6), ("omega_cols", I32x6), ("sketch_cols", I32x6),
+                ("basis_cols", I32x6), ("max_ranks", I32x6), ("omega_off", I64x6),
+                ("sketch_off", I64x6), ("basis_off", I64x6), ("core_off", ctypes.c_int64),
+                ("out_core_off", ctypes.c_int64), ("out_factor_off", I64x6)]
+
+
+class StepProfile_t(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("kind", ctypes.c_int32), ("calls", ctypes.c_int32),
+                ("ms", ctypes.c_double), ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
+_LIB = None
+
+
+def load(path=None):
+    """Load libtks.so (raises if it has not been built)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2603_13532_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    lib.tks_plan_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(Problem_t), ctypes.c_int32,
+                                    ctypes.POINTER(Params_t)]
+    lib.tks_plan_destroy.argtypes = [P]
+    lib.tks_plan_destroy.restype = None
+    lib.tks_plan_info.argtypes = [P, ctypes.POINTER(PlanInfo_t)]
+    lib.tks_problem_info.argtypes = [P, ctypes.c_int32, ctypes.POINTER(ProblemInfo_t)]
+    lib.tks_generate_omega.argtypes = [P, P, P, P]
+    lib.tucker_sum_sketch.argtypes = [P, P, P, P]
+    lib.tks_project_core.argtypes = [P, P, P, P, P]
+    lib.tucker_sum_recompress.argtypes = [P, P, P, P, P]
+    lib.tks_sync_status.argtypes = [P, P]
+    lib.tks_last_error.restype = ctypes.c_char_p
+    lib.tks_status_string.restype = ctypes.c_char_p
+    lib.tks_status_string.argtypes = [ctypes.c_int]
+    lib.tks_profile_begin.argtypes = [P, ctypes.c_int32]
+    lib.tks_profile_end.argtypes = [P, ctypes.POINTER(StepProfile_t), ctypes.c_int32,
+                                    ctypes.POINTER(ctypes.c_int32)]
+    for name in ["tks_plan_create", "tks_plan_info", "tks_problem_info", "tks_generate_omega",
+                 "tucker_sum_sketch", "tks_project_core", "tucker_sum_recompress", "tks_sync_status",
+                 "tks_profile_begin", "tks_profile_end"]:
+        getattr(lib, name).restype = ctypes.c_int
+    _LIB = lib
+    return lib
+
+
+def _check(code):
+    if code != 0:
+        raise TksError(code, _LIB.tks_last_error().decode())
+
+
+def _stream_handle():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def pack_problem(prob, dtype, device):
+    """Device tensors in the C-ABI layout: packed cores and Ucat_m (column-major)."""
+    tdt = torch.float64 if dtype == "fp64" else torch.bfloat16
+    cores = np.concatenate([np.asarray(G, dtype=np.float64).ravel(order="F") for G in prob.cores])
+    core_t = torch.from_numpy(cores).to(device=device, dtype=tdt)
+    facs = []
+    for m in range(prob.order):
+        Ucat = np.hstack([np.asarray(Us[m], dtype=np.float64) for Us in prob.factors])
+        facs.append(torch.from_numpy(Ucat.ravel(order="F").copy()).to(device=device, dtype=tdt))
+    return core_t, facs
+
+
+class Plan:
+    """A plan over a list of ``workloads.Problem`` with their device inputs."""
+
+    def __init__(self, problems, kind="krp", precision="fp64", seed=0, tol=0.0, device="cuda",
+                 inputs=None):
+        self.lib = load()
+        self.problems = list(problems)
+        self.kind, self.precision, self.seed, self.tol = kind, precision, seed, tol
+        self.dtype = "fp64" if precision == "fp64" else "bf16"
+        self.device = torch.device(device)
+        self.inputs = inputs if inputs is not None else [
+            pack_problem(p, self.dtype, self.device) for p in self.problems]
+        self._keep = []
+        arr = (Problem_t * len(self.problems))()
+        for i, (p, (core_t, facs)) in enumerate(zip(self.problems, self.inputs)):
+            d = p.order
+            dims = (ctypes.c_int64 * d)(*p.dims)
+            ranks = (ctypes.c_int32 * (p.num_terms * d))(*[r for rk in p.ranks() for r in rk])
+            tgt = (ctypes.c_int32 * d)(*p.target)
+            ovs = (ctypes.c_int32 * d)(*p.oversampling)
+            alpha = (ctypes.c_double * p.num_terms)(*p.alpha) if p.alpha is not None else None
+            fptrs = (ctypes.c_void_p * d)(*[f.data_ptr() for f in facs])
+            self._keep += [dims, ranks, tgt, ovs, alpha, fptrs]
+            arr[i] = Problem_t(d, dims, p.num_terms, ranks, tgt, ovs,
+                               ctypes.cast(alpha, ctypes.POINTER(ctypes.c_double)) if alpha else None,
+                               ctypes.c_void_p(core_t.data_ptr()), fptrs)
+        prm = Params_t(SKETCH[kind], PRECISION[precision], DTYPE[self.dtype], seed, tol)
+        handle = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(self.lib.tks_plan_create(ctypes.byref(handle), arr, len(self.problems), ctypes.byref(prm)))
+        self.handle = handle
+        self.info = PlanInfo_t()
+        _check(self.lib.tks_plan_info(handle, ctypes.byref(self.info)))
+        self.pinfo = []
+        for i in range(len(self.problems)):
+            pi = ProblemInfo_t()
+            _check(self.lib.tks_problem_info(handle, i, ctypes.byref(pi)))
+            self.pinfo.append(pi)
+        self.workspace = torch.empty(max(1, self.info.workspace_bytes), dtype=torch.uint8, device=self.device)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            self.lib.tks_plan_destroy(h)
+            self.handle = None
+
+    # ---- raw entry points (device buffers in, nothing synchronised)
+    def omega_raw(self, out):
+        _check(self.lib.tks_generate_omega(self.handle, _ptr(self.workspace), _ptr(out), _stream_handle()))
+
+    def sketch_raw(self, Y):
+        _check(self.lib.tucker_sum_sketch(self.handle, _ptr(self.workspace), _ptr(Y), _stream_handle()))
+
+    def project_raw(self, Q, H):
+        _check(self.lib.tks_project_core(self.handle, _ptr(self.workspace), _ptr(Q), _ptr(H), _stream_handle()))
+
+    def recompress_raw(self, out, ranks):
+        _check(self.lib.tucker_sum_recompress(self.handle, _ptr(self.workspace), _ptr(out), _ptr(ranks),
+                                              _stream_handle()))
+
+    def sync(self):
+        _check(self.lib.tks_sync_status(self.handle, _stream_handle()))
+
+    def profile_begin(self, max_calls):
+        _check(self.lib.tks_profile_begin(self.handle, max_calls))
+
+    def profile_end(self):
+        """Stage timings of the recompress calls since profile_begin: one dict per launch."""
+        n = ctypes.c_int32()
+        arr = (StepProfile_t * 512)()
+        _check(self.lib.tks_profile_end(self.handle, arr, 512, ctypes.byref(n)))
+        return [dict(name=a.name.decode(), kind=STEP_KINDS.get(a.kind, a.kind), calls=a.calls, ms=a.ms,
+                     flops=a.flops, bytes=a.bytes) for a in arr[:min(n.value, 512)]]
+
+    # ---- convenience: allocate, run, return numpy per problem
+    def _new(self, n, dtype=torch.float64):
+        return torch.zeros(max(1, n), dtype=dtype, device=self.device)
+
+    def omega(self):
+        out = self._new(self.info.omega_elems)
+        self.omega_raw(out)
+        self.sync()
+        host = out.cpu().numpy()
+        res = []
+        for p, pi in zip(self.problems, self.pinfo):
+            res.append([host[pi.omega_off[m]: pi.omega_off[m] + p.dims[m] * pi.omega_cols[m]]
+                        .reshape(p.dims[m], pi.omega_cols[m], order="F") for m in range(p.order)])
+        return res
+
+    def sketch(self):
+        Y = self._new(self.info.sketch_elems)
+        self.sketch_raw(Y)
+        self.sync()
+        host = Y.cpu().numpy()
+        return [[host[pi.sketch_off[m]: pi.sketch_off[m] + p.dims[m] * pi.sketch_cols[m]]
+                 .reshape(p.dims[m], pi.sketch_cols[m], order="F") for m in range(p.order)]
+                for p, pi in zip(self.problems, self.pinfo)]
+
+    def pack_bases(self, Qs):
+        host = np.zeros(max(1, self.info.basis_elems))
+        for p, pi, Qp in zip(self.problems, self.pinfo, Qs):
+            for m in range(p.order):
+                b = pi.basis_cols[m]
+                host[pi.basis_off[m]: pi.basis_off[m] + p.dims[m] * b] = np.asarray(Qp[m])[:, :b].ravel(order="F")
+        return torch.from_numpy(host).to(self.device)
+
+    def project(self, Qs):
+        Q = self.pack_bases(Qs)
+        H = self._new(self.info.core_elems)
+        self.project_raw(Q, H)
+        self.sync()
+        host = H.cpu().numpy()
+        out = []
+        for p, pi in zip(self.problems, self.pinfo):
+            shape = [pi.basis_cols[m] for m in range(p.order)]
+            out.append(host[pi.core_off: pi.core_off + int(np.prod(shape))].reshape(shape, order="F"))
+        return out
+
+    def recompress(self):
+        out = self._new(self.info.output_elems)
+        ranks = torch.zeros(len(self.problems) * MAX_ORDER, dtype=torch.int32, device=self.device)
+        self.recompress_raw(out, ranks)
+        self.sync()
+        return self.unpack(out, ranks)
+
+    def unpack(self, out, ranks):
+        host = out.cpu().numpy()
+        rk = ranks.cpu().numpy().reshape(-1, MAX_ORDER)
+        res = []
+        for i, (p, pi) in enumerate(zip(self.problems, self.pinfo)):
+            rmax = [pi.max_ranks[m] for m in range(p.order)]
+            core = host[pi.out_core_off: pi.out_core_off + int(np.prod(rmax))].reshape(rmax, order="F")
+            facs = [host[pi.out_factor_off[m]: pi.out_factor_off[m] + p.dims[m] * rmax[m]]
+                    .reshape(p.dims[m], rmax[m], order="F") for m in range(p.order)]
+            res.append(dict(core=core, factors=facs, ranks=[int(x) for x in rk[i, :p.order]]))
+        return res

@@ -1,0 +1,878 @@
+// C ABI of the library: plan creation (validation, sketch sizes, workspace layout, launch
+// tables) and the execute entry points, which bind the caller's buffers to the plan's base
+// ids and enqueue the prebuilt launches on the caller's stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "tks.h"
+#include "tks_internal.h"
+
+using namespace tks;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+tks_status fail(tks_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+#define TKS_CUDA_CHECK(call)                                                                  \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess)                                                                    \
+      return fail(TKS_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));            \
+  } while (0)
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t x, size_t a = kAlign) { return (x + a - 1) / a * a; }
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+Operand op(int32_t base, size_t off_bytes) { return Operand{base, 0, (int64_t)off_bytes}; }
+Operand op_abs(const void* p, size_t off_bytes = 0) {
+  return Operand{B_ABS, 0, (int64_t)(reinterpret_cast<uintptr_t>(p) + off_bytes)};
+}
+
+enum StepKind { S_OMEGA, S_GEMM, S_REDUCE, S_CORESKETCH, S_QR, S_EIG };
+
+struct Step {
+  StepKind kind;
+  size_t table_off;   // offset of the job table in the device arena
+  int njobs;
+  int64_t work;       // tiles / elements / blocks
+  char name[32];
+  double flops, bytes;
+};
+
+Step make_step(StepKind kind, size_t off, int njobs, int64_t work, const char* name, double flops,
+               double bytes) {
+  Step s;
+  s.kind = kind;
+  s.table_off = off;
+  s.njobs = njobs;
+  s.work = work;
+  std::snprintf(s.name, sizeof(s.name), "%s", name);
+  s.flops = flops;
+  s.bytes = bytes;
+  return s;
+}
+
+struct ProbHost {
+  int d = 0, K = 0;
+  int64_t n[MAXD] = {};
+  int s[MAXD] = {}, S[MAXD] = {}, b[MAXD] = {}, R[MAXD] = {}, rmax[MAXD] = {};
+  int target[MAXD] = {}, over[MAXD] = {}, ell[MAXD] = {};
+  std::vector<int> ranks;      // K*d
+  std::vector<int> roff;       // K*d
+  std::vector<int64_t> core_off;
+  std::vector<double> alpha;
+  const void* cores = nullptr;
+  const void* factors[MAXD] = {};
+  // element offsets in the caller-visible buffers
+  int64_t omega_off[MAXD] = {}, y_off[MAXD] = {}, q_off[MAXD] = {}, h_off = 0;
+  int64_t out_core_off = 0, out_fac_off[MAXD] = {};
+  // workspace byte offsets
+  size_t M[MAXD] = {}, V[MAXD] = {}, W[MAXD] = {}, tau[MAXD] = {}, A[MAXD] = {};
+  size_t T = 0, gram = 0, part = 0, P[MAXD] = {}, ev[MAXD] = {}, theta = 0, Hp[2] = {};
+  std::vector<size_t> chain;   // 2 ping-pong buffers per term
+  int gram_ksplit = 1;
+  double flops_low = 0.0, flops_f64 = 0.0;
+};
+
+struct GemmList {
+  std::vector<GemmJob> jobs;
+  int tiles = 0;
+  int64_t red = 0;
+  void add(GemmJob j) {
+    if (j.M <= 0 || j.N <= 0 || j.batch <= 0) return;
+    if (j.K1 <= 0) j.K1 = std::max(j.K, 1);
+    if (j.ksplit < 1) j.ksplit = 1;
+    j.kchunk = std::max(16, (ceil_div(std::max(j.K, 1), j.ksplit) + 15) / 16 * 16);
+    j.ksplit = std::max(1, ceil_div(std::max(j.K, 1), j.kchunk));
+    j.tiles_m = ceil_div(j.M, 64);
+    j.tiles_n = ceil_div(j.N, 64);
+    j.tile_begin = tiles;
+    tiles += j.tiles_m * j.tiles_n * j.batch * j.ksplit;
+    j.red_begin = 0;
+    if (j.ksplit > 1) {
+      j.red_begin = red;
+      red += (int64_t)j.batch * j.M * j.N;
+    }
+    jobs.push_back(j);
+  }
+};
+
+GemmJob gemm(int M, int N, int K, Operand A, int64_t a_m, int64_t a_k0, Operand B, int64_t b_n,
+             int64_t b_k0, Operand C, int64_t c_m, int64_t c_n, double alpha = 1.0) {
+  GemmJob j;
+  std::memset(&j, 0, sizeof(j));
+  j.M = M; j.N = N; j.K = K; j.K1 = K; j.batch = 1; j.ksplit = 1;
+  j.A = A; j.a_m = a_m; j.a_k0 = a_k0;
+  j.B = B; j.b_n = b_n; j.b_k0 = b_k0;
+  j.C = C; j.c_m = c_m; j.c_n = c_n;
+  j.alpha = alpha; j.beta = 0.0;
+  return j;
+}
+
+}  // namespace
+
+struct tks_plan {
+  int device = 0;
+  tks_params params{};
+  int nprob = 0;
+  int dmax = 0;
+  int bmax = 0;
+  std::vector<ProbHost> probs;
+  std::vector<char> arena_host;
+  char* arena_dev = nullptr;
+  Status* status = nullptr;
+  size_t ws_bytes = 0;
+  size_t ws_omega = 0, ws_Y = 0, ws_Q = 0, ws_H = 0;
+  int64_t omega_elems = 0, sketch_elems = 0, basis_elems = 0, core_elems = 0, output_elems = 0;
+  std::vector<Step> st_omega, st_sketch, st_project, st_recompress;
+  double flops_low = 0.0, flops_f64 = 0.0;
+
+  size_t add_table(const void* p, size_t bytes) {
+    const size_t off = align_up(arena_host.size(), 64);
+    arena_host.resize(off + bytes);
+    std::memcpy(arena_host.data() + off, p, bytes);
+    return off;
+  }
+  // profiling: events recorded around the recompress launches
+  int prof_max_calls = 0, prof_calls = 0;
+  std::vector<cudaEvent_t> prof_events;
+
+  template <typename T>
+  void push(std::vector<Step>& steps, StepKind kind, const std::vector<T>& jobs, int64_t work,
+            const char* name, double flops = 0.0, double bytes = 0.0) {
+    if (jobs.empty() || work <= 0) return;
+    steps.push_back(make_step(kind, add_table(jobs.data(), jobs.size() * sizeof(T)), (int)jobs.size(), work,
+                              name, flops, bytes));
+  }
+  void push_gemm(std::vector<Step>& steps, const GemmList& g, const char* name) {
+    if (g.jobs.empty()) return;
+    double flops = 0.0, bytes = 0.0;
+    for (const auto& j : g.jobs) {
+      flops += 2.0 * j.M * j.N * (double)j.K * j.batch;
+      bytes += 8.0 * ((double)j.M * j.K + (double)j.K * j.N + (double)j.M * j.N) * j.batch;
+    }
+    push(steps, S_GEMM, g.jobs, g.tiles, name, flops, bytes);
+    std::vector<GemmJob> split;
+    for (const auto& j : g.jobs)
+      if (j.ksplit > 1) split.push_back(j);
+    char rn[32];
+    std::snprintf(rn, sizeof(rn), "%s:reduce", name);
+    push(steps, S_REDUCE, split, g.red, rn);
+  }
+  void profile_clear() {
+    for (auto e : prof_events) cudaEventDestroy(e);
+    prof_events.clear();
+    prof_max_calls = prof_calls = 0;
+  }
+};
+
+namespace {
+
+int64_t prod(const int* v, int n) {
+  int64_t p = 1;
+  for (int i = 0; i < n; ++i) p *= v[i];
+  return p;
+}
+
+// Least s >= 1 with (s ell_i)^(d-1) >= prod_j ell_j: the exact integer form of
+// s_i = ceil((prod_j ell_j)^(1/(d-1)) / ell_i) (Eq. heuristic_formula).
+int kron_size(const int* ell, int d, int i) {
+  long double P = 1;
+  for (int j = 0; j < d; ++j) P *= ell[j];
+  for (int s = 1;; ++s) {
+    long double v = 1;
+    for (int t = 0; t < d - 1; ++t) v *= (long double)s * ell[i];
+    if (v >= P) return s;
+  }
+}
+
+tks_status validate_and_size(const tks_problem& pr, const tks_params& prm, ProbHost& h, int pidx) {
+  const std::string where = "problem " + std::to_string(pidx) + ": ";
+  if (pr.order < 2 || pr.order > TKS_MAX_ORDER) return fail(TKS_EINVAL, where + "order out of range");
+  if (pr.num_terms < 1) return fail(TKS_EINVAL, where + "num_terms < 1");
+  if (!pr.dims || !pr.ranks || !pr.target_ranks || !pr.oversampling || !pr.cores || !pr.factors)
+    return fail(TKS_EINVAL, where + "null pointer");
+  h.d = pr.order;
+  h.K = pr.num_terms;
+  h.cores = pr.cores;
+  for (int m = 0; m < h.d; ++m) {
+    h.n[m] = pr.dims[m];
+    if (h.n[m] < 1 || h.n[m] > (1 << 24)) return fail(TKS_EINVAL, where + "dimension out of range");
+    h.target[m] = pr.target_ranks[m];
+    h.over[m] = pr.oversampling[m];
+    if (h.target[m] < 1 || h.over[m] < 0) return fail(TKS_EINVAL, where + "bad target/oversampling");
+    h.ell[m] = h.target[m] + h.over[m];
+    if (!pr.factors[m]) return fail(TKS_EINVAL, where + "null factor pointer");
+    h.factors[m] = pr.factors[m];
+  }
+  h.ranks.assign(pr.ranks, pr.ranks + (size_t)h.K * h.d);
+  h.roff.assign((size_t)h.K * h.d, 0);
+  h.core_off.assign(h.K, 0);
+  h.alpha.assign(h.K, 1.0);
+  int64_t coff = 0;
+  for (int k = 0; k < h.K; ++k) {
+    h.core_off[k] = coff;
+    int64_t sz = 1;
+    for (int m = 0; m < h.d; ++m) {
+      const int r = h.ranks[(size_t)k * h.d + m];
+      if (r < 1 || r > TKS_MAX_RANK || r > h.n[m]) return fail(TKS_EINVAL, where + "term rank out of range");
+      h.roff[(size_t)k * h.d + m] = h.R[m];
+      h.R[m] += r;
+      sz *= r;
+    }
+    coff += sz;
+    if (pr.alpha) {
+      h.alpha[k] = pr.alpha[k];
+      if (!std::isfinite(h.alpha[k])) return fail(TKS_EINVAL, where + "non-finite alpha");
+    }
+  }
+  // sketch sizes (Sec. 3.2 / Eq. heuristic_formula)
+  for (int m = 0; m < h.d; ++m) {
+    if (prm.sketch == TKS_SKETCH_KRP) {
+      int s = 0;
+      for (int j = 0; j < h.d; ++j) s = std::max(s, h.ell[j]);
+      h.s[m] = s;
+    } else {
+      h.s[m] = kron_size(h.ell, h.d, m);
+    }
+  }
+  for (int m = 0; m < h.d; ++m) {
+    if (prm.sketch == TKS_SKETCH_KRP) {
+      h.S[m] = h.s[m];
+    } else {
+      int64_t S = 1;
+      for (int j = 0; j < h.d; ++j)
+        if (j != m) S *= h.s[j];
+      if (S > 8192) return fail(TKS_EUNSUPPORTED, where + "Kronecker sketch wider than 8192 columns");
+      h.S[m] = (int)S;
+    }
+    h.b[m] = (int)std::min<int64_t>(h.n[m], h.S[m]);
+    if (h.b[m] > TKS_MAX_BASIS) return fail(TKS_EUNSUPPORTED, where + "basis wider than TKS_MAX_BASIS");
+    h.rmax[m] = std::min(h.target[m], h.b[m]);
+  }
+  (void)prm;
+  return TKS_OK;
+}
+
+void count_flops(ProbHost& h, int kron) {
+  const int d = h.d;
+  double low = 0.0, f64 = 0.0;
+  for (int m = 0; m < d; ++m) low += 2.0 * h.n[m] * h.R[m] * h.s[m];               // (a)
+  for (int k = 0; k < h.K; ++k) {
+    const int* r = &h.ranks[(size_t)k * d];
+    const double pr = (double)prod(r, d);
+    for (int n = 0; n < d; ++n) {                                                  // (b1)
+      if (!kron) {
+        low += 2.0 * h.s[0] * pr;
+      } else {
+        double cur = pr;
+        for (int j = 0; j < d; ++j) {
+          if (j == n) continue;
+          low += 2.0 * h.s[j] * cur;
+          cur = cur / r[j] * h.s[j];
+        }
+      }
+    }
+    double cur = pr;                                                               // (c2)
+    for (int t = 0; t + 1 < d; ++t) {
+      low += 2.0 * h.b[t] * cur;
+      cur = cur / r[t] * h.b[t];
+    }
+  }
+  double Pd = 1;
+  for (int j = 0; j + 1 < d; ++j) Pd *= h.b[j];
+  for (int n = 0; n < d; ++n) {
+    low += 2.0 * h.n[n] * h.R[n] * h.S[n];                                         // (b2)
+    low += 2.0 * h.b[n] * h.n[n] * h.R[n];                                         // (c1)
+    f64 += 4.0 * h.n[n] * (double)h.b[n] * h.b[n];                                 // QR + Q
+  }
+  low += 2.0 * h.b[d - 1] * h.R[d - 1] * Pd;                                       // (c3)
+  double cur[MAXD];
+  for (int j = 0; j < d; ++j) cur[j] = h.b[j];
+  for (int n = 0; n < d; ++n) {                                                    // ST-HOSVD
+    double rest = 1;
+    for (int j = 0; j < d; ++j)
+      if (j != n) rest *= cur[j];
+    f64 += 2.0 * h.b[n] * h.b[n] * rest + 2.0 * h.b[n] * h.rmax[n] * rest + 2.0 * h.n[n] * h.b[n] * h.rmax[n];
+    cur[n] = h.rmax[n];
+  }
+  h.flops_low = low;
+  h.flops_f64 = f64;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* tks_last_error(void) { return g_last_error.c_str(); }
+
+const char* tks_status_string(tks_status s) {
+  switch (s) {
+    case TKS_OK: return "TKS_OK";
+    case TKS_EINVAL: return "TKS_EINVAL";
+    case TKS_ENOMEM: return "TKS_ENOMEM";
+    case TKS_ECUDA: return "TKS_ECUDA";
+    case TKS_ETIMEOUT: return "TKS_ETIMEOUT";
+    case TKS_ENONFINITE: return "TKS_ENONFINITE";
+    case TKS_ENOCONV: return "TKS_ENOCONV";
+    case TKS_EUNSUPPORTED: return "TKS_EUNSUPPORTED";
+  }
+  return "TKS_UNKNOWN";
+}
+
+void tks_plan_destroy(tks_plan* plan) {
+  if (!plan) return;
+  plan->profile_clear();
+  if (plan->arena_dev) cudaFree(plan->arena_dev);
+  delete plan;
+}
+
+tks_status tks_plan_create(tks_plan** out, const tks_problem* problems, int32_t num_problems,
+                           const tks_params* params) {
+  if (!out) return fail(TKS_EINVAL, "plan output pointer is NULL");
+  *out = nullptr;
+  if (!problems || !params || num_problems < 1) return fail(TKS_EINVAL, "no problems or params");
+  const tks_params prm = *params;
+  if (prm.sketch != TKS_SKETCH_KRP && prm.sketch != TKS_SKETCH_KRON) return fail(TKS_EINVAL, "bad sketch");
+  if (!(prm.trunc_tol >= 0.0) || !std::isfinite(prm.trunc_tol)) return fail(TKS_EINVAL, "bad trunc_tol");
+  if (prm.precision == TKS_FP64) {
+    if (prm.dtype != TKS_DT_F64) return fail(TKS_EINVAL, "TKS_FP64 needs float64 cores and factors");
+  } else if (prm.precision == TKS_MIXED) {
+    if (prm.dtype != TKS_DT_BF16) return fail(TKS_EINVAL, "TKS_MIXED needs bfloat16 cores and factors");
+    return fail(TKS_EUNSUPPORTED, "TKS_MIXED is not available in this build");
+  } else {
+    return fail(TKS_EINVAL, "bad precision");
+  }
+
+  auto* plan = new tks_plan();
+  plan->params = prm;
+  plan->nprob = num_problems;
+  plan->probs.resize(num_problems);
+  const int kron = prm.sketch == TKS_SKETCH_KRON;
+  for (int p = 0; p < num_problems; ++p) {
+    tks_status st = validate_and_size(problems[p], prm, plan->probs[p], p);
+    if (st != TKS_OK) {
+      delete plan;
+      return st;
+    }
+    count_flops(plan->probs[p], kron);
+    plan->flops_low += plan->probs[p].flops_low;
+    plan->flops_f64 += plan->probs[p].flops_f64;
+    plan->dmax = std::max(plan->dmax, plan->probs[p].d);
+    for (int m = 0; m < plan->probs[p].d; ++m) plan->bmax = std::max(plan->bmax, plan->probs[p].b[m]);
+  }
+
+  // ---- caller-visible buffer layouts (elements) and workspace (bytes)
+  size_t ws = 0;
+  auto alloc = [&](size_t bytes) {
+    const size_t o = ws;
+    ws = align_up(ws + std::max<size_t>(bytes, 1));
+    return o;
+  };
+  for (auto& h : plan->probs) {
+    for (int m = 0; m < h.d; ++m) {
+      h.omega_off[m] = plan->omega_elems;
+      plan->omega_elems += h.n[m] * h.s[m];
+      h.y_off[m] = plan->sketch_elems;
+      plan->sketch_elems += h.n[m] * h.S[m];
+      h.q_off[m] = plan->basis_elems;
+      plan->basis_elems += h.n[m] * h.b[m];
+    }
+    h.h_off = plan->core_elems;
+    plan->core_elems += prod(h.b, h.d);
+    h.out_core_off = plan->output_elems;
+    plan->output_elems += prod(h.rmax, h.d);
+    for (int m = 0; m < h.d; ++m) {
+      h.out_fac_off[m] = plan->output_elems;
+      plan->output_elems += h.n[m] * h.rmax[m];
+    }
+  }
+  plan->ws_omega = alloc(plan->omega_elems * 8);
+  plan->ws_Y = alloc(plan->sketch_elems * 8);
+  plan->ws_Q = alloc(plan->basis_elems * 8);
+  plan->ws_H = alloc(plan->core_elems * 8);
+  for (auto& h : plan->probs) {
+    const int d = h.d;
+    for (int m = 0; m < d; ++m) {
+      h.M[m] = alloc((size_t)h.R[m] * h.s[m] * 8);
+      h.V[m] = alloc((size_t)h.R[m] * h.S[m] * 8);
+      h.W[m] = alloc((size_t)h.n[m] * h.S[m] * 8);
+      h.tau[m] = alloc((size_t)h.S[m] * 8);
+      h.A[m] = alloc((size_t)h.b[m] * h.R[m] * 8);
+      h.P[m] = alloc((size_t)h.b[m] * h.rmax[m] * 8);
+      h.ev[m] = alloc((size_t)h.b[m] * 8);
+    }
+    int64_t Pd = 1;
+    for (int j = 0; j + 1 < d; ++j) Pd *= h.b[j];
+    h.T = alloc((size_t)h.R[d - 1] * Pd * 8);
+    h.chain.resize((size_t)2 * h.K);
+    for (int k = 0; k < h.K; ++k) {
+      const int* r = &h.ranks[(size_t)k * d];
+      int64_t mx = 1;
+      for (int t = 0; t + 2 < d; ++t) {     // sizes after chain steps 0..d-3
+        int64_t sz = 1;
+        for (int j = 0; j <= t; ++j) sz *= h.b[j];
+        for (int j = t + 1; j < d; ++j) sz *= r[j];
+        mx = std::max(mx, sz);
+      }
+      h.chain[2 * k] = alloc(mx * 8);
+      h.chain[2 * k + 1] = alloc(mx * 8);
+    }
+    int bm = 0;
+    for (int m = 0; m < d; ++m) bm = std::max(bm, h.b[m]);
+    h.gram = alloc((size_t)bm * bm * 8);
+    int64_t Hsz = prod(h.b, d);
+    // split-K for the ST-HOSVD Gram matrices: enough chunks to occupy the SMs across problems
+    int64_t kmax = Hsz / std::max(1, h.b[0]);
+    int ks = (int)std::max<int64_t>(1, std::min<int64_t>(kmax / 512, (2 * 152 + plan->nprob - 1) / plan->nprob));
+    h.gram_ksplit = ks;
+    h.part = alloc((size_t)ks * bm * bm * 8);
+    h.theta = alloc(8);
+    h.Hp[0] = alloc(Hsz * 8);
+    h.Hp[1] = alloc(Hsz * 8);
+  }
+  plan->ws_bytes = align_up(ws);
+
+  // ---- launch tables
+  std::vector<OmegaJob> om_ext, om_int;
+  int64_t om_blocks = 0;
+  GemmList gM, gY, gA, gH;
+  std::vector<CoreSketchJob> cs;
+  int64_t cs_total = 0;
+  std::vector<QrJob> qr;
+  double cs_flops = 0.0, cs_bytes = 0.0, qr_flops = 0.0, qr_bytes = 0.0;
+  std::vector<GemmList> chain(std::max(1, plan->dmax - 1));
+  for (int p = 0; p < plan->nprob; ++p) {
+    auto& h = plan->probs[p];
+    const int d = h.d;
+    for (int m = 0; m < d; ++m) {
+      OmegaJob oj;
+      std::memset(&oj, 0, sizeof(oj));
+      oj.out = op(B_OMEGA, h.omega_off[m] * 8);
+      oj.count = h.n[m] * h.s[m];
+      oj.begin = om_blocks;
+      oj.problem = p;
+      oj.mode = m;
+      oj.bf16 = prm.precision == TKS_MIXED;
+      om_blocks += (oj.count + 3) / 4;
+      om_ext.push_back(oj);
+      // (a) M_m = Ucat_m^T Omega_m  (R_m x s_m)
+      gM.add(gemm(h.R[m], h.s[m], (int)h.n[m], op_abs(h.factors[m]), h.n[m], 1,
+                  op(B_OMEGA, h.omega_off[m] * 8), h.n[m], 1, op(B_WS, h.M[m]), 1, h.R[m]));
+    }
+    for (int k = 0; k < h.K; ++k) {
+      for (int n = 0; n < d; ++n) {
+        CoreSketchJob j;
+        std::memset(&j, 0, sizeof(j));
+        j.core = op_abs(h.cores, (size_t)h.core_off[k] * 8);
+        for (int m = 0; m < d; ++m) {
+          j.M[m] = op(B_WS, h.M[m]);
+          j.r[m] = h.ranks[(size_t)k * d + m];
+          j.roff[m] = h.roff[(size_t)k * d + m];
+          j.R[m] = h.R[m];
+          j.s[m] = h.s[m];
+        }
+        j.V = op(B_WS, h.V[n]);
+        j.d = d;
+        j.n = n;
+        j.kron = kron;
+        j.S = h.S[n];
+        j.Rn = h.R[n];
+        j.alpha = h.alpha[k];
+        j.count = (int64_t)j.r[n] * j.S;
+        {
+          double other = 1.0;
+          for (int m = 0; m < d; ++m)
+            if (m != n) other *= j.r[m];
+          cs_flops += 2.0 * (double)j.count * other;
+          cs_bytes += 8.0 * ((double)j.count * (1.0 + 0.0) + other * j.r[n]);
+        }
+        j.begin = cs_total;
+        cs_total += j.count;
+        cs.push_back(j);
+      }
+    }
+    for (int n = 0; n < d; ++n) {
+      // (b) Y_n = Ucat_n Vcat_n  (n x S)
+      gY.add(gemm((int)h.n[n], h.S[n], h.R[n], op_abs(h.factors[n]), 1, h.n[n], op(B_WS, h.V[n]), h.R[n],
+                  1, op(B_Y, h.y_off[n] * 8), 1, h.n[n]));
+      QrJob q;
+      std::memset(&q, 0, sizeof(q));
+      q.Y = op(B_Y, h.y_off[n] * 8);
+      q.W = op(B_WS, h.W[n]);
+      q.Q = op(B_Q, h.q_off[n] * 8);
+      q.tau = op(B_WS, h.tau[n]);
+      q.n = (int)h.n[n];
+      q.S = h.S[n];
+      q.b = h.b[n];
+      qr.push_back(q);
+      qr_flops += 4.0 * (double)h.n[n] * h.b[n] * h.b[n];
+      qr_bytes += 8.0 * (double)h.n[n] * (h.S[n] + h.b[n]);
+      // (c1) A_n = Q_n^T Ucat_n  (b x R)
+      gA.add(gemm(h.b[n], h.R[n], (int)h.n[n], op(B_Q, h.q_off[n] * 8), h.n[n], 1, op_abs(h.factors[n]),
+                  h.n[n], 1, op(B_WS, h.A[n]), 1, h.b[n]));
+    }
+    // (c2) per-term chain T_k = G_k x_1 A_k1 ... x_{d-1} A_k,d-1, last step into Tcat (R_d x P)
+    const int Rd = h.R[d - 1];
+    for (int k = 0; k < h.K; ++k) {
+      const int* r = &h.ranks[(size_t)k * d];
+      const int rd_off = h.roff[(size_t)k * d + d - 1];
+      for (int t = 0; t + 1 < d; ++t) {
+        int64_t L = 1, Rr = 1;
+        for (int j = 0; j < t; ++j) L *= h.b[j];
+        for (int j = t + 1; j < d; ++j) Rr *= r[j];
+        const int I = r[t], Jn = h.b[t];
+        const Operand X = (t == 0) ? op_abs(h.cores, (size_t)h.core_off[k] * 8)
+                                   : op(B_WS, h.chain[2 * k + ((t - 1) & 1)]);
+        const Operand Ablk = op(B_WS, h.A[t] + (size_t)h.b[t] * h.roff[(size_t)k * d + t] * 8);
+        const bool last = (t == d - 2);
+        const Operand Y = last ? op(B_WS, h.T + (size_t)rd_off * 8) : op(B_WS, h.chain[2 * k + (t & 1)]);
+        const double alpha = (t == 0) ? h.alpha[k] : 1.0;
+        GemmJob j;
+        if (L == 1) {
+          // C[j, rr] = sum_i A[j, i] X[i + I rr]
+          j = gemm(Jn, (int)Rr, I, Ablk, 1, h.b[t], X, I, 1, Y, last ? Rd : 1, last ? 1 : Jn, alpha);
+        } else {
+          // C[l, j] = sum_i X[l + L i + L I rr] A[j + b_t i], batched over rr
+          j = gemm((int)L, Jn, I, X, 1, L, Ablk, 1, h.b[t], Y, last ? Rd : 1, last ? (int64_t)Rd * L : L, alpha);
+          j.batch = (int)Rr;
+          j.a_b = L * I;
+          j.c_b = last ? 1 : L * Jn;
+        }
+        chain[t].add(j);
+      }
+    }
+    // (c3) H_(d)^T = Tcat^T A_d^T  (P x b_d), written as the tensor H (mode 1 fastest)
+    int64_t Pd = 1;
+    for (int j = 0; j + 1 < d; ++j) Pd *= h.b[j];
+    gH.add(gemm((int)Pd, h.b[d - 1], Rd, op(B_WS, h.T), Rd, 1, op(B_WS, h.A[d - 1]), 1, h.b[d - 1],
+                op(B_H, h.h_off * 8), 1, Pd));
+  }
+  plan->push(plan->st_omega, S_OMEGA, om_ext, om_blocks, "a1:omega", 0.0, 8.0 * plan->omega_elems);
+  // sketch: Omega (workspace) -> M -> V -> Y
+  plan->push(plan->st_sketch, S_OMEGA, om_ext, om_blocks, "a1:omega", 0.0, 8.0 * plan->omega_elems);
+  plan->push_gemm(plan->st_sketch, gM, "a2:M=UcatT.Omega");
+  plan->push(plan->st_sketch, S_CORESKETCH, cs, cs_total, "a3:core_sketch", cs_flops, cs_bytes);
+  plan->push_gemm(plan->st_sketch, gY, "a4:Y=Ucat.Vcat");
+  // project: A -> chain -> H
+  plan->push_gemm(plan->st_project, gA, "a6:A=QT.Ucat");
+  for (size_t t = 0; t < chain.size(); ++t) {
+    char nm[32];
+    std::snprintf(nm, sizeof(nm), "a7:chain%d", (int)t);
+    plan->push_gemm(plan->st_project, chain[t], nm);
+  }
+  plan->push_gemm(plan->st_project, gH, "a8:H=Acat.Tcat");
+  // recompress: sketch, QR, project, ST-HOSVD
+  plan->st_recompress = plan->st_sketch;
+  plan->push(plan->st_recompress, S_QR, qr, (int64_t)qr.size(), "a5:qr", qr_flops, qr_bytes);
+  for (const auto& s : plan->st_project) plan->st_recompress.push_back(s);
+  for (int n = 0; n < plan->dmax; ++n) {
+    GemmList gram, ttm, fac;
+    std::vector<EigJob> eig;
+    for (int p = 0; p < plan->nprob; ++p) {
+      auto& h = plan->probs[p];
+      const int d = h.d;
+      if (n >= d) continue;
+      int64_t L = 1, Rr = 1;
+      for (int j = 0; j < n; ++j) L *= h.rmax[j];
+      for (int j = n + 1; j < d; ++j) Rr *= h.b[j];
+      const int b = h.b[n], rmax = h.rmax[n];
+      const Operand X = (n == 0) ? op(B_H, h.h_off * 8) : op(B_WS, h.Hp[(n - 1) & 1]);
+      // Gram B_n = H_(n) H_(n)^T: k = l + L rr
+      GemmJob g = gemm(b, b, (int)(L * Rr), X, L, 1, X, L, 1, op(B_WS, h.gram), 1, b);
+      g.K1 = (int)L;
+      g.a_k1 = L * b;
+      g.b_k1 = L * b;
+      g.ksplit = std::min<int>(h.gram_ksplit, std::max(1, (int)(L * Rr / 64)));
+      g.P = op(B_WS, h.part);
+      gram.add(g);
+      EigJob e;
+      std::memset(&e, 0, sizeof(e));
+      e.B = op(B_WS, h.gram);
+      e.P = op(B_WS, h.P[n]);
+      e.evals = op(B_WS, h.ev[n]);
+      e.theta = op(B_WS, h.theta);
+      e.rank = op(B_RANKS, (size_t)(p * TKS_MAX_ORDER + n) * 4);
+      e.b = b;
+      e.rmax = rmax;
+      e.target = h.target[n];
+      e.first_mode = (n == 0);
+      e.order = d;
+      e.tol = prm.trunc_tol;
+      eig.push_back(e);
+      const Operand Y = (n == d - 1) ? op(B_OUT, h.out_core_off * 8) : op(B_WS, h.Hp[n & 1]);
+      GemmJob t;
+      if (L == 1) {
+        t = gemm(rmax, (int)Rr, b, op(B_WS, h.P[n]), b, 1, X, b, 1, Y, 1, rmax);
+      } else {
+        t = gemm((int)L, rmax, b, X, 1, L, op(B_WS, h.P[n]), b, 1, Y, 1, L);
+        t.batch = (int)Rr;
+        t.a_b = L * b;
+        t.c_b = L * rmax;
+      }
+      ttm.add(t);
+      fac.add(gemm((int)h.n[n], rmax, b, op(B_Q, h.q_off[n] * 8), 1, h.n[n], op(B_WS, h.P[n]), b, 1,
+                   op(B_OUT, h.out_fac_off[n] * 8), 1, h.n[n]));
+    }
+    char nm[32];
+    std::snprintf(nm, sizeof(nm), "a9:gram%d", n);
+    plan->push_gemm(plan->st_recompress, gram, nm);
+    std::snprintf(nm, sizeof(nm), "a9:eig%d", n);
+    plan->push(plan->st_recompress, S_EIG, eig, (int64_t)eig.size(), nm);
+    std::snprintf(nm, sizeof(nm), "a9:ttm%d", n);
+    plan->push_gemm(plan->st_recompress, ttm, nm);
+    std::snprintf(nm, sizeof(nm), "a9:factor%d", n);
+    plan->push_gemm(plan->st_recompress, fac, nm);
+  }
+
+  // ---- device copies
+  if (cudaGetDevice(&plan->device) != cudaSuccess) {
+    tks_plan_destroy(plan);
+    return fail(TKS_ECUDA, "no CUDA device");
+  }
+  if (plan->bmax > 0) {
+    cudaError_t e = prepare_eig_f64(plan->bmax);
+    if (e != cudaSuccess) {
+      tks_plan_destroy(plan);
+      return fail(TKS_ECUDA, std::string("eigensolver shared memory: ") + cudaGetErrorString(e));
+    }
+  }
+  const size_t status_off = plan->add_table(&plan->nprob, 0);
+  plan->arena_host.resize(status_off + 64, 0);
+  if (cudaMalloc(&plan->arena_dev, plan->arena_host.size()) != cudaSuccess) {
+    tks_plan_destroy(plan);
+    return fail(TKS_ENOMEM, "descriptor tables");
+  }
+  if (cudaMemcpy(plan->arena_dev, plan->arena_host.data(), plan->arena_host.size(), cudaMemcpyHostToDevice) !=
+      cudaSuccess) {
+    tks_plan_destroy(plan);
+    return fail(TKS_ECUDA, "copying descriptor tables");
+  }
+  plan->status = reinterpret_cast<Status*>(plan->arena_dev + status_off);
+  *out = plan;
+  return TKS_OK;
+}
+
+tks_status tks_plan_info(const tks_plan* plan, tks_plan_info_t* info) {
+  if (!plan || !info) return fail(TKS_EINVAL, "null argument");
+  std::memset(info, 0, sizeof(*info));
+  info->workspace_bytes = plan->ws_bytes;
+  info->omega_elems = plan->omega_elems;
+  info->sketch_elems = plan->sketch_elems;
+  info->basis_elems = plan->basis_elems;
+  info->core_elems = plan->core_elems;
+  info->output_elems = plan->output_elems;
+  info->num_problems = plan->nprob;
+  info->launches_recompress = (int32_t)plan->st_recompress.size();
+  info->flops_lowprec = plan->flops_low;
+  info->flops_fp64 = plan->flops_f64;
+  return TKS_OK;
+}
+
+tks_status tks_problem_info(const tks_plan* plan, int32_t p, tks_problem_info_t* info) {
+  if (!plan || !info || p < 0 || p >= plan->nprob) return fail(TKS_EINVAL, "bad plan, problem or info");
+  std::memset(info, 0, sizeof(*info));
+  const auto& h = plan->probs[p];
+  info->order = h.d;
+  for (int m = 0; m < h.d; ++m) {
+    info->R[m] = h.R[m];
+    info->omega_cols[m] = h.s[m];
+    info->sketch_cols[m] = h.S[m];
+    info->basis_cols[m] = h.b[m];
+    info->max_ranks[m] = h.rmax[m];
+    info->omega_off[m] = h.omega_off[m];
+    info->sketch_off[m] = h.y_off[m];
+    info->basis_off[m] = h.q_off[m];
+    info->out_factor_off[m] = h.out_fac_off[m];
+  }
+  info->core_off = h.h_off;
+  info->out_core_off = h.out_core_off;
+  return TKS_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+tks_status run_steps(tks_plan* plan, const std::vector<Step>& steps, const Bases& bases, cudaStream_t stream,
+                     bool profile = false) {
+  cudaEvent_t* ev = nullptr;
+  if (profile && plan->prof_calls < plan->prof_max_calls) {
+    ev = plan->prof_events.data() + (size_t)plan->prof_calls * (steps.size() + 1);
+    ++plan->prof_calls;
+  }
+  for (size_t i = 0; i < steps.size(); ++i) {
+    const Step& s = steps[i];
+    if (ev) cudaEventRecord(ev[i], stream);
+    const void* table = plan->arena_dev + s.table_off;
+    switch (s.kind) {
+      case S_OMEGA:
+        launch_omega(static_cast<const OmegaJob*>(table), s.njobs, s.work, bases, plan->params.seed, stream);
+        break;
+      case S_GEMM:
+        launch_gemm_f64(static_cast<const GemmJob*>(table), s.njobs, (int)s.work, bases, stream);
+        break;
+      case S_REDUCE:
+        launch_splitk_reduce_f64(static_cast<const GemmJob*>(table), s.njobs, s.work, bases, stream);
+        break;
+      case S_CORESKETCH:
+        launch_core_sketch_f64(static_cast<const CoreSketchJob*>(table), s.njobs, s.work, bases, stream);
+        break;
+      case S_QR:
+        launch_qr_f64(static_cast<const QrJob*>(table), s.njobs, bases, plan->status, stream);
+        break;
+      case S_EIG:
+        launch_eig_f64(static_cast<const EigJob*>(table), s.njobs, plan->bmax, bases, plan->status, stream);
+        break;
+    }
+  }
+  if (ev) cudaEventRecord(ev[steps.size()], stream);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(TKS_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+  return TKS_OK;
+}
+
+Bases bind(tks_plan* plan, void* ws) {
+  Bases b;
+  std::memset(&b, 0, sizeof(b));
+  char* w = static_cast<char*>(ws);
+  b.p[B_WS] = w;
+  b.p[B_OMEGA] = w + plan->ws_omega;
+  b.p[B_Y] = w + plan->ws_Y;
+  b.p[B_Q] = w + plan->ws_Q;
+  b.p[B_H] = w + plan->ws_H;
+  return b;
+}
+
+tks_status check_ws(tks_plan* plan, void* ws) {
+  if (!plan) return fail(TKS_EINVAL, "null plan");
+  if (!ws && plan->ws_bytes > 0) return fail(TKS_EINVAL, "null workspace");
+  if (reinterpret_cast<uintptr_t>(ws) % kAlign) return fail(TKS_EINVAL, "workspace not 256-byte aligned");
+  return TKS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+tks_status tks_generate_omega(tks_plan* plan, void* workspace, double* omega_out, void* stream) {
+  tks_status st = check_ws(plan, workspace);
+  if (st != TKS_OK) return st;
+  if (!omega_out) return fail(TKS_EINVAL, "null omega_out");
+  Bases b = bind(plan, workspace);
+  b.p[B_OMEGA] = reinterpret_cast<char*>(omega_out);
+  return run_steps(plan, plan->st_omega, b, static_cast<cudaStream_t>(stream));
+}
+
+tks_status tucker_sum_sketch(tks_plan* plan, void* workspace, double* Y_out, void* stream) {
+  tks_status st = check_ws(plan, workspace);
+  if (st != TKS_OK) return st;
+  if (!Y_out) return fail(TKS_EINVAL, "null Y_out");
+  Bases b = bind(plan, workspace);
+  b.p[B_Y] = reinterpret_cast<char*>(Y_out);
+  return run_steps(plan, plan->st_sketch, b, static_cast<cudaStream_t>(stream));
+}
+
+tks_status tks_project_core(tks_plan* plan, void* workspace, const double* Q_in, double* H_out, void* stream) {
+  tks_status st = check_ws(plan, workspace);
+  if (st != TKS_OK) return st;
+  if (!Q_in || !H_out) return fail(TKS_EINVAL, "null Q_in or H_out");
+  Bases b = bind(plan, workspace);
+  b.p[B_Q] = reinterpret_cast<char*>(const_cast<double*>(Q_in));
+  b.p[B_H] = reinterpret_cast<char*>(H_out);
+  return run_steps(plan, plan->st_project, b, static_cast<cudaStream_t>(stream));
+}
+
+tks_status tucker_sum_recompress(tks_plan* plan, void* workspace, double* out, int32_t* ranks_out, void* stream) {
+  tks_status st = check_ws(plan, workspace);
+  if (st != TKS_OK) return st;
+  if (!out || !ranks_out) return fail(TKS_EINVAL, "null out or ranks_out");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  TKS_CUDA_CHECK(cudaMemsetAsync(ranks_out, 0, (size_t)plan->nprob * TKS_MAX_ORDER * sizeof(int32_t), s));
+  TKS_CUDA_CHECK(cudaMemsetAsync(out, 0, (size_t)plan->output_elems * sizeof(double), s));
+  Bases b = bind(plan, workspace);
+  b.p[B_OUT] = reinterpret_cast<char*>(out);
+  b.p[B_RANKS] = reinterpret_cast<char*>(ranks_out);
+  return run_steps(plan, plan->st_recompress, b, s, true);
+}
+
+tks_status tks_profile_begin(tks_plan* plan, int32_t max_calls) {
+  if (!plan || max_calls < 1) return fail(TKS_EINVAL, "bad plan or max_calls");
+  plan->profile_clear();
+  const size_t n = (size_t)max_calls * (plan->st_recompress.size() + 1);
+  plan->prof_events.resize(n);
+  for (size_t i = 0; i < n; ++i) {
+    if (cudaEventCreate(&plan->prof_events[i]) != cudaSuccess) {
+      plan->prof_events.resize(i);
+      plan->profile_clear();
+      return fail(TKS_ECUDA, "cudaEventCreate");
+    }
+  }
+  plan->prof_max_calls = max_calls;
+  plan->prof_calls = 0;
+  return TKS_OK;
+}
+
+tks_status tks_profile_end(tks_plan* plan, tks_step_profile_t* out, int32_t cap, int32_t* nsteps) {
+  if (!plan || !nsteps) return fail(TKS_EINVAL, "bad plan or nsteps");
+  const size_t ns = plan->st_recompress.size();
+  *nsteps = (int32_t)ns;
+  const int calls = plan->prof_calls;
+  if (calls > 0) {
+    cudaError_t e = cudaEventSynchronize(plan->prof_events[(size_t)calls * (ns + 1) - 1]);
+    if (e != cudaSuccess) {
+      plan->profile_clear();
+      return fail(TKS_ECUDA, std::string("cudaEventSynchronize: ") + cudaGetErrorString(e));
+    }
+  }
+  for (size_t i = 0; i < ns && out && (int32_t)i < cap; ++i) {
+    const Step& s = plan->st_recompress[i];
+    tks_step_profile_t& o = out[i];
+    std::memset(&o, 0, sizeof(o));
+    std::snprintf(o.name, sizeof(o.name), "%s", s.name);
+    o.kind = (int32_t)s.kind;
+    o.calls = calls;
+    o.flops = s.flops;
+    o.bytes = s.bytes;
+    double ms = 0.0;
+    for (int c = 0; c < calls; ++c) {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, plan->prof_events[(size_t)c * (ns + 1) + i],
+                           plan->prof_events[(size_t)c * (ns + 1) + i + 1]);
+      ms += t;
+    }
+    o.ms = ms;
+  }
+  plan->profile_clear();
+  return TKS_OK;
+}
+
+tks_status tks_sync_status(tks_plan* plan, void* stream) {
+  if (!plan) return fail(TKS_EINVAL, "null plan");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  TKS_CUDA_CHECK(cudaStreamSynchronize(s));
+  Status h{0, 0};
+  TKS_CUDA_CHECK(cudaMemcpy(&h, plan->status, sizeof(h), cudaMemcpyDeviceToHost));
+  if (h.code != 0) {
+    const Status zero{0, 0};
+    TKS_CUDA_CHECK(cudaMemcpy(plan->status, &zero, sizeof(zero), cudaMemcpyHostToDevice));
+    return fail(static_cast<tks_status>(h.code), std::string("device reported ") +
+                                                     tks_status_string(static_cast<tks_status>(h.code)));
+  }
+  return TKS_OK;
+}
+
+}  // extern "C"

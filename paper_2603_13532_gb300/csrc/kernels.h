@@ -1,0 +1,28 @@
+// Launch wrappers of the stage kernels (all asynchronous on `stream`).
+#pragma once
+
+#include "tks_internal.h"
+
+namespace tks {
+
+// Gaussian Omega (float64, or bf16-rounded values stored as float64 when job.bf16).
+void launch_omega(const OmegaJob* jobs, int njobs, int64_t total_blocks, const Bases& bases,
+                  uint64_t seed, cudaStream_t stream);
+// Grouped strided float64 GEMM; split-K jobs are finished by launch_splitk_reduce_f64.
+void launch_gemm_f64(const GemmJob* jobs, int njobs, int total_tiles, const Bases& bases,
+                     cudaStream_t stream);
+void launch_splitk_reduce_f64(const GemmJob* jobs, int njobs, int64_t total_elems,
+                              const Bases& bases, cudaStream_t stream);
+// Khatri-Rao / Kronecker core sketch V_kn (float64).
+void launch_core_sketch_f64(const CoreSketchJob* jobs, int njobs, int64_t total, const Bases& bases,
+                            cudaStream_t stream);
+// Householder QR, one CTA per job.
+void launch_qr_f64(const QrJob* jobs, int njobs, const Bases& bases, Status* status,
+                   cudaStream_t stream);
+// Jacobi eigensolver + rank selection, one CTA per job; smem_bytes from eig_smem_bytes().
+size_t eig_smem_bytes(int bmax);
+cudaError_t prepare_eig_f64(int bmax);   // raises the dynamic shared memory limit
+void launch_eig_f64(const EigJob* jobs, int njobs, int bmax, const Bases& bases, Status* status,
+                    cudaStream_t stream);
+
+}  // namespace tks

@@ -1,0 +1,115 @@
+// Internal descriptor tables shared by the host planner and the kernels.
+//
+// Every operand in a launch table is (base id, byte offset).  Base ids name the
+// buffers an execute call binds: the workspace, the caller's output buffers and
+// "absolute" (the offset is a device address remembered at plan time, used for
+// the caller's input cores and factors).  Binding at launch time lets one plan
+// serve every entry point without copying tables again.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tks.h"
+
+namespace tks {
+
+constexpr int MAXD = TKS_MAX_ORDER;
+
+enum BaseId : int32_t {
+  B_ABS = -1,    // offset is an absolute device address
+  B_WS = 0,      // workspace
+  B_OMEGA = 1,   // Omega buffer (caller's for tks_generate_omega, else workspace)
+  B_Y = 2,       // sketch buffer
+  B_Q = 3,       // basis buffer
+  B_H = 4,       // projected core buffer
+  B_OUT = 5,     // recompression output (cores and factors)
+  B_RANKS = 6,   // recompression output ranks (int32)
+  NBASE = 7
+};
+
+struct Bases {
+  char* p[NBASE];
+};
+
+struct Operand {
+  int32_t base;
+  int32_t pad;
+  int64_t off;   // bytes
+};
+
+template <typename T>
+__host__ __device__ inline T* at(const Bases& b, const Operand& o) {
+  return reinterpret_cast<T*>(o.base < 0 ? reinterpret_cast<char*>(o.off) : b.p[o.base] + o.off);
+}
+
+// ---------------------------------------------------------------------------
+// Generic strided float64 GEMM job: C[i,j] = alpha * sum_k A[i,k] B[k,j] (+ beta C).
+// The reduction index k splits into k0 = k % K1, k1 = k / K1 with separate strides so
+// that an unfolding whose columns are a two-level index (e.g. the Gram matrix of a
+// mode-n unfolding) is a single job.  batch repeats the job with extra strides.
+// With ksplit > 1 each K chunk writes partial sums to P (ksplit x batch x M x N,
+// column-major) and a second kernel adds the chunks in order, so the result does
+// not depend on scheduling.
+struct GemmJob {
+  int32_t M, N, K, K1;
+  int32_t batch, ksplit, kchunk;
+  int32_t tiles_m, tiles_n;
+  int32_t tile_begin;
+  int64_t red_begin;            // prefix over split jobs of batch * M * N (reduction kernel)
+  Operand A, B, C, P;
+  int64_t a_m, a_k0, a_k1, a_b;
+  int64_t b_n, b_k0, b_k1, b_b;
+  int64_t c_m, c_n, c_b;
+  double alpha, beta;
+};
+
+// Gaussian draws of one (problem, mode): Omega (n x s, column-major).
+struct OmegaJob {
+  Operand out;
+  int64_t count;       // n * s
+  int64_t begin;       // prefix over jobs (elements)
+  int32_t problem, mode;
+  int32_t bf16;        // round to float32 then bfloat16
+  int32_t pad;
+};
+
+// Structured core sketch of one (term, mode n): V_kn (r_kn x S_n) into rows
+// [roff_n, roff_n + r_kn) of Vcat_n (R_n x S_n, column-major).
+struct CoreSketchJob {
+  Operand core;                 // G_k, float64, mode 1 fastest
+  Operand M[MAXD];              // M_j = Ucat_j^T Omega_j (R_j x s_j), float64
+  Operand V;                    // Vcat_n
+  int32_t d, n, kron;
+  int32_t r[MAXD];
+  int32_t roff[MAXD];
+  int32_t R[MAXD];
+  int32_t s[MAXD];              // Omega columns per mode
+  int32_t S;                    // columns of V (s for KRP, prod_{j != n} s_j for Kron)
+  int32_t Rn;                   // leading dimension of Vcat_n
+  double alpha;
+  int64_t count;                // r_kn * S
+  int64_t begin;
+};
+
+// Householder QR of Y (n x S) giving Q (n x b), b = min(n, S), diag(R) >= 0.
+struct QrJob {
+  Operand Y, W, Q, tau;         // W: n x S work copy, tau: S doubles
+  int32_t n, S, b, pad;
+};
+
+// Symmetric eigendecomposition of a Gram matrix B (b x b) by cyclic Jacobi, then
+// rank selection (Alg. 2 rank rule) and P = leading eigenvectors (b x rmax, zero-padded).
+struct EigJob {
+  Operand B, P, evals, theta, rank;
+  int32_t b, rmax, target, first_mode;
+  int32_t order, pad;
+  double tol;                   // 0: rank = rmax
+};
+
+struct Status {
+  int32_t code;                 // first tks_status recorded by a kernel
+  int32_t pad;
+};
+
+}  // namespace tks
