@@ -1,0 +1,374 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the sketched Tucker-sum recompression on GB300.
+
+A step is one tucker_sum_recompress call over a batch of P independent Tucker sums of the
+decay512 shape (d=3, n=512, K=32 terms with ranks ~ U{8..32} per mode, Khatri-Rao sketch,
+target rank 48, oversampling 10; seeded synthetic inputs already resident in HBM).  The
+value is recompressions per second over all ranks.  Under torchrun every rank runs its own
+batch on its own GPU (weak scaling, no data-path collective).
+
+Also reported on the same JSON line:
+  e2e           the same metric with the inputs copied from pinned host memory and the
+                result read back inside every timed step
+  roofline      the dominant launch: algorithmic flops (or bytes) per launch / its average
+                CUDA-event duration inside the timed region, against the measured peak
+  cpu_baseline  the FP64 oracle timed on this host's cores on a bounded sample
+  fp64_path     (mixed precision only) the plain FP64 GPU path on the same batch
+  clocks        nvidia-smi SM clocks and throttle reasons sampled during the timed region
+
+``--impl reference`` times the FP64 CPU oracle (the reference arm) instead.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Tucker-sum recompressions/s & TFLOP/s vs plain FP64 GPU path at ≤1e-5 rel err"
+UNIT = "recompressions/s"
+L2_BYTES = 129e6
+# float64 peak from unit counts and clocks: 152 SMs x 2 FP64 FMA (4 flops) per clock x 2070 MHz
+FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12
+FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--problems", type=int, default=64, help="independent sums per step and GPU")
+    ap.add_argument("--seed", type=int, default=20260315)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0, help="budget of the cpu_baseline sample")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--measure-peaks", action="store_true", help="print FP64/FP32/TF32/BF16 GEMM rates")
+    return ap.parse_args()
+
+
+def workload_label(P):
+    return (f"decay512 x{P}: d=3, n=512, K=32, r~U{{8..32}}, mode spectra 10^(-i/8), Khatri-Rao, "
+            f"target 48, oversampling 10")
+
+
+def make_problems(P, seed, rank, bf16):
+    from paper_2603_13532_gb300 import workloads as wl
+    probs = []
+    for i in range(P):
+        probs += wl.decay512(seed=seed + 7919 * (rank * P + i), bf16=bf16).problems
+    return probs
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return dict(FALLBACK), "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+CLOCK_FIELDS = ["index", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+                "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+                "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+
+class ClockSampler:
+    def __init__(self):
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + ",".join(CLOCK_FIELDS),
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self, gpu_index):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) == len(CLOCK_FIELDS):
+                    rows.append(parts)
+        os.unlink(self.path)
+        idxs = sorted({r[0] for r in rows})
+        pick = idxs[0] if len(idxs) == 1 else str(gpu_index)
+        rows = [r for r in rows if r[0] == pick]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for name, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows),
+                "power_w_max": max((num(r[3]) or 0.0) for r in rows)}
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_rate(problems, seed0, budget_s, kind, rounding):
+    """Recompressions/s of the FP64 oracle over as many problems as fit in budget_s."""
+    from oracle import sketch_sum as ss
+    done, t0 = 0, time.perf_counter()
+    for i, p in enumerate(problems):
+        ss.recompress(p.terms(), kind, p.target, p.oversampling, seed=seed0, problem=i, rounding=rounding)
+        done += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return done / dt, done, dt
+
+
+def run_reference(args, rank, world):
+    import torch.distributed as dist
+    if rank != 0:
+        return
+    from paper_2603_13532_gb300 import workloads as wl
+    bf16 = args.precision == "mixed"
+    per_step = 2
+    probs = make_problems(per_step * (args.steps + args.warmup), args.seed, 0, bf16)
+    rounding = "bf16" if bf16 else None
+    from oracle import sketch_sum as ss
+    times = []
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        for i in range(per_step):
+            p = probs[s * per_step + i]
+            ss.recompress(p.terms(), "krp", p.target, p.oversampling, seed=args.seed, problem=i, rounding=rounding)
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = per_step * len(times) / total
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": workload_label(per_step) + " (reference arm: float64 CPU oracle)",
+                       "problems_per_step": per_step, "parallelism": "host cores"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} problems per step, {args.steps} timed steps"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    del wl, dist
+
+
+# ------------------------------------------------------------------ GPU arm
+def time_steps(fn, steps, stream):
+    import torch
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for _ in range(steps):
+        fn()
+    end.record(stream)
+    end.synchronize()
+    return start.elapsed_time(end) / 1e3
+
+
+def roofline_from_profile(prof, calls, peaks, peak_kind):
+    """The dominant launch of the profiled calls and its achieved rate against its peak."""
+    total_ms = sum(s["ms"] for s in prof)
+    # the longest launch that has an algorithmic flop or byte count (the iterative eigensolver
+    # has none); its share of the call is reported next to it
+    counted = [s for s in prof if s["flops"] > 0 or s["bytes"] > 0]
+    top = max(counted or prof, key=lambda s: s["ms"])
+    overall_top = max(prof, key=lambda s: s["ms"])
+    avg_s = top["ms"] / 1e3 / max(1, calls)
+    if top["kind"] in ("gemm", "qr", "core_sketch") and top["flops"] > 0 and peak_kind == "fp64":
+        achieved = top["flops"] / avg_s / 1e12
+        peak = FP64_PEAK_TFLOPS
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz"}
+    else:
+        achieved = top["bytes"] / avg_s / 1e9
+        peak = peaks["hbm_gbs"]
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "peak_source": "MEASURED_PEAKS hbm_gbs"}
+    roof["kernel"] = top["name"]
+    roof["kernel_share"] = top["ms"] / total_ms if total_ms > 0 else None
+    roof["avg_launch_ms"] = avg_s * 1e3
+    if overall_top is not top:
+        roof["longest_launch"] = {"name": overall_top["name"],
+                                  "share": overall_top["ms"] / total_ms if total_ms > 0 else None}
+    return roof
+
+
+def main():
+    args = parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.measure_peaks:
+        measure_peaks()
+        return
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo" if args.impl == "reference" else "nccl")
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+
+    import numpy as np
+    import torch
+    from paper_2603_13532_gb300 import binding
+
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    bf16 = args.precision == "mixed"
+    P = args.problems
+    problems = make_problems(P, args.seed, rank, bf16)
+    plan = binding.Plan(problems, kind="krp", precision=args.precision, seed=args.seed, device=device)
+    out = torch.zeros(plan.info.output_elems, dtype=torch.float64, device=device)
+    ranks_t = torch.zeros(P * binding.MAX_ORDER, dtype=torch.int32, device=device)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        plan.recompress_raw(out, ranks_t)
+
+    for _ in range(args.warmup):
+        step()
+    plan.sync()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler()
+    clocks.start()
+    plan.profile_begin(args.steps)
+    elapsed = time_steps(step, args.steps, stream)
+    prof = plan.profile_end()
+    clock_info = clocks.stop(local)
+    plan.sync()
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([elapsed], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+        dist.barrier()
+    ms_per_step = 1e3 * elapsed / args.steps
+    value = P * world * args.steps / elapsed
+    tflops = (plan.info.flops_lowprec + plan.info.flops_fp64) * world * args.steps / elapsed / 1e12
+
+    peaks, peak_src = load_peaks()
+    roof = roofline_from_profile(prof, args.steps, peaks, "fp64" if args.precision == "fp64" else "mixed")
+    roof["peak_file"] = peak_src
+
+    # end to end: pinned host inputs -> device, recompress, result -> pinned host, every step
+    e2e = None
+    if not args.no_e2e:
+        host_in, _ = binding.pack_inputs(problems, plan.dtype, "cpu", pin=True)
+        host_out = torch.empty_like(out, device="cpu").pin_memory()
+        host_ranks = torch.empty_like(ranks_t, device="cpu").pin_memory()
+
+        def e2e_step():
+            plan.flat_inputs.copy_(host_in, non_blocking=True)
+            plan.recompress_raw(out, ranks_t)
+            host_out.copy_(out, non_blocking=True)
+            host_ranks.copy_(ranks_t, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        e_el = time_steps(e2e_step, args.steps, stream)
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([e_el], dtype=torch.float64, device=device)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_el = float(t.item())
+        e2e = {"value": P * world * args.steps / e_el, "unit": UNIT,
+               "h2d_bytes_per_step": int(host_in.numel() * host_in.element_size()),
+               "d2h_bytes_per_step": int(host_out.numel() * 8 + host_ranks.numel() * 4)}
+
+    line = None
+    if rank == 0:
+        in_bytes = plan.flat_inputs.numel() * plan.flat_inputs.element_size()
+        cpu = None
+        if not args.no_cpu:
+            rate, done, dt = oracle_rate(problems, args.seed, args.cpu_seconds, "krp",
+                                         "bf16" if bf16 else None)
+            cpu = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                   "sample": f"{done} of the {P} problems of this batch in {dt:.1f} s (numpy float64, "
+                             f"BLAS on all host cores)"}
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if args.precision == "fp64" else "bf16",
+                "data": "synthetic",
+                "config": {"workload": workload_label(P), "problems_per_step": P,
+                           "precision": args.precision, "tflops": tflops,
+                           "flops_per_step": plan.info.flops_lowprec + plan.info.flops_fp64,
+                           "l2": f"inputs {in_bytes / 1e6:.0f} MB per GPU > L2 129 MB, no flush",
+                           "parallelism": f"replicas x{world}"},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(plan.info.launches_recompress) * args.steps,
+                "clocks": clock_info,
+                "stages": [{"name": s["name"], "ms_per_call": s["ms"] / max(1, s["calls"])} for s in prof]}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    del np
+
+
+def measure_peaks():
+    import torch
+    dev = torch.device("cuda", 0)
+    out = {}
+    for name, dt, n, tf32 in [("fp64_tflops", torch.float64, 4096, False), ("fp32_tflops", torch.float32, 8192, False),
+                              ("tf32_tflops", torch.float32, 8192, True), ("bf16_tflops", torch.bfloat16, 8192, False)]:
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        a = torch.randn(n, n, device=dev, dtype=dt)
+        b = torch.randn(n, n, device=dev, dtype=dt)
+        for _ in range(3):
+            a @ b
+        torch.cuda.synchronize()
+        best = 1e9
+        for _ in range(5):
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record()
+            a @ b
+            e.record()
+            e.synchronize()
+            best = min(best, s.elapsed_time(e) / 1e3)
+        out[name] = 2 * n ** 3 / best / 1e12
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -118,30 +118,53 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
-def pack_problem(prob, dtype, device):
-    """Device tensors in the C-ABI layout: packed cores and Ucat_m (column-major)."""
+def pack_inputs(problems, dtype, device, pin=False):
+    """All problems' inputs in the C-ABI layout inside ONE flat buffer.
+
+    Returns (flat, views) where views[p] = (packed cores, [Ucat_1, ..., Ucat_d]) are views of
+    ``flat`` (column-major Ucat_m, cores back to back).  ``device="cpu", pin=True`` builds the
+    pinned host staging copy used by the end-to-end measurement.
+    """
     tdt = torch.float64 if dtype == "fp64" else torch.bfloat16
-    cores = np.concatenate([np.asarray(G, dtype=np.float64).ravel(order="F") for G in prob.cores])
-    core_t = torch.from_numpy(cores).to(device=device, dtype=tdt)
-    facs = []
-    for m in range(prob.order):
-        Ucat = np.hstack([np.asarray(Us[m], dtype=np.float64) for Us in prob.factors])
-        facs.append(torch.from_numpy(Ucat.ravel(order="F").copy()).to(device=device, dtype=tdt))
-    return core_t, facs
+    chunks, shapes = [], []
+    for prob in problems:
+        cores = np.concatenate([np.asarray(G, dtype=np.float64).ravel(order="F") for G in prob.cores])
+        parts = [cores]
+        for m in range(prob.order):
+            Ucat = np.hstack([np.asarray(Us[m], dtype=np.float64) for Us in prob.factors])
+            parts.append(Ucat.ravel(order="F"))
+        # keep every block 256-byte aligned
+        align = 256 // (8 if dtype == "fp64" else 2)
+        sizes = []
+        for a in parts:
+            pad = (-len(a)) % align
+            chunks.append(a)
+            if pad:
+                chunks.append(np.zeros(pad))
+            sizes.append(len(a) + pad)
+        shapes.append(sizes)
+    host = torch.from_numpy(np.concatenate(chunks)).to(tdt)
+    flat = host.pin_memory() if pin else host.to(device)
+    views, off = [], 0
+    for prob, sizes in zip(problems, shapes):
+        v = []
+        for sz in sizes:
+            v.append(flat[off: off + sz])
+            off += sz
+        views.append((v[0], v[1:]))
+    return flat, views
 
 
 class Plan:
     """A plan over a list of ``workloads.Problem`` with their device inputs."""
 
-    def __init__(self, problems, kind="krp", precision="fp64", seed=0, tol=0.0, device="cuda",
-                 inputs=None):
+    def __init__(self, problems, kind="krp", precision="fp64", seed=0, tol=0.0, device="cuda"):
         self.lib = load()
         self.problems = list(problems)
         self.kind, self.precision, self.seed, self.tol = kind, precision, seed, tol
         self.dtype = "fp64" if precision == "fp64" else "bf16"
         self.device = torch.device(device)
-        self.inputs = inputs if inputs is not None else [
-            pack_problem(p, self.dtype, self.device) for p in self.problems]
+        self.flat_inputs, self.inputs = pack_inputs(self.problems, self.dtype, self.device)
         self._keep = []
         arr = (Problem_t * len(self.problems))()
         for i, (p, (core_t, facs)) in enumerate(zip(self.problems, self.inputs)):

@@ -25,4 +25,11 @@ cudaError_t prepare_eig_f64(int bmax);   // raises the dynamic shared memory lim
 void launch_eig_f64(const EigJob* jobs, int njobs, int bmax, const Bases& bases, Status* status,
                     cudaStream_t stream);
 
+// Tensor-core (tcgen05) grouped GEMM over bf16 planes; maps = device array of CUtensorMap.
+size_t tc_gemm_smem_bytes(int stages, int na_max, int nb_max, int bn);
+int tc_gemm_stages(int na_max, int nb_max, int bn);
+cudaError_t prepare_tc_gemm();
+void launch_tc_gemm(const TcJob* jobs, int njobs, int total_tiles, const void* maps, int na_max, int nb_max,
+                    const Bases& bases, Status* status, cudaStream_t stream);
+
 }  // namespace tks

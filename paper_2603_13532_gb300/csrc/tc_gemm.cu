@@ -1,0 +1,203 @@
+// Grouped tensor-core GEMM for the contractions of the mixed-precision path on sm_103a.
+//
+// One CTA computes one 128 x BN output tile of one job.  Warp 0 (one elected thread) streams
+// the bf16 planes of A and B through a ring of shared-memory stages with TMA (128-byte swizzle);
+// warp 1 allocates the TMEM accumulator and (one elected thread) issues tcgen05.mma for every
+// selected plane pair, 16 deep in k per instruction, releasing each stage with tcgen05.commit;
+// warps 2-5 read the accumulator back with tcgen05.ld (one TMEM lane quadrant each) and write
+// the requested outputs.  Every wait is bounded: on a timeout the kernel records TKS_ETIMEOUT,
+// drains its own copies and MMAs (again bounded), frees TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "kernels.h"
+#include "tc.cuh"
+
+namespace tks {
+
+namespace {
+
+constexpr int kBM = 128;
+constexpr int kBK = 64;                       // bf16 elements = 128 bytes = one swizzle row
+constexpr int kATile = kBM * kBK * 2;         // 16 KB
+constexpr long long kWaitCycles = 4000000000LL;   // about 2 s at 2 GHz
+
+__device__ __forceinline__ void record_status_tc(Status* st, int code) {
+  if (st) atomicCAS(&st->code, 0, code);
+}
+
+__device__ __forceinline__ uint16_t bf16_bits(float x) {
+  return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+}
+__device__ __forceinline__ float bf16_float(uint16_t h) {
+  return __bfloat162float(__ushort_as_bfloat16(h));
+}
+
+template <int BN>
+__global__ void __launch_bounds__(192, 1)
+    tc_gemm_kernel(const TcJob* __restrict__ jobs, int njobs, const CUtensorMap* __restrict__ maps, Bases bases,
+                   Status* status, int stages, int na_max, int nb_max) {
+  constexpr int kBTile = BN * kBK * 2;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int stage_bytes = na_max * kATile + nb_max * kBTile;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)stages * stage_bytes);
+  uint64_t* empty = full + stages;
+  uint64_t* tmem_full = empty + stages;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tmem_full + 1);
+  volatile int* err = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].tile_begin <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+  }
+  const TcJob& J = jobs[lo];
+  const int local = blockIdx.x - J.tile_begin;
+  const int tn = local % J.tiles_n, tm = local / J.tiles_n;
+  const int m0 = tm * kBM, n0 = tn * BN;
+  const int nk = (J.K + kBK - 1) / kBK;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < stages; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    tc::mbar_init(tmem_full, 1);
+    *err = 0;
+    tc::fence_barrier_init();
+  }
+  if (warp == 1) tc::tmem_alloc(tmem_slot, BN);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+
+  auto a_tile = [&](int s, int i) { return smem + (size_t)s * stage_bytes + (size_t)i * kATile; };
+  auto b_tile = [&](int s, int j) {
+    return smem + (size_t)s * stage_bytes + (size_t)na_max * kATile + (size_t)j * kBTile;
+  };
+
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int i = 0; i < J.na; ++i) tc::prefetch_tmap(&maps[J.mapA[i]]);
+      for (int j = 0; j < J.nb; ++j) tc::prefetch_tmap(&maps[J.mapB[j]]);
+      int issued = 0;
+      const uint32_t bytes = (uint32_t)(J.na * kATile + J.nb * kBTile);
+      for (int kb = 0; kb < nk; ++kb) {
+        const int s = kb % stages, round = kb / stages;
+        if (*err || !tc::mbar_wait(&empty[s], (round & 1) ^ 1, kWaitCycles)) {
+          *err = 1;
+          break;
+        }
+        tc::mbar_expect_tx(&full[s], bytes);
+        for (int i = 0; i < J.na; ++i) tc::tma_load_2d(a_tile(s, i), &maps[J.mapA[i]], &full[s], kb * kBK, m0);
+        for (int j = 0; j < J.nb; ++j) tc::tma_load_2d(b_tile(s, j), &maps[J.mapB[j]], &full[s], kb * kBK, n0);
+        issued = kb + 1;
+      }
+      // drain: every copy this thread issued has landed before the CTA tears down
+      for (int kb = (issued > stages ? issued - stages : 0); kb < issued; ++kb)
+        if (!tc::mbar_wait(&full[kb % stages], (kb / stages) & 1, kWaitCycles)) *err = 1;
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = tc::idesc_bf16_f32(kBM, BN);
+      uint32_t acc = 0;
+      for (int kb = 0; kb < nk; ++kb) {
+        const int s = kb % stages, round = kb / stages;
+        if (*err || !tc::mbar_wait(&full[s], round & 1, kWaitCycles)) {
+          *err = 1;
+          break;
+        }
+        tc::fence_after_sync();
+        for (int p = 0; p < J.npairs; ++p) {
+          const uint32_t a0 = tc::smem_u32(a_tile(s, J.pa[p]));
+          const uint32_t b0 = tc::smem_u32(b_tile(s, J.pb[p]));
+#pragma unroll
+          for (int k = 0; k < kBK / 16; ++k) {
+            tc::mma_bf16(tmem, tc::sw128_kmajor_desc(a0 + 32 * k), tc::sw128_kmajor_desc(b0 + 32 * k), idesc, acc);
+            acc = 1;
+          }
+        }
+        tc::mma_commit(&empty[s]);
+      }
+      tc::mma_commit(tmem_full);
+      if (!tc::mbar_wait(tmem_full, 0, kWaitCycles)) *err = 1;
+    }
+  } else {
+    // epilogue warps 2..5: TMEM lane quadrant q = warp % 4 holds rows 32q .. 32q+31
+    bool ok = tc::mbar_wait(tmem_full, 0, kWaitCycles);
+    ok = __all_sync(0xffffffffu, ok) && !*err;
+    tc::fence_after_sync();
+    if (ok) {
+      const int q = warp & 3;
+      const int row = m0 + 32 * q + lane;
+      const TcEpi& E = J.epi;
+      float* o32 = E.has_f32 ? at<float>(bases, E.f32) : nullptr;
+      double* o64 = E.has_f64 ? at<double>(bases, E.f64) : nullptr;
+      uint16_t* ob0 = E.nbf > 0 ? at<uint16_t>(bases, E.bf[0]) : nullptr;
+      uint16_t* ob1 = E.nbf > 1 ? at<uint16_t>(bases, E.bf[1]) : nullptr;
+      uint16_t* ob2 = E.nbf > 2 ? at<uint16_t>(bases, E.bf[2]) : nullptr;
+#pragma unroll
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        uint32_t r[32];
+        tc::tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, r);
+        tc::tmem_ld_wait();
+        if (row < J.M) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int col = n0 + c0 + j;
+            if (col >= J.N) continue;
+            const float v = E.alpha * __uint_as_float(r[j]);
+            if (o32) o32[row * E.f32_m + col * E.f32_n] = v;
+            if (o64) o64[row * E.f64_m + col * E.f64_n] = (double)v;
+            if (ob0) {
+              const int64_t off = row * E.bf_m + col * E.bf_n;
+              const uint16_t h0 = bf16_bits(v);
+              const float r1 = v - bf16_float(h0);
+              ob0[off] = h0;
+              if (ob1) {
+                const uint16_t h1 = bf16_bits(r1);
+                ob1[off] = h1;
+                if (ob2) ob2[off] = bf16_bits(r1 - bf16_float(h1));
+              }
+            }
+          }
+        }
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 1) tc::tmem_dealloc(tmem, BN);
+  if (threadIdx.x == 0 && *err) record_status_tc(status, TKS_ETIMEOUT);
+}
+
+}  // namespace
+
+size_t tc_gemm_smem_bytes(int stages, int na_max, int nb_max, int bn) {
+  return 1024 + (size_t)stages * (na_max * kATile + nb_max * bn * kBK * 2) + 8 * (2 * stages + 1) + 16;
+}
+
+int tc_gemm_stages(int na_max, int nb_max, int bn) {
+  const size_t budget = 220 * 1024;
+  for (int s = 4; s >= 2; --s)
+    if (tc_gemm_smem_bytes(s, na_max, nb_max, bn) <= budget) return s;
+  return 1;
+}
+
+cudaError_t prepare_tc_gemm() {
+  return cudaFuncSetAttribute(tc_gemm_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+}
+
+void launch_tc_gemm(const TcJob* jobs, int njobs, int total_tiles, const void* maps, int na_max, int nb_max,
+                    const Bases& bases, Status* status, cudaStream_t stream) {
+  const int stages = tc_gemm_stages(na_max, nb_max, 64);
+  const size_t smem = tc_gemm_smem_bytes(stages, na_max, nb_max, 64);
+  tc_gemm_kernel<64><<<total_tiles, 192, smem, stream>>>(jobs, njobs, static_cast<const CUtensorMap*>(maps), bases,
+                                                         status, stages, na_max, nb_max);
+}
+
+}  // namespace tks

@@ -107,6 +107,30 @@ struct EigJob {
   double tol;                   // 0: rank = rmax
 };
 
+// Tensor-core GEMM (tcgen05, bf16 inputs, f32 accumulation in TMEM):
+//   D (M x N) = alpha * sum_{p < npairs} A_{pa[p]} B_{pb[p]}^T
+// A_i (M x K) and B_j (N x K) are bfloat16 planes in K-major layout read by TMA through the
+// tensor maps mapA[i] / mapB[j]; rows beyond M or N and k beyond K read as zero.  A float32
+// operand enters as up to three planes hi + mid + lo (each bfloat16, their sum equals the
+// float32 value to about 2^-24 relative), and the pair list selects the products kept.
+// The epilogue writes any of: float32 D, float64 D, and D split again into bf16 planes for
+// the next contraction, each with its own (row, column) element strides.
+struct TcEpi {
+  Operand f32, f64, bf[3];
+  int64_t f32_m, f32_n, f64_m, f64_n, bf_m, bf_n;
+  int32_t has_f32, has_f64, nbf;
+  float alpha;
+};
+
+struct TcJob {
+  int32_t M, N, K;
+  int32_t tiles_m, tiles_n, tile_begin;
+  int32_t na, nb, npairs, pad;
+  int32_t mapA[3], mapB[3];
+  uint8_t pa[8], pb[8];
+  TcEpi epi;
+};
+
 struct Status {
   int32_t code;                 // first tks_status recorded by a kernel
   int32_t pad;
