@@ -1,9 +1,13 @@
 // C ABI of the library: plan creation (validation, sketch sizes, workspace layout, launch
 // tables) and the execute entry points, which bind the caller's buffers to the plan's base
 // ids and enqueue the prebuilt launches on the caller's stream.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <map>
+#include <tuple>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -41,7 +45,8 @@ Operand op_abs(const void* p, size_t off_bytes = 0) {
   return Operand{B_ABS, 0, (int64_t)(reinterpret_cast<uintptr_t>(p) + off_bytes)};
 }
 
-enum StepKind { S_OMEGA, S_GEMM, S_REDUCE, S_CORESKETCH, S_QR, S_EIG };
+enum StepKind { S_OMEGA, S_GEMM, S_REDUCE, S_CORESKETCH, S_QR, S_EIG, S_TC, S_SIMT, S_CS32, S_SPLIT,
+                S_TRANSPOSE };
 
 struct Step {
   StepKind kind;
@@ -50,6 +55,7 @@ struct Step {
   int64_t work;       // tiles / elements / blocks
   char name[32];
   double flops, bytes;
+  int na_max = 0, nb_max = 0;   // tensor-core GEMM steps: planes per operand
 };
 
 Step make_step(StepKind kind, size_t off, int njobs, int64_t work, const char* name, double flops,
@@ -83,6 +89,10 @@ struct ProbHost {
   size_t M[MAXD] = {}, V[MAXD] = {}, W[MAXD] = {}, tau[MAXD] = {}, A[MAXD] = {};
   size_t T = 0, gram = 0, part = 0, P[MAXD] = {}, ev[MAXD] = {}, theta = 0, Hp[2] = {};
   std::vector<size_t> chain;   // 2 ping-pong buffers per term
+  // mixed-precision buffers (bytes): bf16 planes and float32 intermediates
+  size_t om_plane[MAXD] = {}, UT[MAXD] = {}, M32[MAXD] = {}, Vp[MAXD][3] = {}, Qp[MAXD][3] = {};
+  size_t AT32[MAXD] = {}, ATp[MAXD][3] = {}, Tp[3] = {};
+  int ldU[MAXD] = {}, ldV[MAXD] = {}, ldA[MAXD] = {}, ldT = 0;
   int gram_ksplit = 1;
   double flops_low = 0.0, flops_f64 = 0.0;
 };
@@ -146,6 +156,29 @@ struct tks_plan {
     std::memcpy(arena_host.data() + off, p, bytes);
     return off;
   }
+  // TMA tensor maps of the mixed path: specs at plan time, encoded per workspace pointer
+  struct MapSpec {
+    int32_t base;
+    size_t off;
+    uint64_t K, rows, ld;
+    uint32_t box_rows;
+  };
+  std::vector<MapSpec> map_specs;
+  std::map<std::tuple<int32_t, size_t, uint64_t, uint64_t, uint64_t, uint32_t>, int> map_index;
+  size_t maps_off = 0;
+  void* maps_host = nullptr;
+  const void* maps_ws = nullptr;
+  bool maps_pending = false;
+  int map_of(int32_t base, size_t off, uint64_t K, uint64_t rows, uint64_t ld, uint32_t box_rows) {
+    auto key = std::make_tuple(base, off, K, rows, ld, box_rows);
+    auto it = map_index.find(key);
+    if (it != map_index.end()) return it->second;
+    const int id = (int)map_specs.size();
+    map_specs.push_back(MapSpec{base, off, K, rows, ld, box_rows});
+    map_index[key] = id;
+    return id;
+  }
+
   // profiling: events recorded around the recompress launches
   int prof_max_calls = 0, prof_calls = 0;
   std::vector<cudaEvent_t> prof_events;
@@ -171,6 +204,40 @@ struct tks_plan {
     char rn[32];
     std::snprintf(rn, sizeof(rn), "%s:reduce", name);
     push(steps, S_REDUCE, split, g.red, rn);
+  }
+  void push_tc(std::vector<Step>& steps, std::vector<TcJob>& jobs, const char* name) {
+    if (jobs.empty()) return;
+    int tiles = 0, na = 1, nb = 1;
+    double flops = 0.0, bytes = 0.0;
+    for (auto& j : jobs) {
+      j.tiles_m = ceil_div(j.M, 128);
+      j.tiles_n = ceil_div(j.N, 64);
+      j.tile_begin = tiles;
+      tiles += j.tiles_m * j.tiles_n;
+      na = std::max(na, j.na);
+      nb = std::max(nb, j.nb);
+      flops += 2.0 * j.M * (double)j.N * j.K;
+      bytes += 2.0 * ((double)j.M * j.K + (double)j.N * j.K) +
+               (double)j.M * j.N * (4.0 * j.epi.has_f32 + 8.0 * j.epi.has_f64 + 2.0 * j.epi.nbf);
+    }
+    Step st = make_step(S_TC, add_table(jobs.data(), jobs.size() * sizeof(TcJob)), (int)jobs.size(), tiles, name,
+                        flops, bytes);
+    st.na_max = na;
+    st.nb_max = nb;
+    steps.push_back(st);
+  }
+  void push_simt(std::vector<Step>& steps, std::vector<SimtJob>& jobs, const char* name) {
+    if (jobs.empty()) return;
+    int tiles = 0;
+    double flops = 0.0;
+    for (auto& j : jobs) {
+      j.tiles_m = ceil_div(j.M, 64);
+      j.tiles_n = ceil_div(j.N, 64);
+      j.tile_begin = tiles;
+      tiles += j.tiles_m * j.tiles_n * j.batch;
+      flops += 2.0 * j.M * (double)j.N * j.K * j.batch;
+    }
+    push(steps, S_SIMT, jobs, tiles, name, flops, 0.0);
   }
   void profile_clear() {
     for (auto e : prof_events) cudaEventDestroy(e);
@@ -315,6 +382,253 @@ void count_flops(ProbHost& h, int kron) {
 
 }  // namespace
 
+namespace {
+
+// Stages (a)-(c) of the mixed-precision path.  bf16 operand planes are laid out K-major for the
+// tensor-core GEMMs (TMA tiles of 64 k x 128 rows for A, 64 k x 64 rows for B):
+//   a1  Omega_m rounded to bf16 (a plane besides the float64 copy)
+//   a2  M_m = Ucat_m^T Omega_m            A = Ucat_m (rows r, k = i)    B = Omega_m (rows c, k = i)
+//   a3  V_kn (float32 core sketch) -> Vcat_n as hi/mid/lo planes, element (r, c) at r + ldV c
+//   a4  Y_n = Ucat_n Vcat_n               A = Ucat_n^T (rows i, k = r)  B = Vcat_n planes (rows c)
+//   a5  Q_n = qr(Y_n) in float64, split into planes
+//   a6  A_n^T = Ucat_n^T Q_n              A = Ucat_n (rows r, k = i)    B = Q_n planes (rows a)
+//   a7  per-term chains in float32, last step written as planes of Tcat (element (r, J) at r + ldT J)
+//   a8  H_(d)^T = Tcat^T A_d^T            A = Tcat planes (rows J)      B = A_d^T planes (rows a)
+static void build_mixed_stages(tks_plan* plan, int kron) {
+  std::vector<OmegaJob> om;
+  int64_t om_blocks = 0;
+  std::vector<TransposeJob> tr;
+  int tr_tiles = 0;
+  std::vector<TcJob> tcM, tcY, tcA, tcH;
+  std::vector<CoreSketchF32Job> cs;
+  int64_t cs_total = 0;
+  double cs_flops = 0.0;
+  std::vector<QrJob> qr;
+  double qr_flops = 0.0, qr_bytes = 0.0;
+  std::vector<SplitJob> sp;
+  int64_t sp_total = 0;
+  std::vector<std::vector<SimtJob>> chain(std::max(1, plan->dmax - 1));
+  auto tc_job = [](int M, int N, int K) {
+    TcJob j;
+    std::memset(&j, 0, sizeof(j));
+    j.M = M; j.N = N; j.K = K;
+    j.epi.alpha = 1.0f;
+    return j;
+  };
+  for (int p = 0; p < plan->nprob; ++p) {
+    auto& h = plan->probs[p];
+    const int d = h.d;
+    for (int m = 0; m < d; ++m) {
+      const uint64_t n = h.n[m];
+      OmegaJob oj;
+      std::memset(&oj, 0, sizeof(oj));
+      oj.out = op(B_OMEGA, h.omega_off[m] * 8);
+      oj.plane = op(B_WS, h.om_plane[m]);
+      oj.has_plane = 1;
+      oj.count = h.n[m] * h.s[m];
+      oj.begin = om_blocks;
+      oj.problem = p;
+      oj.mode = m;
+      oj.bf16 = 1;
+      om_blocks += (oj.count + 3) / 4;
+      om.push_back(oj);
+      TransposeJob t;
+      std::memset(&t, 0, sizeof(t));
+      t.src = op_abs(h.factors[m]);
+      t.dst = op(B_WS, h.UT[m]);
+      t.rows = (int)n;
+      t.cols = h.R[m];
+      t.ld_src = (int64_t)n;
+      t.ld_dst = h.ldU[m];
+      t.tiles_r = ceil_div(n, 32);
+      t.tiles_c = ceil_div(h.R[m], 32);
+      t.tile_begin = tr_tiles;
+      tr_tiles += t.tiles_r * t.tiles_c;
+      tr.push_back(t);
+      TcJob a2 = tc_job(h.R[m], h.s[m], (int)n);
+      a2.na = a2.nb = a2.npairs = 1;
+      a2.mapA[0] = plan->map_of(B_ABS, reinterpret_cast<uintptr_t>(h.factors[m]), n, h.R[m], n, 128);
+      a2.mapB[0] = plan->map_of(B_WS, h.om_plane[m], n, h.s[m], n, 64);
+      a2.epi.has_f32 = 1;
+      a2.epi.f32 = op(B_WS, h.M32[m]);
+      a2.epi.f32_m = 1;
+      a2.epi.f32_n = h.R[m];
+      tcM.push_back(a2);
+    }
+    for (int k = 0; k < h.K; ++k) {
+      for (int n = 0; n < d; ++n) {
+        CoreSketchF32Job j;
+        std::memset(&j, 0, sizeof(j));
+        j.core = op_abs(h.cores, (size_t)h.core_off[k] * 2);
+        for (int m = 0; m < d; ++m) {
+          j.M[m] = op(B_WS, h.M32[m]);
+          j.r[m] = h.ranks[(size_t)k * d + m];
+          j.roff[m] = h.roff[(size_t)k * d + m];
+          j.R[m] = h.R[m];
+          j.s[m] = h.s[m];
+        }
+        for (int t = 0; t < 3; ++t) j.V[t] = op(B_WS, h.Vp[n][t]);
+        j.d = d;
+        j.n = n;
+        j.kron = kron;
+        j.ldv = h.ldV[n];
+        j.S = h.S[n];
+        j.alpha = (float)h.alpha[k];
+        j.count = (int64_t)j.r[n] * j.S;
+        double other = 1.0;
+        for (int m = 0; m < d; ++m)
+          if (m != n) other *= j.r[m];
+        cs_flops += 2.0 * (double)j.count * other;
+        j.begin = cs_total;
+        cs_total += j.count;
+        cs.push_back(j);
+      }
+    }
+    for (int n = 0; n < d; ++n) {
+      const uint64_t nn = h.n[n];
+      TcJob a4 = tc_job((int)nn, h.S[n], h.R[n]);
+      a4.na = 1;
+      a4.nb = 3;
+      a4.npairs = 3;
+      a4.mapA[0] = plan->map_of(B_WS, h.UT[n], h.R[n], nn, h.ldU[n], 128);
+      for (int t = 0; t < 3; ++t) {
+        a4.mapB[t] = plan->map_of(B_WS, h.Vp[n][t], h.R[n], h.S[n], h.ldV[n], 64);
+        a4.pa[t] = 0;
+        a4.pb[t] = (uint8_t)t;
+      }
+      a4.epi.has_f64 = 1;
+      a4.epi.f64 = op(B_Y, h.y_off[n] * 8);
+      a4.epi.f64_m = 1;
+      a4.epi.f64_n = (int64_t)nn;
+      tcY.push_back(a4);
+      QrJob q;
+      std::memset(&q, 0, sizeof(q));
+      q.Y = op(B_Y, h.y_off[n] * 8);
+      q.W = op(B_WS, h.W[n]);
+      q.Q = op(B_Q, h.q_off[n] * 8);
+      q.tau = op(B_WS, h.tau[n]);
+      q.n = (int)nn;
+      q.S = h.S[n];
+      q.b = h.b[n];
+      qr.push_back(q);
+      qr_flops += 4.0 * (double)nn * h.b[n] * h.b[n];
+      qr_bytes += 8.0 * (double)nn * (h.S[n] + h.b[n]);
+      SplitJob sj;
+      std::memset(&sj, 0, sizeof(sj));
+      sj.src = op(B_Q, h.q_off[n] * 8);
+      for (int t = 0; t < 3; ++t) sj.dst[t] = op(B_WS, h.Qp[n][t]);
+      sj.rows = (int64_t)nn;
+      sj.cols = h.b[n];
+      sj.ld_src = sj.ld_dst = (int64_t)nn;
+      sj.count = sj.rows * sj.cols;
+      sj.begin = sp_total;
+      sp_total += sj.count;
+      sp.push_back(sj);
+      TcJob a6 = tc_job(h.R[n], h.b[n], (int)nn);
+      a6.na = 1;
+      a6.nb = 3;
+      a6.npairs = 3;
+      a6.mapA[0] = plan->map_of(B_ABS, reinterpret_cast<uintptr_t>(h.factors[n]), nn, h.R[n], nn, 128);
+      for (int t = 0; t < 3; ++t) {
+        a6.mapB[t] = plan->map_of(B_WS, h.Qp[n][t], nn, h.b[n], nn, 64);
+        a6.pa[t] = 0;
+        a6.pb[t] = (uint8_t)t;
+      }
+      a6.epi.has_f32 = 1;
+      a6.epi.f32 = op(B_WS, h.AT32[n]);
+      a6.epi.f32_m = 1;
+      a6.epi.f32_n = h.R[n];
+      a6.epi.nbf = 3;
+      for (int t = 0; t < 3; ++t) a6.epi.bf[t] = op(B_WS, h.ATp[n][t]);
+      a6.epi.bf_m = 1;
+      a6.epi.bf_n = h.ldA[n];
+      tcA.push_back(a6);
+    }
+    // (c2) chains in float32; A_t^T block of term k: element (j, i) at (roff + i) + R_t j
+    for (int k = 0; k < h.K; ++k) {
+      const int* r = &h.ranks[(size_t)k * d];
+      const int rd_off = h.roff[(size_t)k * d + d - 1];
+      for (int t = 0; t + 1 < d; ++t) {
+        int64_t L = 1, Rr = 1;
+        for (int j = 0; j < t; ++j) L *= h.b[j];
+        for (int j = t + 1; j < d; ++j) Rr *= r[j];
+        const int I = r[t], Jn = h.b[t], Rt = h.R[t];
+        SimtJob j;
+        std::memset(&j, 0, sizeof(j));
+        const Operand X = (t == 0) ? op_abs(h.cores, (size_t)h.core_off[k] * 2)
+                                   : op(B_WS, h.chain[2 * k + ((t - 1) & 1)]);
+        const int32_t xt = (t == 0) ? T_BF16 : T_F32;
+        const Operand Ablk = op(B_WS, h.AT32[t] + (size_t)h.roff[(size_t)k * d + t] * 4);
+        const bool last = (t == d - 2);
+        j.batch = 1;
+        j.alpha = (t == 0) ? (float)h.alpha[k] : 1.0f;
+        if (L == 1) {
+          j.M = Jn; j.N = (int)Rr; j.K = I; j.K1 = I;
+          j.A = Ablk; j.a_type = T_F32; j.a_m = Rt; j.a_k0 = 1;
+          j.B = X; j.b_type = xt; j.b_n = I; j.b_k0 = 1;
+          j.c_m = last ? h.ldT : 1;
+          j.c_n = last ? 1 : Jn;
+        } else {
+          j.M = (int)L; j.N = Jn; j.K = I; j.K1 = I; j.batch = (int)Rr;
+          j.A = X; j.a_type = xt; j.a_m = 1; j.a_k0 = L; j.a_b = L * I;
+          j.B = Ablk; j.b_type = T_F32; j.b_n = Rt; j.b_k0 = 1;
+          j.c_m = last ? h.ldT : 1;
+          j.c_n = last ? (int64_t)h.ldT * L : L;
+          j.c_b = last ? 1 : L * Jn;
+        }
+        if (last) {
+          j.nbf = 3;
+          for (int q = 0; q < 3; ++q) j.cb[q] = op(B_WS, h.Tp[q] + (size_t)rd_off * 2);
+        } else {
+          j.has_c32 = 1;
+          j.c32 = op(B_WS, h.chain[2 * k + (t & 1)]);
+        }
+        chain[t].push_back(j);
+      }
+    }
+    // (c3) H_(d)^T = Tcat^T A_d^T, six plane products (hi/mid/lo x hi/mid/lo up to second order)
+    int64_t Pd = 1;
+    for (int j = 0; j + 1 < d; ++j) Pd *= h.b[j];
+    const int Rd = h.R[d - 1], bd = h.b[d - 1];
+    TcJob c3 = tc_job((int)Pd, bd, Rd);
+    c3.na = c3.nb = 3;
+    for (int t = 0; t < 3; ++t) {
+      c3.mapA[t] = plan->map_of(B_WS, h.Tp[t], Rd, Pd, h.ldT, 128);
+      c3.mapB[t] = plan->map_of(B_WS, h.ATp[d - 1][t], Rd, bd, h.ldA[d - 1], 64);
+    }
+    const uint8_t pa[6] = {0, 0, 1, 0, 2, 1}, pb[6] = {0, 1, 0, 2, 0, 1};
+    c3.npairs = 6;
+    for (int t = 0; t < 6; ++t) {
+      c3.pa[t] = pa[t];
+      c3.pb[t] = pb[t];
+    }
+    c3.epi.has_f64 = 1;
+    c3.epi.f64 = op(B_H, h.h_off * 8);
+    c3.epi.f64_m = 1;
+    c3.epi.f64_n = Pd;
+    tcH.push_back(c3);
+  }
+  plan->push(plan->st_omega, S_OMEGA, om, om_blocks, "a1:omega", 0.0, 10.0 * plan->omega_elems);
+  plan->push(plan->st_sketch, S_OMEGA, om, om_blocks, "a1:omega", 0.0, 10.0 * plan->omega_elems);
+  plan->push(plan->st_sketch, S_TRANSPOSE, tr, tr_tiles, "a4:UcatT", 0.0, 0.0);
+  plan->push_tc(plan->st_sketch, tcM, "a2:M=UcatT.Omega[tc]");
+  plan->push(plan->st_sketch, S_CS32, cs, cs_total, "a3:core_sketch[f32]", cs_flops, 0.0);
+  plan->push_tc(plan->st_sketch, tcY, "a4:Y=Ucat.Vcat[tc]");
+  plan->push(plan->st_project, S_SPLIT, sp, sp_total, "a6:Q->planes", 0.0, 14.0 * sp_total);
+  plan->push_tc(plan->st_project, tcA, "a6:AT=UcatT.Q[tc]");
+  for (size_t t = 0; t < chain.size(); ++t) {
+    char nm[32];
+    std::snprintf(nm, sizeof(nm), "a7:chain%d[f32]", (int)t);
+    plan->push_simt(plan->st_project, chain[t], nm);
+  }
+  plan->push_tc(plan->st_project, tcH, "a8:H=Tcat.AT[tc]");
+  plan->st_recompress = plan->st_sketch;
+  plan->push(plan->st_recompress, S_QR, qr, (int64_t)qr.size(), "a5:qr", qr_flops, qr_bytes);
+  for (const auto& st : plan->st_project) plan->st_recompress.push_back(st);
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* tks_last_error(void) { return g_last_error.c_str(); }
@@ -336,6 +650,7 @@ const char* tks_status_string(tks_status s) {
 void tks_plan_destroy(tks_plan* plan) {
   if (!plan) return;
   plan->profile_clear();
+  if (plan->maps_host) cudaFreeHost(plan->maps_host);
   if (plan->arena_dev) cudaFree(plan->arena_dev);
   delete plan;
 }
@@ -352,7 +667,6 @@ tks_status tks_plan_create(tks_plan** out, const tks_problem* problems, int32_t 
     if (prm.dtype != TKS_DT_F64) return fail(TKS_EINVAL, "TKS_FP64 needs float64 cores and factors");
   } else if (prm.precision == TKS_MIXED) {
     if (prm.dtype != TKS_DT_BF16) return fail(TKS_EINVAL, "TKS_MIXED needs bfloat16 cores and factors");
-    return fail(TKS_EUNSUPPORTED, "TKS_MIXED is not available in this build");
   } else {
     return fail(TKS_EINVAL, "bad precision");
   }
@@ -362,8 +676,19 @@ tks_status tks_plan_create(tks_plan** out, const tks_problem* problems, int32_t 
   plan->nprob = num_problems;
   plan->probs.resize(num_problems);
   const int kron = prm.sketch == TKS_SKETCH_KRON;
+  const bool mixed = prm.precision == TKS_MIXED;
   for (int p = 0; p < num_problems; ++p) {
     tks_status st = validate_and_size(problems[p], prm, plan->probs[p], p);
+    if (st == TKS_OK && mixed) {
+      // the tensor-core stages read Ucat_m by TMA: 16-byte aligned rows of n_m bf16
+      const auto& h = plan->probs[p];
+      for (int m = 0; m < h.d && st == TKS_OK; ++m) {
+        if (h.n[m] % 8 != 0)
+          st = fail(TKS_EUNSUPPORTED, "problem " + std::to_string(p) + ": TKS_MIXED needs n_m % 8 == 0");
+        else if (reinterpret_cast<uintptr_t>(h.factors[m]) % 16 != 0)
+          st = fail(TKS_EINVAL, "problem " + std::to_string(p) + ": factor pointer not 16-byte aligned");
+      }
+    }
     if (st != TKS_OK) {
       delete plan;
       return st;
@@ -406,18 +731,35 @@ tks_status tks_plan_create(tks_plan** out, const tks_problem* problems, int32_t 
   plan->ws_H = alloc(plan->core_elems * 8);
   for (auto& h : plan->probs) {
     const int d = h.d;
-    for (int m = 0; m < d; ++m) {
-      h.M[m] = alloc((size_t)h.R[m] * h.s[m] * 8);
-      h.V[m] = alloc((size_t)h.R[m] * h.S[m] * 8);
-      h.W[m] = alloc((size_t)h.n[m] * h.S[m] * 8);
-      h.tau[m] = alloc((size_t)h.S[m] * 8);
-      h.A[m] = alloc((size_t)h.b[m] * h.R[m] * 8);
-      h.P[m] = alloc((size_t)h.b[m] * h.rmax[m] * 8);
-      h.ev[m] = alloc((size_t)h.b[m] * 8);
-    }
+    auto r8 = [](int x) { return (x + 7) / 8 * 8; };
     int64_t Pd = 1;
     for (int j = 0; j + 1 < d; ++j) Pd *= h.b[j];
-    h.T = alloc((size_t)h.R[d - 1] * Pd * 8);
+    for (int m = 0; m < d; ++m) {
+      h.W[m] = alloc((size_t)h.n[m] * h.S[m] * 8);
+      h.tau[m] = alloc((size_t)h.S[m] * 8);
+      h.P[m] = alloc((size_t)h.b[m] * h.rmax[m] * 8);
+      h.ev[m] = alloc((size_t)h.b[m] * 8);
+      if (!mixed) {
+        h.M[m] = alloc((size_t)h.R[m] * h.s[m] * 8);
+        h.V[m] = alloc((size_t)h.R[m] * h.S[m] * 8);
+        h.A[m] = alloc((size_t)h.b[m] * h.R[m] * 8);
+      } else {
+        h.ldU[m] = h.ldV[m] = h.ldA[m] = r8(h.R[m]);
+        h.om_plane[m] = alloc((size_t)h.n[m] * h.s[m] * 2);
+        h.UT[m] = alloc((size_t)h.ldU[m] * h.n[m] * 2);
+        h.M32[m] = alloc((size_t)h.R[m] * h.s[m] * 4);
+        for (int t = 0; t < 3; ++t) h.Vp[m][t] = alloc((size_t)h.ldV[m] * h.S[m] * 2);
+        for (int t = 0; t < 3; ++t) h.Qp[m][t] = alloc((size_t)h.n[m] * h.b[m] * 2);
+        h.AT32[m] = alloc((size_t)h.R[m] * h.b[m] * 4);
+        for (int t = 0; t < 3; ++t) h.ATp[m][t] = alloc((size_t)h.ldA[m] * h.b[m] * 2);
+      }
+    }
+    if (!mixed) {
+      h.T = alloc((size_t)h.R[d - 1] * Pd * 8);
+    } else {
+      h.ldT = r8(h.R[d - 1]);
+      for (int t = 0; t < 3; ++t) h.Tp[t] = alloc((size_t)h.ldT * Pd * 2);
+    }
     h.chain.resize((size_t)2 * h.K);
     for (int k = 0; k < h.K; ++k) {
       const int* r = &h.ranks[(size_t)k * d];
@@ -447,6 +789,9 @@ tks_status tks_plan_create(tks_plan** out, const tks_problem* problems, int32_t 
   plan->ws_bytes = align_up(ws);
 
   // ---- launch tables
+  if (mixed) {
+    build_mixed_stages(plan, kron);
+  } else {
   std::vector<OmegaJob> om_ext, om_int;
   int64_t om_blocks = 0;
   GemmList gM, gY, gA, gH;
@@ -579,6 +924,7 @@ tks_status tks_plan_create(tks_plan** out, const tks_problem* problems, int32_t 
   plan->st_recompress = plan->st_sketch;
   plan->push(plan->st_recompress, S_QR, qr, (int64_t)qr.size(), "a5:qr", qr_flops, qr_bytes);
   for (const auto& s : plan->st_project) plan->st_recompress.push_back(s);
+  }
   for (int n = 0; n < plan->dmax; ++n) {
     GemmList gram, ttm, fac;
     std::vector<EigJob> eig;
@@ -648,6 +994,22 @@ tks_status tks_plan_create(tks_plan** out, const tks_problem* problems, int32_t 
     if (e != cudaSuccess) {
       tks_plan_destroy(plan);
       return fail(TKS_ECUDA, std::string("eigensolver shared memory: ") + cudaGetErrorString(e));
+    }
+  }
+  if (mixed) {
+    cudaError_t e = prepare_tc_gemm();
+    if (e != cudaSuccess) {
+      tks_plan_destroy(plan);
+      return fail(TKS_ECUDA, std::string("tensor-core GEMM shared memory: ") + cudaGetErrorString(e));
+    }
+    if (!plan->map_specs.empty()) {
+      const size_t bytes = plan->map_specs.size() * sizeof(CUtensorMap);
+      plan->maps_off = align_up(plan->arena_host.size(), 128);
+      plan->arena_host.resize(plan->maps_off + bytes, 0);
+      if (cudaMallocHost(&plan->maps_host, bytes) != cudaSuccess) {
+        tks_plan_destroy(plan);
+        return fail(TKS_ENOMEM, "pinned tensor-map staging buffer");
+      }
     }
   }
   const size_t status_off = plan->add_table(&plan->nprob, 0);
@@ -737,11 +1099,68 @@ tks_status run_steps(tks_plan* plan, const std::vector<Step>& steps, const Bases
       case S_EIG:
         launch_eig_f64(static_cast<const EigJob*>(table), s.njobs, plan->bmax, bases, plan->status, stream);
         break;
+      case S_TC:
+        launch_tc_gemm(static_cast<const TcJob*>(table), s.njobs, (int)s.work, plan->arena_dev + plan->maps_off,
+                       s.na_max, s.nb_max, bases, plan->status, stream);
+        break;
+      case S_SIMT:
+        launch_simt_gemm_f32(static_cast<const SimtJob*>(table), s.njobs, (int)s.work, bases, stream);
+        break;
+      case S_CS32:
+        launch_core_sketch_f32(static_cast<const CoreSketchF32Job*>(table), s.njobs, s.work, bases, stream);
+        break;
+      case S_SPLIT:
+        launch_split_f64(static_cast<const SplitJob*>(table), s.njobs, s.work, bases, stream);
+        break;
+      case S_TRANSPOSE:
+        launch_transpose_bf16(static_cast<const TransposeJob*>(table), s.njobs, (int)s.work, bases, stream);
+        break;
     }
   }
   if (ev) cudaEventRecord(ev[steps.size()], stream);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(TKS_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+  return TKS_OK;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// Encodes the plan's TMA tensor maps for this workspace pointer (bf16, 2-D, 64-element
+// (128-byte) inner box with 128-byte swizzle, zero fill out of bounds) and copies them to the
+// device table on `stream`; reused while the same workspace is passed.
+tks_status ensure_maps(tks_plan* plan, void* ws, cudaStream_t stream) {
+  if (plan->map_specs.empty() || plan->maps_ws == ws) return TKS_OK;
+  auto enc = tensor_map_encoder();
+  if (!enc) return fail(TKS_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  if (plan->maps_pending) TKS_CUDA_CHECK(cudaStreamSynchronize(stream));
+  auto* maps = static_cast<CUtensorMap*>(plan->maps_host);
+  for (size_t i = 0; i < plan->map_specs.size(); ++i) {
+    const auto& m = plan->map_specs[i];
+    void* base = (m.base == B_ABS) ? reinterpret_cast<void*>(m.off) : static_cast<char*>(ws) + m.off;
+    cuuint64_t dims[2] = {m.K, m.rows};
+    cuuint64_t strides[1] = {m.ld * 2};
+    cuuint32_t box[2] = {64, m.box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(&maps[i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(TKS_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+  }
+  TKS_CUDA_CHECK(cudaMemcpyAsync(plan->arena_dev + plan->maps_off, plan->maps_host,
+                                 plan->map_specs.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice, stream));
+  plan->maps_ws = ws;
+  plan->maps_pending = true;
   return TKS_OK;
 }
 
@@ -781,6 +1200,8 @@ tks_status tucker_sum_sketch(tks_plan* plan, void* workspace, double* Y_out, voi
   tks_status st = check_ws(plan, workspace);
   if (st != TKS_OK) return st;
   if (!Y_out) return fail(TKS_EINVAL, "null Y_out");
+  st = ensure_maps(plan, workspace, static_cast<cudaStream_t>(stream));
+  if (st != TKS_OK) return st;
   Bases b = bind(plan, workspace);
   b.p[B_Y] = reinterpret_cast<char*>(Y_out);
   return run_steps(plan, plan->st_sketch, b, static_cast<cudaStream_t>(stream));
@@ -790,6 +1211,8 @@ tks_status tks_project_core(tks_plan* plan, void* workspace, const double* Q_in,
   tks_status st = check_ws(plan, workspace);
   if (st != TKS_OK) return st;
   if (!Q_in || !H_out) return fail(TKS_EINVAL, "null Q_in or H_out");
+  st = ensure_maps(plan, workspace, static_cast<cudaStream_t>(stream));
+  if (st != TKS_OK) return st;
   Bases b = bind(plan, workspace);
   b.p[B_Q] = reinterpret_cast<char*>(const_cast<double*>(Q_in));
   b.p[B_H] = reinterpret_cast<char*>(H_out);
@@ -801,6 +1224,8 @@ tks_status tucker_sum_recompress(tks_plan* plan, void* workspace, double* out, i
   if (st != TKS_OK) return st;
   if (!out || !ranks_out) return fail(TKS_EINVAL, "null out or ranks_out");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  st = ensure_maps(plan, workspace, s);
+  if (st != TKS_OK) return st;
   TKS_CUDA_CHECK(cudaMemsetAsync(ranks_out, 0, (size_t)plan->nprob * TKS_MAX_ORDER * sizeof(int32_t), s));
   TKS_CUDA_CHECK(cudaMemsetAsync(out, 0, (size_t)plan->output_elems * sizeof(double), s));
   Bases b = bind(plan, workspace);

@@ -41,10 +41,19 @@ __global__ void omega_kernel(const OmegaJob* __restrict__ jobs, int njobs, int64
     double z[4];
     rng::gaussian4(seed, (uint64_t)J.problem, (uint64_t)J.mode, 0ull, (uint64_t)blk, z);
     double* out = at<double>(bases, J.out);
+    uint16_t* plane = J.has_plane ? at<uint16_t>(bases, J.plane) : nullptr;
 #pragma unroll
     for (int l = 0; l < 4; ++l) {
       const int64_t e = 4 * blk + l;
-      if (e < J.count) out[e] = J.bf16 ? rng::bf16_bits_to_double(rng::to_bf16_bits(z[l])) : z[l];
+      if (e < J.count) {
+        if (J.bf16) {
+          const uint16_t h = rng::to_bf16_bits(z[l]);
+          out[e] = rng::bf16_bits_to_double(h);
+          if (plane) plane[e] = h;
+        } else {
+          out[e] = z[l];
+        }
+      }
     }
   }
 }

@@ -32,4 +32,19 @@ cudaError_t prepare_tc_gemm();
 void launch_tc_gemm(const TcJob* jobs, int njobs, int total_tiles, const void* maps, int na_max, int nb_max,
                     const Bases& bases, Status* status, cudaStream_t stream);
 
+// Float32 CUDA-core kernels of the mixed path.
+void launch_simt_gemm_f32(const SimtJob* jobs, int njobs, int total_tiles, const Bases& bases,
+                          cudaStream_t stream);
+void launch_core_sketch_f32(const CoreSketchF32Job* jobs, int njobs, int64_t total, const Bases& bases,
+                            cudaStream_t stream);
+void launch_split_f64(const SplitJob* jobs, int njobs, int64_t total, const Bases& bases, cudaStream_t stream);
+void launch_transpose_bf16(const TransposeJob* jobs, int njobs, int total_tiles, const Bases& bases,
+                           cudaStream_t stream);
+
+// Float32 small dense linear algebra (Householder QR, one-sided Jacobi SVD).
+void launch_qr_f32(const QrF32Job* jobs, int njobs, const Bases& bases, Status* status, cudaStream_t stream);
+cudaError_t prepare_svd_f32(int bmax);
+void launch_svd_f32(const SvdJob* jobs, int njobs, int bmax, const Bases& bases, Status* status,
+                    cudaStream_t stream);
+
 }  // namespace tks

@@ -1,0 +1,270 @@
+// Float32 CUDA-core kernels of the mixed-precision path: the small ragged contractions
+// (per-term core chains, core sketch), conversion of float64 bases into bfloat16 planes and
+// the transpose of the concatenated factors into the K-major layout the tensor-core GEMMs read.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "kernels.h"
+
+namespace tks {
+
+namespace {
+
+template <typename Job>
+__device__ __forceinline__ int find_begin(const Job* jobs, int njobs, int64_t key) {
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].begin <= key) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ uint16_t bf16_bits(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
+__device__ __forceinline__ float bf16_float(uint16_t h) { return __bfloat162float(__ushort_as_bfloat16(h)); }
+
+// v ~= hi + mid + lo with each part a bfloat16 (the float32 value to about 2^-24 relative)
+__device__ __forceinline__ void split3(float v, uint16_t& h0, uint16_t& h1, uint16_t& h2) {
+  h0 = bf16_bits(v);
+  const float r1 = v - bf16_float(h0);
+  h1 = bf16_bits(r1);
+  h2 = bf16_bits(r1 - bf16_float(h1));
+}
+__device__ __forceinline__ void split3(double v, uint16_t& h0, uint16_t& h1, uint16_t& h2) {
+  h0 = bf16_bits(__double2float_rn(v));
+  const double r1 = v - (double)bf16_float(h0);
+  h1 = bf16_bits(__double2float_rn(r1));
+  const double r2 = r1 - (double)bf16_float(h1);
+  h2 = bf16_bits(__double2float_rn(r2));
+}
+
+__device__ __forceinline__ float load_typed(const char* base, int32_t type, int64_t idx) {
+  switch (type) {
+    case T_F64: return (float)reinterpret_cast<const double*>(base)[idx];
+    case T_F32: return reinterpret_cast<const float*>(base)[idx];
+    default: return bf16_float(reinterpret_cast<const uint16_t*>(base)[idx]);
+  }
+}
+
+// ----------------------------------------------------------------------------- SIMT GEMM
+constexpr int ST = 64, SK = 16;
+
+__global__ void __launch_bounds__(256) simt_gemm_f32_kernel(const SimtJob* __restrict__ jobs, int njobs,
+                                                            Bases bases) {
+  __shared__ float As[SK][ST + 1];
+  __shared__ float Bs[SK][ST + 1];
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].tile_begin <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+  }
+  const SimtJob& J = jobs[lo];
+  int local = blockIdx.x - J.tile_begin;
+  const int tn = local % J.tiles_n;
+  local /= J.tiles_n;
+  const int tm = local % J.tiles_m;
+  const int bt = local / J.tiles_m;
+  const char* A = at<char>(bases, J.A);
+  const char* B = at<char>(bases, J.B);
+  const int64_t a_bt = bt * J.a_b, b_bt = bt * J.b_b;
+  const int m0 = tm * ST, n0 = tn * ST;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const bool a_mfast = (J.a_m == 1), b_kfast = (J.b_k0 == 1);
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  for (int k0 = 0; k0 < J.K; k0 += SK) {
+    for (int e = threadIdx.x; e < ST * SK; e += 256) {
+      int i, kk;
+      if (a_mfast) { i = e % ST; kk = e / ST; } else { kk = e % SK; i = e / SK; }
+      const int gi = m0 + i, gk = k0 + kk;
+      float v = 0.f;
+      if (gi < J.M && gk < J.K) {
+        const int kq = gk / J.K1, kr = gk - kq * J.K1;
+        v = load_typed(A, J.a_type, a_bt + gi * J.a_m + kr * J.a_k0 + kq * J.a_k1);
+      }
+      As[kk][i] = v;
+      int jj;
+      if (b_kfast) { kk = e % SK; jj = e / SK; } else { jj = e % ST; kk = e / ST; }
+      const int gj = n0 + jj, gk2 = k0 + kk;
+      float w = 0.f;
+      if (gj < J.N && gk2 < J.K) {
+        const int kq = gk2 / J.K1, kr = gk2 - kq * J.K1;
+        w = load_typed(B, J.b_type, b_bt + gj * J.b_n + kr * J.b_k0 + kq * J.b_k1);
+      }
+      Bs[kk][jj] = w;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < SK; ++kk) {
+      float a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  float* c32 = J.has_c32 ? at<float>(bases, J.c32) : nullptr;
+  double* c64 = J.has_c64 ? at<double>(bases, J.c64) : nullptr;
+  uint16_t* cb0 = J.nbf > 0 ? at<uint16_t>(bases, J.cb[0]) : nullptr;
+  uint16_t* cb1 = J.nbf > 1 ? at<uint16_t>(bases, J.cb[1]) : nullptr;
+  uint16_t* cb2 = J.nbf > 2 ? at<uint16_t>(bases, J.cb[2]) : nullptr;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gi = m0 + ty + 16 * i, gj = n0 + tx + 16 * j;
+      if (gi < J.M && gj < J.N) {
+        const int64_t off = bt * J.c_b + gi * J.c_m + gj * J.c_n;
+        const float v = J.alpha * acc[i][j];
+        if (c32) c32[off] = v;
+        if (c64) c64[off] = (double)v;
+        if (cb0) {
+          uint16_t h0, h1, h2;
+          split3(v, h0, h1, h2);
+          cb0[off] = h0;
+          if (cb1) cb1[off] = h1;
+          if (cb2) cb2[off] = h2;
+        }
+      }
+    }
+}
+
+// ----------------------------------------------------------------------------- core sketch
+// Same contraction as the float64 kernel (Eqs. krp_sketch_result / kron_sketch_result) with a
+// bfloat16 core, float32 sketched factors M_j and float32 accumulation.
+__global__ void core_sketch_f32_kernel(const CoreSketchF32Job* __restrict__ jobs, int njobs, int64_t total,
+                                       Bases bases) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const CoreSketchF32Job& J = jobs[find_begin(jobs, njobs, g)];
+    const int64_t e = g - J.begin;
+    const int d = J.d, n = J.n;
+    const int a = (int)(e % J.r[n]);
+    const int c = (int)(e / J.r[n]);
+    int col[MAXD], others[MAXD], st[MAXD];
+    int no = 0;
+    {
+      int rem = c, stride = 1;
+      for (int j = 0; j < d; ++j) {
+        st[j] = stride;
+        stride *= J.r[j];
+        if (j == n) continue;
+        others[no++] = j;
+        if (J.kron) { col[j] = rem % J.s[j]; rem /= J.s[j]; } else { col[j] = c; }
+      }
+    }
+    const uint16_t* G = at<uint16_t>(bases, J.core);
+    const float* Mcol[MAXD];
+    for (int t = 0; t < no; ++t) {
+      const int j = others[t];
+      Mcol[t] = at<float>(bases, J.M[j]) + J.roff[j] + (int64_t)J.R[j] * col[j];
+    }
+    const int f = others[0];
+    const int rf = J.r[f], sf = st[f];
+    int idx[MAXD];
+    for (int t = 0; t < no; ++t) idx[t] = 0;
+    int64_t goff = (int64_t)a * st[n];
+    float acc = 0.f;
+    while (true) {
+      float prod = 1.f;
+      for (int t = 1; t < no; ++t) prod *= Mcol[t][idx[t]];
+      float inner = 0.f;
+      const float* mf = Mcol[0];
+      for (int i = 0; i < rf; ++i) inner = fmaf(bf16_float(G[goff + (int64_t)i * sf]), mf[i], inner);
+      acc = fmaf(prod, inner, acc);
+      int t = 1;
+      for (; t < no; ++t) {
+        const int j = others[t];
+        goff += st[j];
+        if (++idx[t] < J.r[j]) break;
+        goff -= (int64_t)st[j] * J.r[j];
+        idx[t] = 0;
+      }
+      if (t >= no) break;
+    }
+    const int64_t off = (J.roff[n] + a) + (int64_t)J.ldv * c;
+    uint16_t h0, h1, h2;
+    split3(J.alpha * acc, h0, h1, h2);
+    at<uint16_t>(bases, J.V[0])[off] = h0;
+    at<uint16_t>(bases, J.V[1])[off] = h1;
+    at<uint16_t>(bases, J.V[2])[off] = h2;
+  }
+}
+
+// ----------------------------------------------------------------------------- split / transpose
+__global__ void split_f64_kernel(const SplitJob* __restrict__ jobs, int njobs, int64_t total, Bases bases) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const SplitJob& J = jobs[find_begin(jobs, njobs, g)];
+    const int64_t e = g - J.begin;
+    const int64_t i = e % J.rows, j = e / J.rows;
+    const double v = at<double>(bases, J.src)[i + J.ld_src * j];
+    uint16_t h0, h1, h2;
+    split3(v, h0, h1, h2);
+    const int64_t off = i + J.ld_dst * j;
+    at<uint16_t>(bases, J.dst[0])[off] = h0;
+    at<uint16_t>(bases, J.dst[1])[off] = h1;
+    at<uint16_t>(bases, J.dst[2])[off] = h2;
+  }
+}
+
+__global__ void __launch_bounds__(256) transpose_bf16_kernel(const TransposeJob* __restrict__ jobs, int njobs,
+                                                             Bases bases) {
+  __shared__ uint16_t tile[32][33];
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].tile_begin <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+  }
+  const TransposeJob& J = jobs[lo];
+  const int local = blockIdx.x - J.tile_begin;
+  const int tr = local % J.tiles_r, tcol = local / J.tiles_r;
+  const uint16_t* src = at<uint16_t>(bases, J.src);
+  uint16_t* dst = at<uint16_t>(bases, J.dst);
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int y = ty; y < 32; y += 8) {
+    const int i = tr * 32 + tx, j = tcol * 32 + y;
+    if (i < J.rows && j < J.cols) tile[y][tx] = src[i + J.ld_src * j];
+  }
+  __syncthreads();
+  for (int y = ty; y < 32; y += 8) {
+    const int j = tcol * 32 + tx, i = tr * 32 + y;
+    if (i < J.rows && j < J.cols) dst[j + J.ld_dst * i] = tile[tx][y];
+  }
+}
+
+int grid_for(int64_t work, int threads) {
+  const int64_t g = (work + threads - 1) / threads;
+  return (int)(g < 1 ? 1 : (g > 152 * 16 ? 152 * 16 : g));
+}
+
+}  // namespace
+
+void launch_simt_gemm_f32(const SimtJob* jobs, int njobs, int total_tiles, const Bases& bases,
+                          cudaStream_t stream) {
+  simt_gemm_f32_kernel<<<total_tiles, 256, 0, stream>>>(jobs, njobs, bases);
+}
+
+void launch_core_sketch_f32(const CoreSketchF32Job* jobs, int njobs, int64_t total, const Bases& bases,
+                            cudaStream_t stream) {
+  core_sketch_f32_kernel<<<grid_for(total, 128), 128, 0, stream>>>(jobs, njobs, total, bases);
+}
+
+void launch_split_f64(const SplitJob* jobs, int njobs, int64_t total, const Bases& bases, cudaStream_t stream) {
+  split_f64_kernel<<<grid_for(total, 256), 256, 0, stream>>>(jobs, njobs, total, bases);
+}
+
+void launch_transpose_bf16(const TransposeJob* jobs, int njobs, int total_tiles, const Bases& bases,
+                           cudaStream_t stream) {
+  transpose_bf16_kernel<<<total_tiles, 256, 0, stream>>>(jobs, njobs, bases);
+}
+
+}  // namespace tks

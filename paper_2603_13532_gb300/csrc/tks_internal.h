@@ -67,11 +67,65 @@ struct GemmJob {
 // Gaussian draws of one (problem, mode): Omega (n x s, column-major).
 struct OmegaJob {
   Operand out;
+  Operand plane;       // bf16 copy (same layout) when has_plane
   int64_t count;       // n * s
   int64_t begin;       // prefix over jobs (elements)
   int32_t problem, mode;
   int32_t bf16;        // round to float32 then bfloat16
-  int32_t pad;
+  int32_t has_plane;
+};
+
+// Element types of typed operands.
+enum ElemType : int32_t { T_F64 = 0, T_F32 = 1, T_BF16 = 2 };
+
+// Float32 CUDA-core GEMM job with typed operands (same index scheme as GemmJob):
+//   C[i,j] = alpha * sum_k A[i,k] B[k,j], written as float32, float64 and/or split into
+//   bfloat16 planes (hi, mid, lo), all at C + i c_m + j c_n + batch c_b.
+struct SimtJob {
+  int32_t M, N, K, K1;
+  int32_t batch, tiles_m, tiles_n, tile_begin;
+  Operand A, B;
+  int32_t a_type, b_type;
+  int64_t a_m, a_k0, a_k1, a_b;
+  int64_t b_n, b_k0, b_k1, b_b;
+  Operand c32, c64, cb[3];
+  int32_t has_c32, has_c64, nbf, pad;
+  int64_t c_m, c_n, c_b;
+  float alpha, pad2;
+};
+
+// Khatri-Rao / Kronecker core sketch in float32: G_k (bf16) and M_j (float32) in, V_kn out as
+// bfloat16 planes of Vcat_n (element (r, c) at r + ldv c).
+struct CoreSketchF32Job {
+  Operand core;
+  Operand M[MAXD];
+  Operand V[3];
+  int32_t d, n, kron, ldv;
+  int32_t r[MAXD];
+  int32_t roff[MAXD];
+  int32_t R[MAXD];
+  int32_t s[MAXD];
+  int32_t S, pad;
+  float alpha, pad2;
+  int64_t count;
+  int64_t begin;
+};
+
+// Split a float64 matrix (rows x cols, element (i, j) at i + ld_src j) into bf16 planes
+// hi + mid + lo (element (i, j) at i + ld_dst j).
+struct SplitJob {
+  Operand src;
+  Operand dst[3];
+  int64_t rows, cols, ld_src, ld_dst;
+  int64_t count, begin;
+};
+
+// Transpose a bf16 matrix: dst[j + ld_dst i] = src[i + ld_src j] (src rows x cols).
+struct TransposeJob {
+  Operand src, dst;
+  int32_t rows, cols;
+  int64_t ld_src, ld_dst;
+  int32_t tiles_r, tiles_c, tile_begin, pad;
 };
 
 // Structured core sketch of one (term, mode n): V_kn (r_kn x S_n) into rows
@@ -129,6 +183,26 @@ struct TcJob {
   int32_t mapA[3], mapB[3];
   uint8_t pa[8], pb[8];
   TcEpi epi;
+};
+
+// Householder QR in float32 of a tall matrix A (rows x cols) read through a two-level row
+// index: element (i, j) with i = i0 + L0 i1 at src[i0 s0 + i1 s1 + j sc] (src of type src_type).
+// Outputs: the orthonormal factor Q (rows x b, float64, diag(R) >= 0) and/or the triangular
+// factor R (b x b, float32, column-major), b = min(rows, cols).
+struct QrF32Job {
+  Operand src, W, tau, Q, R;
+  int32_t src_type, want_q, want_r, b;
+  int64_t rows, cols, L0, s0, s1, sc;
+};
+
+// One-sided (Hestenes) Jacobi SVD in float32 of the b x b factor R of H_(n)^T = Q~ R: its right
+// singular vectors are the left singular vectors of H_(n).  Selects the rank (min(rmax, b), or
+// the tolerance rule of Alg. 2 with theta = tol^2 ||H||^2 / d fixed at the first mode) and
+// writes P = leading right singular vectors (b x rmax, float32, zero-padded).
+struct SvdJob {
+  Operand R, P, sv, theta, rank;
+  int32_t b, rmax, first_mode, order;
+  double tol;
 };
 
 struct Status {

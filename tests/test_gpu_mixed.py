@@ -1,0 +1,130 @@
+"""GPU parity of the mixed-precision path (TKS_MIXED) against the FP64 CPU oracle, through the C ABI.
+
+The mixed path reads bfloat16 cores and factors and sketches with Omega rounded to float32 then
+bfloat16; the oracle runs on the same bfloat16-valued inputs and the same rounded Omega in
+float64, so every difference is arithmetic of the GPU path:
+
+  Omega              bit-exact
+  Y_n, H (given Q)   1e-5 relative Frobenius.  Products with bf16 inputs are exact in float32;
+                     float32 operands enter the tensor cores as three bf16 planes (about 2^-24
+                     relative) and every sum is accumulated in float32 (about 1e-7 relative per
+                     element, times sqrt of the reduction length)
+  recompression      |X~_gpu - X~_oracle| / ||X|| <= 1e-5 on sampled entries, and the two
+                     truncation errors agree to 1e-5 (the accuracy target of the mixed path)
+"""
+import numpy as np
+import pytest
+
+from oracle import rng
+from oracle import sketch_sum as ss
+from oracle.tensor import tucker_entries, tucker_full, tucker_sum_full
+from paper_2603_13532_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+def _plan(problems, kind, seed, tol=0.0):
+    from paper_2603_13532_gb300 import binding
+    return binding.Plan(problems, kind=kind, precision="mixed", seed=seed, tol=tol)
+
+
+def _rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300)
+
+
+def _bf16_problems(d, seed=0):
+    """Ragged sizes: n a multiple of 8 (TMA row alignment) but not of the 128/64 tiles."""
+    g = np.random.default_rng(200 + d + seed)
+    probs = []
+    for dims, K in ([[72, 40, 136, 48][:d], 3], [[24, 96, 8, 56][:d], 2], [[200] * d, 6]):
+        cores, facs = [], []
+        for _ in range(K):
+            r = [min(int(x), n) for x, n in zip(g.integers(1, 9, size=d), dims)]
+            cores.append(g.standard_normal(r))
+            facs.append([g.standard_normal((n, ri)) for n, ri in zip(dims, r)])
+        p = wl.Problem(list(dims), cores, facs, [6] * d, [2] * d, alpha=list(g.standard_normal(K)))
+        probs.append(p)
+    return wl._finish(probs, True)
+
+
+def _oracle(p, kind, seed, problem, **kw):
+    return ss.recompress(p.terms(), kind, p.target, p.oversampling, seed=seed, problem=problem,
+                         alpha=p.alpha, rounding="bf16", **kw)
+
+
+def test_mixed_omega_is_rounded_draws(cuda_lib):
+    probs = _bf16_problems(3)
+    plan = _plan(probs, "krp", 31)
+    om = plan.omega()
+    for p, (prob, pi) in enumerate(zip(probs, plan.pinfo)):
+        for m in range(3):
+            ref = rng.omega(31, p, m, prob.dims[m], pi.omega_cols[m], rounding="bf16")
+            assert np.array_equal(om[p][m], ref)
+
+
+@pytest.mark.parametrize("kind", ["krp", "kron"])
+@pytest.mark.parametrize("d", [3, 4])
+def test_mixed_sketch_matches_oracle(cuda_lib, kind, d):
+    probs = _bf16_problems(d)
+    Ys = _plan(probs, kind, 5).sketch()
+    for i, prob in enumerate(probs):
+        ref = _oracle(prob, kind, 5, i)
+        for m in range(d):
+            assert _rel(Ys[i][m], ref["Y"][m]) <= 1e-5, (kind, d, i, m, _rel(Ys[i][m], ref["Y"][m]))
+
+
+@pytest.mark.parametrize("kind", ["krp", "kron"])
+@pytest.mark.parametrize("d", [2, 3, 4])
+def test_mixed_projection_matches_oracle_given_q(cuda_lib, kind, d):
+    probs = _bf16_problems(d, 1)
+    refs = [_oracle(p, kind, 6, i) for i, p in enumerate(probs)]
+    Hs = _plan(probs, kind, 6).project([r["Q"] for r in refs])
+    for H, r in zip(Hs, refs):
+        assert _rel(H, r["H"]) <= 1e-5
+
+
+@pytest.mark.parametrize("kind", ["kron", "krp"])
+def test_mixed_recompress_small(cuda_lib, kind):
+    probs = _bf16_problems(3, 2)
+    outs = _plan(probs, kind, 7).recompress()
+    for i, (prob, got) in enumerate(zip(probs, outs)):
+        ref = _oracle(prob, kind, 7, i)
+        X = sum(a * tucker_full(G, Us) for a, (G, Us) in zip(prob.alpha, prob.terms()))
+        Xg = tucker_full(got["core"], got["factors"])
+        Xo = tucker_full(ref["core"], ref["factors"])
+        nx = np.linalg.norm(X)
+        assert np.linalg.norm(Xg - Xo) / nx <= 1e-5
+        assert abs(np.linalg.norm(Xg - X) - np.linalg.norm(Xo - X)) / nx <= 1e-5
+        assert got["ranks"] == ref["ranks"]
+
+
+def test_mixed_decay512_full_size(cuda_lib):
+    w = wl.decay512()
+    p = w.problems[0]
+    plan = _plan(w.problems, "krp", w.seed)
+    ref = _oracle(p, "krp", w.seed, 0)
+    Ys = plan.sketch()[0]
+    for m in range(3):
+        assert _rel(Ys[m], ref["Y"][m]) <= 1e-5
+    assert _rel(plan.project([ref["Q"]])[0], ref["H"]) <= 1e-5
+    got = plan.recompress()[0]
+    assert got["ranks"] == ref["ranks"] == [48, 48, 48]
+    idx = np.random.default_rng(1).integers(0, 512, size=(400, 3))
+    eg = tucker_entries(got["core"], got["factors"], idx)
+    eo = tucker_entries(ref["core"], ref["factors"], idx)
+    ex = sum(tucker_entries(G, Us, idx) for G, Us in p.terms())
+    scale = np.sqrt(np.mean(ex ** 2))
+    assert np.sqrt(np.mean((eg - eo) ** 2)) <= 1e-5 * scale
+    # both truncations are ~1e-6 of ||X|| here; their sampled errors agree to 1e-5
+    assert abs(np.sqrt(np.mean((eg - ex) ** 2)) - np.sqrt(np.mean((eo - ex) ** 2))) <= 1e-5 * scale
+
+
+def test_mixed_rejects_unaligned_mode_size(cuda_lib):
+    from paper_2603_13532_gb300 import binding
+    g = np.random.default_rng(3)
+    dims = [20, 16, 16]
+    p = wl.Problem(dims, [g.standard_normal((2, 2, 2))], [[g.standard_normal((n, 2)) for n in dims]],
+                   [3, 3, 3], [1, 1, 1])
+    with pytest.raises(binding.TksError) as e:
+        _plan(wl._finish([p], True), "krp", 1)
+    assert e.value.code == 7
