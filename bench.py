@@ -44,7 +44,8 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "mixed", "mixed_f32la"], default="mixed_f32la")
+    ap.add_argument("--fp64-steps", type=int, default=3, help="timed steps of the FP64 comparison")
     ap.add_argument("--problems", type=int, default=64, help="independent sums per step and GPU")
     ap.add_argument("--seed", type=int, default=20260315)
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="budget of the cpu_baseline sample")
@@ -57,6 +58,22 @@ def parse_args():
 def workload_label(P):
     return (f"decay512 x{P}: d=3, n=512, K=32, r~U{{8..32}}, mode spectra 10^(-i/8), Khatri-Rao, "
             f"target 48, oversampling 10")
+
+
+def sampled_entries(core, factors, idx):
+    """Entries of the Tucker tensor [[core; factors]] at integer index rows idx (m x d)."""
+    import numpy as np
+    W = np.einsum("ia,ib,ic,abc->i", factors[0][idx[:, 0]], factors[1][idx[:, 1]], factors[2][idx[:, 2]], core) \
+        if core.ndim == 3 else None
+    if W is None:
+        out = []
+        for ii in idx:
+            T = core
+            for k, U in enumerate(factors):
+                T = np.tensordot(U[ii[k]], T, axes=(0, 0))
+            out.append(float(T))
+        W = np.array(out)
+    return W
 
 
 def make_problems(P, seed, rank, bf16):
@@ -156,7 +173,7 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     from paper_2603_13532_gb300 import workloads as wl
-    bf16 = args.precision == "mixed"
+    bf16 = args.precision != "fp64"
     per_step = 2
     probs = make_problems(per_step * (args.steps + args.warmup), args.seed, 0, bf16)
     rounding = "bf16" if bf16 else None
@@ -198,29 +215,49 @@ def time_steps(fn, steps, stream):
     return start.elapsed_time(end) / 1e3
 
 
-def roofline_from_profile(prof, calls, peaks, peak_kind):
-    """The dominant launch of the profiled calls and its achieved rate against its peak."""
+FP32_PEAK_TFLOPS = 152 * 256 * 2.070e9 / 1e12   # 128 FP32 FMA per SM per clock
+FP64_KINDS = {"gemm", "reduce", "qr", "core_sketch", "eig"}
+FP32_KINDS = {"simt", "core_sketch32", "qr32", "svd32"}
+
+
+def roofline_from_profile(prof, calls, peaks):
+    """The longest launch with an algorithmic count, and its achieved rate against its roofline.
+
+    FP64 CUDA-core launches are bound by the FP64 pipe, FP32 CUDA-core launches by the FP32 pipe
+    (peaks from unit counts and the 2070 MHz clock); tensor-core launches by the tensor pipe or
+    HBM, whichever the launch's algorithmic arithmetic intensity puts first (ridge = sustained
+    bf16 peak / HBM bandwidth).
+    """
     total_ms = sum(s["ms"] for s in prof)
-    # the longest launch that has an algorithmic flop or byte count (the iterative eigensolver
-    # has none); its share of the call is reported next to it
     counted = [s for s in prof if s["flops"] > 0 or s["bytes"] > 0]
     top = max(counted or prof, key=lambda s: s["ms"])
     overall_top = max(prof, key=lambda s: s["ms"])
     avg_s = top["ms"] / 1e3 / max(1, calls)
-    if top["kind"] in ("gemm", "qr", "core_sketch") and top["flops"] > 0 and peak_kind == "fp64":
-        achieved = top["flops"] / avg_s / 1e12
-        peak = FP64_PEAK_TFLOPS
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
-                "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz"}
+    kind = top["kind"]
+    if kind in FP64_KINDS and top["flops"] > 0:
+        roof = {"bound": "alu", "achieved": top["flops"] / avg_s / 1e12, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "peak_source": "derived FP64: 152 SMs x 4 flop/clk x 2070 MHz"}
+    elif kind in FP32_KINDS and top["flops"] > 0:
+        roof = {"bound": "alu", "achieved": top["flops"] / avg_s / 1e12, "peak": FP32_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "peak_source": "derived FP32: 152 SMs x 256 flop/clk x 2070 MHz"}
     else:
-        achieved = top["bytes"] / avg_s / 1e9
-        peak = peaks["hbm_gbs"]
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "peak_source": "MEASURED_PEAKS hbm_gbs"}
+        ridge = peaks["bf16_tflops_sustained"] * 1e12 / (peaks["hbm_gbs"] * 1e9)
+        ai = top["flops"] / top["bytes"] if top["bytes"] > 0 else float("inf")
+        if ai > ridge:
+            roof = {"bound": "tensor", "achieved": top["flops"] / avg_s / 1e12,
+                    "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s",
+                    "peak_source": "measured bf16 sustained"}
+        else:
+            roof = {"bound": "hbm", "achieved": top["bytes"] / avg_s / 1e9, "peak": peaks["hbm_gbs"],
+                    "unit": "GB/s", "peak_source": "measured hbm_gbs"}
+        roof["arithmetic_intensity"] = ai
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
     roof["kernel"] = top["name"]
     roof["kernel_share"] = top["ms"] / total_ms if total_ms > 0 else None
     roof["avg_launch_ms"] = avg_s * 1e3
+    roof["algorithmic_flops_per_launch"] = top["flops"]
+    roof["algorithmic_bytes_per_launch"] = top["bytes"]
     if overall_top is not top:
         roof["longest_launch"] = {"name": overall_top["name"],
                                   "share": overall_top["ms"] / total_ms if total_ms > 0 else None}
@@ -251,7 +288,7 @@ def main():
 
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
-    bf16 = args.precision == "mixed"
+    bf16 = args.precision != "fp64"
     P = args.problems
     problems = make_problems(P, args.seed, rank, bf16)
     plan = binding.Plan(problems, kind="krp", precision=args.precision, seed=args.seed, device=device)
@@ -287,7 +324,7 @@ def main():
     tflops = (plan.info.flops_lowprec + plan.info.flops_fp64) * world * args.steps / elapsed / 1e12
 
     peaks, peak_src = load_peaks()
-    roof = roofline_from_profile(prof, args.steps, peaks, "fp64" if args.precision == "fp64" else "mixed")
+    roof = roofline_from_profile(prof, args.steps, peaks)
     roof["peak_file"] = peak_src
 
     # end to end: pinned host inputs -> device, recompress, result -> pinned host, every step
@@ -315,6 +352,39 @@ def main():
                "h2d_bytes_per_step": int(host_in.numel() * host_in.element_size()),
                "d2h_bytes_per_step": int(host_out.numel() * 8 + host_ranks.numel() * 4)}
 
+    # the plain FP64 GPU path on the same batch (same values, float64 storage), and the
+    # difference of the two results on sampled entries of the recompressed tensors
+    fp64_path = None
+    if args.precision != "fp64" and args.fp64_steps > 0:
+        import numpy as _np
+        plan64 = binding.Plan(problems, kind="krp", precision="fp64", seed=args.seed, device=device)
+        out64 = torch.zeros(plan64.info.output_elems, dtype=torch.float64, device=device)
+        r64 = torch.zeros_like(ranks_t)
+
+        def step64():
+            plan64.recompress_raw(out64, r64)
+
+        step64()
+        plan64.sync()
+        el64 = time_steps(step64, args.fp64_steps, stream)
+        plan64.sync()
+        res_m = plan.unpack(out, ranks_t)
+        res_d = plan64.unpack(out64, r64)
+        g = _np.random.default_rng(0)
+        worst = 0.0
+        for pm, pd, pr in list(zip(res_m, res_d, problems))[:8]:
+            idx = _np.stack([g.integers(0, n, size=256) for n in pr.dims], axis=1)
+            em = sampled_entries(pm["core"], pm["factors"], idx)
+            ed = sampled_entries(pd["core"], pd["factors"], idx)
+            worst = max(worst, float(_np.sqrt(_np.mean((em - ed) ** 2)) / _np.sqrt(_np.mean(ed ** 2))))
+        v64 = P * args.fp64_steps / el64
+        fp64_path = {"value": v64 * world, "unit": UNIT, "ms_per_step": 1e3 * el64 / args.fp64_steps,
+                     "steps": args.fp64_steps, "speedup": value / (v64 * world),
+                     "rel_diff_sampled": worst,
+                     "rel_diff_note": "rms difference of 256 sampled entries per problem (8 problems) of the "
+                                      "mixed and FP64 recompressed tensors, relative to the FP64 entries' rms"}
+        del plan64
+
     line = None
     if rank == 0:
         in_bytes = plan.flat_inputs.numel() * plan.flat_inputs.element_size()
@@ -335,7 +405,7 @@ def main():
                            "flops_per_step": plan.info.flops_lowprec + plan.info.flops_fp64,
                            "l2": f"inputs {in_bytes / 1e6:.0f} MB per GPU > L2 129 MB, no flush",
                            "parallelism": f"replicas x{world}"},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fp64_path": fp64_path,
                 "gpu_launches": int(plan.info.launches_recompress) * args.steps,
                 "clocks": clock_info,
                 "stages": [{"name": s["name"], "ms_per_call": s["ms"] / max(1, s["calls"])} for s in prof]}

@@ -65,9 +65,12 @@ typedef enum { TKS_SKETCH_KRON = 0, TKS_SKETCH_KRP = 1 } tks_sketch;
 
 typedef enum {
   TKS_FP64 = 0,   /* every stage in float64 on CUDA cores (the plain FP64 GPU path) */
-  TKS_MIXED = 1   /* contractions on tcgen05 tensor cores with bfloat16 operands (a float32
+  TKS_MIXED = 1,  /* contractions on tcgen05 tensor cores with bfloat16 operands (a float32
                      operand is split into bfloat16 planes) and float32 accumulation; QR and
                      ST-HOSVD as in TKS_FP64 */
+  TKS_MIXED_F32LA = 2  /* contractions as TKS_MIXED; QR of Y_n and ST-HOSVD in float32 with
+                          backward-stable algorithms (Householder QR, one-sided Jacobi SVD of
+                          the triangular factor of H_(n)^T; no Gram matrices) */
 } tks_precision;
 
 typedef enum { TKS_DT_F64 = 0, TKS_DT_BF16 = 1 } tks_dtype;
@@ -93,7 +96,8 @@ typedef struct {
 
 typedef struct {
   tks_sketch sketch;            /* Kronecker (Alg. 3) or Khatri-Rao (Alg. 4) */
-  tks_precision precision;      /* TKS_FP64 needs dtype F64; TKS_MIXED needs dtype BF16 */
+  tks_precision precision;      /* TKS_FP64 needs dtype F64; the mixed modes need dtype BF16
+                                   and n_m % 8 == 0 with 16-byte aligned factors */
   tks_dtype dtype;              /* element type of cores and factors */
   uint64_t seed;                /* key of the Gaussian draws (Philox4x64-10) */
   double trunc_tol;             /* 0: keep min(target_n, b_n) columns per mode; > 0: the

@@ -15,12 +15,13 @@ from .build import LIB_PATH
 
 MAX_ORDER = 6
 SKETCH = {"kron": 0, "krp": 1}
-PRECISION = {"fp64": 0, "mixed": 1}
+PRECISION = {"fp64": 0, "mixed": 1, "mixed_f32la": 2}
 DTYPE = {"fp64": 0, "bf16": 1}
 STATUS = {0: "TKS_OK", 1: "TKS_EINVAL", 2: "TKS_ENOMEM", 3: "TKS_ECUDA", 4: "TKS_ETIMEOUT",
           5: "TKS_ENONFINITE", 6: "TKS_ENOCONV", 7: "TKS_EUNSUPPORTED"}
 
-STEP_KINDS = {0: "omega", 1: "gemm", 2: "reduce", 3: "core_sketch", 4: "qr", 5: "eig"}
+STEP_KINDS = {0: "omega", 1: "gemm", 2: "reduce", 3: "core_sketch", 4: "qr", 5: "eig", 6: "tc", 7: "simt",
+              8: "core_sketch32", 9: "split", 10: "transpose", 11: "qr32", 12: "svd32"}
 
 
 class TksError(RuntimeError):

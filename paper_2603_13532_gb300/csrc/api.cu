@@ -46,7 +46,7 @@ Operand op_abs(const void* p, size_t off_bytes = 0) {
 }
 
 enum StepKind { S_OMEGA, S_GEMM, S_REDUCE, S_CORESKETCH, S_QR, S_EIG, S_TC, S_SIMT, S_CS32, S_SPLIT,
-                S_TRANSPOSE };
+                S_TRANSPOSE, S_QR32, S_SVD32 };
 
 struct Step {
   StepKind kind;
@@ -93,6 +93,7 @@ struct ProbHost {
   size_t om_plane[MAXD] = {}, UT[MAXD] = {}, M32[MAXD] = {}, Vp[MAXD][3] = {}, Qp[MAXD][3] = {};
   size_t AT32[MAXD] = {}, ATp[MAXD][3] = {}, Tp[3] = {};
   int ldU[MAXD] = {}, ldV[MAXD] = {}, ldA[MAXD] = {}, ldT = 0;
+  size_t Wh = 0, tauh = 0, R32 = 0, P32[MAXD] = {}, sv[MAXD] = {};   // float32 ST-HOSVD
   int gram_ksplit = 1;
   double flops_low = 0.0, flops_f64 = 0.0;
 };
@@ -394,7 +395,8 @@ namespace {
 //   a6  A_n^T = Ucat_n^T Q_n              A = Ucat_n (rows r, k = i)    B = Q_n planes (rows a)
 //   a7  per-term chains in float32, last step written as planes of Tcat (element (r, J) at r + ldT J)
 //   a8  H_(d)^T = Tcat^T A_d^T            A = Tcat planes (rows J)      B = A_d^T planes (rows a)
-static void build_mixed_stages(tks_plan* plan, int kron) {
+static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
+  std::vector<QrF32Job> qr32;
   std::vector<OmegaJob> om;
   int64_t om_blocks = 0;
   std::vector<TransposeJob> tr;
@@ -501,16 +503,35 @@ static void build_mixed_stages(tks_plan* plan, int kron) {
       a4.epi.f64_m = 1;
       a4.epi.f64_n = (int64_t)nn;
       tcY.push_back(a4);
-      QrJob q;
-      std::memset(&q, 0, sizeof(q));
-      q.Y = op(B_Y, h.y_off[n] * 8);
-      q.W = op(B_WS, h.W[n]);
-      q.Q = op(B_Q, h.q_off[n] * 8);
-      q.tau = op(B_WS, h.tau[n]);
-      q.n = (int)nn;
-      q.S = h.S[n];
-      q.b = h.b[n];
-      qr.push_back(q);
+      if (f32la) {
+        QrF32Job q;
+        std::memset(&q, 0, sizeof(q));
+        q.src = op(B_Y, h.y_off[n] * 8);
+        q.src_type = T_F64;
+        q.W = op(B_WS, h.W[n]);
+        q.tau = op(B_WS, h.tau[n]);
+        q.Q = op(B_Q, h.q_off[n] * 8);
+        q.want_q = 1;
+        q.b = h.b[n];
+        q.rows = (int64_t)nn;
+        q.cols = h.S[n];
+        q.L0 = (int64_t)nn;
+        q.s0 = 1;
+        q.s1 = 0;
+        q.sc = (int64_t)nn;
+        qr32.push_back(q);
+      } else {
+        QrJob q;
+        std::memset(&q, 0, sizeof(q));
+        q.Y = op(B_Y, h.y_off[n] * 8);
+        q.W = op(B_WS, h.W[n]);
+        q.Q = op(B_Q, h.q_off[n] * 8);
+        q.tau = op(B_WS, h.tau[n]);
+        q.n = (int)nn;
+        q.S = h.S[n];
+        q.b = h.b[n];
+        qr.push_back(q);
+      }
       qr_flops += 4.0 * (double)nn * h.b[n] * h.b[n];
       qr_bytes += 8.0 * (double)nn * (h.S[n] + h.b[n]);
       SplitJob sj;
@@ -624,7 +645,106 @@ static void build_mixed_stages(tks_plan* plan, int kron) {
   plan->push_tc(plan->st_project, tcH, "a8:H=Tcat.AT[tc]");
   plan->st_recompress = plan->st_sketch;
   plan->push(plan->st_recompress, S_QR, qr, (int64_t)qr.size(), "a5:qr", qr_flops, qr_bytes);
+  plan->push(plan->st_recompress, S_QR32, qr32, (int64_t)qr32.size(), "a5:qr[f32]", qr_flops, qr_bytes);
   for (const auto& st : plan->st_project) plan->st_recompress.push_back(st);
+}
+
+// ST-HOSVD of H in float32 (Alg. 2 phase 2, modes 1..d in order): per mode, Householder QR of
+// H_(n)^T (rows = the other modes, two-level index), one-sided Jacobi SVD of its b x b triangular
+// factor (right singular vectors = left singular vectors of H_(n)), rank rule, then
+// H <- H x_n P_n^T and U~_n = Q_n P_n on CUDA cores.
+static void build_hosvd_f32(tks_plan* plan) {
+  for (int n = 0; n < plan->dmax; ++n) {
+    std::vector<QrF32Job> qrs;
+    std::vector<SvdJob> svds;
+    std::vector<SimtJob> ttm, fac;
+    double qflops = 0.0;
+    for (int p = 0; p < plan->nprob; ++p) {
+      auto& h = plan->probs[p];
+      const int d = h.d;
+      if (n >= d) continue;
+      int64_t L = 1, Rr = 1;
+      for (int j = 0; j < n; ++j) L *= h.rmax[j];
+      for (int j = n + 1; j < d; ++j) Rr *= h.b[j];
+      const int b = h.b[n], rmax = h.rmax[n];
+      const Operand X = (n == 0) ? op(B_H, h.h_off * 8) : op(B_WS, h.Hp[(n - 1) & 1]);
+      const int32_t xt = (n == 0) ? T_F64 : T_F32;
+      QrF32Job q;
+      std::memset(&q, 0, sizeof(q));
+      q.src = X;
+      q.src_type = xt;
+      q.W = op(B_WS, h.Wh);
+      q.tau = op(B_WS, h.tauh);
+      q.R = op(B_WS, h.R32);
+      q.want_r = 1;
+      q.rows = L * Rr;
+      q.cols = b;
+      q.b = (int)std::min<int64_t>(q.rows, b);
+      q.L0 = L;
+      q.s0 = 1;
+      q.s1 = L * b;
+      q.sc = L;
+      qrs.push_back(q);
+      qflops += 2.0 * (double)q.rows * b * b;
+      SvdJob sj;
+      std::memset(&sj, 0, sizeof(sj));
+      sj.R = op(B_WS, h.R32);
+      sj.P = op(B_WS, h.P32[n]);
+      sj.sv = op(B_WS, h.sv[n]);
+      sj.theta = op(B_WS, h.theta);
+      sj.rank = op(B_RANKS, (size_t)(p * TKS_MAX_ORDER + n) * 4);
+      sj.b = b;
+      sj.rmax = rmax;
+      sj.first_mode = (n == 0);
+      sj.order = d;
+      sj.tol = plan->params.trunc_tol;
+      svds.push_back(sj);
+      SimtJob t;
+      std::memset(&t, 0, sizeof(t));
+      t.batch = 1;
+      t.alpha = 1.0f;
+      if (L == 1) {
+        t.M = rmax; t.N = (int)Rr; t.K = b; t.K1 = b;
+        t.A = op(B_WS, h.P32[n]); t.a_type = T_F32; t.a_m = b; t.a_k0 = 1;
+        t.B = X; t.b_type = xt; t.b_n = b; t.b_k0 = 1;
+        t.c_m = 1; t.c_n = rmax;
+      } else {
+        t.M = (int)L; t.N = rmax; t.K = b; t.K1 = b; t.batch = (int)Rr;
+        t.A = X; t.a_type = xt; t.a_m = 1; t.a_k0 = L; t.a_b = L * b;
+        t.B = op(B_WS, h.P32[n]); t.b_type = T_F32; t.b_n = b; t.b_k0 = 1;
+        t.c_m = 1; t.c_n = L; t.c_b = L * rmax;
+      }
+      if (n == d - 1) {
+        t.has_c64 = 1;
+        t.c64 = op(B_OUT, h.out_core_off * 8);
+      } else {
+        t.has_c32 = 1;
+        t.c32 = op(B_WS, h.Hp[n & 1]);
+      }
+      ttm.push_back(t);
+      SimtJob f;
+      std::memset(&f, 0, sizeof(f));
+      f.batch = 1;
+      f.alpha = 1.0f;
+      f.M = (int)h.n[n]; f.N = rmax; f.K = b; f.K1 = b;
+      f.A = op(B_Q, h.q_off[n] * 8); f.a_type = T_F64; f.a_m = 1; f.a_k0 = h.n[n];
+      f.B = op(B_WS, h.P32[n]); f.b_type = T_F32; f.b_n = b; f.b_k0 = 1;
+      f.has_c64 = 1;
+      f.c64 = op(B_OUT, h.out_fac_off[n] * 8);
+      f.c_m = 1;
+      f.c_n = h.n[n];
+      fac.push_back(f);
+    }
+    char nm[32];
+    std::snprintf(nm, sizeof(nm), "a9:qr%d[f32]", n);
+    plan->push(plan->st_recompress, S_QR32, qrs, (int64_t)qrs.size(), nm, qflops, 0.0);
+    std::snprintf(nm, sizeof(nm), "a9:svd%d[f32]", n);
+    plan->push(plan->st_recompress, S_SVD32, svds, (int64_t)svds.size(), nm);
+    std::snprintf(nm, sizeof(nm), "a9:ttm%d[f32]", n);
+    plan->push_simt(plan->st_recompress, ttm, nm);
+    std::snprintf(nm, sizeof(nm), "a9:factor%d[f32]", n);
+    plan->push_simt(plan->st_recompress, fac, nm);
+  }
 }
 
 }  // namespace
@@ -665,8 +785,8 @@ tks_status tks_plan_create(tks_plan** out, const tks_problem* problems, int32_t 
   if (!(prm.trunc_tol >= 0.0) || !std::isfinite(prm.trunc_tol)) return fail(TKS_EINVAL, "bad trunc_tol");
   if (prm.precision == TKS_FP64) {
     if (prm.dtype != TKS_DT_F64) return fail(TKS_EINVAL, "TKS_FP64 needs float64 cores and factors");
-  } else if (prm.precision == TKS_MIXED) {
-    if (prm.dtype != TKS_DT_BF16) return fail(TKS_EINVAL, "TKS_MIXED needs bfloat16 cores and factors");
+  } else if (prm.precision == TKS_MIXED || prm.precision == TKS_MIXED_F32LA) {
+    if (prm.dtype != TKS_DT_BF16) return fail(TKS_EINVAL, "the mixed modes need bfloat16 cores and factors");
   } else {
     return fail(TKS_EINVAL, "bad precision");
   }
@@ -676,7 +796,8 @@ tks_status tks_plan_create(tks_plan** out, const tks_problem* problems, int32_t 
   plan->nprob = num_problems;
   plan->probs.resize(num_problems);
   const int kron = prm.sketch == TKS_SKETCH_KRON;
-  const bool mixed = prm.precision == TKS_MIXED;
+  const bool mixed = prm.precision != TKS_FP64;
+  const bool f32la = prm.precision == TKS_MIXED_F32LA;
   for (int p = 0; p < num_problems; ++p) {
     tks_status st = validate_and_size(problems[p], prm, plan->probs[p], p);
     if (st == TKS_OK && mixed) {
@@ -785,12 +906,21 @@ tks_status tks_plan_create(tks_plan** out, const tks_problem* problems, int32_t 
     h.theta = alloc(8);
     h.Hp[0] = alloc(Hsz * 8);
     h.Hp[1] = alloc(Hsz * 8);
+    if (f32la) {
+      h.Wh = alloc(Hsz * 4);
+      h.tauh = alloc((size_t)bm * 4);
+      h.R32 = alloc((size_t)bm * bm * 4);
+      for (int m = 0; m < d; ++m) {
+        h.P32[m] = alloc((size_t)h.b[m] * h.rmax[m] * 4);
+        h.sv[m] = alloc((size_t)h.b[m] * 4);
+      }
+    }
   }
   plan->ws_bytes = align_up(ws);
 
   // ---- launch tables
   if (mixed) {
-    build_mixed_stages(plan, kron);
+    build_mixed_stages(plan, kron, f32la);
   } else {
   std::vector<OmegaJob> om_ext, om_int;
   int64_t om_blocks = 0;
@@ -925,7 +1055,8 @@ tks_status tks_plan_create(tks_plan** out, const tks_problem* problems, int32_t 
   plan->push(plan->st_recompress, S_QR, qr, (int64_t)qr.size(), "a5:qr", qr_flops, qr_bytes);
   for (const auto& s : plan->st_project) plan->st_recompress.push_back(s);
   }
-  for (int n = 0; n < plan->dmax; ++n) {
+  if (f32la) build_hosvd_f32(plan);
+  for (int n = 0; n < plan->dmax && !f32la; ++n) {
     GemmList gram, ttm, fac;
     std::vector<EigJob> eig;
     for (int p = 0; p < plan->nprob; ++p) {
@@ -994,6 +1125,13 @@ tks_status tks_plan_create(tks_plan** out, const tks_problem* problems, int32_t 
     if (e != cudaSuccess) {
       tks_plan_destroy(plan);
       return fail(TKS_ECUDA, std::string("eigensolver shared memory: ") + cudaGetErrorString(e));
+    }
+  }
+  if (f32la) {
+    cudaError_t e = prepare_svd_f32(plan->bmax);
+    if (e != cudaSuccess) {
+      tks_plan_destroy(plan);
+      return fail(TKS_ECUDA, std::string("SVD shared memory: ") + cudaGetErrorString(e));
     }
   }
   if (mixed) {
@@ -1114,6 +1252,12 @@ tks_status run_steps(tks_plan* plan, const std::vector<Step>& steps, const Bases
         break;
       case S_TRANSPOSE:
         launch_transpose_bf16(static_cast<const TransposeJob*>(table), s.njobs, (int)s.work, bases, stream);
+        break;
+      case S_QR32:
+        launch_qr_f32(static_cast<const QrF32Job*>(table), s.njobs, bases, plan->status, stream);
+        break;
+      case S_SVD32:
+        launch_svd_f32(static_cast<const SvdJob*>(table), s.njobs, plan->bmax, bases, plan->status, stream);
         break;
     }
   }

@@ -97,10 +97,11 @@ __global__ void __launch_bounds__(512) qr_f32_kernel(const QrF32Job* __restrict_
     __syncthreads();
   }
   if (J.want_r) {
+    // R is cols x cols; rows at and below b = min(rows, cols) are zero (rank <= rows)
     float* R = at<float>(bases, J.R);
-    for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
-      const int c = e / b, r = e - c * b;
-      R[e] = (r <= c && c < S) ? W[r + n * c] : 0.f;
+    for (int e = threadIdx.x; e < S * S; e += blockDim.x) {
+      const int c = e / S, r = e - c * S;
+      R[e] = (r <= c && r < b) ? W[r + n * c] : 0.f;
     }
   }
   if (J.want_q) {

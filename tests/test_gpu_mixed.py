@@ -23,9 +23,12 @@ from paper_2603_13532_gb300 import workloads as wl
 pytestmark = pytest.mark.gpu
 
 
-def _plan(problems, kind, seed, tol=0.0):
+MODES = ["mixed", "mixed_f32la"]
+
+
+def _plan(problems, kind, seed, tol=0.0, precision="mixed"):
     from paper_2603_13532_gb300 import binding
-    return binding.Plan(problems, kind=kind, precision="mixed", seed=seed, tol=tol)
+    return binding.Plan(problems, kind=kind, precision=precision, seed=seed, tol=tol)
 
 
 def _rel(a, b):
@@ -83,10 +86,11 @@ def test_mixed_projection_matches_oracle_given_q(cuda_lib, kind, d):
         assert _rel(H, r["H"]) <= 1e-5
 
 
+@pytest.mark.parametrize("precision", MODES)
 @pytest.mark.parametrize("kind", ["kron", "krp"])
-def test_mixed_recompress_small(cuda_lib, kind):
+def test_mixed_recompress_small(cuda_lib, kind, precision):
     probs = _bf16_problems(3, 2)
-    outs = _plan(probs, kind, 7).recompress()
+    outs = _plan(probs, kind, 7, precision=precision).recompress()
     for i, (prob, got) in enumerate(zip(probs, outs)):
         ref = _oracle(prob, kind, 7, i)
         X = sum(a * tucker_full(G, Us) for a, (G, Us) in zip(prob.alpha, prob.terms()))
@@ -98,10 +102,11 @@ def test_mixed_recompress_small(cuda_lib, kind):
         assert got["ranks"] == ref["ranks"]
 
 
-def test_mixed_decay512_full_size(cuda_lib):
+@pytest.mark.parametrize("precision", MODES)
+def test_mixed_decay512_full_size(cuda_lib, precision):
     w = wl.decay512()
     p = w.problems[0]
-    plan = _plan(w.problems, "krp", w.seed)
+    plan = _plan(w.problems, "krp", w.seed, precision=precision)
     ref = _oracle(p, "krp", w.seed, 0)
     Ys = plan.sketch()[0]
     for m in range(3):
@@ -117,6 +122,24 @@ def test_mixed_decay512_full_size(cuda_lib):
     assert np.sqrt(np.mean((eg - eo) ** 2)) <= 1e-5 * scale
     # both truncations are ~1e-6 of ||X|| here; their sampled errors agree to 1e-5
     assert abs(np.sqrt(np.mean((eg - ex) ** 2)) - np.sqrt(np.mean((eo - ex) ** 2))) <= 1e-5 * scale
+
+
+@pytest.mark.parametrize("precision", MODES)
+def test_mixed_tolerance_rule_and_d4(cuda_lib, precision):
+    # Sec. 5.1.1-style low rank that survives bf16 rounding: every term uses the same bf16 basis
+    # Q_m (n x 10) and a rank-1 bf16 core, so each mode of the sum has rank 10 exactly
+    g = np.random.default_rng(4)
+    dims = [64, 48, 56, 40]
+    Qs = [wl.to_bf16_values(wl.haar(g, n, 10)) for n in dims]
+    cores = []
+    for _ in range(20):
+        vs = [g.standard_normal(10) for _ in dims]
+        cores.append(wl.to_bf16_values(np.einsum("a,b,c,d->abcd", *vs)))
+    prob = wl.Problem(dims, cores, [list(Qs) for _ in cores], [10] * 4, [2] * 4)
+    got = _plan([prob], "krp", 11, tol=1e-6, precision=precision).recompress()[0]
+    assert got["ranks"] == [10, 10, 10, 10]
+    X = tucker_sum_full(prob.terms())
+    assert np.linalg.norm(tucker_full(got["core"], got["factors"]) - X) <= 1e-5 * np.linalg.norm(X)
 
 
 def test_mixed_rejects_unaligned_mode_size(cuda_lib):
