@@ -37,6 +37,7 @@ tks_status fail(tks_status st, const std::string& msg) {
   } while (0)
 
 constexpr size_t kAlign = 256;
+constexpr int kTsqrBlockRows = 256;   // rows of one TSQR block (shared-memory Householder)
 inline size_t align_up(size_t x, size_t a = kAlign) { return (x + a - 1) / a * a; }
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
@@ -46,7 +47,7 @@ Operand op_abs(const void* p, size_t off_bytes = 0) {
 }
 
 enum StepKind { S_OMEGA, S_GEMM, S_REDUCE, S_CORESKETCH, S_QR, S_EIG, S_TC, S_SIMT, S_CS32, S_SPLIT,
-                S_TRANSPOSE, S_QR32, S_SVD32 };
+                S_TRANSPOSE, S_QR32, S_SVD32, S_TSQR, S_CS3, S_CHAIN3, S_QRSM };
 
 struct Step {
   StepKind kind;
@@ -56,6 +57,7 @@ struct Step {
   char name[32];
   double flops, bytes;
   int na_max = 0, nb_max = 0;   // tensor-core GEMM steps: planes per operand
+  size_t smem = 0;              // dynamic shared memory of one-CTA-per-job steps
 };
 
 Step make_step(StepKind kind, size_t off, int njobs, int64_t work, const char* name, double flops,
@@ -94,6 +96,7 @@ struct ProbHost {
   size_t AT32[MAXD] = {}, ATp[MAXD][3] = {}, Tp[3] = {};
   int ldU[MAXD] = {}, ldV[MAXD] = {}, ldA[MAXD] = {}, ldT = 0;
   size_t Wh = 0, tauh = 0, R32 = 0, P32[MAXD] = {}, sv[MAXD] = {};   // float32 ST-HOSVD
+  size_t stk[2] = {};                                                 // TSQR stacked factors
   int gram_ksplit = 1;
   double flops_low = 0.0, flops_f64 = 0.0;
 };
@@ -396,7 +399,14 @@ namespace {
 //   a7  per-term chains in float32, last step written as planes of Tcat (element (r, J) at r + ldT J)
 //   a8  H_(d)^T = Tcat^T A_d^T            A = Tcat planes (rows J)      B = A_d^T planes (rows a)
 static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
-  std::vector<QrF32Job> qr32;
+  std::vector<QrF32Job> qr32, qrsm;
+  size_t qrsm_smem = 0;
+  std::vector<CoreSketchF32Job> cs3;
+  std::vector<Chain3Job> ch3;
+  size_t cs3_smem = 0, ch3_smem = 0;
+  double cs3_flops = 0.0, ch3_flops = 0.0;
+  constexpr size_t kSmemCap = 200 * 1024;
+  constexpr int kChainRows = 8;
   std::vector<OmegaJob> om;
   int64_t om_blocks = 0;
   std::vector<TransposeJob> tr;
@@ -480,6 +490,14 @@ static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
         double other = 1.0;
         for (int m = 0; m < d; ++m)
           if (m != n) other *= j.r[m];
+        const size_t smem3 = d == 3 ? (size_t)j.S * 4 * (j.r[0] + j.r[1] + j.r[2]) + (size_t)2 * j.r[0] * j.r[1] * j.r[2]
+                                    : 0;
+        if (d == 3 && !kron && smem3 <= kSmemCap) {
+          cs3.push_back(j);
+          cs3_smem = std::max(cs3_smem, smem3);
+          cs3_flops += 2.0 * (double)j.count * other;
+          continue;
+        }
         cs_flops += 2.0 * (double)j.count * other;
         j.begin = cs_total;
         cs_total += j.count;
@@ -519,7 +537,13 @@ static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
         q.s0 = 1;
         q.s1 = 0;
         q.sc = (int64_t)nn;
-        qr32.push_back(q);
+        const size_t sm = qr_smem_bytes((int64_t)nn, h.S[n]);
+        if (sm <= 216 * 1024) {
+          qrsm.push_back(q);
+          qrsm_smem = std::max(qrsm_smem, sm);
+        } else {
+          qr32.push_back(q);
+        }
       } else {
         QrJob q;
         std::memset(&q, 0, sizeof(q));
@@ -569,6 +593,36 @@ static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
     for (int k = 0; k < h.K; ++k) {
       const int* r = &h.ranks[(size_t)k * d];
       const int rd_off = h.roff[(size_t)k * d + d - 1];
+      if (d == 3) {
+        const size_t smem = 4 * ((size_t)kChainRows * r[0] + (size_t)r[1] * h.b[1] + (size_t)r[2] * kChainRows * r[1]) +
+                            (size_t)2 * r[0] * r[1] * r[2];
+        if (smem <= kSmemCap) {
+          for (int a0 = 0; a0 < h.b[0]; a0 += kChainRows) {
+            Chain3Job c;
+            std::memset(&c, 0, sizeof(c));
+            c.core = op_abs(h.cores, (size_t)h.core_off[k] * 2);
+            c.AT[0] = op(B_WS, h.AT32[0]);
+            c.AT[1] = op(B_WS, h.AT32[1]);
+            for (int q = 0; q < 3; ++q) {
+              c.T[q] = op(B_WS, h.Tp[q]);
+              c.r[q] = r[q];
+              c.roff[q] = h.roff[(size_t)k * d + q];
+            }
+            c.R[0] = h.R[0];
+            c.R[1] = h.R[1];
+            c.b[0] = h.b[0];
+            c.b[1] = h.b[1];
+            c.a0 = a0;
+            c.rows = std::min(kChainRows, h.b[0] - a0);
+            c.ldT = h.ldT;
+            c.alpha = (float)h.alpha[k];
+            ch3.push_back(c);
+          }
+          ch3_smem = std::max(ch3_smem, smem);
+          ch3_flops += 2.0 * h.b[0] * (double)r[0] * r[1] * r[2] + 2.0 * h.b[0] * (double)h.b[1] * r[1] * r[2];
+          continue;
+        }
+      }
       for (int t = 0; t + 1 < d; ++t) {
         int64_t L = 1, Rr = 1;
         for (int j = 0; j < t; ++j) L *= h.b[j];
@@ -634,6 +688,10 @@ static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
   plan->push(plan->st_sketch, S_TRANSPOSE, tr, tr_tiles, "a4:UcatT", 0.0, 0.0);
   plan->push_tc(plan->st_sketch, tcM, "a2:M=UcatT.Omega[tc]");
   plan->push(plan->st_sketch, S_CS32, cs, cs_total, "a3:core_sketch[f32]", cs_flops, 0.0);
+  if (!cs3.empty()) {
+    plan->push(plan->st_sketch, S_CS3, cs3, (int64_t)cs3.size(), "a3:core_sketch3[f32]", cs3_flops, 0.0);
+    plan->st_sketch.back().smem = cs3_smem;
+  }
   plan->push_tc(plan->st_sketch, tcY, "a4:Y=Ucat.Vcat[tc]");
   plan->push(plan->st_project, S_SPLIT, sp, sp_total, "a6:Q->planes", 0.0, 14.0 * sp_total);
   plan->push_tc(plan->st_project, tcA, "a6:AT=UcatT.Q[tc]");
@@ -642,10 +700,18 @@ static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
     std::snprintf(nm, sizeof(nm), "a7:chain%d[f32]", (int)t);
     plan->push_simt(plan->st_project, chain[t], nm);
   }
+  if (!ch3.empty()) {
+    plan->push(plan->st_project, S_CHAIN3, ch3, (int64_t)ch3.size(), "a7:chain3[f32]", ch3_flops, 0.0);
+    plan->st_project.back().smem = ch3_smem;
+  }
   plan->push_tc(plan->st_project, tcH, "a8:H=Tcat.AT[tc]");
   plan->st_recompress = plan->st_sketch;
   plan->push(plan->st_recompress, S_QR, qr, (int64_t)qr.size(), "a5:qr", qr_flops, qr_bytes);
   plan->push(plan->st_recompress, S_QR32, qr32, (int64_t)qr32.size(), "a5:qr[f32]", qr_flops, qr_bytes);
+  if (!qrsm.empty()) {
+    plan->push(plan->st_recompress, S_QRSM, qrsm, (int64_t)qrsm.size(), "a5:qr_smem[f32]", qr_flops, qr_bytes);
+    plan->st_recompress.back().smem = qrsm_smem;
+  }
   for (const auto& st : plan->st_project) plan->st_recompress.push_back(st);
 }
 
@@ -655,7 +721,7 @@ static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
 // H <- H x_n P_n^T and U~_n = Q_n P_n on CUDA cores.
 static void build_hosvd_f32(tks_plan* plan) {
   for (int n = 0; n < plan->dmax; ++n) {
-    std::vector<QrF32Job> qrs;
+    std::vector<std::vector<TsqrJob>> tsqr;
     std::vector<SvdJob> svds;
     std::vector<SimtJob> ttm, fac;
     double qflops = 0.0;
@@ -669,23 +735,48 @@ static void build_hosvd_f32(tks_plan* plan) {
       const int b = h.b[n], rmax = h.rmax[n];
       const Operand X = (n == 0) ? op(B_H, h.h_off * 8) : op(B_WS, h.Hp[(n - 1) & 1]);
       const int32_t xt = (n == 0) ? T_F64 : T_F32;
-      QrF32Job q;
-      std::memset(&q, 0, sizeof(q));
-      q.src = X;
-      q.src_type = xt;
-      q.W = op(B_WS, h.Wh);
-      q.tau = op(B_WS, h.tauh);
-      q.R = op(B_WS, h.R32);
-      q.want_r = 1;
-      q.rows = L * Rr;
-      q.cols = b;
-      q.b = (int)std::min<int64_t>(q.rows, b);
-      q.L0 = L;
-      q.s0 = 1;
-      q.s1 = L * b;
-      q.sc = L;
-      qrs.push_back(q);
-      qflops += 2.0 * (double)q.rows * b * b;
+      // TSQR of H_(n)^T (rows = L Rr with the two-level index (l, rr), cols = b): level 0 reads
+      // H, later levels read the stacked b x b factors, the last level writes R32
+      {
+        int64_t rows = L * Rr;
+        qflops += 2.0 * (double)rows * b * b;
+        Operand src = X;
+        int32_t stype = xt;
+        int64_t L0 = L, s0 = 1, s1 = L * b, sc = L;
+        for (int lvl = 0;; ++lvl) {
+          const int nblk = std::max(1, ceil_div(rows, kTsqrBlockRows));
+          const int brows = ceil_div(rows, nblk);
+          const bool final_level = (nblk == 1);
+          const Operand dst = final_level ? op(B_WS, h.R32) : op(B_WS, h.stk[lvl & 1]);
+          const int64_t dst_ld = final_level ? b : (int64_t)nblk * b;
+          if ((int)tsqr.size() <= lvl) tsqr.resize(lvl + 1);
+          for (int i = 0; i < nblk; ++i) {
+            TsqrJob t;
+            std::memset(&t, 0, sizeof(t));
+            t.src = src;
+            t.src_type = stype;
+            t.row_begin = (int64_t)i * brows;
+            t.rows = (int)std::min<int64_t>(brows, rows - t.row_begin);
+            t.cols = b;
+            t.L0 = L0;
+            t.s0 = s0;
+            t.s1 = s1;
+            t.sc = sc;
+            t.dst = dst;
+            t.dst_row0 = (int64_t)i * b;
+            t.dst_ld = dst_ld;
+            tsqr[lvl].push_back(t);
+          }
+          if (final_level) break;
+          src = dst;
+          stype = T_F32;
+          rows = (int64_t)nblk * b;
+          L0 = rows;
+          s0 = 1;
+          s1 = 0;
+          sc = dst_ld;
+        }
+      }
       SvdJob sj;
       std::memset(&sj, 0, sizeof(sj));
       sj.R = op(B_WS, h.R32);
@@ -736,8 +827,11 @@ static void build_hosvd_f32(tks_plan* plan) {
       fac.push_back(f);
     }
     char nm[32];
-    std::snprintf(nm, sizeof(nm), "a9:qr%d[f32]", n);
-    plan->push(plan->st_recompress, S_QR32, qrs, (int64_t)qrs.size(), nm, qflops, 0.0);
+    for (size_t lvl = 0; lvl < tsqr.size(); ++lvl) {
+      std::snprintf(nm, sizeof(nm), "a9:tsqr%d.%d[f32]", n, (int)lvl);
+      plan->push(plan->st_recompress, S_TSQR, tsqr[lvl], (int64_t)tsqr[lvl].size(), nm, lvl == 0 ? qflops : 0.0,
+                 0.0);
+    }
     std::snprintf(nm, sizeof(nm), "a9:svd%d[f32]", n);
     plan->push(plan->st_recompress, S_SVD32, svds, (int64_t)svds.size(), nm);
     std::snprintf(nm, sizeof(nm), "a9:ttm%d[f32]", n);
@@ -907,6 +1001,13 @@ tks_status tks_plan_create(tks_plan** out, const tks_problem* problems, int32_t 
     h.Hp[0] = alloc(Hsz * 8);
     h.Hp[1] = alloc(Hsz * 8);
     if (f32la) {
+      int64_t stack_rows = 0;
+      for (int m = 0; m < d; ++m) {
+        const int64_t rows = Hsz / h.b[m];
+        stack_rows = std::max<int64_t>(stack_rows, (int64_t)ceil_div(rows, kTsqrBlockRows) * h.b[m]);
+      }
+      h.stk[0] = alloc((size_t)stack_rows * bm * 4);
+      h.stk[1] = alloc((size_t)stack_rows * bm * 4);
       h.Wh = alloc(Hsz * 4);
       h.tauh = alloc((size_t)bm * 4);
       h.R32 = alloc((size_t)bm * bm * 4);
@@ -1129,13 +1230,15 @@ tks_status tks_plan_create(tks_plan** out, const tks_problem* problems, int32_t 
   }
   if (f32la) {
     cudaError_t e = prepare_svd_f32(plan->bmax);
+    if (e == cudaSuccess) e = prepare_tsqr_f32();
     if (e != cudaSuccess) {
       tks_plan_destroy(plan);
-      return fail(TKS_ECUDA, std::string("SVD shared memory: ") + cudaGetErrorString(e));
+      return fail(TKS_ECUDA, std::string("float32 QR/SVD shared memory: ") + cudaGetErrorString(e));
     }
   }
   if (mixed) {
     cudaError_t e = prepare_tc_gemm();
+    if (e == cudaSuccess) e = prepare_order3_kernels();
     if (e != cudaSuccess) {
       tks_plan_destroy(plan);
       return fail(TKS_ECUDA, std::string("tensor-core GEMM shared memory: ") + cudaGetErrorString(e));
@@ -1258,6 +1361,18 @@ tks_status run_steps(tks_plan* plan, const std::vector<Step>& steps, const Bases
         break;
       case S_SVD32:
         launch_svd_f32(static_cast<const SvdJob*>(table), s.njobs, plan->bmax, bases, plan->status, stream);
+        break;
+      case S_TSQR:
+        launch_tsqr_f32(static_cast<const TsqrJob*>(table), s.njobs, kTsqrBlockRows, plan->bmax, bases, stream);
+        break;
+      case S_QRSM:
+        launch_qr_smem_f32(static_cast<const QrF32Job*>(table), s.njobs, s.smem, bases, plan->status, stream);
+        break;
+      case S_CS3:
+        launch_core_sketch_krp3(static_cast<const CoreSketchF32Job*>(table), s.njobs, s.smem, bases, stream);
+        break;
+      case S_CHAIN3:
+        launch_chain3(static_cast<const Chain3Job*>(table), s.njobs, s.smem, bases, stream);
         break;
     }
   }

@@ -37,6 +37,11 @@ void launch_simt_gemm_f32(const SimtJob* jobs, int njobs, int total_tiles, const
                           cudaStream_t stream);
 void launch_core_sketch_f32(const CoreSketchF32Job* jobs, int njobs, int64_t total, const Bases& bases,
                             cudaStream_t stream);
+// Order-3 shared-memory kernels (one CTA per job); smem = bytes of the largest job.
+cudaError_t prepare_order3_kernels();
+void launch_core_sketch_krp3(const CoreSketchF32Job* jobs, int njobs, size_t smem, const Bases& bases,
+                             cudaStream_t stream);
+void launch_chain3(const Chain3Job* jobs, int njobs, size_t smem, const Bases& bases, cudaStream_t stream);
 void launch_split_f64(const SplitJob* jobs, int njobs, int64_t total, const Bases& bases, cudaStream_t stream);
 void launch_transpose_bf16(const TransposeJob* jobs, int njobs, int total_tiles, const Bases& bases,
                            cudaStream_t stream);
@@ -44,6 +49,14 @@ void launch_transpose_bf16(const TransposeJob* jobs, int njobs, int total_tiles,
 // Float32 small dense linear algebra (Householder QR, one-sided Jacobi SVD).
 void launch_qr_f32(const QrF32Job* jobs, int njobs, const Bases& bases, Status* status, cudaStream_t stream);
 cudaError_t prepare_svd_f32(int bmax);
+// Householder QR with the matrix resident in shared memory (n * S floats), explicit Q.
+size_t qr_smem_bytes(int64_t n, int S);
+void launch_qr_smem_f32(const QrF32Job* jobs, int njobs, size_t smem, const Bases& bases, Status* status,
+                        cudaStream_t stream);
+// One TSQR level: each job factors one block of rows and writes its triangular factor.
+cudaError_t prepare_tsqr_f32();
+void launch_tsqr_f32(const TsqrJob* jobs, int njobs, int max_rows, int max_cols, const Bases& bases,
+                     cudaStream_t stream);
 void launch_svd_f32(const SvdJob* jobs, int njobs, int bmax, const Bases& bases, Status* status,
                     cudaStream_t stream);
 

@@ -138,13 +138,175 @@ __global__ void __launch_bounds__(512) qr_f32_kernel(const QrF32Job* __restrict_
   if (threadIdx.x == 0 && sh_bad) record_status_la(status, TKS_ENONFINITE);
 }
 
+
+
+// ----------------------------------------------------------------------------- QR in shared memory
+// Householder QR of Y (n x S, float64 in, float32 arithmetic) held in shared memory, then the
+// explicit Q formed in place from the stored reflectors (backward accumulation: for j = b-1..0
+// apply H_j to the columns right of j, then replace column j by H_j e_j), columns flipped so
+// that diag(R) >= 0, written as float64.
+__global__ void __launch_bounds__(512) qr_smem_f32_kernel(const QrF32Job* __restrict__ jobs, Bases bases,
+                                                          Status* status) {
+  extern __shared__ float sq[];
+  __shared__ float red[32];
+  __shared__ float sh_tau, sh_scale;
+  __shared__ int sh_bad;
+  const QrF32Job& J = jobs[blockIdx.x];
+  const int n = (int)J.rows, S = (int)J.cols, b = J.b;
+  float* W = sq;                 // n x S, ld n
+  float* tau = W + (size_t)n * S;
+  float* rdiag = tau + S;
+  const char* src = at<char>(bases, J.src);
+  for (int e = threadIdx.x; e < n * S; e += blockDim.x) {
+    const int j = e / n, i = e - j * n;
+    const int64_t i1 = i / J.L0, i0 = i - i1 * J.L0;
+    W[e] = load_any(src, J.src_type, i0 * J.s0 + i1 * J.s1 + j * J.sc);
+  }
+  if (threadIdx.x == 0) sh_bad = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = 0; j < b; ++j) {
+    float* wj = W + (size_t)n * j;
+    float part = 0.f;
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) part = fmaf(wj[i], wj[i], part);
+    const float tail2 = block_sum_f(part, red);
+    if (threadIdx.x == 0) {
+      const float alpha = wj[j];
+      const float nrm = sqrtf(fmaf(alpha, alpha, tail2));
+      if (!isfinite(nrm)) sh_bad = 1;
+      if (tail2 == 0.f || !isfinite(nrm)) {
+        sh_tau = 0.f;
+        sh_scale = 0.f;
+        rdiag[j] = alpha;
+      } else {
+        const float beta = (alpha >= 0.f) ? -nrm : nrm;
+        sh_tau = (beta - alpha) / beta;
+        sh_scale = 1.f / (alpha - beta);
+        rdiag[j] = beta;
+      }
+      tau[j] = sh_tau;
+    }
+    __syncthreads();
+    const float t = sh_tau;
+    if (t != 0.f) {
+      const float sc = sh_scale;
+      for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) wj[i] *= sc;
+      __syncthreads();
+      for (int l = j + 1 + warp; l < b; l += nw) {
+        float* wl = W + (size_t)n * l;
+        float dot = 0.f;
+        for (int i = j + 1 + lane; i < n; i += 32) dot = fmaf(wj[i], wl[i], dot);
+        dot = warp_sum_f(dot) + wl[j];
+        const float w = t * dot;
+        if (lane == 0) wl[j] -= w;
+        for (int i = j + 1 + lane; i < n; i += 32) wl[i] = fmaf(-w, wj[i], wl[i]);
+      }
+    }
+    __syncthreads();
+  }
+  // explicit Q in place (columns 0..b-1)
+  for (int j = b - 1; j >= 0; --j) {
+    const float t = tau[j];
+    float* wj = W + (size_t)n * j;
+    if (t != 0.f) {
+      for (int l = j + 1 + warp; l < b; l += nw) {
+        float* wl = W + (size_t)n * l;
+        float dot = 0.f;
+        for (int i = j + 1 + lane; i < n; i += 32) dot = fmaf(wj[i], wl[i], dot);
+        dot = warp_sum_f(dot) + wl[j];
+        const float w = t * dot;
+        if (lane == 0) wl[j] -= w;
+        for (int i = j + 1 + lane; i < n; i += 32) wl[i] = fmaf(-w, wj[i], wl[i]);
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      if (i < j) wj[i] = 0.f;
+      else if (i == j) wj[i] = 1.f - t;
+      else wj[i] = -t * wj[i];
+    }
+    __syncthreads();
+  }
+  double* Q = at<double>(bases, J.Q);
+  for (int e = threadIdx.x; e < n * b; e += blockDim.x) {
+    const int l = e / n;
+    const float sgn = rdiag[l] < 0.f ? -1.f : 1.f;
+    Q[e] = (double)(sgn * W[e]);
+  }
+  if (threadIdx.x == 0 && sh_bad) record_status_la(status, TKS_ENONFINITE);
+}
+
+// ----------------------------------------------------------------------------- TSQR block
+// Householder QR of a rows x cols block held in shared memory (column-major, ld = rows + 1),
+// one thread block; only the triangular factor is kept.
+__global__ void __launch_bounds__(256) tsqr_f32_kernel(const TsqrJob* __restrict__ jobs, Bases bases) {
+  extern __shared__ float smem_t[];
+  __shared__ float red[32];
+  __shared__ float sh_tau, sh_scale;
+  const TsqrJob& J = jobs[blockIdx.x];
+  const int m = J.rows, b = J.cols;
+  const int ld = m + 1;
+  float* A = smem_t;
+  const char* src = at<char>(bases, J.src);
+  for (int e = threadIdx.x; e < m * b; e += blockDim.x) {
+    const int c = e / m, r = e - c * m;
+    const int64_t i = J.row_begin + r;
+    const int64_t i1 = i / J.L0, i0 = i - i1 * J.L0;
+    A[r + ld * c] = load_any(src, J.src_type, i0 * J.s0 + i1 * J.s1 + c * J.sc);
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int kmax = m < b ? m : b;
+  for (int j = 0; j < kmax; ++j) {
+    float* aj = A + ld * j;
+    float part = 0.f;
+    for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) part = fmaf(aj[i], aj[i], part);
+    const float tail2 = block_sum_f(part, red);
+    if (threadIdx.x == 0) {
+      const float alpha = aj[j];
+      const float nrm = sqrtf(fmaf(alpha, alpha, tail2));
+      if (tail2 == 0.f || !isfinite(nrm)) {
+        sh_tau = 0.f;
+        sh_scale = 0.f;
+      } else {
+        const float beta = (alpha >= 0.f) ? -nrm : nrm;
+        sh_tau = (beta - alpha) / beta;
+        sh_scale = 1.f / (alpha - beta);
+        aj[j] = beta;
+      }
+    }
+    __syncthreads();
+    const float t = sh_tau;
+    if (t != 0.f) {
+      const float sc = sh_scale;
+      for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) aj[i] *= sc;
+      __syncthreads();
+      for (int l = j + 1 + warp; l < b; l += nw) {
+        float* al = A + ld * l;
+        float dot = 0.f;
+        for (int i = j + 1 + lane; i < m; i += 32) dot = fmaf(aj[i], al[i], dot);
+        dot = warp_sum_f(dot) + al[j];
+        const float w = t * dot;
+        if (lane == 0) al[j] -= w;
+        for (int i = j + 1 + lane; i < m; i += 32) al[i] = fmaf(-w, aj[i], al[i]);
+      }
+    }
+    __syncthreads();
+  }
+  float* dst = at<float>(bases, J.dst);
+  for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+    const int c = e / b, r = e - c * b;
+    dst[(J.dst_row0 + r) + J.dst_ld * c] = (r <= c && r < kmax) ? A[r + ld * c] : 0.f;
+  }
+}
+
 // One-sided Jacobi on the columns of the b x b matrix A = R with the round-robin ordering:
 // each round rotates b/2 disjoint column pairs (one warp per pair) so that they become
 // orthogonal; V accumulates the rotations.  At convergence A = U Sigma, R = U Sigma V^T.
 constexpr int kSvdSweeps = 40;
 
-__global__ void __launch_bounds__(512) svd_jacobi_f32_kernel(const SvdJob* __restrict__ jobs, Bases bases,
-                                                             Status* status) {
+__global__ void __launch_bounds__(1024) svd_jacobi_f32_kernel(const SvdJob* __restrict__ jobs, Bases bases,
+                                                              Status* status) {
   extern __shared__ float sm[];
   const SvdJob& J = jobs[blockIdx.x];
   const int b = J.b;
@@ -164,6 +326,8 @@ __global__ void __launch_bounds__(512) svd_jacobi_f32_kernel(const SvdJob* __res
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  // rotate while |a_p . a_q| > b eps_f32 ||a_p|| ||a_q|| (the usual m eps convergence test)
+  const float thr = (float)b * 5.96e-8f;
   int sweep = 0;
   for (; sweep < kSvdSweeps; ++sweep) {
     if (threadIdx.x == 0) sh_rot = 0;
@@ -185,7 +349,7 @@ __global__ void __launch_bounds__(512) svd_jacobi_f32_kernel(const SvdJob* __res
         al = warp_sum_f(al);
         be = warp_sum_f(be);
         ga = warp_sum_f(ga);
-        if (fabsf(ga) > 1e-7f * sqrtf(al * be) && ga != 0.f) {
+        if (fabsf(ga) > thr * sqrtf(al * be) && ga != 0.f) {
           const float zeta = (be - al) / (2.f * ga);
           const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
           const float c = 1.f / sqrtf(1.f + t * t), s = c * t;
@@ -279,6 +443,26 @@ size_t svd_smem(int bmax) {
 
 }  // namespace
 
+size_t tsqr_smem(int rows, int cols) { return (size_t)(rows + 1) * cols * sizeof(float); }
+
+cudaError_t prepare_tsqr_f32() {
+  cudaError_t e = cudaFuncSetAttribute(qr_smem_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 222 * 1024);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(tsqr_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 222 * 1024);
+}
+
+size_t qr_smem_bytes(int64_t n, int S) { return (size_t)(n * S + 2 * S) * sizeof(float); }
+
+void launch_qr_smem_f32(const QrF32Job* jobs, int njobs, size_t smem, const Bases& bases, Status* status,
+                        cudaStream_t stream) {
+  qr_smem_f32_kernel<<<njobs, 512, smem, stream>>>(jobs, bases, status);
+}
+
+void launch_tsqr_f32(const TsqrJob* jobs, int njobs, int max_rows, int max_cols, const Bases& bases,
+                     cudaStream_t stream) {
+  tsqr_f32_kernel<<<njobs, 256, tsqr_smem(max_rows, max_cols), stream>>>(jobs, bases);
+}
+
 void launch_qr_f32(const QrF32Job* jobs, int njobs, const Bases& bases, Status* status, cudaStream_t stream) {
   qr_f32_kernel<<<njobs, 512, 0, stream>>>(jobs, bases, status);
 }
@@ -290,7 +474,8 @@ cudaError_t prepare_svd_f32(int bmax) {
 
 void launch_svd_f32(const SvdJob* jobs, int njobs, int bmax, const Bases& bases, Status* status,
                     cudaStream_t stream) {
-  svd_jacobi_f32_kernel<<<njobs, 512, svd_smem(bmax), stream>>>(jobs, bases, status);
+  // one warp per column pair of a round: b / 2 <= 48 pairs, 32 warps
+  svd_jacobi_f32_kernel<<<njobs, 1024, svd_smem(bmax), stream>>>(jobs, bases, status);
 }
 
 }  // namespace tks

@@ -199,6 +199,121 @@ __global__ void core_sketch_f32_kernel(const CoreSketchF32Job* __restrict__ jobs
   }
 }
 
+
+// ----------------------------------------------------------------------------- order-3 kernels
+// Khatri-Rao core sketch of one (term, mode n) of an order-3 problem, in shared memory:
+//   V[a, c] = alpha sum_{p2} M2[p2, c] sum_{p1} G[a, p1, p2] M1[p1, c]
+// (p1, p2 the rank indices of the two other modes in ascending order).  Threads run over
+// outputs with c fastest, so the core reads are warp broadcasts and the M1 reads consecutive;
+// V is staged in shared memory and written with a fastest.
+__global__ void __launch_bounds__(256) core_sketch_krp3_kernel(const CoreSketchF32Job* __restrict__ jobs,
+                                                               Bases bases) {
+  extern __shared__ float sm3[];
+  const CoreSketchF32Job& J = jobs[blockIdx.x];
+  const int n = J.n;
+  const int j1 = (n == 0) ? 1 : 0, j2 = (n == 2) ? 1 : 2;
+  const int rn = J.r[n], r1 = J.r[j1], r2 = J.r[j2], s = J.S;
+  float* M1 = sm3;                       // [c + s p1]
+  float* M2 = M1 + r1 * s;               // [c + s p2]
+  float* Vs = M2 + r2 * s;               // [a + rn c]
+  uint16_t* Gs = reinterpret_cast<uint16_t*>(Vs + rn * s);   // [a + rn (p1 + r1 p2)]
+  const uint16_t* G = at<uint16_t>(bases, J.core);
+  const int st[3] = {1, J.r[0], J.r[0] * J.r[1]};
+  const int tot = rn * r1 * r2;
+  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+    const int a = e % rn, p1 = (e / rn) % r1, p2 = e / (rn * r1);
+    Gs[e] = G[a * st[n] + p1 * st[j1] + p2 * st[j2]];
+  }
+  const float* Mg1 = at<float>(bases, J.M[j1]) + J.roff[j1];
+  const float* Mg2 = at<float>(bases, J.M[j2]) + J.roff[j2];
+  for (int e = threadIdx.x; e < r1 * s; e += blockDim.x) {
+    const int c = e % s, p = e / s;
+    M1[e] = Mg1[p + (int64_t)J.R[j1] * c];
+  }
+  for (int e = threadIdx.x; e < r2 * s; e += blockDim.x) {
+    const int c = e % s, p = e / s;
+    M2[e] = Mg2[p + (int64_t)J.R[j2] * c];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < rn * s; e += blockDim.x) {
+    const int c = e % s, a = e / s;
+    float acc = 0.f;
+    for (int p2 = 0; p2 < r2; ++p2) {
+      const uint16_t* g = Gs + a + rn * r1 * p2;
+      float inner = 0.f;
+      for (int p1 = 0; p1 < r1; ++p1) inner = fmaf(bf16_float(g[rn * p1]), M1[c + s * p1], inner);
+      acc = fmaf(M2[c + s * p2], inner, acc);
+    }
+    Vs[a + rn * c] = J.alpha * acc;
+  }
+  __syncthreads();
+  uint16_t* V0 = at<uint16_t>(bases, J.V[0]);
+  uint16_t* V1 = at<uint16_t>(bases, J.V[1]);
+  uint16_t* V2 = at<uint16_t>(bases, J.V[2]);
+  for (int e = threadIdx.x; e < rn * s; e += blockDim.x) {
+    const int a = e % rn, c = e / rn;
+    const int64_t off = (J.roff[n] + a) + (int64_t)J.ldv * c;
+    uint16_t h0, h1, h2;
+    split3(Vs[e], h0, h1, h2);
+    V0[off] = h0;
+    V1[off] = h1;
+    V2[off] = h2;
+  }
+}
+
+// Stage (c2) chain of one term of an order-3 problem for a block of mode-1 rows, in shared
+// memory.  W[c, a, i1] = sum_{i0} A1[a, i0] G[i0, i1, c], then T[c, a, a1] = sum_{i1} W A2[a1, i1];
+// threads run with c fastest so the Tcat writes ((roff_2 + c) + ldT J) come out in runs.
+__global__ void __launch_bounds__(256) chain3_kernel(const Chain3Job* __restrict__ jobs, Bases bases) {
+  extern __shared__ float sc3[];
+  const Chain3Job& J = jobs[blockIdx.x];
+  const int r0 = J.r[0], r1 = J.r[1], r2 = J.r[2], b0 = J.b[0], b1 = J.b[1], AB = J.rows;
+  float* A1 = sc3;                  // [ia + AB i0]
+  float* A2 = A1 + AB * r0;         // [i1 + r1 a1]
+  float* Ws = A2 + r1 * b1;         // [c + r2 (ia + AB i1)]
+  uint16_t* Gt = reinterpret_cast<uint16_t*>(Ws + r2 * AB * r1);   // [c + r2 (i0 + r0 i1)]
+  const uint16_t* G = at<uint16_t>(bases, J.core);
+  for (int e = threadIdx.x; e < r0 * r1 * r2; e += blockDim.x) {
+    const int c = e % r2, i0 = (e / r2) % r0, i1 = e / (r2 * r0);
+    Gt[e] = G[i0 + r0 * (i1 + r1 * c)];
+  }
+  const float* At1 = at<float>(bases, J.AT[0]) + J.roff[0];
+  const float* At2 = at<float>(bases, J.AT[1]) + J.roff[1];
+  for (int e = threadIdx.x; e < AB * r0; e += blockDim.x) {
+    const int ia = e % AB, i0 = e / AB;
+    A1[e] = At1[i0 + (int64_t)J.R[0] * (J.a0 + ia)];
+  }
+  for (int e = threadIdx.x; e < r1 * b1; e += blockDim.x) {
+    const int i1 = e % r1, a1 = e / r1;
+    A2[e] = At2[i1 + (int64_t)J.R[1] * a1];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < r2 * AB * r1; e += blockDim.x) {
+    const int c = e % r2, ia = (e / r2) % AB, i1 = e / (r2 * AB);
+    const uint16_t* g = Gt + c + r2 * r0 * i1;
+    float w = 0.f;
+    for (int i0 = 0; i0 < r0; ++i0) w = fmaf(A1[ia + AB * i0], bf16_float(g[r2 * i0]), w);
+    Ws[e] = w;
+  }
+  __syncthreads();
+  uint16_t* T0 = at<uint16_t>(bases, J.T[0]);
+  uint16_t* T1 = at<uint16_t>(bases, J.T[1]);
+  uint16_t* T2 = at<uint16_t>(bases, J.T[2]);
+  for (int e = threadIdx.x; e < r2 * AB * b1; e += blockDim.x) {
+    const int c = e % r2, ia = (e / r2) % AB, a1 = e / (r2 * AB);
+    const float* w = Ws + c + r2 * ia;
+    const float* a2 = A2 + r1 * a1;
+    float t = 0.f;
+    for (int i1 = 0; i1 < r1; ++i1) t = fmaf(w[r2 * AB * i1], a2[i1], t);
+    const int64_t off = (J.roff[2] + c) + (int64_t)J.ldT * (J.a0 + ia + (int64_t)b0 * a1);
+    uint16_t h0, h1, h2;
+    split3(J.alpha * t, h0, h1, h2);
+    T0[off] = h0;
+    T1[off] = h1;
+    T2[off] = h2;
+  }
+}
+
 // ----------------------------------------------------------------------------- split / transpose
 __global__ void split_f64_kernel(const SplitJob* __restrict__ jobs, int njobs, int64_t total, Bases bases) {
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total;
@@ -256,6 +371,22 @@ void launch_simt_gemm_f32(const SimtJob* jobs, int njobs, int total_tiles, const
 void launch_core_sketch_f32(const CoreSketchF32Job* jobs, int njobs, int64_t total, const Bases& bases,
                             cudaStream_t stream) {
   core_sketch_f32_kernel<<<grid_for(total, 128), 128, 0, stream>>>(jobs, njobs, total, bases);
+}
+
+cudaError_t prepare_order3_kernels() {
+  cudaError_t e = cudaFuncSetAttribute(core_sketch_krp3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       222 * 1024);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(chain3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 222 * 1024);
+}
+
+void launch_core_sketch_krp3(const CoreSketchF32Job* jobs, int njobs, size_t smem, const Bases& bases,
+                             cudaStream_t stream) {
+  core_sketch_krp3_kernel<<<njobs, 256, smem, stream>>>(jobs, bases);
+}
+
+void launch_chain3(const Chain3Job* jobs, int njobs, size_t smem, const Bases& bases, cudaStream_t stream) {
+  chain3_kernel<<<njobs, 256, smem, stream>>>(jobs, bases);
 }
 
 void launch_split_f64(const SplitJob* jobs, int njobs, int64_t total, const Bases& bases, cudaStream_t stream) {

@@ -111,6 +111,17 @@ struct CoreSketchF32Job {
   int64_t begin;
 };
 
+// Order-3 chain of one term for rows [a0, a0 + AB) of mode 1 (stage c2, float32):
+//   T[a0, a1, c] = alpha sum_{i0, i1} A1[a0, i0] A2[a1, i1] G[i0, i1, c]
+// with A_t[a, i] = AT_t[(roff_t + i) + R_t a]; written as bf16 planes of Tcat at
+// (roff_2 + c) + ldT (a0 + b0 a1).
+struct Chain3Job {
+  Operand core, AT[2], T[3];
+  int32_t r[3], roff[3], R[2], b[2];
+  int32_t a0, rows, ldT, pad;
+  float alpha, pad2;
+};
+
 // Split a float64 matrix (rows x cols, element (i, j) at i + ld_src j) into bf16 planes
 // hi + mid + lo (element (i, j) at i + ld_dst j).
 struct SplitJob {
@@ -193,6 +204,18 @@ struct QrF32Job {
   Operand src, W, tau, Q, R;
   int32_t src_type, want_q, want_r, b;
   int64_t rows, cols, L0, s0, s1, sc;
+};
+
+// One block of a TSQR level: rows [row_begin, row_begin + rows) x cols of a (typed, two-level
+// row index) source are factored by Householder in shared memory; the b x b triangular factor
+// (rows below min(rows, cols) zero) is written at rows [dst_row0, dst_row0 + cols) of dst
+// (float32, column-major, leading dimension dst_ld).  Stacking the blocks' factors and
+// factoring again gives the triangular factor of the whole matrix.
+struct TsqrJob {
+  Operand src, dst;
+  int32_t src_type, rows, cols, pad;
+  int64_t row_begin, L0, s0, s1, sc;
+  int64_t dst_row0, dst_ld;
 };
 
 // One-sided (Hestenes) Jacobi SVD in float32 of the b x b factor R of H_(n)^T = Q~ R: its right
