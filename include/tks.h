@@ -194,6 +194,28 @@ typedef struct {
 TKS_API tks_status tks_profile_begin(tks_plan* plan, int32_t max_calls);
 TKS_API tks_status tks_profile_end(tks_plan* plan, tks_step_profile_t* out, int32_t cap, int32_t* nsteps);
 
+/* The structured sketch of ONE problem (same result as tucker_sum_sketch with TKS_FP64 and that
+ * problem alone in a plan) for callers that cannot allocate device memory: code that must not
+ * call cudaMalloc because another framework owns all device memory through its own pool, because
+ * it runs where allocation is forbidden or too slow (real-time loops, callbacks on a hot path),
+ * or because it is embedded in a host program that never creates a plan.  There is no
+ * counterpart in the paper; this is a deployment variant of tucker_sum_sketch.
+ *
+ * Inputs and outputs are the caller's: problem and params as for tks_plan_create (params must be
+ * TKS_FP64 with dtype F64), Y_out a device buffer of sum_n n_n S_n float64 where Y_n (n_n x S_n,
+ * column-major, S_n from Sec. 3.2) starts at element sum_{m<n} n_m S_m.  The descriptor tables and
+ * the intermediates Omega_j, M_j, Vcat_n live in a static device array of TKS_NOALLOC_SCRATCH_BYTES
+ * that every GPU loading this library holds until the process exits; a problem needing more is
+ * rejected with TKS_EINVAL and a message giving both sizes.  No cudaMalloc, cudaFree or other
+ * allocating call is made.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) for that device, so make that first call before any stream capture.
+ * Every call reuses the same array and leaves its contents behind; nothing in it needs to start
+ * at zero (each element a call reads is written earlier by the same call).  Calls whose work
+ * overlaps on a GPU (other streams, other host threads) race on the array: serialize them. */
+#define TKS_NOALLOC_SCRATCH_BYTES (8u << 20)
+TKS_API tks_status tucker_sum_sketch_noalloc(const tks_problem* problem, const tks_params* params, double* Y_out,
+                                             void* stream);
+
 TKS_API const char* tks_last_error(void);
 TKS_API const char* tks_status_string(tks_status status);
 

@@ -96,6 +96,8 @@ def load(path=None):
     lib.tks_last_error.restype = ctypes.c_char_p
     lib.tks_status_string.restype = ctypes.c_char_p
     lib.tks_status_string.argtypes = [ctypes.c_int]
+    lib.tucker_sum_sketch_noalloc.argtypes = [ctypes.POINTER(Problem_t), ctypes.POINTER(Params_t), P, P]
+    lib.tucker_sum_sketch_noalloc.restype = ctypes.c_int
     lib.tks_profile_begin.argtypes = [P, ctypes.c_int32]
     lib.tks_profile_end.argtypes = [P, ctypes.POINTER(StepProfile_t), ctypes.c_int32,
                                     ctypes.POINTER(ctypes.c_int32)]

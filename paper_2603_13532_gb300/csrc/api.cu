@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <map>
+#include <mutex>
 #include <tuple>
 #include <cmath>
 #include <cstdio>
@@ -1560,3 +1561,143 @@ tks_status tks_sync_status(tks_plan* plan, void* stream) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// Allocation-free structured sketch of one problem (FP64).  Its descriptor tables and scratch
+// live in this file-scope device array; host code only ever uses the address returned by
+// cudaGetSymbolAddress for the current device (the symbol itself is a host-side stand-in).
+static __device__ __align__(256) unsigned char g_noalloc_scratch[TKS_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kMaxDevices = 128;
+std::mutex g_noalloc_mutex;
+void* g_noalloc_ptr[kMaxDevices] = {};
+
+tks_status noalloc_scratch(void** out) {
+  int dev = -1;
+  TKS_CUDA_CHECK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return fail(TKS_EUNSUPPORTED, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return fail(TKS_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return TKS_OK;
+}
+
+struct HostTables {
+  std::vector<char> bytes;
+  template <typename T>
+  size_t add(const std::vector<T>& v) {
+    const size_t off = align_up(bytes.size(), 64);
+    bytes.resize(off + v.size() * sizeof(T));
+    if (!v.empty()) std::memcpy(bytes.data() + off, v.data(), v.size() * sizeof(T));
+    return off;
+  }
+};
+
+}  // namespace
+
+extern "C" tks_status tucker_sum_sketch_noalloc(const tks_problem* problem, const tks_params* params, double* Y_out,
+                                                void* stream) {
+  if (!problem || !params || !Y_out) return fail(TKS_EINVAL, "null problem, params or Y_out");
+  if (params->precision != TKS_FP64 || params->dtype != TKS_DT_F64)
+    return fail(TKS_EINVAL, "tucker_sum_sketch_noalloc needs TKS_FP64 with float64 inputs");
+  if (params->sketch != TKS_SKETCH_KRP && params->sketch != TKS_SKETCH_KRON) return fail(TKS_EINVAL, "bad sketch");
+  ProbHost h;
+  tks_status st = validate_and_size(*problem, *params, h, 0);
+  if (st != TKS_OK) return st;
+  const int d = h.d;
+  const int kron = params->sketch == TKS_SKETCH_KRON;
+  // scratch layout after the tables: Omega_m, M_m, Vcat_n (float64)
+  size_t ws = 0;
+  auto alloc = [&](size_t bytes) {
+    const size_t o = ws;
+    ws = align_up(ws + std::max<size_t>(bytes, 1));
+    return o;
+  };
+  int64_t y_off = 0;
+  size_t om[MAXD], Mw[MAXD], Vw[MAXD];
+  for (int m = 0; m < d; ++m) {
+    om[m] = alloc((size_t)h.n[m] * h.s[m] * 8);
+    Mw[m] = alloc((size_t)h.R[m] * h.s[m] * 8);
+    Vw[m] = alloc((size_t)h.R[m] * h.S[m] * 8);
+    h.y_off[m] = y_off;
+    y_off += h.n[m] * h.S[m];
+  }
+  std::vector<OmegaJob> omj;
+  int64_t om_blocks = 0;
+  GemmList gM, gY;
+  std::vector<CoreSketchJob> cs;
+  int64_t cs_total = 0;
+  for (int m = 0; m < d; ++m) {
+    OmegaJob oj;
+    std::memset(&oj, 0, sizeof(oj));
+    oj.out = op(B_WS, om[m]);
+    oj.count = h.n[m] * h.s[m];
+    oj.begin = om_blocks;
+    oj.problem = 0;
+    oj.mode = m;
+    om_blocks += (oj.count + 3) / 4;
+    omj.push_back(oj);
+    gM.add(gemm(h.R[m], h.s[m], (int)h.n[m], op_abs(h.factors[m]), h.n[m], 1, op(B_WS, om[m]), h.n[m], 1,
+                op(B_WS, Mw[m]), 1, h.R[m]));
+  }
+  for (int k = 0; k < h.K; ++k) {
+    for (int n = 0; n < d; ++n) {
+      CoreSketchJob j;
+      std::memset(&j, 0, sizeof(j));
+      j.core = op_abs(h.cores, (size_t)h.core_off[k] * 8);
+      for (int m = 0; m < d; ++m) {
+        j.M[m] = op(B_WS, Mw[m]);
+        j.r[m] = h.ranks[(size_t)k * d + m];
+        j.roff[m] = h.roff[(size_t)k * d + m];
+        j.R[m] = h.R[m];
+        j.s[m] = h.s[m];
+      }
+      j.V = op(B_WS, Vw[n]);
+      j.d = d;
+      j.n = n;
+      j.kron = kron;
+      j.S = h.S[n];
+      j.Rn = h.R[n];
+      j.alpha = h.alpha[k];
+      j.count = (int64_t)j.r[n] * j.S;
+      j.begin = cs_total;
+      cs_total += j.count;
+      cs.push_back(j);
+    }
+  }
+  for (int n = 0; n < d; ++n)
+    gY.add(gemm((int)h.n[n], h.S[n], h.R[n], op_abs(h.factors[n]), 1, h.n[n], op(B_WS, Vw[n]), h.R[n], 1,
+                op(B_Y, h.y_off[n] * 8), 1, h.n[n]));
+  HostTables t;
+  const size_t t_om = t.add(omj), t_gM = t.add(gM.jobs), t_cs = t.add(cs), t_gY = t.add(gY.jobs);
+  const size_t tables = align_up(t.bytes.size());
+  const size_t need = tables + ws;
+  if (need > TKS_NOALLOC_SCRATCH_BYTES)
+    return fail(TKS_EINVAL, "tucker_sum_sketch_noalloc: problem needs " + std::to_string(need) +
+                                " bytes of scratch, the static scratch holds " +
+                                std::to_string((size_t)TKS_NOALLOC_SCRATCH_BYTES));
+  void* scratch = nullptr;
+  st = noalloc_scratch(&scratch);
+  if (st != TKS_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char* base = static_cast<char*>(scratch);
+  TKS_CUDA_CHECK(cudaMemcpyAsync(base, t.bytes.data(), t.bytes.size(), cudaMemcpyHostToDevice, s));
+  Bases b;
+  std::memset(&b, 0, sizeof(b));
+  b.p[B_WS] = base + tables;
+  b.p[B_Y] = reinterpret_cast<char*>(Y_out);
+  launch_omega(reinterpret_cast<const OmegaJob*>(base + t_om), (int)omj.size(), om_blocks, b, params->seed, s);
+  launch_gemm_f64(reinterpret_cast<const GemmJob*>(base + t_gM), (int)gM.jobs.size(), gM.tiles, b, s);
+  launch_core_sketch_f64(reinterpret_cast<const CoreSketchJob*>(base + t_cs), (int)cs.size(), cs_total, b, s);
+  launch_gemm_f64(reinterpret_cast<const GemmJob*>(base + t_gY), (int)gY.jobs.size(), gY.tiles, b, s);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(TKS_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+  return TKS_OK;
+}
