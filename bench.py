@@ -76,12 +76,33 @@ def sampled_entries(core, factors, idx):
     return W
 
 
+def problem_seeds(P, seed, rank):
+    """Seeds of the P problems of one rank: disjoint across ranks (weak scaling)."""
+    return [seed + 7919 * (rank * P + i) for i in range(P)]
+
+
 def make_problems(P, seed, rank, bf16):
     from paper_2603_13532_gb300 import workloads as wl
     probs = []
-    for i in range(P):
-        probs += wl.decay512(seed=seed + 7919 * (rank * P + i), bf16=bf16).problems
+    for s in problem_seeds(P, seed, rank):
+        probs += wl.decay512(seed=s, bf16=bf16).problems
     return probs
+
+
+def max_over_ranks(x, device):
+    """The maximum of a per-rank float over all ranks of the default process group (x if none)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_rate(P, world, steps, elapsed_max):
+    """Whole-job throughput: every rank processed P problems per step; time = slowest rank."""
+    return P * world * steps / elapsed_max
 
 
 def load_peaks():
@@ -313,14 +334,12 @@ def main():
     prof = plan.profile_end()
     clock_info = clocks.stop(local)
     plan.sync()
+    elapsed = max_over_ranks(elapsed, device)
     if world > 1:
         import torch.distributed as dist
-        t = torch.tensor([elapsed], dtype=torch.float64, device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
         dist.barrier()
     ms_per_step = 1e3 * elapsed / args.steps
-    value = P * world * args.steps / elapsed
+    value = weak_scaling_rate(P, world, args.steps, elapsed)
     tflops = (plan.info.flops_lowprec + plan.info.flops_fp64) * world * args.steps / elapsed / 1e12
 
     peaks, peak_src = load_peaks()
@@ -342,13 +361,8 @@ def main():
 
         e2e_step()
         torch.cuda.synchronize()
-        e_el = time_steps(e2e_step, args.steps, stream)
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([e_el], dtype=torch.float64, device=device)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e_el = float(t.item())
-        e2e = {"value": P * world * args.steps / e_el, "unit": UNIT,
+        e_el = max_over_ranks(time_steps(e2e_step, args.steps, stream), device)
+        e2e = {"value": weak_scaling_rate(P, world, args.steps, e_el), "unit": UNIT,
                "h2d_bytes_per_step": int(host_in.numel() * host_in.element_size()),
                "d2h_bytes_per_step": int(host_out.numel() * 8 + host_ranks.numel() * 4)}
 

@@ -117,6 +117,8 @@ typedef struct {
   int32_t launches_recompress;  /* kernel launches one tucker_sum_recompress enqueues */
   double flops_lowprec;         /* algorithmic flops of the contraction stages, all problems */
   double flops_fp64;            /* algorithmic flops of QR and ST-HOSVD, all problems */
+  int64_t grad_core_elems;      /* float64 elements of the core-gradient buffer (backward) */
+  int64_t grad_factor_elems;    /* float64 elements of the factor-gradient buffer (backward) */
 } tks_plan_info_t;
 
 typedef struct {
@@ -132,6 +134,8 @@ typedef struct {
   int64_t core_off;                      /* element offset of H (b_1 x ... x b_d) */
   int64_t out_core_off;                  /* element offset of the output core (rmax_1 x ... ) */
   int64_t out_factor_off[TKS_MAX_ORDER]; /* element offsets of U~_n (n_n x rmax_n) */
+  int64_t grad_core_off;                 /* element offset of this problem's packed core gradients */
+  int64_t grad_factor_off[TKS_MAX_ORDER];/* element offsets of dUcat_n (n_n x R_n) */
 } tks_problem_info_t;
 
 /* Validates the problems, computes sketch sizes (Sec. 3.2: s = max_n ell_n for Khatri-Rao,
@@ -170,6 +174,20 @@ TKS_API tks_status tks_project_core(tks_plan* plan, void* workspace, const doubl
  * columns of U~_n beyond them are zero, so the padded arrays are the same Tucker tensor. */
 TKS_API tks_status tucker_sum_recompress(tks_plan* plan, void* workspace, double* out, int32_t* ranks_out,
                                  void* stream);
+
+/* Backward of the core projection (Sec. 3.3) with the bases held fixed (stop-gradient through Q):
+ * with A_kn = Q_n^T U_k^(n) and Hbar = dL/dH given (device, float64, the H layout of
+ * tks_project_core), writes
+ *   dcores   (device, float64, grad_core_elems): per problem at grad_core_off the cores' packing of
+ *            tks_problem.cores, term k holding dL/dG_k = alpha_k Hbar x_1 A_k1^T ... x_d A_kd^T
+ *   dfactors (device, float64, grad_factor_elems): per problem and mode at grad_factor_off[n] the
+ *            Ucat layout n_n x R_n, term k's columns holding
+ *            dL/dU_k^(n) = alpha_k Q_n [ (Hbar x_{j != n} A_kj^T)_(n) G_k,(n)^T ].
+ * The A_kn are recomputed from Q_in and the factors (nothing is kept from a forward call).
+ * TKS_FP64 plans only (TKS_EUNSUPPORTED otherwise). */
+TKS_API tks_status tks_project_core_backward(tks_plan* plan, void* workspace, const double* Q_in,
+                                             const double* Hbar_in, double* dcores, double* dfactors,
+                                             void* stream);
 
 /* Synchronizes stream, then returns and clears the first error a kernel of this plan recorded
  * since the previous call (TKS_ENONFINITE, TKS_ENOCONV, TKS_ETIMEOUT), else TKS_OK. */

@@ -50,7 +50,8 @@ class PlanInfo_t(ctypes.Structure):
                 ("sketch_elems", ctypes.c_int64), ("basis_elems", ctypes.c_int64),
                 ("core_elems", ctypes.c_int64), ("output_elems", ctypes.c_int64),
                 ("num_problems", ctypes.c_int32), ("launches_recompress", ctypes.c_int32),
-                ("flops_lowprec", ctypes.c_double), ("flops_fp64", ctypes.c_double)]
+                ("flops_lowprec", ctypes.c_double), ("flops_fp64", ctypes.c_double),
+                ("grad_core_elems", ctypes.c_int64), ("grad_factor_elems", ctypes.c_int64)]
 
 
 I32x6 = ctypes.c_int32 * MAX_ORDER
@@ -61,7 +62,8 @@ class ProblemInfo_t(ctypes.Structure):
     _fields_ = [("order", ctypes.c_int32), ("R", I32x6), ("omega_cols", I32x6), ("sketch_cols", I32x6),
                 ("basis_cols", I32x6), ("max_ranks", I32x6), ("omega_off", I64x6),
                 ("sketch_off", I64x6), ("basis_off", I64x6), ("core_off", ctypes.c_int64),
-                ("out_core_off", ctypes.c_int64), ("out_factor_off", I64x6)]
+                ("out_core_off", ctypes.c_int64), ("out_factor_off", I64x6),
+                ("grad_core_off", ctypes.c_int64), ("grad_factor_off", I64x6)]
 
 
 class StepProfile_t(ctypes.Structure):
@@ -92,6 +94,8 @@ def load(path=None):
     lib.tucker_sum_sketch.argtypes = [P, P, P, P]
     lib.tks_project_core.argtypes = [P, P, P, P, P]
     lib.tucker_sum_recompress.argtypes = [P, P, P, P, P]
+    lib.tks_project_core_backward.argtypes = [P, P, P, P, P, P, P]
+    lib.tks_project_core_backward.restype = ctypes.c_int
     lib.tks_sync_status.argtypes = [P, P]
     lib.tks_last_error.restype = ctypes.c_char_p
     lib.tks_status_string.restype = ctypes.c_char_p
@@ -213,6 +217,10 @@ class Plan:
     def project_raw(self, Q, H):
         _check(self.lib.tks_project_core(self.handle, _ptr(self.workspace), _ptr(Q), _ptr(H), _stream_handle()))
 
+    def backward_raw(self, Q, Hbar, dcores, dfactors):
+        _check(self.lib.tks_project_core_backward(self.handle, _ptr(self.workspace), _ptr(Q), _ptr(Hbar),
+                                                  _ptr(dcores), _ptr(dfactors), _stream_handle()))
+
     def recompress_raw(self, out, ranks):
         _check(self.lib.tucker_sum_recompress(self.handle, _ptr(self.workspace), _ptr(out), _ptr(ranks),
                                               _stream_handle()))
@@ -275,6 +283,41 @@ class Plan:
             out.append(host[pi.core_off: pi.core_off + int(np.prod(shape))].reshape(shape, order="F"))
         return out
 
+    def pack_core(self, Hs):
+        host = np.zeros(max(1, self.info.core_elems))
+        for p, pi, H in zip(self.problems, self.pinfo, Hs):
+            H = np.asarray(H)
+            host[pi.core_off: pi.core_off + H.size] = H.ravel(order="F")
+        return torch.from_numpy(host).to(self.device)
+
+    def backward(self, Qs, Hbars):
+        """dL/dG_k and dL/dU_k^(n) (lists per problem) for dL/dH = Hbars, bases Qs held fixed."""
+        Q = self.pack_bases(Qs)
+        Hb = self.pack_core(Hbars)
+        dc = self._new(self.info.grad_core_elems)
+        df = self._new(self.info.grad_factor_elems)
+        self.backward_raw(Q, Hb, dc, df)
+        self.sync()
+        dc, df = dc.cpu().numpy(), df.cpu().numpy()
+        res = []
+        for p, pi in zip(self.problems, self.pinfo):
+            dG, off = [], pi.grad_core_off
+            for G in p.cores:
+                dG.append(dc[off: off + G.size].reshape(G.shape, order="F"))
+                off += G.size
+            dU = []
+            for m in range(p.order):
+                R = pi.R[m]
+                Ucat = df[pi.grad_factor_off[m]: pi.grad_factor_off[m] + p.dims[m] * R].reshape(p.dims[m], R,
+                                                                                                order="F")
+                cols, c0 = [], 0
+                for G in p.cores:
+                    cols.append(Ucat[:, c0: c0 + G.shape[m]])
+                    c0 += G.shape[m]
+                dU.append(cols)
+            res.append((dG, [[dU[m][k] for m in range(p.order)] for k in range(p.num_terms)]))
+        return res
+
     def recompress(self):
         out = self._new(self.info.output_elems)
         ranks = torch.zeros(len(self.problems) * MAX_ORDER, dtype=torch.int32, device=self.device)
@@ -293,3 +336,43 @@ class Plan:
                     .reshape(p.dims[m], rmax[m], order="F") for m in range(p.order)]
             res.append(dict(core=core, factors=facs, ranks=[int(x) for x in rk[i, :p.order]]))
         return res
+
+
+class ProjectCore(torch.autograd.Function):
+    """H(G, U; Q) = sum_k alpha_k G_k x_1 (Q_1^T U_k^(1)) ... x_d (Q_d^T U_k^(d)) as an autograd op.
+
+    Differentiable input: ``plan.flat_inputs`` (the plan's packed cores and factors; the plan reads
+    them in place).  Q is a constant: its gradient is not computed (stop-gradient), matching a
+    method whose bases come from a QR that is not differentiated.  Forward and backward both run
+    in libtks.so (tks_project_core / tks_project_core_backward); the backward recomputes
+    A_kn = Q_n^T U_k^(n) instead of storing it.
+    """
+
+    @staticmethod
+    def forward(ctx, flat_inputs, Q, plan):
+        H = torch.zeros(max(1, plan.info.core_elems), dtype=torch.float64, device=plan.device)
+        plan.project_raw(Q, H)
+        ctx.plan = plan
+        ctx.save_for_backward(Q)
+        ctx.mark_non_differentiable(Q)
+        return H
+
+    @staticmethod
+    def backward(ctx, gH):
+        (Q,) = ctx.saved_tensors
+        plan = ctx.plan
+        gH = gH.contiguous().to(torch.float64)
+        dc = torch.zeros(max(1, plan.info.grad_core_elems), dtype=torch.float64, device=plan.device)
+        df = torch.zeros(max(1, plan.info.grad_factor_elems), dtype=torch.float64, device=plan.device)
+        plan.backward_raw(Q, gH, dc, df)
+        grad = torch.zeros_like(plan.flat_inputs)
+        base = plan.flat_inputs.storage_offset()
+        for p, pi, (core_v, fac_v) in zip(plan.problems, plan.pinfo, plan.inputs):
+            nc = sum(G.size for G in p.cores)
+            o = core_v.storage_offset() - base
+            grad[o: o + nc] = dc[pi.grad_core_off: pi.grad_core_off + nc]
+            for m in range(p.order):
+                nf = p.dims[m] * pi.R[m]
+                o = fac_v[m].storage_offset() - base
+                grad[o: o + nf] = df[pi.grad_factor_off[m]: pi.grad_factor_off[m] + nf]
+        return grad, None, None

@@ -98,6 +98,10 @@ struct ProbHost {
   int ldU[MAXD] = {}, ldV[MAXD] = {}, ldA[MAXD] = {}, ldT = 0;
   size_t Wh = 0, tauh = 0, R32 = 0, P32[MAXD] = {}, sv[MAXD] = {};   // float32 ST-HOSVD
   size_t stk[2] = {};                                                 // TSQR stacked factors
+  // backward of the core projection (order 3, float64)
+  size_t bZ0 = 0, bZ2 = 0, bB[MAXD] = {};
+  std::vector<size_t> bterm;   // per term: Z01, W1, W0
+  int64_t gcore_off = 0, gfac_off[MAXD] = {};
   int gram_ksplit = 1;
   double flops_low = 0.0, flops_f64 = 0.0;
 };
@@ -152,7 +156,9 @@ struct tks_plan {
   size_t ws_bytes = 0;
   size_t ws_omega = 0, ws_Y = 0, ws_Q = 0, ws_H = 0;
   int64_t omega_elems = 0, sketch_elems = 0, basis_elems = 0, core_elems = 0, output_elems = 0;
-  std::vector<Step> st_omega, st_sketch, st_project, st_recompress;
+  std::vector<Step> st_omega, st_sketch, st_project, st_recompress, st_backward;
+  int64_t grad_core_elems = 0, grad_factor_elems = 0;
+  bool backward_ok = false;
   double flops_low = 0.0, flops_f64 = 0.0;
 
   size_t add_table(const void* p, size_t bytes) {
@@ -491,7 +497,10 @@ static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
         double other = 1.0;
         for (int m = 0; m < d; ++m)
           if (m != n) other *= j.r[m];
-        const size_t smem3 = d == 3 ? (size_t)j.S * 4 * (j.r[0] + j.r[1] + j.r[2]) + (size_t)2 * j.r[0] * j.r[1] * j.r[2]
+        // core_sketch_krp3 layout: M1, M2, V (rows padded to 8) in float32, core in bf16 (rows padded)
+        const int rnp = (j.r[n] + 7) / 8 * 8;
+        const size_t smem3 = d == 3 ? (size_t)j.S * 4 * (j.r[0] + j.r[1] + j.r[2] - j.r[n] + rnp) +
+                                          (size_t)2 * rnp * (j.r[0] * j.r[1] * j.r[2] / j.r[n]) + 16
                                     : 0;
         if (d == 3 && !kron && smem3 <= kSmemCap) {
           cs3.push_back(j);
@@ -842,6 +851,78 @@ static void build_hosvd_f32(tks_plan* plan) {
   }
 }
 
+// Backward of the core projection for order-3 problems in float64 (stop-gradient through Q).
+// With Hbar (b0 x b1 x b2) and A_n = Q_n^T Ucat_n:
+//   Z0 = Hbar x_1 A_0cat^T (R0 x b1 x b2), Z2 = Hbar x_3 A_2cat^T (b0 x b1 x R2)   [all terms]
+//   per term k (rank offsets o_n):  Z01 = Z0_k x_2 A_k1^T,  dG_k = alpha_k Z01 x_3 A_k2^T,
+//   B_k2 = alpha_k (Z01)_(3) G_k,(3)^T,  W1 = Z0_k x_3 A_k2^T,  B_k1 = alpha_k (W1)_(2) G_k,(2)^T,
+//   W0 = Z2_k x_2 A_k1^T,  B_k0 = alpha_k (W0)_(1) G_k,(1)^T;   dUcat_n = Q_n Bcat_n.
+static void build_backward3(tks_plan* plan) {
+  GemmList big, step1, step2, du;
+  for (auto& h : plan->probs) {
+    const int b0 = h.b[0], b1 = h.b[1], b2 = h.b[2];
+    const int R0 = h.R[0], R2 = h.R[2];
+    // Z0[i + R0 J] = sum_a A_0[a + b0 i] Hbar[a + b0 J]
+    big.add(gemm(R0, b1 * b2, b0, op(B_WS, h.A[0]), b0, 1, op(B_HBAR, h.h_off * 8), b0, 1, op(B_WS, h.bZ0), 1, R0));
+    // Z2[J01 + b0 b1 i] = sum_a Hbar[J01 + b0 b1 a] A_2[a + b2 i]
+    big.add(gemm(b0 * b1, R2, b2, op(B_HBAR, h.h_off * 8), 1, (int64_t)b0 * b1, op(B_WS, h.A[2]), b2, 1,
+                 op(B_WS, h.bZ2), 1, (int64_t)b0 * b1));
+    for (int k = 0; k < h.K; ++k) {
+      const int* r = &h.ranks[(size_t)k * 3];
+      const int o0 = h.roff[(size_t)k * 3], o1 = h.roff[(size_t)k * 3 + 1], o2 = h.roff[(size_t)k * 3 + 2];
+      const double al = h.alpha[k];
+      const Operand Z0k = op(B_WS, h.bZ0 + (size_t)o0 * 8);
+      const Operand Z2k = op(B_WS, h.bZ2 + (size_t)b0 * b1 * o2 * 8);
+      const Operand A1k = op(B_WS, h.A[1] + (size_t)b1 * o1 * 8);
+      const Operand A2k = op(B_WS, h.A[2] + (size_t)b2 * o2 * 8);
+      const Operand Gk = op_abs(h.cores, (size_t)h.core_off[k] * 8);
+      const Operand Z01 = op(B_WS, h.bterm[3 * k]), W1 = op(B_WS, h.bterm[3 * k + 1]);
+      const Operand W0 = op(B_WS, h.bterm[3 * k + 2]);
+      // Z01[i0 + r0 i1 + r0 r1 j2] = sum_j1 Z0k[i0 + R0 j1 + R0 b1 j2] A_1[j1 + b1 (o1 + i1)]
+      GemmJob g = gemm(r[0], r[1], b1, Z0k, 1, R0, A1k, b1, 1, Z01, 1, r[0]);
+      g.batch = b2;
+      g.a_b = (int64_t)R0 * b1;
+      g.c_b = (int64_t)r[0] * r[1];
+      step1.add(g);
+      // W1[i0 + r0 j1 + r0 b1 i2] = sum_j2 Z0k[i0 + R0 j1 + R0 b1 j2] A_2[j2 + b2 (o2 + i2)]
+      g = gemm(r[0], r[2], b2, Z0k, 1, (int64_t)R0 * b1, A2k, b2, 1, W1, 1, (int64_t)r[0] * b1);
+      g.batch = b1;
+      g.a_b = R0;
+      g.c_b = r[0];
+      step1.add(g);
+      // W0[j0 + b0 i1 + b0 r1 i2] = sum_j1 Z2k[j0 + b0 j1 + b0 b1 i2] A_1[j1 + b1 (o1 + i1)]
+      g = gemm(b0, r[1], b1, Z2k, 1, b0, A1k, b1, 1, W0, 1, b0);
+      g.batch = r[2];
+      g.a_b = (int64_t)b0 * b1;
+      g.c_b = (int64_t)b0 * r[1];
+      step1.add(g);
+      // dG_k[J + r0 r1 i2] = alpha sum_j2 Z01[J + r0 r1 j2] A_2[j2 + b2 (o2 + i2)]
+      step2.add(gemm(r[0] * r[1], r[2], b2, Z01, 1, (int64_t)r[0] * r[1], A2k, b2, 1,
+                     op(B_DCORE, (size_t)(h.gcore_off + h.core_off[k]) * 8), 1, (int64_t)r[0] * r[1], al));
+      // B_k2[j2 + b2 (o2 + i2)] = alpha sum_J Z01[J + r0 r1 j2] G[J + r0 r1 i2]
+      step2.add(gemm(b2, r[2], r[0] * r[1], Z01, (int64_t)r[0] * r[1], 1, Gk, (int64_t)r[0] * r[1], 1,
+                     op(B_WS, h.bB[2] + (size_t)b2 * o2 * 8), 1, b2, al));
+      // B_k1[j1 + b1 (o1 + i1)] = alpha sum_{i0, i2} W1[i0 + r0 j1 + r0 b1 i2] G[i0 + r0 i1 + r0 r1 i2]
+      g = gemm(b1, r[1], r[0] * r[2], W1, r[0], 1, Gk, r[0], 1, op(B_WS, h.bB[1] + (size_t)b1 * o1 * 8), 1, b1, al);
+      g.K1 = r[0];
+      g.a_k1 = (int64_t)r[0] * b1;
+      g.b_k1 = (int64_t)r[0] * r[1];
+      step2.add(g);
+      // B_k0[j0 + b0 (o0 + i0)] = alpha sum_{i1, i2} W0[j0 + b0 (i1 + r1 i2)] G[i0 + r0 (i1 + r1 i2)]
+      step2.add(gemm(b0, r[0], r[1] * r[2], W0, 1, b0, Gk, 1, r[0], op(B_WS, h.bB[0] + (size_t)b0 * o0 * 8), 1, b0,
+                     al));
+    }
+    for (int n = 0; n < 3; ++n)
+      // dUcat_n[i + n col] = sum_a Q[i + n a] Bcat_n[a + b col]
+      du.add(gemm((int)h.n[n], h.R[n], h.b[n], op(B_Q, h.q_off[n] * 8), 1, h.n[n], op(B_WS, h.bB[n]), h.b[n], 1,
+                  op(B_DFAC, (size_t)h.gfac_off[n] * 8), 1, h.n[n]));
+  }
+  plan->push_gemm(plan->st_backward, big, "bwd:Z=Hbar.Acat");
+  plan->push_gemm(plan->st_backward, step1, "bwd:per-term1");
+  plan->push_gemm(plan->st_backward, step2, "bwd:per-term2");
+  plan->push_gemm(plan->st_backward, du, "bwd:dU=Q.B");
+}
+
 }  // namespace
 
 extern "C" {
@@ -941,6 +1022,17 @@ tks_status tks_plan_create(tks_plan** out, const tks_problem* problems, int32_t 
       plan->output_elems += h.n[m] * h.rmax[m];
     }
   }
+  for (auto& h : plan->probs) {
+    h.gcore_off = plan->grad_core_elems;
+    for (int k = 0; k < h.K; ++k) plan->grad_core_elems += prod(&h.ranks[(size_t)k * h.d], h.d);
+    for (int m = 0; m < h.d; ++m) {
+      h.gfac_off[m] = plan->grad_factor_elems;
+      plan->grad_factor_elems += h.n[m] * h.R[m];
+    }
+  }
+  plan->backward_ok = !mixed;
+  for (auto& h : plan->probs)
+    if (h.d != 3) plan->backward_ok = false;
   plan->ws_omega = alloc(plan->omega_elems * 8);
   plan->ws_Y = alloc(plan->sketch_elems * 8);
   plan->ws_Q = alloc(plan->basis_elems * 8);
@@ -1001,6 +1093,18 @@ tks_status tks_plan_create(tks_plan** out, const tks_problem* problems, int32_t 
     h.theta = alloc(8);
     h.Hp[0] = alloc(Hsz * 8);
     h.Hp[1] = alloc(Hsz * 8);
+    if (plan->backward_ok) {
+      h.bZ0 = alloc((size_t)h.R[0] * h.b[1] * h.b[2] * 8);
+      h.bZ2 = alloc((size_t)h.b[0] * h.b[1] * h.R[2] * 8);
+      for (int m = 0; m < 3; ++m) h.bB[m] = alloc((size_t)h.b[m] * h.R[m] * 8);
+      h.bterm.resize((size_t)3 * h.K);
+      for (int k = 0; k < h.K; ++k) {
+        const int* r = &h.ranks[(size_t)k * 3];
+        h.bterm[3 * k] = alloc((size_t)r[0] * r[1] * h.b[2] * 8);
+        h.bterm[3 * k + 1] = alloc((size_t)r[0] * h.b[1] * r[2] * 8);
+        h.bterm[3 * k + 2] = alloc((size_t)h.b[0] * r[1] * r[2] * 8);
+      }
+    }
     if (f32la) {
       int64_t stack_rows = 0;
       for (int m = 0; m < d; ++m) {
@@ -1156,6 +1260,10 @@ tks_status tks_plan_create(tks_plan** out, const tks_problem* problems, int32_t 
   plan->st_recompress = plan->st_sketch;
   plan->push(plan->st_recompress, S_QR, qr, (int64_t)qr.size(), "a5:qr", qr_flops, qr_bytes);
   for (const auto& s : plan->st_project) plan->st_recompress.push_back(s);
+  if (plan->backward_ok) {
+    plan->push_gemm(plan->st_backward, gA, "bwd:A=QT.Ucat");
+    build_backward3(plan);
+  }
   }
   if (f32la) build_hosvd_f32(plan);
   for (int n = 0; n < plan->dmax && !f32la; ++n) {
@@ -1283,6 +1391,8 @@ tks_status tks_plan_info(const tks_plan* plan, tks_plan_info_t* info) {
   info->launches_recompress = (int32_t)plan->st_recompress.size();
   info->flops_lowprec = plan->flops_low;
   info->flops_fp64 = plan->flops_f64;
+  info->grad_core_elems = plan->grad_core_elems;
+  info->grad_factor_elems = plan->grad_factor_elems;
   return TKS_OK;
 }
 
@@ -1304,6 +1414,8 @@ tks_status tks_problem_info(const tks_plan* plan, int32_t p, tks_problem_info_t*
   }
   info->core_off = h.h_off;
   info->out_core_off = h.out_core_off;
+  info->grad_core_off = h.gcore_off;
+  for (int m = 0; m < h.d; ++m) info->grad_factor_off[m] = h.gfac_off[m];
   return TKS_OK;
 }
 
@@ -1543,6 +1655,21 @@ tks_status tks_profile_end(tks_plan* plan, tks_step_profile_t* out, int32_t cap,
   }
   plan->profile_clear();
   return TKS_OK;
+}
+
+tks_status tks_project_core_backward(tks_plan* plan, void* workspace, const double* Q_in, const double* Hbar_in,
+                                     double* dcores, double* dfactors, void* stream) {
+  tks_status st = check_ws(plan, workspace);
+  if (st != TKS_OK) return st;
+  if (!plan->backward_ok)
+    return fail(TKS_EUNSUPPORTED, "tks_project_core_backward needs a TKS_FP64 plan of order-3 problems");
+  if (!Q_in || !Hbar_in || !dcores || !dfactors) return fail(TKS_EINVAL, "null Q_in, Hbar_in, dcores or dfactors");
+  Bases b = bind(plan, workspace);
+  b.p[B_Q] = reinterpret_cast<char*>(const_cast<double*>(Q_in));
+  b.p[B_HBAR] = reinterpret_cast<char*>(const_cast<double*>(Hbar_in));
+  b.p[B_DCORE] = reinterpret_cast<char*>(dcores);
+  b.p[B_DFAC] = reinterpret_cast<char*>(dfactors);
+  return run_steps(plan, plan->st_backward, b, static_cast<cudaStream_t>(stream));
 }
 
 tks_status tks_sync_status(tks_plan* plan, void* stream) {

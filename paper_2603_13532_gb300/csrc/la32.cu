@@ -145,8 +145,8 @@ __global__ void __launch_bounds__(512) qr_f32_kernel(const QrF32Job* __restrict_
 // explicit Q formed in place from the stored reflectors (backward accumulation: for j = b-1..0
 // apply H_j to the columns right of j, then replace column j by H_j e_j), columns flipped so
 // that diag(R) >= 0, written as float64.
-__global__ void __launch_bounds__(512) qr_smem_f32_kernel(const QrF32Job* __restrict__ jobs, Bases bases,
-                                                          Status* status) {
+__global__ void __launch_bounds__(1024) qr_smem_f32_kernel(const QrF32Job* __restrict__ jobs, Bases bases,
+                                                           Status* status) {
   extern __shared__ float sq[];
   __shared__ float red[32];
   __shared__ float sh_tau, sh_scale;
@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(512) qr_smem_f32_kernel(const QrF32Job* __rest
 // ----------------------------------------------------------------------------- TSQR block
 // Householder QR of a rows x cols block held in shared memory (column-major, ld = rows + 1),
 // one thread block; only the triangular factor is kept.
-__global__ void __launch_bounds__(256) tsqr_f32_kernel(const TsqrJob* __restrict__ jobs, Bases bases) {
+__global__ void __launch_bounds__(512) tsqr_f32_kernel(const TsqrJob* __restrict__ jobs, Bases bases) {
   extern __shared__ float smem_t[];
   __shared__ float red[32];
   __shared__ float sh_tau, sh_scale;
@@ -455,12 +455,12 @@ size_t qr_smem_bytes(int64_t n, int S) { return (size_t)(n * S + 2 * S) * sizeof
 
 void launch_qr_smem_f32(const QrF32Job* jobs, int njobs, size_t smem, const Bases& bases, Status* status,
                         cudaStream_t stream) {
-  qr_smem_f32_kernel<<<njobs, 512, smem, stream>>>(jobs, bases, status);
+  qr_smem_f32_kernel<<<njobs, 1024, smem, stream>>>(jobs, bases, status);
 }
 
 void launch_tsqr_f32(const TsqrJob* jobs, int njobs, int max_rows, int max_cols, const Bases& bases,
                      cudaStream_t stream) {
-  tsqr_f32_kernel<<<njobs, 256, tsqr_smem(max_rows, max_cols), stream>>>(jobs, bases);
+  tsqr_f32_kernel<<<njobs, 512, tsqr_smem(max_rows, max_cols), stream>>>(jobs, bases);
 }
 
 void launch_qr_f32(const QrF32Job* jobs, int njobs, const Bases& bases, Status* status, cudaStream_t stream) {

@@ -203,26 +203,39 @@ __global__ void core_sketch_f32_kernel(const CoreSketchF32Job* __restrict__ jobs
 // ----------------------------------------------------------------------------- order-3 kernels
 // Khatri-Rao core sketch of one (term, mode n) of an order-3 problem, in shared memory:
 //   V[a, c] = alpha sum_{p2} M2[p2, c] sum_{p1} G[a, p1, p2] M1[p1, c]
-// (p1, p2 the rank indices of the two other modes in ascending order).  Threads run over
-// outputs with c fastest, so the core reads are warp broadcasts and the M1 reads consecutive;
-// V is staged in shared memory and written with a fastest.
+// (p1, p2 the rank indices of the two other modes in ascending order).  A thread owns one column
+// c and 8 consecutive rows a: per (p1, p2) it loads one M1 value and the 8 core values as one
+// 16-byte broadcast, so each shared-memory wavefront feeds several FMAs.  V is staged in shared
+// memory and written with a fastest.
+constexpr int kCsRows = 8;
+
 __global__ void __launch_bounds__(256) core_sketch_krp3_kernel(const CoreSketchF32Job* __restrict__ jobs,
                                                                Bases bases) {
-  extern __shared__ float sm3[];
+  extern __shared__ __align__(16) float sm3[];
   const CoreSketchF32Job& J = jobs[blockIdx.x];
   const int n = J.n;
   const int j1 = (n == 0) ? 1 : 0, j2 = (n == 2) ? 1 : 2;
   const int rn = J.r[n], r1 = J.r[j1], r2 = J.r[j2], s = J.S;
+  const int rnp = (rn + kCsRows - 1) / kCsRows * kCsRows;   // rows padded to whole 8-row groups
   float* M1 = sm3;                       // [c + s p1]
   float* M2 = M1 + r1 * s;               // [c + s p2]
-  float* Vs = M2 + r2 * s;               // [a + rn c]
-  uint16_t* Gs = reinterpret_cast<uint16_t*>(Vs + rn * s);   // [a + rn (p1 + r1 p2)]
+  float* Vs = M2 + r2 * s;               // [a + rnp c]
+  // [a + rnp (p1 + r1 p2)], base rounded up to 16 bytes for the 8-wide loads
+  uint16_t* Gs = reinterpret_cast<uint16_t*>((reinterpret_cast<uintptr_t>(Vs + rnp * s) + 15) & ~uintptr_t(15));
   const uint16_t* G = at<uint16_t>(bases, J.core);
-  const int st[3] = {1, J.r[0], J.r[0] * J.r[1]};
   const int tot = rn * r1 * r2;
-  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-    const int a = e % rn, p1 = (e / rn) % r1, p2 = e / (rn * r1);
-    Gs[e] = G[a * st[n] + p1 * st[j1] + p2 * st[j2]];
+  {
+    int dst_stride[3];
+    dst_stride[n] = 1;
+    dst_stride[j1] = rnp;
+    dst_stride[j2] = rnp * r1;
+    const int q0 = J.r[0], q1 = J.r[1];
+    for (int e = threadIdx.x; e < rnp * r1 * r2; e += blockDim.x) Gs[e] = 0;
+    __syncthreads();
+    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+      const int i0 = e % q0, i1 = (e / q0) % q1, i2 = e / (q0 * q1);
+      Gs[i0 * dst_stride[0] + i1 * dst_stride[1] + i2 * dst_stride[2]] = G[e];
+    }
   }
   const float* Mg1 = at<float>(bases, J.M[j1]) + J.roff[j1];
   const float* Mg2 = at<float>(bases, J.M[j2]) + J.roff[j2];
@@ -235,16 +248,33 @@ __global__ void __launch_bounds__(256) core_sketch_krp3_kernel(const CoreSketchF
     M2[e] = Mg2[p + (int64_t)J.R[j2] * c];
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < rn * s; e += blockDim.x) {
-    const int c = e % s, a = e / s;
-    float acc = 0.f;
+  const int groups = rnp / kCsRows;
+  for (int e = threadIdx.x; e < groups * s; e += blockDim.x) {
+    const int c = e % s, a0 = (e / s) * kCsRows;
+    float acc[kCsRows];
+#pragma unroll
+    for (int t = 0; t < kCsRows; ++t) acc[t] = 0.f;
     for (int p2 = 0; p2 < r2; ++p2) {
-      const uint16_t* g = Gs + a + rn * r1 * p2;
-      float inner = 0.f;
-      for (int p1 = 0; p1 < r1; ++p1) inner = fmaf(bf16_float(g[rn * p1]), M1[c + s * p1], inner);
-      acc = fmaf(M2[c + s * p2], inner, acc);
+      float inner[kCsRows];
+#pragma unroll
+      for (int t = 0; t < kCsRows; ++t) inner[t] = 0.f;
+      const uint16_t* g = Gs + a0 + rnp * r1 * p2;
+      for (int p1 = 0; p1 < r1; ++p1) {
+        const float m1 = M1[c + s * p1];
+        const uint4 packed = *reinterpret_cast<const uint4*>(g + rnp * p1);
+        const uint32_t w[4] = {packed.x, packed.y, packed.z, packed.w};
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          inner[2 * t] = fmaf(__uint_as_float(w[t] << 16), m1, inner[2 * t]);
+          inner[2 * t + 1] = fmaf(__uint_as_float(w[t] & 0xffff0000u), m1, inner[2 * t + 1]);
+        }
+      }
+      const float m2 = M2[c + s * p2];
+#pragma unroll
+      for (int t = 0; t < kCsRows; ++t) acc[t] = fmaf(m2, inner[t], acc[t]);
     }
-    Vs[a + rn * c] = J.alpha * acc;
+#pragma unroll
+    for (int t = 0; t < kCsRows; ++t) Vs[a0 + t + rnp * c] = J.alpha * acc[t];
   }
   __syncthreads();
   uint16_t* V0 = at<uint16_t>(bases, J.V[0]);
@@ -254,63 +284,105 @@ __global__ void __launch_bounds__(256) core_sketch_krp3_kernel(const CoreSketchF
     const int a = e % rn, c = e / rn;
     const int64_t off = (J.roff[n] + a) + (int64_t)J.ldv * c;
     uint16_t h0, h1, h2;
-    split3(Vs[e], h0, h1, h2);
+    split3(Vs[a + rnp * c], h0, h1, h2);
     V0[off] = h0;
     V1[off] = h1;
     V2[off] = h2;
   }
 }
 
-// Stage (c2) chain of one term of an order-3 problem for a block of mode-1 rows, in shared
-// memory.  W[c, a, i1] = sum_{i0} A1[a, i0] G[i0, i1, c], then T[c, a, a1] = sum_{i1} W A2[a1, i1];
-// threads run with c fastest so the Tcat writes ((roff_2 + c) + ldT J) come out in runs.
+// Stage (c2) chain of one term of an order-3 problem for a block of AB <= 8 mode-1 rows, in shared
+// memory:  W[ia, i1, c] = sum_{i0} A1[a0 + ia, i0] G[i0, i1, c]  (a thread owns one (c, i1) and all
+// rows ia), then  T[ia, a1, c] = sum_{i1} W[ia, i1, c] A2[a1, i1]  (a thread owns one c, 4 columns
+// a1 and all rows ia: 32 accumulators).  Threads run with c fastest so the Tcat writes
+// ((roff_2 + c) + ldT J) come out in runs.
+constexpr int kChainCols = 4;
+
 __global__ void __launch_bounds__(256) chain3_kernel(const Chain3Job* __restrict__ jobs, Bases bases) {
   extern __shared__ float sc3[];
   const Chain3Job& J = jobs[blockIdx.x];
   const int r0 = J.r[0], r1 = J.r[1], r2 = J.r[2], b0 = J.b[0], b1 = J.b[1], AB = J.rows;
-  float* A1 = sc3;                  // [ia + AB i0]
-  float* A2 = A1 + AB * r0;         // [i1 + r1 a1]
-  float* Ws = A2 + r1 * b1;         // [c + r2 (ia + AB i1)]
-  uint16_t* Gt = reinterpret_cast<uint16_t*>(Ws + r2 * AB * r1);   // [c + r2 (i0 + r0 i1)]
+  constexpr int kAB = 8;
+  float* A1 = sc3;                  // [ia + 8 i0]
+  float* A2 = A1 + kAB * r0;        // [i1 + r1 a1]
+  float* Ws = A2 + r1 * b1;         // [c + r2 (ia + 8 i1)]
+  uint16_t* Gt = reinterpret_cast<uint16_t*>(Ws + r2 * kAB * r1);   // [c + r2 (i0 + r0 i1)]
   const uint16_t* G = at<uint16_t>(bases, J.core);
   for (int e = threadIdx.x; e < r0 * r1 * r2; e += blockDim.x) {
-    const int c = e % r2, i0 = (e / r2) % r0, i1 = e / (r2 * r0);
-    Gt[e] = G[i0 + r0 * (i1 + r1 * c)];
+    const int i0 = e % r0, i1 = (e / r0) % r1, c = e / (r0 * r1);
+    Gt[c + r2 * (i0 + r0 * i1)] = G[e];
   }
   const float* At1 = at<float>(bases, J.AT[0]) + J.roff[0];
   const float* At2 = at<float>(bases, J.AT[1]) + J.roff[1];
-  for (int e = threadIdx.x; e < AB * r0; e += blockDim.x) {
-    const int ia = e % AB, i0 = e / AB;
-    A1[e] = At1[i0 + (int64_t)J.R[0] * (J.a0 + ia)];
+  for (int e = threadIdx.x; e < kAB * r0; e += blockDim.x) {
+    const int ia = e % kAB, i0 = e / kAB;
+    A1[e] = ia < AB ? At1[i0 + (int64_t)J.R[0] * (J.a0 + ia)] : 0.f;
   }
   for (int e = threadIdx.x; e < r1 * b1; e += blockDim.x) {
     const int i1 = e % r1, a1 = e / r1;
     A2[e] = At2[i1 + (int64_t)J.R[1] * a1];
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < r2 * AB * r1; e += blockDim.x) {
-    const int c = e % r2, ia = (e / r2) % AB, i1 = e / (r2 * AB);
+  for (int e = threadIdx.x; e < r2 * r1; e += blockDim.x) {
+    const int c = e % r2, i1 = e / r2;
     const uint16_t* g = Gt + c + r2 * r0 * i1;
-    float w = 0.f;
-    for (int i0 = 0; i0 < r0; ++i0) w = fmaf(A1[ia + AB * i0], bf16_float(g[r2 * i0]), w);
-    Ws[e] = w;
+    float w[kAB];
+#pragma unroll
+    for (int t = 0; t < kAB; ++t) w[t] = 0.f;
+    for (int i0 = 0; i0 < r0; ++i0) {
+      const float gv = bf16_float(g[r2 * i0]);
+      const float4 a_lo = *reinterpret_cast<const float4*>(A1 + kAB * i0);
+      const float4 a_hi = *reinterpret_cast<const float4*>(A1 + kAB * i0 + 4);
+      w[0] = fmaf(a_lo.x, gv, w[0]);
+      w[1] = fmaf(a_lo.y, gv, w[1]);
+      w[2] = fmaf(a_lo.z, gv, w[2]);
+      w[3] = fmaf(a_lo.w, gv, w[3]);
+      w[4] = fmaf(a_hi.x, gv, w[4]);
+      w[5] = fmaf(a_hi.y, gv, w[5]);
+      w[6] = fmaf(a_hi.z, gv, w[6]);
+      w[7] = fmaf(a_hi.w, gv, w[7]);
+    }
+#pragma unroll
+    for (int t = 0; t < kAB; ++t) Ws[c + r2 * (t + kAB * i1)] = w[t];
   }
   __syncthreads();
   uint16_t* T0 = at<uint16_t>(bases, J.T[0]);
   uint16_t* T1 = at<uint16_t>(bases, J.T[1]);
   uint16_t* T2 = at<uint16_t>(bases, J.T[2]);
-  for (int e = threadIdx.x; e < r2 * AB * b1; e += blockDim.x) {
-    const int c = e % r2, ia = (e / r2) % AB, a1 = e / (r2 * AB);
-    const float* w = Ws + c + r2 * ia;
-    const float* a2 = A2 + r1 * a1;
-    float t = 0.f;
-    for (int i1 = 0; i1 < r1; ++i1) t = fmaf(w[r2 * AB * i1], a2[i1], t);
-    const int64_t off = (J.roff[2] + c) + (int64_t)J.ldT * (J.a0 + ia + (int64_t)b0 * a1);
-    uint16_t h0, h1, h2;
-    split3(J.alpha * t, h0, h1, h2);
-    T0[off] = h0;
-    T1[off] = h1;
-    T2[off] = h2;
+  const int ncol = (b1 + kChainCols - 1) / kChainCols;
+  for (int e = threadIdx.x; e < r2 * ncol; e += blockDim.x) {
+    const int c = e % r2, a1b = (e / r2) * kChainCols;
+    float t[kAB][kChainCols];
+#pragma unroll
+    for (int x = 0; x < kAB; ++x)
+#pragma unroll
+      for (int y = 0; y < kChainCols; ++y) t[x][y] = 0.f;
+    for (int i1 = 0; i1 < r1; ++i1) {
+      float w[kAB], a2[kChainCols];
+#pragma unroll
+      for (int x = 0; x < kAB; ++x) w[x] = Ws[c + r2 * (x + kAB * i1)];
+#pragma unroll
+      for (int y = 0; y < kChainCols; ++y) a2[y] = (a1b + y < b1) ? A2[i1 + r1 * (a1b + y)] : 0.f;
+#pragma unroll
+      for (int x = 0; x < kAB; ++x)
+#pragma unroll
+        for (int y = 0; y < kChainCols; ++y) t[x][y] = fmaf(w[x], a2[y], t[x][y]);
+    }
+#pragma unroll
+    for (int x = 0; x < kAB; ++x) {
+      if (x >= AB) break;
+#pragma unroll
+      for (int y = 0; y < kChainCols; ++y) {
+        const int a1 = a1b + y;
+        if (a1 >= b1) break;
+        const int64_t off = (J.roff[2] + c) + (int64_t)J.ldT * (J.a0 + x + (int64_t)b0 * a1);
+        uint16_t h0, h1, h2;
+        split3(J.alpha * t[x][y], h0, h1, h2);
+        T0[off] = h0;
+        T1[off] = h1;
+        T2[off] = h2;
+      }
+    }
   }
 }
 

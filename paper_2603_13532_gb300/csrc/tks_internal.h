@@ -25,7 +25,10 @@ enum BaseId : int32_t {
   B_H = 4,       // projected core buffer
   B_OUT = 5,     // recompression output (cores and factors)
   B_RANKS = 6,   // recompression output ranks (int32)
-  NBASE = 7
+  B_HBAR = 7,    // backward: dL/dH
+  B_DCORE = 8,   // backward: core gradients
+  B_DFAC = 9,    // backward: factor gradients
+  NBASE = 10
 };
 
 struct Bases {
