@@ -46,7 +46,10 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp64", "mixed", "mixed_f32la"], default="mixed_f32la")
     ap.add_argument("--fp64-steps", type=int, default=3, help="timed steps of the FP64 comparison")
-    ap.add_argument("--problems", type=int, default=64, help="independent sums per step and GPU")
+    ap.add_argument("--problems", type=int, default=152, help="independent sums per step and GPU")
+    ap.add_argument("--workload", default="decay512",
+                    choices=["decay512", "order4-krp", "order4-kron", "batched", "exact_recovery"])
+    ap.add_argument("--no-graph", action="store_true", help="time eager launches instead of graph replays")
     ap.add_argument("--seed", type=int, default=20260315)
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="budget of the cpu_baseline sample")
     ap.add_argument("--no-e2e", action="store_true")
@@ -55,9 +58,25 @@ def parse_args():
     return ap.parse_args()
 
 
-def workload_label(P):
-    return (f"decay512 x{P}: d=3, n=512, K=32, r~U{{8..32}}, mode spectra 10^(-i/8), Khatri-Rao, "
-            f"target 48, oversampling 10")
+WORKLOAD_LABELS = {
+    "decay512": "decay512 x{P}: d=3, n=512, K=32, r~U{{8..32}}, mode spectra 10^(-i/8), Khatri-Rao, target 48, "
+                "oversampling 10",
+    "order4-krp": "order4 x{P}: d=4, n=256, K=64, r~U{{4..24}}, cores N(0,1) 2^(-k/4), Khatri-Rao, target 40, "
+                  "oversampling 8",
+    "order4-kron": "order4 x{P}: d=4, n=256, K=64, r~U{{4..24}}, cores N(0,1) 2^(-k/4), Kronecker, target 40, "
+                   "oversampling 8",
+    "batched": "batched: {P} sums, d=3, n~U{{128,256,512,1024}}, K~U{{8..48}}, r~U{{4..32}}, Khatri-Rao, "
+               "target 1.5 x median rank, oversampling 5",
+    "exact_recovery": "exact_recovery x{P}: d=3, n=64, K=4, r=8, Kronecker, target 32",
+}
+
+
+def workload_label(P, workload="decay512"):
+    return WORKLOAD_LABELS[workload].format(P=P)
+
+
+def workload_kind(workload):
+    return "kron" if workload in ("order4-kron", "exact_recovery") else "krp"
 
 
 def sampled_entries(core, factors, idx):
@@ -81,11 +100,18 @@ def problem_seeds(P, seed, rank):
     return [seed + 7919 * (rank * P + i) for i in range(P)]
 
 
-def make_problems(P, seed, rank, bf16):
+def make_problems(P, seed, rank, bf16, workload="decay512"):
     from paper_2603_13532_gb300 import workloads as wl
+    if workload == "batched":
+        return wl.batched(seed=seed + 7919 * rank, num_problems=P, bf16=bf16).problems
     probs = []
     for s in problem_seeds(P, seed, rank):
-        probs += wl.decay512(seed=s, bf16=bf16).problems
+        if workload == "decay512":
+            probs += wl.decay512(seed=s, bf16=bf16).problems
+        elif workload.startswith("order4"):
+            probs += wl.order4(seed=s, kind=workload_kind(workload), bf16=bf16).problems
+        else:
+            probs += wl.exact_recovery(seed=s).problems
     return probs
 
 
@@ -181,7 +207,8 @@ def oracle_rate(problems, seed0, budget_s, kind, rounding):
     from oracle import sketch_sum as ss
     done, t0 = 0, time.perf_counter()
     for i, p in enumerate(problems):
-        ss.recompress(p.terms(), kind, p.target, p.oversampling, seed=seed0, problem=i, rounding=rounding)
+        ss.recompress(p.terms(), kind, p.target, p.oversampling, seed=seed0, problem=i, rounding=rounding,
+                      alpha=p.alpha)
         done += 1
         if time.perf_counter() - t0 >= budget_s:
             break
@@ -194,9 +221,10 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     from paper_2603_13532_gb300 import workloads as wl
-    bf16 = args.precision != "fp64"
+    bf16 = args.precision != "fp64" and args.workload != "exact_recovery"
     per_step = 2
-    probs = make_problems(per_step * (args.steps + args.warmup), args.seed, 0, bf16)
+    kind = workload_kind(args.workload)
+    probs = make_problems(per_step * (args.steps + args.warmup), args.seed, 0, bf16, args.workload)
     rounding = "bf16" if bf16 else None
     from oracle import sketch_sum as ss
     times = []
@@ -204,7 +232,8 @@ def run_reference(args, rank, world):
         t0 = time.perf_counter()
         for i in range(per_step):
             p = probs[s * per_step + i]
-            ss.recompress(p.terms(), "krp", p.target, p.oversampling, seed=args.seed, problem=i, rounding=rounding)
+            ss.recompress(p.terms(), kind, p.target, p.oversampling, seed=args.seed, problem=i, rounding=rounding,
+                          alpha=p.alpha)
         if s >= args.warmup:
             times.append(time.perf_counter() - t0)
     total = sum(times)
@@ -214,7 +243,7 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": workload_label(per_step) + " (reference arm: float64 CPU oracle)",
+            "config": {"workload": workload_label(per_step, args.workload) + " (reference arm: float64 CPU oracle)",
                        "problems_per_step": per_step, "parallelism": "host cores"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{per_step} problems per step, {args.steps} timed steps"},
@@ -311,8 +340,11 @@ def main():
     device = torch.device("cuda", local)
     bf16 = args.precision != "fp64"
     P = args.problems
-    problems = make_problems(P, args.seed, rank, bf16)
-    plan = binding.Plan(problems, kind="krp", precision=args.precision, seed=args.seed, device=device)
+    kind = workload_kind(args.workload)
+    if args.workload == "exact_recovery" and args.precision != "fp64":
+        raise SystemExit("the exact_recovery workload is float64 only")
+    problems = make_problems(P, args.seed, rank, bf16, args.workload)
+    plan = binding.Plan(problems, kind=kind, precision=args.precision, seed=args.seed, device=device)
     out = torch.zeros(plan.info.output_elems, dtype=torch.float64, device=device)
     ranks_t = torch.zeros(P * binding.MAX_ORDER, dtype=torch.int32, device=device)
     stream = torch.cuda.current_stream()
@@ -323,15 +355,33 @@ def main():
     for _ in range(args.warmup):
         step()
     plan.sync()
+    # per-stage times: CUDA events between the plan's launches over an eager pass of K steps
+    plan.profile_begin(args.steps)
+    eager_elapsed = time_steps(step, args.steps, stream)
+    prof = plan.profile_end()
+    plan.sync()
+    timed = step
+    graph = None
+    if not args.no_graph:
+        # the whole recompression as one CUDA graph (the launch sequence is fixed per plan)
+        graph = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream()
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            step()
+        stream.wait_stream(side)
+        with torch.cuda.graph(graph):
+            step()
+        graph.replay()
+        torch.cuda.synchronize()
+        timed = graph.replay
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
     torch.cuda.synchronize()
     clocks = ClockSampler()
     clocks.start()
-    plan.profile_begin(args.steps)
-    elapsed = time_steps(step, args.steps, stream)
-    prof = plan.profile_end()
+    elapsed = time_steps(timed, args.steps, stream)
     clock_info = clocks.stop(local)
     plan.sync()
     elapsed = max_over_ranks(elapsed, device)
@@ -355,7 +405,7 @@ def main():
 
         def e2e_step():
             plan.flat_inputs.copy_(host_in, non_blocking=True)
-            plan.recompress_raw(out, ranks_t)
+            timed()
             host_out.copy_(out, non_blocking=True)
             host_ranks.copy_(ranks_t, non_blocking=True)
 
@@ -371,7 +421,7 @@ def main():
     fp64_path = None
     if args.precision != "fp64" and args.fp64_steps > 0:
         import numpy as _np
-        plan64 = binding.Plan(problems, kind="krp", precision="fp64", seed=args.seed, device=device)
+        plan64 = binding.Plan(problems, kind=kind, precision="fp64", seed=args.seed, device=device)
         out64 = torch.zeros(plan64.info.output_elems, dtype=torch.float64, device=device)
         r64 = torch.zeros_like(ranks_t)
 
@@ -404,7 +454,7 @@ def main():
         in_bytes = plan.flat_inputs.numel() * plan.flat_inputs.element_size()
         cpu = None
         if not args.no_cpu:
-            rate, done, dt = oracle_rate(problems, args.seed, args.cpu_seconds, "krp",
+            rate, done, dt = oracle_rate(problems, args.seed, args.cpu_seconds, kind,
                                          "bf16" if bf16 else None)
             cpu = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                    "sample": f"{done} of the {P} problems of this batch in {dt:.1f} s (numpy float64, "
@@ -414,13 +464,16 @@ def main():
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64" if args.precision == "fp64" else "bf16",
                 "data": "synthetic",
-                "config": {"workload": workload_label(P), "problems_per_step": P,
+                "config": {"workload": workload_label(P, args.workload), "problems_per_step": P,
                            "precision": args.precision, "tflops": tflops,
                            "flops_per_step": plan.info.flops_lowprec + plan.info.flops_fp64,
                            "l2": f"inputs {in_bytes / 1e6:.0f} MB per GPU > L2 129 MB, no flush",
                            "parallelism": f"replicas x{world}"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fp64_path": fp64_path,
                 "gpu_launches": int(plan.info.launches_recompress) * args.steps,
+                "timing": ("CUDA-graph replays of the whole recompression" if graph is not None
+                           else "eager launches") + "; stage times from an eager pass with events",
+                "eager_ms_per_step": 1e3 * eager_elapsed / args.steps,
                 "clocks": clock_info,
                 "stages": [{"name": s["name"], "ms_per_call": s["ms"] / max(1, s["calls"])} for s in prof]}
         print(json.dumps(line), flush=True)

@@ -459,8 +459,8 @@ static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
       t.cols = h.R[m];
       t.ld_src = (int64_t)n;
       t.ld_dst = h.ldU[m];
-      t.tiles_r = ceil_div(n, 32);
-      t.tiles_c = ceil_div(h.R[m], 32);
+      t.tiles_r = ceil_div(n, 64);
+      t.tiles_c = ceil_div(h.R[m], 64);
       t.tile_begin = tr_tiles;
       tr_tiles += t.tiles_r * t.tiles_c;
       tr.push_back(t);

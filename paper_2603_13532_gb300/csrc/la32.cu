@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(512) tsqr_f32_kernel(const TsqrJob* __restrict
 // One-sided Jacobi on the columns of the b x b matrix A = R with the round-robin ordering:
 // each round rotates b/2 disjoint column pairs (one warp per pair) so that they become
 // orthogonal; V accumulates the rotations.  At convergence A = U Sigma, R = U Sigma V^T.
-constexpr int kSvdSweeps = 40;
+constexpr int kSvdSweeps = 30;
 
 __global__ void __launch_bounds__(1024) svd_jacobi_f32_kernel(const SvdJob* __restrict__ jobs, Bases bases,
                                                               Status* status) {
@@ -326,8 +326,25 @@ __global__ void __launch_bounds__(1024) svd_jacobi_f32_kernel(const SvdJob* __re
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  // rotate while |a_p . a_q| > b eps_f32 ||a_p|| ||a_q|| (the usual m eps convergence test)
+  // rotate while |a_p . a_q| > b eps_f32 ||a_p|| ||a_q|| (the usual m eps convergence test), except
+  // for columns at the float32 noise floor (norm <= 8 eps max column norm): their couplings are
+  // rounding noise that the relative test would chase forever, and they cannot be resolved anyway
   const float thr = (float)b * 5.96e-8f;
+  __shared__ float sh_noise2;
+  {
+    if (threadIdx.x == 0) sh_noise2 = 0.f;
+    __syncthreads();
+    for (int c = warp; c < b; c += nw) {
+      float s2 = 0.f;
+      for (int i = lane; i < b; i += 32) s2 = fmaf(A[i + c * ld], A[i + c * ld], s2);
+      s2 = warp_sum_f(s2);
+      if (lane == 0) atomicMax(reinterpret_cast<int*>(&sh_noise2), __float_as_int(s2));
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) sh_noise2 *= (8.f * 5.96e-8f) * (8.f * 5.96e-8f);
+    __syncthreads();
+  }
+  const float noise2 = sh_noise2;
   int sweep = 0;
   for (; sweep < kSvdSweeps; ++sweep) {
     if (threadIdx.x == 0) sh_rot = 0;
@@ -349,7 +366,7 @@ __global__ void __launch_bounds__(1024) svd_jacobi_f32_kernel(const SvdJob* __re
         al = warp_sum_f(al);
         be = warp_sum_f(be);
         ga = warp_sum_f(ga);
-        if (fabsf(ga) > thr * sqrtf(al * be) && ga != 0.f) {
+        if (fabsf(ga) > thr * sqrtf(al * be) && ga != 0.f && fminf(al, be) > noise2) {
           const float zeta = (be - al) / (2.f * ga);
           const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
           const float c = 1.f / sqrtf(1.f + t * t), s = c * t;

@@ -405,7 +405,9 @@ __global__ void split_f64_kernel(const SplitJob* __restrict__ jobs, int njobs, i
 
 __global__ void __launch_bounds__(256) transpose_bf16_kernel(const TransposeJob* __restrict__ jobs, int njobs,
                                                              Bases bases) {
-  __shared__ uint16_t tile[32][33];
+  // 64 x 64 tiles; columns are read and rows written as pairs of bf16 (4-byte accesses) when the
+  // leading dimensions are even, so a warp moves 128 contiguous bytes per access
+  __shared__ uint16_t tile[64][66];
   int lo = 0, hi = njobs - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
@@ -416,15 +418,32 @@ __global__ void __launch_bounds__(256) transpose_bf16_kernel(const TransposeJob*
   const int tr = local % J.tiles_r, tcol = local / J.tiles_r;
   const uint16_t* src = at<uint16_t>(bases, J.src);
   uint16_t* dst = at<uint16_t>(bases, J.dst);
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  for (int y = ty; y < 32; y += 8) {
-    const int i = tr * 32 + tx, j = tcol * 32 + y;
-    if (i < J.rows && j < J.cols) tile[y][tx] = src[i + J.ld_src * j];
-  }
-  __syncthreads();
-  for (int y = ty; y < 32; y += 8) {
-    const int j = tcol * 32 + tx, i = tr * 32 + y;
-    if (i < J.rows && j < J.cols) dst[j + J.ld_dst * i] = tile[tx][y];
+  const int i0 = tr * 64, j0 = tcol * 64;
+  const bool pairs = ((J.ld_src | J.ld_dst) & 1) == 0 && i0 + 64 <= J.rows && j0 + 64 <= J.cols;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 lanes x 8 warps
+  if (pairs) {
+    for (int y = ty; y < 64; y += 8) {   // column j0 + y, rows i0 + 2 tx, i0 + 2 tx + 1
+      const uint32_t v = *reinterpret_cast<const uint32_t*>(src + (i0 + 2 * tx) + J.ld_src * (int64_t)(j0 + y));
+      tile[2 * tx][y] = (uint16_t)(v & 0xffffu);
+      tile[2 * tx + 1][y] = (uint16_t)(v >> 16);
+    }
+    __syncthreads();
+    for (int y = ty; y < 64; y += 8) {   // row i0 + y of the source = column of dst
+      const uint32_t v = (uint32_t)tile[y][2 * tx] | ((uint32_t)tile[y][2 * tx + 1] << 16);
+      *reinterpret_cast<uint32_t*>(dst + (j0 + 2 * tx) + J.ld_dst * (int64_t)(i0 + y)) = v;
+    }
+  } else {
+    for (int y = ty; y < 64; y += 8)
+      for (int x = tx; x < 64; x += 32) {
+        const int i = i0 + x, j = j0 + y;
+        if (i < J.rows && j < J.cols) tile[x][y] = src[i + J.ld_src * (int64_t)j];
+      }
+    __syncthreads();
+    for (int y = ty; y < 64; y += 8)
+      for (int x = tx; x < 64; x += 32) {
+        const int j = j0 + x, i = i0 + y;
+        if (i < J.rows && j < J.cols) dst[j + J.ld_dst * (int64_t)i] = tile[y][x];
+      }
   }
 }
 
