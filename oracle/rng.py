@@ -26,8 +26,12 @@ Element e of Omega (column-major, e = i + n_j * c) is lane e % 4 of block
 e // 4.  Lanes 0, 1 are r(w0) cos(2 pi u(w1)), r(w0) sin(2 pi u(w1)); lanes
 2, 3 the same for (w2, w3).
 
-The low-precision sketch (``rounding="bf16"``) uses the same draws rounded to
-float32 and then to bfloat16, each round-to-nearest-even.
+The low-precision sketch (``rounding="bf16"``) only needs bfloat16 draws, so it
+takes them from a float32 Box-Muller on the same Philox words (``gaussian_f32``):
+u = (floor(w / 2^41) + 1/2) * 2^-23 (exact in float32), then the same two series
+with float32 coefficients and fewer terms, every step a correctly rounded
+float32 operation in one fixed order (numpy's float32 array arithmetic), and the
+float32 result rounded to bfloat16 (round-to-nearest-even).
 """
 import numpy as np
 
@@ -168,6 +172,99 @@ def gaussian(seed, problem, mode, index, stream=OMEGA_STREAM):
     return np.where((lane & 1) == 0, r * c, r * s)
 
 
+# ---- float32 variant (low-precision sketch) -------------------------------
+_F32 = np.float32
+_SQRT_HALF_F = _F32(float.fromhex("0x1.6a09e6p-1"))
+_LN2_HI_F = _F32(float.fromhex("0x1.62e4p-1"))       # 16 significant bits: e*_LN2_HI_F exact
+_LN2_LO_F = _F32(float.fromhex("0x1.7f7d1cp-20"))    # ln 2 - _LN2_HI_F, rounded to float32
+_LOG_C_F = [_F32(1.0 / (2 * k + 1)) for k in range(1, 6)]   # 1/(2k+1), k = 1..5
+_PIO4_F = _F32(float.fromhex("0x1.921fb6p-1"))
+_SIN_C_F = [_F32(float.fromhex(h)) for h in (
+    "-0x1.555556p-3", "0x1.111112p-7", "-0x1.a01a02p-13", "0x1.71de3ap-19")]          # k = 1..4
+_COS_C_F = [_F32(float.fromhex(h)) for h in (
+    "-0x1p-1", "0x1.555556p-5", "-0x1.6c16c2p-10", "0x1.a01a02p-16", "-0x1.27e4fcp-22")]  # k = 1..5
+
+
+def uniform_open01_f32(w):
+    """Map uint64 words to float32 in (0, 1): (floor(w/2^41) + 1/2) * 2^-23 (exact)."""
+    return ((np.asarray(w, dtype=_U64) >> _U64(41)).astype(_F32) + _F32(0.5)) * _F32(2.0 ** -23)
+
+
+def ln_f32(u):
+    """ln u in float32 for u in (0, 1): the atanh series of ``ln`` with 5 terms.
+
+    |f| <= 0.1716, so the first omitted term s^5/13 is below 2^-27 relative to q.
+    Reduction and the split ln 2 = _LN2_HI_F + _LN2_LO_F as in ``ln``; e lies in
+    [-23, 0] for the inputs of ``uniform_open01_f32``, so e * _LN2_HI_F is exact.
+    """
+    u = np.asarray(u, dtype=_F32)
+    m, e = np.frexp(u)
+    low = m < _SQRT_HALF_F
+    m = np.where(low, m * _F32(2.0), m).astype(_F32)
+    e = np.where(low, e - 1, e).astype(_F32)
+    f = (m - _F32(1.0)) / (m + _F32(1.0))
+    s = f * f
+    q = np.full_like(s, _LOG_C_F[-1])
+    for c in reversed(_LOG_C_F[:-1]):
+        q = q * s + c
+    two_f = f * _F32(2.0)
+    ln_m = two_f + (two_f * s) * q
+    return e * _LN2_HI_F + (e * _LN2_LO_F + ln_m)
+
+
+def sincos_2pi_f32(u):
+    """(cos 2 pi u, sin 2 pi u) in float32: the octant reduction of ``sincos_2pi``, then
+    Taylor series with 4 (sine) and 5 (cosine) terms; on [0, pi/4] the omitted terms are
+    below 2^-28 of the result."""
+    u = np.asarray(u, dtype=_F32)
+    x = u * _F32(8.0)
+    k = np.floor(x)
+    f = x - k
+    k = k.astype(np.int64)
+    odd = (k & 1) == 1
+    g = np.where(odd, _F32(1.0) - f, f).astype(_F32)
+    t = g * _PIO4_F
+    s2 = t * t
+    p = np.full_like(s2, _SIN_C_F[-1])
+    for c in reversed(_SIN_C_F[:-1]):
+        p = p * s2 + c
+    sin_t = t + (t * s2) * p
+    q = np.full_like(s2, _COS_C_F[-1])
+    for c in reversed(_COS_C_F[:-1]):
+        q = q * s2 + c
+    cos_t = _F32(1.0) + s2 * q
+    swap = (k == 1) | (k == 2) | (k == 5) | (k == 6)
+    c_abs = np.where(swap, sin_t, cos_t)
+    s_abs = np.where(swap, cos_t, sin_t)
+    cos_neg = (k >= 2) & (k <= 5)
+    sin_neg = k >= 4
+    return (np.where(cos_neg, -c_abs, c_abs).astype(_F32),
+            np.where(sin_neg, -s_abs, s_abs).astype(_F32))
+
+
+def gaussian_f32(seed, problem, mode, index, stream=OMEGA_STREAM):
+    """float32 standard normal draw ``index`` of (seed, problem, mode, stream): the same
+    Philox words and lane layout as ``gaussian``, evaluated in float32."""
+    index = np.asarray(index, dtype=np.int64)
+    block = (index >> 2).astype(_U64)
+    lane = index & 3
+    w0, w1, w2, w3 = philox4x64_10(block, _U64(mode), _U64(problem), _U64(stream),
+                                   _U64(seed), _U64(0))
+    first = lane < 2
+    u1 = uniform_open01_f32(np.where(first, w0, w2))
+    u2 = uniform_open01_f32(np.where(first, w1, w3))
+    r = np.sqrt(_F32(-2.0) * ln_f32(u1))
+    c, s = sincos_2pi_f32(u2)
+    return np.where((lane & 1) == 0, r * c, r * s).astype(_F32)
+
+
+def round_bf16(x):
+    """float32 -> bfloat16 (round-to-nearest-even), returned as float64 values."""
+    b = np.asarray(x, dtype=_F32).view(np.uint32).astype(np.uint64)
+    b = (b + np.uint64(0x7FFF) + ((b >> np.uint64(16)) & np.uint64(1))) >> np.uint64(16)
+    return (b.astype(np.uint32) << np.uint32(16)).view(_F32).astype(np.float64)
+
+
 def round_fp32_then_bf16(x):
     """float64 -> float32 (RNE) -> bfloat16 (RNE), returned as float64 values."""
     f = np.asarray(x, dtype=np.float64).astype(np.float32)
@@ -179,9 +276,10 @@ def round_fp32_then_bf16(x):
 def omega(seed, problem, mode, n, s, rounding=None):
     """Omega_mode in R^{n x s}, column-major draw order (Sec. 3.1, one per mode)."""
     idx = np.arange(n * s, dtype=np.int64)
-    z = gaussian(seed, problem, mode, idx)
     if rounding == "bf16":
-        z = round_fp32_then_bf16(z)
-    elif rounding is not None:
+        z = round_bf16(gaussian_f32(seed, problem, mode, idx))
+    elif rounding is None:
+        z = gaussian(seed, problem, mode, idx)
+    else:
         raise ValueError(f"unknown rounding {rounding!r}")
     return z.reshape(n, s, order="F")

@@ -38,21 +38,28 @@ __global__ void omega_kernel(const OmegaJob* __restrict__ jobs, int njobs, int64
     const int j = find_job(jobs, njobs, g);
     const OmegaJob& J = jobs[j];
     const int64_t blk = g - J.begin;
-    double z[4];
-    rng::gaussian4(seed, (uint64_t)J.problem, (uint64_t)J.mode, 0ull, (uint64_t)blk, z);
     double* out = at<double>(bases, J.out);
-    uint16_t* plane = J.has_plane ? at<uint16_t>(bases, J.plane) : nullptr;
+    if (J.bf16) {
+      // low-precision sketch: float32 draws rounded to bfloat16
+      float z[4];
+      rng::gaussian4_f32(seed, (uint64_t)J.problem, (uint64_t)J.mode, 0ull, (uint64_t)blk, z);
+      uint16_t* plane = J.has_plane ? at<uint16_t>(bases, J.plane) : nullptr;
 #pragma unroll
-    for (int l = 0; l < 4; ++l) {
-      const int64_t e = 4 * blk + l;
-      if (e < J.count) {
-        if (J.bf16) {
-          const uint16_t h = rng::to_bf16_bits(z[l]);
+      for (int l = 0; l < 4; ++l) {
+        const int64_t e = 4 * blk + l;
+        if (e < J.count) {
+          const uint16_t h = rng::f32_to_bf16_bits(z[l]);
           out[e] = rng::bf16_bits_to_double(h);
           if (plane) plane[e] = h;
-        } else {
-          out[e] = z[l];
         }
+      }
+    } else {
+      double z[4];
+      rng::gaussian4(seed, (uint64_t)J.problem, (uint64_t)J.mode, 0ull, (uint64_t)blk, z);
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {
+        const int64_t e = 4 * blk + l;
+        if (e < J.count) out[e] = z[l];
       }
     }
   }

@@ -11,6 +11,11 @@
 // reduction) with only correctly rounded IEEE operations in one fixed order, written with
 // explicit __d*_rn intrinsics so the compiler cannot contract them into fused multiply-adds.
 // Any transcription performing the same operations in the same order produces the same bits.
+//
+// The low-precision sketch draws in float32 instead (gaussian4_f32): the same Philox words,
+// u = (floor(w/2^41) + 1/2) 2^-23 (exact in float32), the same two series with float32
+// coefficients and fewer terms (5 for ln, 4 for sin, 5 for cos), explicit __f*_rn operations,
+// then round-to-nearest-even to bfloat16.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -121,9 +126,81 @@ __device__ __forceinline__ void gaussian4(uint64_t seed, uint64_t problem, uint6
   }
 }
 
-// float64 -> float32 (RNE) -> bfloat16 (RNE), returned as the bfloat16 bit pattern.
-__device__ __forceinline__ uint16_t to_bf16_bits(double x) {
-  uint32_t b = __float_as_uint(__double2float_rn(x));
+// ---- float32 variant -------------------------------------------------------------------
+
+__device__ __forceinline__ float uniform_open01_f32(uint64_t w) {
+  return __fmul_rn(__fadd_rn(static_cast<float>(static_cast<uint32_t>(w >> 41)), 0.5f), 0x1p-23f);
+}
+
+// ln u, u in [2^-24, 1): reduction as in ln_open01, atanh series with 1/(2k+1), k = 1..5;
+// e lies in [-23, 0], so e * ln2_hi (16 significant bits) is exact.
+__device__ __forceinline__ float ln_open01_f32(float u) {
+  const uint32_t bits = __float_as_uint(u);
+  int e = static_cast<int>((bits >> 23) & 0xffu) - 126;
+  float m = __uint_as_float((bits & 0x007fffffu) | 0x3f000000u);
+  if (m < 0x1.6a09e6p-1f) {
+    m = __fmul_rn(m, 2.0f);
+    e -= 1;
+  }
+  const float f = __fdiv_rn(__fsub_rn(m, 1.0f), __fadd_rn(m, 1.0f));
+  const float s = __fmul_rn(f, f);
+  const float c[5] = {0x1.555556p-2f, 0x1.99999ap-3f, 0x1.24924ap-3f, 0x1.c71c72p-4f, 0x1.745d18p-4f};
+  float q = c[4];
+#pragma unroll
+  for (int k = 3; k >= 0; --k) q = __fadd_rn(__fmul_rn(q, s), c[k]);
+  const float two_f = __fmul_rn(f, 2.0f);
+  const float ln_m = __fadd_rn(two_f, __fmul_rn(__fmul_rn(two_f, s), q));
+  const float ef = static_cast<float>(e);
+  return __fadd_rn(__fmul_rn(ef, 0x1.62e4p-1f), __fadd_rn(__fmul_rn(ef, 0x1.7f7d1cp-20f), ln_m));
+}
+
+// (cos 2 pi u, sin 2 pi u) in float32; octant reduction as in sincos_2pi, Taylor terms
+// (-1)^k/(2k+1)!, k = 1..4 and (-1)^k/(2k)!, k = 1..5.
+__device__ __forceinline__ void sincos_2pi_f32(float u, float* cs, float* sn) {
+  const float x = __fmul_rn(u, 8.0f);
+  const float kf = floorf(x);
+  const float f = __fsub_rn(x, kf);
+  const int k = static_cast<int>(kf);
+  const float g = (k & 1) ? __fsub_rn(1.0f, f) : f;
+  const float t = __fmul_rn(g, 0x1.921fb6p-1f);
+  const float s2 = __fmul_rn(t, t);
+  const float sc[4] = {-0x1.555556p-3f, 0x1.111112p-7f, -0x1.a01a02p-13f, 0x1.71de3ap-19f};
+  const float cc[5] = {-0x1p-1f, 0x1.555556p-5f, -0x1.6c16c2p-10f, 0x1.a01a02p-16f, -0x1.27e4fcp-22f};
+  float p = sc[3];
+#pragma unroll
+  for (int i = 2; i >= 0; --i) p = __fadd_rn(__fmul_rn(p, s2), sc[i]);
+  const float sin_t = __fadd_rn(t, __fmul_rn(__fmul_rn(t, s2), p));
+  float q = cc[4];
+#pragma unroll
+  for (int i = 3; i >= 0; --i) q = __fadd_rn(__fmul_rn(q, s2), cc[i]);
+  const float cos_t = __fadd_rn(1.0f, __fmul_rn(s2, q));
+  const bool swap = (k == 1) || (k == 2) || (k == 5) || (k == 6);
+  const float ca = swap ? sin_t : cos_t;
+  const float sa = swap ? cos_t : sin_t;
+  *cs = (k >= 2 && k <= 5) ? -ca : ca;
+  *sn = (k >= 4) ? -sa : sa;
+}
+
+// The four float32 normals of Philox block `block` (same words and lanes as gaussian4).
+__device__ __forceinline__ void gaussian4_f32(uint64_t seed, uint64_t problem, uint64_t mode,
+                                              uint64_t stream, uint64_t block, float z[4]) {
+  uint64_t c[4] = {block, mode, problem, stream};
+  philox4x64_10(c, seed, 0ull);
+#pragma unroll
+  for (int pair = 0; pair < 2; ++pair) {
+    const float u1 = uniform_open01_f32(c[2 * pair]);
+    const float u2 = uniform_open01_f32(c[2 * pair + 1]);
+    const float r = __fsqrt_rn(__fmul_rn(-2.0f, ln_open01_f32(u1)));
+    float cs, sn;
+    sincos_2pi_f32(u2, &cs, &sn);
+    z[2 * pair] = __fmul_rn(r, cs);
+    z[2 * pair + 1] = __fmul_rn(r, sn);
+  }
+}
+
+// float32 -> bfloat16 (RNE), returned as the bfloat16 bit pattern.
+__device__ __forceinline__ uint16_t f32_to_bf16_bits(float x) {
+  uint32_t b = __float_as_uint(x);
   b = (b + 0x7FFFu + ((b >> 16) & 1u)) >> 16;
   return static_cast<uint16_t>(b);
 }

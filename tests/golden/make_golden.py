@@ -1,7 +1,8 @@
 """Writes the stored expected values under tests/golden/ by calling only oracle/.
 
-  omega_head.json   first draws of Omega_j (hex floats) for a few (seed, problem, mode);
-                    definition: oracle/rng.py (Philox4x64-10 + Box-Muller, Sec. 3.1)
+  omega_head.json   first draws of Omega_j (hex floats) for a few (seed, problem, mode):
+                    float64 draws, float32 draws and their bfloat16 roundings (low-precision
+                    sketch); definition: oracle/rng.py (Philox4x64-10 + Box-Muller, Sec. 3.1)
   sketch_sizes.json sketch sizes from Eq. heuristic_formula (Kronecker, integer form) and
                     s = max ell (Khatri-Rao, Sec. 3.2) for the measured workloads
 
@@ -23,9 +24,11 @@ def main():
     heads = []
     for seed, problem, mode in [(20260315, 0, 0), (20260315, 0, 2), (20260315, 5, 1), (1, 0, 0)]:
         z = rng.gaussian(seed, problem, mode, np.arange(32))
-        zb = rng.round_fp32_then_bf16(z)
+        z32 = rng.gaussian_f32(seed, problem, mode, np.arange(32))
+        zb = rng.round_bf16(z32)
         heads.append(dict(seed=seed, problem=problem, mode=mode,
                           values=[float(x).hex() for x in z],
+                          f32_values=[float(x).hex() for x in z32],
                           bf16_values=[float(x).hex() for x in zb]))
     with open(os.path.join(HERE, "omega_head.json"), "w") as f:
         json.dump(dict(source="oracle/rng.py (Philox4x64-10 + Box-Muller)", draws=heads), f, indent=1)

@@ -1,7 +1,7 @@
 """GPU parity of the mixed-precision path (TKS_MIXED) against the FP64 CPU oracle, through the C ABI.
 
-The mixed path reads bfloat16 cores and factors and sketches with Omega rounded to float32 then
-bfloat16; the oracle runs on the same bfloat16-valued inputs and the same rounded Omega in
+The mixed path reads bfloat16 cores and factors and sketches with Omega drawn in float32 and
+rounded to bfloat16 (oracle.rng.gaussian_f32); the oracle runs on the same bfloat16-valued inputs and the same rounded Omega in
 float64, so every difference is arithmetic of the GPU path:
 
   Omega              bit-exact
@@ -63,6 +63,23 @@ def test_mixed_omega_is_rounded_draws(cuda_lib):
         for m in range(3):
             ref = rng.omega(31, p, m, prob.dims[m], pi.omega_cols[m], rounding="bf16")
             assert np.array_equal(om[p][m], ref)
+
+
+def test_mixed_omega_matches_golden_heads(cuda_lib):
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                                       "omega_head.json")))
+    for entry in gold["draws"]:
+        p = entry["problem"]
+        probs = wl._finish([wl.exact_recovery(n=16, K=1, r=2, target=2).problems[0] for _ in range(p + 1)],
+                           True)
+        for q in probs:
+            q.target = [4, 4, 4]
+            q.oversampling = [0, 0, 0]
+        om = _plan(probs, "krp", entry["seed"]).omega()[p][entry["mode"]].ravel(order="F")[:32]
+        want = np.array([float.fromhex(h) for h in entry["bf16_values"]])
+        assert np.array_equal(om, want)
 
 
 @pytest.mark.parametrize("kind", ["krp", "kron"])

@@ -111,9 +111,96 @@ def test_omega_column_major_and_bf16_rounding():
     Om = rng.omega(5, 2, 1, 7, 3)
     flat = rng.gaussian(5, 2, 1, np.arange(21))
     np.testing.assert_array_equal(Om[:, 1], flat[7:14])
-    Ob = rng.omega(5, 2, 1, 7, 3, rounding="bf16")
     ref = torch.from_numpy(Om).to(torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
-    np.testing.assert_array_equal(Ob, ref)
+    np.testing.assert_array_equal(rng.round_fp32_then_bf16(Om), ref)
     # halfway cases round to even
     x = np.array([1 + 2.0 ** -8, 1 + 3 * 2.0 ** -8, -(1 + 2.0 ** -8)])
     np.testing.assert_array_equal(rng.round_fp32_then_bf16(x), [1.0, 1 + 4 * 2.0 ** -8, -1.0])
+
+
+# ---- float32 variant used by the low-precision sketch ----------------------
+
+def test_uniform_f32_open_interval_exact():
+    w = np.array([0, 2**41 - 1, 2**41, 2**63, 2**64 - 1], dtype=np.uint64)
+    u = rng.uniform_open01_f32(w)
+    assert u.dtype == np.float32
+    assert u[0] == 2.0 ** -24 and u[1] == 2.0 ** -24
+    assert u[2] == 1.5 * 2.0 ** -23
+    assert u[3] == 0.5 + 2.0 ** -24
+    assert u[-1] == 1.0 - 2.0 ** -24
+    # every value is (j + 1/2) 2^-23 exactly
+    j = (w >> np.uint64(41)).astype(np.float64)
+    np.testing.assert_array_equal(u.astype(np.float64), (j + 0.5) * 2.0 ** -23)
+
+
+def _ulp32_err(x, ref):
+    return abs(float(x) - float(ref)) / float(np.spacing(np.float32(abs(float(ref)))))
+
+
+def test_ln_f32_within_two_ulp():
+    g = np.random.default_rng(11)
+    w = g.integers(0, 2**63, size=3000, dtype=np.uint64) * np.uint64(2)
+    u = np.concatenate([rng.uniform_open01_f32(w),
+                        np.array([2.0 ** -24, 1.5 * 2.0 ** -23, 0.5, 0.5 + 2.0 ** -24, 1 - 2.0 ** -24,
+                                  np.sqrt(0.5), 0.75], dtype=np.float32)]).astype(np.float32)
+    out = rng.ln_f32(u)
+    assert out.dtype == np.float32
+    mpmath.mp.prec = 80
+    worst = max(_ulp32_err(o, mpmath.log(mpmath.mpf(float(x)))) for o, x in zip(out, u))
+    assert worst <= 2.0, worst
+
+
+def test_sincos_2pi_f32_accuracy():
+    g = np.random.default_rng(12)
+    u = np.concatenate([rng.uniform_open01_f32(g.integers(0, 2**63, size=2000, dtype=np.uint64)),
+                        np.array([0.125, 0.25, 0.375, 0.5, 0.625, 0.75, 0.875, 2.0 ** -24,
+                                  1 - 2.0 ** -24], dtype=np.float32)]).astype(np.float32)
+    c, s = rng.sincos_2pi_f32(u)
+    mpmath.mp.prec = 80
+    for ci, si, ui in zip(c, s, u):
+        ang = 2 * mpmath.pi * mpmath.mpf(float(ui))
+        # absolute error at the exact float32 argument, within 1.5 float32 ulp of 1
+        assert abs(float(ci) - float(mpmath.cos(ang))) <= 1.8e-7
+        assert abs(float(si) - float(mpmath.sin(ang))) <= 1.8e-7
+
+
+def test_gaussian_f32_lane_layout_is_box_muller():
+    seed, prob, mode = 77, 3, 1
+    idx = np.arange(16)
+    z = rng.gaussian_f32(seed, prob, mode, idx)
+    assert z.dtype == np.float32
+    w = rng.philox4x64_10(np.arange(4, dtype=np.uint64), mode, prob, 0, seed, 0)
+    u = [rng.uniform_open01_f32(x) for x in w]
+    mpmath.mp.prec = 80
+    for e in idx:
+        b, lane = e // 4, e % 4
+        u1, u2 = (u[0][b], u[1][b]) if lane < 2 else (u[2][b], u[3][b])
+        r = mpmath.sqrt(-2 * mpmath.log(mpmath.mpf(float(u1))))
+        ang = 2 * mpmath.pi * mpmath.mpf(float(u2))
+        ref = r * (mpmath.cos(ang) if lane % 2 == 0 else mpmath.sin(ang))
+        assert abs(float(z[e]) - float(ref)) <= 1e-6 * max(1.0, abs(float(ref)))
+
+
+def test_gaussian_f32_statistics_and_agreement_with_f64_draws():
+    n = 1_000_000
+    z = rng.gaussian_f32(20260315, 0, 0, np.arange(n)).astype(np.float64)
+    assert abs(z.mean()) < 5 / np.sqrt(n)
+    assert abs(z.var() - 1) < 5 * np.sqrt(2 / n)
+    assert stats.kstest(z, "norm").pvalue > 1e-4
+    # u keeps 23 of the 52 bits of the float64 variant: the two draws agree to ~1e-7
+    # except where ln u1 is steep (u1 near 0), and never by more than the 2^-24 shift in u1
+    z64 = rng.gaussian(20260315, 0, 0, np.arange(n))
+    d = np.abs(z - z64)
+    assert np.median(d) < 5e-7
+    assert np.mean(d > 1e-4) < 1e-3
+    assert d.max() < 0.05
+
+
+def test_omega_bf16_is_rounded_f32_draws():
+    import torch
+    Ob = rng.omega(5, 2, 1, 7, 3, rounding="bf16")
+    z = rng.gaussian_f32(5, 2, 1, np.arange(21))
+    ref = torch.from_numpy(z).to(torch.bfloat16).to(torch.float64).numpy().reshape(7, 3, order="F")
+    np.testing.assert_array_equal(Ob, ref)
+    x = np.array([1 + 2.0 ** -8, 1 + 3 * 2.0 ** -8, -(1 + 2.0 ** -8)], dtype=np.float32)
+    np.testing.assert_array_equal(rng.round_bf16(x), [1.0, 1 + 4 * 2.0 ** -8, -1.0])
