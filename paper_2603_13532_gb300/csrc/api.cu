@@ -48,7 +48,7 @@ Operand op_abs(const void* p, size_t off_bytes = 0) {
 }
 
 enum StepKind { S_OMEGA, S_GEMM, S_REDUCE, S_CORESKETCH, S_QR, S_EIG, S_TC, S_SIMT, S_CS32, S_SPLIT,
-                S_TRANSPOSE, S_QR32, S_SVD32, S_TSQR, S_CS3, S_CHAIN3, S_QRSM };
+                S_TRANSPOSE, S_QR32, S_SVD32, S_TSQR, S_CS3, S_CHAIN3, S_QRSM, S_PROJ3 };
 
 struct Step {
   StepKind kind;
@@ -96,6 +96,7 @@ struct ProbHost {
   size_t om_plane[MAXD] = {}, UT[MAXD] = {}, M32[MAXD] = {}, Vp[MAXD][3] = {}, Qp[MAXD][3] = {};
   size_t AT32[MAXD] = {}, ATp[MAXD][3] = {}, Tp[3] = {};
   int ldU[MAXD] = {}, ldV[MAXD] = {}, ldA[MAXD] = {}, ldT = 0;
+  bool fused3 = false;   // mixed path: order 3 with b_2, b_3 <= 64 -> fused projection kernel
   size_t Wh = 0, tauh = 0, R32 = 0, P32[MAXD] = {}, sv[MAXD] = {};   // float32 ST-HOSVD
   size_t stk[2] = {};                                                 // TSQR stacked factors
   // backward of the core projection (order 3, float64)
@@ -410,6 +411,9 @@ static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
   size_t qrsm_smem = 0;
   std::vector<CoreSketchF32Job> cs3;
   std::vector<Chain3Job> ch3;
+  std::vector<Proj3Job> p3;
+  std::vector<Proj3Term> p3terms;
+  double p3_flops = 0.0, p3_bytes = 0.0;
   size_t cs3_smem = 0, ch3_smem = 0;
   double cs3_flops = 0.0, ch3_flops = 0.0;
   constexpr size_t kSmemCap = 200 * 1024;
@@ -593,11 +597,48 @@ static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
       a6.epi.f32 = op(B_WS, h.AT32[n]);
       a6.epi.f32_m = 1;
       a6.epi.f32_n = h.R[n];
-      a6.epi.nbf = 3;
-      for (int t = 0; t < 3; ++t) a6.epi.bf[t] = op(B_WS, h.ATp[n][t]);
-      a6.epi.bf_m = 1;
-      a6.epi.bf_n = h.ldA[n];
+      if (n == d - 1 && !h.fused3) {
+        a6.epi.nbf = 3;
+        for (int t = 0; t < 3; ++t) a6.epi.bf[t] = op(B_WS, h.ATp[n][t]);
+        a6.epi.bf_m = 1;
+        a6.epi.bf_n = h.ldA[n];
+      }
       tcA.push_back(a6);
+    }
+    if (h.fused3) {
+      // (c2 + c3) fused: one CTA per kProj3Rows mode-1 rows of H
+      const int tb = (int)p3terms.size();
+      for (int k = 0; k < h.K; ++k) {
+        const int* r = &h.ranks[(size_t)k * d];
+        Proj3Term t;
+        std::memset(&t, 0, sizeof(t));
+        t.core = op_abs(h.cores, (size_t)h.core_off[k] * 2);
+        for (int q = 0; q < 3; ++q) {
+          t.r[q] = r[q];
+          t.roff[q] = h.roff[(size_t)k * d + q];
+        }
+        t.alpha = (float)h.alpha[k];
+        p3terms.push_back(t);
+        p3_flops += 2.0 * h.b[0] * ((double)r[0] * r[1] * r[2] + (double)h.b[1] * r[1] * r[2] +
+                                    (double)h.b[1] * h.b[2] * r[2]);
+      }
+      for (int x0 = 0; x0 < h.b[0]; x0 += kProj3Rows) {
+        Proj3Job j;
+        std::memset(&j, 0, sizeof(j));
+        for (int q = 0; q < 3; ++q) {
+          j.AT[q] = op(B_WS, h.AT32[q]);
+          j.R[q] = h.R[q];
+          j.b[q] = h.b[q];
+        }
+        j.H = op(B_H, h.h_off * 8);
+        j.x0 = x0;
+        j.rows = std::min(kProj3Rows, h.b[0] - x0);
+        j.term_begin = tb;
+        j.nterms = h.K;
+        p3.push_back(j);
+      }
+      p3_bytes += 8.0 * (double)h.b[0] * h.b[1] * h.b[2];
+      continue;
     }
     // (c2) chains in float32; A_t^T block of term k: element (j, i) at (roff + i) + R_t j
     for (int k = 0; k < h.K; ++k) {
@@ -715,6 +756,16 @@ static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
     plan->st_project.back().smem = ch3_smem;
   }
   plan->push_tc(plan->st_project, tcH, "a8:H=Tcat.AT[tc]");
+  if (!p3.empty()) {
+    // one table: the jobs, then the term records they index
+    std::vector<char> blob(p3.size() * sizeof(Proj3Job) + p3terms.size() * sizeof(Proj3Term));
+    std::memcpy(blob.data(), p3.data(), p3.size() * sizeof(Proj3Job));
+    if (!p3terms.empty())
+      std::memcpy(blob.data() + p3.size() * sizeof(Proj3Job), p3terms.data(), p3terms.size() * sizeof(Proj3Term));
+    plan->st_project.push_back(make_step(S_PROJ3, plan->add_table(blob.data(), blob.size()), (int)p3.size(),
+                                         (int64_t)p3.size(), "a7:project3[f32]", p3_flops, p3_bytes));
+    plan->st_project.back().smem = proj3_smem_bytes();
+  }
   plan->st_recompress = plan->st_sketch;
   plan->push(plan->st_recompress, S_QR, qr, (int64_t)qr.size(), "a5:qr", qr_flops, qr_bytes);
   plan->push(plan->st_recompress, S_QR32, qr32, (int64_t)qr32.size(), "a5:qr[f32]", qr_flops, qr_bytes);
@@ -1059,14 +1110,18 @@ tks_status tks_plan_create(tks_plan** out, const tks_problem* problems, int32_t 
         for (int t = 0; t < 3; ++t) h.Vp[m][t] = alloc((size_t)h.ldV[m] * h.S[m] * 2);
         for (int t = 0; t < 3; ++t) h.Qp[m][t] = alloc((size_t)h.n[m] * h.b[m] * 2);
         h.AT32[m] = alloc((size_t)h.R[m] * h.b[m] * 4);
-        for (int t = 0; t < 3; ++t) h.ATp[m][t] = alloc((size_t)h.ldA[m] * h.b[m] * 2);
       }
     }
     if (!mixed) {
       h.T = alloc((size_t)h.R[d - 1] * Pd * 8);
     } else {
-      h.ldT = r8(h.R[d - 1]);
-      for (int t = 0; t < 3; ++t) h.Tp[t] = alloc((size_t)h.ldT * Pd * 2);
+      h.fused3 = d == 3 && h.b[1] <= 64 && h.b[2] <= 64;
+      if (!h.fused3) {
+        // planes of A_d^T and of Tcat for the last-mode tensor-core product
+        for (int t = 0; t < 3; ++t) h.ATp[d - 1][t] = alloc((size_t)h.ldA[d - 1] * h.b[d - 1] * 2);
+        h.ldT = r8(h.R[d - 1]);
+        for (int t = 0; t < 3; ++t) h.Tp[t] = alloc((size_t)h.ldT * Pd * 2);
+      }
     }
     h.chain.resize((size_t)2 * h.K);
     for (int k = 0; k < h.K; ++k) {
@@ -1348,6 +1403,7 @@ tks_status tks_plan_create(tks_plan** out, const tks_problem* problems, int32_t 
   if (mixed) {
     cudaError_t e = prepare_tc_gemm();
     if (e == cudaSuccess) e = prepare_order3_kernels();
+    if (e == cudaSuccess) e = prepare_proj3();
     if (e != cudaSuccess) {
       tks_plan_destroy(plan);
       return fail(TKS_ECUDA, std::string("tensor-core GEMM shared memory: ") + cudaGetErrorString(e));
@@ -1486,6 +1542,9 @@ tks_status run_steps(tks_plan* plan, const std::vector<Step>& steps, const Bases
         break;
       case S_CHAIN3:
         launch_chain3(static_cast<const Chain3Job*>(table), s.njobs, s.smem, bases, stream);
+        break;
+      case S_PROJ3:
+        launch_proj3(static_cast<const Proj3Job*>(table), s.njobs, bases, stream);
         break;
     }
   }

@@ -42,6 +42,10 @@ cudaError_t prepare_order3_kernels();
 void launch_core_sketch_krp3(const CoreSketchF32Job* jobs, int njobs, size_t smem, const Bases& bases,
                              cudaStream_t stream);
 void launch_chain3(const Chain3Job* jobs, int njobs, size_t smem, const Bases& bases, cudaStream_t stream);
+// Fused order-3 projection; `jobs` is followed in memory by the Proj3Term records.
+size_t proj3_smem_bytes();
+cudaError_t prepare_proj3();
+void launch_proj3(const Proj3Job* jobs, int njobs, const Bases& bases, cudaStream_t stream);
 void launch_split_f64(const SplitJob* jobs, int njobs, int64_t total, const Bases& bases, cudaStream_t stream);
 void launch_transpose_bf16(const TransposeJob* jobs, int njobs, int total_tiles, const Bases& bases,
                            cudaStream_t stream);

@@ -74,7 +74,7 @@ struct OmegaJob {
   int64_t count;       // n * s
   int64_t begin;       // prefix over jobs (elements)
   int32_t problem, mode;
-  int32_t bf16;        // round to float32 then bfloat16
+  int32_t bf16;        // float32 draws (gaussian4_f32) rounded to bfloat16
   int32_t has_plane;
 };
 
@@ -113,6 +113,29 @@ struct CoreSketchF32Job {
   int64_t count;
   int64_t begin;
 };
+
+// Fused order-3 projection (stage c, float32): one CTA per (problem, kProj3Rows mode-1 rows of H),
+// requires b_2, b_3 <= 64.  The job table is followed by the Proj3Term records of all problems;
+// job j reads terms [term_begin, term_begin + nterms) of that array.
+constexpr int kProj3Rows = 4;
+
+struct Proj3Term {
+  Operand core;          // bf16 core of the term, mode-1 fastest
+  int32_t r[3];          // term ranks
+  int32_t roff[3];       // first row of the term in A_n^T
+  float alpha;           // term weight
+  int32_t pad;
+};
+
+struct Proj3Job {
+  Operand AT[3];         // float32 A_n^T = (Q_n^T Ucat_n)^T: element (i, a) at i + R_n a
+  Operand H;             // float64 H, element (a0, a1, a2) at a0 + b0 (a1 + b1 a2)
+  int32_t R[3], b[3];
+  int32_t x0, rows;      // mode-1 rows [x0, x0 + rows), rows <= kProj3Rows
+  int32_t term_begin, nterms;
+  int32_t pad[6];
+};
+static_assert(sizeof(Proj3Job) % 16 == 0 && sizeof(Proj3Term) % 16 == 0, "term records follow the jobs");
 
 // Order-3 chain of one term for rows [a0, a0 + AB) of mode 1 (stage c2, float32):
 //   T[a0, a1, c] = alpha sum_{i0, i1} A1[a0, i0] A2[a1, i1] G[i0, i1, c]

@@ -103,6 +103,28 @@ def test_mixed_projection_matches_oracle_given_q(cuda_lib, kind, d):
         assert _rel(H, r["H"]) <= 1e-5
 
 
+@pytest.mark.parametrize("kind", ["krp", "kron"])
+def test_mixed_projection_order3_tile_edges(cuda_lib, kind):
+    """Order-3 projection at the edges of the fused kernel's tiling: b_1 = 21 (not a multiple of
+    its 4-row blocks), core slices split into several mode-3 chunks (r_1 r_2 = 1920 > 1024),
+    rank-1 terms, and a problem whose b_3 > 64 takes the tensor-core path for the last mode."""
+    g = np.random.default_rng(77)
+    specs = [([56, 48, 40], [[48, 40, 37], [1, 1, 1], [5, 33, 17]], [10, 15, 8], [3, 6, 3]),
+             ([72, 64, 80], [[8, 8, 8], [20, 3, 30]], [60, 56, 62], [6, 6, 6])]
+    probs = []
+    for dims, ranks, target, over in specs:
+        cores = [g.standard_normal(r) for r in ranks]
+        facs = [[g.standard_normal((n, ri)) for n, ri in zip(dims, r)] for r in ranks]
+        probs.append(wl.Problem(dims, cores, facs, target, over, alpha=list(g.standard_normal(len(ranks)))))
+    probs = wl._finish(probs, True)
+    plan = _plan(probs, kind, 8)
+    refs = [_oracle(p, kind, 8, i) for i, p in enumerate(probs)]
+    Hs = plan.project([r["Q"] for r in refs])
+    for H, r in zip(Hs, refs):
+        assert H.shape == r["H"].shape
+        assert _rel(H, r["H"]) <= 1e-5, _rel(H, r["H"])
+
+
 @pytest.mark.parametrize("precision", MODES)
 @pytest.mark.parametrize("kind", ["kron", "krp"])
 def test_mixed_recompress_small(cuda_lib, kind, precision):
