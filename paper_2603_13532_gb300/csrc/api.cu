@@ -48,7 +48,7 @@ Operand op_abs(const void* p, size_t off_bytes = 0) {
 }
 
 enum StepKind { S_OMEGA, S_GEMM, S_REDUCE, S_CORESKETCH, S_QR, S_EIG, S_TC, S_SIMT, S_CS32, S_SPLIT,
-                S_TRANSPOSE, S_QR32, S_SVD32, S_TSQR, S_CS3, S_CHAIN3, S_QRSM, S_PROJ3 };
+                S_TRANSPOSE, S_QR32, S_SVD32, S_TSQR, S_CS3, S_CHAIN3, S_QRSM, S_PROJ3, S_SK3 };
 
 struct Step {
   StepKind kind;
@@ -411,6 +411,9 @@ static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
   size_t qrsm_smem = 0;
   std::vector<CoreSketchF32Job> cs3;
   std::vector<Chain3Job> ch3;
+  std::vector<Sketch3Job> sk3;
+  size_t sk3_smem = 0;
+  double sk3_flops = 0.0;
   std::vector<Proj3Job> p3;
   std::vector<Proj3Term> p3terms;
   double p3_flops = 0.0, p3_bytes = 0.0;
@@ -479,6 +482,28 @@ static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
       tcM.push_back(a2);
     }
     for (int k = 0; k < h.K; ++k) {
+      if (d == 3 && !kron && h.s[0] <= 64) {
+        const int* r = &h.ranks[(size_t)k * d];
+        if (r[0] <= kSketch3MaxRank && r[1] <= kSketch3MaxRank && r[2] <= kSketch3MaxRank) {
+          Sketch3Job j;
+          std::memset(&j, 0, sizeof(j));
+          j.core = op_abs(h.cores, (size_t)h.core_off[k] * 2);
+          for (int m = 0; m < 3; ++m) {
+            j.M[m] = op(B_WS, h.M32[m]);
+            for (int t = 0; t < 3; ++t) j.V[m][t] = op(B_WS, h.Vp[m][t]);
+            j.r[m] = r[m];
+            j.roff[m] = h.roff[(size_t)k * d + m];
+            j.R[m] = h.R[m];
+            j.ldv[m] = h.ldV[m];
+          }
+          j.s = h.s[0];
+          j.alpha = (float)h.alpha[k];
+          sk3.push_back(j);
+          sk3_smem = std::max(sk3_smem, sketch3_smem_bytes(r));
+          sk3_flops += 2.0 * h.s[0] * (2.0 * r[0] * r[1] * r[2] + 2.0 * r[0] * r[1] + (double)r[1] * r[2]);
+          continue;
+        }
+      }
       for (int n = 0; n < d; ++n) {
         CoreSketchF32Job j;
         std::memset(&j, 0, sizeof(j));
@@ -742,6 +767,10 @@ static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
   if (!cs3.empty()) {
     plan->push(plan->st_sketch, S_CS3, cs3, (int64_t)cs3.size(), "a3:core_sketch3[f32]", cs3_flops, 0.0);
     plan->st_sketch.back().smem = cs3_smem;
+  }
+  if (!sk3.empty()) {
+    plan->push(plan->st_sketch, S_SK3, sk3, (int64_t)sk3.size(), "a3:sketch3[f32]", sk3_flops, 0.0);
+    plan->st_sketch.back().smem = sk3_smem;
   }
   plan->push_tc(plan->st_sketch, tcY, "a4:Y=Ucat.Vcat[tc]");
   plan->push(plan->st_project, S_SPLIT, sp, sp_total, "a6:Q->planes", 0.0, 14.0 * sp_total);
@@ -1404,6 +1433,7 @@ tks_status tks_plan_create(tks_plan** out, const tks_problem* problems, int32_t 
     cudaError_t e = prepare_tc_gemm();
     if (e == cudaSuccess) e = prepare_order3_kernels();
     if (e == cudaSuccess) e = prepare_proj3();
+    if (e == cudaSuccess) e = prepare_sketch3();
     if (e != cudaSuccess) {
       tks_plan_destroy(plan);
       return fail(TKS_ECUDA, std::string("tensor-core GEMM shared memory: ") + cudaGetErrorString(e));
@@ -1542,6 +1572,9 @@ tks_status run_steps(tks_plan* plan, const std::vector<Step>& steps, const Bases
         break;
       case S_CHAIN3:
         launch_chain3(static_cast<const Chain3Job*>(table), s.njobs, s.smem, bases, stream);
+        break;
+      case S_SK3:
+        launch_sketch3(static_cast<const Sketch3Job*>(table), s.njobs, s.smem, bases, stream);
         break;
       case S_PROJ3:
         launch_proj3(static_cast<const Proj3Job*>(table), s.njobs, bases, stream);

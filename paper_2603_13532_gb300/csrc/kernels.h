@@ -42,6 +42,10 @@ cudaError_t prepare_order3_kernels();
 void launch_core_sketch_krp3(const CoreSketchF32Job* jobs, int njobs, size_t smem, const Bases& bases,
                              cudaStream_t stream);
 void launch_chain3(const Chain3Job* jobs, int njobs, size_t smem, const Bases& bases, cudaStream_t stream);
+// Khatri-Rao core sketches of order-3 terms, one CTA per term.
+size_t sketch3_smem_bytes(const int r[3]);
+cudaError_t prepare_sketch3();
+void launch_sketch3(const Sketch3Job* jobs, int njobs, size_t smem, const Bases& bases, cudaStream_t stream);
 // Fused order-3 projection; `jobs` is followed in memory by the Proj3Term records.
 size_t proj3_smem_bytes();
 cudaError_t prepare_proj3();

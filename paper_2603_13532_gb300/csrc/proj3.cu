@@ -13,6 +13,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include "bf16.cuh"
 #include "kernels.h"
 
 namespace tks {
@@ -27,8 +28,6 @@ constexpr int kGBuf = kGElems + 16;  // + room for the 16-byte realignment of th
 constexpr int kM = kRows * kPad;     // rows (a2, x) of the register block
 constexpr int kThreads = 256;
 constexpr int kR = TKS_MAX_RANK;
-
-__device__ __forceinline__ float bf16_float(uint16_t h) { return __bfloat162float(__ushort_as_bfloat16(h)); }
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));

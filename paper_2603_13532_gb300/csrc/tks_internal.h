@@ -114,6 +114,20 @@ struct CoreSketchF32Job {
   int64_t begin;
 };
 
+// Khatri-Rao core sketches of all three modes of one order-3 term (stage b, float32), one CTA per
+// term; requires s <= 64 and ranks <= kSketch3MaxRank.
+constexpr int kSketch3MaxRank = 32;
+
+struct Sketch3Job {
+  Operand core;          // bf16 core, mode-1 fastest
+  Operand M[3];          // float32 M_m = Ucat_m^T Omega_m: element (i, c) at i + R_m c
+  Operand V[3][3];       // bf16 planes of Vcat_n: element (i, c) at i + ldv_n c
+  int32_t r[3], roff[3], R[3], ldv[3];
+  int32_t s;
+  float alpha;
+  int32_t pad[2];
+};
+
 // Fused order-3 projection (stage c, float32): one CTA per (problem, kProj3Rows mode-1 rows of H),
 // requires b_2, b_3 <= 64.  The job table is followed by the Proj3Term records of all problems;
 // job j reads terms [term_begin, term_begin + nterms) of that array.

@@ -103,6 +103,28 @@ def test_mixed_projection_matches_oracle_given_q(cuda_lib, kind, d):
         assert _rel(H, r["H"]) <= 1e-5
 
 
+def test_mixed_krp_sketch_order3_term_kernel_edges(cuda_lib):
+    """Khatri-Rao sketches of order-3 terms at the edges of the per-term kernel: ranks 1, 3 (not a
+    multiple of its 4-wide loads), 32 (its limit) and 33 (per-mode fallback) in one problem with
+    s = 64 (its column limit), and a problem with s = 66 that takes the per-mode kernels."""
+    g = np.random.default_rng(78)
+    specs = [([64, 72, 80], [[1, 1, 1], [3, 5, 7], [32, 32, 32], [33, 9, 4], [12, 32, 30]], [56, 60, 50], [8, 4, 8]),
+             ([72, 72, 72], [[6, 7, 8], [20, 3, 11]], [60, 60, 60], [6, 6, 6])]
+    probs = []
+    for dims, ranks, target, over in specs:
+        cores = [g.standard_normal(r) for r in ranks]
+        facs = [[g.standard_normal((n, ri)) for n, ri in zip(dims, r)] for r in ranks]
+        probs.append(wl.Problem(dims, cores, facs, target, over, alpha=list(g.standard_normal(len(ranks)))))
+    probs = wl._finish(probs, True)
+    plan = _plan(probs, "krp", 9)
+    assert [pi.sketch_cols[0] for pi in plan.pinfo] == [64, 66]
+    Ys = plan.sketch()
+    for i, prob in enumerate(probs):
+        ref = _oracle(prob, "krp", 9, i)
+        for m in range(3):
+            assert _rel(Ys[i][m], ref["Y"][m]) <= 1e-5, (i, m, _rel(Ys[i][m], ref["Y"][m]))
+
+
 @pytest.mark.parametrize("kind", ["krp", "kron"])
 def test_mixed_projection_order3_tile_edges(cuda_lib, kind):
     """Order-3 projection at the edges of the fused kernel's tiling: b_1 = 21 (not a multiple of
