@@ -31,6 +31,9 @@ __device__ float block_sum_f(float v, float* red) {
   return s;
 }
 
+constexpr int kLoadBatch = 8;   // global loads in flight per thread when staging a block
+constexpr int kTsqrMaxRows = 256;   // rows of one TSQR block (at most; the planner uses 256)
+
 __device__ __forceinline__ float load_any(const char* base, int32_t type, int64_t idx) {
   if (type == T_F64) return (float)reinterpret_cast<const double*>(base)[idx];
   if (type == T_F32) return reinterpret_cast<const float*>(base)[idx];
@@ -148,8 +151,6 @@ __global__ void __launch_bounds__(512) qr_f32_kernel(const QrF32Job* __restrict_
 __global__ void __launch_bounds__(1024) qr_smem_f32_kernel(const QrF32Job* __restrict__ jobs, Bases bases,
                                                            Status* status) {
   extern __shared__ float sq[];
-  __shared__ float red[32];
-  __shared__ float sh_tau, sh_scale;
   __shared__ int sh_bad;
   const QrF32Job& J = jobs[blockIdx.x];
   const int n = (int)J.rows, S = (int)J.cols, b = J.b;
@@ -157,73 +158,97 @@ __global__ void __launch_bounds__(1024) qr_smem_f32_kernel(const QrF32Job* __res
   float* tau = W + (size_t)n * S;
   float* rdiag = tau + S;
   const char* src = at<char>(bases, J.src);
-  for (int e = threadIdx.x; e < n * S; e += blockDim.x) {
-    const int j = e / n, i = e - j * n;
-    const int64_t i1 = i / J.L0, i0 = i - i1 * J.L0;
-    W[e] = load_any(src, J.src_type, i0 * J.s0 + i1 * J.s1 + j * J.sc);
+  const uint32_t L0 = (uint32_t)J.L0;
+  for (int e0 = 0; e0 < n * S; e0 += kLoadBatch * (int)blockDim.x) {
+    float v[kLoadBatch];
+#pragma unroll
+    for (int u = 0; u < kLoadBatch; ++u) {
+      const int e = e0 + u * blockDim.x + threadIdx.x;
+      v[u] = 0.f;
+      if (e < n * S) {
+        const int j = e / n, i = e - j * n;
+        const uint32_t i1 = (uint32_t)i / L0, i0 = (uint32_t)i - i1 * L0;
+        v[u] = load_any(src, J.src_type, (int64_t)i0 * J.s0 + (int64_t)i1 * J.s1 + (int64_t)j * J.sc);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kLoadBatch; ++u) {
+      const int e = e0 + u * blockDim.x + threadIdx.x;
+      if (e < n * S) W[e] = v[u];
+    }
   }
   if (threadIdx.x == 0) sh_bad = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  // reflectors stay unscaled (x below the diagonal, v = (1, x / (alpha - beta))); the warp that
+  // updates column j + 1 also returns its new tail norm, so each column costs one barrier
+  float* vscale = rdiag + S;
+  __shared__ float sh_tail[2];
+  if (warp == 0) {
+    float t = 0.f;
+    for (int i = 1 + lane; i < n; i += 32) t = fmaf(W[i], W[i], t);
+    t = warp_sum_f(t);
+    if (lane == 0) sh_tail[0] = t;
+  }
+  __syncthreads();
   for (int j = 0; j < b; ++j) {
-    float* wj = W + (size_t)n * j;
-    float part = 0.f;
-    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) part = fmaf(wj[i], wj[i], part);
-    const float tail2 = block_sum_f(part, red);
+    const float* wj = W + (size_t)n * j;
+    const float alpha = wj[j];
+    const float tail2 = sh_tail[j & 1];
+    const float nrm = sqrtf(fmaf(alpha, alpha, tail2));
+    const bool reflect = tail2 > 0.f && isfinite(nrm);
+    const float beta = alpha >= 0.f ? -nrm : nrm;
+    const float t = reflect ? (beta - alpha) / beta : 0.f;
+    const float sc = reflect ? 1.f / (alpha - beta) : 0.f;
     if (threadIdx.x == 0) {
-      const float alpha = wj[j];
-      const float nrm = sqrtf(fmaf(alpha, alpha, tail2));
       if (!isfinite(nrm)) sh_bad = 1;
-      if (tail2 == 0.f || !isfinite(nrm)) {
-        sh_tau = 0.f;
-        sh_scale = 0.f;
-        rdiag[j] = alpha;
-      } else {
-        const float beta = (alpha >= 0.f) ? -nrm : nrm;
-        sh_tau = (beta - alpha) / beta;
-        sh_scale = 1.f / (alpha - beta);
-        rdiag[j] = beta;
-      }
-      tau[j] = sh_tau;
+      rdiag[j] = reflect ? beta : alpha;
+      tau[j] = t;
+      vscale[j] = sc;
     }
-    __syncthreads();
-    const float t = sh_tau;
-    if (t != 0.f) {
-      const float sc = sh_scale;
-      for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) wj[i] *= sc;
-      __syncthreads();
-      for (int l = j + 1 + warp; l < b; l += nw) {
-        float* wl = W + (size_t)n * l;
+    for (int l = j + 1 + warp; l < b; l += nw) {
+      float* wl = W + (size_t)n * l;
+      if (reflect) {
         float dot = 0.f;
         for (int i = j + 1 + lane; i < n; i += 32) dot = fmaf(wj[i], wl[i], dot);
-        dot = warp_sum_f(dot) + wl[j];
+        dot = fmaf(warp_sum_f(dot), sc, wl[j]);
         const float w = t * dot;
         if (lane == 0) wl[j] -= w;
-        for (int i = j + 1 + lane; i < n; i += 32) wl[i] = fmaf(-w, wj[i], wl[i]);
+        const float ws = w * sc;
+        for (int i = j + 1 + lane; i < n; i += 32) wl[i] = fmaf(-ws, wj[i], wl[i]);
+      }
+      if (l == j + 1) {
+        __syncwarp();   // the column's update by other lanes is visible
+        float tt = 0.f;
+        for (int i = j + 2 + lane; i < n; i += 32) tt = fmaf(wl[i], wl[i], tt);
+        tt = warp_sum_f(tt);
+        if (lane == 0) sh_tail[(j + 1) & 1] = tt;
       }
     }
     __syncthreads();
   }
-  // explicit Q in place (columns 0..b-1)
+  // explicit Q in place (columns 0..b-1), v_j = (1, vscale_j x_j)
   for (int j = b - 1; j >= 0; --j) {
-    const float t = tau[j];
+    const float t = tau[j], sc = vscale[j];
     float* wj = W + (size_t)n * j;
     if (t != 0.f) {
       for (int l = j + 1 + warp; l < b; l += nw) {
         float* wl = W + (size_t)n * l;
         float dot = 0.f;
         for (int i = j + 1 + lane; i < n; i += 32) dot = fmaf(wj[i], wl[i], dot);
-        dot = warp_sum_f(dot) + wl[j];
+        dot = fmaf(warp_sum_f(dot), sc, wl[j]);
         const float w = t * dot;
         if (lane == 0) wl[j] -= w;
-        for (int i = j + 1 + lane; i < n; i += 32) wl[i] = fmaf(-w, wj[i], wl[i]);
+        const float ws = w * sc;
+        for (int i = j + 1 + lane; i < n; i += 32) wl[i] = fmaf(-ws, wj[i], wl[i]);
       }
     }
     __syncthreads();
+    const float tv = t * sc;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       if (i < j) wj[i] = 0.f;
       else if (i == j) wj[i] = 1.f - t;
-      else wj[i] = -t * wj[i];
+      else wj[i] = -tv * wj[i];
     }
     __syncthreads();
   }
@@ -237,75 +262,154 @@ __global__ void __launch_bounds__(1024) qr_smem_f32_kernel(const QrF32Job* __res
 }
 
 // ----------------------------------------------------------------------------- TSQR block
-// Householder QR of a rows x cols block held in shared memory (column-major, ld = rows + 1),
-// one thread block; only the triangular factor is kept.
-__global__ void __launch_bounds__(512) tsqr_f32_kernel(const TsqrJob* __restrict__ jobs, Bases bases) {
+// Householder QR of a rows x cols block (rows <= 256, cols <= 32 kSlots), only the triangular
+// factor kept.  The block is staged through shared memory once and then lives in registers:
+// column l belongs to warp l % 16 (slot l / 16), lane L holds rows L + 32 u, u < 8.  Step j
+// reads the published reflector v_j = (0, .., 0, 1, x / (alpha - beta)) and tau_j from shared
+// memory; every warp updates its columns l > j in registers (a_l -= tau v (v^T a_l), one warp
+// reduction per column), and the warp owning column j + 1 then forms that column's reflector
+// and publishes it, so each column costs one barrier and no shared-memory traffic for the
+// trailing matrix.
+constexpr int kTsqrThreads = 512;
+constexpr int kTsqrWarps = kTsqrThreads / 32;
+constexpr int kTsqrRowsPerLane = kTsqrMaxRows / 32;
+
+// Forms the reflector of column c (owned by this warp, values a[u] at rows lane + 32 u) below
+// row c and publishes v, tau and the diagonal entry of R.
+__device__ __forceinline__ void tsqr_publish(const float (&a)[kTsqrRowsPerLane], int c, int m, float* v_out,
+                                             float* tau_out, float* rdiag) {
+  const int lane = threadIdx.x & 31;
+  float t2 = 0.f, alpha = 0.f;
+#pragma unroll
+  for (int u = 0; u < kTsqrRowsPerLane; ++u) {
+    const int i = lane + 32 * u;
+    if (i > c && i < m) t2 = fmaf(a[u], a[u], t2);
+    if (i == c) alpha = a[u];
+  }
+  t2 = warp_sum_f(t2);
+  alpha = __shfl_sync(0xffffffffu, alpha, c & 31);
+  const float nrm = sqrtf(fmaf(alpha, alpha, t2));
+  const bool reflect = t2 > 0.f && isfinite(nrm);
+  const float beta = alpha >= 0.f ? -nrm : nrm;
+  const float tau = reflect ? (beta - alpha) / beta : 0.f;
+  const float sc = reflect ? 1.f / (alpha - beta) : 0.f;
+#pragma unroll
+  for (int u = 0; u < kTsqrRowsPerLane; ++u) {
+    const int i = lane + 32 * u;
+    v_out[i] = i < c ? 0.f : (i == c ? 1.f : (i < m ? sc * a[u] : 0.f));
+  }
+  if (lane == 0) {
+    *tau_out = tau;
+    rdiag[c] = reflect ? beta : alpha;
+  }
+}
+
+template <int kSlots>
+__global__ void __launch_bounds__(kTsqrThreads, kSlots <= 4 ? 2 : 1) tsqr_f32_kernel(const TsqrJob* __restrict__ jobs, Bases bases) {
   extern __shared__ float smem_t[];
-  __shared__ float red[32];
-  __shared__ float sh_tau, sh_scale;
+  __shared__ float vbuf[2][kTsqrMaxRows];
+  __shared__ float sh_tau[2];
+  __shared__ float rdiag[32 * kSlots];
+  __shared__ int64_t rowoff[kTsqrMaxRows];
   const TsqrJob& J = jobs[blockIdx.x];
   const int m = J.rows, b = J.cols;
   const int ld = m + 1;
   float* A = smem_t;
   const char* src = at<char>(bases, J.src);
-  for (int e = threadIdx.x; e < m * b; e += blockDim.x) {
-    const int c = e / m, r = e - c * m;
-    const int64_t i = J.row_begin + r;
-    const int64_t i1 = i / J.L0, i0 = i - i1 * J.L0;
-    A[r + ld * c] = load_any(src, J.src_type, i0 * J.s0 + i1 * J.s1 + c * J.sc);
+  // source offset of each row of the block (row index i = (i0, i1) with i0 fastest)
+  for (int r = threadIdx.x; r < m; r += blockDim.x) {
+    const uint64_t i = (uint64_t)(J.row_begin + r), L0 = (uint64_t)J.L0;
+    const uint64_t i1 = i / L0, i0 = i - i1 * L0;
+    rowoff[r] = (int64_t)i0 * J.s0 + (int64_t)i1 * J.s1;
   }
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int kmax = m < b ? m : b;
-  for (int j = 0; j < kmax; ++j) {
-    float* aj = A + ld * j;
-    float part = 0.f;
-    for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) part = fmaf(aj[i], aj[i], part);
-    const float tail2 = block_sum_f(part, red);
-    if (threadIdx.x == 0) {
-      const float alpha = aj[j];
-      const float nrm = sqrtf(fmaf(alpha, alpha, tail2));
-      if (tail2 == 0.f || !isfinite(nrm)) {
-        sh_tau = 0.f;
-        sh_scale = 0.f;
-      } else {
-        const float beta = (alpha >= 0.f) ? -nrm : nrm;
-        sh_tau = (beta - alpha) / beta;
-        sh_scale = 1.f / (alpha - beta);
-        aj[j] = beta;
+  // stage: columns fastest when a row is contiguous in the source, else rows; kLoadBatch loads
+  // in flight per thread before the shared-memory stores
+  const bool row_major = J.sc == 1;
+  const int mb = m * b;
+  for (int e0 = 0; e0 < mb; e0 += kLoadBatch * kTsqrThreads) {
+    float v[kLoadBatch];
+    int dst[kLoadBatch];
+#pragma unroll
+    for (int u = 0; u < kLoadBatch; ++u) {
+      const int e = e0 + u * kTsqrThreads + threadIdx.x;
+      v[u] = 0.f;
+      dst[u] = -1;
+      if (e < mb) {
+        const int q = row_major ? e / b : e / m;
+        const int r = row_major ? q : e - q * m, c = row_major ? e - q * b : q;
+        v[u] = load_any(src, J.src_type, rowoff[r] + (int64_t)c * J.sc);
+        dst[u] = r + ld * c;
       }
     }
-    __syncthreads();
-    const float t = sh_tau;
-    if (t != 0.f) {
-      const float sc = sh_scale;
-      for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) aj[i] *= sc;
-      __syncthreads();
-      for (int l = j + 1 + warp; l < b; l += nw) {
-        float* al = A + ld * l;
-        float dot = 0.f;
-        for (int i = j + 1 + lane; i < m; i += 32) dot = fmaf(aj[i], al[i], dot);
-        dot = warp_sum_f(dot) + al[j];
-        const float w = t * dot;
-        if (lane == 0) al[j] -= w;
-        for (int i = j + 1 + lane; i < m; i += 32) al[i] = fmaf(-w, aj[i], al[i]);
+#pragma unroll
+    for (int u = 0; u < kLoadBatch; ++u)
+      if (dst[u] >= 0) A[dst[u]] = v[u];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float a[kSlots][kTsqrRowsPerLane];
+#pragma unroll
+  for (int sl = 0; sl < kSlots; ++sl) {
+    const int l = warp + kTsqrWarps * sl;
+#pragma unroll
+    for (int u = 0; u < kTsqrRowsPerLane; ++u) {
+      const int i = lane + 32 * u;
+      a[sl][u] = (l < b && i < m) ? A[i + ld * l] : 0.f;
+    }
+  }
+  const int kmax = m < b ? m : b;
+  if (warp == 0 && kmax > 0) tsqr_publish(a[0], 0, m, vbuf[0], &sh_tau[0], rdiag);
+  __syncthreads();
+  for (int j = 0; j < kmax; ++j) {
+    const float tau = sh_tau[j & 1];
+    float vj[kTsqrRowsPerLane];
+#pragma unroll
+    for (int u = 0; u < kTsqrRowsPerLane; ++u) vj[u] = vbuf[j & 1][lane + 32 * u];
+#pragma unroll
+    for (int sl = 0; sl < kSlots; ++sl) {
+      const int l = warp + kTsqrWarps * sl;
+      if (l > j && l < b) {
+        if (tau != 0.f) {
+          float dot = 0.f;
+#pragma unroll
+          for (int u = 0; u < kTsqrRowsPerLane; ++u) dot = fmaf(vj[u], a[sl][u], dot);
+          const float w = tau * warp_sum_f(dot);
+#pragma unroll
+          for (int u = 0; u < kTsqrRowsPerLane; ++u) a[sl][u] = fmaf(-w, vj[u], a[sl][u]);
+        }
+        if (l == j + 1 && l < kmax) tsqr_publish(a[sl], l, m, vbuf[(j + 1) & 1], &sh_tau[(j + 1) & 1], rdiag);
       }
     }
     __syncthreads();
   }
+  // R: row r < c of column c from the owner's registers, the diagonal from rdiag, zeros below
   float* dst = at<float>(bases, J.dst);
-  for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
-    const int c = e / b, r = e - c * b;
-    dst[(J.dst_row0 + r) + J.dst_ld * c] = (r <= c && r < kmax) ? A[r + ld * c] : 0.f;
+#pragma unroll
+  for (int sl = 0; sl < kSlots; ++sl) {
+    const int c = warp + kTsqrWarps * sl;
+    if (c < b) {
+#pragma unroll
+      for (int u = 0; u < kTsqrRowsPerLane; ++u) {
+        const int r = lane + 32 * u;
+        if (r < b) {
+          float v = 0.f;
+          if (r < kmax && r <= c) v = (r == c) ? rdiag[r] : a[sl][u];
+          dst[(J.dst_row0 + r) + J.dst_ld * c] = v;
+        }
+      }
+    }
   }
 }
 
 // One-sided Jacobi on the columns of the b x b matrix A = R with the round-robin ordering:
-// each round rotates b/2 disjoint column pairs (one warp per pair) so that they become
+// each round rotates b/2 disjoint column pairs (kSvdLanes lanes per pair) so that they become
 // orthogonal; V accumulates the rotations.  At convergence A = U Sigma, R = U Sigma V^T.
 constexpr int kSvdSweeps = 30;
+constexpr int kSvdLanes = 8;      // lanes per column pair
+constexpr int kSvdThreads = 384;  // kSvdLanes x (TKS_MAX_BASIS / 2) pairs
 
-__global__ void __launch_bounds__(1024) svd_jacobi_f32_kernel(const SvdJob* __restrict__ jobs, Bases bases,
+__global__ void __launch_bounds__(kSvdThreads) svd_jacobi_f32_kernel(const SvdJob* __restrict__ jobs, Bases bases,
                                                               Status* status) {
   extern __shared__ float sm[];
   const SvdJob& J = jobs[blockIdx.x];
@@ -345,44 +449,68 @@ __global__ void __launch_bounds__(1024) svd_jacobi_f32_kernel(const SvdJob* __re
     __syncthreads();
   }
   const float noise2 = sh_noise2;
+  // a group of kSvdLanes lanes rotates one pair; pair k of a round is (round + k, round - k) mod
+  // (m - 1), pair 0 is (round, m - 1)
+  const int sub = lane % kSvdLanes;
+  const int k = (threadIdx.x / kSvdLanes);
+  const int pairs = m / 2;
   int sweep = 0;
   for (; sweep < kSvdSweeps; ++sweep) {
     if (threadIdx.x == 0) sh_rot = 0;
     __syncthreads();
+    int any = 0;
     for (int round = 0; round < m - 1; ++round) {
-      for (int k = warp; k < m / 2; k += nw) {
-        int p, q;
-        if (k == 0) { p = round; q = m - 1; }
-        else { p = (round + k) % (m - 1); q = (round - k + (m - 1)) % (m - 1); }
-        if (p > q) { const int t = p; p = q; q = t; }
-        if (q >= b) continue;
-        float al = 0.f, be = 0.f, ga = 0.f;
-        for (int i = lane; i < b; i += 32) {
-          const float x = A[i + p * ld], y = A[i + q * ld];
+      int p = 0, q = 0;
+      if (k == 0) {
+        p = round;
+        q = m - 1;
+      } else {
+        p = round + k;
+        if (p >= m - 1) p -= m - 1;
+        q = round - k;
+        if (q < 0) q += m - 1;
+      }
+      if (p > q) { const int t = p; p = q; q = t; }
+      const bool valid = k < pairs && q < b;
+      if (!valid) p = q = 0;
+      float* ap = A + p * ld;
+      float* aq = A + q * ld;
+      float al = 0.f, be = 0.f, ga = 0.f;
+      if (valid) {
+        for (int i = sub; i < b; i += kSvdLanes) {
+          const float x = ap[i], y = aq[i];
           al = fmaf(x, x, al);
           be = fmaf(y, y, be);
           ga = fmaf(x, y, ga);
         }
-        al = warp_sum_f(al);
-        be = warp_sum_f(be);
-        ga = warp_sum_f(ga);
-        if (fabsf(ga) > thr * sqrtf(al * be) && ga != 0.f && fminf(al, be) > noise2) {
-          const float zeta = (be - al) / (2.f * ga);
-          const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
-          const float c = 1.f / sqrtf(1.f + t * t), s = c * t;
-          for (int i = lane; i < b; i += 32) {
-            const float x = A[i + p * ld], y = A[i + q * ld];
-            A[i + p * ld] = c * x - s * y;
-            A[i + q * ld] = s * x + c * y;
-            const float vx = V[i + p * ld], vy = V[i + q * ld];
-            V[i + p * ld] = c * vx - s * vy;
-            V[i + q * ld] = s * vx + c * vy;
-          }
-          if (lane == 0) sh_rot = 1;
+      }
+      // every lane takes part in the group reductions
+#pragma unroll
+      for (int o = kSvdLanes / 2; o > 0; o >>= 1) {
+        al += __shfl_xor_sync(0xffffffffu, al, o, kSvdLanes);
+        be += __shfl_xor_sync(0xffffffffu, be, o, kSvdLanes);
+        ga += __shfl_xor_sync(0xffffffffu, ga, o, kSvdLanes);
+      }
+      if (valid && fabsf(ga) > thr * sqrtf(al * be) && ga != 0.f && fminf(al, be) > noise2) {
+        const float zeta = (be - al) / (2.f * ga);
+        const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+        const float c = 1.f / sqrtf(1.f + t * t), s = c * t;
+        float* vp = V + p * ld;
+        float* vq = V + q * ld;
+        for (int i = sub; i < b; i += kSvdLanes) {
+          const float x = ap[i], y = aq[i];
+          ap[i] = c * x - s * y;
+          aq[i] = s * x + c * y;
+          const float vx = vp[i], vy = vq[i];
+          vp[i] = c * vx - s * vy;
+          vq[i] = s * vx + c * vy;
         }
+        any = 1;
       }
       __syncthreads();
     }
+    if (any) sh_rot = 1;
+    __syncthreads();
     const int rot = sh_rot;
     __syncthreads();
     if (!rot) break;
@@ -465,10 +593,16 @@ size_t tsqr_smem(int rows, int cols) { return (size_t)(rows + 1) * cols * sizeof
 cudaError_t prepare_tsqr_f32() {
   cudaError_t e = cudaFuncSetAttribute(qr_smem_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 222 * 1024);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(tsqr_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 222 * 1024);
+  e = cudaFuncSetAttribute(tsqr_f32_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(tsqr_f32_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(tsqr_f32_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(tsqr_f32_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
 }
 
-size_t qr_smem_bytes(int64_t n, int S) { return (size_t)(n * S + 2 * S) * sizeof(float); }
+size_t qr_smem_bytes(int64_t n, int S) { return (size_t)(n * S + 3 * S) * sizeof(float); }
 
 void launch_qr_smem_f32(const QrF32Job* jobs, int njobs, size_t smem, const Bases& bases, Status* status,
                         cudaStream_t stream) {
@@ -477,7 +611,16 @@ void launch_qr_smem_f32(const QrF32Job* jobs, int njobs, size_t smem, const Base
 
 void launch_tsqr_f32(const TsqrJob* jobs, int njobs, int max_rows, int max_cols, const Bases& bases,
                      cudaStream_t stream) {
-  tsqr_f32_kernel<<<njobs, 512, tsqr_smem(max_rows, max_cols), stream>>>(jobs, bases);
+  // columns per warp: the smallest instantiation that covers max_cols
+  const size_t smem = tsqr_smem(max_rows, max_cols);
+  if (max_cols <= 2 * kTsqrWarps)
+    tsqr_f32_kernel<2><<<njobs, kTsqrThreads, smem, stream>>>(jobs, bases);
+  else if (max_cols <= 3 * kTsqrWarps)
+    tsqr_f32_kernel<3><<<njobs, kTsqrThreads, smem, stream>>>(jobs, bases);
+  else if (max_cols <= 4 * kTsqrWarps)
+    tsqr_f32_kernel<4><<<njobs, kTsqrThreads, smem, stream>>>(jobs, bases);
+  else
+    tsqr_f32_kernel<6><<<njobs, kTsqrThreads, smem, stream>>>(jobs, bases);
 }
 
 void launch_qr_f32(const QrF32Job* jobs, int njobs, const Bases& bases, Status* status, cudaStream_t stream) {
@@ -491,8 +634,8 @@ cudaError_t prepare_svd_f32(int bmax) {
 
 void launch_svd_f32(const SvdJob* jobs, int njobs, int bmax, const Bases& bases, Status* status,
                     cudaStream_t stream) {
-  // one warp per column pair of a round: b / 2 <= 48 pairs, 32 warps
-  svd_jacobi_f32_kernel<<<njobs, 1024, svd_smem(bmax), stream>>>(jobs, bases, status);
+  // kSvdLanes lanes per column pair of a round: b / 2 <= 48 pairs
+  svd_jacobi_f32_kernel<<<njobs, kSvdThreads, svd_smem(bmax), stream>>>(jobs, bases, status);
 }
 
 }  // namespace tks
