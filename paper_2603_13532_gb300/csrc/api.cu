@@ -48,7 +48,7 @@ Operand op_abs(const void* p, size_t off_bytes = 0) {
 }
 
 enum StepKind { S_OMEGA, S_GEMM, S_REDUCE, S_CORESKETCH, S_QR, S_EIG, S_TC, S_SIMT, S_CS32, S_SPLIT,
-                S_TRANSPOSE, S_QR32, S_SVD32, S_TSQR, S_CS3, S_CHAIN3, S_QRSM, S_PROJ3, S_SK3 };
+                S_TRANSPOSE, S_QR32, S_SVD32, S_TSQR, S_CS3, S_CHAIN3, S_QRSM, S_PROJ3, S_SK3, S_QRREG };
 
 struct Step {
   StepKind kind;
@@ -407,8 +407,10 @@ namespace {
 //   a7  per-term chains in float32, last step written as planes of Tcat (element (r, J) at r + ldT J)
 //   a8  H_(d)^T = Tcat^T A_d^T            A = Tcat planes (rows J)      B = A_d^T planes (rows a)
 static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
-  std::vector<QrF32Job> qr32, qrsm;
-  size_t qrsm_smem = 0;
+  std::vector<QrF32Job> qr32, qrsm, qrreg;
+  size_t qrsm_smem = 0, qrreg_smem = 0;
+  double qrreg_flops = 0.0;
+  int64_t qrreg_rows = 0;
   std::vector<CoreSketchF32Job> cs3;
   std::vector<Chain3Job> ch3;
   std::vector<Sketch3Job> sk3;
@@ -577,7 +579,12 @@ static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
         q.s1 = 0;
         q.sc = (int64_t)nn;
         const size_t sm = qr_smem_bytes((int64_t)nn, h.S[n]);
-        if (sm <= 216 * 1024) {
+        if (qr_reg_fits((int64_t)nn, h.S[n])) {
+          qrreg_flops += 4.0 * (double)nn * h.b[n] * h.b[n];
+          qrreg.push_back(q);
+          qrreg_smem = std::max(qrreg_smem, qr_reg_smem_bytes((int64_t)nn, h.S[n]));
+          qrreg_rows = std::max<int64_t>(qrreg_rows, (int64_t)nn);
+        } else if (sm <= 216 * 1024) {
           qrsm.push_back(q);
           qrsm_smem = std::max(qrsm_smem, sm);
         } else {
@@ -798,8 +805,14 @@ static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
   plan->st_recompress = plan->st_sketch;
   plan->push(plan->st_recompress, S_QR, qr, (int64_t)qr.size(), "a5:qr", qr_flops, qr_bytes);
   plan->push(plan->st_recompress, S_QR32, qr32, (int64_t)qr32.size(), "a5:qr[f32]", qr_flops, qr_bytes);
+  if (!qrreg.empty()) {
+    // work = the largest row count (selects the kernel's rows per lane)
+    plan->push(plan->st_recompress, S_QRREG, qrreg, qrreg_rows, "a5:qr_reg[f32]", qrreg_flops, 0.0);
+    plan->st_recompress.back().smem = qrreg_smem;
+  }
   if (!qrsm.empty()) {
-    plan->push(plan->st_recompress, S_QRSM, qrsm, (int64_t)qrsm.size(), "a5:qr_smem[f32]", qr_flops, qr_bytes);
+    plan->push(plan->st_recompress, S_QRSM, qrsm, (int64_t)qrsm.size(), "a5:qr_smem[f32]", qr_flops - qrreg_flops,
+               0.0);
     plan->st_recompress.back().smem = qrsm_smem;
   }
   for (const auto& st : plan->st_project) plan->st_recompress.push_back(st);
@@ -1434,6 +1447,7 @@ tks_status tks_plan_create(tks_plan** out, const tks_problem* problems, int32_t 
     if (e == cudaSuccess) e = prepare_order3_kernels();
     if (e == cudaSuccess) e = prepare_proj3();
     if (e == cudaSuccess) e = prepare_sketch3();
+    if (e == cudaSuccess) e = prepare_qr_reg_f32();
     if (e != cudaSuccess) {
       tks_plan_destroy(plan);
       return fail(TKS_ECUDA, std::string("tensor-core GEMM shared memory: ") + cudaGetErrorString(e));
@@ -1563,6 +1577,10 @@ tks_status run_steps(tks_plan* plan, const std::vector<Step>& steps, const Bases
         break;
       case S_TSQR:
         launch_tsqr_f32(static_cast<const TsqrJob*>(table), s.njobs, kTsqrBlockRows, plan->bmax, bases, stream);
+        break;
+      case S_QRREG:
+        launch_qr_reg_f32(static_cast<const QrF32Job*>(table), s.njobs, (int)s.work, s.smem, bases, plan->status,
+                          stream);
         break;
       case S_QRSM:
         launch_qr_smem_f32(static_cast<const QrF32Job*>(table), s.njobs, s.smem, bases, plan->status, stream);

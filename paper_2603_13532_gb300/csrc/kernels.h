@@ -42,6 +42,11 @@ cudaError_t prepare_order3_kernels();
 void launch_core_sketch_krp3(const CoreSketchF32Job* jobs, int njobs, size_t smem, const Bases& bases,
                              cudaStream_t stream);
 void launch_chain3(const Chain3Job* jobs, int njobs, size_t smem, const Bases& bases, cudaStream_t stream);
+// Mode products with a small matrix (128 fibres per CTA).
+int ttm_rows_tiles(int64_t rows);
+bool ttm_rows_fits(int b, int rmax);
+cudaError_t prepare_ttm_rows();
+void launch_ttm_rows(const TtmJob* jobs, int njobs, int total_tiles, const Bases& bases, cudaStream_t stream);
 // Khatri-Rao core sketches of order-3 terms, one CTA per term.
 size_t sketch3_smem_bytes(const int r[3]);
 cudaError_t prepare_sketch3();
@@ -59,6 +64,12 @@ void launch_qr_f32(const QrF32Job* jobs, int njobs, const Bases& bases, Status* 
 cudaError_t prepare_svd_f32(int bmax);
 // Householder QR with the matrix resident in shared memory (n * S floats), explicit Q.
 size_t qr_smem_bytes(int64_t n, int S);
+// Householder QR with Y held in registers (n <= 512, S <= 64), one CTA per job.
+bool qr_reg_fits(int64_t n, int S);
+size_t qr_reg_smem_bytes(int64_t n, int S);
+cudaError_t prepare_qr_reg_f32();
+void launch_qr_reg_f32(const QrF32Job* jobs, int njobs, int max_rows, size_t smem, const Bases& bases,
+                       Status* status, cudaStream_t stream);
 void launch_qr_smem_f32(const QrF32Job* jobs, int njobs, size_t smem, const Bases& bases, Status* status,
                         cudaStream_t stream);
 // One TSQR level: each job factors one block of rows and writes its triangular factor.

@@ -261,27 +261,16 @@ __global__ void __launch_bounds__(1024) qr_smem_f32_kernel(const QrF32Job* __res
   if (threadIdx.x == 0 && sh_bad) record_status_la(status, TKS_ENONFINITE);
 }
 
-// ----------------------------------------------------------------------------- TSQR block
-// Householder QR of a rows x cols block (rows <= 256, cols <= 32 kSlots), only the triangular
-// factor kept.  The block is staged through shared memory once and then lives in registers:
-// column l belongs to warp l % 16 (slot l / 16), lane L holds rows L + 32 u, u < 8.  Step j
-// reads the published reflector v_j = (0, .., 0, 1, x / (alpha - beta)) and tau_j from shared
-// memory; every warp updates its columns l > j in registers (a_l -= tau v (v^T a_l), one warp
-// reduction per column), and the warp owning column j + 1 then forms that column's reflector
-// and publishes it, so each column costs one barrier and no shared-memory traffic for the
-// trailing matrix.
-constexpr int kTsqrThreads = 512;
-constexpr int kTsqrWarps = kTsqrThreads / 32;
-constexpr int kTsqrRowsPerLane = kTsqrMaxRows / 32;
-
-// Forms the reflector of column c (owned by this warp, values a[u] at rows lane + 32 u) below
-// row c and publishes v, tau and the diagonal entry of R.
-__device__ __forceinline__ void tsqr_publish(const float (&a)[kTsqrRowsPerLane], int c, int m, float* v_out,
-                                             float* tau_out, float* rdiag) {
+// Forms the reflector of column c (owned by this warp, values a[u] at rows lane + 32 u, m rows)
+// below row c and publishes v (entries [0, vlen)), tau and the diagonal entry of R; returns
+// false when the column norm is not finite.
+template <int kRpl>
+__device__ __forceinline__ bool reflector_publish(const float (&a)[kRpl], int c, int m, float* v_out, int vlen,
+                                                  float* tau_out, float* rdiag) {
   const int lane = threadIdx.x & 31;
   float t2 = 0.f, alpha = 0.f;
 #pragma unroll
-  for (int u = 0; u < kTsqrRowsPerLane; ++u) {
+  for (int u = 0; u < kRpl; ++u) {
     const int i = lane + 32 * u;
     if (i > c && i < m) t2 = fmaf(a[u], a[u], t2);
     if (i == c) alpha = a[u];
@@ -294,15 +283,147 @@ __device__ __forceinline__ void tsqr_publish(const float (&a)[kTsqrRowsPerLane],
   const float tau = reflect ? (beta - alpha) / beta : 0.f;
   const float sc = reflect ? 1.f / (alpha - beta) : 0.f;
 #pragma unroll
-  for (int u = 0; u < kTsqrRowsPerLane; ++u) {
+  for (int u = 0; u < kRpl; ++u) {
     const int i = lane + 32 * u;
-    v_out[i] = i < c ? 0.f : (i == c ? 1.f : (i < m ? sc * a[u] : 0.f));
+    if (i < vlen) v_out[i] = i < c ? 0.f : (i == c ? 1.f : (i < m ? sc * a[u] : 0.f));
   }
   if (lane == 0) {
     *tau_out = tau;
     rdiag[c] = reflect ? beta : alpha;
   }
+  return isfinite(nrm);
 }
+
+// ----------------------------------------------------------------------------- QR in registers
+// Householder QR of Y (n x S, n <= 32 kRpl, S <= 16 kSlots) with the explicit Q (first b columns),
+// float32 arithmetic, float64 in and out.  Y is staged through shared memory and then held in
+// registers as in the TSQR block kernel (column l in warp l % 16, rows lane + 32 u); reflector j
+// is published into column j of the staging buffer, which afterwards holds all of them, so the
+// columns of Q = H_0 .. H_{b-1} [I_b; 0] are formed without further barriers (column l needs
+// H_l .. H_0 applied to e_l).  Columns are flipped so that diag(R) >= 0.
+constexpr int kQrRegThreads = 512;
+constexpr int kQrRegWarps = kQrRegThreads / 32;
+
+template <int kRpl, int kSlots>
+__global__ void __launch_bounds__(kQrRegThreads, 1) qr_reg_f32_kernel(const QrF32Job* __restrict__ jobs, Bases bases,
+                                                                     Status* status) {
+  extern __shared__ float vs[];            // n x S: Y staged, then reflector j in column j
+  __shared__ float tau_s[TKS_MAX_BASIS];
+  __shared__ float rdiag_s[TKS_MAX_BASIS];
+  __shared__ int sh_bad;
+  const QrF32Job& J = jobs[blockIdx.x];
+  const int n = (int)J.rows, S = (int)J.cols, b = J.b;
+  const char* src = at<char>(bases, J.src);
+  const uint32_t L0 = (uint32_t)J.L0;
+  if (threadIdx.x == 0) sh_bad = 0;
+  for (int e0 = 0; e0 < n * S; e0 += kLoadBatch * kQrRegThreads) {
+    float v[kLoadBatch];
+#pragma unroll
+    for (int u = 0; u < kLoadBatch; ++u) {
+      const int e = e0 + u * kQrRegThreads + threadIdx.x;
+      v[u] = 0.f;
+      if (e < n * S) {
+        const int j = e / n, i = e - j * n;
+        const uint32_t i1 = (uint32_t)i / L0, i0 = (uint32_t)i - i1 * L0;
+        v[u] = load_any(src, J.src_type, (int64_t)i0 * J.s0 + (int64_t)i1 * J.s1 + (int64_t)j * J.sc);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kLoadBatch; ++u) {
+      const int e = e0 + u * kQrRegThreads + threadIdx.x;
+      if (e < n * S) vs[e] = v[u];
+    }
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float a[kSlots][kRpl];
+#pragma unroll
+  for (int sl = 0; sl < kSlots; ++sl) {
+    const int l = warp + kQrRegWarps * sl;
+#pragma unroll
+    for (int u = 0; u < kRpl; ++u) {
+      const int i = lane + 32 * u;
+      a[sl][u] = (l < S && i < n) ? vs[i + n * l] : 0.f;
+    }
+  }
+  __syncthreads();   // the staging buffer now receives the reflectors
+  bool bad = false;
+  if (warp == 0 && b > 0) bad |= !reflector_publish(a[0], 0, n, vs, n, &tau_s[0], rdiag_s);
+  __syncthreads();
+  for (int j = 0; j < b; ++j) {
+    const float tau = tau_s[j];
+    float vj[kRpl];
+#pragma unroll
+    for (int u = 0; u < kRpl; ++u) {
+      const int i = lane + 32 * u;
+      vj[u] = i < n ? vs[i + n * j] : 0.f;
+    }
+#pragma unroll
+    for (int sl = 0; sl < kSlots; ++sl) {
+      const int l = warp + kQrRegWarps * sl;
+      if (l > j && l < S) {
+        if (tau != 0.f) {
+          float dot = 0.f;
+#pragma unroll
+          for (int u = 0; u < kRpl; ++u) dot = fmaf(vj[u], a[sl][u], dot);
+          const float w = tau * warp_sum_f(dot);
+#pragma unroll
+          for (int u = 0; u < kRpl; ++u) a[sl][u] = fmaf(-w, vj[u], a[sl][u]);
+        }
+        if (l == j + 1 && l < b) bad |= !reflector_publish(a[sl], l, n, vs + n * l, n, &tau_s[l], rdiag_s);
+      }
+    }
+    __syncthreads();
+  }
+  if (bad && lane == 0) sh_bad = 1;
+  // Q: column l = H_0 .. H_l e_l, reflectors read from shared memory
+  double* Q = at<double>(bases, J.Q);
+#pragma unroll
+  for (int sl = 0; sl < kSlots; ++sl) {
+    const int l = warp + kQrRegWarps * sl;
+    if (l < b) {
+      float q[kRpl];
+#pragma unroll
+      for (int u = 0; u < kRpl; ++u) q[u] = (lane + 32 * u == l) ? 1.f : 0.f;
+      for (int jj = l; jj >= 0; --jj) {
+        const float t = tau_s[jj];
+        if (t == 0.f) continue;
+        float v[kRpl];
+        float dot = 0.f;
+#pragma unroll
+        for (int u = 0; u < kRpl; ++u) {
+          const int i = lane + 32 * u;
+          v[u] = i < n ? vs[i + n * jj] : 0.f;
+          dot = fmaf(v[u], q[u], dot);
+        }
+        const float w = t * warp_sum_f(dot);
+#pragma unroll
+        for (int u = 0; u < kRpl; ++u) q[u] = fmaf(-w, v[u], q[u]);
+      }
+      const float sgn = rdiag_s[l] < 0.f ? -1.f : 1.f;
+#pragma unroll
+      for (int u = 0; u < kRpl; ++u) {
+        const int i = lane + 32 * u;
+        if (i < n) Q[i + (int64_t)n * l] = (double)(sgn * q[u]);
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && sh_bad) record_status_la(status, TKS_ENONFINITE);
+}
+
+// ----------------------------------------------------------------------------- TSQR block
+// Householder QR of a rows x cols block (rows <= 256, cols <= 32 kSlots), only the triangular
+// factor kept.  The block is staged through shared memory once and then lives in registers:
+// column l belongs to warp l % 16 (slot l / 16), lane L holds rows L + 32 u, u < 8.  Step j
+// reads the published reflector v_j = (0, .., 0, 1, x / (alpha - beta)) and tau_j from shared
+// memory; every warp updates its columns l > j in registers (a_l -= tau v (v^T a_l), one warp
+// reduction per column), and the warp owning column j + 1 then forms that column's reflector
+// and publishes it, so each column costs one barrier and no shared-memory traffic for the
+// trailing matrix.
+constexpr int kTsqrThreads = 512;
+constexpr int kTsqrWarps = kTsqrThreads / 32;
+constexpr int kTsqrRowsPerLane = kTsqrMaxRows / 32;
 
 template <int kSlots>
 __global__ void __launch_bounds__(kTsqrThreads, kSlots <= 4 ? 2 : 1) tsqr_f32_kernel(const TsqrJob* __restrict__ jobs, Bases bases) {
@@ -359,7 +480,7 @@ __global__ void __launch_bounds__(kTsqrThreads, kSlots <= 4 ? 2 : 1) tsqr_f32_ke
     }
   }
   const int kmax = m < b ? m : b;
-  if (warp == 0 && kmax > 0) tsqr_publish(a[0], 0, m, vbuf[0], &sh_tau[0], rdiag);
+  if (warp == 0 && kmax > 0) reflector_publish(a[0], 0, m, vbuf[0], kTsqrMaxRows, &sh_tau[0], rdiag);
   __syncthreads();
   for (int j = 0; j < kmax; ++j) {
     const float tau = sh_tau[j & 1];
@@ -378,7 +499,8 @@ __global__ void __launch_bounds__(kTsqrThreads, kSlots <= 4 ? 2 : 1) tsqr_f32_ke
 #pragma unroll
           for (int u = 0; u < kTsqrRowsPerLane; ++u) a[sl][u] = fmaf(-w, vj[u], a[sl][u]);
         }
-        if (l == j + 1 && l < kmax) tsqr_publish(a[sl], l, m, vbuf[(j + 1) & 1], &sh_tau[(j + 1) & 1], rdiag);
+        if (l == j + 1 && l < kmax)
+          reflector_publish(a[sl], l, m, vbuf[(j + 1) & 1], kTsqrMaxRows, &sh_tau[(j + 1) & 1], rdiag);
       }
     }
     __syncthreads();
@@ -407,7 +529,8 @@ __global__ void __launch_bounds__(kTsqrThreads, kSlots <= 4 ? 2 : 1) tsqr_f32_ke
 // orthogonal; V accumulates the rotations.  At convergence A = U Sigma, R = U Sigma V^T.
 constexpr int kSvdSweeps = 30;
 constexpr int kSvdLanes = 8;      // lanes per column pair
-constexpr int kSvdThreads = 384;  // kSvdLanes x (TKS_MAX_BASIS / 2) pairs
+constexpr int kSvdThreads = 384;  // kSvdLanes x (TKS_MAX_BASIS / 2) pairs, at most
+constexpr int kSvdElems = (TKS_MAX_BASIS + kSvdLanes - 1) / kSvdLanes;   // column entries per lane
 
 __global__ void __launch_bounds__(kSvdThreads) svd_jacobi_f32_kernel(const SvdJob* __restrict__ jobs, Bases bases,
                                                               Status* status) {
@@ -475,14 +598,19 @@ __global__ void __launch_bounds__(kSvdThreads) svd_jacobi_f32_kernel(const SvdJo
       if (!valid) p = q = 0;
       float* ap = A + p * ld;
       float* aq = A + q * ld;
+      float x[kSvdElems], y[kSvdElems];
       float al = 0.f, be = 0.f, ga = 0.f;
-      if (valid) {
-        for (int i = sub; i < b; i += kSvdLanes) {
-          const float x = ap[i], y = aq[i];
-          al = fmaf(x, x, al);
-          be = fmaf(y, y, be);
-          ga = fmaf(x, y, ga);
-        }
+#pragma unroll
+      for (int u = 0; u < kSvdElems; ++u) {
+        const int i = sub + kSvdLanes * u;
+        x[u] = (valid && i < b) ? ap[i] : 0.f;
+        y[u] = (valid && i < b) ? aq[i] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < kSvdElems; ++u) {
+        al = fmaf(x[u], x[u], al);
+        be = fmaf(y[u], y[u], be);
+        ga = fmaf(x[u], y[u], ga);
       }
       // every lane takes part in the group reductions
 #pragma unroll
@@ -492,18 +620,28 @@ __global__ void __launch_bounds__(kSvdThreads) svd_jacobi_f32_kernel(const SvdJo
         ga += __shfl_xor_sync(0xffffffffu, ga, o, kSvdLanes);
       }
       if (valid && fabsf(ga) > thr * sqrtf(al * be) && ga != 0.f && fminf(al, be) > noise2) {
-        const float zeta = (be - al) / (2.f * ga);
-        const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
-        const float c = 1.f / sqrtf(1.f + t * t), s = c * t;
+        // the angle only steers convergence, so t is formed with fast division; the rotation's
+        // orthogonality rests on c^2 + s^2 = 1, so c = 1 / sqrt(1 + t^2) gets a Newton step
+        const float zeta = __fdividef(be - al, 2.f * ga);
+        const float az = fabsf(zeta);
+        const float tm = az > 1e18f ? __fdividef(0.5f, az) : __fdividef(1.f, az + sqrtf(fmaf(az, az, 1.f)));
+        const float t = copysignf(tm, zeta);
+        const float w = fmaf(t, t, 1.f);
+        float c = rsqrtf(w);
+        c = c * fmaf(-0.5f * w * c, c, 1.5f);
+        const float s = c * t;
         float* vp = V + p * ld;
         float* vq = V + q * ld;
-        for (int i = sub; i < b; i += kSvdLanes) {
-          const float x = ap[i], y = aq[i];
-          ap[i] = c * x - s * y;
-          aq[i] = s * x + c * y;
-          const float vx = vp[i], vy = vq[i];
-          vp[i] = c * vx - s * vy;
-          vq[i] = s * vx + c * vy;
+#pragma unroll
+        for (int u = 0; u < kSvdElems; ++u) {
+          const int i = sub + kSvdLanes * u;
+          if (i < b) {
+            ap[i] = c * x[u] - s * y[u];
+            aq[i] = s * x[u] + c * y[u];
+            const float vx = vp[i], vy = vq[i];
+            vp[i] = c * vx - s * vy;
+            vq[i] = s * vx + c * vy;
+          }
         }
         any = 1;
       }
@@ -590,6 +728,14 @@ size_t svd_smem(int bmax) {
 
 size_t tsqr_smem(int rows, int cols) { return (size_t)(rows + 1) * cols * sizeof(float); }
 
+cudaError_t prepare_qr_reg_f32() {
+  cudaError_t e = cudaFuncSetAttribute(qr_reg_f32_kernel<4, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(qr_reg_f32_kernel<8, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(qr_reg_f32_kernel<16, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+
 cudaError_t prepare_tsqr_f32() {
   cudaError_t e = cudaFuncSetAttribute(qr_smem_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 222 * 1024);
   if (e != cudaSuccess) return e;
@@ -623,6 +769,20 @@ void launch_tsqr_f32(const TsqrJob* jobs, int njobs, int max_rows, int max_cols,
     tsqr_f32_kernel<6><<<njobs, kTsqrThreads, smem, stream>>>(jobs, bases);
 }
 
+size_t qr_reg_smem_bytes(int64_t n, int S) { return (size_t)(n * S) * sizeof(float); }
+
+bool qr_reg_fits(int64_t n, int S) { return n <= 512 && S <= 4 * kQrRegWarps && qr_reg_smem_bytes(n, S) <= 200 * 1024; }
+
+void launch_qr_reg_f32(const QrF32Job* jobs, int njobs, int max_rows, size_t smem, const Bases& bases,
+                       Status* status, cudaStream_t stream) {
+  if (max_rows <= 128)
+    qr_reg_f32_kernel<4, 4><<<njobs, kQrRegThreads, smem, stream>>>(jobs, bases, status);
+  else if (max_rows <= 256)
+    qr_reg_f32_kernel<8, 4><<<njobs, kQrRegThreads, smem, stream>>>(jobs, bases, status);
+  else
+    qr_reg_f32_kernel<16, 4><<<njobs, kQrRegThreads, smem, stream>>>(jobs, bases, status);
+}
+
 void launch_qr_f32(const QrF32Job* jobs, int njobs, const Bases& bases, Status* status, cudaStream_t stream) {
   qr_f32_kernel<<<njobs, 512, 0, stream>>>(jobs, bases, status);
 }
@@ -634,8 +794,10 @@ cudaError_t prepare_svd_f32(int bmax) {
 
 void launch_svd_f32(const SvdJob* jobs, int njobs, int bmax, const Bases& bases, Status* status,
                     cudaStream_t stream) {
-  // kSvdLanes lanes per column pair of a round: b / 2 <= 48 pairs
-  svd_jacobi_f32_kernel<<<njobs, kSvdThreads, svd_smem(bmax), stream>>>(jobs, bases, status);
+  // kSvdLanes lanes per column pair of a round, whole warps: ceil(bmax / 2) <= 48 pairs
+  const int pairs = (bmax + 1) / 2;
+  const int threads = ((pairs * kSvdLanes + 31) / 32) * 32;
+  svd_jacobi_f32_kernel<<<njobs, threads, svd_smem(bmax), stream>>>(jobs, bases, status);
 }
 
 }  // namespace tks

@@ -164,6 +164,31 @@ def test_mixed_recompress_small(cuda_lib, kind, precision):
 
 
 @pytest.mark.parametrize("precision", MODES)
+def test_mixed_recompress_short_modes(cuda_lib, precision):
+    """Modes with fewer rows than sketch columns (n_1 = 16 < S = 20, so b_1 = n_1 and the QR of Y_1
+    is wide) next to rows-per-lane boundaries of the float32 QR kernels (n = 128, 136, 256, 264)."""
+    g = np.random.default_rng(79)
+    specs = [([16, 24, 64], 5, [12, 12, 12], [8, 8, 8]), ([128, 136, 256], 4, [10, 10, 10], [4, 4, 4]),
+             ([264, 40, 32], 3, [8, 8, 8], [3, 3, 3])]
+    probs = []
+    for dims, K, target, over in specs:
+        ranks = [[int(min(x, n)) for x, n in zip(g.integers(2, 9, size=3), dims)] for _ in range(K)]
+        cores = [g.standard_normal(r) for r in ranks]
+        facs = [[g.standard_normal((n, ri)) for n, ri in zip(dims, r)] for r in ranks]
+        probs.append(wl.Problem(dims, cores, facs, target, over, alpha=list(g.standard_normal(K))))
+    probs = wl._finish(probs, True)
+    outs = _plan(probs, "krp", 12, precision=precision).recompress()
+    for i, (prob, got) in enumerate(zip(probs, outs)):
+        ref = _oracle(prob, "krp", 12, i)
+        assert got["ranks"] == ref["ranks"]
+        X = sum(a * tucker_full(G, Us) for a, (G, Us) in zip(prob.alpha, prob.terms()))
+        Xg = tucker_full(got["core"], got["factors"])
+        Xo = tucker_full(ref["core"], ref["factors"])
+        nx = np.linalg.norm(X)
+        assert np.linalg.norm(Xg - Xo) / nx <= 1e-5, (i, np.linalg.norm(Xg - Xo) / nx)
+
+
+@pytest.mark.parametrize("precision", MODES)
 def test_mixed_decay512_full_size(cuda_lib, precision):
     w = wl.decay512()
     p = w.problems[0]
