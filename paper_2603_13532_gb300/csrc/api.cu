@@ -48,7 +48,7 @@ Operand op_abs(const void* p, size_t off_bytes = 0) {
 }
 
 enum StepKind { S_OMEGA, S_GEMM, S_REDUCE, S_CORESKETCH, S_QR, S_EIG, S_TC, S_SIMT, S_CS32, S_SPLIT,
-                S_TRANSPOSE, S_QR32, S_SVD32, S_TSQR, S_CS3, S_CHAIN3, S_QRSM, S_PROJ3, S_SK3, S_QRREG };
+                S_TRANSPOSE, S_QR32, S_SVD32, S_TSQR, S_CS3, S_CHAIN3, S_QRSM, S_PROJ3, S_SK3, S_QRREG, S_TTM };
 
 struct Step {
   StepKind kind;
@@ -408,6 +408,7 @@ namespace {
 //   a8  H_(d)^T = Tcat^T A_d^T            A = Tcat planes (rows J)      B = A_d^T planes (rows a)
 static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
   std::vector<QrF32Job> qr32, qrsm, qrreg;
+  bool planes_in_qr = false;   // the register QR of this mode also writes the bf16 planes of Q
   size_t qrsm_smem = 0, qrreg_smem = 0;
   double qrreg_flops = 0.0;
   int64_t qrreg_rows = 0;
@@ -581,6 +582,9 @@ static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
         const size_t sm = qr_smem_bytes((int64_t)nn, h.S[n]);
         if (qr_reg_fits((int64_t)nn, h.S[n])) {
           qrreg_flops += 4.0 * (double)nn * h.b[n] * h.b[n];
+          q.nplanes = 3;
+          for (int t = 0; t < 3; ++t) q.Qp[t] = op(B_WS, h.Qp[n][t]);
+          planes_in_qr = true;
           qrreg.push_back(q);
           qrreg_smem = std::max(qrreg_smem, qr_reg_smem_bytes((int64_t)nn, h.S[n]));
           qrreg_rows = std::max<int64_t>(qrreg_rows, (int64_t)nn);
@@ -604,6 +608,9 @@ static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
       }
       qr_flops += 4.0 * (double)nn * h.b[n] * h.b[n];
       qr_bytes += 8.0 * (double)nn * (h.S[n] + h.b[n]);
+      if (planes_in_qr) {
+        planes_in_qr = false;
+      } else {
       SplitJob sj;
       std::memset(&sj, 0, sizeof(sj));
       sj.src = op(B_Q, h.q_off[n] * 8);
@@ -615,6 +622,7 @@ static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
       sj.begin = sp_total;
       sp_total += sj.count;
       sp.push_back(sj);
+      }
       TcJob a6 = tc_job(h.R[n], h.b[n], (int)nn);
       a6.na = 1;
       a6.nb = 3;
@@ -827,6 +835,9 @@ static void build_hosvd_f32(tks_plan* plan) {
     std::vector<std::vector<TsqrJob>> tsqr;
     std::vector<SvdJob> svds;
     std::vector<SimtJob> ttm, fac;
+    std::vector<TtmJob> ttm2, fac2;
+    int ttm_tiles = 0, fac_tiles = 0;
+    double ttm_flops = 0.0, fac_flops = 0.0;
     double qflops = 0.0;
     for (int p = 0; p < plan->nprob; ++p) {
       auto& h = plan->probs[p];
@@ -893,6 +904,47 @@ static void build_hosvd_f32(tks_plan* plan) {
       sj.order = d;
       sj.tol = plan->params.trunc_tol;
       svds.push_back(sj);
+      if (ttm_rows_fits(b, rmax)) {
+        // H x_n P^T and Q_n P with the fibre kernel
+        TtmJob tj;
+        std::memset(&tj, 0, sizeof(tj));
+        tj.X = X;
+        tj.x_type = xt;
+        tj.P = op(B_WS, h.P32[n]);
+        tj.L = L;
+        tj.Rr = Rr;
+        tj.b = b;
+        tj.rmax = rmax;
+        if (n == d - 1) {
+          tj.Y = op(B_OUT, h.out_core_off * 8);
+          tj.y_type = T_F64;
+        } else {
+          tj.Y = op(B_WS, h.Hp[n & 1]);
+          tj.y_type = T_F32;
+        }
+        tj.tiles = ttm_rows_tiles(L * Rr);
+        tj.tile_begin = ttm_tiles;
+        ttm_tiles += tj.tiles;
+        ttm2.push_back(tj);
+        ttm_flops += 2.0 * (double)L * Rr * b * rmax;
+        TtmJob fj;
+        std::memset(&fj, 0, sizeof(fj));
+        fj.X = op(B_Q, h.q_off[n] * 8);
+        fj.x_type = T_F64;
+        fj.P = op(B_WS, h.P32[n]);
+        fj.Y = op(B_OUT, h.out_fac_off[n] * 8);
+        fj.y_type = T_F64;
+        fj.L = (int64_t)h.n[n];
+        fj.Rr = 1;
+        fj.b = b;
+        fj.rmax = rmax;
+        fj.tiles = ttm_rows_tiles((int64_t)h.n[n]);
+        fj.tile_begin = fac_tiles;
+        fac_tiles += fj.tiles;
+        fac2.push_back(fj);
+        fac_flops += 2.0 * (double)h.n[n] * b * rmax;
+        continue;
+      }
       SimtJob t;
       std::memset(&t, 0, sizeof(t));
       t.batch = 1;
@@ -939,8 +991,10 @@ static void build_hosvd_f32(tks_plan* plan) {
     plan->push(plan->st_recompress, S_SVD32, svds, (int64_t)svds.size(), nm);
     std::snprintf(nm, sizeof(nm), "a9:ttm%d[f32]", n);
     plan->push_simt(plan->st_recompress, ttm, nm);
+    plan->push(plan->st_recompress, S_TTM, ttm2, ttm_tiles, nm, ttm_flops, 0.0);
     std::snprintf(nm, sizeof(nm), "a9:factor%d[f32]", n);
     plan->push_simt(plan->st_recompress, fac, nm);
+    plan->push(plan->st_recompress, S_TTM, fac2, fac_tiles, nm, fac_flops, 0.0);
   }
 }
 
@@ -1448,6 +1502,7 @@ tks_status tks_plan_create(tks_plan** out, const tks_problem* problems, int32_t 
     if (e == cudaSuccess) e = prepare_proj3();
     if (e == cudaSuccess) e = prepare_sketch3();
     if (e == cudaSuccess) e = prepare_qr_reg_f32();
+    if (e == cudaSuccess) e = prepare_ttm_rows();
     if (e != cudaSuccess) {
       tks_plan_destroy(plan);
       return fail(TKS_ECUDA, std::string("tensor-core GEMM shared memory: ") + cudaGetErrorString(e));
@@ -1577,6 +1632,9 @@ tks_status run_steps(tks_plan* plan, const std::vector<Step>& steps, const Bases
         break;
       case S_TSQR:
         launch_tsqr_f32(static_cast<const TsqrJob*>(table), s.njobs, kTsqrBlockRows, plan->bmax, bases, stream);
+        break;
+      case S_TTM:
+        launch_ttm_rows(static_cast<const TtmJob*>(table), s.njobs, (int)s.work, bases, stream);
         break;
       case S_QRREG:
         launch_qr_reg_f32(static_cast<const QrF32Job*>(table), s.njobs, (int)s.work, s.smem, bases, plan->status,

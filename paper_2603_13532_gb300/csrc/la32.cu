@@ -4,6 +4,7 @@
 // perturbs the kept subspaces by about 1e-7 relative to ||H|| instead of squaring the spectrum.
 #include <cuda_runtime.h>
 
+#include "bf16.cuh"
 #include "kernels.h"
 
 namespace tks {
@@ -404,7 +405,18 @@ __global__ void __launch_bounds__(kQrRegThreads, 1) qr_reg_f32_kernel(const QrF3
 #pragma unroll
       for (int u = 0; u < kRpl; ++u) {
         const int i = lane + 32 * u;
-        if (i < n) Q[i + (int64_t)n * l] = (double)(sgn * q[u]);
+        if (i < n) {
+          const float v = sgn * q[u];
+          Q[i + (int64_t)n * l] = (double)v;
+          if (J.nplanes) {
+            // the same planes the float64 -> bf16 split gives for this float32 value
+            uint16_t h0, h1, h2;
+            split3(v, h0, h1, h2);
+            at<uint16_t>(bases, J.Qp[0])[i + (int64_t)n * l] = h0;
+            at<uint16_t>(bases, J.Qp[1])[i + (int64_t)n * l] = h1;
+            at<uint16_t>(bases, J.Qp[2])[i + (int64_t)n * l] = h2;
+          }
+        }
       }
     }
   }

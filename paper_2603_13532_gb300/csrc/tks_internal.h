@@ -114,6 +114,16 @@ struct CoreSketchF32Job {
   int64_t begin;
 };
 
+// Mode product with a small matrix (ST-HOSVD truncation and final factors, float32 arithmetic):
+// Y[l + L (c + rmax r)] = sum_a X[l + L (a + b r)] P[a + b c] for l < L, r < Rr, c < rmax <= 64.
+struct TtmJob {
+  Operand X, P, Y;       // X typed (T_F64 / T_F32), P float32, Y typed
+  int32_t x_type, y_type;
+  int64_t L, Rr;
+  int32_t b, rmax;
+  int32_t tile_begin, tiles;
+};
+
 // Khatri-Rao core sketches of all three modes of one order-3 term (stage b, float32), one CTA per
 // term; requires s <= 64 and ranks <= kSketch3MaxRank.
 constexpr int kSketch3MaxRank = 32;
@@ -242,8 +252,10 @@ struct TcJob {
 // factor R (b x b, float32, column-major), b = min(rows, cols).
 struct QrF32Job {
   Operand src, W, tau, Q, R;
+  Operand Qp[3];         // register kernel: Q also as bf16 planes hi/mid/lo (same layout) when nplanes
   int32_t src_type, want_q, want_r, b;
   int64_t rows, cols, L0, s0, s1, sc;
+  int32_t nplanes, pad;
 };
 
 // One block of a TSQR level: rows [row_begin, row_begin + rows) x cols of a (typed, two-level
