@@ -542,7 +542,7 @@ __global__ void __launch_bounds__(kTsqrThreads, kSlots <= 4 ? 2 : 1) tsqr_f32_ke
 constexpr int kSvdSweeps = 30;
 constexpr int kSvdLanes = 8;      // lanes per column pair
 constexpr int kSvdThreads = 384;  // kSvdLanes x (TKS_MAX_BASIS / 2) pairs, at most
-constexpr int kSvdElems = (TKS_MAX_BASIS + kSvdLanes - 1) / kSvdLanes;   // column entries per lane
+constexpr int kSvdChunks = (TKS_MAX_BASIS + 4 * kSvdLanes - 1) / (4 * kSvdLanes);   // 4-row chunks per lane
 
 __global__ void __launch_bounds__(kSvdThreads) svd_jacobi_f32_kernel(const SvdJob* __restrict__ jobs, Bases bases,
                                                               Status* status) {
@@ -550,7 +550,7 @@ __global__ void __launch_bounds__(kSvdThreads) svd_jacobi_f32_kernel(const SvdJo
   const SvdJob& J = jobs[blockIdx.x];
   const int b = J.b;
   const int m = b + (b & 1);
-  const int ld = m + 1;
+  const int ld = (m + 3) & ~3;   // columns start 16-byte aligned; rows in [b, ld) stay zero
   float* A = sm;
   float* V = A + m * ld;
   float* nrm = V + m * ld;
@@ -558,10 +558,10 @@ __global__ void __launch_bounds__(kSvdThreads) svd_jacobi_f32_kernel(const SvdJo
   __shared__ int sh_rot, sh_rank;
   __shared__ float red[32];
   const float* Rg = at<float>(bases, J.R);
-  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-    const int r = e % m, c = e / m;
-    A[r + c * ld] = (r < b && c < b) ? Rg[r + c * b] : 0.f;
-    V[r + c * ld] = (r == c) ? 1.f : 0.f;
+  for (int e = threadIdx.x; e < m * ld; e += blockDim.x) {
+    const int r = e % ld, c = e / ld;
+    A[e] = (r < b && c < b) ? Rg[r + c * b] : 0.f;
+    V[e] = (r == c) ? 1.f : 0.f;
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -610,19 +610,21 @@ __global__ void __launch_bounds__(kSvdThreads) svd_jacobi_f32_kernel(const SvdJo
       if (!valid) p = q = 0;
       float* ap = A + p * ld;
       float* aq = A + q * ld;
-      float x[kSvdElems], y[kSvdElems];
+      // lane `sub` of the group holds the 4-row chunks sub, sub + 8, ... of both columns
+      float4 x[kSvdChunks], y[kSvdChunks];
       float al = 0.f, be = 0.f, ga = 0.f;
 #pragma unroll
-      for (int u = 0; u < kSvdElems; ++u) {
-        const int i = sub + kSvdLanes * u;
-        x[u] = (valid && i < b) ? ap[i] : 0.f;
-        y[u] = (valid && i < b) ? aq[i] : 0.f;
+      for (int u = 0; u < kSvdChunks; ++u) {
+        const int i = 4 * (sub + kSvdLanes * u);
+        const bool in = valid && i < b;
+        x[u] = in ? *reinterpret_cast<const float4*>(ap + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+        y[u] = in ? *reinterpret_cast<const float4*>(aq + i) : make_float4(0.f, 0.f, 0.f, 0.f);
       }
 #pragma unroll
-      for (int u = 0; u < kSvdElems; ++u) {
-        al = fmaf(x[u], x[u], al);
-        be = fmaf(y[u], y[u], be);
-        ga = fmaf(x[u], y[u], ga);
+      for (int u = 0; u < kSvdChunks; ++u) {
+        al = fmaf(x[u].x, x[u].x, fmaf(x[u].y, x[u].y, fmaf(x[u].z, x[u].z, fmaf(x[u].w, x[u].w, al))));
+        be = fmaf(y[u].x, y[u].x, fmaf(y[u].y, y[u].y, fmaf(y[u].z, y[u].z, fmaf(y[u].w, y[u].w, be))));
+        ga = fmaf(x[u].x, y[u].x, fmaf(x[u].y, y[u].y, fmaf(x[u].z, y[u].z, fmaf(x[u].w, y[u].w, ga))));
       }
       // every lane takes part in the group reductions
 #pragma unroll
@@ -645,14 +647,20 @@ __global__ void __launch_bounds__(kSvdThreads) svd_jacobi_f32_kernel(const SvdJo
         float* vp = V + p * ld;
         float* vq = V + q * ld;
 #pragma unroll
-        for (int u = 0; u < kSvdElems; ++u) {
-          const int i = sub + kSvdLanes * u;
+        for (int u = 0; u < kSvdChunks; ++u) {
+          const int i = 4 * (sub + kSvdLanes * u);
           if (i < b) {
-            ap[i] = c * x[u] - s * y[u];
-            aq[i] = s * x[u] + c * y[u];
-            const float vx = vp[i], vy = vq[i];
-            vp[i] = c * vx - s * vy;
-            vq[i] = s * vx + c * vy;
+            const float4 a = x[u], bb = y[u];
+            *reinterpret_cast<float4*>(ap + i) =
+                make_float4(c * a.x - s * bb.x, c * a.y - s * bb.y, c * a.z - s * bb.z, c * a.w - s * bb.w);
+            *reinterpret_cast<float4*>(aq + i) =
+                make_float4(s * a.x + c * bb.x, s * a.y + c * bb.y, s * a.z + c * bb.z, s * a.w + c * bb.w);
+            const float4 vx = *reinterpret_cast<const float4*>(vp + i);
+            const float4 vy = *reinterpret_cast<const float4*>(vq + i);
+            *reinterpret_cast<float4*>(vp + i) =
+                make_float4(c * vx.x - s * vy.x, c * vx.y - s * vy.y, c * vx.z - s * vy.z, c * vx.w - s * vy.w);
+            *reinterpret_cast<float4*>(vq + i) =
+                make_float4(s * vx.x + c * vy.x, s * vx.y + c * vy.y, s * vx.z + c * vy.z, s * vx.w + c * vy.w);
           }
         }
         any = 1;
@@ -732,8 +740,8 @@ __global__ void __launch_bounds__(kSvdThreads) svd_jacobi_f32_kernel(const SvdJo
 }
 
 size_t svd_smem(int bmax) {
-  const int m = bmax + (bmax & 1);
-  return (size_t)2 * m * (m + 1) * sizeof(float) + (size_t)m * sizeof(float) + (size_t)m * sizeof(int);
+  const int m = bmax + (bmax & 1), ld = (m + 3) & ~3;
+  return (size_t)2 * m * ld * sizeof(float) + (size_t)m * sizeof(float) + (size_t)m * sizeof(int);
 }
 
 }  // namespace
