@@ -32,11 +32,14 @@ constexpr int kR = TKS_MAX_RANK;
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
+// No "memory" clobber on the copies themselves: their destinations are read only after
+// cp_async_wait_all (which has one) and a barrier, and a clobber here would make the compiler
+// reload every job field from global memory after each copy.
 __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src));
 }
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src));
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
@@ -67,31 +70,39 @@ __device__ __forceinline__ void chunk_range(const Proj3Term& T, const Pos& p, in
 
 // Issue the asynchronous copies of one chunk (and, on its first chunk, of the term's A1 and A2)
 // into buffer `buf`; returns the element shift of the core slice inside its buffer.
-__device__ __forceinline__ int issue_chunk(Smem& S, const Proj3Job& J, const Proj3Term& T, const Pos& p, int buf,
+// The job's fields as registers.
+struct JobRegs {
+  const float* AT[3];
+  int64_t R[3];
+  int b[3];
+  int x0, rows;
+};
+
+__device__ __forceinline__ int issue_chunk(Smem& S, const JobRegs& J, const Proj3Term& T, const Pos& p, int buf,
                                            const Bases& bases) {
   const int tid = threadIdx.x;
   const int r0 = T.r[0], r1 = T.r[1];
   int c0, nc;
   chunk_range(T, p, c0, nc);
   if (p.c == 0) {
-    const float* AT0 = at<float>(bases, J.AT[0]) + T.roff[0];
-    const float* AT1 = at<float>(bases, J.AT[1]) + T.roff[1];
+    const float* AT0 = J.AT[0] + T.roff[0];
+    const float* AT1 = J.AT[1] + T.roff[1];
     float* A1 = S.A1[p.k & 1];
     float* A2 = S.A2[p.k & 1];
     for (int e = tid; e < r0 * J.rows; e += kThreads) {
       const int i0 = e % r0, x = e / r0;
-      cp_async4(A1 + i0 * kRows + x, AT0 + i0 + (int64_t)J.R[0] * (J.x0 + x));
+      cp_async4(A1 + i0 * kRows + x, AT0 + i0 + J.R[0] * (J.x0 + x));
     }
     for (int e = tid; e < r1 * J.b[1]; e += kThreads) {
       const int i1 = e % r1, a1 = e / r1;
-      cp_async4(A2 + i1 * kPad + a1, AT1 + i1 + (int64_t)J.R[1] * a1);
+      cp_async4(A2 + i1 * kPad + a1, AT1 + i1 + J.R[1] * a1);
     }
   }
-  const float* AT2 = at<float>(bases, J.AT[2]) + T.roff[2] + c0;
+  const float* AT2 = J.AT[2] + T.roff[2] + c0;
   float* A3 = S.A3[buf];
   for (int e = tid; e < nc * J.b[2]; e += kThreads) {
     const int i2c = e % nc, a2 = e / nc;
-    cp_async4(A3 + i2c * kPad + a2, AT2 + i2c + (int64_t)J.R[2] * a2);
+    cp_async4(A3 + i2c * kPad + a2, AT2 + i2c + J.R[2] * a2);
   }
   // the slice is contiguous: copy the 16-byte blocks that cover it (they lie in the pages of the
   // slice's own first and last bytes, so nothing outside mapped memory is touched)
@@ -116,8 +127,19 @@ __global__ void __launch_bounds__(kThreads, 2) project3_kernel(const Proj3Job* _
                                                                 Bases bases) {
   extern __shared__ __align__(16) unsigned char p3raw[];
   Smem& S = *reinterpret_cast<Smem*>(p3raw);
-  const Proj3Job& J = jobs[blockIdx.x];
-  const Proj3Term* terms = reinterpret_cast<const Proj3Term*>(jobs + njobs) + J.term_begin;
+  const Proj3Job& Jg = jobs[blockIdx.x];
+  const Proj3Term* terms = reinterpret_cast<const Proj3Term*>(jobs + njobs) + Jg.term_begin;
+  const int nterms = Jg.nterms;
+  JobRegs J;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    J.AT[q] = at<float>(bases, Jg.AT[q]);
+    J.R[q] = Jg.R[q];
+    J.b[q] = Jg.b[q];
+  }
+  J.x0 = Jg.x0;
+  J.rows = Jg.rows;
+  double* const Hout = at<double>(bases, Jg.H);
   const int tid = threadIdx.x;
   const int tm = tid & 31, tn = tid >> 5;
 
@@ -135,7 +157,7 @@ __global__ void __launch_bounds__(kThreads, 2) project3_kernel(const Proj3Job* _
   for (int e = tid; e < 2 * kR * kRows; e += kThreads) (&S.A1[0][0])[e] = 0.f;
   __syncthreads();   // the zero fill lands before any copy into A1
 
-  if (J.nterms > 0) {
+  if (nterms > 0) {
     Pos cur{0, 0, (terms[0].r[2] + chunk_max(terms[0]) - 1) / chunk_max(terms[0])};
     int shift = issue_chunk(S, J, terms[0], cur, 0, bases);
     int buf = 0;
@@ -148,7 +170,7 @@ __global__ void __launch_bounds__(kThreads, 2) project3_kernel(const Proj3Job* _
       cp_async_wait_all();
       __syncthreads();   // this chunk is in shared memory; every thread is done with the other buffers
       Pos nxt = cur;
-      more = advance(terms, J.nterms, nxt);
+      more = advance(terms, nterms, nxt);
       int next_shift = 0;
       if (more) next_shift = issue_chunk(S, J, terms[nxt.k], nxt, buf ^ 1, bases);
       const float alpha = T.alpha;
@@ -227,7 +249,7 @@ __global__ void __launch_bounds__(kThreads, 2) project3_kernel(const Proj3Job* _
   // H (float64, mode-1 fastest): a lane writes the kRows consecutive rows of one (a1, a2); rows,
   // columns beyond b2, b3 hold whatever the uncopied padding of A2, A3 produced and are not written
   const int b0 = J.b[0], b1 = J.b[1], b2 = J.b[2];
-  double* H = at<double>(bases, J.H);
+  double* H = Hout;
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     const int a1 = 32 * h + tm;
