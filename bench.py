@@ -41,7 +41,7 @@ FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1
 def parse_args():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp64", "mixed", "mixed_f32la"], default="mixed_f32la")
@@ -156,7 +156,7 @@ class ClockSampler:
             os.close(fd)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + ",".join(CLOCK_FIELDS),
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -271,7 +271,13 @@ FP32_KINDS = {"simt", "core_sketch32", "qr32", "svd32", "tsqr32", "core_sketch3"
               "project3", "sketch3", "qr_reg32", "ttm32"}
 
 
-def roofline_from_profile(prof, calls, peaks):
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch per problem, from an ncu
+# capture of the same kernel binary on 16 decay512 problems (15.567 MB read + 0.151 MB written),
+# used to scale the measured traffic to the bench launch; only valid for that kernel and workload.
+NCU_TRAFFIC_PER_PROBLEM = {("decay512", "a7:project3[f32]"): (15.567104e6 + 0.150528e6) / 16}
+
+
+def roofline_from_profile(prof, calls, peaks, workload=None, problems=0):
     """The longest launch with an algorithmic count, and its achieved rate against its roofline.
 
     FP64 CUDA-core launches are bound by the FP64 pipe, FP32 CUDA-core launches by the FP32 pipe
@@ -303,7 +309,10 @@ def roofline_from_profile(prof, calls, peaks):
                     "unit": "GB/s", "peak_source": "measured hbm_gbs"}
         roof["arithmetic_intensity"] = ai
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    per_problem = NCU_TRAFFIC_PER_PROBLEM.get((workload, top["name"]))
+    roof["traffic"] = per_problem * problems if per_problem is not None else None
+    if per_problem is not None:
+        roof["traffic_note"] = "ncu DRAM bytes of the kernel on 16 problems, scaled to this launch's problems"
     roof["kernel"] = top["name"]
     roof["kernel_share"] = top["ms"] / total_ms if total_ms > 0 else None
     roof["avg_launch_ms"] = avg_s * 1e3
@@ -394,7 +403,7 @@ def main():
     tflops = (plan.info.flops_lowprec + plan.info.flops_fp64) * world * args.steps / elapsed / 1e12
 
     peaks, peak_src = load_peaks()
-    roof = roofline_from_profile(prof, args.steps, peaks)
+    roof = roofline_from_profile(prof, args.steps, peaks, args.workload, P)
     roof["peak_file"] = peak_src
 
     # end to end: pinned host inputs -> device, recompress, result -> pinned host, every step
