@@ -268,7 +268,7 @@ def time_steps(fn, steps, stream):
 FP32_PEAK_TFLOPS = 152 * 256 * 2.070e9 / 1e12   # 128 FP32 FMA per SM per clock
 FP64_KINDS = {"gemm", "reduce", "qr", "core_sketch", "eig"}
 FP32_KINDS = {"simt", "core_sketch32", "qr32", "svd32", "tsqr32", "core_sketch3", "chain3", "qr_smem32",
-              "project3", "sketch3", "qr_reg32", "ttm32"}
+              "project3", "sketch3", "qr_reg32", "ttm32", "fold4", "project4"}
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch per problem, from an ncu
@@ -431,7 +431,9 @@ def main():
     fp64_path = None
     if args.precision != "fp64" and args.fp64_steps > 0:
         import numpy as _np
-        plan64 = binding.Plan(problems, kind=kind, precision="fp64", seed=args.seed, device=device)
+        # the same Gaussian draws as the mixed plan, so the comparison below is arithmetic only
+        plan64 = binding.Plan(problems, kind=kind, precision="fp64", seed=args.seed, device=device,
+                              omega_lowprec=True)
         out64 = torch.zeros(plan64.info.output_elems, dtype=torch.float64, device=device)
         r64 = torch.zeros_like(ranks_t)
 
@@ -445,18 +447,30 @@ def main():
         res_m = plan.unpack(out, ranks_t)
         res_d = plan64.unpack(out64, r64)
         g = _np.random.default_rng(0)
-        worst = 0.0
+        worst = worst_trunc = 0.0
         for pm, pd, pr in list(zip(res_m, res_d, problems))[:8]:
             idx = _np.stack([g.integers(0, n, size=256) for n in pr.dims], axis=1)
             em = sampled_entries(pm["core"], pm["factors"], idx)
             ed = sampled_entries(pd["core"], pd["factors"], idx)
+            # the sum itself at the same entries, term by term
+            alpha = pr.alpha if pr.alpha is not None else [1.0] * pr.num_terms
+            ex = sum(a * sampled_entries(G, Us, idx) for a, (G, Us) in zip(alpha, pr.terms()))
+            scale = float(_np.sqrt(_np.mean(ex ** 2)))
             worst = max(worst, float(_np.sqrt(_np.mean((em - ed) ** 2)) / _np.sqrt(_np.mean(ed ** 2))))
+            trunc_m = float(_np.sqrt(_np.mean((em - ex) ** 2)))
+            trunc_d = float(_np.sqrt(_np.mean((ed - ex) ** 2)))
+            worst_trunc = max(worst_trunc, abs(trunc_m - trunc_d) / scale)
         v64 = P * args.fp64_steps / el64
         fp64_path = {"value": v64 * world, "unit": UNIT, "ms_per_step": 1e3 * el64 / args.fp64_steps,
                      "steps": args.fp64_steps, "speedup": value / (v64 * world),
                      "rel_diff_sampled": worst,
                      "rel_diff_note": "rms difference of 256 sampled entries per problem (8 problems) of the "
-                                      "mixed and FP64 recompressed tensors, relative to the FP64 entries' rms"}
+                                      "mixed and FP64 recompressed tensors (same Gaussian draws), relative to "
+                                      "the FP64 entries' rms",
+                     "trunc_err_diff_sampled": worst_trunc,
+                     "trunc_err_note": "|e_mixed - e_fp64| / rms(X) with e = rms(X~ - X) over the same entries "
+                                       "(X evaluated term by term): the accuracy target when the truncation is "
+                                       "far from exact and the kept subspace is not unique"}
         del plan64
 
     line = None

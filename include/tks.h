@@ -102,6 +102,11 @@ typedef struct {
   uint64_t seed;                /* key of the Gaussian draws (Philox4x64-10) */
   double trunc_tol;             /* 0: keep min(target_n, b_n) columns per mode; > 0: the
                                    relative tolerance rule of Alg. 2, capped by the target */
+  int32_t omega_lowprec;        /* 0: the precision's own Gaussian draws (float64 Box-Muller for
+                                   TKS_FP64, float32 rounded to bfloat16 for the mixed modes);
+                                   1: the mixed modes' draws for every precision, so that a
+                                   TKS_FP64 plan computes with the Omega of a mixed plan (an
+                                   arithmetic-only comparison of the two) */
 } tks_params;
 
 typedef struct tks_plan tks_plan;

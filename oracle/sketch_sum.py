@@ -16,7 +16,7 @@ follows the paper's stages in order:
            core projection paragraph)
   stage 4  ST-HOSVD(H) (Alg. 2, phase 2), U~_n = Q_n P_n
 
-Readings where the paper is silent or inconsistent (listed in the design doc):
+Readings where the paper is silent or inconsistent:
 * the paper's d (number of summands) is K here and its N (order) is d;
 * effective ranks: ell_n = target_rank_n + oversampling_n replaces Alg. 5
   phase 1; the final truncation keeps min(target_n, columns of Q_n), or the
@@ -191,7 +191,7 @@ def st_hosvd(H, target=None, tol=0.0):
 
 # ---------------------------------------------------------------- full method
 def scaled_terms(terms, alpha=None):
-    """Fold term weights into the cores (Alg. 1, lines 1-2)."""
+    """Fold term weights into the cores, as TuckerAxby (Alg. 1) scales them."""
     if alpha is None:
         return list(terms)
     return [(a * G, Us) for a, (G, Us) in zip(alpha, terms)]

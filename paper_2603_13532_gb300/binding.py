@@ -23,7 +23,7 @@ STATUS = {0: "TKS_OK", 1: "TKS_EINVAL", 2: "TKS_ENOMEM", 3: "TKS_ECUDA", 4: "TKS
 STEP_KINDS = {0: "omega", 1: "gemm", 2: "reduce", 3: "core_sketch", 4: "qr", 5: "eig", 6: "tc", 7: "simt",
               8: "core_sketch32", 9: "split", 10: "transpose", 11: "qr32", 12: "svd32", 13: "tsqr32",
               14: "core_sketch3", 15: "chain3", 16: "qr_smem32", 17: "project3",
-              18: "sketch3", 19: "qr_reg32", 20: "ttm32"}
+              18: "sketch3", 19: "qr_reg32", 20: "ttm32", 21: "fold4", 22: "project4"}
 
 
 class TksError(RuntimeError):
@@ -43,7 +43,7 @@ class Problem_t(ctypes.Structure):
 
 class Params_t(ctypes.Structure):
     _fields_ = [("sketch", ctypes.c_int), ("precision", ctypes.c_int), ("dtype", ctypes.c_int),
-                ("seed", ctypes.c_uint64), ("trunc_tol", ctypes.c_double)]
+                ("seed", ctypes.c_uint64), ("trunc_tol", ctypes.c_double), ("omega_lowprec", ctypes.c_int32)]
 
 
 class PlanInfo_t(ctypes.Structure):
@@ -167,7 +167,7 @@ def pack_inputs(problems, dtype, device, pin=False):
 class Plan:
     """A plan over a list of ``workloads.Problem`` with their device inputs."""
 
-    def __init__(self, problems, kind="krp", precision="fp64", seed=0, tol=0.0, device="cuda"):
+    def __init__(self, problems, kind="krp", precision="fp64", seed=0, tol=0.0, device="cuda", omega_lowprec=False):
         self.lib = load()
         self.problems = list(problems)
         self.kind, self.precision, self.seed, self.tol = kind, precision, seed, tol
@@ -188,7 +188,7 @@ class Plan:
             arr[i] = Problem_t(d, dims, p.num_terms, ranks, tgt, ovs,
                                ctypes.cast(alpha, ctypes.POINTER(ctypes.c_double)) if alpha else None,
                                ctypes.c_void_p(core_t.data_ptr()), fptrs)
-        prm = Params_t(SKETCH[kind], PRECISION[precision], DTYPE[self.dtype], seed, tol)
+        prm = Params_t(SKETCH[kind], PRECISION[precision], DTYPE[self.dtype], seed, tol, int(omega_lowprec))
         handle = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             _check(self.lib.tks_plan_create(ctypes.byref(handle), arr, len(self.problems), ctypes.byref(prm)))

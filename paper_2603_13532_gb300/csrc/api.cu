@@ -48,7 +48,8 @@ Operand op_abs(const void* p, size_t off_bytes = 0) {
 }
 
 enum StepKind { S_OMEGA, S_GEMM, S_REDUCE, S_CORESKETCH, S_QR, S_EIG, S_TC, S_SIMT, S_CS32, S_SPLIT,
-                S_TRANSPOSE, S_QR32, S_SVD32, S_TSQR, S_CS3, S_CHAIN3, S_QRSM, S_PROJ3, S_SK3, S_QRREG, S_TTM };
+                S_TRANSPOSE, S_QR32, S_SVD32, S_TSQR, S_CS3, S_CHAIN3, S_QRSM, S_PROJ3, S_SK3, S_QRREG, S_TTM,
+                S_FOLD4, S_PROJ3F };
 
 struct Step {
   StepKind kind;
@@ -97,6 +98,9 @@ struct ProbHost {
   size_t AT32[MAXD] = {}, ATp[MAXD][3] = {}, Tp[3] = {};
   int ldU[MAXD] = {}, ldV[MAXD] = {}, ldA[MAXD] = {}, ldT = 0;
   bool fused3 = false;   // mixed path: order 3 with b_2, b_3 <= 64 -> fused projection kernel
+  bool fused4 = false;   // mixed path: order 4 with b_3, b_4 <= 64 -> fold + fused projection
+  size_t g4 = 0;         // workspace of the folded cores G'_k(a1) (float32)
+  std::vector<int64_t> g4_off;   // per term: float offset of its b_2 folded cores in g4
   size_t Wh = 0, tauh = 0, R32 = 0, P32[MAXD] = {}, sv[MAXD] = {};   // float32 ST-HOSVD
   size_t stk[2] = {};                                                 // TSQR stacked factors
   // backward of the core projection (order 3, float64)
@@ -417,9 +421,12 @@ static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
   std::vector<Sketch3Job> sk3;
   size_t sk3_smem = 0;
   double sk3_flops = 0.0;
-  std::vector<Proj3Job> p3;
-  std::vector<Proj3Term> p3terms;
-  double p3_flops = 0.0, p3_bytes = 0.0;
+  std::vector<Proj3Job> p3, p3f;
+  std::vector<Proj3Term> p3terms, p3fterms;
+  double p3_flops = 0.0, p3_bytes = 0.0, p3f_flops = 0.0, p3f_bytes = 0.0;
+  std::vector<Fold4Job> f4;
+  size_t f4_smem = 0;
+  double f4_flops = 0.0;
   size_t cs3_smem = 0, ch3_smem = 0;
   double cs3_flops = 0.0, ch3_flops = 0.0;
   constexpr size_t kSmemCap = 200 * 1024;
@@ -434,8 +441,8 @@ static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
   double cs_flops = 0.0;
   std::vector<QrJob> qr;
   double qr_flops = 0.0, qr_bytes = 0.0;
-  std::vector<SplitJob> sp;
-  int64_t sp_total = 0;
+  std::vector<SplitJob> sp, sp_all;
+  int64_t sp_total = 0, sp_all_total = 0;
   std::vector<std::vector<SimtJob>> chain(std::max(1, plan->dmax - 1));
   auto tc_job = [](int M, int N, int K) {
     TcJob j;
@@ -608,9 +615,8 @@ static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
       }
       qr_flops += 4.0 * (double)nn * h.b[n] * h.b[n];
       qr_bytes += 8.0 * (double)nn * (h.S[n] + h.b[n]);
-      if (planes_in_qr) {
-        planes_in_qr = false;
-      } else {
+      // Q -> bf16 planes: always when Q is given (tks_project_core); in the recompression only
+      // where the QR kernel did not write them itself
       SplitJob sj;
       std::memset(&sj, 0, sizeof(sj));
       sj.src = op(B_Q, h.q_off[n] * 8);
@@ -619,10 +625,15 @@ static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
       sj.cols = h.b[n];
       sj.ld_src = sj.ld_dst = (int64_t)nn;
       sj.count = sj.rows * sj.cols;
-      sj.begin = sp_total;
-      sp_total += sj.count;
-      sp.push_back(sj);
+      sj.begin = sp_all_total;
+      sp_all_total += sj.count;
+      sp_all.push_back(sj);
+      if (!planes_in_qr) {
+        sj.begin = sp_total;
+        sp_total += sj.count;
+        sp.push_back(sj);
       }
+      planes_in_qr = false;
       TcJob a6 = tc_job(h.R[n], h.b[n], (int)nn);
       a6.na = 1;
       a6.nb = 3;
@@ -637,7 +648,7 @@ static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
       a6.epi.f32 = op(B_WS, h.AT32[n]);
       a6.epi.f32_m = 1;
       a6.epi.f32_n = h.R[n];
-      if (n == d - 1 && !h.fused3) {
+      if (n == d - 1 && !h.fused3 && !h.fused4) {
         a6.epi.nbf = 3;
         for (int t = 0; t < 3; ++t) a6.epi.bf[t] = op(B_WS, h.ATp[n][t]);
         a6.epi.bf_m = 1;
@@ -675,9 +686,73 @@ static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
         j.rows = std::min(kProj3Rows, h.b[0] - x0);
         j.term_begin = tb;
         j.nterms = h.K;
+        j.hs1 = h.b[0];
+        j.hs2 = (int64_t)h.b[0] * h.b[1];
         p3.push_back(j);
       }
       p3_bytes += 8.0 * (double)h.b[0] * h.b[1] * h.b[2];
+      continue;
+    }
+    if (h.fused4) {
+      // fold mode 2 into the cores: G'_k(a1) = alpha_k G_k x_2 A_2k[a1, :] for every a1 < b_2,
+      // then H[:, a1, :, :] is the order-3 projection of the G'_k(a1) (modes 1, 3, 4)
+      const int b0 = h.b[0], b1 = h.b[1], b2 = h.b[2], b3 = h.b[3];
+      for (int k = 0; k < h.K; ++k) {
+        const int* r = &h.ranks[(size_t)k * d];
+        for (int i3 = 0; i3 < r[3]; ++i3) {
+          Fold4Job f;
+          std::memset(&f, 0, sizeof(f));
+          f.core = op_abs(h.cores, (size_t)h.core_off[k] * 2);
+          f.AT1 = op(B_WS, h.AT32[1]);
+          f.out = op(B_WS, h.g4 + (size_t)h.g4_off[k] * 4);
+          for (int q = 0; q < 4; ++q) f.r[q] = r[q];
+          f.R1 = h.R[1];
+          f.roff1 = h.roff[(size_t)k * d + 1];
+          f.b1 = b1;
+          f.alpha = (float)h.alpha[k];
+          f.i3 = i3;
+          f4.push_back(f);
+          f4_smem = std::max(f4_smem, fold4_smem_bytes(r[0], r[1], r[2], b1));
+        }
+        f4_flops += 2.0 * b1 * (double)r[0] * r[1] * r[2] * r[3];
+      }
+      for (int a1 = 0; a1 < b1; ++a1) {
+        const int tb = (int)p3fterms.size();
+        for (int k = 0; k < h.K; ++k) {
+          const int* r = &h.ranks[(size_t)k * d];
+          Proj3Term t;
+          std::memset(&t, 0, sizeof(t));
+          const int64_t blk = (int64_t)r[0] * r[2] * r[3];
+          t.core = op(B_WS, h.g4 + (size_t)(h.g4_off[k] + blk * a1) * 4);
+          const int modes[3] = {0, 2, 3};
+          for (int q = 0; q < 3; ++q) {
+            t.r[q] = r[modes[q]];
+            t.roff[q] = h.roff[(size_t)k * d + modes[q]];
+          }
+          t.alpha = 1.0f;
+          p3fterms.push_back(t);
+          p3f_flops += 2.0 * b0 * ((double)r[0] * r[2] * r[3] + (double)b2 * r[2] * r[3] + (double)b2 * b3 * r[3]);
+        }
+        for (int x0 = 0; x0 < b0; x0 += kProj3Rows) {
+          Proj3Job j;
+          std::memset(&j, 0, sizeof(j));
+          const int modes[3] = {0, 2, 3};
+          for (int q = 0; q < 3; ++q) {
+            j.AT[q] = op(B_WS, h.AT32[modes[q]]);
+            j.R[q] = h.R[modes[q]];
+            j.b[q] = h.b[modes[q]];
+          }
+          j.H = op(B_H, (h.h_off + (int64_t)b0 * a1) * 8);
+          j.x0 = x0;
+          j.rows = std::min(kProj3Rows, b0 - x0);
+          j.term_begin = tb;
+          j.nterms = h.K;
+          j.hs1 = (int64_t)b0 * b1;
+          j.hs2 = (int64_t)b0 * b1 * b2;
+          p3f.push_back(j);
+        }
+      }
+      p3f_bytes += 8.0 * (double)b0 * b1 * b2 * b3;
       continue;
     }
     // (c2) chains in float32; A_t^T block of term k: element (j, i) at (roff + i) + R_t j
@@ -788,7 +863,8 @@ static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
     plan->st_sketch.back().smem = sk3_smem;
   }
   plan->push_tc(plan->st_sketch, tcY, "a4:Y=Ucat.Vcat[tc]");
-  plan->push(plan->st_project, S_SPLIT, sp, sp_total, "a6:Q->planes", 0.0, 14.0 * sp_total);
+  plan->push(plan->st_project, S_SPLIT, sp_all, sp_all_total, "a6:Q->planes", 0.0, 14.0 * sp_all_total);
+  const size_t project_from = plan->st_project.size();   // the recompression takes its own split
   plan->push_tc(plan->st_project, tcA, "a6:AT=UcatT.Q[tc]");
   for (size_t t = 0; t < chain.size(); ++t) {
     char nm[32];
@@ -800,16 +876,24 @@ static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
     plan->st_project.back().smem = ch3_smem;
   }
   plan->push_tc(plan->st_project, tcH, "a8:H=Tcat.AT[tc]");
-  if (!p3.empty()) {
-    // one table: the jobs, then the term records they index
-    std::vector<char> blob(p3.size() * sizeof(Proj3Job) + p3terms.size() * sizeof(Proj3Term));
-    std::memcpy(blob.data(), p3.data(), p3.size() * sizeof(Proj3Job));
-    if (!p3terms.empty())
-      std::memcpy(blob.data() + p3.size() * sizeof(Proj3Job), p3terms.data(), p3terms.size() * sizeof(Proj3Term));
-    plan->st_project.push_back(make_step(S_PROJ3, plan->add_table(blob.data(), blob.size()), (int)p3.size(),
-                                         (int64_t)p3.size(), "a7:project3[f32]", p3_flops, p3_bytes));
+  // fused projections: one table each, the jobs followed by the term records they index
+  auto push_proj = [&](StepKind kind, const std::vector<Proj3Job>& jobs, const std::vector<Proj3Term>& terms,
+                       const char* name, double flops, double bytes) {
+    if (jobs.empty()) return;
+    std::vector<char> blob(jobs.size() * sizeof(Proj3Job) + terms.size() * sizeof(Proj3Term));
+    std::memcpy(blob.data(), jobs.data(), jobs.size() * sizeof(Proj3Job));
+    if (!terms.empty())
+      std::memcpy(blob.data() + jobs.size() * sizeof(Proj3Job), terms.data(), terms.size() * sizeof(Proj3Term));
+    plan->st_project.push_back(make_step(kind, plan->add_table(blob.data(), blob.size()), (int)jobs.size(),
+                                         (int64_t)jobs.size(), name, flops, bytes));
     plan->st_project.back().smem = proj3_smem_bytes();
+  };
+  push_proj(S_PROJ3, p3, p3terms, "a7:project3[f32]", p3_flops, p3_bytes);
+  if (!f4.empty()) {
+    plan->push(plan->st_project, S_FOLD4, f4, (int64_t)f4.size(), "a7:fold4[f32]", f4_flops, 0.0);
+    plan->st_project.back().smem = f4_smem;
   }
+  push_proj(S_PROJ3F, p3f, p3fterms, "a7:project4[f32]", p3f_flops, p3f_bytes);
   plan->st_recompress = plan->st_sketch;
   plan->push(plan->st_recompress, S_QR, qr, (int64_t)qr.size(), "a5:qr", qr_flops, qr_bytes);
   plan->push(plan->st_recompress, S_QR32, qr32, (int64_t)qr32.size(), "a5:qr[f32]", qr_flops, qr_bytes);
@@ -823,7 +907,8 @@ static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
                0.0);
     plan->st_recompress.back().smem = qrsm_smem;
   }
-  for (const auto& st : plan->st_project) plan->st_recompress.push_back(st);
+  plan->push(plan->st_recompress, S_SPLIT, sp, sp_total, "a6:Q->planes", 0.0, 14.0 * sp_total);
+  for (size_t i = project_from; i < plan->st_project.size(); ++i) plan->st_recompress.push_back(plan->st_project[i]);
 }
 
 // ST-HOSVD of H in float32 (Alg. 2 phase 2, modes 1..d in order): per mode, Householder QR of
@@ -1106,6 +1191,7 @@ tks_status tks_plan_create(tks_plan** out, const tks_problem* problems, int32_t 
   const tks_params prm = *params;
   if (prm.sketch != TKS_SKETCH_KRP && prm.sketch != TKS_SKETCH_KRON) return fail(TKS_EINVAL, "bad sketch");
   if (!(prm.trunc_tol >= 0.0) || !std::isfinite(prm.trunc_tol)) return fail(TKS_EINVAL, "bad trunc_tol");
+  if (prm.omega_lowprec != 0 && prm.omega_lowprec != 1) return fail(TKS_EINVAL, "omega_lowprec must be 0 or 1");
   if (prm.precision == TKS_FP64) {
     if (prm.dtype != TKS_DT_F64) return fail(TKS_EINVAL, "TKS_FP64 needs float64 cores and factors");
   } else if (prm.precision == TKS_MIXED || prm.precision == TKS_MIXED_F32LA) {
@@ -1212,7 +1298,20 @@ tks_status tks_plan_create(tks_plan** out, const tks_problem* problems, int32_t 
       h.T = alloc((size_t)h.R[d - 1] * Pd * 8);
     } else {
       h.fused3 = d == 3 && h.b[1] <= 64 && h.b[2] <= 64;
-      if (!h.fused3) {
+      if (d == 4 && h.b[2] <= 64 && h.b[3] <= 64) {
+        bool fits = true;
+        int64_t per_a1 = 0;
+        h.g4_off.assign(h.K, 0);
+        for (int k = 0; k < h.K; ++k) {
+          const int* r = &h.ranks[(size_t)k * d];
+          fits = fits && fold4_smem_bytes(r[0], r[1], r[2], h.b[1]) <= 200 * 1024;
+          h.g4_off[k] = per_a1 * h.b[1];
+          per_a1 += (int64_t)r[0] * r[2] * r[3];
+        }
+        h.fused4 = fits;
+        if (fits) h.g4 = alloc((size_t)per_a1 * h.b[1] * 4);
+      }
+      if (!h.fused3 && !h.fused4) {
         // planes of A_d^T and of Tcat for the last-mode tensor-core product
         for (int t = 0; t < 3; ++t) h.ATp[d - 1][t] = alloc((size_t)h.ldA[d - 1] * h.b[d - 1] * 2);
         h.ldT = r8(h.R[d - 1]);
@@ -1298,7 +1397,7 @@ tks_status tks_plan_create(tks_plan** out, const tks_problem* problems, int32_t 
       oj.begin = om_blocks;
       oj.problem = p;
       oj.mode = m;
-      oj.bf16 = prm.precision == TKS_MIXED;
+      oj.bf16 = prm.omega_lowprec != 0;
       om_blocks += (oj.count + 3) / 4;
       om_ext.push_back(oj);
       // (a) M_m = Ucat_m^T Omega_m  (R_m x s_m)
@@ -1500,6 +1599,7 @@ tks_status tks_plan_create(tks_plan** out, const tks_problem* problems, int32_t 
     cudaError_t e = prepare_tc_gemm();
     if (e == cudaSuccess) e = prepare_order3_kernels();
     if (e == cudaSuccess) e = prepare_proj3();
+    if (e == cudaSuccess) e = prepare_fold4();
     if (e == cudaSuccess) e = prepare_sketch3();
     if (e == cudaSuccess) e = prepare_qr_reg_f32();
     if (e == cudaSuccess) e = prepare_ttm_rows();
@@ -1653,7 +1753,13 @@ tks_status run_steps(tks_plan* plan, const std::vector<Step>& steps, const Bases
         launch_sketch3(static_cast<const Sketch3Job*>(table), s.njobs, s.smem, bases, stream);
         break;
       case S_PROJ3:
-        launch_proj3(static_cast<const Proj3Job*>(table), s.njobs, bases, stream);
+        launch_proj3(static_cast<const Proj3Job*>(table), s.njobs, false, bases, stream);
+        break;
+      case S_PROJ3F:
+        launch_proj3(static_cast<const Proj3Job*>(table), s.njobs, true, bases, stream);
+        break;
+      case S_FOLD4:
+        launch_fold4(static_cast<const Fold4Job*>(table), s.njobs, s.smem, bases, stream);
         break;
     }
   }

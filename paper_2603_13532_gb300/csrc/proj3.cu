@@ -23,8 +23,8 @@ namespace {
 constexpr int kRows = kProj3Rows;    // mode-1 rows per CTA
 constexpr int kPad = 64;             // b2, b3 padded to 64
 constexpr int kChunk = 16;           // mode-3 indices per chunk (at most)
-constexpr int kGElems = 8192;        // bf16 core elements per chunk (at most)
-constexpr int kGBuf = kGElems + 16;  // + room for the 16-byte realignment of the slice
+constexpr int kGBytes = 16384;       // bytes of the core slice per chunk (at most)
+constexpr int kGBuf = kGBytes + 32;  // + room for the 16-byte realignment of the slice
 constexpr int kM = kRows * kPad;     // rows (a2, x) of the register block
 constexpr int kThreads = 256;
 constexpr int kR = TKS_MAX_RANK;
@@ -52,11 +52,17 @@ struct Smem {
   float A3[2][kChunk * kPad];       // [i2c][a2]
   float W1[kChunk * kR * kRows];    // [i2c][i1][x]
   float W2[kChunk * kM];            // [i2c][a1][x]
-  __align__(16) uint16_t G[2][kGBuf];   // core slice G[:, :, c0 : c0 + nc], realigned to 16 bytes
+  __align__(16) unsigned char G[2][kGBuf];   // core slice G[:, :, c0 : c0 + nc], realigned to 16 bytes
 };
 
 // Chunks of a term: r2 split into ceil(r2 / cmax) nearly equal pieces.
-__device__ __forceinline__ int chunk_max(const Proj3Term& T) { return min(kChunk, kGElems / (T.r[0] * T.r[1])); }
+template <typename CoreT>
+__device__ __forceinline__ int chunk_max(const Proj3Term& T) {
+  return min(kChunk, (int)(kGBytes / sizeof(CoreT)) / (T.r[0] * T.r[1]));
+}
+
+__device__ __forceinline__ float core_value(uint16_t h) { return bf16_float(h); }
+__device__ __forceinline__ float core_value(float v) { return v; }
 
 struct Pos {
   int k, c, nchunks;   // term, chunk of the term, chunks of the term
@@ -74,10 +80,12 @@ __device__ __forceinline__ void chunk_range(const Proj3Term& T, const Pos& p, in
 struct JobRegs {
   const float* AT[3];
   int64_t R[3];
+  int64_t hs1, hs2;
   int b[3];
   int x0, rows;
 };
 
+template <typename CoreT>
 __device__ __forceinline__ int issue_chunk(Smem& S, const JobRegs& J, const Proj3Term& T, const Pos& p, int buf,
                                            const Bases& bases) {
   const int tid = threadIdx.x;
@@ -106,23 +114,25 @@ __device__ __forceinline__ int issue_chunk(Smem& S, const JobRegs& J, const Proj
   }
   // the slice is contiguous: copy the 16-byte blocks that cover it (they lie in the pages of the
   // slice's own first and last bytes, so nothing outside mapped memory is touched)
-  const char* g = reinterpret_cast<const char*>(at<uint16_t>(bases, T.core) + (int64_t)r0 * r1 * c0);
+  const char* g = reinterpret_cast<const char*>(at<CoreT>(bases, T.core) + (int64_t)r0 * r1 * c0);
   const char* g16 = reinterpret_cast<const char*>(reinterpret_cast<uintptr_t>(g) & ~uintptr_t(15));
-  const int shift = (int)(g - g16) / 2;
-  const int blocks = (2 * (shift + r0 * r1 * nc) + 15) / 16;
-  for (int e = tid; e < blocks; e += kThreads) cp_async16(S.G[buf] + 8 * e, g16 + 16 * e);
+  const int shift = (int)(g - g16) / (int)sizeof(CoreT);
+  const int blocks = ((int)sizeof(CoreT) * (shift + r0 * r1 * nc) + 15) / 16;
+  for (int e = tid; e < blocks; e += kThreads) cp_async16(S.G[buf] + 16 * e, g16 + 16 * e);
   cp_async_commit();
   return shift;
 }
 
+template <typename CoreT>
 __device__ __forceinline__ bool advance(const Proj3Term* terms, int nterms, Pos& p) {
   if (++p.c < p.nchunks) return true;
   p.c = 0;
   if (++p.k >= nterms) return false;
-  p.nchunks = (terms[p.k].r[2] + chunk_max(terms[p.k]) - 1) / chunk_max(terms[p.k]);
+  p.nchunks = (terms[p.k].r[2] + chunk_max<CoreT>(terms[p.k]) - 1) / chunk_max<CoreT>(terms[p.k]);
   return true;
 }
 
+template <typename CoreT>
 __global__ void __launch_bounds__(kThreads, 2) project3_kernel(const Proj3Job* __restrict__ jobs, int njobs,
                                                                 Bases bases) {
   extern __shared__ __align__(16) unsigned char p3raw[];
@@ -139,6 +149,8 @@ __global__ void __launch_bounds__(kThreads, 2) project3_kernel(const Proj3Job* _
   }
   J.x0 = Jg.x0;
   J.rows = Jg.rows;
+  J.hs1 = Jg.hs1;
+  J.hs2 = Jg.hs2;
   double* const Hout = at<double>(bases, Jg.H);
   const int tid = threadIdx.x;
   const int tm = tid & 31, tn = tid >> 5;
@@ -158,8 +170,8 @@ __global__ void __launch_bounds__(kThreads, 2) project3_kernel(const Proj3Job* _
   __syncthreads();   // the zero fill lands before any copy into A1
 
   if (nterms > 0) {
-    Pos cur{0, 0, (terms[0].r[2] + chunk_max(terms[0]) - 1) / chunk_max(terms[0])};
-    int shift = issue_chunk(S, J, terms[0], cur, 0, bases);
+    Pos cur{0, 0, (terms[0].r[2] + chunk_max<CoreT>(terms[0]) - 1) / chunk_max<CoreT>(terms[0])};
+    int shift = issue_chunk<CoreT>(S, J, terms[0], cur, 0, bases);
     int buf = 0;
     bool more = true;
     while (more) {
@@ -170,20 +182,20 @@ __global__ void __launch_bounds__(kThreads, 2) project3_kernel(const Proj3Job* _
       cp_async_wait_all();
       __syncthreads();   // this chunk is in shared memory; every thread is done with the other buffers
       Pos nxt = cur;
-      more = advance(terms, nterms, nxt);
+      more = advance<CoreT>(terms, nterms, nxt);
       int next_shift = 0;
-      if (more) next_shift = issue_chunk(S, J, terms[nxt.k], nxt, buf ^ 1, bases);
+      if (more) next_shift = issue_chunk<CoreT>(S, J, terms[nxt.k], nxt, buf ^ 1, bases);
       const float alpha = T.alpha;
       const float* A1 = S.A1[cur.k & 1];
       const float* A2 = S.A2[cur.k & 1];
       const float* A3 = S.A3[buf];
-      const uint16_t* Gs = S.G[buf] + shift;
+      const CoreT* Gs = reinterpret_cast<const CoreT*>(S.G[buf]) + shift;
       // s1: pair p = i1 + r1 i2c reads the contiguous core column G[:, i1, c0 + i2c]
       for (int p = tid; p < nc * r1; p += kThreads) {
-        const uint16_t* g = Gs + r0 * p;
+        const CoreT* g = Gs + r0 * p;
         float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
         for (int i0 = 0; i0 < r0; ++i0) {
-          const float gv = bf16_float(g[i0]);
+          const float gv = core_value(g[i0]);
           const float4 a = *reinterpret_cast<const float4*>(A1 + kRows * i0);
           w.x = fmaf(a.x, gv, w.x);
           w.y = fmaf(a.y, gv, w.y);
@@ -260,7 +272,7 @@ __global__ void __launch_bounds__(kThreads, 2) project3_kernel(const Proj3Job* _
       for (int j = 0; j < 4; ++j) {
         const int a2 = 32 * nh + 4 * tn + j;
         if (a2 >= b2) continue;
-        double* dst = H + J.x0 + (int64_t)b0 * (a1 + (int64_t)b1 * a2);
+        double* dst = H + J.x0 + J.hs1 * a1 + J.hs2 * a2;
 #pragma unroll
         for (int x = 0; x < kRows; ++x)
           if (x < J.rows) dst[x] = (double)acc[h][x][nh][j];
@@ -270,16 +282,68 @@ __global__ void __launch_bounds__(kThreads, 2) project3_kernel(const Proj3Job* _
 
 constexpr size_t kSmemBytes = sizeof(Smem);
 
+// ----------------------------------------------------------------------------- order-4 fold
+// G'_k(a1)[i0, i2, i3] = alpha_k sum_i1 A_2k[a1, i1] G_k[i0, i1, i2, i3] for one i3 and all a1:
+// the slice G_k[:, :, :, i3] and the rows of A_2k go to shared memory; a thread forms outputs
+// (i0, i2, a1) with i0 fastest, so the writes run along the output's contiguous index.
+__global__ void __launch_bounds__(256) fold4_kernel(const Fold4Job* __restrict__ jobs, Bases bases) {
+  extern __shared__ __align__(16) float f4s[];
+  const Fold4Job& J = jobs[blockIdx.x];
+  const int r0 = J.r[0], r1 = J.r[1], r2 = J.r[2], r3 = J.r[3], b1 = J.b1, i3 = J.i3;
+  const int slice = r0 * r1 * r2;
+  float* A2 = f4s;                 // [a1][i1]
+  float* Gs = A2 + b1 * r1;        // [i0 + r0 (i1 + r1 i2)]
+  const uint16_t* G = at<uint16_t>(bases, J.core) + (int64_t)slice * i3;
+  const float* AT1 = at<float>(bases, J.AT1) + J.roff1;
+  const float alpha = J.alpha;
+  for (int e = threadIdx.x; e < b1 * r1; e += blockDim.x) {
+    const int i1 = e % r1, a1 = e / r1;
+    A2[a1 * r1 + i1] = alpha * AT1[i1 + J.R1 * a1];
+  }
+  for (int e = threadIdx.x; e < slice; e += blockDim.x) Gs[e] = bf16_float(G[e]);
+  __syncthreads();
+  float* out = at<float>(bases, J.out);
+  const int64_t blk = (int64_t)r0 * r2 * r3;
+  const int per_a1 = r0 * r2;
+  for (int e = threadIdx.x; e < b1 * per_a1; e += blockDim.x) {
+    const int a1 = e / per_a1, rem = e - a1 * per_a1;
+    const int i0 = rem % r0, i2 = rem / r0;
+    const float* g = Gs + i0 + r0 * r1 * i2;
+    const float* a = A2 + a1 * r1;
+    float v = 0.f;
+    for (int i1 = 0; i1 < r1; ++i1) v = fmaf(a[i1], g[r0 * i1], v);
+    out[blk * a1 + i0 + (int64_t)r0 * (i2 + (int64_t)r2 * i3)] = v;
+  }
+}
+
 }  // namespace
 
 size_t proj3_smem_bytes() { return kSmemBytes; }
 
 cudaError_t prepare_proj3() {
-  return cudaFuncSetAttribute(project3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+  cudaError_t e =
+      cudaFuncSetAttribute(project3_kernel<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(project3_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
 }
 
-void launch_proj3(const Proj3Job* jobs, int njobs, const Bases& bases, cudaStream_t stream) {
-  project3_kernel<<<njobs, kThreads, kSmemBytes, stream>>>(jobs, njobs, bases);
+size_t fold4_smem_bytes(int r0, int r1, int r2, int b1) {
+  return sizeof(float) * ((size_t)b1 * r1 + (size_t)r0 * r1 * r2);
+}
+
+cudaError_t prepare_fold4() {
+  return cudaFuncSetAttribute(fold4_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+
+void launch_fold4(const Fold4Job* jobs, int njobs, size_t smem, const Bases& bases, cudaStream_t stream) {
+  fold4_kernel<<<njobs, 256, smem, stream>>>(jobs, bases);
+}
+
+void launch_proj3(const Proj3Job* jobs, int njobs, bool f32_cores, const Bases& bases, cudaStream_t stream) {
+  if (f32_cores)
+    project3_kernel<float><<<njobs, kThreads, kSmemBytes, stream>>>(jobs, njobs, bases);
+  else
+    project3_kernel<uint16_t><<<njobs, kThreads, kSmemBytes, stream>>>(jobs, njobs, bases);
 }
 
 }  // namespace tks

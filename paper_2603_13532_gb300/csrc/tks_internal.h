@@ -153,13 +153,28 @@ struct Proj3Term {
 
 struct Proj3Job {
   Operand AT[3];         // float32 A_n^T = (Q_n^T Ucat_n)^T: element (i, a) at i + R_n a
-  Operand H;             // float64 H, element (a0, a1, a2) at a0 + b0 (a1 + b1 a2)
+  Operand H;             // float64 H, element (a0, a1, a2) at a0 + hs1 a1 + hs2 a2
   int32_t R[3], b[3];
   int32_t x0, rows;      // mode-1 rows [x0, x0 + rows), rows <= kProj3Rows
   int32_t term_begin, nterms;
-  int32_t pad[6];
+  int64_t hs1, hs2;      // strides of a1 and a2 in H (b0 and b0 b1 for an order-3 core)
+  int32_t pad[2];
 };
 static_assert(sizeof(Proj3Job) % 16 == 0 && sizeof(Proj3Term) % 16 == 0, "term records follow the jobs");
+
+// Order-4 problems on the fused projection: G'_k(a1) = alpha_k G_k x_2 A_2k[a1, :] (r0 x r2 x r3,
+// float32) for every row a1 of A_2k, so that H[:, a1, :, :] is the order-3 projection of the
+// G'_k(a1) with A_1k, A_3k, A_4k.  One CTA per (term, mode-4 index i3).
+struct Fold4Job {
+  Operand core;          // bf16 G_k, mode-1 fastest (r0, r1, r2, r3)
+  Operand AT1;           // float32 A_2^T: element (i, a) at i + R1 a, term rows from roff1
+  Operand out;           // float32; G'_k(a1)[i0, i2, i3] at out + a1 r0 r2 r3 + i0 + r0 (i2 + r2 i3)
+  int32_t r[4];
+  int64_t R1;
+  int32_t roff1, b1;
+  float alpha;
+  int32_t i3;
+};
 
 // Order-3 chain of one term for rows [a0, a0 + AB) of mode 1 (stage c2, float32):
 //   T[a0, a1, c] = alpha sum_{i0, i1} A1[a0, i0] A2[a1, i1] G[i0, i1, c]

@@ -83,6 +83,20 @@ def test_mixed_omega_matches_golden_heads(cuda_lib):
 
 
 @pytest.mark.parametrize("kind", ["krp", "kron"])
+def test_fp64_plan_with_the_mixed_draws_matches_the_oracle(cuda_lib, kind):
+    """omega_lowprec: a float64 plan on the mixed modes' Omega equals the oracle's low-precision
+    sketch to float64 accuracy (the bench compares the mixed and float64 paths this way)."""
+    from paper_2603_13532_gb300 import binding
+    probs = _bf16_problems(3, 4)
+    plan = binding.Plan(probs, kind=kind, precision="fp64", seed=15, omega_lowprec=True)
+    Ys = plan.sketch()
+    for i, prob in enumerate(probs):
+        ref = _oracle(prob, kind, 15, i)
+        for m in range(3):
+            assert _rel(Ys[i][m], ref["Y"][m]) <= 1e-12
+
+
+@pytest.mark.parametrize("kind", ["krp", "kron"])
 @pytest.mark.parametrize("d", [3, 4])
 def test_mixed_sketch_matches_oracle(cuda_lib, kind, d):
     probs = _bf16_problems(d)
@@ -145,6 +159,22 @@ def test_mixed_projection_order3_tile_edges(cuda_lib, kind):
     for H, r in zip(Hs, refs):
         assert H.shape == r["H"].shape
         assert _rel(H, r["H"]) <= 1e-5, _rel(H, r["H"])
+
+
+@pytest.mark.parametrize("precision", MODES)
+@pytest.mark.parametrize("d", [3, 4])
+def test_mixed_projection_of_an_arbitrary_given_basis(cuda_lib, precision, d):
+    """tks_project_core with caller-given orthonormal bases that no QR of this plan produced,
+    called on a fresh plan before any recompression: the bf16 planes of Q must come from the given
+    Q (the register QR writes them only inside the recompression)."""
+    probs = _bf16_problems(d, 3)
+    plan = _plan(probs, "krp", 13, precision=precision)
+    g = np.random.default_rng(14)
+    Qs = [[wl.haar(g, n, b) for n, b in zip(p.dims, pi.basis_cols)] for p, pi in zip(probs, plan.pinfo)]
+    Hs = plan.project(Qs)
+    for p, Q, H in zip(probs, Qs, Hs):
+        ref = ss.project_core(ss.scaled_terms(p.terms(), p.alpha), Q)
+        assert _rel(H, ref) <= 1e-5, _rel(H, ref)
 
 
 @pytest.mark.parametrize("precision", MODES)
