@@ -2,10 +2,11 @@
 //
 // One CTA computes one 128 x BN output tile of one job.  Warp 0 (one elected thread) streams
 // the bf16 planes of A and B through a ring of shared-memory stages with TMA (128-byte swizzle);
-// warp 1 allocates the TMEM accumulator and (one elected thread) issues tcgen05.mma for every
-// selected plane pair, 16 deep in k per instruction, releasing each stage with tcgen05.commit;
-// warps 2-5 read the accumulator back with tcgen05.ld (one TMEM lane quadrant each) and write
-// the requested outputs.  Every wait is bounded: on a timeout the kernel records TKS_ETIMEOUT,
+// warp 1 allocates kAcc TMEM accumulators and (one elected thread) issues tcgen05.mma for every
+// selected plane pair, 16 deep in k per instruction, k-block kb into accumulator kb % kAcc,
+// releasing each stage with tcgen05.commit; warps 2-5 read the accumulators back with
+// tcgen05.ld (one TMEM lane quadrant each), add them and write the requested outputs.
+// Every wait is bounded: on a timeout the kernel records TKS_ETIMEOUT,
 // drains its own copies and MMAs (again bounded), frees TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -22,6 +23,10 @@ constexpr int kBM = 128;
 constexpr int kBK = 64;                       // bf16 elements = 128 bytes = one swizzle row
 constexpr int kATile = kBM * kBK * 2;         // 16 KB
 constexpr long long kWaitCycles = 4000000000LL;   // about 2 s at 2 GHz
+// Partial accumulators in TMEM: k-block kb goes to accumulator kb % kAcc and the epilogue adds
+// them, so each float32 accumulator takes 1/kAcc of the K-steps (the rounding error of a long
+// contraction whose products share a sign grows with the number of steps).
+constexpr int kAcc = 4;
 
 __device__ __forceinline__ void record_status_tc(Status* st, int code) {
   if (st) atomicCAS(&st->code, 0, code);
@@ -69,7 +74,7 @@ __global__ void __launch_bounds__(192, 1)
     *err = 0;
     tc::fence_barrier_init();
   }
-  if (warp == 1) tc::tmem_alloc(tmem_slot, BN);
+  if (warp == 1) tc::tmem_alloc(tmem_slot, BN * kAcc);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
@@ -104,7 +109,6 @@ __global__ void __launch_bounds__(192, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       constexpr uint32_t idesc = tc::idesc_bf16_f32(kBM, BN);
-      uint32_t acc = 0;
       for (int kb = 0; kb < nk; ++kb) {
         const int s = kb % stages, round = kb / stages;
         if (*err || !tc::mbar_wait(&full[s], round & 1, kWaitCycles)) {
@@ -112,12 +116,15 @@ __global__ void __launch_bounds__(192, 1)
           break;
         }
         tc::fence_after_sync();
+        // k-block kb accumulates into accumulator kb % kAcc; its first block starts it at zero
+        const uint32_t d = tmem + (uint32_t)((kb % kAcc) * BN);
+        uint32_t acc = kb >= kAcc ? 1u : 0u;
         for (int p = 0; p < J.npairs; ++p) {
           const uint32_t a0 = tc::smem_u32(a_tile(s, J.pa[p]));
           const uint32_t b0 = tc::smem_u32(b_tile(s, J.pb[p]));
 #pragma unroll
           for (int k = 0; k < kBK / 16; ++k) {
-            tc::mma_bf16(tmem, tc::sw128_kmajor_desc(a0 + 32 * k), tc::sw128_kmajor_desc(b0 + 32 * k), idesc, acc);
+            tc::mma_bf16(d, tc::sw128_kmajor_desc(a0 + 32 * k), tc::sw128_kmajor_desc(b0 + 32 * k), idesc, acc);
             acc = 1;
           }
         }
@@ -140,19 +147,31 @@ __global__ void __launch_bounds__(192, 1)
       uint16_t* ob0 = E.nbf > 0 ? at<uint16_t>(bases, E.bf[0]) : nullptr;
       uint16_t* ob1 = E.nbf > 1 ? at<uint16_t>(bases, E.bf[1]) : nullptr;
       uint16_t* ob2 = E.nbf > 2 ? at<uint16_t>(bases, E.bf[2]) : nullptr;
+      const int nacc = nk < kAcc ? nk : kAcc;
 #pragma unroll
       for (int c0 = 0; c0 < BN; c0 += 32) {
-        uint32_t r[32];
-        tc::tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, r);
-        tc::tmem_ld_wait();
+        // the partial accumulators of this column chunk (kAcc - 1 float32 additions: negligible
+        // next to the K / (16 kAcc) roundings inside each accumulator; float64 arithmetic here
+        // would run at the FP64 rate)
+        float sum[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) sum[j] = 0.f;
+        for (int a = 0; a < nacc; ++a) {
+          uint32_t r[32];
+          tc::tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(a * BN + c0), r);
+          tc::tmem_ld_wait();
+#pragma unroll
+          for (int j = 0; j < 32; ++j) sum[j] += __uint_as_float(r[j]);
+        }
         if (row < J.M) {
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
             const int col = n0 + c0 + j;
             if (col >= J.N) continue;
-            const float v = E.alpha * __uint_as_float(r[j]);
+            const float v = E.alpha * sum[j];
+            const double vd = (double)v;
             if (o32) o32[row * E.f32_m + col * E.f32_n] = v;
-            if (o64) o64[row * E.f64_m + col * E.f64_n] = (double)v;
+            if (o64) o64[row * E.f64_m + col * E.f64_n] = vd;
             if (ob0) {
               const int64_t off = row * E.bf_m + col * E.bf_n;
               const uint16_t h0 = bf16_bits(v);
@@ -171,7 +190,7 @@ __global__ void __launch_bounds__(192, 1)
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (warp == 1) tc::tmem_dealloc(tmem, BN);
+  if (warp == 1) tc::tmem_dealloc(tmem, BN * kAcc);
   if (threadIdx.x == 0 && *err) record_status_tc(status, TKS_ETIMEOUT);
 }
 

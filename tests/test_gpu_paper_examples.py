@@ -59,8 +59,8 @@ def test_e1_shared_subspace_full_size_mixed(cuda_lib, precision):
     assert all(r <= 10 for r in got["ranks"])
     eg, ex, _ = _sampled(p, got)
     rel = np.sqrt(np.mean((eg - ex) ** 2) / np.mean(ex ** 2))
-    # the tensor-core products accumulate over n = 4000 in float32: 250 K-steps of 16, each rounding
-    # once, and in A_n = Q_n^T Ucat_n the products share a sign (U_k lies in the span of Q_n), so
-    # each contraction carries up to (n / 16) 2^-24 = 1.5e-5; three of them feed H (measured 4e-5,
-    # against 7e-6 for the same construction at n = 512)
-    assert rel <= 1e-4, rel
+    # the tensor-core products accumulate over n = 4000 in float32: 250 K-steps of 16 spread over
+    # four partial accumulators, each step rounding once, and in A_n = Q_n^T Ucat_n the products
+    # share a sign (U_k lies in the span of Q_n), so each contraction carries up to
+    # (n / 64) 2^-24 = 3.7e-6; three of them feed H (measured 1.1e-5; 4e-6 at n = 512)
+    assert rel <= 3e-5, rel
