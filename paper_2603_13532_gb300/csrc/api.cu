@@ -39,6 +39,7 @@ tks_status fail(tks_status st, const std::string& msg) {
 
 constexpr size_t kAlign = 256;
 constexpr int kTsqrBlockRows = 256;   // rows of one TSQR block (shared-memory Householder)
+constexpr size_t kSketch3F32Smem = 110 * 1024;   // largest float32-core sketch CTA (two per SM)
 inline size_t align_up(size_t x, size_t a = kAlign) { return (x + a - 1) / a * a; }
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
@@ -49,7 +50,7 @@ Operand op_abs(const void* p, size_t off_bytes = 0) {
 
 enum StepKind { S_OMEGA, S_GEMM, S_REDUCE, S_CORESKETCH, S_QR, S_EIG, S_TC, S_SIMT, S_CS32, S_SPLIT,
                 S_TRANSPOSE, S_QR32, S_SVD32, S_TSQR, S_CS3, S_CHAIN3, S_QRSM, S_PROJ3, S_SK3, S_QRREG, S_TTM,
-                S_FOLD4, S_PROJ3F };
+                S_FOLD4, S_PROJ3F, S_SK3F };
 
 struct Step {
   StepKind kind;
@@ -418,9 +419,9 @@ static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
   int64_t qrreg_rows = 0;
   std::vector<CoreSketchF32Job> cs3;
   std::vector<Chain3Job> ch3;
-  std::vector<Sketch3Job> sk3;
-  size_t sk3_smem = 0;
-  double sk3_flops = 0.0;
+  std::vector<Sketch3Job> sk3, sk3f;   // bf16 / float32 core copies in shared memory
+  size_t sk3_smem = 0, sk3f_smem = 0;
+  double sk3_flops = 0.0, sk3f_flops = 0.0;
   std::vector<Proj3Job> p3, p3f;
   std::vector<Proj3Term> p3terms, p3fterms;
   double p3_flops = 0.0, p3_bytes = 0.0, p3f_flops = 0.0, p3f_bytes = 0.0;
@@ -508,9 +509,17 @@ static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
           }
           j.s = h.s[0];
           j.alpha = (float)h.alpha[k];
-          sk3.push_back(j);
-          sk3_smem = std::max(sk3_smem, sketch3_smem_bytes(r));
-          sk3_flops += 2.0 * h.s[0] * (2.0 * r[0] * r[1] * r[2] + 2.0 * r[0] * r[1] + (double)r[1] * r[2]);
+          const double fl = 2.0 * h.s[0] * (2.0 * r[0] * r[1] * r[2] + 2.0 * r[0] * r[1] + (double)r[1] * r[2]);
+          // float32 core copies when two CTAs per SM still fit, else bf16 copies
+          if (sketch3_smem_bytes(r, true) <= kSketch3F32Smem) {
+            sk3f.push_back(j);
+            sk3f_smem = std::max(sk3f_smem, sketch3_smem_bytes(r, true));
+            sk3f_flops += fl;
+          } else {
+            sk3.push_back(j);
+            sk3_smem = std::max(sk3_smem, sketch3_smem_bytes(r, false));
+            sk3_flops += fl;
+          }
           continue;
         }
       }
@@ -858,8 +867,12 @@ static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
     plan->push(plan->st_sketch, S_CS3, cs3, (int64_t)cs3.size(), "a3:core_sketch3[f32]", cs3_flops, 0.0);
     plan->st_sketch.back().smem = cs3_smem;
   }
+  if (!sk3f.empty()) {
+    plan->push(plan->st_sketch, S_SK3F, sk3f, (int64_t)sk3f.size(), "a3:sketch3[f32]", sk3f_flops, 0.0);
+    plan->st_sketch.back().smem = sk3f_smem;
+  }
   if (!sk3.empty()) {
-    plan->push(plan->st_sketch, S_SK3, sk3, (int64_t)sk3.size(), "a3:sketch3[f32]", sk3_flops, 0.0);
+    plan->push(plan->st_sketch, S_SK3, sk3, (int64_t)sk3.size(), "a3:sketch3b[f32]", sk3_flops, 0.0);
     plan->st_sketch.back().smem = sk3_smem;
   }
   plan->push_tc(plan->st_sketch, tcY, "a4:Y=Ucat.Vcat[tc]");
@@ -1750,7 +1763,10 @@ tks_status run_steps(tks_plan* plan, const std::vector<Step>& steps, const Bases
         launch_chain3(static_cast<const Chain3Job*>(table), s.njobs, s.smem, bases, stream);
         break;
       case S_SK3:
-        launch_sketch3(static_cast<const Sketch3Job*>(table), s.njobs, s.smem, bases, stream);
+        launch_sketch3(static_cast<const Sketch3Job*>(table), s.njobs, s.smem, false, bases, stream);
+        break;
+      case S_SK3F:
+        launch_sketch3(static_cast<const Sketch3Job*>(table), s.njobs, s.smem, true, bases, stream);
         break;
       case S_PROJ3:
         launch_proj3(static_cast<const Proj3Job*>(table), s.njobs, false, bases, stream);

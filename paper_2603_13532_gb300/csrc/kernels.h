@@ -48,9 +48,11 @@ bool ttm_rows_fits(int b, int rmax);
 cudaError_t prepare_ttm_rows();
 void launch_ttm_rows(const TtmJob* jobs, int njobs, int total_tiles, const Bases& bases, cudaStream_t stream);
 // Khatri-Rao core sketches of order-3 terms, one CTA per term.
-size_t sketch3_smem_bytes(const int r[3]);
+// f32_core: the core copies in shared memory are float32 (faster, twice the shared memory).
+size_t sketch3_smem_bytes(const int r[3], bool f32_core);
 cudaError_t prepare_sketch3();
-void launch_sketch3(const Sketch3Job* jobs, int njobs, size_t smem, const Bases& bases, cudaStream_t stream);
+void launch_sketch3(const Sketch3Job* jobs, int njobs, size_t smem, bool f32_core, const Bases& bases,
+                    cudaStream_t stream);
 // Fused order-3 projection; `jobs` is followed in memory by the Proj3Term records.
 size_t proj3_smem_bytes();
 cudaError_t prepare_proj3();

@@ -31,6 +31,15 @@ constexpr int kBatch = 8;       // core elements loaded per thread before they a
 __device__ __forceinline__ float lo_bf16(uint32_t w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float hi_bf16(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
 
+// four consecutive core values starting at a 4-aligned index
+__device__ __forceinline__ float4 load4(const uint16_t* p) {
+  const uint2 pk = *reinterpret_cast<const uint2*>(p);
+  return make_float4(lo_bf16(pk.x), hi_bf16(pk.x), lo_bf16(pk.y), hi_bf16(pk.y));
+}
+__device__ __forceinline__ float4 load4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ uint16_t to_core(uint16_t h, uint16_t) { return h; }
+__device__ __forceinline__ float to_core(uint16_t h, float) { return __uint_as_float((uint32_t)h << 16); }
+
 __device__ __forceinline__ void store_planes(const Bases& bases, const Operand* planes, int64_t off, float v) {
   uint16_t h0, h1, h2;
   split3(v, h0, h1, h2);
@@ -39,6 +48,9 @@ __device__ __forceinline__ void store_planes(const Bases& bases, const Operand* 
   at<uint16_t>(bases, planes[2])[off] = h2;
 }
 
+// CoreT: the element type of the core copies in shared memory (float: converted once while
+// staging, so the contractions load 16 bytes per four values; bf16: half the shared memory).
+template <typename CoreT>
 __global__ void __launch_bounds__(kThreads) sketch3_term_kernel(const Sketch3Job* __restrict__ jobs, Bases bases) {
   extern __shared__ __align__(16) float s3s[];
   const Sketch3Job& J = jobs[blockIdx.x];
@@ -49,7 +61,7 @@ __global__ void __launch_bounds__(kThreads) sketch3_term_kernel(const Sketch3Job
   float* M0s = s3s;                                   // [i0][c]
   float* M1s = M0s + kMaxR * kCols;                   // [i1][c]
   float* V0p = M1s + kMaxR * kCols;                   // [grp][i0][c], partial sums of V_0
-  uint16_t* Gb = reinterpret_cast<uint16_t*>(V0p + kGroups * kMaxR * kCols);
+  CoreT* Gb = reinterpret_cast<CoreT*>(V0p + kGroups * kMaxR * kCols);
   const uint16_t* G = at<uint16_t>(bases, J.core);
   const float* Mg0 = at<float>(bases, J.M[0]) + J.roff[0];
   const float* Mg1 = at<float>(bases, J.M[1]) + J.roff[1];
@@ -67,7 +79,7 @@ __global__ void __launch_bounds__(kThreads) sketch3_term_kernel(const Sketch3Job
   // first-pass copy of the core: Gb[i2 + r2p (i0 + r0 i1)], zero for i2 in [r2, r2p)
   for (int e = tid; e < r0 * r1 * (r2p - r2); e += kThreads) {
     const int pad = e % (r2p - r2), rest = e / (r2p - r2);
-    Gb[r2 + pad + r2p * rest] = 0;
+    Gb[r2 + pad + r2p * rest] = CoreT(0);
   }
   for (int e0 = 0; e0 < tot; e0 += kBatch * kThreads) {
     // kBatch independent loads in flight per thread before the scattered shared-memory stores
@@ -82,7 +94,7 @@ __global__ void __launch_bounds__(kThreads) sketch3_term_kernel(const Sketch3Job
       const int e = e0 + u * kThreads + tid;
       if (e < tot) {
         const int i0 = e % r0, i1 = (e / r0) % r1, i2 = e / (r0 * r1);
-        Gb[i2 + r2p * (i0 + r0 * i1)] = v[u];
+        Gb[i2 + r2p * (i0 + r0 * i1)] = to_core(v[u], CoreT());
       }
     }
   }
@@ -109,11 +121,11 @@ __global__ void __launch_bounds__(kThreads) sketch3_term_kernel(const Sketch3Job
         for (int j = 0; j < 4; ++j) {
           // rows i0 >= r0 of the last quad read the next core fibre (or the padding); their z is unused
           const int i0 = min(4 * q0 + j, r0 - 1);
-          const uint2 pk = *reinterpret_cast<const uint2*>(Gb + r2p * (i0 + r0 * i1) + 4 * q2);
-          z[j] = fmaf(lo_bf16(pk.x), m2[4 * q2], z[j]);
-          z[j] = fmaf(hi_bf16(pk.x), m2[4 * q2 + 1], z[j]);
-          z[j] = fmaf(lo_bf16(pk.y), m2[4 * q2 + 2], z[j]);
-          z[j] = fmaf(hi_bf16(pk.y), m2[4 * q2 + 3], z[j]);
+          const float4 gv = load4(Gb + r2p * (i0 + r0 * i1) + 4 * q2);
+          z[j] = fmaf(gv.x, m2[4 * q2], z[j]);
+          z[j] = fmaf(gv.y, m2[4 * q2 + 1], z[j]);
+          z[j] = fmaf(gv.z, m2[4 * q2 + 2], z[j]);
+          z[j] = fmaf(gv.w, m2[4 * q2 + 3], z[j]);
         }
       }
 #pragma unroll
@@ -143,7 +155,7 @@ __global__ void __launch_bounds__(kThreads) sketch3_term_kernel(const Sketch3Job
   // second-pass copy: Gb[i0 + r0p (i1 + r1 i2)], zero for i0 in [r0, r0p)
   for (int e = tid; e < r1 * r2 * (r0p - r0); e += kThreads) {
     const int pad = e % (r0p - r0), rest = e / (r0p - r0);
-    Gb[r0 + pad + r0p * rest] = 0;
+    Gb[r0 + pad + r0p * rest] = CoreT(0);
   }
   for (int e0 = 0; e0 < tot; e0 += kBatch * kThreads) {
     uint16_t v[kBatch];
@@ -155,7 +167,7 @@ __global__ void __launch_bounds__(kThreads) sketch3_term_kernel(const Sketch3Job
 #pragma unroll
     for (int u = 0; u < kBatch; ++u) {
       const int e = e0 + u * kThreads + tid;
-      if (e < tot) Gb[e % r0 + r0p * (e / r0)] = v[u];
+      if (e < tot) Gb[e % r0 + r0p * (e / r0)] = to_core(v[u], CoreT());
     }
   }
   float m0[kMaxR];
@@ -167,16 +179,16 @@ __global__ void __launch_bounds__(kThreads) sketch3_term_kernel(const Sketch3Job
   for (int i2 = grp; i2 < r2; i2 += kGroups) {
     float acc = 0.f;
     for (int i1 = 0; i1 < r1; ++i1) {
-      const uint16_t* g = Gb + r0p * (i1 + r1 * i2);
+      const CoreT* g = Gb + r0p * (i1 + r1 * i2);
       float y[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
       for (int q0 = 0; q0 < kQuads; ++q0) {
         if (4 * q0 >= r0) continue;
-        const uint2 pk = *reinterpret_cast<const uint2*>(g + 4 * q0);
-        y[0] = fmaf(lo_bf16(pk.x), m0[4 * q0], y[0]);
-        y[1] = fmaf(hi_bf16(pk.x), m0[4 * q0 + 1], y[1]);
-        y[2] = fmaf(lo_bf16(pk.y), m0[4 * q0 + 2], y[2]);
-        y[3] = fmaf(hi_bf16(pk.y), m0[4 * q0 + 3], y[3]);
+        const float4 gv = load4(g + 4 * q0);
+        y[0] = fmaf(gv.x, m0[4 * q0], y[0]);
+        y[1] = fmaf(gv.y, m0[4 * q0 + 1], y[1]);
+        y[2] = fmaf(gv.z, m0[4 * q0 + 2], y[2]);
+        y[3] = fmaf(gv.w, m0[4 * q0 + 3], y[3]);
       }
       acc = fmaf((y[0] + y[1]) + (y[2] + y[3]), M1s[i1 * kCols + c], acc);
     }
@@ -186,18 +198,25 @@ __global__ void __launch_bounds__(kThreads) sketch3_term_kernel(const Sketch3Job
 
 }  // namespace
 
-size_t sketch3_smem_bytes(const int r[3]) {
+size_t sketch3_smem_bytes(const int r[3], bool f32_core) {
   const size_t r0p = (r[0] + 3) & ~3, r2p = (r[2] + 3) & ~3;
   const size_t g = std::max(r2p * r[0] * r[1], r0p * r[1] * r[2]);
-  return sizeof(float) * (2 + kGroups) * kMaxR * kCols + 2 * g;
+  return sizeof(float) * (2 + kGroups) * kMaxR * kCols + (f32_core ? 4 : 2) * g;
 }
 
 cudaError_t prepare_sketch3() {
-  return cudaFuncSetAttribute(sketch3_term_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaError_t e =
+      cudaFuncSetAttribute(sketch3_term_kernel<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(sketch3_term_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
-void launch_sketch3(const Sketch3Job* jobs, int njobs, size_t smem, const Bases& bases, cudaStream_t stream) {
-  sketch3_term_kernel<<<njobs, kThreads, smem, stream>>>(jobs, bases);
+void launch_sketch3(const Sketch3Job* jobs, int njobs, size_t smem, bool f32_core, const Bases& bases,
+                    cudaStream_t stream) {
+  if (f32_core)
+    sketch3_term_kernel<float><<<njobs, kThreads, smem, stream>>>(jobs, bases);
+  else
+    sketch3_term_kernel<uint16_t><<<njobs, kThreads, smem, stream>>>(jobs, bases);
 }
 
 }  // namespace tks
