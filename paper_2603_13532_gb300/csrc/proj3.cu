@@ -76,6 +76,22 @@ __device__ __forceinline__ void chunk_range(const Proj3Term& T, const Pos& p, in
 
 // Issue the asynchronous copies of one chunk (and, on its first chunk, of the term's A1 and A2)
 // into buffer `buf`; returns the element shift of the core slice inside its buffer.
+// Walks the elements e = tid, tid + kThreads, ... of a column-major (rows x cols) block as
+// (row, col) = (e % rows, e / rows) without a division per element.
+struct Walk {
+  int row, col, drow, dcol;
+  __device__ __forceinline__ Walk(int e, int rows)
+      : row(e % rows), col(e / rows), drow(kThreads % rows), dcol(kThreads / rows) {}
+  __device__ __forceinline__ void next(int rows) {
+    row += drow;
+    col += dcol;
+    if (row >= rows) {
+      row -= rows;
+      col += 1;
+    }
+  }
+};
+
 // The job's fields as registers.
 struct JobRegs {
   const float* AT[3];
@@ -97,21 +113,15 @@ __device__ __forceinline__ int issue_chunk(Smem& S, const JobRegs& J, const Proj
     const float* AT1 = J.AT[1] + T.roff[1];
     float* A1 = S.A1[p.k & 1];
     float* A2 = S.A2[p.k & 1];
-    for (int e = tid; e < r0 * J.rows; e += kThreads) {
-      const int i0 = e % r0, x = e / r0;
-      cp_async4(A1 + i0 * kRows + x, AT0 + i0 + J.R[0] * (J.x0 + x));
-    }
-    for (int e = tid; e < r1 * J.b[1]; e += kThreads) {
-      const int i1 = e % r1, a1 = e / r1;
-      cp_async4(A2 + i1 * kPad + a1, AT1 + i1 + J.R[1] * a1);
-    }
+    for (Walk w(tid, r0); w.col < J.rows; w.next(r0))
+      cp_async4(A1 + w.row * kRows + w.col, AT0 + w.row + J.R[0] * (J.x0 + w.col));
+    for (Walk w(tid, r1); w.col < J.b[1]; w.next(r1))
+      cp_async4(A2 + w.row * kPad + w.col, AT1 + w.row + J.R[1] * w.col);
   }
   const float* AT2 = J.AT[2] + T.roff[2] + c0;
   float* A3 = S.A3[buf];
-  for (int e = tid; e < nc * J.b[2]; e += kThreads) {
-    const int i2c = e % nc, a2 = e / nc;
-    cp_async4(A3 + i2c * kPad + a2, AT2 + i2c + J.R[2] * a2);
-  }
+  for (Walk w(tid, nc); w.col < J.b[2]; w.next(nc))
+    cp_async4(A3 + w.row * kPad + w.col, AT2 + w.row + J.R[2] * w.col);
   // the slice is contiguous: copy the 16-byte blocks that cover it (they lie in the pages of the
   // slice's own first and last bytes, so nothing outside mapped memory is touched)
   const char* g = reinterpret_cast<const char*>(at<CoreT>(bases, T.core) + (int64_t)r0 * r1 * c0);
