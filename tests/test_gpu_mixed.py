@@ -267,3 +267,32 @@ def test_mixed_rejects_unaligned_mode_size(cuda_lib):
     with pytest.raises(binding.TksError) as e:
         _plan(wl._finish([p], True), "krp", 1)
     assert e.value.code == 7
+
+
+@pytest.mark.parametrize("precision", ["fp64"] + MODES)
+@pytest.mark.parametrize("kind", ["krp", "kron"])
+@pytest.mark.parametrize("d", [5, 6])
+def test_high_order_recompress_matches_oracle(cuda_lib, precision, kind, d):
+    """Orders 5 and 6 (the generic chain path of every precision) against the oracle on the same
+    draws: entrywise for float64, and reconstruction plus truncation error for the mixed modes."""
+    g = np.random.default_rng(400 + d)
+    dims = [8, 16, 8, 16, 8, 8][:d]
+    cores, facs = [], []
+    for _ in range(3):
+        r = [int(x) for x in g.integers(1, 4, size=d)]
+        cores.append(g.standard_normal(r))
+        facs.append([g.standard_normal((n, ri)) for n, ri in zip(dims, r)])
+    prob = wl.Problem(dims, cores, facs, [3] * d, [2] * d, alpha=list(g.standard_normal(3)))
+    bf16 = precision != "fp64"
+    prob = wl._finish([prob], bf16)[0]
+    got = _plan([prob], kind, 21, precision=precision).recompress()[0]
+    ref = ss.recompress(prob.terms(), kind, prob.target, prob.oversampling, seed=21, alpha=prob.alpha,
+                        rounding="bf16" if bf16 else None)
+    assert got["ranks"] == ref["ranks"]
+    X = sum(a * tucker_full(G, Us) for a, (G, Us) in zip(prob.alpha, prob.terms()))
+    Xg = tucker_full(got["core"], got["factors"])
+    Xo = tucker_full(ref["core"], ref["factors"])
+    nx = np.linalg.norm(X)
+    tol = 1e-11 if precision == "fp64" else 1e-5
+    assert np.linalg.norm(Xg - Xo) / nx <= tol, np.linalg.norm(Xg - Xo) / nx
+    assert abs(np.linalg.norm(Xg - X) - np.linalg.norm(Xo - X)) / nx <= tol
