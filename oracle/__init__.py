@@ -10,10 +10,12 @@ Modules
   tensor      Kronecker / Khatri-Rao products, unfoldings, TTM, Tucker helpers
   sketch_sum  the method: sketch sizes, structured sketches, QR basis, core
               projection (and its gradient with Q fixed), ST-HOSVD, recompress
+  subrank     the effective subrank heuristic (Alg. 5): weighted Gram spectra,
+              effective ranks and the sketch sizes they give
 
 Every function is pinned by ``tests/test_oracle_*.py`` against something other
 than itself (numpy's Philox, brute-force dense sketches, closed-form recovery,
 invariants, finite differences).  Parity unpinned: none of the functions here;
 the randomized accuracy of the method itself is not bounded by the paper.
 """
-from . import rng, sketch_sum, tensor  # noqa: F401
+from . import rng, sketch_sum, subrank, tensor  # noqa: F401
