@@ -38,7 +38,6 @@ tks_status fail(tks_status st, const std::string& msg) {
   } while (0)
 
 constexpr size_t kAlign = 256;
-constexpr int kTsqrBlockRows = 256;   // rows of one TSQR block (shared-memory Householder)
 constexpr size_t kSketch3F32Smem = 110 * 1024;   // largest float32-core sketch CTA (two per SM)
 inline size_t align_up(size_t x, size_t a = kAlign) { return (x + a - 1) / a * a; }
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
@@ -956,7 +955,7 @@ static void build_hosvd_f32(tks_plan* plan) {
         int32_t stype = xt;
         int64_t L0 = L, s0 = 1, s1 = L * b, sc = L;
         for (int lvl = 0;; ++lvl) {
-          const int nblk = std::max(1, ceil_div(rows, kTsqrBlockRows));
+          const int nblk = std::max(1, ceil_div(rows, tsqr_block_rows(plan->bmax)));
           const int brows = ceil_div(rows, nblk);
           const bool final_level = (nblk == 1);
           const Operand dst = final_level ? op(B_WS, h.R32) : op(B_WS, h.stk[lvl & 1]);
@@ -1372,7 +1371,7 @@ tks_status tks_plan_create(tks_plan** out, const tks_problem* problems, int32_t 
       int64_t stack_rows = 0;
       for (int m = 0; m < d; ++m) {
         const int64_t rows = Hsz / h.b[m];
-        stack_rows = std::max<int64_t>(stack_rows, (int64_t)ceil_div(rows, kTsqrBlockRows) * h.b[m]);
+        stack_rows = std::max<int64_t>(stack_rows, (int64_t)ceil_div(rows, tsqr_block_rows(plan->bmax)) * h.b[m]);
       }
       h.stk[0] = alloc((size_t)stack_rows * bm * 4);
       h.stk[1] = alloc((size_t)stack_rows * bm * 4);
@@ -1744,7 +1743,8 @@ tks_status run_steps(tks_plan* plan, const std::vector<Step>& steps, const Bases
         launch_svd_f32(static_cast<const SvdJob*>(table), s.njobs, plan->bmax, bases, plan->status, stream);
         break;
       case S_TSQR:
-        launch_tsqr_f32(static_cast<const TsqrJob*>(table), s.njobs, kTsqrBlockRows, plan->bmax, bases, stream);
+        launch_tsqr_f32(static_cast<const TsqrJob*>(table), s.njobs, tsqr_block_rows(plan->bmax), plan->bmax, bases,
+                        stream);
         break;
       case S_TTM:
         launch_ttm_rows(static_cast<const TtmJob*>(table), s.njobs, (int)s.work, bases, stream);

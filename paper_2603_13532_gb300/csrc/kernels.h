@@ -80,6 +80,9 @@ void launch_qr_smem_f32(const QrF32Job* jobs, int njobs, size_t smem, const Base
                         cudaStream_t stream);
 // One TSQR level: each job factors one block of rows and writes its triangular factor.
 cudaError_t prepare_tsqr_f32();
+// Rows of one TSQR block for factors of at most max_cols columns (512 when the block fits in
+// registers with 16 rows per lane, else 256).
+int tsqr_block_rows(int max_cols);
 void launch_tsqr_f32(const TsqrJob* jobs, int njobs, int max_rows, int max_cols, const Bases& bases,
                      cudaStream_t stream);
 void launch_svd_f32(const SvdJob* jobs, int njobs, int bmax, const Bases& bases, Status* status,

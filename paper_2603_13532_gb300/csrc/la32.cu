@@ -33,7 +33,7 @@ __device__ float block_sum_f(float v, float* red) {
 }
 
 constexpr int kLoadBatch = 8;   // global loads in flight per thread when staging a block
-constexpr int kTsqrMaxRows = 256;   // rows of one TSQR block (at most; the planner uses 256)
+constexpr int kTsqrMaxRows = 512;   // rows of one TSQR block (at most; 32 x rows per lane)
 
 __device__ __forceinline__ float load_any(const char* base, int32_t type, int64_t idx) {
   if (type == T_F64) return (float)reinterpret_cast<const double*>(base)[idx];
@@ -435,15 +435,16 @@ __global__ void __launch_bounds__(kQrRegThreads, 1) qr_reg_f32_kernel(const QrF3
 // trailing matrix.
 constexpr int kTsqrThreads = 512;
 constexpr int kTsqrWarps = kTsqrThreads / 32;
-constexpr int kTsqrRowsPerLane = kTsqrMaxRows / 32;
 
-template <int kSlots>
-__global__ void __launch_bounds__(kTsqrThreads, kSlots <= 4 ? 2 : 1) tsqr_f32_kernel(const TsqrJob* __restrict__ jobs, Bases bases) {
+template <int kTsqrRowsPerLane, int kSlots>
+__global__ void __launch_bounds__(kTsqrThreads, kTsqrRowsPerLane * kSlots <= 32 ? 2 : 1)
+    tsqr_f32_kernel(const TsqrJob* __restrict__ jobs, Bases bases) {
+  constexpr int kBlockRows = 32 * kTsqrRowsPerLane;
   extern __shared__ float smem_t[];
-  __shared__ float vbuf[2][kTsqrMaxRows];
+  __shared__ float vbuf[2][kBlockRows];
   __shared__ float sh_tau[2];
   __shared__ float rdiag[32 * kSlots];
-  __shared__ int64_t rowoff[kTsqrMaxRows];
+  __shared__ int64_t rowoff[kBlockRows];
   const TsqrJob& J = jobs[blockIdx.x];
   const int m = J.rows, b = J.cols;
   const int ld = m + 1;
@@ -492,7 +493,7 @@ __global__ void __launch_bounds__(kTsqrThreads, kSlots <= 4 ? 2 : 1) tsqr_f32_ke
     }
   }
   const int kmax = m < b ? m : b;
-  if (warp == 0 && kmax > 0) reflector_publish(a[0], 0, m, vbuf[0], kTsqrMaxRows, &sh_tau[0], rdiag);
+  if (warp == 0 && kmax > 0) reflector_publish(a[0], 0, m, vbuf[0], kBlockRows, &sh_tau[0], rdiag);
   __syncthreads();
   for (int j = 0; j < kmax; ++j) {
     const float tau = sh_tau[j & 1];
@@ -512,7 +513,7 @@ __global__ void __launch_bounds__(kTsqrThreads, kSlots <= 4 ? 2 : 1) tsqr_f32_ke
           for (int u = 0; u < kTsqrRowsPerLane; ++u) a[sl][u] = fmaf(-w, vj[u], a[sl][u]);
         }
         if (l == j + 1 && l < kmax)
-          reflector_publish(a[sl], l, m, vbuf[(j + 1) & 1], kTsqrMaxRows, &sh_tau[(j + 1) & 1], rdiag);
+          reflector_publish(a[sl], l, m, vbuf[(j + 1) & 1], kBlockRows, &sh_tau[(j + 1) & 1], rdiag);
       }
     }
     __syncthreads();
@@ -759,13 +760,16 @@ cudaError_t prepare_qr_reg_f32() {
 cudaError_t prepare_tsqr_f32() {
   cudaError_t e = cudaFuncSetAttribute(qr_smem_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 222 * 1024);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(tsqr_f32_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(tsqr_f32_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(tsqr_f32_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(tsqr_f32_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+  const void* kernels[] = {
+      reinterpret_cast<const void*>(tsqr_f32_kernel<8, 2>), reinterpret_cast<const void*>(tsqr_f32_kernel<8, 3>),
+      reinterpret_cast<const void*>(tsqr_f32_kernel<8, 4>), reinterpret_cast<const void*>(tsqr_f32_kernel<8, 6>),
+      reinterpret_cast<const void*>(tsqr_f32_kernel<16, 2>), reinterpret_cast<const void*>(tsqr_f32_kernel<16, 3>),
+      reinterpret_cast<const void*>(tsqr_f32_kernel<16, 4>)};
+  for (const void* k : kernels) {
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 size_t qr_smem_bytes(int64_t n, int S) { return (size_t)(n * S + 3 * S) * sizeof(float); }
@@ -777,17 +781,22 @@ void launch_qr_smem_f32(const QrF32Job* jobs, int njobs, size_t smem, const Base
 
 void launch_tsqr_f32(const TsqrJob* jobs, int njobs, int max_rows, int max_cols, const Bases& bases,
                      cudaStream_t stream) {
-  // columns per warp: the smallest instantiation that covers max_cols
+  // rows per lane and columns per warp: the smallest instantiation that covers the block
   const size_t smem = tsqr_smem(max_rows, max_cols);
-  if (max_cols <= 2 * kTsqrWarps)
-    tsqr_f32_kernel<2><<<njobs, kTsqrThreads, smem, stream>>>(jobs, bases);
-  else if (max_cols <= 3 * kTsqrWarps)
-    tsqr_f32_kernel<3><<<njobs, kTsqrThreads, smem, stream>>>(jobs, bases);
-  else if (max_cols <= 4 * kTsqrWarps)
-    tsqr_f32_kernel<4><<<njobs, kTsqrThreads, smem, stream>>>(jobs, bases);
-  else
-    tsqr_f32_kernel<6><<<njobs, kTsqrThreads, smem, stream>>>(jobs, bases);
+  const int slots = max_cols <= 2 * kTsqrWarps ? 2 : max_cols <= 3 * kTsqrWarps ? 3 : max_cols <= 4 * kTsqrWarps ? 4 : 6;
+  if (max_rows <= 256) {
+    if (slots == 2) tsqr_f32_kernel<8, 2><<<njobs, kTsqrThreads, smem, stream>>>(jobs, bases);
+    else if (slots == 3) tsqr_f32_kernel<8, 3><<<njobs, kTsqrThreads, smem, stream>>>(jobs, bases);
+    else if (slots == 4) tsqr_f32_kernel<8, 4><<<njobs, kTsqrThreads, smem, stream>>>(jobs, bases);
+    else tsqr_f32_kernel<8, 6><<<njobs, kTsqrThreads, smem, stream>>>(jobs, bases);
+  } else {
+    if (slots == 2) tsqr_f32_kernel<16, 2><<<njobs, kTsqrThreads, smem, stream>>>(jobs, bases);
+    else if (slots == 3) tsqr_f32_kernel<16, 3><<<njobs, kTsqrThreads, smem, stream>>>(jobs, bases);
+    else tsqr_f32_kernel<16, 4><<<njobs, kTsqrThreads, smem, stream>>>(jobs, bases);
+  }
 }
+
+int tsqr_block_rows(int max_cols) { return max_cols <= 4 * kTsqrWarps ? 512 : 256; }
 
 size_t qr_reg_smem_bytes(int64_t n, int S) { return (size_t)(n * S) * sizeof(float); }
 
