@@ -14,6 +14,8 @@ Also reported on the same JSON line:
                 CUDA-event duration inside the timed region, against the measured peak
   cpu_baseline  the FP64 oracle timed on this host's cores on a bounded sample
   fp64_path     (mixed precision only) the plain FP64 GPU path on the same batch
+  subrank       the effective subrank heuristic (Alg. 5, float64) on the same batch: problems/s,
+                its float64 roofline, and the oracle's rate on a sample
   clocks        nvidia-smi SM clocks and throttle reasons sampled during the timed region
 
 ``--impl reference`` times the FP64 CPU oracle (the reference arm) instead.
@@ -55,6 +57,9 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--measure-peaks", action="store_true", help="print FP64/FP32/TF32/BF16 GEMM rates")
+    ap.add_argument("--no-subrank", action="store_true", help="skip the effective subrank (Alg. 5) leg")
+    ap.add_argument("--subrank-eps", type=float, default=1e-6, help="tolerance of the Alg. 5 leg")
+    ap.add_argument("--subrank-steps", type=int, default=3, help="timed calls of the Alg. 5 leg")
     return ap.parse_args()
 
 
@@ -209,6 +214,19 @@ def oracle_rate(problems, seed0, budget_s, kind, rounding):
     for i, p in enumerate(problems):
         ss.recompress(p.terms(), kind, p.target, p.oversampling, seed=seed0, problem=i, rounding=rounding,
                       alpha=p.alpha)
+        done += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return done / dt, done, dt
+
+
+def oracle_subrank_rate(problems, eps, budget_s):
+    """Problems/s of the FP64 oracle's effective subrank heuristic over a bounded sample."""
+    from oracle import subrank as sr
+    done, t0 = 0, time.perf_counter()
+    for p in problems:
+        sr.effective_subrank(p.terms(), eps, p.oversampling, alpha=p.alpha)
         done += 1
         if time.perf_counter() - t0 >= budget_s:
             break
@@ -530,6 +548,44 @@ def main():
                                        "far from exact and the kept subspace is not unique"}
         del plan64
 
+    # the effective subrank heuristic (Alg. 5) on the same batch and device inputs, float64
+    subrank = None
+    if not args.no_subrank:
+        sp = binding.SubrankPlan(problems, args.subrank_eps, dtype=plan.dtype, device=device, inputs=plan.inputs)
+        sr_rank = torch.zeros(P * binding.MAX_ORDER, dtype=torch.int32, device=device)
+        sr_ell = torch.zeros_like(sr_rank)
+
+        def run_subrank():
+            sp.run_raw(sr_rank, sr_ell)
+
+        run_subrank()
+        sp.sync()
+        el_sr = time_steps(run_subrank, args.subrank_steps, stream)
+        sp.sync()
+        el_sr = max_over_ranks(el_sr, device)
+        got = sr_rank.cpu().numpy().reshape(-1, binding.MAX_ORDER)
+        got = np.concatenate([got[i, :p.order] for i, p in enumerate(problems)])
+        achieved = sp.info.flops * args.subrank_steps / el_sr / 1e12
+        subrank = {"value": weak_scaling_rate(P, world, args.subrank_steps, el_sr), "unit": "problems/s",
+                   "ms_per_call": 1e3 * el_sr / args.subrank_steps, "steps": args.subrank_steps,
+                   "eps": args.subrank_eps, "launches_per_call": int(sp.info.launches),
+                   "max_gram_order": int(sp.info.max_dim),
+                   "ranks": {"min": int(got.min()), "mean": float(got.mean()), "max": int(got.max())},
+                   "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                "frac": achieved / FP64_PEAK_TFLOPS,
+                                "peak_source": "derived FP64: 152 SMs x 4 flop/clk x 2070 MHz",
+                                "flops_per_call": sp.info.flops,
+                                "flops_note": "Gram matrices 2 x contraction x m(m+1)/2 plus tridiagonalization "
+                                              "4/3 m^3 per (problem, mode), m = min(n, R)",
+                                "traffic": None}}
+        if rank == 0 and not args.no_cpu:
+            rate, done, dt = oracle_subrank_rate(problems, args.subrank_eps, args.cpu_seconds / 2)
+            subrank["cpu_baseline"] = {"value": rate, "unit": "problems/s", "cores": os.cpu_count(),
+                                       "kind": "oracle",
+                                       "sample": f"{done} of the {P} problems in {dt:.1f} s (numpy eigvalsh of "
+                                                 f"the R x R Gram matrices, LAPACK on all host cores)"}
+        del sp
+
     line = None
     if rank == 0:
         in_bytes = plan.flat_inputs.numel() * plan.flat_inputs.element_size()
@@ -550,7 +606,7 @@ def main():
                            "flops_per_step": plan.info.flops_lowprec + plan.info.flops_fp64,
                            "l2": f"inputs {in_bytes / 1e6:.0f} MB per GPU > L2 129 MB, no flush",
                            "parallelism": f"replicas x{world}"},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fp64_path": fp64_path,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fp64_path": fp64_path, "subrank": subrank,
                 "gpu_launches": int(plan.info.launches_recompress) * args.steps,
                 "timing": ("CUDA-graph replays of the whole recompression" if graph is not None
                            else "eager launches") + "; stage times from an eager pass with events",

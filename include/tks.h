@@ -239,6 +239,58 @@ TKS_API tks_status tks_profile_end(tks_plan* plan, tks_step_profile_t* out, int3
 TKS_API tks_status tucker_sum_sketch_noalloc(const tks_problem* problem, const tks_params* params, double* Y_out,
                                              void* stream);
 
+/* ---------------------------------------------------------------------------------------------
+ * Effective subrank heuristic (Alg. 5, Sec. 3.2 "Heuristic Subrank Selection"), the step before
+ * the sketch sizes of Alg. 3/4 when the ranks come from a tolerance instead of target ranks.
+ * For every problem and mode n, in float64:
+ *   V_n = [ w_1 U_1^(n), ..., w_K U_K^(n) ],  w_k = |alpha_k| ||G_k||_F
+ *   lambda = eigenvalues of V_n^T V_n, clamped at zero, descending
+ *   rank_n = min{ r >= 1 : sum_{j > r} lambda_j <= eps^2 / d * sum_j lambda_j }
+ *   ell_n = rank_n + p_n
+ * The library forms the smaller of V_n^T V_n (R_n x R_n) and V_n V_n^T (n_n x n_n): both have the
+ * same nonzero eigenvalues, and the zero ones change no sum of the rule.  The Gram matrix has
+ * order m_n = min(n_n, R_n) <= 2048 (TKS_EUNSUPPORTED otherwise).  Sketch sizes follow from ell
+ * exactly as in tks_plan_create: a plan whose problems carry target_ranks = ell and
+ * oversampling = 0 (with trunc_tol = eps for the final ST-HOSVD) runs Alg. 3/4 as printed.
+ *
+ * tks_subrank_plan_create reads problems as tks_plan_create does, except that target_ranks is
+ * ignored and oversampling gives p_n; of params only dtype (F64 or BF16 cores and factors) and
+ * trunc_tol (eps > 0) are used.  Host-only apart from one device allocation for the launch
+ * tables and the status word; synchronous.  On error *plan is set to NULL. */
+typedef struct tks_subrank_plan tks_subrank_plan;
+
+typedef struct {
+  size_t workspace_bytes;       /* device scratch of tks_effective_subrank (256-byte aligned) */
+  int64_t eigenvalue_elems;     /* float64 elements of the optional eigenvalue buffer */
+  int32_t num_problems;
+  int32_t launches;             /* kernel launches one tks_effective_subrank enqueues */
+  int32_t max_dim;              /* largest Gram order m over all problems and modes */
+  int32_t pad;
+  double flops;                 /* algorithmic float64 flops of one call: the Gram matrices
+                                   (2 x contraction x m(m+1)/2) and their tridiagonalization
+                                   (4/3 m^3) */
+} tks_subrank_info_t;
+
+TKS_API tks_status tks_subrank_plan_create(tks_subrank_plan** plan, const tks_problem* problems,
+                                           int32_t num_problems, const tks_params* params);
+TKS_API void tks_subrank_plan_destroy(tks_subrank_plan* plan);
+TKS_API tks_status tks_subrank_info(const tks_subrank_plan* plan, tks_subrank_info_t* info);
+/* Per mode of one problem (host arrays of TKS_MAX_ORDER entries, unused modes 0): the Gram order
+ * m_n and the element offset of its eigenvalues in the eigenvalue buffer. */
+TKS_API tks_status tks_subrank_problem_info(const tks_subrank_plan* plan, int32_t problem, int32_t* dims_out,
+                                            int64_t* eig_off_out);
+/* Enqueues the heuristic on stream.  ranks_out and ell_out (device, int32, [num_problems *
+ * TKS_MAX_ORDER], entry p*TKS_MAX_ORDER + n; entries n >= d are not written) receive rank_n and
+ * ell_n.  eigenvalues_out (device, float64, eigenvalue_elems, or NULL) receives each mode's m_n
+ * eigenvalues in descending order, unclamped, at the offsets of tks_subrank_problem_info.
+ * workspace: workspace_bytes of device memory, 256-byte aligned. */
+TKS_API tks_status tks_effective_subrank(tks_subrank_plan* plan, void* workspace, int32_t* ranks_out,
+                                         int32_t* ell_out, double* eigenvalues_out, void* stream);
+/* Synchronizes stream, then returns and clears the first error a kernel of this plan recorded
+ * (TKS_ENONFINITE for a NaN or Inf in a Gram matrix, TKS_ENOCONV when the tridiagonal QR steps hit
+ * their limit), else TKS_OK. */
+TKS_API tks_status tks_subrank_sync_status(tks_subrank_plan* plan, void* stream);
+
 TKS_API const char* tks_last_error(void);
 TKS_API const char* tks_status_string(tks_status status);
 

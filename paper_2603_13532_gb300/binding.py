@@ -68,6 +68,12 @@ class ProblemInfo_t(ctypes.Structure):
                 ("grad_core_off", ctypes.c_int64), ("grad_factor_off", I64x6)]
 
 
+class SubrankInfo_t(ctypes.Structure):
+    _fields_ = [("workspace_bytes", ctypes.c_size_t), ("eigenvalue_elems", ctypes.c_int64),
+                ("num_problems", ctypes.c_int32), ("launches", ctypes.c_int32), ("max_dim", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("flops", ctypes.c_double)]
+
+
 class StepProfile_t(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("kind", ctypes.c_int32), ("calls", ctypes.c_int32),
                 ("ms", ctypes.c_double), ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
@@ -107,9 +113,19 @@ def load(path=None):
     lib.tks_profile_begin.argtypes = [P, ctypes.c_int32]
     lib.tks_profile_end.argtypes = [P, ctypes.POINTER(StepProfile_t), ctypes.c_int32,
                                     ctypes.POINTER(ctypes.c_int32)]
+    lib.tks_subrank_plan_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(Problem_t), ctypes.c_int32,
+                                            ctypes.POINTER(Params_t)]
+    lib.tks_subrank_plan_destroy.argtypes = [P]
+    lib.tks_subrank_plan_destroy.restype = None
+    lib.tks_subrank_info.argtypes = [P, ctypes.POINTER(SubrankInfo_t)]
+    lib.tks_subrank_problem_info.argtypes = [P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                             ctypes.POINTER(ctypes.c_int64)]
+    lib.tks_effective_subrank.argtypes = [P, P, P, P, P, P]
+    lib.tks_subrank_sync_status.argtypes = [P, P]
     for name in ["tks_plan_create", "tks_plan_info", "tks_problem_info", "tks_generate_omega",
                  "tucker_sum_sketch", "tks_project_core", "tucker_sum_recompress", "tks_sync_status",
-                 "tks_profile_begin", "tks_profile_end"]:
+                 "tks_profile_begin", "tks_profile_end", "tks_subrank_plan_create", "tks_subrank_info",
+                 "tks_subrank_problem_info", "tks_effective_subrank", "tks_subrank_sync_status"]:
         getattr(lib, name).restype = ctypes.c_int
     _LIB = lib
     return lib
@@ -165,6 +181,25 @@ def pack_inputs(problems, dtype, device, pin=False):
     return flat, views
 
 
+def _problem_structs(problems, inputs, keep):
+    """tks_problem array over ``problems`` with device inputs ``inputs`` (from pack_inputs); the
+    host arrays it points to are appended to ``keep`` and must outlive the C call."""
+    arr = (Problem_t * len(problems))()
+    for i, (p, (core_t, facs)) in enumerate(zip(problems, inputs)):
+        d = p.order
+        dims = (ctypes.c_int64 * d)(*p.dims)
+        ranks = (ctypes.c_int32 * (p.num_terms * d))(*[r for rk in p.ranks() for r in rk])
+        tgt = (ctypes.c_int32 * d)(*p.target)
+        ovs = (ctypes.c_int32 * d)(*p.oversampling)
+        alpha = (ctypes.c_double * p.num_terms)(*p.alpha) if p.alpha is not None else None
+        fptrs = (ctypes.c_void_p * d)(*[f.data_ptr() for f in facs])
+        keep += [dims, ranks, tgt, ovs, alpha, fptrs]
+        arr[i] = Problem_t(d, dims, p.num_terms, ranks, tgt, ovs,
+                           ctypes.cast(alpha, ctypes.POINTER(ctypes.c_double)) if alpha else None,
+                           ctypes.c_void_p(core_t.data_ptr()), fptrs)
+    return arr
+
+
 class Plan:
     """A plan over a list of ``workloads.Problem`` with their device inputs."""
 
@@ -176,19 +211,7 @@ class Plan:
         self.device = torch.device(device)
         self.flat_inputs, self.inputs = pack_inputs(self.problems, self.dtype, self.device)
         self._keep = []
-        arr = (Problem_t * len(self.problems))()
-        for i, (p, (core_t, facs)) in enumerate(zip(self.problems, self.inputs)):
-            d = p.order
-            dims = (ctypes.c_int64 * d)(*p.dims)
-            ranks = (ctypes.c_int32 * (p.num_terms * d))(*[r for rk in p.ranks() for r in rk])
-            tgt = (ctypes.c_int32 * d)(*p.target)
-            ovs = (ctypes.c_int32 * d)(*p.oversampling)
-            alpha = (ctypes.c_double * p.num_terms)(*p.alpha) if p.alpha is not None else None
-            fptrs = (ctypes.c_void_p * d)(*[f.data_ptr() for f in facs])
-            self._keep += [dims, ranks, tgt, ovs, alpha, fptrs]
-            arr[i] = Problem_t(d, dims, p.num_terms, ranks, tgt, ovs,
-                               ctypes.cast(alpha, ctypes.POINTER(ctypes.c_double)) if alpha else None,
-                               ctypes.c_void_p(core_t.data_ptr()), fptrs)
+        arr = _problem_structs(self.problems, self.inputs, self._keep)
         prm = Params_t(SKETCH[kind], PRECISION[precision], DTYPE[self.dtype], seed, tol, int(omega_lowprec))
         handle = ctypes.c_void_p()
         with torch.cuda.device(self.device):
@@ -378,3 +401,80 @@ class ProjectCore(torch.autograd.Function):
                 o = fac_v[m].storage_offset() - base
                 grad[o: o + nf] = df[pi.grad_factor_off[m]: pi.grad_factor_off[m] + nf]
         return grad, None, None
+
+
+class SubrankPlan:
+    """The effective subrank heuristic (Alg. 5) over a list of ``workloads.Problem``.
+
+    ``eps`` is the user tolerance; each problem's ``oversampling`` gives p_n (its ``target`` is
+    not used).  ``dtype`` is the element type the inputs are passed in ("fp64" or "bf16").
+    """
+
+    def __init__(self, problems, eps, dtype="fp64", device="cuda", inputs=None):
+        self.lib = load()
+        self.problems = list(problems)
+        self.eps, self.dtype = eps, dtype
+        self.device = torch.device(device)
+        if inputs is None:
+            self.flat_inputs, self.inputs = pack_inputs(self.problems, dtype, self.device)
+        else:
+            self.inputs = inputs
+        self._keep = []
+        arr = _problem_structs(self.problems, self.inputs, self._keep)
+        prm = Params_t(SKETCH["krp"], PRECISION["fp64"], DTYPE[dtype], 0, float(eps), 0)
+        handle = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(self.lib.tks_subrank_plan_create(ctypes.byref(handle), arr, len(self.problems), ctypes.byref(prm)))
+        self.handle = handle
+        self.info = SubrankInfo_t()
+        _check(self.lib.tks_subrank_info(handle, ctypes.byref(self.info)))
+        self.dims, self.eig_off = [], []
+        for i in range(len(self.problems)):
+            dims = (ctypes.c_int32 * MAX_ORDER)()
+            offs = (ctypes.c_int64 * MAX_ORDER)()
+            _check(self.lib.tks_subrank_problem_info(handle, i, dims, offs))
+            self.dims.append(list(dims))
+            self.eig_off.append(list(offs))
+        self.workspace = torch.empty(max(1, self.info.workspace_bytes), dtype=torch.uint8, device=self.device)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            self.lib.tks_subrank_plan_destroy(h)
+            self.handle = None
+
+    def run_raw(self, ranks, ell, evals=None):
+        _check(self.lib.tks_effective_subrank(self.handle, _ptr(self.workspace), _ptr(ranks), _ptr(ell),
+                                              _ptr(evals) if evals is not None else None, _stream_handle()))
+
+    def sync(self):
+        _check(self.lib.tks_subrank_sync_status(self.handle, _stream_handle()))
+
+    def run(self, eigenvalues=False):
+        """Per problem: dict(rank=[rank_n], ell=[ell_n], lam=[descending eigenvalues] or None)."""
+        n = len(self.problems) * MAX_ORDER
+        ranks = torch.zeros(n, dtype=torch.int32, device=self.device)
+        ell = torch.zeros(n, dtype=torch.int32, device=self.device)
+        ev = torch.zeros(max(1, self.info.eigenvalue_elems), dtype=torch.float64, device=self.device) \
+            if eigenvalues else None
+        self.run_raw(ranks, ell, ev)
+        self.sync()
+        rk = ranks.cpu().numpy().reshape(-1, MAX_ORDER)
+        el = ell.cpu().numpy().reshape(-1, MAX_ORDER)
+        host = ev.cpu().numpy() if eigenvalues else None
+        res = []
+        for i, p in enumerate(self.problems):
+            lam = None
+            if eigenvalues:
+                lam = [host[self.eig_off[i][m]: self.eig_off[i][m] + self.dims[i][m]] for m in range(p.order)]
+            res.append(dict(rank=[int(x) for x in rk[i, :p.order]], ell=[int(x) for x in el[i, :p.order]],
+                            lam=lam))
+        return res
+
+
+def with_sketch_ranks(problems, ells):
+    """Copies of ``problems`` whose plan sketches with ell_n from the subrank heuristic: target_n =
+    ell_n and oversampling 0 (so a Plan with ``tol=eps`` runs Alg. 3/4 as printed, the final
+    ST-HOSVD ranks capped at ell_n)."""
+    import dataclasses
+    return [dataclasses.replace(p, target=list(e), oversampling=[0] * p.order) for p, e in zip(problems, ells)]

@@ -2118,3 +2118,7 @@ extern "C" tks_status tucker_sum_sketch_noalloc(const tks_problem* problem, cons
   if (e != cudaSuccess) return fail(TKS_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
   return TKS_OK;
 }
+
+namespace tks {
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace tks

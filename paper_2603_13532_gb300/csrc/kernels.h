@@ -88,4 +88,16 @@ void launch_tsqr_f32(const TsqrJob* jobs, int njobs, int max_rows, int max_cols,
 void launch_svd_f32(const SvdJob* jobs, int njobs, int bmax, const Bases& bases, Status* status,
                     cudaStream_t stream);
 
+// Effective subrank heuristic (Alg. 5): term weights, weighted Gram tiles, tridiagonalization
+// (one CTA per matrix) and eigenvalues + rank rule (one CTA per matrix).
+constexpr int kSubrankMaxDim = 2048;   // largest Gram matrix, m = min(n, R)
+void launch_subrank_weights(const WeightJob* jobs, int njobs, const Bases& bases, cudaStream_t stream);
+void launch_gram_f64(const GramJob* jobs, int njobs, int total_tiles, const Bases& bases, cudaStream_t stream);
+cudaError_t prepare_subrank();
+// max_m: the largest m among the jobs of the launch (sizes shared memory and rows per thread)
+void launch_tridiag_f64(const SubrankJob* jobs, int njobs, int max_m, const Bases& bases, Status* status,
+                        cudaStream_t stream);
+void launch_subrank_eig(const SubrankJob* jobs, int njobs, int max_m, const Bases& bases, Status* status,
+                        cudaStream_t stream);
+
 }  // namespace tks

@@ -1,0 +1,447 @@
+// Effective subrank heuristic (Alg. 5, Sec. 3.2) in float64.
+//
+// Per (problem, mode n):  V_n = [w_1 U_1^(n), ..., w_K U_K^(n)] with w_k = ||alpha_k G_k||_F, the
+// Gram matrix of V_n, its eigenvalues (clamped at zero, descending), the threshold
+// tau = eps^2 / d * sum_j lambda_j and rank = min{r >= 1 : sum_{j > r} lambda_j <= tau}.
+//
+// Kernels:
+//   subrank_weight_kernel  one CTA per term: ||G_k||_F by a fixed-order block reduction, written
+//                          as the weight of each of the term's columns in every mode.
+//   gram_f64_kernel        64 x 64 float64 tiles of the lower triangle of V^T V (R <= n) or V V^T
+//                          (n < R; same nonzero eigenvalues, smaller matrix), mirrored.
+//   tridiag_f64_kernel     one CTA per matrix: Householder reduction to tridiagonal form.  The
+//                          rank-2 update of step k-1 and the matrix-vector product of step k are
+//                          one pass over the trailing block (a_ij -= v_i w_j + w_i v_j, then
+//                          p_i += a_ij v'_j), so the block is read and written once per step.
+//   subrank_eig_kernel     one CTA per matrix: implicit QR steps with Wilkinson shifts on the
+//                          tridiagonal matrix, sort, rank rule, ell = rank + p.
+// GB300 issues about two FP64 FMAs per SM per clock, so every kernel here is bound by FP64 issue;
+// the matrices (m <= 2048) stay in global memory and L2.
+#include <cuda_runtime.h>
+
+#include "bf16.cuh"
+#include "kernels.h"
+
+namespace tks {
+
+namespace {
+
+__device__ __forceinline__ void record_status(Status* st, int code) {
+  if (st) atomicCAS(&st->code, 0, code);
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over the block in a fixed order (deterministic); every thread gets the result.
+__device__ double block_sum_d(double v, double* red) {
+  v = warp_sum_d(v);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int w = 0; w < nw; ++w) s += red[w];
+  return s;
+}
+
+// ----------------------------------------------------------------------------- term weights
+constexpr int kWeightThreads = 256;
+
+__global__ void __launch_bounds__(kWeightThreads) subrank_weight_kernel(const WeightJob* __restrict__ jobs,
+                                                                        Bases bases) {
+  __shared__ double red[32];
+  const WeightJob& J = jobs[blockIdx.x];
+  double part = 0.0;
+  if (J.type == T_BF16) {
+    const uint16_t* g = at<uint16_t>(bases, J.core);
+    for (int64_t e = threadIdx.x; e < J.count; e += kWeightThreads) {
+      const double x = (double)bf16_float(g[e]);
+      part = fma(x, x, part);
+    }
+  } else {
+    const double* g = at<double>(bases, J.core);
+    for (int64_t e = threadIdx.x; e < J.count; e += kWeightThreads) part = fma(g[e], g[e], part);
+  }
+  const double w = fabs(J.alpha) * sqrt(block_sum_d(part, red));
+  for (int m = 0; m < J.d; ++m) {
+    double* wc = at<double>(bases, J.wcol[m]);
+    for (int i = threadIdx.x; i < J.r[m]; i += kWeightThreads) wc[i] = w;
+  }
+}
+
+// ----------------------------------------------------------------------------- Gram tiles
+constexpr int kGT = 64;        // output tile
+constexpr int kGK = 16;        // contraction chunk
+constexpr int kGThreads = 256; // 16 x 16 threads, 4 x 4 outputs each
+constexpr int kGPad = kGT + 2;
+
+__device__ __forceinline__ double load_typed(const char* base, int32_t type, int64_t idx) {
+  return type == T_BF16 ? (double)bf16_float(reinterpret_cast<const uint16_t*>(base)[idx])
+                        : reinterpret_cast<const double*>(base)[idx];
+}
+
+__global__ void __launch_bounds__(kGThreads) gram_f64_kernel(const GramJob* __restrict__ jobs, int njobs,
+                                                             Bases bases) {
+  __shared__ double As[kGK][kGPad];
+  __shared__ double Bs[kGK][kGPad];
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].tile_begin <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+  }
+  const GramJob& J = jobs[lo];
+  const int t = (int)blockIdx.x - J.tile_begin;
+  int ti = 0;
+  while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+  const int tj = t - ti * (ti + 1) / 2;
+  const int row0 = ti * kGT, col0 = tj * kGT, m = J.m;
+  const int64_t n = J.n;
+  const int64_t kc = J.aat ? (int64_t)J.R : n;   // contraction length
+  const char* U = at<char>(bases, J.U);
+  const double* wcol = at<double>(bases, J.wcol);
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+
+  for (int64_t k0 = 0; k0 < kc; k0 += kGK) {
+    if (!J.aat) {
+      // X(a, i) = U[i + n a]: tile column a of U, contraction over the rows i
+      for (int e = threadIdx.x; e < kGK * kGT; e += kGThreads) {
+        const int kk = e % kGK, a = e / kGK;
+        const int64_t i = k0 + kk;
+        const int ra = row0 + a, cb = col0 + a;
+        As[kk][a] = (i < kc && ra < m) ? load_typed(U, J.type, i + n * ra) : 0.0;
+        Bs[kk][a] = (i < kc && cb < m) ? load_typed(U, J.type, i + n * cb) : 0.0;
+      }
+    } else {
+      // X(i, c) = w_c U[i + n c]: tile row i of U, contraction over the columns c
+      for (int e = threadIdx.x; e < kGK * kGT; e += kGThreads) {
+        const int a = e % kGT, kk = e / kGT;
+        const int64_t c = k0 + kk;
+        const int ra = row0 + a, cb = col0 + a;
+        const double w = c < kc ? wcol[c] : 0.0;
+        As[kk][a] = (c < kc && ra < m) ? w * load_typed(U, J.type, ra + n * c) : 0.0;
+        Bs[kk][a] = (c < kc && cb < m) ? w * load_typed(U, J.type, cb + n * c) : 0.0;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kGK; ++kk) {
+      double av[4], bv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        av[i] = As[kk][ty * 4 + i];
+        bv[i] = Bs[kk][tx * 4 + i];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  double* B = at<double>(bases, J.B);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = row0 + ty * 4 + i;
+    if (r >= m) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = col0 + tx * 4 + j;
+      if (c >= m || c > r) continue;
+      const double v = J.aat ? acc[i][j] : wcol[r] * wcol[c] * acc[i][j];
+      B[r + (int64_t)m * c] = v;
+      B[c + (int64_t)m * r] = v;
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------- tridiagonalization
+constexpr int kTriThreads = 512;
+
+// Rows are owned by absolute index: thread t holds rows t + kTriThreads q, q < kRows, so the
+// previous step's v_i, w_i for its rows stay in registers from one step to the next.
+template <int kRows>
+__global__ void __launch_bounds__(kTriThreads, 1) tridiag_f64_kernel(const SubrankJob* __restrict__ jobs,
+                                                                    Bases bases, Status* status) {
+  extern __shared__ double tsm[];
+  __shared__ double red[32];
+  const SubrankJob& J = jobs[blockIdx.x];
+  const int m = J.m;
+  double* A = at<double>(bases, J.B);
+  double* dg = at<double>(bases, J.d);
+  double* eg = at<double>(bases, J.e);
+  double* vc = tsm;            // v of this step (rows k+1..m-1, v_{k+1} = 1)
+  double* vp = tsm + m;        // v of the previous step
+  double* wc = tsm + 2 * m;    // w of this step
+  double* wp = tsm + 3 * m;    // w of the previous step
+  const int tid = threadIdx.x;
+  double vpr[kRows], wpr[kRows], p[kRows];
+#pragma unroll
+  for (int q = 0; q < kRows; ++q) vpr[q] = wpr[q] = 0.0;
+  bool have_prev = false;
+  bool bad = false;
+  for (int k = 0; k + 1 < m; ++k) {
+    double* colk = A + (int64_t)m * k;
+    // column k, rows k..m-1: apply the previous step's update
+    if (have_prev) {
+      const double vk = vp[k], wk = wp[k];
+      for (int i = k + tid; i < m; i += kTriThreads) colk[i] = fma(-vp[i], wk, fma(-wp[i], vk, colk[i]));
+    }
+    __syncthreads();
+    // Householder reflector H = I - tau v v^T with H x = beta e_1, x = A[k+1:m, k]
+    double part = 0.0;
+    for (int i = k + 2 + tid; i < m; i += kTriThreads) part = fma(colk[i], colk[i], part);
+    const double sigma = block_sum_d(part, red);
+    const double alpha = colk[k + 1];
+    double tau = 0.0, beta = alpha, scale = 0.0;
+    if (sigma > 0.0) {
+      const double mu = sqrt(fma(alpha, alpha, sigma));
+      beta = alpha <= 0.0 ? mu : -mu;
+      tau = (beta - alpha) / beta;
+      scale = 1.0 / (alpha - beta);
+    }
+    if (!isfinite(sigma) || !isfinite(alpha)) bad = true;
+    if (tid == 0) {
+      dg[k] = colk[k];
+      eg[k] = beta;
+    }
+    for (int i = k + 1 + tid; i < m; i += kTriThreads) vc[i] = i == k + 1 ? 1.0 : colk[i] * scale;
+    __syncthreads();
+    // trailing block rows/cols k+1..m-1: pending update, then p = A v
+#pragma unroll
+    for (int q = 0; q < kRows; ++q) p[q] = 0.0;
+    if (have_prev || tau != 0.0) {
+      int j = k + 1;
+      for (; j + 4 <= m; j += 4) {
+        double a[4][kRows];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int q = 0; q < kRows; ++q) {
+            const int i = tid + q * kTriThreads;
+            a[u][q] = (i > k && i < m) ? A[i + (int64_t)m * (j + u)] : 0.0;
+          }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const double vj = vc[j + u], vpj = vp[j + u], wpj = wp[j + u];
+#pragma unroll
+          for (int q = 0; q < kRows; ++q) {
+            const int i = tid + q * kTriThreads;
+            if (i > k && i < m) {
+              double x = a[u][q];
+              if (have_prev) {
+                x = fma(-vpr[q], wpj, fma(-wpr[q], vpj, x));
+                A[i + (int64_t)m * (j + u)] = x;
+              }
+              p[q] = fma(x, vj, p[q]);
+            }
+          }
+        }
+      }
+      for (; j < m; ++j) {
+        const double vj = vc[j], vpj = vp[j], wpj = wp[j];
+#pragma unroll
+        for (int q = 0; q < kRows; ++q) {
+          const int i = tid + q * kTriThreads;
+          if (i > k && i < m) {
+            double x = A[i + (int64_t)m * j];
+            if (have_prev) {
+              x = fma(-vpr[q], wpj, fma(-wpr[q], vpj, x));
+              A[i + (int64_t)m * j] = x;
+            }
+            p[q] = fma(x, vj, p[q]);
+          }
+        }
+      }
+    }
+    // w = tau A v - (tau^2 / 2)(v^T A v) v
+    double pv = 0.0;
+#pragma unroll
+    for (int q = 0; q < kRows; ++q) {
+      const int i = tid + q * kTriThreads;
+      if (i > k && i < m) pv = fma(p[q], vc[i], pv);
+    }
+    const double vav = block_sum_d(pv, red);
+    const double half = 0.5 * tau * tau * vav;
+#pragma unroll
+    for (int q = 0; q < kRows; ++q) {
+      const int i = tid + q * kTriThreads;
+      if (i > k && i < m) {
+        const double w = fma(tau, p[q], -half * vc[i]);
+        wc[i] = w;
+        vpr[q] = vc[i];
+        wpr[q] = w;
+      }
+    }
+    have_prev = tau != 0.0;
+    double* t0 = vp; vp = vc; vc = t0;
+    double* t1 = wp; wp = wc; wc = t1;
+    __syncthreads();
+  }
+  if (tid == 0) {
+    dg[m - 1] = A[(int64_t)m * m - 1];
+    eg[m - 1] = 0.0;
+    if (!isfinite(dg[m - 1])) bad = true;
+  }
+  if (bad) record_status(status, TKS_ENONFINITE);
+}
+
+// ----------------------------------------------------------------------------- eigenvalues + rule
+constexpr int kEigThreads = 128;
+constexpr int kQrIterPerDim = 30;   // implicit QR steps allowed in total: 30 m
+
+// Eigenvalues of the symmetric tridiagonal matrix (a on the diagonal, b[i] coupling i and i+1)
+// by implicit QR steps with Wilkinson shifts (Golub and Van Loan, Sec. 8.3): each step chases
+// a bulge from the top of the unreduced block [lo, hi] to its bottom with plane rotations;
+// off-diagonals below u (|a_i| + |a_{i+1}|) are set to zero.  One thread; a[] ends up holding
+// the eigenvalues.  The step budget is global (30 m steps, as LAPACK's steqr allows): a block of
+// rounding-level entries below much larger ones can take a hundred steps to deflate its first
+// eigenvalue and then deflate the rest in one or two.  Returns false when the budget runs out.
+__device__ bool tridiag_eigenvalues(double* a, double* b, int m) {
+  const double u = 0x1p-53;
+  int hi = m - 1;
+  int64_t budget = (int64_t)kQrIterPerDim * m;
+  while (hi > 0) {
+    if (fabs(b[hi - 1]) <= u * (fabs(a[hi - 1]) + fabs(a[hi]))) {
+      b[hi - 1] = 0.0;
+      --hi;
+      continue;
+    }
+    int lo = hi - 1;
+    while (lo > 0 && fabs(b[lo - 1]) > u * (fabs(a[lo - 1]) + fabs(a[lo]))) --lo;
+    if (lo > 0) b[lo - 1] = 0.0;
+    if (--budget < 0) return false;
+    // shift: the eigenvalue of the trailing 2 x 2 block closer to a[hi]
+    const double bh = b[hi - 1];
+    const double delta = 0.5 * (a[hi - 1] - a[hi]);
+    const double den = delta + copysign(hypot(delta, bh), delta);
+    const double mu = a[hi] - bh * (bh / den);
+    double x = a[lo] - mu, z = b[lo];
+    for (int k = lo; k < hi; ++k) {
+      // rotation [c s; -s c] on rows/columns k, k+1 that maps (x, z) to (r, 0)
+      const double r = hypot(x, z);
+      double c = 1.0, s = 0.0;
+      if (r > 0.0) {
+        const double ri = 1.0 / r;
+        c = x * ri;
+        s = z * ri;
+      }
+      if (k > lo) b[k - 1] = r;
+      const double ak = a[k], ak1 = a[k + 1], bk = b[k];
+      const double cc = c * c, ss = s * s, cs2 = 2.0 * c * s * bk;
+      a[k] = fma(cc, ak, fma(ss, ak1, cs2));
+      a[k + 1] = fma(ss, ak, fma(cc, ak1, -cs2));
+      b[k] = fma(c * s, ak1 - ak, (cc - ss) * bk);
+      if (k + 1 < hi) {
+        z = s * b[k + 1];
+        b[k + 1] *= c;
+      }
+      x = b[k];
+    }
+  }
+  return true;
+}
+
+__global__ void __launch_bounds__(kEigThreads) subrank_eig_kernel(const SubrankJob* __restrict__ jobs, Bases bases,
+                                                                  Status* status) {
+  extern __shared__ double esm[];
+  __shared__ int sh_ok;
+  const SubrankJob& J = jobs[blockIdx.x];
+  const int m = J.m;
+  double* a = esm;
+  double* b = esm + m;
+  double* srt = esm + 2 * m;
+  const double* dg = at<double>(bases, J.d);
+  const double* eg = at<double>(bases, J.e);
+  for (int i = threadIdx.x; i < m; i += kEigThreads) {
+    a[i] = dg[i];
+    b[i] = i + 1 < m ? eg[i] : 0.0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) sh_ok = tridiag_eigenvalues(a, b, m) ? 1 : 0;
+  __syncthreads();
+  // descending order; ties keep the lower index first
+  for (int i = threadIdx.x; i < m; i += kEigThreads) {
+    const double x = a[i];
+    int pos = 0;
+    for (int j = 0; j < m; ++j) pos += (a[j] > x) || (a[j] == x && j < i);
+    srt[pos] = x;
+  }
+  __syncthreads();
+  double* ev = at<double>(bases, J.ev);
+  for (int i = threadIdx.x; i < m; i += kEigThreads) ev[i] = srt[i];
+  if (threadIdx.x == 0) {
+    bool finite = true;
+    double total = 0.0;
+    for (int i = m - 1; i >= 0; --i) {
+      finite = finite && isfinite(srt[i]);
+      total += fmax(srt[i], 0.0);
+    }
+    const double tau = J.eps * J.eps / J.order * total;
+    // the largest c <= m - 1 whose c smallest eigenvalues sum to at most tau; rank = m - c
+    double tail = 0.0;
+    int c = 0;
+    while (c < m - 1) {
+      const double next = tail + fmax(srt[m - 1 - c], 0.0);
+      if (!(next <= tau)) break;
+      tail = next;
+      ++c;
+    }
+    const int rank = m - c;
+    *at<int32_t>(bases, J.rank) = rank;
+    *at<int32_t>(bases, J.ell) = rank + J.p;
+    if (!finite) record_status(status, TKS_ENONFINITE);
+    else if (!sh_ok) record_status(status, TKS_ENOCONV);
+  }
+}
+
+}  // namespace
+
+void launch_subrank_weights(const WeightJob* jobs, int njobs, const Bases& bases, cudaStream_t stream) {
+  subrank_weight_kernel<<<njobs, kWeightThreads, 0, stream>>>(jobs, bases);
+}
+
+void launch_gram_f64(const GramJob* jobs, int njobs, int total_tiles, const Bases& bases, cudaStream_t stream) {
+  gram_f64_kernel<<<total_tiles, kGThreads, 0, stream>>>(jobs, njobs, bases);
+}
+
+constexpr size_t kTriSmem = 4 * kSubrankMaxDim * sizeof(double);
+constexpr size_t kEigSmem = 3 * kSubrankMaxDim * sizeof(double);
+
+cudaError_t prepare_subrank() {
+  cudaError_t e = cudaFuncSetAttribute(tridiag_f64_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTriSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(tridiag_f64_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTriSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(tridiag_f64_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTriSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(subrank_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEigSmem);
+  return e;
+}
+
+// max_m: the largest matrix of the launch (picks the rows each thread owns)
+void launch_tridiag_f64(const SubrankJob* jobs, int njobs, int max_m, const Bases& bases, Status* status,
+                        cudaStream_t stream) {
+  const size_t smem = 4 * (size_t)max_m * sizeof(double);
+  if (max_m <= kTriThreads)
+    tridiag_f64_kernel<1><<<njobs, kTriThreads, smem, stream>>>(jobs, bases, status);
+  else if (max_m <= 2 * kTriThreads)
+    tridiag_f64_kernel<2><<<njobs, kTriThreads, smem, stream>>>(jobs, bases, status);
+  else
+    tridiag_f64_kernel<4><<<njobs, kTriThreads, smem, stream>>>(jobs, bases, status);
+}
+
+void launch_subrank_eig(const SubrankJob* jobs, int njobs, int max_m, const Bases& bases, Status* status,
+                        cudaStream_t stream) {
+  subrank_eig_kernel<<<njobs, kEigThreads, 3 * (size_t)max_m * sizeof(double), stream>>>(jobs, bases, status);
+}
+
+}  // namespace tks

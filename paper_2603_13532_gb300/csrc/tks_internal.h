@@ -10,6 +10,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "tks.h"
 
 namespace tks {
@@ -28,7 +30,10 @@ enum BaseId : int32_t {
   B_HBAR = 7,    // backward: dL/dH
   B_DCORE = 8,   // backward: core gradients
   B_DFAC = 9,    // backward: factor gradients
-  NBASE = 10
+  B_EVALS = 10,  // effective subrank: eigenvalues of the weighted Gram matrices
+  B_SRANK = 11,  // effective subrank: ranks (int32)
+  B_ELL = 12,    // effective subrank: ell = rank + oversampling (int32)
+  NBASE = 13
 };
 
 struct Bases {
@@ -295,9 +300,48 @@ struct SvdJob {
   double tol;
 };
 
+// Effective subrank heuristic (Alg. 5), float64 throughout.
+//
+// Term weight w_k = |alpha_k| ||G_k||_F, written as the weight of each of the term's columns of
+// every Ucat_m (so the energy-weighted concatenation is V_m = Ucat_m diag(wcol_m)).
+struct WeightJob {
+  Operand core;           // typed (T_F64 / T_BF16), `count` elements
+  Operand wcol[MAXD];     // float64: this term's r_km column weights in mode m
+  int64_t count;
+  int32_t type, d;
+  int32_t r[MAXD];
+  double alpha;
+};
+
+// Weighted Gram matrix of one (problem, mode) in float64, computed in 64 x 64 tiles of the lower
+// triangle and mirrored:
+//   aat = 0:  B = W Ucat^T Ucat W     (m = R, used when R <= n)
+//   aat = 1:  B = Ucat W^2 Ucat^T     (m = n, used when n < R)
+// with W = diag(wcol).  The two products have the same nonzero eigenvalues.
+struct GramJob {
+  Operand U, wcol, B;     // U typed, n x R column-major (ld n); B m x m (ld m)
+  int64_t n;
+  int32_t R, m, type, aat;
+  int32_t tiles, tile_begin;   // T (T + 1) / 2 lower-triangle tiles, T = ceil(m / 64)
+};
+
+// Eigenvalues of one weighted Gram matrix and the rank rule of Alg. 5: Householder
+// tridiagonalization of B (overwritten) into diagonal d and off-diagonal e, implicit QR steps
+// on (d, e), then rank = min{r >= 1 : sum_{j > r} lambda_j <= eps^2 / order * sum_j lambda_j}
+// over the eigenvalues clamped at zero, and ell = rank + p.
+struct SubrankJob {
+  Operand B, d, e, ev;    // ev: the m eigenvalues in descending order (float64)
+  Operand rank, ell;      // int32 outputs
+  int32_t m, order, p, pad;
+  double eps;
+};
+
 struct Status {
   int32_t code;                 // first tks_status recorded by a kernel
   int32_t pad;
 };
+
+// Sets the thread-local message returned by tks_last_error (host code of every entry point).
+void set_last_error(const std::string& msg);
 
 }  // namespace tks

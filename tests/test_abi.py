@@ -111,3 +111,38 @@ def test_execute_rejects_null_plan(lib):
 def test_status_strings(lib):
     assert lib.tks_status_string(0) == b"TKS_OK"
     assert lib.tks_status_string(6) == b"TKS_ENOCONV"
+
+
+@pytest.mark.parametrize("mutate,eps,code", [
+    (lambda p, k: None, 0.0, 1),                          # the heuristic needs eps > 0
+    (lambda p, k: None, float("nan"), 1),
+    (lambda p, k: setattr(p, "order", 7), 1e-6, 1),
+    (lambda p, k: k["ranks"].__setitem__(2, 0), 1e-6, 1),
+    (lambda p, k: k["ovs"].__setitem__(1, -2), 1e-6, 1),
+    (lambda p, k: setattr(p, "cores", None), 1e-6, 1),
+])
+def test_subrank_plan_rejects_bad_arguments(lib, mutate, eps, code):
+    from paper_2603_13532_gb300 import binding
+    p, keep = _problem(binding)
+    mutate(p, keep)
+    prm = binding.Params_t(1, 0, 0, 1, eps)
+    h = ctypes.c_void_p()
+    assert lib.tks_subrank_plan_create(ctypes.byref(h), ctypes.byref(p), 1, ctypes.byref(prm)) == code
+    assert not h.value
+    assert lib.tks_last_error()
+
+
+def test_subrank_plan_rejects_oversized_gram(lib):
+    # min(n, R) = min(3000, 47 x 64) = 3000 > 2048: unsupported, reported before any device call
+    from paper_2603_13532_gb300 import binding
+    p, keep = _problem(binding, dims=(3000, 64, 64), ranks=tuple((64, 2, 2) for _ in range(47)))
+    h = ctypes.c_void_p()
+    prm = binding.Params_t(1, 0, 0, 1, 1e-6)
+    assert lib.tks_subrank_plan_create(ctypes.byref(h), ctypes.byref(p), 1, ctypes.byref(prm)) == 7
+    assert b"2048" in lib.tks_last_error()
+
+
+def test_subrank_execute_rejects_null_arguments(lib):
+    assert lib.tks_effective_subrank(None, None, None, None, None, None) == 1
+    assert lib.tks_subrank_info(None, None) == 1
+    assert lib.tks_subrank_sync_status(None, None) == 1
