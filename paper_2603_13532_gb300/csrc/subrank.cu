@@ -48,6 +48,18 @@ __device__ double block_sum_d(double v, double* red) {
   return s;
 }
 
+__device__ double block_max_d(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int w = 0; w < nw; ++w) s = fmax(s, red[w]);
+  return s;
+}
+
 // ----------------------------------------------------------------------------- term weights
 constexpr int kWeightThreads = 256;
 
@@ -196,19 +208,30 @@ __global__ void __launch_bounds__(kTriThreads, 1) tridiag_f64_kernel(const Subra
       for (int i = k + tid; i < m; i += kTriThreads) colk[i] = fma(-vp[i], wk, fma(-wp[i], vk, colk[i]));
     }
     __syncthreads();
-    // Householder reflector H = I - tau v v^T with H x = beta e_1, x = A[k+1:m, k]
-    double part = 0.0;
-    for (int i = k + 2 + tid; i < m; i += kTriThreads) part = fma(colk[i], colk[i], part);
-    const double sigma = block_sum_d(part, red);
+    // Householder reflector H = I - tau v v^T with H x = beta e_1, x = A[k+1:m, k]; the norm is
+    // taken of x scaled by a power of two near 1 / max |x_i| (no underflow or overflow of x_i^2)
+    double amax = 0.0;
+    for (int i = k + 1 + tid; i < m; i += kTriThreads) amax = fmax(amax, fabs(colk[i]));
+    amax = block_max_d(amax, red);
     const double alpha = colk[k + 1];
     double tau = 0.0, beta = alpha, scale = 0.0;
-    if (sigma > 0.0) {
-      const double mu = sqrt(fma(alpha, alpha, sigma));
-      beta = alpha <= 0.0 ? mu : -mu;
-      tau = (beta - alpha) / beta;
-      scale = 1.0 / (alpha - beta);
+    if (amax > 0.0 && isfinite(amax)) {
+      const double sc = ldexp(1.0, -ilogb(amax));
+      double part = 0.0;
+      for (int i = k + 2 + tid; i < m; i += kTriThreads) {
+        const double x = colk[i] * sc;
+        part = fma(x, x, part);
+      }
+      const double sigma = block_sum_d(part, red);
+      if (sigma > 0.0) {
+        const double as = alpha * sc;
+        const double mu = sqrt(fma(as, as, sigma)) / sc;
+        beta = alpha <= 0.0 ? mu : -mu;
+        tau = (beta - alpha) / beta;
+        scale = 1.0 / (alpha - beta);
+      }
     }
-    if (!isfinite(sigma) || !isfinite(alpha)) bad = true;
+    if (!isfinite(amax)) bad = true;
     if (tid == 0) {
       dg[k] = colk[k];
       eg[k] = beta;
@@ -300,39 +323,58 @@ constexpr int kQrIterPerDim = 30;   // implicit QR steps allowed in total: 30 m
 
 // Eigenvalues of the symmetric tridiagonal matrix (a on the diagonal, b[i] coupling i and i+1)
 // by implicit QR steps with Wilkinson shifts (Golub and Van Loan, Sec. 8.3): each step chases
-// a bulge from the top of the unreduced block [lo, hi] to its bottom with plane rotations;
-// off-diagonals below u (|a_i| + |a_{i+1}|) are set to zero.  One thread; a[] ends up holding
-// the eigenvalues.  The step budget is global (30 m steps, as LAPACK's steqr allows): a block of
-// rounding-level entries below much larger ones can take a hundred steps to deflate its first
-// eigenvalue and then deflate the rest in one or two.  Returns false when the budget runs out.
+// a bulge from the top of the unreduced block [lo, hi] to its bottom with plane rotations.
+// An off-diagonal is set to zero when it is below u (|a_i| + |a_{i+1}|) or below u ||T||: the
+// second (absolute) test perturbs every eigenvalue by at most u ||T||, the accuracy the
+// Householder reduction already has, and deflates the rounding-level part of a numerically
+// rank-deficient Gram matrix at once instead of iterating on noise.  The matrix is scaled by a
+// power of two so that ||T|| is about 1 and the rotations can use x^2 + z^2 without overflow.
+// One thread; a[] ends up holding the eigenvalues.  Returns false when the global budget of
+// 30 m steps (as LAPACK's steqr allows) runs out.
 __device__ bool tridiag_eigenvalues(double* a, double* b, int m) {
   const double u = 0x1p-53;
+  double tn = 0.0;
+  for (int i = 0; i < m; ++i) tn = fmax(tn, fabs(a[i]) + fabs(b[i]) + (i > 0 ? fabs(b[i - 1]) : 0.0));
+  if (!(tn > 0.0) || !isfinite(tn)) return isfinite(tn);
+  int ex;
+  frexp(tn, &ex);
+  const double down = ldexp(1.0, -ex), up = ldexp(1.0, ex);
+  for (int i = 0; i < m; ++i) {
+    a[i] *= down;
+    b[i] *= down;
+  }
+  const double thr = u * tn * down;
   int hi = m - 1;
   int64_t budget = (int64_t)kQrIterPerDim * m;
+  bool ok = true;
   while (hi > 0) {
-    if (fabs(b[hi - 1]) <= u * (fabs(a[hi - 1]) + fabs(a[hi]))) {
+    if (fabs(b[hi - 1]) <= fmax(thr, u * (fabs(a[hi - 1]) + fabs(a[hi])))) {
       b[hi - 1] = 0.0;
       --hi;
       continue;
     }
     int lo = hi - 1;
-    while (lo > 0 && fabs(b[lo - 1]) > u * (fabs(a[lo - 1]) + fabs(a[lo]))) --lo;
+    while (lo > 0 && fabs(b[lo - 1]) > fmax(thr, u * (fabs(a[lo - 1]) + fabs(a[lo])))) --lo;
     if (lo > 0) b[lo - 1] = 0.0;
-    if (--budget < 0) return false;
+    if (--budget < 0) {
+      ok = false;
+      break;
+    }
     // shift: the eigenvalue of the trailing 2 x 2 block closer to a[hi]
     const double bh = b[hi - 1];
     const double delta = 0.5 * (a[hi - 1] - a[hi]);
-    const double den = delta + copysign(hypot(delta, bh), delta);
+    const double den = delta + copysign(sqrt(fma(delta, delta, bh * bh)), delta);
     const double mu = a[hi] - bh * (bh / den);
     double x = a[lo] - mu, z = b[lo];
     for (int k = lo; k < hi; ++k) {
       // rotation [c s; -s c] on rows/columns k, k+1 that maps (x, z) to (r, 0)
-      const double r = hypot(x, z);
-      double c = 1.0, s = 0.0;
-      if (r > 0.0) {
-        const double ri = 1.0 / r;
+      const double r2 = fma(x, x, z * z);
+      double c = 1.0, s = 0.0, r = 0.0;
+      if (r2 > 0.0) {
+        const double ri = rsqrt(r2);
         c = x * ri;
         s = z * ri;
+        r = r2 * ri;
       }
       if (k > lo) b[k - 1] = r;
       const double ak = a[k], ak1 = a[k + 1], bk = b[k];
@@ -347,7 +389,8 @@ __device__ bool tridiag_eigenvalues(double* a, double* b, int m) {
       x = b[k];
     }
   }
-  return true;
+  for (int i = 0; i < m; ++i) a[i] *= up;
+  return ok;
 }
 
 __global__ void __launch_bounds__(kEigThreads) subrank_eig_kernel(const SubrankJob* __restrict__ jobs, Bases bases,

@@ -192,6 +192,15 @@ def test_edges(cuda_lib):
     terms = _random_terms(9, (30, 31, 32), 5, 2, 6)
     got = _gpu([_problem(terms, [0, 0, 0])], 50.0)[0]
     assert got["rank"] == [1, 1, 1]
+    # cores scaled by 1e-100 and 1e+100: Gram entries near 1e-200 and 1e+200 (the Householder norms
+    # and the tridiagonal QR are scaled internally); same ranks, eigenvalues scaled by 1e-+200
+    base = _gpu([_problem(terms, [0, 0, 0])], 1e-5)[0]
+    for f in (1e-100, 1e100):
+        got_s = _gpu([_problem([(f * G, Us) for G, Us in terms], [0, 0, 0])], 1e-5)[0]
+        ref_s = sr.effective_subrank([(f * G, Us) for G, Us in terms], 1e-5, [0, 0, 0])
+        assert got_s["rank"] == base["rank"] == ref_s["rank"]
+        for m in range(3):
+            _check_eigenvalues(got_s["lam"][m], ref_s["lam"][m])
     a = [1.0, -2.0, 0.5, -0.25, 3.0]
     got_p = _gpu([_problem(terms, [0, 0, 0], alpha=[abs(x) for x in a])], 1e-5)[0]
     got_n = _gpu([_problem(terms, [0, 0, 0], alpha=a)], 1e-5)[0]
