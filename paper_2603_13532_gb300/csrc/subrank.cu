@@ -200,6 +200,8 @@ __global__ void __launch_bounds__(kTriThreads, 1) tridiag_f64_kernel(const Subra
   for (int q = 0; q < kRows; ++q) vpr[q] = wpr[q] = 0.0;
   bool have_prev = false;
   bool bad = false;
+  bool stopped = false;
+  double delta = 0.0;
   for (int k = 0; k + 1 < m; ++k) {
     double* colk = A + (int64_t)m * k;
     // column k, rows k..m-1: apply the previous step's update
@@ -208,6 +210,32 @@ __global__ void __launch_bounds__(kTriThreads, 1) tridiag_f64_kernel(const Subra
       for (int i = k + tid; i < m; i += kTriThreads) colk[i] = fma(-vp[i], wk, fma(-wp[i], vk, colk[i]));
     }
     __syncthreads();
+    // Early end: the trailing block C = A[k:, k:] of the (positive semidefinite) Gram matrix, with
+    // the pending update, has sum |c_ii| <= delta.  Replacing C by zero moves the eigenvalues by a
+    // total of at most trace(C) (nuclear norm of a semidefinite perturbation), so every sum of the
+    // rank rule changes by at most delta = min(m u trace(B), 2^-10 tau): the rounding level of the
+    // reduction, and far below the threshold.  This skips the numerically zero part of a
+    // rank-deficient Gram matrix.
+    {
+      double part = 0.0;
+#pragma unroll
+      for (int q = 0; q < kRows; ++q) {
+        const int i = tid + q * kTriThreads;
+        if (i == k) part += fabs(colk[k]);
+        else if (i > k && i < m)
+          part += fabs(have_prev ? fma(-2.0 * vpr[q], wpr[q], A[i + (int64_t)m * i]) : A[i + (int64_t)m * i]);
+      }
+      const double trail = block_sum_d(part, red);
+      if (k == 0) delta = fmin(m * 0x1p-53 * trail, 0x1p-10 * J.eps * J.eps / J.order * trail);
+      if (trail <= delta) {
+        for (int i = k + tid; i < m; i += kTriThreads) {
+          dg[i] = 0.0;
+          eg[i] = 0.0;
+        }
+        stopped = true;
+        break;
+      }
+    }
     // Householder reflector H = I - tau v v^T with H x = beta e_1, x = A[k+1:m, k]; the norm is
     // taken of x scaled by a power of two near 1 / max |x_i| (no underflow or overflow of x_i^2)
     double amax = 0.0;
@@ -309,7 +337,7 @@ __global__ void __launch_bounds__(kTriThreads, 1) tridiag_f64_kernel(const Subra
     double* t1 = wp; wp = wc; wc = t1;
     __syncthreads();
   }
-  if (tid == 0) {
+  if (tid == 0 && !stopped) {
     dg[m - 1] = A[(int64_t)m * m - 1];
     eg[m - 1] = 0.0;
     if (!isfinite(dg[m - 1])) bad = true;
