@@ -287,8 +287,7 @@ TKS_API tks_status tks_subrank_problem_info(const tks_subrank_plan* plan, int32_
 TKS_API tks_status tks_effective_subrank(tks_subrank_plan* plan, void* workspace, int32_t* ranks_out,
                                          int32_t* ell_out, double* eigenvalues_out, void* stream);
 /* Synchronizes stream, then returns and clears the first error a kernel of this plan recorded
- * (TKS_ENONFINITE for a NaN or Inf in a Gram matrix, TKS_ENOCONV when the tridiagonal QR steps hit
- * their limit), else TKS_OK. */
+ * (TKS_ENONFINITE for a NaN or Inf in a Gram matrix), else TKS_OK. */
 TKS_API tks_status tks_subrank_sync_status(tks_subrank_plan* plan, void* stream);
 
 TKS_API const char* tks_last_error(void);

@@ -9,12 +9,13 @@
 //                          as the weight of each of the term's columns in every mode.
 //   gram_f64_kernel        64 x 64 float64 tiles of the lower triangle of V^T V (R <= n) or V V^T
 //                          (n < R; same nonzero eigenvalues, smaller matrix), mirrored.
-//   tridiag_f64_kernel     one CTA per matrix: Householder reduction to tridiagonal form.  The
-//                          rank-2 update of step k-1 and the matrix-vector product of step k are
-//                          one pass over the trailing block (a_ij -= v_i w_j + w_i v_j, then
-//                          p_i += a_ij v'_j), so the block is read and written once per step.
-//   subrank_eig_kernel     one CTA per matrix: implicit QR steps with Wilkinson shifts on the
-//                          tridiagonal matrix, sort, rank rule, ell = rank + p.
+//   tridiag_f64_kernel     one CTA per matrix: Householder reduction to tridiagonal form on the
+//                          lower triangle only: per step the pending rank-2 update of the previous
+//                          step (2 FMAs per stored element) and the symmetric product p = A v (each
+//                          stored element feeds two rows), 2 m^3 / 3 FMAs in all instead of m^3.
+//   subrank_eig_kernel     one CTA per matrix: the tridiagonal matrix's eigenvalues by bisection
+//                          with division-free Sturm counts (one eigenvalue per thread), rank rule,
+//                          ell = rank + p.
 // GB300 issues about two FP64 FMAs per SM per clock, so every kernel here is bound by FP64 issue;
 // the matrices (m <= 2048) stay in global memory and L2.
 #include <cuda_runtime.h>
@@ -266,50 +267,65 @@ __global__ void __launch_bounds__(kTriThreads, 1) tridiag_f64_kernel(const Subra
     }
     for (int i = k + 1 + tid; i < m; i += kTriThreads) vc[i] = i == k + 1 ? 1.0 : colk[i] * scale;
     __syncthreads();
-    // trailing block rows/cols k+1..m-1: pending update, then p = A v
+    // Trailing block rows/cols k+1..m-1, lower triangle only (the upper one is never read).
+    // Pass 1: the pending rank-2 update of step k-1, a_ij -= v_i w_j + w_i v_j for j <= i.
+    if (have_prev) {
 #pragma unroll
-    for (int q = 0; q < kRows; ++q) p[q] = 0.0;
-    if (have_prev || tau != 0.0) {
-      int j = k + 1;
-      for (; j + 4 <= m; j += 4) {
-        double a[4][kRows];
+      for (int q = 0; q < kRows; ++q) {
+        const int i = tid + q * kTriThreads;
+        if (i > k && i < m) {
+          double* row = A + i;
+          const double vi = vpr[q], wi = wpr[q];
+          int j = k + 1;
+          for (; j + 4 <= i + 1; j += 4) {
+            double x[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+            for (int u = 0; u < 4; ++u) x[u] = row[(int64_t)m * (j + u)];
 #pragma unroll
-          for (int q = 0; q < kRows; ++q) {
-            const int i = tid + q * kTriThreads;
-            a[u][q] = (i > k && i < m) ? A[i + (int64_t)m * (j + u)] : 0.0;
+            for (int u = 0; u < 4; ++u)
+              row[(int64_t)m * (j + u)] = fma(-vi, wp[j + u], fma(-wi, vp[j + u], x[u]));
           }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const double vj = vc[j + u], vpj = vp[j + u], wpj = wp[j + u];
-#pragma unroll
-          for (int q = 0; q < kRows; ++q) {
-            const int i = tid + q * kTriThreads;
-            if (i > k && i < m) {
-              double x = a[u][q];
-              if (have_prev) {
-                x = fma(-vpr[q], wpj, fma(-wpr[q], vpj, x));
-                A[i + (int64_t)m * (j + u)] = x;
-              }
-              p[q] = fma(x, vj, p[q]);
-            }
-          }
+          for (; j <= i; ++j) row[(int64_t)m * j] = fma(-vi, wp[j], fma(-wi, vp[j], row[(int64_t)m * j]));
         }
       }
-      for (; j < m; ++j) {
-        const double vj = vc[j], vpj = vp[j], wpj = wp[j];
+      __syncthreads();
+    }
+    // Pass 2: p = A v from the lower triangle: row i left of the diagonal (coalesced over the
+    // threads) and column i below it (contiguous for each thread).  Every thread reads m - k - 1
+    // elements per row it owns, and each stored element feeds two rows of p.
 #pragma unroll
-        for (int q = 0; q < kRows; ++q) {
-          const int i = tid + q * kTriThreads;
-          if (i > k && i < m) {
-            double x = A[i + (int64_t)m * j];
-            if (have_prev) {
-              x = fma(-vpr[q], wpj, fma(-wpr[q], vpj, x));
-              A[i + (int64_t)m * j] = x;
-            }
-            p[q] = fma(x, vj, p[q]);
+    for (int q = 0; q < kRows; ++q) p[q] = 0.0;
+    if (tau != 0.0) {
+#pragma unroll
+      for (int q = 0; q < kRows; ++q) {
+        const int i = tid + q * kTriThreads;
+        if (i > k && i < m) {
+          const double* row = A + i;
+          double s0 = 0.0, s1 = 0.0;
+          int j = k + 1;
+          for (; j + 4 <= i + 1; j += 4) {
+            double x[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) x[u] = row[(int64_t)m * (j + u)];
+            s0 = fma(x[0], vc[j], s0);
+            s1 = fma(x[1], vc[j + 1], s1);
+            s0 = fma(x[2], vc[j + 2], s0);
+            s1 = fma(x[3], vc[j + 3], s1);
           }
+          for (; j <= i; ++j) s0 = fma(row[(int64_t)m * j], vc[j], s0);
+          const double* col = A + (int64_t)m * i;
+          j = i + 1;
+          for (; j + 4 <= m; j += 4) {
+            double x[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) x[u] = col[j + u];
+            s0 = fma(x[0], vc[j], s0);
+            s1 = fma(x[1], vc[j + 1], s1);
+            s0 = fma(x[2], vc[j + 2], s0);
+            s1 = fma(x[3], vc[j + 3], s1);
+          }
+          for (; j < m; ++j) s1 = fma(col[j], vc[j], s1);
+          p[q] = s0 + s1;
         }
       }
     }
@@ -346,122 +362,139 @@ __global__ void __launch_bounds__(kTriThreads, 1) tridiag_f64_kernel(const Subra
 }
 
 // ----------------------------------------------------------------------------- eigenvalues + rule
-constexpr int kEigThreads = 128;
-constexpr int kQrIterPerDim = 30;   // implicit QR steps allowed in total: 30 m
+constexpr int kEigThreads = 256;
+constexpr int kBisectMaxIter = 64;
 
-// Eigenvalues of the symmetric tridiagonal matrix (a on the diagonal, b[i] coupling i and i+1)
-// by implicit QR steps with Wilkinson shifts (Golub and Van Loan, Sec. 8.3): each step chases
-// a bulge from the top of the unreduced block [lo, hi] to its bottom with plane rotations.
-// An off-diagonal is set to zero when it is below u (|a_i| + |a_{i+1}|) or below u ||T||: the
-// second (absolute) test perturbs every eigenvalue by at most u ||T||, the accuracy the
-// Householder reduction already has, and deflates the rounding-level part of a numerically
-// rank-deficient Gram matrix at once instead of iterating on noise.  The matrix is scaled by a
-// power of two so that ||T|| is about 1 and the rotations can use x^2 + z^2 without overflow.
-// One thread; a[] ends up holding the eigenvalues.  Returns false when the global budget of
-// 30 m steps (as LAPACK's steqr allows) runs out.
-__device__ bool tridiag_eigenvalues(double* a, double* b, int m) {
-  const double u = 0x1p-53;
-  double tn = 0.0;
-  for (int i = 0; i < m; ++i) tn = fmax(tn, fabs(a[i]) + fabs(b[i]) + (i > 0 ? fabs(b[i - 1]) : 0.0));
-  if (!(tn > 0.0) || !isfinite(tn)) return isfinite(tn);
-  int ex;
-  frexp(tn, &ex);
-  const double down = ldexp(1.0, -ex), up = ldexp(1.0, ex);
-  for (int i = 0; i < m; ++i) {
-    a[i] *= down;
-    b[i] *= down;
-  }
-  const double thr = u * tn * down;
-  int hi = m - 1;
-  int64_t budget = (int64_t)kQrIterPerDim * m;
-  bool ok = true;
-  while (hi > 0) {
-    if (fabs(b[hi - 1]) <= fmax(thr, u * (fabs(a[hi - 1]) + fabs(a[hi])))) {
-      b[hi - 1] = 0.0;
-      --hi;
-      continue;
-    }
-    int lo = hi - 1;
-    while (lo > 0 && fabs(b[lo - 1]) > fmax(thr, u * (fabs(a[lo - 1]) + fabs(a[lo])))) --lo;
-    if (lo > 0) b[lo - 1] = 0.0;
-    if (--budget < 0) {
-      ok = false;
-      break;
-    }
-    // shift: the eigenvalue of the trailing 2 x 2 block closer to a[hi]
-    const double bh = b[hi - 1];
-    const double delta = 0.5 * (a[hi - 1] - a[hi]);
-    const double den = delta + copysign(sqrt(fma(delta, delta, bh * bh)), delta);
-    const double mu = a[hi] - bh * (bh / den);
-    double x = a[lo] - mu, z = b[lo];
-    for (int k = lo; k < hi; ++k) {
-      // rotation [c s; -s c] on rows/columns k, k+1 that maps (x, z) to (r, 0)
-      const double r2 = fma(x, x, z * z);
-      double c = 1.0, s = 0.0, r = 0.0;
-      if (r2 > 0.0) {
-        const double ri = rsqrt(r2);
-        c = x * ri;
-        s = z * ri;
-        r = r2 * ri;
-      }
-      if (k > lo) b[k - 1] = r;
-      const double ak = a[k], ak1 = a[k + 1], bk = b[k];
-      const double cc = c * c, ss = s * s, cs2 = 2.0 * c * s * bk;
-      a[k] = fma(cc, ak, fma(ss, ak1, cs2));
-      a[k + 1] = fma(ss, ak, fma(cc, ak1, -cs2));
-      b[k] = fma(c * s, ak1 - ak, (cc - ss) * bk);
-      if (k + 1 < hi) {
-        z = s * b[k + 1];
-        b[k + 1] *= c;
-      }
-      x = b[k];
-    }
-  }
-  for (int i = 0; i < m; ++i) a[i] *= up;
-  return ok;
+__device__ __forceinline__ int sign_bit(double v) {
+  return (int)((unsigned long long)__double_as_longlong(v) >> 63);
+}
+__device__ __forceinline__ int exponent_bits(double v) {
+  return (int)(((unsigned long long)__double_as_longlong(v) >> 52) & 0x7ff);
 }
 
+// Number of eigenvalues smaller than x of the symmetric tridiagonal matrix with diagonal d and
+// squared off-diagonals e2 (n x n): the sign changes of the Sturm sequence of its leading
+// principal minors, p_i = (d_i - x) p_{i-1} - e2_{i-1} p_{i-2} with p_{-1} = 1 (Givens' bisection,
+// Wilkinson, The Algebraic Eigenvalue Problem, Ch. 5).  A zero p_i takes the sign opposite to
+// p_{i-1} (the limit of a small negative pivot).  The pair (p_{i-1}, p_i) is rescaled by 2^-+256
+// when p_i leaves [2^-256, 2^256], so nothing overflows or underflows; signs and exponents are
+// read from the bits.  Three float64 operations per row, no division: on GB300 a division is a
+// long chain of dependent float64 operations.
+__device__ int sturm_count(const double* d, const double* e2, int n, double x) {
+  double p0 = 1.0, p1 = d[0] - x;
+  int sp = (__double_as_longlong(p1) << 1) == 0 ? 1 : sign_bit(p1);
+  int cnt = sp;
+  for (int i = 1; i < n; ++i) {
+    double p2 = fma(d[i] - x, p1, -e2[i - 1] * p0);
+    const long long bits = __double_as_longlong(p2);
+    const int ex = (int)((bits >> 52) & 0x7ff);
+    if (ex > 1023 + 256) {
+      p2 *= 0x1p-256;
+      p1 *= 0x1p-256;
+    } else if (ex < 1023 - 256 && (bits << 1) != 0 && exponent_bits(p1) < 1023 + 256) {
+      p2 *= 0x1p+256;
+      p1 *= 0x1p+256;
+    }
+    const int s2 = (bits << 1) == 0 ? 1 - sp : (int)((unsigned long long)bits >> 63);
+    cnt += s2 != sp;
+    sp = s2;
+    p0 = p1;
+    p1 = p2;
+  }
+  return cnt;
+}
+
+__device__ double block_min_d(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double s = red[0];
+  for (int w = 1; w < nw; ++w) s = fmin(s, red[w]);
+  return s;
+}
+
+// Eigenvalues of the tridiagonal matrix by bisection, one eigenvalue per thread (every thread
+// runs the same Sturm recurrence on a different shift, so the block is throughput-bound rather
+// than bound by the latency of one long sequential chain), then the rank rule.  Rows after the
+// last nonzero diagonal or off-diagonal entry form an exact zero block (the early end of the
+// reduction) and contribute zero eigenvalues without bisection.
 __global__ void __launch_bounds__(kEigThreads) subrank_eig_kernel(const SubrankJob* __restrict__ jobs, Bases bases,
                                                                   Status* status) {
   extern __shared__ double esm[];
-  __shared__ int sh_ok;
+  __shared__ double red[32];
+  __shared__ int sh_last;
   const SubrankJob& J = jobs[blockIdx.x];
   const int m = J.m;
-  double* a = esm;
-  double* b = esm + m;
-  double* srt = esm + 2 * m;
+  double* d = esm;
+  double* e2 = esm + m;
+  double* lam = esm + 2 * m;
   const double* dg = at<double>(bases, J.d);
   const double* eg = at<double>(bases, J.e);
+  if (threadIdx.x == 0) sh_last = -1;
+  __syncthreads();
+  // active size, infinity norm (Gershgorin) of the active block
+  double tn = 0.0;
   for (int i = threadIdx.x; i < m; i += kEigThreads) {
-    a[i] = dg[i];
-    b[i] = i + 1 < m ? eg[i] : 0.0;
+    const double di = dg[i], ei = i + 1 < m ? eg[i] : 0.0, em = i > 0 ? eg[i - 1] : 0.0;
+    if (di != 0.0 || em != 0.0) atomicMax(&sh_last, i);
+    tn = fmax(tn, fabs(di) + fabs(ei) + fabs(em));
   }
-  __syncthreads();
-  if (threadIdx.x == 0) sh_ok = tridiag_eigenvalues(a, b, m) ? 1 : 0;
-  __syncthreads();
-  // descending order; ties keep the lower index first
-  for (int i = threadIdx.x; i < m; i += kEigThreads) {
-    const double x = a[i];
-    int pos = 0;
-    for (int j = 0; j < m; ++j) pos += (a[j] > x) || (a[j] == x && j < i);
-    srt[pos] = x;
+  tn = block_max_d(tn, red);
+  const int n = sh_last + 1;
+  const bool finite = isfinite(tn);
+  double sc = 1.0;
+  if (tn > 0.0 && finite) sc = ldexp(1.0, -ilogb(tn));
+  double glo = 0.0, ghi = 0.0;
+  for (int i = threadIdx.x; i < n; i += kEigThreads) {
+    const double di = dg[i] * sc, ei = i + 1 < n ? eg[i] * sc : 0.0, em = i > 0 ? eg[i - 1] * sc : 0.0;
+    d[i] = di;
+    e2[i] = ei * ei;
+    glo = fmin(glo, di - fabs(ei) - fabs(em));
+    ghi = fmax(ghi, di + fabs(ei) + fabs(em));
   }
-  __syncthreads();
-  double* ev = at<double>(bases, J.ev);
-  for (int i = threadIdx.x; i < m; i += kEigThreads) ev[i] = srt[i];
-  if (threadIdx.x == 0) {
-    bool finite = true;
-    double total = 0.0;
-    for (int i = m - 1; i >= 0; --i) {
-      finite = finite && isfinite(srt[i]);
-      total += fmax(srt[i], 0.0);
+  glo = block_min_d(glo, red);
+  ghi = block_max_d(ghi, red);   // ends with a barrier: d, e2 are complete
+  if (finite) {
+    const double tol = 0x1p-50 * fmax(fabs(glo), fabs(ghi));
+    for (int j = threadIdx.x; j < n; j += kEigThreads) {
+      double lo = glo, hi = ghi;
+      for (int it = 0; it < kBisectMaxIter && hi - lo > tol; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (sturm_count(d, e2, n, mid) > j) hi = mid; else lo = mid;
+      }
+      lam[j] = 0.5 * (lo + hi) / sc;   // ascending in j
     }
+  }
+  __syncthreads();
+  // all m eigenvalues in descending order: the active ones with the m - n zeros merged in
+  int npos = 0;
+  for (int j = threadIdx.x; j < n; j += kEigThreads) npos += finite && lam[j] > 0.0;
+  npos = (int)block_sum_d((double)npos, red);
+  double* ev = at<double>(bases, J.ev);
+  for (int t = threadIdx.x; t < m; t += kEigThreads) {
+    double v;
+    if (!finite) v = tn;
+    else if (t < npos) v = lam[n - 1 - t];
+    else if (t < npos + (m - n)) v = 0.0;
+    else v = lam[n - 1 - (t - (m - n))];
+    ev[t] = v;
+  }
+  if (threadIdx.x == 0) {
+    double total = 0.0;
+    for (int j = 0; j < n; ++j) total += finite ? fmax(lam[j], 0.0) : 0.0;
     const double tau = J.eps * J.eps / J.order * total;
-    // the largest c <= m - 1 whose c smallest eigenvalues sum to at most tau; rank = m - c
+    // the largest c <= m - 1 whose c smallest eigenvalues sum to at most tau; rank = m - c.
+    // The m - n zeros (and the clamped negatives) come first in ascending order.
     double tail = 0.0;
     int c = 0;
     while (c < m - 1) {
-      const double next = tail + fmax(srt[m - 1 - c], 0.0);
+      // c-th smallest: first the active eigenvalues <= 0 and the zero block (all clamp to 0)
+      const int nonpos = m - npos;
+      const double v = c < nonpos ? 0.0 : lam[n - npos + (c - nonpos)];
+      const double next = tail + v;
       if (!(next <= tau)) break;
       tail = next;
       ++c;
@@ -470,7 +503,6 @@ __global__ void __launch_bounds__(kEigThreads) subrank_eig_kernel(const SubrankJ
     *at<int32_t>(bases, J.rank) = rank;
     *at<int32_t>(bases, J.ell) = rank + J.p;
     if (!finite) record_status(status, TKS_ENONFINITE);
-    else if (!sh_ok) record_status(status, TKS_ENOCONV);
   }
 }
 

@@ -226,3 +226,40 @@ def test_krpsum_with_effective_ranks(cuda_lib):
     ex = sum(tucker_entries(G, Us, idx) for G, Us in p.terms())
     eg = tucker_entries(got["core"], got["factors"], idx)
     assert np.sqrt(np.mean((eg - ex) ** 2)) <= 1e-10 * np.sqrt(np.mean(ex ** 2))
+
+
+# ------------------------------------------------------------------ full-size batches, sampled
+def _sampled_parity(problems, got, eps, picks):
+    for i in picks:
+        p, g = problems[i], got[i]
+        ref = sr.effective_subrank(p.terms(), eps, p.oversampling, alpha=p.alpha)
+        for m in range(p.order):
+            _check_eigenvalues(g["lam"][m], ref["lam"][m])
+            lam = np.asarray(ref["lam"][m])
+            k = ref["rank"][m]
+            tau = ref["tau"][m]
+            # the rank where tau is not within the eigenvalue error of a tail sum
+            if float(np.sum(lam[k - 1:])) - tau > 1e-9 * lam[0] and tau - float(np.sum(lam[k:])) > 1e-9 * lam[0]:
+                assert g["rank"][m] == k, (i, m, g["rank"], ref["rank"])
+                assert g["ell"][m] == ref["ell"][m]
+
+
+def test_decay512_152_problems(cuda_lib):
+    # the bench's launch: 152 decay512 problems (one plan, bf16 inputs, eps = 1e-6), 4 checked
+    from paper_2603_13532_gb300 import binding
+    import bench
+    probs = bench.make_problems(152, 20260315, 0, True, "decay512")
+    got = binding.SubrankPlan(probs, 1e-6, dtype="bf16").run(eigenvalues=True)
+    assert all(1 <= r <= 512 for g in got for r in g["rank"])
+    _sampled_parity(probs, got, 1e-6, [0, 51, 102, 151])
+
+
+def test_batched_256_problems(cuda_lib):
+    # the batched workload at full size: 256 problems, n up to 1024, K up to 48 (Gram orders up to
+    # 1024, both Gram forms), 4 problems checked, the largest among them
+    from paper_2603_13532_gb300 import binding
+    w = wl.batched()
+    got = binding.SubrankPlan(w.problems, 1e-5, dtype="bf16").run(eigenvalues=True)
+    orders = [min(p.dims[0], sum(r[0] for r in p.ranks())) for p in w.problems]
+    big = int(np.argmax(orders))
+    _sampled_parity(w.problems, got, 1e-5, sorted({0, 100, 200, big}))
