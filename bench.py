@@ -576,7 +576,10 @@ def main():
                                 "peak_source": "derived FP64: 152 SMs x 4 flop/clk x 2070 MHz",
                                 "flops_per_call": sp.info.flops,
                                 "flops_note": "Gram matrices 2 x contraction x m(m+1)/2 plus tridiagonalization "
-                                              "4/3 m^3 per (problem, mode), m = min(n, R)",
+                                              "4/3 m^3 per (problem, mode), m = min(n, R); the reduction "
+                                              "ends early on numerically rank-deficient Gram matrices "
+                                              "(decay512: after ~130 of 512 steps), so the count exceeds "
+                                              "the executed work there",
                                 "traffic": None}}
         if rank == 0 and not args.no_cpu:
             rate, done, dt = oracle_subrank_rate(problems, args.subrank_eps, args.cpu_seconds / 2)
