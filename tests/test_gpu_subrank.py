@@ -263,3 +263,24 @@ def test_batched_256_problems(cuda_lib):
     orders = [min(p.dims[0], sum(r[0] for r in p.ranks())) for p in w.problems]
     big = int(np.argmax(orders))
     _sampled_parity(w.problems, got, 1e-5, sorted({0, 100, 200, big}))
+
+
+def test_kronsum_with_effective_ranks(cuda_lib):
+    # Alg. 3 as printed on the exact-recovery workload (K = 4 terms of rank 8, Kronecker sketch):
+    # the heuristic finds rank 32 = sum of the term ranks in every mode, the Kronecker sizes follow
+    # from ell, and the recompression recovers the sum
+    from paper_2603_13532_gb300 import binding
+    from oracle.tensor import tucker_full, tucker_sum_full
+    w = wl.exact_recovery()
+    p = w.problems[0]
+    eps = 1e-8
+    sub = binding.SubrankPlan([p], eps).run()[0]
+    ref_sub = sr.effective_subrank(p.terms(), eps, p.oversampling, kind="kron")
+    assert sub["rank"] == ref_sub["rank"] == [32, 32, 32]
+    q = binding.with_sketch_ranks([p], [sub["ell"]])[0]
+    plan = binding.Plan([q], kind="kron", precision="fp64", seed=w.seed, tol=eps)
+    assert [plan.pinfo[0].omega_cols[m] for m in range(3)] == ref_sub["cols"]
+    got = plan.recompress()[0]
+    X = tucker_sum_full(p.terms())
+    err = np.linalg.norm(tucker_full(got["core"], got["factors"]) - X) / np.linalg.norm(X)
+    assert err <= 1e-12 and got["ranks"] == [32, 32, 32]
