@@ -58,7 +58,7 @@ typedef enum {
   TKS_ETIMEOUT = 4,      /* a bounded device-side wait ran out (kernel returned early) */
   TKS_ENONFINITE = 5,    /* a NaN or Inf reached the sketch or the projected core */
   TKS_ENOCONV = 6,       /* the small symmetric eigensolver hit its sweep limit */
-  TKS_EUNSUPPORTED = 7   /* valid input outside what this build supports */
+  TKS_EUNSUPPORTED = 7   /* valid input outside the limits the library supports */
 } tks_status;
 
 typedef enum { TKS_SKETCH_KRON = 0, TKS_SKETCH_KRP = 1 } tks_sketch;
