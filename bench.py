@@ -57,6 +57,8 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--measure-peaks", action="store_true", help="print FP64/FP32/TF32/BF16 GEMM rates")
+    ap.add_argument("--lanes", type=int, default=2,
+                    help="groups of problems whose recompressions run on concurrent streams (tks_params.lanes)")
     ap.add_argument("--no-subrank", action="store_true", help="skip the effective subrank (Alg. 5) leg")
     ap.add_argument("--subrank-eps", type=float, default=1e-6, help="tolerance of the Alg. 5 leg")
     ap.add_argument("--subrank-steps", type=int, default=3, help="timed calls of the Alg. 5 leg")
@@ -372,7 +374,8 @@ def main():
     if args.workload == "exact_recovery" and args.precision != "fp64":
         raise SystemExit("the exact_recovery workload is float64 only")
     problems = make_problems(P, args.seed, rank, bf16, args.workload)
-    plan = binding.Plan(problems, kind=kind, precision=args.precision, seed=args.seed, device=device)
+    plan = binding.Plan(problems, kind=kind, precision=args.precision, seed=args.seed, device=device,
+                        lanes=args.lanes)
     out = torch.zeros(plan.info.output_elems, dtype=torch.float64, device=device)
     ranks_t = torch.zeros(P * binding.MAX_ORDER, dtype=torch.int32, device=device)
     stream = torch.cuda.current_stream()
@@ -432,7 +435,8 @@ def main():
     if not args.no_e2e:
         host_in, _ = binding.pack_inputs(problems, plan.dtype, "cpu", pin=True)
         lanes = [(plan, out, ranks_t, timed)]
-        plan_b = binding.Plan(problems, kind=kind, precision=args.precision, seed=args.seed, device=device)
+        plan_b = binding.Plan(problems, kind=kind, precision=args.precision, seed=args.seed, device=device,
+                              lanes=args.lanes)
         out_b = torch.zeros_like(out)
         ranks_b = torch.zeros_like(ranks_t)
         plan_b.recompress_raw(out_b, ranks_b)
@@ -608,11 +612,13 @@ def main():
                            "precision": args.precision, "tflops": tflops,
                            "flops_per_step": plan.info.flops_lowprec + plan.info.flops_fp64,
                            "l2": f"inputs {in_bytes / 1e6:.0f} MB per GPU > L2 129 MB, no flush",
-                           "parallelism": f"replicas x{world}"},
+                           "parallelism": f"replicas x{world}",
+                           "lanes": args.lanes if args.precision != "fp64" else 1},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fp64_path": fp64_path, "subrank": subrank,
                 "gpu_launches": int(plan.info.launches_recompress) * args.steps,
                 "timing": ("CUDA-graph replays of the whole recompression" if graph is not None
-                           else "eager launches") + "; stage times from an eager pass with events",
+                           else "eager launches") + "; stage times from an eager pass with events (one "
+                          "launch sequence: a profiled call does not split into lanes)",
                 "eager_ms_per_step": 1e3 * eager_elapsed / args.steps,
                 "clocks": clock_info,
                 "stages": [{"name": s["name"], "ms_per_call": s["ms"] / max(1, s["calls"])} for s in prof]}

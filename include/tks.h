@@ -107,6 +107,13 @@ typedef struct {
                                    1: the mixed modes' draws for every precision, so that a
                                    TKS_FP64 plan computes with the Omega of a mixed plan (an
                                    arithmetic-only comparison of the two) */
+  int32_t lanes;                /* 0 or 1: tucker_sum_recompress is one sequence of grouped launches.
+                                   2..8 (mixed modes): the problems are split into that many
+                                   contiguous groups whose launch sequences run on concurrent
+                                   streams, forked from and joined back to the caller's stream (the
+                                   latency-bound stages of one group overlap the others' work);
+                                   results are identical.  Ignored by TKS_FP64 and by the other
+                                   entry points. */
 } tks_params;
 
 typedef struct tks_plan tks_plan;

@@ -44,7 +44,8 @@ class Problem_t(ctypes.Structure):
 
 class Params_t(ctypes.Structure):
     _fields_ = [("sketch", ctypes.c_int), ("precision", ctypes.c_int), ("dtype", ctypes.c_int),
-                ("seed", ctypes.c_uint64), ("trunc_tol", ctypes.c_double), ("omega_lowprec", ctypes.c_int32)]
+                ("seed", ctypes.c_uint64), ("trunc_tol", ctypes.c_double), ("omega_lowprec", ctypes.c_int32),
+                ("lanes", ctypes.c_int32)]
 
 
 class PlanInfo_t(ctypes.Structure):
@@ -203,7 +204,8 @@ def _problem_structs(problems, inputs, keep):
 class Plan:
     """A plan over a list of ``workloads.Problem`` with their device inputs."""
 
-    def __init__(self, problems, kind="krp", precision="fp64", seed=0, tol=0.0, device="cuda", omega_lowprec=False):
+    def __init__(self, problems, kind="krp", precision="fp64", seed=0, tol=0.0, device="cuda", omega_lowprec=False,
+                 lanes=0):
         self.lib = load()
         self.problems = list(problems)
         self.kind, self.precision, self.seed, self.tol = kind, precision, seed, tol
@@ -212,7 +214,7 @@ class Plan:
         self.flat_inputs, self.inputs = pack_inputs(self.problems, self.dtype, self.device)
         self._keep = []
         arr = _problem_structs(self.problems, self.inputs, self._keep)
-        prm = Params_t(SKETCH[kind], PRECISION[precision], DTYPE[self.dtype], seed, tol, int(omega_lowprec))
+        prm = Params_t(SKETCH[kind], PRECISION[precision], DTYPE[self.dtype], seed, tol, int(omega_lowprec), int(lanes))
         handle = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             _check(self.lib.tks_plan_create(ctypes.byref(handle), arr, len(self.problems), ctypes.byref(prm)))
@@ -421,7 +423,7 @@ class SubrankPlan:
             self.inputs = inputs
         self._keep = []
         arr = _problem_structs(self.problems, self.inputs, self._keep)
-        prm = Params_t(SKETCH["krp"], PRECISION["fp64"], DTYPE[dtype], 0, float(eps), 0)
+        prm = Params_t(SKETCH["krp"], PRECISION["fp64"], DTYPE[dtype], 0, float(eps), 0, 0)
         handle = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             _check(self.lib.tks_subrank_plan_create(ctypes.byref(handle), arr, len(self.problems), ctypes.byref(prm)))

@@ -162,6 +162,13 @@ struct tks_plan {
   size_t ws_omega = 0, ws_Y = 0, ws_Q = 0, ws_H = 0;
   int64_t omega_elems = 0, sketch_elems = 0, basis_elems = 0, core_elems = 0, output_elems = 0;
   std::vector<Step> st_omega, st_sketch, st_project, st_recompress, st_backward;
+  // problems [lane_p0, lane_p1) go into the launch tables being built; with lanes > 1 the
+  // recompression has one step list per contiguous group of problems, run on its own stream
+  int lane_p0 = 0, lane_p1 = 0;
+  std::vector<std::vector<Step>> lane_steps;
+  std::vector<cudaStream_t> lane_streams;   // lanes 1..L-1 (lane 0 runs on the caller's stream)
+  std::vector<cudaEvent_t> lane_join;       // one per extra lane
+  cudaEvent_t lane_fork = nullptr;
   int64_t grad_core_elems = 0, grad_factor_elems = 0;
   bool backward_ok = false;
   double flops_low = 0.0, flops_f64 = 0.0;
@@ -451,7 +458,7 @@ static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
     j.epi.alpha = 1.0f;
     return j;
   };
-  for (int p = 0; p < plan->nprob; ++p) {
+  for (int p = plan->lane_p0; p < plan->lane_p1; ++p) {
     auto& h = plan->probs[p];
     const int d = h.d;
     for (int m = 0; m < d; ++m) {
@@ -936,7 +943,7 @@ static void build_hosvd_f32(tks_plan* plan) {
     int ttm_tiles = 0, fac_tiles = 0;
     double ttm_flops = 0.0, fac_flops = 0.0;
     double qflops = 0.0;
-    for (int p = 0; p < plan->nprob; ++p) {
+    for (int p = plan->lane_p0; p < plan->lane_p1; ++p) {
       auto& h = plan->probs[p];
       const int d = h.d;
       if (n >= d) continue;
@@ -1169,6 +1176,70 @@ static void build_backward3(tks_plan* plan) {
 
 }  // namespace
 
+// ST-HOSVD of H in float64 (TKS_FP64 and TKS_MIXED): Gram matrices, Jacobi eigensolver, mode
+// products; problems [lane_p0, lane_p1).
+static void build_hosvd_f64(tks_plan* plan) {
+  for (int n = 0; n < plan->dmax; ++n) {
+    GemmList gram, ttm, fac;
+    std::vector<EigJob> eig;
+    for (int p = plan->lane_p0; p < plan->lane_p1; ++p) {
+      auto& h = plan->probs[p];
+      const int d = h.d;
+      if (n >= d) continue;
+      int64_t L = 1, Rr = 1;
+      for (int j = 0; j < n; ++j) L *= h.rmax[j];
+      for (int j = n + 1; j < d; ++j) Rr *= h.b[j];
+      const int b = h.b[n], rmax = h.rmax[n];
+      const Operand X = (n == 0) ? op(B_H, h.h_off * 8) : op(B_WS, h.Hp[(n - 1) & 1]);
+      // Gram B_n = H_(n) H_(n)^T: k = l + L rr
+      GemmJob g = gemm(b, b, (int)(L * Rr), X, L, 1, X, L, 1, op(B_WS, h.gram), 1, b);
+      g.K1 = (int)L;
+      g.a_k1 = L * b;
+      g.b_k1 = L * b;
+      g.ksplit = std::min<int>(h.gram_ksplit, std::max(1, (int)(L * Rr / 64)));
+      g.P = op(B_WS, h.part);
+      gram.add(g);
+      EigJob e;
+      std::memset(&e, 0, sizeof(e));
+      e.B = op(B_WS, h.gram);
+      e.P = op(B_WS, h.P[n]);
+      e.evals = op(B_WS, h.ev[n]);
+      e.theta = op(B_WS, h.theta);
+      e.rank = op(B_RANKS, (size_t)(p * TKS_MAX_ORDER + n) * 4);
+      e.b = b;
+      e.rmax = rmax;
+      e.target = h.target[n];
+      e.first_mode = (n == 0);
+      e.order = d;
+      e.tol = plan->params.trunc_tol;
+      eig.push_back(e);
+      const Operand Y = (n == d - 1) ? op(B_OUT, h.out_core_off * 8) : op(B_WS, h.Hp[n & 1]);
+      GemmJob t;
+      if (L == 1) {
+        t = gemm(rmax, (int)Rr, b, op(B_WS, h.P[n]), b, 1, X, b, 1, Y, 1, rmax);
+      } else {
+        t = gemm((int)L, rmax, b, X, 1, L, op(B_WS, h.P[n]), b, 1, Y, 1, L);
+        t.batch = (int)Rr;
+        t.a_b = L * b;
+        t.c_b = L * rmax;
+      }
+      ttm.add(t);
+      fac.add(gemm((int)h.n[n], rmax, b, op(B_Q, h.q_off[n] * 8), 1, h.n[n], op(B_WS, h.P[n]), b, 1,
+                   op(B_OUT, h.out_fac_off[n] * 8), 1, h.n[n]));
+    }
+    char nm[32];
+    std::snprintf(nm, sizeof(nm), "a9:gram%d", n);
+    plan->push_gemm(plan->st_recompress, gram, nm);
+    std::snprintf(nm, sizeof(nm), "a9:eig%d", n);
+    plan->push(plan->st_recompress, S_EIG, eig, (int64_t)eig.size(), nm);
+    std::snprintf(nm, sizeof(nm), "a9:ttm%d", n);
+    plan->push_gemm(plan->st_recompress, ttm, nm);
+    std::snprintf(nm, sizeof(nm), "a9:factor%d", n);
+    plan->push_gemm(plan->st_recompress, fac, nm);
+  }
+
+}
+
 extern "C" {
 
 const char* tks_last_error(void) { return g_last_error.c_str(); }
@@ -1190,6 +1261,9 @@ const char* tks_status_string(tks_status s) {
 void tks_plan_destroy(tks_plan* plan) {
   if (!plan) return;
   plan->profile_clear();
+  for (cudaStream_t st : plan->lane_streams) cudaStreamDestroy(st);
+  for (cudaEvent_t ev : plan->lane_join) cudaEventDestroy(ev);
+  if (plan->lane_fork) cudaEventDestroy(plan->lane_fork);
   if (plan->maps_host) cudaFreeHost(plan->maps_host);
   if (plan->arena_dev) cudaFree(plan->arena_dev);
   delete plan;
@@ -1204,6 +1278,7 @@ tks_status tks_plan_create(tks_plan** out, const tks_problem* problems, int32_t 
   if (prm.sketch != TKS_SKETCH_KRP && prm.sketch != TKS_SKETCH_KRON) return fail(TKS_EINVAL, "bad sketch");
   if (!(prm.trunc_tol >= 0.0) || !std::isfinite(prm.trunc_tol)) return fail(TKS_EINVAL, "bad trunc_tol");
   if (prm.omega_lowprec != 0 && prm.omega_lowprec != 1) return fail(TKS_EINVAL, "omega_lowprec must be 0 or 1");
+  if (prm.lanes < 0 || prm.lanes > 8) return fail(TKS_EINVAL, "lanes must be 0..8");
   if (prm.precision == TKS_FP64) {
     if (prm.dtype != TKS_DT_F64) return fail(TKS_EINVAL, "TKS_FP64 needs float64 cores and factors");
   } else if (prm.precision == TKS_MIXED || prm.precision == TKS_MIXED_F32LA) {
@@ -1387,6 +1462,8 @@ tks_status tks_plan_create(tks_plan** out, const tks_problem* problems, int32_t 
   plan->ws_bytes = align_up(ws);
 
   // ---- launch tables
+  plan->lane_p0 = 0;
+  plan->lane_p1 = num_problems;
   if (mixed) {
     build_mixed_stages(plan, kron, f32la);
   } else {
@@ -1528,63 +1605,46 @@ tks_status tks_plan_create(tks_plan** out, const tks_problem* problems, int32_t 
   }
   }
   if (f32la) build_hosvd_f32(plan);
-  for (int n = 0; n < plan->dmax && !f32la; ++n) {
-    GemmList gram, ttm, fac;
-    std::vector<EigJob> eig;
-    for (int p = 0; p < plan->nprob; ++p) {
-      auto& h = plan->probs[p];
-      const int d = h.d;
-      if (n >= d) continue;
-      int64_t L = 1, Rr = 1;
-      for (int j = 0; j < n; ++j) L *= h.rmax[j];
-      for (int j = n + 1; j < d; ++j) Rr *= h.b[j];
-      const int b = h.b[n], rmax = h.rmax[n];
-      const Operand X = (n == 0) ? op(B_H, h.h_off * 8) : op(B_WS, h.Hp[(n - 1) & 1]);
-      // Gram B_n = H_(n) H_(n)^T: k = l + L rr
-      GemmJob g = gemm(b, b, (int)(L * Rr), X, L, 1, X, L, 1, op(B_WS, h.gram), 1, b);
-      g.K1 = (int)L;
-      g.a_k1 = L * b;
-      g.b_k1 = L * b;
-      g.ksplit = std::min<int>(h.gram_ksplit, std::max(1, (int)(L * Rr / 64)));
-      g.P = op(B_WS, h.part);
-      gram.add(g);
-      EigJob e;
-      std::memset(&e, 0, sizeof(e));
-      e.B = op(B_WS, h.gram);
-      e.P = op(B_WS, h.P[n]);
-      e.evals = op(B_WS, h.ev[n]);
-      e.theta = op(B_WS, h.theta);
-      e.rank = op(B_RANKS, (size_t)(p * TKS_MAX_ORDER + n) * 4);
-      e.b = b;
-      e.rmax = rmax;
-      e.target = h.target[n];
-      e.first_mode = (n == 0);
-      e.order = d;
-      e.tol = prm.trunc_tol;
-      eig.push_back(e);
-      const Operand Y = (n == d - 1) ? op(B_OUT, h.out_core_off * 8) : op(B_WS, h.Hp[n & 1]);
-      GemmJob t;
-      if (L == 1) {
-        t = gemm(rmax, (int)Rr, b, op(B_WS, h.P[n]), b, 1, X, b, 1, Y, 1, rmax);
-      } else {
-        t = gemm((int)L, rmax, b, X, 1, L, op(B_WS, h.P[n]), b, 1, Y, 1, L);
-        t.batch = (int)Rr;
-        t.a_b = L * b;
-        t.c_b = L * rmax;
+  else build_hosvd_f64(plan);
+
+  if (mixed) {
+    const int lanes = std::min<int>(prm.lanes, num_problems);
+    if (lanes > 1) {
+      // one more set of launch tables per group of problems; the full-range lists stay for the
+      // other entry points and for profiled calls
+      auto om = plan->st_omega, sk = plan->st_sketch, pr = plan->st_project, rc = plan->st_recompress;
+      for (int l = 0; l < lanes; ++l) {
+        plan->st_omega.clear();
+        plan->st_sketch.clear();
+        plan->st_project.clear();
+        plan->st_recompress.clear();
+        plan->lane_p0 = (int)((int64_t)l * num_problems / lanes);
+        plan->lane_p1 = (int)((int64_t)(l + 1) * num_problems / lanes);
+        build_mixed_stages(plan, kron, f32la);
+        if (f32la) build_hosvd_f32(plan);
+        else build_hosvd_f64(plan);
+        plan->lane_steps.push_back(std::move(plan->st_recompress));
       }
-      ttm.add(t);
-      fac.add(gemm((int)h.n[n], rmax, b, op(B_Q, h.q_off[n] * 8), 1, h.n[n], op(B_WS, h.P[n]), b, 1,
-                   op(B_OUT, h.out_fac_off[n] * 8), 1, h.n[n]));
+      plan->st_omega = std::move(om);
+      plan->st_sketch = std::move(sk);
+      plan->st_project = std::move(pr);
+      plan->st_recompress = std::move(rc);
+      plan->lane_p0 = 0;
+      plan->lane_p1 = num_problems;
+      bool ok = cudaEventCreateWithFlags(&plan->lane_fork, cudaEventDisableTiming) == cudaSuccess;
+      for (int l = 1; l < lanes && ok; ++l) {
+        cudaStream_t st = nullptr;
+        cudaEvent_t ev = nullptr;
+        ok = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess;
+        if (ok) plan->lane_streams.push_back(st);
+        ok = ok && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess;
+        if (ok) plan->lane_join.push_back(ev);
+      }
+      if (!ok) {
+        tks_plan_destroy(plan);
+        return fail(TKS_ECUDA, "lane streams and events");
+      }
     }
-    char nm[32];
-    std::snprintf(nm, sizeof(nm), "a9:gram%d", n);
-    plan->push_gemm(plan->st_recompress, gram, nm);
-    std::snprintf(nm, sizeof(nm), "a9:eig%d", n);
-    plan->push(plan->st_recompress, S_EIG, eig, (int64_t)eig.size(), nm);
-    std::snprintf(nm, sizeof(nm), "a9:ttm%d", n);
-    plan->push_gemm(plan->st_recompress, ttm, nm);
-    std::snprintf(nm, sizeof(nm), "a9:factor%d", n);
-    plan->push_gemm(plan->st_recompress, fac, nm);
   }
 
   // ---- device copies
@@ -1655,7 +1715,13 @@ tks_status tks_plan_info(const tks_plan* plan, tks_plan_info_t* info) {
   info->core_elems = plan->core_elems;
   info->output_elems = plan->output_elems;
   info->num_problems = plan->nprob;
-  info->launches_recompress = (int32_t)plan->st_recompress.size();
+  if (plan->lane_steps.empty()) {
+    info->launches_recompress = (int32_t)plan->st_recompress.size();
+  } else {
+    size_t n = 0;
+    for (const auto& ls : plan->lane_steps) n += ls.size();
+    info->launches_recompress = (int32_t)n;
+  }
   info->flops_lowprec = plan->flops_low;
   info->flops_fp64 = plan->flops_f64;
   info->grad_core_elems = plan->grad_core_elems;
@@ -1893,7 +1959,20 @@ tks_status tucker_sum_recompress(tks_plan* plan, void* workspace, double* out, i
   Bases b = bind(plan, workspace);
   b.p[B_OUT] = reinterpret_cast<char*>(out);
   b.p[B_RANKS] = reinterpret_cast<char*>(ranks_out);
-  return run_steps(plan, plan->st_recompress, b, s, true);
+  const bool profiled = plan->prof_calls < plan->prof_max_calls;
+  if (plan->lane_steps.empty() || profiled) return run_steps(plan, plan->st_recompress, b, s, true);
+  // fork: every extra lane waits for the caller's stream, runs its problems, and is joined back
+  TKS_CUDA_CHECK(cudaEventRecord(plan->lane_fork, s));
+  for (cudaStream_t ls : plan->lane_streams) TKS_CUDA_CHECK(cudaStreamWaitEvent(ls, plan->lane_fork, 0));
+  for (size_t l = 0; l < plan->lane_steps.size(); ++l) {
+    st = run_steps(plan, plan->lane_steps[l], b, l == 0 ? s : plan->lane_streams[l - 1], false);
+    if (st != TKS_OK) return st;
+  }
+  for (size_t l = 1; l < plan->lane_steps.size(); ++l) {
+    TKS_CUDA_CHECK(cudaEventRecord(plan->lane_join[l - 1], plan->lane_streams[l - 1]));
+    TKS_CUDA_CHECK(cudaStreamWaitEvent(s, plan->lane_join[l - 1], 0));
+  }
+  return TKS_OK;
 }
 
 tks_status tks_profile_begin(tks_plan* plan, int32_t max_calls) {

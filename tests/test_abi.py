@@ -94,7 +94,8 @@ def test_plan_create_rejects_bad_params(lib):
     h = ctypes.c_void_p()
     for prm in [binding.Params_t(5, 0, 0, 1, 0.0), binding.Params_t(1, 0, 1, 1, 0.0),
                 binding.Params_t(1, 0, 0, 1, -1.0), binding.Params_t(1, 9, 0, 1, 0.0),
-                binding.Params_t(1, 0, 0, 1, 0.0, 2)]:
+                binding.Params_t(1, 0, 0, 1, 0.0, 2), binding.Params_t(1, 0, 0, 1, 0.0, 0, 9),
+                binding.Params_t(1, 0, 0, 1, 0.0, 0, -1)]:
         assert lib.tks_plan_create(ctypes.byref(h), ctypes.byref(p), 1, ctypes.byref(prm)) == 1
     assert lib.tks_plan_create(None, ctypes.byref(p), 1, ctypes.byref(binding.Params_t(1, 0, 0, 1, 0.0))) == 1
     assert lib.tks_plan_create(ctypes.byref(h), ctypes.byref(p), 0, ctypes.byref(binding.Params_t(1, 0, 0, 1, 0.0))) == 1

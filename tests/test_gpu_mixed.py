@@ -296,3 +296,38 @@ def test_high_order_recompress_matches_oracle(cuda_lib, precision, kind, d):
     tol = 1e-11 if precision == "fp64" else 1e-5
     assert np.linalg.norm(Xg - Xo) / nx <= tol, np.linalg.norm(Xg - Xo) / nx
     assert abs(np.linalg.norm(Xg - X) - np.linalg.norm(Xo - X)) / nx <= tol
+
+
+@pytest.mark.parametrize("precision", MODES)
+def test_lanes_give_identical_results(cuda_lib, precision):
+    # the same problems split into 3 lanes on concurrent streams (eager and CUDA-graph replay) give
+    # bit-identical outputs to one launch sequence: every problem's arithmetic is per problem
+    import torch
+    from paper_2603_13532_gb300 import binding
+    probs = _bf16_problems(3) + _bf16_problems(3, seed=1) + wl.decay512(num_problems=2).problems
+    one = binding.Plan(probs, kind="krp", precision=precision, seed=5)
+    ref = one.recompress()
+    three = binding.Plan(probs, kind="krp", precision=precision, seed=5, lanes=3)
+    assert three.info.launches_recompress > one.info.launches_recompress
+    got = three.recompress()
+    for a, b in zip(got, ref):
+        assert a["ranks"] == b["ranks"]
+        assert np.array_equal(a["core"], b["core"])
+        for fa, fb in zip(a["factors"], b["factors"]):
+            assert np.array_equal(fa, fb)
+    out = torch.zeros(three.info.output_elems, dtype=torch.float64, device="cuda")
+    ranks = torch.zeros(len(probs) * binding.MAX_ORDER, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(stream):
+        three.recompress_raw(out, ranks)
+    torch.cuda.current_stream().wait_stream(stream)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        three.recompress_raw(out, ranks)
+    out.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    three.sync()
+    for a, b in zip(three.unpack(out, ranks), ref):
+        assert a["ranks"] == b["ranks"] and np.array_equal(a["core"], b["core"])
