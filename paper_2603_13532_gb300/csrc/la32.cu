@@ -718,12 +718,12 @@ __global__ void __launch_bounds__(kSvdThreads) svd_jacobi_f32_kernel(const SvdJo
   }
   __syncthreads();
   const int r = sh_rank;
-  float* P = at<float>(bases, J.P);
-  for (int t = warp; t < J.rmax; t += nw) {
-    if (t >= r) {
-      for (int i = lane; i < b; i += 32) P[i + t * b] = 0.f;
-      continue;
-    }
+  // The kept right singular vectors, sign-fixed (largest entry positive), into the A buffer
+  // (column t at A + t ld).  V comes out of some b x sweeps plane rotations per column, each
+  // orthogonal to float32 rounding, so its columns drift from orthonormality by about
+  // b sweeps eps (5e-5 for b = 64); one Newton-Schulz step P <- P (3 I - P^T P) / 2, which keeps
+  // span(P) and squares the deviation, restores it to rounding level.
+  for (int t = warp; t < r; t += nw) {
     const int src = order[t];
     float best = 0.f;
     for (int i = lane; i < b; i += 32) {
@@ -736,7 +736,29 @@ __global__ void __launch_bounds__(kSvdThreads) svd_jacobi_f32_kernel(const SvdJo
       if (fabsf(other) > fabsf(best) || (fabsf(other) == fabsf(best) && other > best)) best = other;
     }
     const float sgn = (best < 0.f) ? -1.f : 1.f;
-    for (int i = lane; i < b; i += 32) P[i + t * b] = sgn * V[i + src * ld];
+    for (int i = lane; i < b; i += 32) A[i + t * ld] = sgn * V[i + src * ld];
+  }
+  __syncthreads();
+  // G = P^T P into the V buffer (G[t1 + t2 ld])
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int t1 = e % r, t2 = e / r;
+    const float* p1 = A + t1 * ld;
+    const float* p2 = A + t2 * ld;
+    float acc = 0.f;
+    for (int i = 0; i < b; ++i) acc = fmaf(p1[i], p2[i], acc);
+    V[t1 + t2 * ld] = acc;
+  }
+  __syncthreads();
+  float* P = at<float>(bases, J.P);
+  for (int e = threadIdx.x; e < b * J.rmax; e += blockDim.x) {
+    const int i = e % b, t = e / b;
+    float v = 0.f;
+    if (t < r) {
+      float acc = 0.f;
+      for (int t2 = 0; t2 < r; ++t2) acc = fmaf(A[i + t2 * ld], V[t2 + t * ld], acc);
+      v = fmaf(1.5f, A[i + t * ld], -0.5f * acc);
+    }
+    P[i + t * b] = v;
   }
 }
 

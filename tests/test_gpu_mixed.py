@@ -331,3 +331,36 @@ def test_lanes_give_identical_results(cuda_lib, precision):
     three.sync()
     for a, b in zip(three.unpack(out, ranks), ref):
         assert a["ranks"] == b["ranks"] and np.array_equal(a["core"], b["core"])
+
+
+@pytest.mark.parametrize("precision", ["fp64"] + MODES)
+@pytest.mark.parametrize("kind,ell", [("krp", 96), ("kron", 81)])
+def test_limits_rank64_basis96(cuda_lib, precision, kind, ell):
+    # a term of rank 64 (TKS_MAX_RANK) and sketches with up to 96 columns (TKS_MAX_BASIS for the
+    # Khatri-Rao case; the Kronecker sizes of ell = 81 give S_n = 81): every stage runs its
+    # general kernels (no rank-32 / basis-64 fast paths).  The sum has multilinear rank 74, below
+    # both targets (90 and 75), so the recompression reproduces it; checked against the dense sum
+    # and the oracle.
+    from paper_2603_13532_gb300 import binding
+    g = np.random.default_rng(64)
+    n = 128
+    ranks = [(64, 64, 64), (8, 8, 8), (2, 2, 2)]
+    cores = [g.standard_normal(r) for r in ranks]
+    facs = [[wl.haar(g, n, ri) for ri in r] for r in ranks]
+    target = ell - 6
+    p = wl.Problem([n] * 3, cores, facs, [target] * 3, [6] * 3)
+    if precision != "fp64":
+        p = wl._finish([p], True)[0]
+    plan = binding.Plan([p], kind=kind, precision=precision, seed=3)
+    assert [plan.pinfo[0].basis_cols[m] for m in range(3)] == [96 if kind == "krp" else 81] * 3
+    got = plan.recompress()[0]
+    ref = ss.recompress(p.terms(), kind, p.target, p.oversampling, seed=3,
+                        rounding=None if precision == "fp64" else "bf16")
+    X = tucker_sum_full(p.terms())
+    nx = np.linalg.norm(X)
+    Xg = tucker_full(got["core"], got["factors"])
+    Xo = tucker_full(ref["core"], ref["factors"])
+    tol = 1e-11 if precision == "fp64" else 1e-5
+    assert np.linalg.norm(Xg - X) <= tol * nx
+    assert np.linalg.norm(Xg - Xo) <= tol * nx
+    assert got["ranks"] == ref["ranks"] == [target] * 3
