@@ -388,9 +388,12 @@ __global__ void split_f64_kernel(const SplitJob* __restrict__ jobs, int njobs, i
 
 __global__ void __launch_bounds__(256) transpose_bf16_kernel(const TransposeJob* __restrict__ jobs, int njobs,
                                                              Bases bases) {
-  // 64 x 64 tiles; columns are read and rows written as pairs of bf16 (4-byte accesses) when the
-  // leading dimensions are even, so a warp moves 128 contiguous bytes per access
-  __shared__ uint16_t tile[64][66];
+  // 64 x 64 tiles.  Full tiles with leading dimensions that are multiples of 8 move 16 bytes per
+  // access: a column segment of 8 rows is read into row y of the shared tile (source order), the
+  // tile's 16-byte chunks XOR-swizzled by y / 8 so that the reads of 8 column segments that feed one
+  // 16-byte store of the destination hit distinct banks; each destination row gets 128 contiguous
+  // bytes from 8 lanes.
+  __shared__ __align__(16) uint16_t tile[64][66];
   int lo = 0, hi = njobs - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
@@ -402,18 +405,32 @@ __global__ void __launch_bounds__(256) transpose_bf16_kernel(const TransposeJob*
   const uint16_t* src = at<uint16_t>(bases, J.src);
   uint16_t* dst = at<uint16_t>(bases, J.dst);
   const int i0 = tr * 64, j0 = tcol * 64;
-  const bool pairs = ((J.ld_src | J.ld_dst) & 1) == 0 && i0 + 64 <= J.rows && j0 + 64 <= J.cols;
+  const bool vec = ((J.ld_src | J.ld_dst) & 7) == 0 && i0 + 64 <= J.rows && j0 + 64 <= J.cols;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 lanes x 8 warps
-  if (pairs) {
-    for (int y = ty; y < 64; y += 8) {   // column j0 + y, rows i0 + 2 tx, i0 + 2 tx + 1
-      const uint32_t v = *reinterpret_cast<const uint32_t*>(src + (i0 + 2 * tx) + J.ld_src * (int64_t)(j0 + y));
-      tile[2 * tx][y] = (uint16_t)(v & 0xffffu);
-      tile[2 * tx + 1][y] = (uint16_t)(v >> 16);
+  if (vec) {
+    uint4* t4 = reinterpret_cast<uint4*>(&tile[0][0]);       // viewed as [64 rows][8 chunks], no padding
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int idx = threadIdx.x + 256 * k;
+      const int y = idx >> 3, seg = idx & 7;                // column j0 + y, rows i0 + 8 seg .. + 7
+      const uint4 v = *reinterpret_cast<const uint4*>(src + (i0 + 8 * seg) + J.ld_src * (int64_t)(j0 + y));
+      t4[y * 8 + (seg ^ ((y >> 3) & 7))] = v;
     }
     __syncthreads();
-    for (int y = ty; y < 64; y += 8) {   // row i0 + y of the source = column of dst
-      const uint32_t v = (uint32_t)tile[y][2 * tx] | ((uint32_t)tile[y][2 * tx + 1] << 16);
-      *reinterpret_cast<uint32_t*>(dst + (j0 + 2 * tx) + J.ld_dst * (int64_t)(i0 + y)) = v;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int idx = threadIdx.x + 256 * k;
+      const int jseg = idx & 7, i = idx >> 3;               // destination row i0 + i, columns j0 + 8 jseg .. + 7
+      const uint16_t* tb = reinterpret_cast<const uint16_t*>(t4);
+      uint32_t w[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int y0 = 8 * jseg + 2 * u, y1 = y0 + 1;
+        const uint32_t a = tb[(y0 * 8 + ((i >> 3) ^ jseg)) * 8 + (i & 7)];
+        const uint32_t b = tb[(y1 * 8 + ((i >> 3) ^ jseg)) * 8 + (i & 7)];
+        w[u] = a | (b << 16);
+      }
+      *reinterpret_cast<uint4*>(dst + (j0 + 8 * jseg) + J.ld_dst * (int64_t)(i0 + i)) = make_uint4(w[0], w[1], w[2], w[3]);
     }
   } else {
     for (int y = ty; y < 64; y += 8)
