@@ -289,7 +289,7 @@ def time_steps(fn, steps, stream):
 FP32_PEAK_TFLOPS = 152 * 256 * 2.070e9 / 1e12   # 128 FP32 FMA per SM per clock
 FP64_KINDS = {"gemm", "reduce", "qr", "core_sketch", "eig"}
 FP32_KINDS = {"simt", "core_sketch32", "qr32", "svd32", "tsqr32", "core_sketch3", "chain3", "qr_smem32",
-              "project3", "sketch3", "qr_reg32", "ttm32", "fold4", "project4", "sketch3f"}
+              "project3", "sketch3", "qr_reg32", "ttm32", "fold4", "project4", "sketch3f", "sketch4"}
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch per problem, from an ncu

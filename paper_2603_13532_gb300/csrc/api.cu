@@ -49,7 +49,7 @@ Operand op_abs(const void* p, size_t off_bytes = 0) {
 
 enum StepKind { S_OMEGA, S_GEMM, S_REDUCE, S_CORESKETCH, S_QR, S_EIG, S_TC, S_SIMT, S_CS32, S_SPLIT,
                 S_TRANSPOSE, S_QR32, S_SVD32, S_TSQR, S_CS3, S_CHAIN3, S_QRSM, S_PROJ3, S_SK3, S_QRREG, S_TTM,
-                S_FOLD4, S_PROJ3F, S_SK3F };
+                S_FOLD4, S_PROJ3F, S_SK3F, S_SK4 };
 
 struct Step {
   StepKind kind;
@@ -426,6 +426,9 @@ static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
   std::vector<CoreSketchF32Job> cs3;
   std::vector<Chain3Job> ch3;
   std::vector<Sketch3Job> sk3, sk3f;   // bf16 / float32 core copies in shared memory
+  std::vector<Sketch4Job> sk4;         // order-4 Khatri-Rao terms, one CTA each
+  size_t sk4_smem = 0;
+  double sk4_flops = 0.0;
   size_t sk3_smem = 0, sk3f_smem = 0;
   double sk3_flops = 0.0, sk3f_flops = 0.0;
   std::vector<Proj3Job> p3, p3f;
@@ -526,6 +529,30 @@ static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
             sk3_smem = std::max(sk3_smem, sketch3_smem_bytes(r, false));
             sk3_flops += fl;
           }
+          continue;
+        }
+      }
+      if (d == 4 && !kron && h.s[0] <= 64) {
+        const int* r = &h.ranks[(size_t)k * d];
+        if (r[0] <= kSketch4MaxRank && r[1] <= kSketch4MaxRank && r[2] <= kSketch4MaxRank &&
+            r[3] <= kSketch4MaxRank) {
+          Sketch4Job j;
+          std::memset(&j, 0, sizeof(j));
+          j.core = op_abs(h.cores, (size_t)h.core_off[k] * 2);
+          for (int m = 0; m < 4; ++m) {
+            j.M[m] = op(B_WS, h.M32[m]);
+            for (int t = 0; t < 3; ++t) j.V[m][t] = op(B_WS, h.Vp[m][t]);
+            j.r[m] = r[m];
+            j.roff[m] = h.roff[(size_t)k * d + m];
+            j.R[m] = h.R[m];
+            j.ldv[m] = h.ldV[m];
+          }
+          j.s = h.s[0];
+          j.kc = sketch4_slice(r, 40 * 1024);
+          j.alpha = (float)h.alpha[k];
+          sk4.push_back(j);
+          sk4_smem = std::max(sk4_smem, sketch4_smem_bytes(r, j.kc));
+          sk4_flops += 2.0 * h.s[0] * 4.0 * r[0] * r[1] * r[2] * r[3];
           continue;
         }
       }
@@ -872,6 +899,10 @@ static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
   if (!cs3.empty()) {
     plan->push(plan->st_sketch, S_CS3, cs3, (int64_t)cs3.size(), "a3:core_sketch3[f32]", cs3_flops, 0.0);
     plan->st_sketch.back().smem = cs3_smem;
+  }
+  if (!sk4.empty()) {
+    plan->push(plan->st_sketch, S_SK4, sk4, (int64_t)sk4.size(), "a3:sketch4[f32]", sk4_flops, 0.0);
+    plan->st_sketch.back().smem = sk4_smem;
   }
   if (!sk3f.empty()) {
     plan->push(plan->st_sketch, S_SK3F, sk3f, (int64_t)sk3f.size(), "a3:sketch3[f32]", sk3f_flops, 0.0);
@@ -1673,6 +1704,7 @@ tks_status tks_plan_create(tks_plan** out, const tks_problem* problems, int32_t 
     if (e == cudaSuccess) e = prepare_proj3();
     if (e == cudaSuccess) e = prepare_fold4();
     if (e == cudaSuccess) e = prepare_sketch3();
+    if (e == cudaSuccess) e = prepare_sketch4();
     if (e == cudaSuccess) e = prepare_qr_reg_f32();
     if (e == cudaSuccess) e = prepare_ttm_rows();
     if (e != cudaSuccess) {
@@ -1830,6 +1862,9 @@ tks_status run_steps(tks_plan* plan, const std::vector<Step>& steps, const Bases
         break;
       case S_SK3:
         launch_sketch3(static_cast<const Sketch3Job*>(table), s.njobs, s.smem, false, bases, stream);
+        break;
+      case S_SK4:
+        launch_sketch4(static_cast<const Sketch4Job*>(table), s.njobs, s.smem, bases, stream);
         break;
       case S_SK3F:
         launch_sketch3(static_cast<const Sketch3Job*>(table), s.njobs, s.smem, true, bases, stream);

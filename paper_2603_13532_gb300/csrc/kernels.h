@@ -53,6 +53,12 @@ size_t sketch3_smem_bytes(const int r[3], bool f32_core);
 cudaError_t prepare_sketch3();
 void launch_sketch3(const Sketch3Job* jobs, int njobs, size_t smem, bool f32_core, const Bases& bases,
                     cudaStream_t stream);
+// Khatri-Rao core sketches of order-4 terms, one CTA per term: the core slice kc (mode-1 indices per
+// pass) that fits budget_bytes of shared memory, and the dynamic shared memory of a job.
+int sketch4_slice(const int r[4], size_t budget_bytes);
+size_t sketch4_smem_bytes(const int r[4], int kc);
+cudaError_t prepare_sketch4();
+void launch_sketch4(const Sketch4Job* jobs, int njobs, size_t smem, const Bases& bases, cudaStream_t stream);
 // Fused order-3 projection; `jobs` is followed in memory by the Proj3Term records.
 size_t proj3_smem_bytes();
 cudaError_t prepare_proj3();

@@ -143,6 +143,21 @@ struct Sketch3Job {
   int32_t pad[2];
 };
 
+// Khatri-Rao core sketches of all four modes of one order-4 term (stage b, float32), one CTA per
+// term; requires s <= 64 and ranks <= kSketch4MaxRank.  The core is staged in slices of kc mode-1
+// indices.
+constexpr int kSketch4MaxRank = 24;
+
+struct Sketch4Job {
+  Operand core;          // bf16 core, mode-1 fastest
+  Operand M[4];          // float32 M_m = Ucat_m^T Omega_m: element (i, c) at i + R_m c
+  Operand V[4][3];       // bf16 planes of Vcat_n: element (i, c) at i + ldv_n c
+  int32_t r[4], roff[4], R[4], ldv[4];
+  int32_t s, kc;
+  float alpha;
+  int32_t pad;
+};
+
 // Fused order-3 projection (stage c, float32): one CTA per (problem, kProj3Rows mode-1 rows of H),
 // requires b_2, b_3 <= 64.  The job table is followed by the Proj3Term records of all problems;
 // job j reads terms [term_begin, term_begin + nterms) of that array.
