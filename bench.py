@@ -224,6 +224,23 @@ def oracle_rate(problems, seed0, budget_s, kind, rounding):
     return done / dt, done, dt
 
 
+def oracle_rate_one_core(workload, seed, bf16, count=2):
+    """The oracle's rate with BLAS and OpenMP pinned to one thread, in a child process (the thread
+    counts are fixed when numpy loads), on the first `count` problems of the same batch."""
+    code = ("import json, sys, time; sys.path.insert(0, %r); import bench; "
+            "p = bench.make_problems(%d, %d, 0, %r, %r); "
+            "r, n, dt = bench.oracle_rate(p, %d, 1e9, bench.workload_kind(%r), %r); "
+            "print(json.dumps([r, n, dt]))") % (ROOT, count, seed, bf16, workload, seed, workload,
+                                                "bf16" if bf16 else None)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    try:
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+        rate, done, dt = json.loads(out.stdout.strip().splitlines()[-1])
+        return {"value": rate, "cores": 1, "sample": f"{done} problems in {dt:.1f} s, one BLAS/OpenMP thread"}
+    except Exception as e:   # the baseline is informative only
+        return {"value": None, "cores": 1, "sample": f"not measured: {type(e).__name__}"}
+
+
 def oracle_subrank_rate(problems, eps, budget_s):
     """Problems/s of the FP64 oracle's effective subrank heuristic over a bounded sample."""
     from oracle import subrank as sr
@@ -605,7 +622,8 @@ def main():
                                          "bf16" if bf16 else None)
             cpu = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                    "sample": f"{done} of the {P} problems of this batch in {dt:.1f} s (numpy float64, "
-                             f"BLAS on all host cores)"}
+                             f"BLAS on all host cores)",
+                   "single_core": oracle_rate_one_core(args.workload, args.seed, bf16)}
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
