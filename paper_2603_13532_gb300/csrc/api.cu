@@ -1422,7 +1422,8 @@ tks_status tks_plan_create(tks_plan** out, const tks_problem* problems, int32_t 
         h.g4_off.assign(h.K, 0);
         for (int k = 0; k < h.K; ++k) {
           const int* r = &h.ranks[(size_t)k * d];
-          fits = fits && fold4_smem_bytes(r[0], r[1], r[2], h.b[1]) <= 200 * 1024;
+          fits = fits && fold4_smem_bytes(r[0], r[1], r[2], h.b[1]) <= 200 * 1024 &&
+                 (int64_t)r[0] * r[2] * 4 <= kProj3SliceBytes;   // one float32 slice G'[:, :, i3]
           h.g4_off[k] = per_a1 * h.b[1];
           per_a1 += (int64_t)r[0] * r[2] * r[3];
         }
@@ -1870,10 +1871,10 @@ tks_status run_steps(tks_plan* plan, const std::vector<Step>& steps, const Bases
         launch_sketch3(static_cast<const Sketch3Job*>(table), s.njobs, s.smem, true, bases, stream);
         break;
       case S_PROJ3:
-        launch_proj3(static_cast<const Proj3Job*>(table), s.njobs, false, bases, stream);
+        launch_proj3(static_cast<const Proj3Job*>(table), s.njobs, false, bases, plan->status, stream);
         break;
       case S_PROJ3F:
-        launch_proj3(static_cast<const Proj3Job*>(table), s.njobs, true, bases, stream);
+        launch_proj3(static_cast<const Proj3Job*>(table), s.njobs, true, bases, plan->status, stream);
         break;
       case S_FOLD4:
         launch_fold4(static_cast<const Fold4Job*>(table), s.njobs, s.smem, bases, stream);

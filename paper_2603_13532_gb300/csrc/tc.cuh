@@ -119,6 +119,24 @@ __device__ __forceinline__ uint64_t sw128_kmajor_desc(uint32_t saddr) {
   return d;
 }
 
+// Shared-memory matrix descriptor of a K-major tile without swizzle: 8-row x 16-byte core
+// matrices (128 contiguous bytes), the core matrices of consecutive k blocks `lbo` bytes apart and
+// those of consecutive 8-row groups `sbo` bytes apart (both multiples of 16).
+__device__ __forceinline__ uint64_t plain_kmajor_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);   // start address, bits [0,14)
+  d |= static_cast<uint64_t>(lbo >> 4) << 16;            // leading (k) byte offset
+  d |= static_cast<uint64_t>(sbo >> 4) << 32;            // stride (row group) byte offset
+  d |= static_cast<uint64_t>(1) << 46;                   // descriptor version for tcgen05
+  return d;                                               // layout field 0: no swizzle
+}
+
+// Makes this thread's generic-proxy writes to shared memory visible to the tensor cores (async
+// proxy); a barrier after it orders them before an MMA issued by another thread.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 // Instruction descriptor of kind::f16: A, B bf16, D f32, both K-major, shape M x N.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |

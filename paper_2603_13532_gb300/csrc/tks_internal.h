@@ -158,10 +158,13 @@ struct Sketch4Job {
   int32_t pad;
 };
 
-// Fused order-3 projection (stage c, float32): one CTA per (problem, kProj3Rows mode-1 rows of H),
-// requires b_2, b_3 <= 64.  The job table is followed by the Proj3Term records of all problems;
-// job j reads terms [term_begin, term_begin + nterms) of that array.
+// Fused order-3 projection (stage c; float32 on the CUDA cores, split bf16 on the tensor cores):
+// one CTA per (problem, kProj3Rows mode-1 rows of H), requires b_2, b_3 <= 64.  The job table is
+// followed by the Proj3Term records of all problems; job j reads terms [term_begin, term_begin +
+// nterms) of that array.  A chunk stages at most kProj3SliceBytes of a core, and at least one
+// mode-3 slice G[:, :, i3] must fit.
 constexpr int kProj3Rows = 4;
+constexpr int kProj3SliceBytes = 12288;
 
 struct Proj3Term {
   Operand core;          // bf16 core of the term, mode-1 fastest
