@@ -711,6 +711,7 @@ static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
           t.roff[q] = h.roff[(size_t)k * d + q];
         }
         t.alpha = (float)h.alpha[k];
+        t.chunk = proj3_chunk(t.r, 2);
         p3terms.push_back(t);
         p3_flops += 2.0 * h.b[0] * ((double)r[0] * r[1] * r[2] + (double)h.b[1] * r[1] * r[2] +
                                     (double)h.b[1] * h.b[2] * r[2]);
@@ -772,6 +773,7 @@ static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
             t.roff[q] = h.roff[(size_t)k * d + modes[q]];
           }
           t.alpha = 1.0f;
+          t.chunk = proj3_chunk(t.r, 4);
           p3fterms.push_back(t);
           p3f_flops += 2.0 * b0 * ((double)r[0] * r[2] * r[3] + (double)b2 * r[2] * r[3] + (double)b2 * b3 * r[3]);
         }

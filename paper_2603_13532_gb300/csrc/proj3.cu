@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 
 #include "bf16.cuh"
+#include "fastdiv.cuh"
 #include "kernels.h"
 #include "tc.cuh"
 
@@ -30,10 +31,10 @@ namespace {
 
 constexpr int kRows = kProj3Rows;          // mode-1 rows per CTA
 constexpr int kPad = 64;                   // b2, b3 padded to 64 (N of the product)
-constexpr int kChunk = 16;                 // mode-3 indices per chunk (at most) = K of one MMA
+constexpr int kChunk = kProj3Chunk;        // mode-3 indices per chunk (at most) = K of one MMA
 constexpr int kGBytes = kProj3SliceBytes;  // bytes of the core slice per chunk (at most)
 constexpr int kGBuf = kGBytes + 32;        // + room for the 16-byte realignment of the slice
-constexpr int kW1 = 2048;                  // floats of W1 per chunk (at most)
+constexpr int kW1 = kProj3W1Floats;        // floats of W1 per chunk (at most)
 constexpr int kThreads = 256;
 constexpr int kR = TKS_MAX_RANK;
 // bf16 operand planes of s3, K-major without swizzle: core matrices of 8 rows x 8 k (16 bytes a
@@ -76,42 +77,18 @@ struct Smem {
   int err;
 };
 
-// Chunks of a term: r2 split into ceil(r2 / cmax) nearly equal pieces.
-template <typename CoreT>
-__device__ __forceinline__ int chunk_max(const Proj3Term& T) {
-  const int by_core = (int)(kGBytes / sizeof(CoreT)) / (T.r[0] * T.r[1]);
-  const int by_w1 = kW1 / (kRows * (T.r[1] | 1));
-  return min(kChunk, min(by_core, by_w1));
-}
-
 __device__ __forceinline__ float core_value(uint16_t h) { return bf16_float(h); }
 __device__ __forceinline__ float core_value(float v) { return v; }
 
 struct Pos {
-  int k, c, nchunks;   // term, chunk of the term, chunks of the term
+  int k, c;   // term, chunk of the term
 };
 
+// Chunk c of a term covers mode-3 indices [c0, c0 + nc) (the chunk length comes with the term).
 __device__ __forceinline__ void chunk_range(const Proj3Term& T, const Pos& p, int& c0, int& nc) {
-  const int r2 = T.r[2];
-  c0 = (p.c * r2) / p.nchunks;
-  nc = ((p.c + 1) * r2) / p.nchunks - c0;
+  c0 = p.c * T.chunk;
+  nc = min(T.chunk, T.r[2] - c0);
 }
-
-// Walks the elements e = tid, tid + kThreads, ... of a column-major (rows x cols) block as
-// (row, col) = (e % rows, e / rows) without a division per element.
-struct Walk {
-  int row, col, drow, dcol;
-  __device__ __forceinline__ Walk(int e, int rows)
-      : row(e % rows), col(e / rows), drow(kThreads % rows), dcol(kThreads / rows) {}
-  __device__ __forceinline__ void next(int rows) {
-    row += drow;
-    col += dcol;
-    if (row >= rows) {
-      row -= rows;
-      col += 1;
-    }
-  }
-};
 
 // The job's fields as registers.
 struct JobRegs {
@@ -131,20 +108,31 @@ __device__ __forceinline__ int issue_chunk(Smem& S, const JobRegs& J, const Proj
   const int r0 = T.r[0], r1 = T.r[1];
   int c0, nc;
   chunk_range(T, p, c0, nc);
+  // (the index maps below use shifts and masks only: a division by a rank costs ~20 instructions)
   if (p.c == 0) {
     const float* AT0 = J.AT[0] + T.roff[0];
     const float* AT1 = J.AT[1] + T.roff[1];
     float* A1 = S.A1[p.k & 1];
     float* A2 = S.A2[p.k & 1];
-    for (Walk w(tid, r0); w.col < J.rows; w.next(r0))
-      cp_async4(A1 + w.row * kRows + w.col, AT0 + w.row + J.R[0] * (J.x0 + w.col));
-    for (Walk w(tid, r1); w.col < J.b[1]; w.next(r1))
-      cp_async4(A2 + w.row * kPad + w.col, AT1 + w.row + J.R[1] * w.col);
+    // A1[i0][x] = A_1k[x0 + x, i0], e = kRows i0 + x
+    for (int e = tid; e < r0 * kRows; e += kThreads) {
+      const int x = e & (kRows - 1), i0 = e / kRows;
+      if (x < J.rows) cp_async4(A1 + e, AT0 + i0 + J.R[0] * (J.x0 + x));
+    }
+    // A2[i1][a1] = A_2k[a1, i1]: lanes along i1, contiguous in A_2^T
+    for (int e = tid; e < 32 * J.b[1]; e += kThreads) {
+      const int a1 = e >> 5;
+      const float* src = AT1 + J.R[1] * a1;
+      for (int i1 = e & 31; i1 < r1; i1 += 32) cp_async4(A2 + i1 * kPad + a1, src + i1);
+    }
   }
+  // A3[i2c][a2] = A_3k[a2, c0 + i2c]
   const float* AT2 = J.AT[2] + T.roff[2] + c0;
   float* A3 = S.A3[buf];
-  for (Walk w(tid, nc); w.col < J.b[2]; w.next(nc))
-    cp_async4(A3 + w.row * kPad + w.col, AT2 + w.row + J.R[2] * w.col);
+  for (int e = tid; e < kChunk * J.b[2]; e += kThreads) {
+    const int i2c = e & (kChunk - 1), a2 = e / kChunk;
+    if (i2c < nc) cp_async4(A3 + i2c * kPad + a2, AT2 + i2c + J.R[2] * a2);
+  }
   // the slice is contiguous: copy the 16-byte blocks that cover it (they lie in the pages of the
   // slice's own first and last bytes, so nothing outside mapped memory is touched)
   const char* g = reinterpret_cast<const char*>(at<CoreT>(bases, T.core) + (int64_t)r0 * r1 * c0);
@@ -156,13 +144,10 @@ __device__ __forceinline__ int issue_chunk(Smem& S, const JobRegs& J, const Proj
   return shift;
 }
 
-template <typename CoreT>
 __device__ __forceinline__ bool advance(const Proj3Term* terms, int nterms, Pos& p) {
-  if (++p.c < p.nchunks) return true;
+  if (++p.c * terms[p.k].chunk < terms[p.k].r[2]) return true;
   p.c = 0;
-  if (++p.k >= nterms) return false;
-  p.nchunks = (terms[p.k].r[2] + chunk_max<CoreT>(terms[p.k]) - 1) / chunk_max<CoreT>(terms[p.k]);
-  return true;
+  return ++p.k < nterms;
 }
 
 // Byte offset of element (row, k) in a plane: row group, k block, row in the group, k in the block.
@@ -216,7 +201,7 @@ __global__ void __launch_bounds__(kThreads, 2) project3_kernel(const Proj3Job* _
   int issued = 0;   // chunks whose products were issued
 
   if (nterms > 0) {
-    Pos cur{0, 0, (terms[0].r[2] + chunk_max<CoreT>(terms[0]) - 1) / chunk_max<CoreT>(terms[0])};
+    Pos cur{0, 0};
     int shift = issue_chunk<CoreT>(S, J, terms[0], cur, 0, bases);
     int buf = 0;
     bool more = true;
@@ -228,7 +213,7 @@ __global__ void __launch_bounds__(kThreads, 2) project3_kernel(const Proj3Job* _
       cp_async_wait_all();
       __syncthreads();   // this chunk is in shared memory; every thread is done with the other buffers
       Pos nxt = cur;
-      more = advance<CoreT>(terms, nterms, nxt);
+      more = advance(terms, nterms, nxt);
       int next_shift = 0;
       if (more) next_shift = issue_chunk<CoreT>(S, J, terms[nxt.k], nxt, buf ^ 1, bases);
       const float alpha = T.alpha;
@@ -237,8 +222,9 @@ __global__ void __launch_bounds__(kThreads, 2) project3_kernel(const Proj3Job* _
       const float* A3 = S.A3[buf];
       const CoreT* Gs = reinterpret_cast<const CoreT*>(S.G[buf]) + shift;
       // s1: pair p = i1 + r1 i2c reads the contiguous core column G[:, i1, c0 + i2c]
+      const SmallDiv dr1(r1);
       for (int p = tid; p < nc * r1; p += kThreads) {
-        const int i2c = p / r1, i1 = p - i2c * r1;
+        const int i2c = dr1.quo(p), i1 = p - i2c * r1;
         const CoreT* g = Gs + r0 * p;
         float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
         for (int i0 = 0; i0 < r0; ++i0) {

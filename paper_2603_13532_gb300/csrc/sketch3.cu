@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include "bf16.cuh"
+#include "fastdiv.cuh"
 #include "kernels.h"
 
 namespace tks {
@@ -66,20 +67,24 @@ __global__ void __launch_bounds__(kThreads) sketch3_term_kernel(const Sketch3Job
   const float* Mg0 = at<float>(bases, J.M[0]) + J.roff[0];
   const float* Mg1 = at<float>(bases, J.M[1]) + J.roff[1];
   const float* Mg2 = at<float>(bases, J.M[2]) + J.roff[2];
-  const int tot = r0 * r1 * r2;
+  const int tot = r0 * r1 * r2;   // <= 2^15: the index quotients below are SmallDiv's
+  const SmallDiv dr0(r0), dr1(r1);
 
   for (int e = tid; e < r0 * kCols; e += kThreads) {
-    const int i = e % r0, cc = e / r0;
+    const int cc = dr0.quo(e), i = e - cc * r0;
     M0s[i * kCols + cc] = cc < s ? Mg0[i + (int64_t)J.R[0] * cc] : 0.f;
   }
   for (int e = tid; e < r1 * kCols; e += kThreads) {
-    const int i = e % r1, cc = e / r1;
+    const int cc = dr1.quo(e), i = e - cc * r1;
     M1s[i * kCols + cc] = cc < s ? Mg1[i + (int64_t)J.R[1] * cc] : 0.f;
   }
   // first-pass copy of the core: Gb[i2 + r2p (i0 + r0 i1)], zero for i2 in [r2, r2p)
-  for (int e = tid; e < r0 * r1 * (r2p - r2); e += kThreads) {
-    const int pad = e % (r2p - r2), rest = e / (r2p - r2);
-    Gb[r2 + pad + r2p * rest] = CoreT(0);
+  if (r2p > r2) {
+    const SmallDiv dp(r2p - r2);
+    for (int e = tid; e < r0 * r1 * (r2p - r2); e += kThreads) {
+      const int rest = dp.quo(e), pad = e - rest * (r2p - r2);
+      Gb[r2 + pad + r2p * rest] = CoreT(0);
+    }
   }
   for (int e0 = 0; e0 < tot; e0 += kBatch * kThreads) {
     // kBatch independent loads in flight per thread before the scattered shared-memory stores
@@ -93,7 +98,7 @@ __global__ void __launch_bounds__(kThreads) sketch3_term_kernel(const Sketch3Job
     for (int u = 0; u < kBatch; ++u) {
       const int e = e0 + u * kThreads + tid;
       if (e < tot) {
-        const int i0 = e % r0, i1 = (e / r0) % r1, i2 = e / (r0 * r1);
+        const int q = dr0.quo(e), i0 = e - q * r0, i2 = dr1.quo(q), i1 = q - i2 * r1;
         Gb[i2 + r2p * (i0 + r0 * i1)] = to_core(v[u], CoreT());
       }
     }
@@ -144,7 +149,7 @@ __global__ void __launch_bounds__(kThreads) sketch3_term_kernel(const Sketch3Job
     if (i < r0) V0p[(grp * kMaxR + i) * kCols + c] = v0[i];
   __syncthreads();   // pass 1 is done with Gb; the V_0 partials are in place
   for (int e = tid; e < r0 * kCols; e += kThreads) {
-    const int i = e % r0, cc = e / r0;   // runs of consecutive rows of one column
+    const int cc = dr0.quo(e), i = e - cc * r0;   // runs of consecutive rows of one column
     if (cc < s) {
       float v = 0.f;
 #pragma unroll
@@ -153,9 +158,12 @@ __global__ void __launch_bounds__(kThreads) sketch3_term_kernel(const Sketch3Job
     }
   }
   // second-pass copy: Gb[i0 + r0p (i1 + r1 i2)], zero for i0 in [r0, r0p)
-  for (int e = tid; e < r1 * r2 * (r0p - r0); e += kThreads) {
-    const int pad = e % (r0p - r0), rest = e / (r0p - r0);
-    Gb[r0 + pad + r0p * rest] = CoreT(0);
+  if (r0p > r0) {
+    const SmallDiv dp(r0p - r0);
+    for (int e = tid; e < r1 * r2 * (r0p - r0); e += kThreads) {
+      const int rest = dp.quo(e), pad = e - rest * (r0p - r0);
+      Gb[r0 + pad + r0p * rest] = CoreT(0);
+    }
   }
   for (int e0 = 0; e0 < tot; e0 += kBatch * kThreads) {
     uint16_t v[kBatch];
@@ -167,7 +175,10 @@ __global__ void __launch_bounds__(kThreads) sketch3_term_kernel(const Sketch3Job
 #pragma unroll
     for (int u = 0; u < kBatch; ++u) {
       const int e = e0 + u * kThreads + tid;
-      if (e < tot) Gb[e % r0 + r0p * (e / r0)] = to_core(v[u], CoreT());
+      if (e < tot) {
+        const int q = dr0.quo(e);
+        Gb[e - q * r0 + r0p * q] = to_core(v[u], CoreT());
+      }
     }
   }
   float m0[kMaxR];

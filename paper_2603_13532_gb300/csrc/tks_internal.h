@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <string>
 
 #include "tks.h"
@@ -165,13 +166,24 @@ struct Sketch4Job {
 // mode-3 slice G[:, :, i3] must fit.
 constexpr int kProj3Rows = 4;
 constexpr int kProj3SliceBytes = 12288;
+constexpr int kProj3Chunk = 16;        // mode-3 indices of a chunk (at most): K of one MMA
+constexpr int kProj3W1Floats = 2048;   // first-stage products of a chunk (at most)
+
+// Mode-3 indices per chunk of a term with ranks r and core elements of `elem` bytes: the chunk's
+// core slice fits kProj3SliceBytes and its first-stage products kProj3W1Floats (odd row stride).
+inline int proj3_chunk(const int32_t r[3], int elem) {
+  int c = kProj3Chunk;
+  c = std::min(c, kProj3SliceBytes / elem / (r[0] * r[1]));
+  c = std::min(c, kProj3W1Floats / (kProj3Rows * (r[1] | 1)));
+  return c;
+}
 
 struct Proj3Term {
   Operand core;          // bf16 core of the term, mode-1 fastest
   int32_t r[3];          // term ranks
   int32_t roff[3];       // first row of the term in A_n^T
   float alpha;           // term weight
-  int32_t pad;
+  int32_t chunk;         // mode-3 indices per chunk: chunk c covers [c chunk, min(r3, (c + 1) chunk))
 };
 
 struct Proj3Job {

@@ -8,6 +8,7 @@
 // result goes back through shared memory so the stores are coalesced too.
 #include <cuda_runtime.h>
 
+#include "fastdiv.cuh"
 #include "kernels.h"
 
 namespace tks {
@@ -51,6 +52,7 @@ __global__ void __launch_bounds__(kThreads) ttm_rows_kernel(const TtmJob* __rest
   if (L == 1) {
     // the tile's fibres are contiguous: elements e = q b + a of a run starting at q0 b
     const int total = b * kRowsPerCta, valid = b * nq;
+    const SmallDiv db(b);
     for (int e0 = 0; e0 < total; e0 += kBatch * kThreads) {
       float v[kBatch];
 #pragma unroll
@@ -61,8 +63,8 @@ __global__ void __launch_bounds__(kThreads) ttm_rows_kernel(const TtmJob* __rest
 #pragma unroll
       for (int u = 0; u < kBatch; ++u) {
         const int e = e0 + u * kThreads + threadIdx.x;
-        if (e < total) {
-          const int q = e / b;
+        if (e < total) {   // e < TKS_MAX_BASIS kRowsPerCta < 2^16
+          const int q = db.quo(e);
           Xs[(e - q * b) * kXs + q] = v[u];
         }
       }
@@ -118,8 +120,9 @@ __global__ void __launch_bounds__(kThreads) ttm_rows_kernel(const TtmJob* __rest
   char* Y = at<char>(bases, J.Y);
   const bool f64 = J.y_type == T_F64;
   if (L == 1) {
+    const SmallDiv dr(rmax);
     for (int e = threadIdx.x; e < rmax * nq; e += kThreads) {
-      const int q = e / rmax, c = e % rmax;
+      const int q = dr.quo(e), c = e - q * rmax;
       const int64_t off = c + (int64_t)rmax * (q0 + q);
       const float v = Xs[c * kXs + q];
       if (f64) reinterpret_cast<double*>(Y)[off] = (double)v; else reinterpret_cast<float*>(Y)[off] = v;
