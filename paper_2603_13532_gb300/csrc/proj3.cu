@@ -44,6 +44,7 @@ constexpr int kLbo = 144;
 constexpr int kSbo = 288;
 constexpr int kPlaneA = 16 * kSbo;         // one M-half (128 rows (a1, x)) of one plane of W2
 constexpr int kPlaneB = 8 * kSbo;          // the 64 rows a2 of one plane of A_3k
+constexpr int kLd3 = 20;                   // row stride of A3 (floats): conflict-free 16-byte reads of 8 rows
 constexpr int kTmemCols = 256;             // [hi x hi | corrections] x [M-half 0 | M-half 1] x 64
 constexpr long long kWaitCycles = 4000000000LL;   // about 2 s at 2 GHz
 
@@ -68,8 +69,8 @@ struct Smem {
   unsigned char PA[3][2][kPlaneA];  // bf16 planes of W2 [plane][M-half], rows (a1, x) = 4 a1 + x
   unsigned char PB[3][kPlaneB];     // bf16 planes of the chunk's A_3k [plane], rows a2
   float A1[2][kR * kRows];          // [i0][x]
-  float A2[2][kR * kPad];           // [i1][a1]
-  float A3[2][kChunk * kPad];       // [i2c][a2]
+  float A2[2][kPad * kR];           // [a1][i1], row stride (r1 + 3) & ~3
+  float A3[2][kPad * kLd3];         // [a2][i2c]
   float W1[kW1];                    // [i2c][i1][x], i2c stride (r1 | 1) kRows
   __align__(16) unsigned char G[2][kGBuf];   // core slice G[:, :, c0 : c0 + nc], realigned to 16 bytes
   uint64_t mma_done;                // one phase per chunk: its products have completed
@@ -119,19 +120,20 @@ __device__ __forceinline__ int issue_chunk(Smem& S, const JobRegs& J, const Proj
       const int x = e & (kRows - 1), i0 = e / kRows;
       if (x < J.rows) cp_async4(A1 + e, AT0 + i0 + J.R[0] * (J.x0 + x));
     }
-    // A2[i1][a1] = A_2k[a1, i1]: lanes along i1, contiguous in A_2^T
+    // A2[a1][i1] = A_2k[a1, i1]: lanes along i1, contiguous in A_2^T and in shared memory
+    const int ld2 = (r1 + 3) & ~3;
     for (int e = tid; e < 32 * J.b[1]; e += kThreads) {
       const int a1 = e >> 5;
       const float* src = AT1 + J.R[1] * a1;
-      for (int i1 = e & 31; i1 < r1; i1 += 32) cp_async4(A2 + i1 * kPad + a1, src + i1);
+      for (int i1 = e & 31; i1 < r1; i1 += 32) cp_async4(A2 + a1 * ld2 + i1, src + i1);
     }
   }
-  // A3[i2c][a2] = A_3k[a2, c0 + i2c]
+  // A3[a2][i2c] = A_3k[a2, c0 + i2c]: lanes along i2c
   const float* AT2 = J.AT[2] + T.roff[2] + c0;
   float* A3 = S.A3[buf];
   for (int e = tid; e < kChunk * J.b[2]; e += kThreads) {
     const int i2c = e & (kChunk - 1), a2 = e / kChunk;
-    if (i2c < nc) cp_async4(A3 + i2c * kPad + a2, AT2 + i2c + J.R[2] * a2);
+    if (i2c < nc) cp_async4(A3 + a2 * kLd3 + i2c, AT2 + i2c + J.R[2] * a2);
   }
   // the slice is contiguous: copy the 16-byte blocks that cover it (they lie in the pages of the
   // slice's own first and last bytes, so nothing outside mapped memory is touched)
@@ -254,16 +256,36 @@ __global__ void __launch_bounds__(kThreads, 2) project3_kernel(const Proj3Job* _
             for (int x = 0; x < kRows; ++x) w2[j][x] = 0.f;
           if (i2c < nc) {
             const float* w1 = S.W1 + kRows * (i2c * r1s);
-            for (int i1 = 0; i1 < r1; ++i1) {
-              const float4 a = *reinterpret_cast<const float4*>(A2 + i1 * kPad + a1b);
-              const float4 w = *reinterpret_cast<const float4*>(w1 + kRows * i1);
-              const float av[4] = {a.x, a.y, a.z, a.w};
+            const int ld2 = (r1 + 3) & ~3;
+            const float* a2r = A2 + a1b * ld2;   // rows a1b .. a1b + 3
+            int i1 = 0;
+            for (; i1 + 4 <= r1; i1 += 4) {   // four i1 at a time: 16-byte reads along i1
+              float4 a[4], w[4];
+#pragma unroll
+              for (int j = 0; j < 4; ++j) a[j] = *reinterpret_cast<const float4*>(a2r + j * ld2 + i1);
+#pragma unroll
+              for (int u = 0; u < 4; ++u) w[u] = *reinterpret_cast<const float4*>(w1 + kRows * (i1 + u));
 #pragma unroll
               for (int j = 0; j < 4; ++j) {
-                w2[j][0] = fmaf(av[j], w.x, w2[j][0]);
-                w2[j][1] = fmaf(av[j], w.y, w2[j][1]);
-                w2[j][2] = fmaf(av[j], w.z, w2[j][2]);
-                w2[j][3] = fmaf(av[j], w.w, w2[j][3]);
+                const float av[4] = {a[j].x, a[j].y, a[j].z, a[j].w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                  w2[j][0] = fmaf(av[u], w[u].x, w2[j][0]);
+                  w2[j][1] = fmaf(av[u], w[u].y, w2[j][1]);
+                  w2[j][2] = fmaf(av[u], w[u].z, w2[j][2]);
+                  w2[j][3] = fmaf(av[u], w[u].w, w2[j][3]);
+                }
+              }
+            }
+            for (; i1 < r1; ++i1) {
+              const float4 w = *reinterpret_cast<const float4*>(w1 + kRows * i1);
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                const float av = a2r[j * ld2 + i1];
+                w2[j][0] = fmaf(av, w.x, w2[j][0]);
+                w2[j][1] = fmaf(av, w.y, w2[j][1]);
+                w2[j][2] = fmaf(av, w.z, w2[j][2]);
+                w2[j][3] = fmaf(av, w.w, w2[j][3]);
               }
             }
           }
@@ -284,12 +306,15 @@ __global__ void __launch_bounds__(kThreads, 2) project3_kernel(const Proj3Job* _
       // rows a2 < b2 of the chunk's A_3k, split, k = i2c (zeros for i2c >= nc)
       if (tid < 2 * kPad && (tid & (kPad - 1)) < b2) {
         const int a2 = tid & (kPad - 1), kb = tid >> 6;
+        const float4 lo = *reinterpret_cast<const float4*>(A3 + a2 * kLd3 + 8 * kb);
+        const float4 hi = *reinterpret_cast<const float4*>(A3 + a2 * kLd3 + 8 * kb + 4);
+        const float av[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
         uint32_t q0[4], q1[4], q2[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           const int k = 8 * kb + 2 * e;
-          const float v0 = k < nc ? A3[k * kPad + a2] : 0.f;
-          const float v1 = k + 1 < nc ? A3[(k + 1) * kPad + a2] : 0.f;
+          const float v0 = k < nc ? av[2 * e] : 0.f;
+          const float v1 = k + 1 < nc ? av[2 * e + 1] : 0.f;
           uint16_t l0, l1, l2, u0, u1, u2;
           split3(v0, l0, l1, l2);
           split3(v1, u0, u1, u2);
