@@ -315,13 +315,28 @@ FP32_KINDS = {"simt", "core_sketch32", "qr32", "svd32", "tsqr32", "core_sketch3"
 NCU_TRAFFIC_PER_PROBLEM = {("decay512", "a7:project3[f32]"): (15.567104e6 + 0.150528e6) / 16}
 
 
-def roofline_from_profile(prof, calls, peaks, workload=None, problems=0):
+def project3_tensor_flops(plan, problems):
+    """Algorithmic flops of the fused projection's tensor-core contraction (s3: 2 b0 b1 b2 r_k3 per
+    term) over the problems that take that kernel (order 3, b2, b3 <= 64, mixed precision)."""
+    total = 0.0
+    for p, pi in zip(problems, plan.pinfo):
+        b = [pi.basis_cols[m] for m in range(p.order)]
+        if p.order != 3 or b[1] > 64 or b[2] > 64:
+            continue
+        total += sum(2.0 * b[0] * b[1] * b[2] * r[2] for r in p.ranks())
+    return total
+
+
+def roofline_from_profile(prof, calls, peaks, workload=None, problems=0, tensor_flops=None):
     """The longest launch with an algorithmic count, and its achieved rate against its roofline.
 
     FP64 CUDA-core launches are bound by the FP64 pipe, FP32 CUDA-core launches by the FP32 pipe
     (peaks from unit counts and the 2070 MHz clock); tensor-core launches by the tensor pipe or
     HBM, whichever the launch's algorithmic arithmetic intensity puts first (ridge = sustained
-    bf16 peak / HBM bandwidth).
+    bf16 peak / HBM bandwidth).  The fused projection runs on two pipes at once: its first two
+    contractions on the FP32 pipe and the third (`tensor_flops`) on the tensor pipe as six bf16
+    products of split operands; its peak is the rate at which the busier of the two pipes would
+    finish the launch's algorithmic flops.
     """
     total_ms = sum(s["ms"] for s in prof)
     counted = [s for s in prof if s["flops"] > 0 or s["bytes"] > 0]
@@ -329,7 +344,17 @@ def roofline_from_profile(prof, calls, peaks, workload=None, problems=0):
     overall_top = max(prof, key=lambda s: s["ms"])
     avg_s = top["ms"] / 1e3 / max(1, calls)
     kind = top["kind"]
-    if kind in FP64_KINDS and top["flops"] > 0:
+    if kind == "project3" and top["flops"] > 0 and tensor_flops:
+        f_tc = min(tensor_flops, top["flops"])
+        t_alu = (top["flops"] - f_tc) / (FP32_PEAK_TFLOPS * 1e12)
+        t_tc = 6.0 * f_tc / (peaks["bf16_tflops_sustained"] * 1e12)
+        roof = {"bound": "alu" if t_alu >= t_tc else "tensor", "achieved": top["flops"] / avg_s / 1e12,
+                "peak": top["flops"] / max(t_alu, t_tc) / 1e12, "unit": "TFLOP/s",
+                "peak_source": "two pipes: s1, s2 on the FP32 pipe (derived 152 SMs x 256 flop/clk x 2070 MHz), "
+                               "s3 as 6 bf16 products on the tensor pipe (measured bf16 sustained / 6); peak = "
+                               "algorithmic flops / the longer of the two pipe times",
+                "tensor_flops_per_launch": f_tc}
+    elif kind in FP64_KINDS and top["flops"] > 0:
         roof = {"bound": "alu", "achieved": top["flops"] / avg_s / 1e12, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "peak_source": "derived FP64: 152 SMs x 4 flop/clk x 2070 MHz"}
     elif kind in FP32_KINDS and top["flops"] > 0:
@@ -444,7 +469,8 @@ def main():
     tflops = (plan.info.flops_lowprec + plan.info.flops_fp64) * world * args.steps / elapsed / 1e12
 
     peaks, peak_src = load_peaks()
-    roof = roofline_from_profile(prof, args.steps, peaks, args.workload, P)
+    roof = roofline_from_profile(prof, args.steps, peaks, args.workload, P,
+                                 tensor_flops=project3_tensor_flops(plan, problems) if bf16 else None)
     roof["peak_file"] = peak_src
 
     # end to end: every step copies its inputs from pinned host memory, recompresses and reads the

@@ -38,7 +38,6 @@ tks_status fail(tks_status st, const std::string& msg) {
   } while (0)
 
 constexpr size_t kAlign = 256;
-constexpr size_t kSketch3F32Smem = 110 * 1024;   // largest float32-core sketch CTA (two per SM)
 inline size_t align_up(size_t x, size_t a = kAlign) { return (x + a - 1) / a * a; }
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
@@ -520,7 +519,9 @@ static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
           j.alpha = (float)h.alpha[k];
           const double fl = 2.0 * h.s[0] * (2.0 * r[0] * r[1] * r[2] + 2.0 * r[0] * r[1] + (double)r[1] * r[2]);
           // float32 core copies when two CTAs per SM still fit, else bf16 copies
-          if (sketch3_smem_bytes(r, true) <= kSketch3F32Smem) {
+          const bool f32_copy = sketch3_fits_f32(r);
+          j.r2p = sketch3_stride(r, f32_copy);
+          if (f32_copy) {
             sk3f.push_back(j);
             sk3f_smem = std::max(sk3f_smem, sketch3_smem_bytes(r, true));
             sk3f_flops += fl;

@@ -50,6 +50,8 @@ void launch_ttm_rows(const TtmJob* jobs, int njobs, int total_tiles, const Bases
 // Khatri-Rao core sketches of order-3 terms, one CTA per term.
 // f32_core: the core copies in shared memory are float32 (faster, twice the shared memory).
 size_t sketch3_smem_bytes(const int r[3], bool f32_core);
+bool sketch3_fits_f32(const int r[3]);   // float32 core copies with two CTAs per SM
+int sketch3_stride(const int r[3], bool f32_core);   // Sketch3Job::r2p
 cudaError_t prepare_sketch3();
 void launch_sketch3(const Sketch3Job* jobs, int njobs, size_t smem, bool f32_core, const Bases& bases,
                     cudaStream_t stream);

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "bf16.cuh"
+#include "fastdiv.cuh"
 #include "kernels.h"
 
 namespace tks {
@@ -316,6 +317,7 @@ __global__ void __launch_bounds__(kQrRegThreads, 1) qr_reg_f32_kernel(const QrF3
   const int n = (int)J.rows, S = (int)J.cols, b = J.b;
   const char* src = at<char>(bases, J.src);
   const uint32_t L0 = (uint32_t)J.L0;
+  const SmallDiv dn(n), dl0((int)L0);   // n <= 512, L0 <= n, e < n S <= 2^15
   if (threadIdx.x == 0) sh_bad = 0;
   for (int e0 = 0; e0 < n * S; e0 += kLoadBatch * kQrRegThreads) {
     float v[kLoadBatch];
@@ -324,8 +326,8 @@ __global__ void __launch_bounds__(kQrRegThreads, 1) qr_reg_f32_kernel(const QrF3
       const int e = e0 + u * kQrRegThreads + threadIdx.x;
       v[u] = 0.f;
       if (e < n * S) {
-        const int j = e / n, i = e - j * n;
-        const uint32_t i1 = (uint32_t)i / L0, i0 = (uint32_t)i - i1 * L0;
+        const int j = dn.quo(e), i = e - j * n;
+        const uint32_t i1 = (uint32_t)dl0.quo(i), i0 = (uint32_t)i - i1 * L0;
         v[u] = load_any(src, J.src_type, (int64_t)i0 * J.s0 + (int64_t)i1 * J.s1 + (int64_t)j * J.sc);
       }
     }
@@ -460,7 +462,8 @@ __global__ void __launch_bounds__(kTsqrThreads, kTsqrRowsPerLane * kSlots <= 32 
   // stage: columns fastest when a row is contiguous in the source, else rows; kLoadBatch loads
   // in flight per thread before the shared-memory stores
   const bool row_major = J.sc == 1;
-  const int mb = m * b;
+  const int mb = m * b;   // <= 2^15 (m <= 512 when b <= 64, else m <= 256)
+  const SmallDiv dq(row_major ? b : m);
   for (int e0 = 0; e0 < mb; e0 += kLoadBatch * kTsqrThreads) {
     float v[kLoadBatch];
     int dst[kLoadBatch];
@@ -470,7 +473,7 @@ __global__ void __launch_bounds__(kTsqrThreads, kTsqrRowsPerLane * kSlots <= 32 
       v[u] = 0.f;
       dst[u] = -1;
       if (e < mb) {
-        const int q = row_major ? e / b : e / m;
+        const int q = dq.quo(e);
         const int r = row_major ? q : e - q * m, c = row_major ? e - q * b : q;
         v[u] = load_any(src, J.src_type, rowoff[r] + (int64_t)c * J.sc);
         dst[u] = r + ld * c;

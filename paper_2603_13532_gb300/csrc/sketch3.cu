@@ -41,6 +41,24 @@ __device__ __forceinline__ float4 load4(const float* p) { return *reinterpret_ca
 __device__ __forceinline__ uint16_t to_core(uint16_t h, uint16_t) { return h; }
 __device__ __forceinline__ float to_core(uint16_t h, float) { return __uint_as_float((uint32_t)h << 16); }
 
+constexpr size_t kF32Smem = 110 * 1024;   // largest float32-core CTA (two per SM)
+
+size_t smem_for(int r0, int r1, int r2, int r2p, bool f32) {
+  const size_t r0p = (r0 + 3) & ~3;
+  const size_t g = (size_t)r2p * r0 * r1 > r0p * r1 * r2 ? (size_t)r2p * r0 * r1 : r0p * r1 * r2;
+  return sizeof(float) * (2 + kGroups) * kMaxR * kCols + (f32 ? 4 : 2) * g;
+}
+
+// Row stride of the first-pass core copy (i2 fastest): a multiple of 4 for the 16-byte reads.
+// Float32 copies take 4 mod 8 where that still fits two CTAs per SM, so that the staging stores
+// of consecutive i0 (r2p floats apart) are 4-way bank conflicts instead of up to 32-way (r2p = 32);
+// the bf16 launch keeps the plain stride (its shared memory is that of its largest term).
+int pass1_stride(int r0, int r1, int r2, bool f32) {
+  const int p = (r2 + 3) & ~3;
+  if (!f32 || (p & 7) != 0) return p;
+  return smem_for(r0, r1, r2, p + 4, true) <= kF32Smem ? p + 4 : p;
+}
+
 __device__ __forceinline__ void store_planes(const Bases& bases, const Operand* planes, int64_t off, float v) {
   uint16_t h0, h1, h2;
   split3(v, h0, h1, h2);
@@ -56,7 +74,7 @@ __global__ void __launch_bounds__(kThreads) sketch3_term_kernel(const Sketch3Job
   extern __shared__ __align__(16) float s3s[];
   const Sketch3Job& J = jobs[blockIdx.x];
   const int r0 = J.r[0], r1 = J.r[1], r2 = J.r[2], s = J.s;
-  const int r0p = (r0 + 3) & ~3, r2p = (r2 + 3) & ~3;
+  const int r0p = (r0 + 3) & ~3, r2p = J.r2p;
   const int tid = threadIdx.x, c = tid % kCols, grp = tid / kCols;
   const bool live = c < s;
   float* M0s = s3s;                                   // [i0][c]
@@ -210,10 +228,12 @@ __global__ void __launch_bounds__(kThreads) sketch3_term_kernel(const Sketch3Job
 }  // namespace
 
 size_t sketch3_smem_bytes(const int r[3], bool f32_core) {
-  const size_t r0p = (r[0] + 3) & ~3, r2p = (r[2] + 3) & ~3;
-  const size_t g = std::max(r2p * r[0] * r[1], r0p * r[1] * r[2]);
-  return sizeof(float) * (2 + kGroups) * kMaxR * kCols + (f32_core ? 4 : 2) * g;
+  return smem_for(r[0], r[1], r[2], pass1_stride(r[0], r[1], r[2], f32_core), f32_core);
 }
+
+int sketch3_stride(const int r[3], bool f32_core) { return pass1_stride(r[0], r[1], r[2], f32_core); }
+
+bool sketch3_fits_f32(const int r[3]) { return smem_for(r[0], r[1], r[2], (r[2] + 3) & ~3, true) <= kF32Smem; }
 
 cudaError_t prepare_sketch3() {
   cudaError_t e =
