@@ -310,9 +310,9 @@ FP32_KINDS = {"simt", "core_sketch32", "qr32", "svd32", "tsqr32", "core_sketch3"
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch per problem, from an ncu
-# capture of the same kernel binary on 16 decay512 problems (15.567 MB read + 0.151 MB written),
+# capture of the same kernel binary on 16 decay512 problems (15.594 MB read + 0.274 MB written),
 # used to scale the measured traffic to the bench launch; only valid for that kernel and workload.
-NCU_TRAFFIC_PER_PROBLEM = {("decay512", "a7:project3[f32]"): (15.567104e6 + 0.150528e6) / 16}
+NCU_TRAFFIC_PER_PROBLEM = {("decay512", "a7:project3[f32]"): (15.593984e6 + 0.273920e6) / 16}
 
 
 def project3_tensor_flops(plan, problems):
