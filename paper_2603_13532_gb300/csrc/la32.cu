@@ -22,6 +22,47 @@ __device__ __forceinline__ float warp_sum_f(float v) {
   return v;
 }
 
+// Warp sums of kN independent values, their butterflies interleaved (one shuffle latency per
+// level instead of kN).
+template <int kN>
+__device__ __forceinline__ void warp_sum_n(float (&v)[kN]) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int q = 0; q < kN; ++q) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+}
+
+// Step j of the register-resident Householder sweeps: apply reflector (vj, tau) to every column
+// l > j (l < ncols) that this warp holds, all slots' dot products and warp reductions interleaved.
+template <int kRpl, int kSlots, int kWarps>
+__device__ __forceinline__ void apply_reflector(float (&a)[kSlots][kRpl], const float (&vj)[kRpl], float tau, int j,
+                                                int ncols) {
+  const int warp = threadIdx.x >> 5;
+  if (tau == 0.f) return;
+  float dot[kSlots];
+#pragma unroll
+  for (int sl = 0; sl < kSlots; ++sl) {
+    float d0 = 0.f, d1 = 0.f;
+#pragma unroll
+    for (int u = 0; u + 1 < kRpl; u += 2) {
+      d0 = fmaf(vj[u], a[sl][u], d0);
+      d1 = fmaf(vj[u + 1], a[sl][u + 1], d1);
+    }
+    if (kRpl & 1) d0 = fmaf(vj[kRpl - 1], a[sl][kRpl - 1], d0);
+    dot[sl] = d0 + d1;
+  }
+  warp_sum_n(dot);
+#pragma unroll
+  for (int sl = 0; sl < kSlots; ++sl) {
+    const int l = warp + kWarps * sl;
+    if (l > j && l < ncols) {
+      const float w = tau * dot[sl];
+#pragma unroll
+      for (int u = 0; u < kRpl; ++u) a[sl][u] = fmaf(-w, vj[u], a[sl][u]);
+    }
+  }
+}
+
 __device__ float block_sum_f(float v, float* red) {
   v = warp_sum_f(v);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -361,20 +402,11 @@ __global__ void __launch_bounds__(kQrRegThreads, 1) qr_reg_f32_kernel(const QrF3
       const int i = lane + 32 * u;
       vj[u] = i < n ? vs[i + n * j] : 0.f;
     }
+    apply_reflector<kRpl, kSlots, kQrRegWarps>(a, vj, tau, j, S);
 #pragma unroll
     for (int sl = 0; sl < kSlots; ++sl) {
       const int l = warp + kQrRegWarps * sl;
-      if (l > j && l < S) {
-        if (tau != 0.f) {
-          float dot = 0.f;
-#pragma unroll
-          for (int u = 0; u < kRpl; ++u) dot = fmaf(vj[u], a[sl][u], dot);
-          const float w = tau * warp_sum_f(dot);
-#pragma unroll
-          for (int u = 0; u < kRpl; ++u) a[sl][u] = fmaf(-w, vj[u], a[sl][u]);
-        }
-        if (l == j + 1 && l < b) bad |= !reflector_publish(a[sl], l, n, vs + n * l, n, &tau_s[l], rdiag_s);
-      }
+      if (l == j + 1 && l < b) bad |= !reflector_publish(a[sl], l, n, vs + n * l, n, &tau_s[l], rdiag_s);
     }
     __syncthreads();
   }
@@ -503,21 +535,12 @@ __global__ void __launch_bounds__(kTsqrThreads, kTsqrRowsPerLane * kSlots <= 32 
     float vj[kTsqrRowsPerLane];
 #pragma unroll
     for (int u = 0; u < kTsqrRowsPerLane; ++u) vj[u] = vbuf[j & 1][lane + 32 * u];
+    apply_reflector<kTsqrRowsPerLane, kSlots, kTsqrWarps>(a, vj, tau, j, b);
 #pragma unroll
     for (int sl = 0; sl < kSlots; ++sl) {
       const int l = warp + kTsqrWarps * sl;
-      if (l > j && l < b) {
-        if (tau != 0.f) {
-          float dot = 0.f;
-#pragma unroll
-          for (int u = 0; u < kTsqrRowsPerLane; ++u) dot = fmaf(vj[u], a[sl][u], dot);
-          const float w = tau * warp_sum_f(dot);
-#pragma unroll
-          for (int u = 0; u < kTsqrRowsPerLane; ++u) a[sl][u] = fmaf(-w, vj[u], a[sl][u]);
-        }
-        if (l == j + 1 && l < kmax)
-          reflector_publish(a[sl], l, m, vbuf[(j + 1) & 1], kBlockRows, &sh_tau[(j + 1) & 1], rdiag);
-      }
+      if (l == j + 1 && l < kmax)
+        reflector_publish(a[sl], l, m, vbuf[(j + 1) & 1], kBlockRows, &sh_tau[(j + 1) & 1], rdiag);
     }
     __syncthreads();
   }
