@@ -99,7 +99,10 @@ __global__ void __launch_bounds__(kThreads) ttm_rows_kernel(const TtmJob* __rest
   for (int i = 0; i < 8; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-  for (int a = 0; a < b; ++a) {
+  // columns 4 tc .. 4 tc + 3 at or beyond rmax are never written out: their threads skip the
+  // product (with rmax = 48 a quarter of the tile)
+  const int bq = 4 * tc < rmax ? b : 0;
+  for (int a = 0; a < bq; ++a) {
     const float4 x0 = *reinterpret_cast<const float4*>(Xs + a * kXs + 8 * tr);
     const float4 x1 = *reinterpret_cast<const float4*>(Xs + a * kXs + 8 * tr + 4);
     const float4 p = *reinterpret_cast<const float4*>(Ps + a * kMaxCols + 4 * tc);
