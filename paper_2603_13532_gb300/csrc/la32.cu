@@ -714,14 +714,21 @@ __global__ void __launch_bounds__(kSvdThreads) svd_jacobi_f32_kernel(const SvdJo
     for (int i = threadIdx.x; i < b; i += blockDim.x) part += nrm[i];
     tot = block_sum_f(part, red);
   }
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < b; ++i) order[i] = i;
-    for (int i = 0; i < b; ++i) {
-      int best = i;
-      for (int j = i + 1; j < b; ++j)
-        if (nrm[order[j]] > nrm[order[best]]) best = j;
-      const int t = order[i]; order[i] = order[best]; order[best] = t;
+  // columns by decreasing norm: thread i places column i at its rank (ties by index; a NaN norm
+  // counts as -1, so the ranks always form a permutation); a serial selection sort here cost
+  // b^2 / 2 dependent shared-memory reads in one thread
+  if ((int)threadIdx.x < b) {
+    const int i = threadIdx.x;
+    const float ni = nrm[i] == nrm[i] ? nrm[i] : -1.f;
+    int rk = 0;
+    for (int j = 0; j < b; ++j) {
+      const float nj = nrm[j] == nrm[j] ? nrm[j] : -1.f;
+      rk += (nj > ni || (nj == ni && j < i)) ? 1 : 0;
     }
+    order[rk] = i;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
     float* sv = at<float>(bases, J.sv);
     for (int i = 0; i < b; ++i) sv[i] = sqrtf(nrm[order[i]]);
     double* theta = at<double>(bases, J.theta);
