@@ -42,13 +42,16 @@ __device__ __forceinline__ void apply_reflector(float (&a)[kSlots][kRpl], const 
   float dot[kSlots];
 #pragma unroll
   for (int sl = 0; sl < kSlots; ++sl) {
+    const int l = warp + kWarps * sl;
     float d0 = 0.f, d1 = 0.f;
+    if (l > j && l < ncols) {   // warp-uniform: finished and absent columns skip the products
 #pragma unroll
-    for (int u = 0; u + 1 < kRpl; u += 2) {
-      d0 = fmaf(vj[u], a[sl][u], d0);
-      d1 = fmaf(vj[u + 1], a[sl][u + 1], d1);
+      for (int u = 0; u + 1 < kRpl; u += 2) {
+        d0 = fmaf(vj[u], a[sl][u], d0);
+        d1 = fmaf(vj[u + 1], a[sl][u + 1], d1);
+      }
+      if (kRpl & 1) d0 = fmaf(vj[kRpl - 1], a[sl][kRpl - 1], d0);
     }
-    if (kRpl & 1) d0 = fmaf(vj[kRpl - 1], a[sl][kRpl - 1], d0);
     dot[sl] = d0 + d1;
   }
   warp_sum_n(dot);
