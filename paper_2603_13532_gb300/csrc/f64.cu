@@ -461,19 +461,23 @@ __global__ void __launch_bounds__(512) eig_f64_kernel(const EigJob* __restrict__
     if (!sh_rot) break;
     __syncthreads();
   }
-  // sort eigenvalues descending (stable selection by index), choose the rank, emit P
+  // eigenvalues in decreasing order (ties by index): thread i places eigenvalue i at its rank, a
+  // NaN counting as -inf so that the ranks always form a permutation (a one-thread selection
+  // sort here cost b^2 / 2 dependent shared-memory reads); then choose the rank, emit P
+  for (int i = threadIdx.x; i < b; i += blockDim.x) ev[i] = A[i + i * ld];
+  __syncthreads();
+  for (int i = threadIdx.x; i < b; i += blockDim.x) {
+    const double ei = ev[i] == ev[i] ? ev[i] : -INFINITY;
+    int rk = 0;
+    for (int j = 0; j < b; ++j) {
+      const double ej = ev[j] == ev[j] ? ev[j] : -INFINITY;
+      rk += (ej > ei || (ej == ei && j < i)) ? 1 : 0;
+    }
+    pp[rk] = i;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
     bool bad = !isfinite(tr);
-    for (int i = 0; i < b; ++i) {
-      ev[i] = A[i + i * ld];
-      pp[i] = i;
-    }
-    for (int i = 0; i < b; ++i) {
-      int best = i;
-      for (int j = i + 1; j < b; ++j)
-        if (ev[pp[j]] > ev[pp[best]]) best = j;
-      const int t = pp[i]; pp[i] = pp[best]; pp[best] = t;
-    }
     double* evals = at<double>(bases, J.evals);
     for (int i = 0; i < b; ++i) evals[i] = ev[pp[i]];
     double* theta = at<double>(bases, J.theta);
