@@ -57,7 +57,7 @@ typedef enum {
   TKS_ECUDA = 3,         /* a CUDA runtime call failed (message in tks_last_error) */
   TKS_ETIMEOUT = 4,      /* a bounded device-side wait ran out (kernel returned early) */
   TKS_ENONFINITE = 5,    /* a NaN or Inf reached the sketch or the projected core */
-  TKS_ENOCONV = 6,       /* the small symmetric eigensolver hit its sweep limit */
+  TKS_ENOCONV = 6,       /* a Jacobi SVD of the ST-HOSVD hit its sweep limit */
   TKS_EUNSUPPORTED = 7   /* valid input outside the limits the library supports */
 } tks_status;
 
@@ -214,7 +214,8 @@ TKS_API tks_status tks_sync_status(tks_plan* plan, void* stream);
  * once (float64 or the operand's own element size). */
 typedef struct {
   char name[32];          /* stage, e.g. "b2:Y=UcatVcat" */
-  int32_t kind;           /* 0 Omega, 1 GEMM, 2 split-K reduction, 3 core sketch, 4 QR, 5 eig */
+  int32_t kind;           /* launch kind: 0 Omega, 1 float64 GEMM, 2 split-K reduction, 3 core sketch,
+                             4 QR, 5 float64 TSQR level, 6 tensor-core GEMM, ... (the list in binding.py) */
   int32_t calls;          /* recompress calls timed */
   double ms;              /* summed duration over those calls */
   double flops;           /* algorithmic flops of one call */
@@ -228,20 +229,27 @@ TKS_API tks_status tks_profile_end(tks_plan* plan, tks_step_profile_t* out, int3
  * problem alone in a plan) for callers that cannot allocate device memory: code that must not
  * call cudaMalloc because another framework owns all device memory through its own pool, because
  * it runs where allocation is forbidden or too slow (real-time loops, callbacks on a hot path),
- * or because it is embedded in a host program that never creates a plan.  There is no
- * counterpart in the paper; this is a deployment variant of tucker_sum_sketch.
+ * or because it is embedded in a host program that never creates a plan.  The paper has no
+ * counterpart of this entry point; it is a deployment variant of tucker_sum_sketch.
  *
  * Inputs and outputs are the caller's: problem and params as for tks_plan_create (params must be
- * TKS_FP64 with dtype F64), Y_out a device buffer of sum_n n_n S_n float64 where Y_n (n_n x S_n,
- * column-major, S_n from Sec. 3.2) starts at element sum_{m<n} n_m S_m.  The descriptor tables and
- * the intermediates Omega_j, M_j, Vcat_n live in a static device array of TKS_NOALLOC_SCRATCH_BYTES
- * that every GPU loading this library holds until the process exits; a problem needing more is
- * rejected with TKS_EINVAL and a message giving both sizes.  No cudaMalloc, cudaFree or other
- * allocating call is made.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) for that device, so make that first call before any stream capture.
- * Every call reuses the same array and leaves its contents behind; nothing in it needs to start
- * at zero (each element a call reads is written earlier by the same call).  Calls whose work
- * overlaps on a GPU (other streams, other host threads) race on the array: serialize them. */
+ * TKS_FP64 with dtype F64; omega_lowprec and lanes are checked as there, and omega_lowprec = 1
+ * draws the mixed modes' Omega), Y_out a device buffer of sum_n n_n S_n float64 where Y_n
+ * (n_n x S_n, column-major) starts at element sum_{m<n} n_m S_m, S_n being the sketch_cols that
+ * tks_problem_info reports for the same problem (Khatri-Rao: max_m ell_m; Kronecker: the product
+ * of the other modes' s_j).  The descriptor tables and the intermediates Omega_j, M_j, Vcat_n live
+ * in a static device array of TKS_NOALLOC_SCRATCH_BYTES that every GPU loading this library holds
+ * until the process exits; a problem needing more is rejected with TKS_EINVAL and a message giving
+ * both sizes.  No cudaMalloc, cudaFree or other allocating call is made.  The first call on a
+ * device (and the first call after that device's context was destroyed, e.g. by cudaDeviceReset)
+ * looks up the array's device address (cudaGetSymbolAddress) for that device, so make that first
+ * call before any stream capture.  The descriptor tables are copied to the array from host memory
+ * that lives only for the duration of the call, so while `stream` is being captured the call
+ * returns TKS_EUNSUPPORTED and enqueues nothing.  Every call reuses the same array and leaves its
+ * contents behind; nothing in it needs to start at zero (each element a call reads is written
+ * earlier by the same call).  Calls enqueued one after another on one stream are ordered; calls
+ * whose work overlaps on a GPU (other streams, other host threads) race on the array: serialize
+ * them. */
 #define TKS_NOALLOC_SCRATCH_BYTES (8u << 20)
 TKS_API tks_status tucker_sum_sketch_noalloc(const tks_problem* problem, const tks_params* params, double* Y_out,
                                              void* stream);

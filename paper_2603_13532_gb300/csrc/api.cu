@@ -46,9 +46,9 @@ Operand op_abs(const void* p, size_t off_bytes = 0) {
   return Operand{B_ABS, 0, (int64_t)(reinterpret_cast<uintptr_t>(p) + off_bytes)};
 }
 
-enum StepKind { S_OMEGA, S_GEMM, S_REDUCE, S_CORESKETCH, S_QR, S_EIG, S_TC, S_SIMT, S_CS32, S_SPLIT,
+enum StepKind { S_OMEGA, S_GEMM, S_REDUCE, S_CORESKETCH, S_QR, S_TSQR64, S_TC, S_SIMT, S_CS32, S_SPLIT,
                 S_TRANSPOSE, S_QR32, S_SVD32, S_TSQR, S_CS3, S_CHAIN3, S_QRSM, S_PROJ3, S_SK3, S_QRREG, S_TTM,
-                S_FOLD4, S_PROJ3F, S_SK3F, S_SK4 };
+                S_FOLD4, S_PROJ3F, S_SK3F, S_SK4, S_SVD64 };
 
 struct Step {
   StepKind kind;
@@ -90,7 +90,8 @@ struct ProbHost {
   int64_t out_core_off = 0, out_fac_off[MAXD] = {};
   // workspace byte offsets
   size_t M[MAXD] = {}, V[MAXD] = {}, W[MAXD] = {}, tau[MAXD] = {}, A[MAXD] = {};
-  size_t T = 0, gram = 0, part = 0, P[MAXD] = {}, ev[MAXD] = {}, theta = 0, Hp[2] = {};
+  size_t T = 0, P[MAXD] = {}, ev[MAXD] = {}, theta = 0, Hp[2] = {};
+  size_t R64 = 0, stk64[2] = {};   // float64 ST-HOSVD: triangular factor and TSQR stacks
   std::vector<size_t> chain;   // 2 ping-pong buffers per term
   // mixed-precision buffers (bytes): bf16 planes and float32 intermediates
   size_t om_plane[MAXD] = {}, UT[MAXD] = {}, M32[MAXD] = {}, Vp[MAXD][3] = {}, Qp[MAXD][3] = {};
@@ -106,7 +107,6 @@ struct ProbHost {
   size_t bZ0 = 0, bZ2 = 0, bB[MAXD] = {};
   std::vector<size_t> bterm;   // per term: Z01, W1, W0
   int64_t gcore_off = 0, gfac_off[MAXD] = {};
-  int gram_ksplit = 1;
   double flops_low = 0.0, flops_f64 = 0.0;
 };
 
@@ -1210,12 +1210,16 @@ static void build_backward3(tks_plan* plan) {
 
 }  // namespace
 
-// ST-HOSVD of H in float64 (TKS_FP64 and TKS_MIXED): Gram matrices, Jacobi eigensolver, mode
-// products; problems [lane_p0, lane_p1).
+// ST-HOSVD of H in float64 (TKS_FP64 and TKS_MIXED; Alg. 2 phase 2, modes 1..d in order): per mode,
+// TSQR of H_(n)^T (rows = the other modes, two-level index) in float64, one-sided Jacobi SVD of its
+// b x b triangular factor (right singular vectors = left singular vectors of H_(n)), rank rule, then
+// H <- H x_n P_n^T and U~_n = Q_n P_n as float64 GEMMs; problems [lane_p0, lane_p1).
 static void build_hosvd_f64(tks_plan* plan) {
   for (int n = 0; n < plan->dmax; ++n) {
-    GemmList gram, ttm, fac;
-    std::vector<EigJob> eig;
+    std::vector<std::vector<TsqrJob>> tsqr;
+    std::vector<SvdJob> svds;
+    GemmList ttm, fac;
+    double qflops = 0.0;
     for (int p = plan->lane_p0; p < plan->lane_p1; ++p) {
       auto& h = plan->probs[p];
       const int d = h.d;
@@ -1225,28 +1229,60 @@ static void build_hosvd_f64(tks_plan* plan) {
       for (int j = n + 1; j < d; ++j) Rr *= h.b[j];
       const int b = h.b[n], rmax = h.rmax[n];
       const Operand X = (n == 0) ? op(B_H, h.h_off * 8) : op(B_WS, h.Hp[(n - 1) & 1]);
-      // Gram B_n = H_(n) H_(n)^T: k = l + L rr
-      GemmJob g = gemm(b, b, (int)(L * Rr), X, L, 1, X, L, 1, op(B_WS, h.gram), 1, b);
-      g.K1 = (int)L;
-      g.a_k1 = L * b;
-      g.b_k1 = L * b;
-      g.ksplit = std::min<int>(h.gram_ksplit, std::max(1, (int)(L * Rr / 64)));
-      g.P = op(B_WS, h.part);
-      gram.add(g);
-      EigJob e;
-      std::memset(&e, 0, sizeof(e));
-      e.B = op(B_WS, h.gram);
-      e.P = op(B_WS, h.P[n]);
-      e.evals = op(B_WS, h.ev[n]);
-      e.theta = op(B_WS, h.theta);
-      e.rank = op(B_RANKS, (size_t)(p * TKS_MAX_ORDER + n) * 4);
-      e.b = b;
-      e.rmax = rmax;
-      e.target = h.target[n];
-      e.first_mode = (n == 0);
-      e.order = d;
-      e.tol = plan->params.trunc_tol;
-      eig.push_back(e);
+      // TSQR of H_(n)^T: element (l + L rr, c) at l + L c + L b rr; level 0 reads H, later levels
+      // the stacked b x b factors, the last level writes R64
+      {
+        int64_t rows = L * Rr;
+        qflops += 2.0 * (double)rows * b * b;
+        Operand src = X;
+        int64_t L0 = L, s0 = 1, s1 = L * b, sc = L;
+        const int brows_max = tsqr64_block_rows(plan->bmax);
+        for (int lvl = 0;; ++lvl) {
+          const int nblk = std::max(1, ceil_div(rows, brows_max));
+          const int brows = ceil_div(rows, nblk);
+          const bool final_level = (nblk == 1);
+          const Operand dst = final_level ? op(B_WS, h.R64) : op(B_WS, h.stk64[lvl & 1]);
+          const int64_t dst_ld = final_level ? b : (int64_t)nblk * b;
+          if ((int)tsqr.size() <= lvl) tsqr.resize(lvl + 1);
+          for (int i = 0; i < nblk; ++i) {
+            TsqrJob t;
+            std::memset(&t, 0, sizeof(t));
+            t.src = src;
+            t.src_type = T_F64;
+            t.row_begin = (int64_t)i * brows;
+            t.rows = (int)std::min<int64_t>(brows, rows - t.row_begin);
+            t.cols = b;
+            t.L0 = L0;
+            t.s0 = s0;
+            t.s1 = s1;
+            t.sc = sc;
+            t.dst = dst;
+            t.dst_row0 = (int64_t)i * b;
+            t.dst_ld = dst_ld;
+            tsqr[lvl].push_back(t);
+          }
+          if (final_level) break;
+          src = dst;
+          rows = (int64_t)nblk * b;
+          L0 = rows;
+          s0 = 1;
+          s1 = 0;
+          sc = dst_ld;
+        }
+      }
+      SvdJob sj;
+      std::memset(&sj, 0, sizeof(sj));
+      sj.R = op(B_WS, h.R64);
+      sj.P = op(B_WS, h.P[n]);
+      sj.sv = op(B_WS, h.ev[n]);
+      sj.theta = op(B_WS, h.theta);
+      sj.rank = op(B_RANKS, (size_t)(p * TKS_MAX_ORDER + n) * 4);
+      sj.b = b;
+      sj.rmax = rmax;
+      sj.first_mode = (n == 0);
+      sj.order = d;
+      sj.tol = plan->params.trunc_tol;
+      svds.push_back(sj);
       const Operand Y = (n == d - 1) ? op(B_OUT, h.out_core_off * 8) : op(B_WS, h.Hp[n & 1]);
       GemmJob t;
       if (L == 1) {
@@ -1262,16 +1298,18 @@ static void build_hosvd_f64(tks_plan* plan) {
                    op(B_OUT, h.out_fac_off[n] * 8), 1, h.n[n]));
     }
     char nm[32];
-    std::snprintf(nm, sizeof(nm), "a9:gram%d", n);
-    plan->push_gemm(plan->st_recompress, gram, nm);
-    std::snprintf(nm, sizeof(nm), "a9:eig%d", n);
-    plan->push(plan->st_recompress, S_EIG, eig, (int64_t)eig.size(), nm);
+    for (size_t lvl = 0; lvl < tsqr.size(); ++lvl) {
+      std::snprintf(nm, sizeof(nm), "a9:tsqr%d.%d", n, (int)lvl);
+      plan->push(plan->st_recompress, S_TSQR64, tsqr[lvl], (int64_t)tsqr[lvl].size(), nm, lvl == 0 ? qflops : 0.0,
+                 0.0);
+    }
+    std::snprintf(nm, sizeof(nm), "a9:svd%d", n);
+    plan->push(plan->st_recompress, S_SVD64, svds, (int64_t)svds.size(), nm);
     std::snprintf(nm, sizeof(nm), "a9:ttm%d", n);
     plan->push_gemm(plan->st_recompress, ttm, nm);
     std::snprintf(nm, sizeof(nm), "a9:factor%d", n);
     plan->push_gemm(plan->st_recompress, fac, nm);
   }
-
 }
 
 extern "C" {
@@ -1455,13 +1493,7 @@ tks_status tks_plan_create(tks_plan** out, const tks_problem* problems, int32_t 
     }
     int bm = 0;
     for (int m = 0; m < d; ++m) bm = std::max(bm, h.b[m]);
-    h.gram = alloc((size_t)bm * bm * 8);
     int64_t Hsz = prod(h.b, d);
-    // split-K for the ST-HOSVD Gram matrices: enough chunks to occupy the SMs across problems
-    int64_t kmax = Hsz / std::max(1, h.b[0]);
-    int ks = (int)std::max<int64_t>(1, std::min<int64_t>(kmax / 512, (2 * 152 + plan->nprob - 1) / plan->nprob));
-    h.gram_ksplit = ks;
-    h.part = alloc((size_t)ks * bm * bm * 8);
     h.theta = alloc(8);
     h.Hp[0] = alloc(Hsz * 8);
     h.Hp[1] = alloc(Hsz * 8);
@@ -1476,6 +1508,17 @@ tks_status tks_plan_create(tks_plan** out, const tks_problem* problems, int32_t 
         h.bterm[3 * k + 1] = alloc((size_t)r[0] * h.b[1] * r[2] * 8);
         h.bterm[3 * k + 2] = alloc((size_t)h.b[0] * r[1] * r[2] * 8);
       }
+    }
+    if (!f32la) {
+      // float64 TSQR stacks: at most ceil(rows / block) factors of b rows per level
+      int64_t stack_rows = 0;
+      for (int m = 0; m < d; ++m) {
+        const int64_t rows = Hsz / h.b[m];
+        stack_rows = std::max<int64_t>(stack_rows, (int64_t)ceil_div(rows, tsqr64_block_rows(plan->bmax)) * h.b[m]);
+      }
+      h.R64 = alloc((size_t)bm * bm * 8);
+      h.stk64[0] = alloc((size_t)stack_rows * bm * 8);
+      h.stk64[1] = alloc((size_t)stack_rows * bm * 8);
     }
     if (f32la) {
       int64_t stack_rows = 0;
@@ -1687,11 +1730,11 @@ tks_status tks_plan_create(tks_plan** out, const tks_problem* problems, int32_t 
     tks_plan_destroy(plan);
     return fail(TKS_ECUDA, "no CUDA device");
   }
-  if (plan->bmax > 0) {
-    cudaError_t e = prepare_eig_f64(plan->bmax);
+  if (plan->bmax > 0 && !f32la) {
+    cudaError_t e = prepare_la64(plan->bmax);
     if (e != cudaSuccess) {
       tks_plan_destroy(plan);
-      return fail(TKS_ECUDA, std::string("eigensolver shared memory: ") + cudaGetErrorString(e));
+      return fail(TKS_ECUDA, std::string("float64 TSQR/SVD shared memory: ") + cudaGetErrorString(e));
     }
   }
   if (f32la) {
@@ -1819,8 +1862,11 @@ tks_status run_steps(tks_plan* plan, const std::vector<Step>& steps, const Bases
       case S_QR:
         launch_qr_f64(static_cast<const QrJob*>(table), s.njobs, bases, plan->status, stream);
         break;
-      case S_EIG:
-        launch_eig_f64(static_cast<const EigJob*>(table), s.njobs, plan->bmax, bases, plan->status, stream);
+      case S_TSQR64:
+        launch_tsqr_f64(static_cast<const TsqrJob*>(table), s.njobs, plan->bmax, bases, stream);
+        break;
+      case S_SVD64:
+        launch_svd_f64(static_cast<const SvdJob*>(table), s.njobs, plan->bmax, bases, plan->status, stream);
         break;
       case S_TC:
         launch_tc_gemm(static_cast<const TcJob*>(table), s.njobs, (int)s.work, plan->arena_dev + plan->maps_off,
@@ -2107,18 +2153,41 @@ namespace {
 
 constexpr int kMaxDevices = 128;
 std::mutex g_noalloc_mutex;
+// per device: the context the address was looked up in, and the address itself (a destroyed
+// context, e.g. after cudaDeviceReset, reloads the module at another address)
+CUcontext g_noalloc_ctx[kMaxDevices] = {};
 void* g_noalloc_ptr[kMaxDevices] = {};
+
+typedef CUresult (*PFN_ctx_get_current)(CUcontext*);
+
+PFN_ctx_get_current ctx_get_current() {
+  static PFN_ctx_get_current fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_ctx_get_current>(p);
+  }
+  return fn;
+}
 
 tks_status noalloc_scratch(void** out) {
   int dev = -1;
   TKS_CUDA_CHECK(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices) return fail(TKS_EUNSUPPORTED, "device ordinal out of range");
+  TKS_CUDA_CHECK(cudaSetDevice(dev));   // initializes the device's primary context and makes it current
+  auto get_ctx = ctx_get_current();
+  if (!get_ctx) return fail(TKS_ECUDA, "cuCtxGetCurrent is not available from the driver");
+  CUcontext ctx = nullptr;
+  if (get_ctx(&ctx) != CUDA_SUCCESS || !ctx) return fail(TKS_ECUDA, "no current CUDA context");
   std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-  if (!g_noalloc_ptr[dev]) {
+  if (!g_noalloc_ptr[dev] || g_noalloc_ctx[dev] != ctx) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p) return fail(TKS_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
     g_noalloc_ptr[dev] = p;
+    g_noalloc_ctx[dev] = ctx;
   }
   *out = g_noalloc_ptr[dev];
   return TKS_OK;
@@ -2143,6 +2212,21 @@ extern "C" tks_status tucker_sum_sketch_noalloc(const tks_problem* problem, cons
   if (params->precision != TKS_FP64 || params->dtype != TKS_DT_F64)
     return fail(TKS_EINVAL, "tucker_sum_sketch_noalloc needs TKS_FP64 with float64 inputs");
   if (params->sketch != TKS_SKETCH_KRP && params->sketch != TKS_SKETCH_KRON) return fail(TKS_EINVAL, "bad sketch");
+  if (params->omega_lowprec != 0 && params->omega_lowprec != 1)
+    return fail(TKS_EINVAL, "omega_lowprec must be 0 or 1");
+  if (params->lanes < 0 || params->lanes > 8) return fail(TKS_EINVAL, "lanes must be 0..8");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  {
+    // the tables are copied from host memory that lives only during this call
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(TKS_ECUDA, std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(e));
+    }
+    if (cs != cudaStreamCaptureStatusNone)
+      return fail(TKS_EUNSUPPORTED, "tucker_sum_sketch_noalloc cannot be enqueued while its stream is being captured");
+  }
   ProbHost h;
   tks_status st = validate_and_size(*problem, *params, h, 0);
   if (st != TKS_OK) return st;
@@ -2177,6 +2261,7 @@ extern "C" tks_status tucker_sum_sketch_noalloc(const tks_problem* problem, cons
     oj.begin = om_blocks;
     oj.problem = 0;
     oj.mode = m;
+    oj.bf16 = params->omega_lowprec != 0;
     om_blocks += (oj.count + 3) / 4;
     omj.push_back(oj);
     gM.add(gemm(h.R[m], h.s[m], (int)h.n[m], op_abs(h.factors[m]), h.n[m], 1, op(B_WS, om[m]), h.n[m], 1,
@@ -2221,7 +2306,6 @@ extern "C" tks_status tucker_sum_sketch_noalloc(const tks_problem* problem, cons
   void* scratch = nullptr;
   st = noalloc_scratch(&scratch);
   if (st != TKS_OK) return st;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
   char* base = static_cast<char*>(scratch);
   TKS_CUDA_CHECK(cudaMemcpyAsync(base, t.bytes.data(), t.bytes.size(), cudaMemcpyHostToDevice, s));
   Bases b;
