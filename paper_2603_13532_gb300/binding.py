@@ -20,11 +20,11 @@ DTYPE = {"fp64": 0, "bf16": 1}
 STATUS = {0: "TKS_OK", 1: "TKS_EINVAL", 2: "TKS_ENOMEM", 3: "TKS_ECUDA", 4: "TKS_ETIMEOUT",
           5: "TKS_ENONFINITE", 6: "TKS_ENOCONV", 7: "TKS_EUNSUPPORTED"}
 
-STEP_KINDS = {0: "omega", 1: "gemm", 2: "reduce", 3: "core_sketch", 4: "qr", 5: "eig", 6: "tc", 7: "simt",
+STEP_KINDS = {0: "omega", 1: "gemm", 2: "reduce", 3: "core_sketch", 4: "qr", 5: "tsqr64", 6: "tc", 7: "simt",
               8: "core_sketch32", 9: "split", 10: "transpose", 11: "qr32", 12: "svd32", 13: "tsqr32",
               14: "core_sketch3", 15: "chain3", 16: "qr_smem32", 17: "project3",
               18: "sketch3", 19: "qr_reg32", 20: "ttm32", 21: "fold4", 22: "project4",
-              23: "sketch3f", 24: "sketch4"}
+              23: "sketch3f", 24: "sketch4", 25: "svd64"}
 
 
 class TksError(RuntimeError):

@@ -1,6 +1,5 @@
-// Float64 stage kernels: the plain FP64 GPU path of the method and the FP64 small dense
-// linear algebra (Householder QR of the sketches, Jacobi eigensolver of the ST-HOSVD
-// Gram matrices) that the mixed-precision path shares.
+// Float64 stage kernels: the plain FP64 GPU path of the method and the Householder QR of the
+// sketches that the TKS_MIXED path shares (the ST-HOSVD's TSQR and SVD are in la64.cu).
 //
 // GB300 runs float64 at about 1/64 of the float32 CUDA-core rate (about two FP64 FMAs per
 // SM per clock), so these kernels are bound by FP64 issue, not by memory: tiles are sized
@@ -360,171 +359,6 @@ __global__ void __launch_bounds__(256) qr_f64_kernel(const QrJob* __restrict__ j
   if (threadIdx.x == 0 && sh_bad) record_status(status, TKS_ENONFINITE);
 }
 
-// ----------------------------------------------------------------------------- Jacobi eigensolver
-// Cyclic Jacobi on the symmetric b x b Gram matrix with the round-robin parallel ordering
-// (b/2 disjoint rotations per round, b-1 rounds per sweep).  Rotation per Golub & Van Loan,
-// Alg. 8.4.1 (symmetric Schur decomposition of a 2x2 block).
-constexpr int kMaxSweeps = 40;
-
-size_t eig_smem_bytes_impl(int bmax) {
-  const int m = bmax + (bmax & 1);
-  return (size_t)2 * m * (m + 1) * sizeof(double) + (size_t)3 * m * sizeof(double) +
-         (size_t)2 * m * sizeof(int);
-}
-
-__global__ void __launch_bounds__(512) eig_f64_kernel(const EigJob* __restrict__ jobs, Bases bases,
-                                                      Status* status) {
-  extern __shared__ double smem[];
-  const EigJob& J = jobs[blockIdx.x];
-  const int b = J.b;
-  const int m = b + (b & 1);          // even size; index b is a dummy when b is odd
-  const int ld = m + 1;
-  double* A = smem;                   // m x ld
-  double* V = A + (size_t)m * ld;     // m x ld
-  double* cs = V + (size_t)m * ld;    // m/2
-  double* sn = cs + m;                // m/2
-  double* ev = sn + m;                // m
-  int* pp = reinterpret_cast<int*>(ev + m);
-  int* qq = pp + m;
-  __shared__ double red[32];
-  __shared__ int sh_rot, sh_rank;
-  const double* Bg = at<double>(bases, J.B);
-  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-    const int r = e % m, c = e / m;
-    A[r + c * ld] = (r < b && c < b) ? Bg[r + (int64_t)c * b] : 0.0;
-    V[r + c * ld] = (r == c) ? 1.0 : 0.0;
-  }
-  __syncthreads();
-  double tr = 0.0;
-  {
-    double part = 0.0;
-    for (int i = threadIdx.x; i < b; i += blockDim.x) part += A[i + i * ld];
-    tr = block_sum(part, red);
-  }
-  int sweep = 0;
-  for (; sweep < kMaxSweeps; ++sweep) {
-    if (threadIdx.x == 0) sh_rot = 0;
-    __syncthreads();
-    for (int round = 0; round < m - 1; ++round) {
-      // pairs of the circle method: (round, m-1) and ((round+k) mod (m-1), (round-k) mod (m-1))
-      for (int k = threadIdx.x; k < m / 2; k += blockDim.x) {
-        int p, q;
-        if (k == 0) { p = round; q = m - 1; }
-        else { p = (round + k) % (m - 1); q = (round - k + (m - 1)) % (m - 1); }
-        if (p > q) { const int t = p; p = q; q = t; }
-        pp[k] = p;
-        qq[k] = q;
-        double c = 1.0, s = 0.0;
-        if (q < b) {
-          const double apq = A[p + q * ld], app = A[p + p * ld], aqq = A[q + q * ld];
-          const double thr = fmax(1e-16 * sqrt(fabs(app * aqq)), 1e-22 * fabs(tr));
-          if (fabs(apq) > thr && apq != 0.0) {
-            const double tau = (aqq - app) / (2.0 * apq);
-            double t;
-            if (fabs(tau) > 1e150) t = 0.5 / tau;
-            else t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-            c = 1.0 / sqrt(1.0 + t * t);
-            s = t * c;
-            sh_rot = 1;
-          }
-        }
-        cs[k] = c;
-        sn[k] = s;
-      }
-      __syncthreads();
-      // rows p, q of A
-      for (int e = threadIdx.x; e < (m / 2) * m; e += blockDim.x) {
-        const int k = e / m, col = e - k * m;
-        const double c = cs[k], s = sn[k];
-        if (s == 0.0) continue;
-        const int p = pp[k], q = qq[k];
-        const double ap = A[p + col * ld], aq = A[q + col * ld];
-        A[p + col * ld] = c * ap - s * aq;
-        A[q + col * ld] = s * ap + c * aq;
-      }
-      __syncthreads();
-      // columns p, q of A and V
-      for (int e = threadIdx.x; e < (m / 2) * m; e += blockDim.x) {
-        const int k = e / m, row = e - k * m;
-        const double c = cs[k], s = sn[k];
-        if (s == 0.0) continue;
-        const int p = pp[k], q = qq[k];
-        const double ap = A[row + p * ld], aq = A[row + q * ld];
-        A[row + p * ld] = c * ap - s * aq;
-        A[row + q * ld] = s * ap + c * aq;
-        const double vp = V[row + p * ld], vq = V[row + q * ld];
-        V[row + p * ld] = c * vp - s * vq;
-        V[row + q * ld] = s * vp + c * vq;
-      }
-      __syncthreads();
-    }
-    if (!sh_rot) break;
-    __syncthreads();
-  }
-  // eigenvalues in decreasing order (ties by index): thread i places eigenvalue i at its rank, a
-  // NaN counting as -inf so that the ranks always form a permutation (a one-thread selection
-  // sort here cost b^2 / 2 dependent shared-memory reads); then choose the rank, emit P
-  for (int i = threadIdx.x; i < b; i += blockDim.x) ev[i] = A[i + i * ld];
-  __syncthreads();
-  for (int i = threadIdx.x; i < b; i += blockDim.x) {
-    const double ei = ev[i] == ev[i] ? ev[i] : -INFINITY;
-    int rk = 0;
-    for (int j = 0; j < b; ++j) {
-      const double ej = ev[j] == ev[j] ? ev[j] : -INFINITY;
-      rk += (ej > ei || (ej == ei && j < i)) ? 1 : 0;
-    }
-    pp[rk] = i;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    bool bad = !isfinite(tr);
-    double* evals = at<double>(bases, J.evals);
-    for (int i = 0; i < b; ++i) evals[i] = ev[pp[i]];
-    double* theta = at<double>(bases, J.theta);
-    if (J.first_mode) *theta = J.tol * J.tol * tr / J.order;
-    int r = J.rmax;
-    if (J.tol > 0.0) {
-      const double th = *theta;
-      // r = min{r >= 1 : sum_{j > r} lambda_j <= theta}, lambda clipped at 0 (Alg. 2 rank rule)
-      double tail = 0.0;
-      r = b;
-      for (int i = b - 1; i >= 1; --i) {
-        tail += fmax(ev[pp[i]], 0.0);
-        if (tail <= th) r = i; else break;
-      }
-      if (r > J.rmax) r = J.rmax;
-    }
-    sh_rank = r;
-    *at<int32_t>(bases, J.rank) = r;
-    if (bad) record_status(status, TKS_ENONFINITE);
-    if (sweep >= kMaxSweeps) record_status(status, TKS_ENOCONV);
-  }
-  __syncthreads();
-  const int r = sh_rank;
-  double* P = at<double>(bases, J.P);
-  // P[:, t] = V[:, pp[t]] for t < r, zero beyond; sign: largest-magnitude entry positive
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int t = warp; t < J.rmax; t += nw) {
-    if (t >= r) {
-      for (int i = lane; i < b; i += 32) P[i + (int64_t)t * b] = 0.0;
-      continue;
-    }
-    const int src = pp[t];
-    double best = 0.0;
-    for (int i = lane; i < b; i += 32) {
-      const double v = V[i + src * ld];
-      if (fabs(v) > fabs(best)) best = v;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const double other = __shfl_xor_sync(0xffffffffu, best, o);
-      if (fabs(other) > fabs(best) || (fabs(other) == fabs(best) && other > best)) best = other;
-    }
-    const double sgn = (best < 0.0) ? -1.0 : 1.0;
-    for (int i = lane; i < b; i += 32) P[i + (int64_t)t * b] = sgn * V[i + src * ld];
-  }
-}
-
 }  // namespace
 
 // ----------------------------------------------------------------------------- launchers
@@ -557,18 +391,6 @@ void launch_core_sketch_f64(const CoreSketchJob* jobs, int njobs, int64_t total,
 void launch_qr_f64(const QrJob* jobs, int njobs, const Bases& bases, Status* status,
                    cudaStream_t stream) {
   qr_f64_kernel<<<njobs, 256, 0, stream>>>(jobs, bases, status);
-}
-
-size_t eig_smem_bytes(int bmax) { return eig_smem_bytes_impl(bmax); }
-
-cudaError_t prepare_eig_f64(int bmax) {
-  return cudaFuncSetAttribute(eig_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)eig_smem_bytes_impl(bmax));
-}
-
-void launch_eig_f64(const EigJob* jobs, int njobs, int bmax, const Bases& bases, Status* status,
-                    cudaStream_t stream) {
-  eig_f64_kernel<<<njobs, 512, eig_smem_bytes_impl(bmax), stream>>>(jobs, bases, status);
 }
 
 }  // namespace tks

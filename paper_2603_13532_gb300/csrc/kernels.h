@@ -19,10 +19,12 @@ void launch_core_sketch_f64(const CoreSketchJob* jobs, int njobs, int64_t total,
 // Householder QR, one CTA per job.
 void launch_qr_f64(const QrJob* jobs, int njobs, const Bases& bases, Status* status,
                    cudaStream_t stream);
-// Jacobi eigensolver + rank selection, one CTA per job; smem_bytes from eig_smem_bytes().
-size_t eig_smem_bytes(int bmax);
-cudaError_t prepare_eig_f64(int bmax);   // raises the dynamic shared memory limit
-void launch_eig_f64(const EigJob* jobs, int njobs, int bmax, const Bases& bases, Status* status,
+// Float64 ST-HOSVD: one TSQR level (each job factors one block of a float64 source into a float64
+// triangular factor) and the one-sided Jacobi SVD of the b x b factors, one CTA per job.
+int tsqr64_block_rows(int max_cols);     // rows of a block: 256 up to 64 columns, else 128
+cudaError_t prepare_la64(int bmax);      // raises the dynamic shared memory limits
+void launch_tsqr_f64(const TsqrJob* jobs, int njobs, int max_cols, const Bases& bases, cudaStream_t stream);
+void launch_svd_f64(const SvdJob* jobs, int njobs, int bmax, const Bases& bases, Status* status,
                     cudaStream_t stream);
 
 // Tensor-core (tcgen05) grouped GEMM over bf16 planes; maps = device array of CUtensorMap.

@@ -264,15 +264,6 @@ struct QrJob {
   int32_t n, S, b, pad;
 };
 
-// Symmetric eigendecomposition of a Gram matrix B (b x b) by cyclic Jacobi, then
-// rank selection (Alg. 2 rank rule) and P = leading eigenvectors (b x rmax, zero-padded).
-struct EigJob {
-  Operand B, P, evals, theta, rank;
-  int32_t b, rmax, target, first_mode;
-  int32_t order, pad;
-  double tol;                   // 0: rank = rmax
-};
-
 // Tensor-core GEMM (tcgen05, bf16 inputs, f32 accumulation in TMEM):
 //   D (M x N) = alpha * sum_{p < npairs} A_{pa[p]} B_{pb[p]}^T
 // A_i (M x K) and B_j (N x K) are bfloat16 planes in K-major layout read by TMA through the
@@ -310,9 +301,10 @@ struct QrF32Job {
 };
 
 // One block of a TSQR level: rows [row_begin, row_begin + rows) x cols of a (typed, two-level
-// row index) source are factored by Householder in shared memory; the b x b triangular factor
-// (rows below min(rows, cols) zero) is written at rows [dst_row0, dst_row0 + cols) of dst
-// (float32, column-major, leading dimension dst_ld).  Stacking the blocks' factors and
+// row index) source are factored by Householder; the b x b triangular factor (rows below
+// min(rows, cols) zero) is written at rows [dst_row0, dst_row0 + cols) of dst (column-major,
+// leading dimension dst_ld; float32 for the float32 kernel, float64 with a float64 source for
+// the float64 kernel).  Stacking the blocks' factors and
 // factoring again gives the triangular factor of the whole matrix.
 struct TsqrJob {
   Operand src, dst;
@@ -321,10 +313,11 @@ struct TsqrJob {
   int64_t dst_row0, dst_ld;
 };
 
-// One-sided (Hestenes) Jacobi SVD in float32 of the b x b factor R of H_(n)^T = Q~ R: its right
-// singular vectors are the left singular vectors of H_(n).  Selects the rank (min(rmax, b), or
-// the tolerance rule of Alg. 2 with theta = tol^2 ||H||^2 / d fixed at the first mode) and
-// writes P = leading right singular vectors (b x rmax, float32, zero-padded).
+// One-sided (Hestenes) Jacobi SVD of the b x b factor R of H_(n)^T = Q~ R: its right singular
+// vectors are the left singular vectors of H_(n).  Selects the rank (min(rmax, b), or the
+// tolerance rule of Alg. 2 with theta = tol^2 ||H||^2 / d fixed at the first mode) and writes
+// P = leading right singular vectors (b x rmax, zero-padded) and the b singular values sv, all
+// float32 for the float32 kernel and float64 for the float64 kernel (theta is float64 in both).
 struct SvdJob {
   Operand R, P, sv, theta, rank;
   int32_t b, rmax, first_mode, order;
