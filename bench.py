@@ -7,13 +7,21 @@ target rank 48, oversampling 10; seeded synthetic inputs already resident in HBM
 value is recompressions per second over all ranks.  Under torchrun every rank runs its own
 batch on its own GPU (weak scaling, no data-path collective).
 
+The default precision is TKS_MIXED: the contractions on tcgen05 tensor cores (bf16 operands,
+float32 accumulation), the QR of each sketch and the ST-HOSVD in float64.
+
 Also reported on the same JSON line:
   e2e           the same metric with the inputs copied from pinned host memory and the
                 result read back inside every timed step
   roofline      the dominant launch: algorithmic flops (or bytes) per launch / its average
                 CUDA-event duration inside the timed region, against the measured peak
+  projection_tensor_roofline  the fused projection launch against the bf16 tensor peak
   cpu_baseline  the FP64 oracle timed on this host's cores on a bounded sample
   fp64_path     (mixed precision only) the plain FP64 GPU path on the same batch
+  vs_oracle     sampled entries of the first recompressions against the FP64 oracle
+  mixed_f32la   (precision mixed) the same batch with float32 QR and ST-HOSVD
+  workloads     short runs of the other workloads (256-problem batch, order-4 Khatri-Rao and
+                Kronecker): rate, FP64-path rate, speedup, error against the oracle
   subrank       the effective subrank heuristic (Alg. 5, float64) on the same batch: problems/s,
                 its float64 roofline, and the oracle's rate on a sample
   clocks        nvidia-smi SM clocks and throttle reasons sampled during the timed region
@@ -46,7 +54,9 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp64", "mixed", "mixed_f32la"], default="mixed_f32la")
+    ap.add_argument("--precision", choices=["fp64", "mixed", "mixed_f32la"], default="mixed",
+                    help="mixed: tensor-core contractions with float64 QR and ST-HOSVD (TKS_MIXED); mixed_f32la: "
+                         "the same contractions with float32 QR and ST-HOSVD")
     ap.add_argument("--fp64-steps", type=int, default=3, help="timed steps of the FP64 comparison")
     ap.add_argument("--problems", type=int, default=152, help="independent sums per step and GPU")
     ap.add_argument("--workload", default="decay512",
@@ -61,6 +71,13 @@ def parse_args():
                     help="groups of problems whose recompressions run on concurrent streams (tks_params.lanes); "
                          "default 2 for decay512 and batched, 1 for order4 (measured: +4% and -20%)")
     ap.add_argument("--no-subrank", action="store_true", help="skip the effective subrank (Alg. 5) leg")
+    ap.add_argument("--no-f32la", action="store_true", help="skip the float32-linear-algebra comparison leg")
+    ap.add_argument("--oracle-problems", type=int, default=2,
+                    help="problems whose recompression is checked against the FP64 oracle (sampled entries)")
+    ap.add_argument("--extra-workloads", default="batched,order4-krp,order4-kron",
+                    help="comma list of other workloads timed briefly (mixed vs FP64 path, error vs oracle); "
+                         "'' for none")
+    ap.add_argument("--extra-steps", type=int, default=5, help="timed steps of each extra workload (mixed)")
     ap.add_argument("--subrank-eps", type=float, default=1e-6, help="tolerance of the Alg. 5 leg")
     ap.add_argument("--subrank-steps", type=int, default=3, help="timed calls of the Alg. 5 leg")
     return ap.parse_args()
@@ -303,8 +320,107 @@ def time_steps(fn, steps, stream):
     return start.elapsed_time(end) / 1e3
 
 
+def graph_step(plan, out, ranks, stream, use_graph=True):
+    """The plan's recompression into (out, ranks) as a callable: a CUDA-graph replay of the whole
+    launch sequence (or an eager call).  Runs it once, synchronized, before returning."""
+    import torch
+    step = lambda: plan.recompress_raw(out, ranks)
+    step()
+    plan.sync()
+    if not use_graph:
+        return step, None
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        step()
+    stream.wait_stream(side)
+    with torch.cuda.graph(graph):
+        step()
+    graph.replay()
+    torch.cuda.synchronize()
+    return graph.replay, graph
+
+
+def _rms(x):
+    import numpy as np
+    return float(np.sqrt(np.mean(np.asarray(x) ** 2)))
+
+
+def oracle_errors(results, problems, kind, seed, rounding, count, nsamp=256):
+    """The first `count` recompressions of a batch against the FP64 oracle on the same Gaussian draws,
+    on nsamp sampled entries per problem: rel_err = rms(x_gpu - x_oracle) / rms(x_oracle) and
+    trunc_diff = |rms(x_gpu - x) - rms(x_oracle - x)| / rms(x), x the sum evaluated term by term."""
+    import numpy as np
+    from oracle import sketch_sum as ss
+    worst_rel = worst_tr = 0.0
+    ranks_ok = True
+    count = min(count, len(problems))
+    for i in range(count):
+        p = problems[i]
+        ref = ss.recompress(p.terms(), kind, p.target, p.oversampling, seed=seed, problem=i, rounding=rounding,
+                            alpha=p.alpha)
+        g = np.random.default_rng(1000 + i)
+        idx = np.stack([g.integers(0, n, size=nsamp) for n in p.dims], axis=1)
+        eg = sampled_entries(results[i]["core"], results[i]["factors"], idx)
+        eo = sampled_entries(ref["core"], ref["factors"], idx)
+        alpha = p.alpha if p.alpha is not None else [1.0] * p.num_terms
+        ex = sum(a * sampled_entries(G, Us, idx) for a, (G, Us) in zip(alpha, p.terms()))
+        worst_rel = max(worst_rel, _rms(eg - eo) / _rms(eo))
+        worst_tr = max(worst_tr, abs(_rms(eg - ex) - _rms(eo - ex)) / _rms(ex))
+        ranks_ok = ranks_ok and list(results[i]["ranks"]) == list(ref["ranks"])
+    return {"rel_err": worst_rel, "trunc_err_diff": worst_tr, "ranks_match": ranks_ok, "problems": count,
+            "samples_per_problem": nsamp,
+            "note": "max over the first problems of the batch: rms difference of sampled entries of the "
+                    "recompressed tensor from the FP64 oracle's (same Gaussian draws), relative to the oracle "
+                    "entries' rms; and the difference of the two truncation errors relative to rms(X)"}
+
+
+EXTRA_PROBLEMS = {"batched": 256, "order4-krp": 38, "order4-kron": 38}
+
+
+def extra_workload_leg(args, workload, device, stream, rank, world):
+    """A short measurement of another workload: the mixed path (graph replays), the plain FP64 path
+    on the same inputs and Gaussian draws, and the error against the FP64 oracle."""
+    import torch
+    from paper_2603_13532_gb300 import binding
+    P = EXTRA_PROBLEMS[workload]
+    kind = workload_kind(workload)
+    lanes = 1 if workload.startswith("order4") else 2
+    problems = make_problems(P, args.seed, rank, True, workload)
+    plan = binding.Plan(problems, kind=kind, precision=args.precision, seed=args.seed, device=device, lanes=lanes)
+    out = torch.zeros(plan.info.output_elems, dtype=torch.float64, device=device)
+    ranks_t = torch.zeros(P * binding.MAX_ORDER, dtype=torch.int32, device=device)
+    timed, graph = graph_step(plan, out, ranks_t, stream)
+    el = max_over_ranks(time_steps(timed, args.extra_steps, stream), device)
+    plan.sync()
+    value = weak_scaling_rate(P, world, args.extra_steps, el)
+    res = plan.unpack(out, ranks_t)
+    leg = {"workload": workload_label(P, workload), "precision": args.precision, "value": value, "unit": UNIT,
+           "ms_per_step": 1e3 * el / args.extra_steps, "steps": args.extra_steps, "lanes": lanes,
+           "tflops": (plan.info.flops_lowprec + plan.info.flops_fp64) * world * args.extra_steps / el / 1e12}
+    del graph, plan
+    plan64 = binding.Plan(problems, kind=kind, precision="fp64", seed=args.seed, device=device, omega_lowprec=True)
+    out64 = torch.zeros(plan64.info.output_elems, dtype=torch.float64, device=device)
+    r64 = torch.zeros_like(ranks_t)
+    step64 = lambda: plan64.recompress_raw(out64, r64)
+    step64()
+    plan64.sync()
+    steps64 = 1 if workload.startswith("order4") else 2
+    el64 = max_over_ranks(time_steps(step64, steps64, stream), device)
+    plan64.sync()
+    v64 = weak_scaling_rate(P, world, steps64, el64)
+    leg["fp64_path"] = {"value": v64, "unit": UNIT, "ms_per_step": 1e3 * el64 / steps64, "steps": steps64}
+    leg["speedup"] = value / v64
+    del plan64
+    if rank == 0:
+        leg["vs_oracle"] = oracle_errors(res, problems, kind, args.seed, "bf16",
+                                         1 if workload.startswith("order4") else 2)
+    return leg
+
+
 FP32_PEAK_TFLOPS = 152 * 256 * 2.070e9 / 1e12   # 128 FP32 FMA per SM per clock
-FP64_KINDS = {"gemm", "reduce", "qr", "core_sketch", "eig"}
+FP64_KINDS = {"gemm", "reduce", "qr", "core_sketch", "tsqr64", "svd64"}
 FP32_KINDS = {"simt", "core_sketch32", "qr32", "svd32", "tsqr32", "core_sketch3", "chain3", "qr_smem32",
               "project3", "sketch3", "qr_reg32", "ttm32", "fold4", "project4", "sketch3f", "sketch4"}
 
@@ -387,6 +503,22 @@ def roofline_from_profile(prof, calls, peaks, workload=None, problems=0, tensor_
     return roof
 
 
+def projection_tensor_roofline(prof, calls, peaks):
+    """The fused projection launches (a7+a8) against the measured bf16 tensor peak (burst): their
+    algorithmic flops per launch over their average CUDA-event duration."""
+    rows = [s for s in prof if s["kind"] in ("project3", "project4") and s["flops"] > 0]
+    if not rows:
+        return None
+    out = []
+    for s in rows:
+        avg = s["ms"] / 1e3 / max(1, calls)
+        ach = s["flops"] / avg / 1e12
+        out.append({"kernel": s["name"], "achieved": ach, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                    "frac": ach / peaks["bf16_tflops"], "avg_launch_ms": avg * 1e3,
+                    "algorithmic_flops_per_launch": s["flops"], "peak_source": "measured bf16 burst"})
+    return out
+
+
 def main():
     args = parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -436,21 +568,8 @@ def main():
     eager_elapsed = time_steps(step, args.steps, stream)
     prof = plan.profile_end()
     plan.sync()
-    timed = step
-    graph = None
-    if not args.no_graph:
-        # the whole recompression as one CUDA graph (the launch sequence is fixed per plan)
-        graph = torch.cuda.CUDAGraph()
-        side = torch.cuda.Stream()
-        side.wait_stream(stream)
-        with torch.cuda.stream(side):
-            step()
-        stream.wait_stream(side)
-        with torch.cuda.graph(graph):
-            step()
-        graph.replay()
-        torch.cuda.synchronize()
-        timed = graph.replay
+    # the whole recompression as one CUDA graph (the launch sequence is fixed per plan)
+    timed, graph = graph_step(plan, out, ranks_t, stream, use_graph=not args.no_graph)
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
@@ -598,6 +717,28 @@ def main():
                                        "far from exact and the kept subspace is not unique"}
         del plan64
 
+    # the same contractions with float32 QR and ST-HOSVD (TKS_MIXED_F32LA) on the same batch
+    f32la = None
+    if args.precision == "mixed" and not args.no_f32la:
+        plan32 = binding.Plan(problems, kind=kind, precision="mixed_f32la", seed=args.seed, device=device,
+                              lanes=args.lanes)
+        out32 = torch.zeros(plan32.info.output_elems, dtype=torch.float64, device=device)
+        r32 = torch.zeros_like(ranks_t)
+        timed32, graph32 = graph_step(plan32, out32, r32, stream, use_graph=not args.no_graph)
+        el32 = max_over_ranks(time_steps(timed32, args.steps, stream), device)
+        plan32.sync()
+        v32 = weak_scaling_rate(P, world, args.steps, el32)
+        f32la = {"value": v32, "unit": UNIT, "ms_per_step": 1e3 * el32 / args.steps, "steps": args.steps,
+                 "precision": "mixed_f32la",
+                 "note": "the same tensor-core contractions with the QR of Y_n and the ST-HOSVD in float32 "
+                         "(Householder QR, TSQR and one-sided Jacobi SVD; no Gram matrices)"}
+        if fp64_path is not None:
+            f32la["speedup_vs_fp64_path"] = v32 / fp64_path["value"]
+        if rank == 0 and args.oracle_problems > 0:
+            f32la["vs_oracle"] = oracle_errors(plan32.unpack(out32, r32), problems, kind, args.seed, "bf16",
+                                               args.oracle_problems)
+        del graph32, plan32
+
     # the effective subrank heuristic (Alg. 5) on the same batch and device inputs, float64
     subrank = None
     if not args.no_subrank:
@@ -639,8 +780,18 @@ def main():
                                                  f"the R x R Gram matrices, LAPACK on all host cores)"}
         del sp
 
+    extra = {}
+    for wk in [w for w in args.extra_workloads.split(",") if w]:
+        if wk == args.workload or args.precision == "fp64":
+            continue
+        extra[wk] = extra_workload_leg(args, wk, device, stream, rank, world)
+
     line = None
     if rank == 0:
+        vs_oracle = None
+        if args.oracle_problems > 0:
+            vs_oracle = oracle_errors(plan.unpack(out, ranks_t), problems, kind, args.seed, "bf16" if bf16 else None,
+                                      args.oracle_problems)
         in_bytes = plan.flat_inputs.numel() * plan.flat_inputs.element_size()
         cpu = None
         if not args.no_cpu:
@@ -661,7 +812,10 @@ def main():
                            "l2": f"inputs {in_bytes / 1e6:.0f} MB per GPU > L2 129 MB, no flush",
                            "parallelism": f"replicas x{world}",
                            "lanes": args.lanes if args.precision != "fp64" else 1},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fp64_path": fp64_path, "subrank": subrank,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fp64_path": fp64_path, "vs_oracle": vs_oracle,
+                "mixed_f32la": f32la, "workloads": extra or None,
+                "projection_tensor_roofline": projection_tensor_roofline(prof, args.steps, peaks),
+                "subrank": subrank,
                 "gpu_launches": int(plan.info.launches_recompress) * args.steps,
                 "timing": ("CUDA-graph replays of the whole recompression" if graph is not None
                            else "eager launches") + "; stage times from an eager pass with events (one "

@@ -170,6 +170,7 @@ struct tks_plan {
   cudaEvent_t lane_fork = nullptr;
   int64_t grad_core_elems = 0, grad_factor_elems = 0;
   bool backward_ok = false;
+  std::string build_error;   // set by a table builder that cannot plan a problem
   double flops_low = 0.0, flops_f64 = 0.0;
 
   size_t add_table(const void* p, size_t bytes) {
@@ -998,6 +999,10 @@ static void build_hosvd_f32(tks_plan* plan) {
         for (int lvl = 0;; ++lvl) {
           const int nblk = std::max(1, ceil_div(rows, tsqr_block_rows(plan->bmax)));
           const int brows = ceil_div(rows, nblk);
+          if (nblk > 1 && (int64_t)nblk * b >= rows) {   // blocks of at least 2b rows always shrink
+            plan->build_error = "TSQR levels do not shrink";
+            return;
+          }
           const bool final_level = (nblk == 1);
           const Operand dst = final_level ? op(B_WS, h.R32) : op(B_WS, h.stk[lvl & 1]);
           const int64_t dst_ld = final_level ? b : (int64_t)nblk * b;
@@ -1240,6 +1245,10 @@ static void build_hosvd_f64(tks_plan* plan) {
         for (int lvl = 0;; ++lvl) {
           const int nblk = std::max(1, ceil_div(rows, brows_max));
           const int brows = ceil_div(rows, nblk);
+          if (nblk > 1 && (int64_t)nblk * b >= rows) {   // blocks of at least 2b rows always shrink
+            plan->build_error = "TSQR levels do not shrink";
+            return;
+          }
           const bool final_level = (nblk == 1);
           const Operand dst = final_level ? op(B_WS, h.R64) : op(B_WS, h.stk64[lvl & 1]);
           const int64_t dst_ld = final_level ? b : (int64_t)nblk * b;
@@ -1685,6 +1694,12 @@ tks_status tks_plan_create(tks_plan** out, const tks_problem* problems, int32_t 
   if (f32la) build_hosvd_f32(plan);
   else build_hosvd_f64(plan);
 
+  if (!plan->build_error.empty()) {
+    const std::string msg = plan->build_error;
+    tks_plan_destroy(plan);
+    return fail(TKS_EUNSUPPORTED, msg);
+  }
+
   if (mixed) {
     const int lanes = std::min<int>(prm.lanes, num_problems);
     if (lanes > 1) {
@@ -1702,6 +1717,11 @@ tks_status tks_plan_create(tks_plan** out, const tks_problem* problems, int32_t 
         if (f32la) build_hosvd_f32(plan);
         else build_hosvd_f64(plan);
         plan->lane_steps.push_back(std::move(plan->st_recompress));
+      }
+      if (!plan->build_error.empty()) {
+        const std::string msg = plan->build_error;
+        tks_plan_destroy(plan);
+        return fail(TKS_EUNSUPPORTED, msg);
       }
       plan->st_omega = std::move(om);
       plan->st_sketch = std::move(sk);

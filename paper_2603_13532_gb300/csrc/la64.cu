@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(kT64Threads, 1) tsqr_f64_kernel(const TsqrJob*
   }
   __syncthreads();
   const bool row_major = J.sc == 1;
-  const int mb = m * b;   // <= 256 x 64 or 128 x 96, below 2^15
+  const int mb = m * b;   // <= 256 x 64 or 192 x 96, below 2^15
   const SmallDiv dq(row_major ? b : m);
   for (int e0 = 0; e0 < mb; e0 += kT64LoadBatch * kT64Threads) {
     double v[kT64LoadBatch];
@@ -424,7 +424,8 @@ size_t tsqr64_smem(int rows, int cols) { return (size_t)(rows + 1) * cols * size
 
 }  // namespace
 
-int tsqr64_block_rows(int max_cols) { return max_cols <= 4 * kT64Warps ? 256 : 128; }
+// At least twice the columns, so that every TSQR level shrinks the stack of factors.
+int tsqr64_block_rows(int max_cols) { return max_cols <= 4 * kT64Warps ? 256 : 192; }
 
 cudaError_t prepare_la64(int bmax) {
   cudaError_t e = cudaFuncSetAttribute(svd_jacobi_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -433,7 +434,7 @@ cudaError_t prepare_la64(int bmax) {
   const void* kernels[] = {reinterpret_cast<const void*>(tsqr_f64_kernel<8, 2>),
                            reinterpret_cast<const void*>(tsqr_f64_kernel<8, 3>),
                            reinterpret_cast<const void*>(tsqr_f64_kernel<8, 4>),
-                           reinterpret_cast<const void*>(tsqr_f64_kernel<4, 6>)};
+                           reinterpret_cast<const void*>(tsqr_f64_kernel<6, 6>)};
   for (const void* k : kernels) {
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsqr64_smem(256, 64));
     if (e != cudaSuccess) return e;
@@ -443,7 +444,7 @@ cudaError_t prepare_la64(int bmax) {
 
 void launch_tsqr_f64(const TsqrJob* jobs, int njobs, int max_cols, const Bases& bases, cudaStream_t stream) {
   // columns per warp: the smallest instantiation that covers max_cols; 256-row blocks up to 64
-  // columns, 128-row blocks beyond (the register tile stays at 32 or 24 doubles per thread)
+  // columns, 192-row blocks beyond (the register tile stays at 32 or 36 doubles per thread)
   if (max_cols <= 2 * kT64Warps) {
     tsqr_f64_kernel<8, 2><<<njobs, kT64Threads, tsqr64_smem(256, 2 * kT64Warps), stream>>>(jobs, bases);
   } else if (max_cols <= 3 * kT64Warps) {
@@ -451,7 +452,7 @@ void launch_tsqr_f64(const TsqrJob* jobs, int njobs, int max_cols, const Bases& 
   } else if (max_cols <= 4 * kT64Warps) {
     tsqr_f64_kernel<8, 4><<<njobs, kT64Threads, tsqr64_smem(256, 4 * kT64Warps), stream>>>(jobs, bases);
   } else {
-    tsqr_f64_kernel<4, 6><<<njobs, kT64Threads, tsqr64_smem(128, 6 * kT64Warps), stream>>>(jobs, bases);
+    tsqr_f64_kernel<6, 6><<<njobs, kT64Threads, tsqr64_smem(192, 6 * kT64Warps), stream>>>(jobs, bases);
   }
 }
 
