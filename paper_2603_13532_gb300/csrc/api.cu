@@ -48,7 +48,7 @@ Operand op_abs(const void* p, size_t off_bytes = 0) {
 
 enum StepKind { S_OMEGA, S_GEMM, S_REDUCE, S_CORESKETCH, S_QR, S_TSQR64, S_TC, S_SIMT, S_CS32, S_SPLIT,
                 S_TRANSPOSE, S_QR32, S_SVD32, S_TSQR, S_CS3, S_CHAIN3, S_QRSM, S_PROJ3, S_SK3, S_QRREG, S_TTM,
-                S_FOLD4, S_PROJ3F, S_SK3F, S_SK4, S_SVD64 };
+                S_FOLD4, S_PROJ3F, S_SK3F, S_SK4, S_SVD64, S_TTM64 };
 
 struct Step {
   StepKind kind;
@@ -1223,8 +1223,9 @@ static void build_hosvd_f64(tks_plan* plan) {
   for (int n = 0; n < plan->dmax; ++n) {
     std::vector<std::vector<TsqrJob>> tsqr;
     std::vector<SvdJob> svds;
-    GemmList ttm, fac;
-    double qflops = 0.0;
+    std::vector<TtmJob> ttm, fac;
+    int ttm_tiles = 0, fac_tiles = 0;
+    double qflops = 0.0, ttm_flops = 0.0, fac_flops = 0.0;
     for (int p = plan->lane_p0; p < plan->lane_p1; ++p) {
       auto& h = plan->probs[p];
       const int d = h.d;
@@ -1234,18 +1235,24 @@ static void build_hosvd_f64(tks_plan* plan) {
       for (int j = n + 1; j < d; ++j) Rr *= h.b[j];
       const int b = h.b[n], rmax = h.rmax[n];
       const Operand X = (n == 0) ? op(B_H, h.h_off * 8) : op(B_WS, h.Hp[(n - 1) & 1]);
-      // TSQR of H_(n)^T: element (l + L rr, c) at l + L c + L b rr; level 0 reads H, later levels
-      // the stacked b x b factors, the last level writes R64
+      // TSQR of H_(n)^T: element (l + L rr, c) at l + L c + L b rr.  Level 0 factors blocks of dense
+      // rows; every later level factors groups of the previous level's b x b triangular factors,
+      // each group read with its factors' rows interleaved (row f + k r of a group of k is row r of
+      // factor f), so that column j of the group is zero below row k (j + 1) and the kernel skips
+      // those rows.  The last level writes R64.
       {
-        int64_t rows = L * Rr;
-        qflops += 2.0 * (double)rows * b * b;
-        Operand src = X;
-        int64_t L0 = L, s0 = 1, s1 = L * b, sc = L;
+        const int64_t rows0 = L * Rr;
+        qflops += 2.0 * (double)rows0 * b * b;
         const int brows_max = tsqr64_block_rows(plan->bmax);
+        const int nblk0 = std::max(1, ceil_div(rows0, brows_max));
+        const int brows0 = ceil_div(rows0, nblk0);
+        int nfac = nblk0;               // factors written by the level just planned
+        int64_t ld_prev = 0;
+        Operand prev;
         for (int lvl = 0;; ++lvl) {
-          const int nblk = std::max(1, ceil_div(rows, brows_max));
-          const int brows = ceil_div(rows, nblk);
-          if (nblk > 1 && (int64_t)nblk * b >= rows) {   // blocks of at least 2b rows always shrink
+          const int kf_max = std::max(2, brows_max / b);
+          const int nblk = lvl == 0 ? nblk0 : std::max(1, ceil_div(nfac, kf_max));
+          if (lvl > 0 && nblk > 1 && nblk >= nfac) {   // groups of at least two factors always shrink
             plan->build_error = "TSQR levels do not shrink";
             return;
           }
@@ -1256,27 +1263,38 @@ static void build_hosvd_f64(tks_plan* plan) {
           for (int i = 0; i < nblk; ++i) {
             TsqrJob t;
             std::memset(&t, 0, sizeof(t));
-            t.src = src;
             t.src_type = T_F64;
-            t.row_begin = (int64_t)i * brows;
-            t.rows = (int)std::min<int64_t>(brows, rows - t.row_begin);
             t.cols = b;
-            t.L0 = L0;
-            t.s0 = s0;
-            t.s1 = s1;
-            t.sc = sc;
             t.dst = dst;
             t.dst_row0 = (int64_t)i * b;
             t.dst_ld = dst_ld;
+            if (lvl == 0) {
+              t.src = X;
+              t.row_begin = (int64_t)i * brows0;
+              t.rows = (int)std::min<int64_t>(brows0, rows0 - t.row_begin);
+              t.L0 = L;
+              t.s0 = 1;
+              t.s1 = L * b;
+              t.sc = L;
+            } else {
+              // factors [f0, f1) of the previous level, spread evenly over the groups
+              const int f0 = (int)((int64_t)i * nfac / nblk), f1 = (int)((int64_t)(i + 1) * nfac / nblk);
+              t.src = prev;
+              t.src.off += (int64_t)f0 * b * 8;
+              t.row_begin = 0;
+              t.rows = (f1 - f0) * b;
+              t.L0 = f1 - f0;
+              t.s0 = b;
+              t.s1 = 1;
+              t.sc = ld_prev;
+              t.tri = f1 - f0;
+            }
             tsqr[lvl].push_back(t);
           }
           if (final_level) break;
-          src = dst;
-          rows = (int64_t)nblk * b;
-          L0 = rows;
-          s0 = 1;
-          s1 = 0;
-          sc = dst_ld;
+          prev = dst;
+          ld_prev = dst_ld;
+          nfac = nblk;
         }
       }
       SvdJob sj;
@@ -1292,19 +1310,33 @@ static void build_hosvd_f64(tks_plan* plan) {
       sj.order = d;
       sj.tol = plan->params.trunc_tol;
       svds.push_back(sj);
-      const Operand Y = (n == d - 1) ? op(B_OUT, h.out_core_off * 8) : op(B_WS, h.Hp[n & 1]);
-      GemmJob t;
-      if (L == 1) {
-        t = gemm(rmax, (int)Rr, b, op(B_WS, h.P[n]), b, 1, X, b, 1, Y, 1, rmax);
-      } else {
-        t = gemm((int)L, rmax, b, X, 1, L, op(B_WS, h.P[n]), b, 1, Y, 1, L);
-        t.batch = (int)Rr;
-        t.a_b = L * b;
-        t.c_b = L * rmax;
-      }
-      ttm.add(t);
-      fac.add(gemm((int)h.n[n], rmax, b, op(B_Q, h.q_off[n] * 8), 1, h.n[n], op(B_WS, h.P[n]), b, 1,
-                   op(B_OUT, h.out_fac_off[n] * 8), 1, h.n[n]));
+      // H x_n P_n^T (fibres (l, rr) of H_(n)) and U~_n = Q_n P_n (fibres = rows of Q_n)
+      TtmJob tj;
+      std::memset(&tj, 0, sizeof(tj));
+      tj.X = X;
+      tj.x_type = T_F64;
+      tj.P = op(B_WS, h.P[n]);
+      tj.Y = (n == d - 1) ? op(B_OUT, h.out_core_off * 8) : op(B_WS, h.Hp[n & 1]);
+      tj.y_type = T_F64;
+      tj.L = L;
+      tj.Rr = Rr;
+      tj.b = b;
+      tj.rmax = rmax;
+      tj.tiles = ttm64_tiles(L * Rr);
+      tj.tile_begin = ttm_tiles;
+      ttm_tiles += tj.tiles;
+      ttm.push_back(tj);
+      ttm_flops += 2.0 * (double)L * Rr * b * rmax;
+      TtmJob fj = tj;
+      fj.X = op(B_Q, h.q_off[n] * 8);
+      fj.Y = op(B_OUT, h.out_fac_off[n] * 8);
+      fj.L = (int64_t)h.n[n];
+      fj.Rr = 1;
+      fj.tiles = ttm64_tiles((int64_t)h.n[n]);
+      fj.tile_begin = fac_tiles;
+      fac_tiles += fj.tiles;
+      fac.push_back(fj);
+      fac_flops += 2.0 * (double)h.n[n] * b * rmax;
     }
     char nm[32];
     for (size_t lvl = 0; lvl < tsqr.size(); ++lvl) {
@@ -1314,10 +1346,14 @@ static void build_hosvd_f64(tks_plan* plan) {
     }
     std::snprintf(nm, sizeof(nm), "a9:svd%d", n);
     plan->push(plan->st_recompress, S_SVD64, svds, (int64_t)svds.size(), nm);
+    int max_cols = 1;
+    for (const auto& t : ttm) max_cols = std::max(max_cols, t.rmax);
     std::snprintf(nm, sizeof(nm), "a9:ttm%d", n);
-    plan->push_gemm(plan->st_recompress, ttm, nm);
+    plan->push(plan->st_recompress, S_TTM64, ttm, ttm_tiles, nm, ttm_flops, 0.0);
+    if (!ttm.empty()) plan->st_recompress.back().nb_max = max_cols;   // column groups of the kernel
     std::snprintf(nm, sizeof(nm), "a9:factor%d", n);
-    plan->push_gemm(plan->st_recompress, fac, nm);
+    plan->push(plan->st_recompress, S_TTM64, fac, fac_tiles, nm, fac_flops, 0.0);
+    if (!fac.empty()) plan->st_recompress.back().nb_max = max_cols;
   }
 }
 
@@ -1887,6 +1923,9 @@ tks_status run_steps(tks_plan* plan, const std::vector<Step>& steps, const Bases
         break;
       case S_SVD64:
         launch_svd_f64(static_cast<const SvdJob*>(table), s.njobs, plan->bmax, bases, plan->status, stream);
+        break;
+      case S_TTM64:
+        launch_ttm_f64(static_cast<const TtmJob*>(table), s.njobs, (int)s.work, s.nb_max, plan->bmax, bases, stream);
         break;
       case S_TC:
         launch_tc_gemm(static_cast<const TcJob*>(table), s.njobs, (int)s.work, plan->arena_dev + plan->maps_off,

@@ -26,6 +26,11 @@ cudaError_t prepare_la64(int bmax);      // raises the dynamic shared memory lim
 void launch_tsqr_f64(const TsqrJob* jobs, int njobs, int max_cols, const Bases& bases, cudaStream_t stream);
 void launch_svd_f64(const SvdJob* jobs, int njobs, int bmax, const Bases& bases, Status* status,
                     cudaStream_t stream);
+// Float64 mode products with a small matrix (ST-HOSVD truncation and final factors), 64 fibres per CTA.
+int ttm64_tiles(int64_t fibres);
+// max_cols: the largest rmax among the launch's jobs
+void launch_ttm_f64(const TtmJob* jobs, int njobs, int total_tiles, int max_cols, int bmax, const Bases& bases,
+                    cudaStream_t stream);
 
 // Tensor-core (tcgen05) grouped GEMM over bf16 planes; maps = device array of CUtensorMap.
 size_t tc_gemm_smem_bytes(int stages, int na_max, int nb_max, int bn);

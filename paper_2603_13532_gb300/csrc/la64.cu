@@ -9,6 +9,8 @@
 // thousand warp-level FMAs, against a few hundred cycles of reduction and barrier.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "fastdiv.cuh"
 #include "kernels.h"
 
@@ -26,72 +28,143 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
-// Warp sums of kN independent values with their butterflies interleaved.
+// Sums over the 32 lanes of kN (1, 2, 4 or 8) per-lane values; returns, in every lane, the total of
+// value s(lane), where s(lane) collects the lane bits 16, 8, ... of the first log2(kN) levels (see
+// slot_lane).  A transposed butterfly: at each of those levels a lane keeps half of its values and
+// sends the other half, so the warp spends kN - 1 + 5 - log2(kN) additions per lane instead of 5 kN.
 template <int kN>
-__device__ __forceinline__ void warp_sum_nd(double (&v)[kN]) {
+__device__ __forceinline__ double warp_sum_transposed(double (&v)[kN]) {
+  const int lane = threadIdx.x & 31;
+  int o = 16;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1)
+  for (int h = kN / 2; h >= 1; h /= 2, o >>= 1) {
+    const bool up = (lane & o) != 0;
 #pragma unroll
-    for (int q = 0; q < kN; ++q) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+    for (int i = 0; i < h; ++i) {
+      const double send = up ? v[i] : v[i + h];
+      const double keep = up ? v[i + h] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  double r = v[0];
+  for (; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+  return r;
+}
+
+// A lane that holds the total of value s after warp_sum_transposed<kN>.
+template <int kN>
+__device__ __forceinline__ int slot_lane(int s) {
+  int lane = 0, o = 16;
+#pragma unroll
+  for (int h = kN / 2; h >= 1; h /= 2, o >>= 1)
+    if (s & h) lane |= o;
+  return lane;
 }
 
 // Step j of the register-resident Householder sweep: a_l -= tau v_j (v_j^T a_l) for every column
-// l > j (l < ncols) this warp holds (column l lives in warp l % kWarps, slot l / kWarps).
+// l > j (l < ncols) this warp holds (column l lives in warp l % kWarps, slot l / kWarps).  Row slots
+// u whose bit in umask is clear hold only rows where v_j is zero and are skipped.
 template <int kRpl, int kSlots, int kWarps>
 __device__ __forceinline__ void apply_reflector_d(double (&a)[kSlots][kRpl], const double (&vj)[kRpl], double tau,
-                                                  int j, int ncols) {
+                                                  int j, int ncols, unsigned umask) {
   const int warp = threadIdx.x >> 5;
   if (tau == 0.0) return;
-  double dot[kSlots];
+  constexpr int kP = kSlots <= 1 ? 1 : kSlots <= 2 ? 2 : kSlots <= 4 ? 4 : 8;
+  double dot[kP];
 #pragma unroll
-  for (int sl = 0; sl < kSlots; ++sl) {
+  for (int sl = 0; sl < kP; ++sl) {
+    dot[sl] = 0.0;
     const int l = warp + kWarps * sl;
-    double d0 = 0.0, d1 = 0.0;
-    if (l > j && l < ncols) {   // warp-uniform: finished and absent columns skip the products
+    if (sl < kSlots && l > j && l < ncols) {   // warp-uniform: finished and absent columns skip the products
+      double d = 0.0;
 #pragma unroll
-      for (int u = 0; u + 1 < kRpl; u += 2) {
-        d0 = fma(vj[u], a[sl][u], d0);
-        d1 = fma(vj[u + 1], a[sl][u + 1], d1);
-      }
-      if (kRpl & 1) d0 = fma(vj[kRpl - 1], a[sl][kRpl - 1], d0);
+      for (int u = 0; u < kRpl; ++u)
+        if ((umask >> u) & 1u) d = fma(vj[u], a[sl < kSlots ? sl : 0][u], d);
+      dot[sl] = d;
     }
-    dot[sl] = d0 + d1;
   }
-  warp_sum_nd(dot);
+  // each lane scales the total it holds; the owner lanes broadcast w = tau v_j^T a_l
+  const double w_own = tau * warp_sum_transposed<kP>(dot);
 #pragma unroll
   for (int sl = 0; sl < kSlots; ++sl) {
     const int l = warp + kWarps * sl;
+    const double w = __shfl_sync(0xffffffffu, w_own, slot_lane<kP>(sl));
     if (l > j && l < ncols) {
-      const double w = tau * dot[sl];
 #pragma unroll
-      for (int u = 0; u < kRpl; ++u) a[sl][u] = fma(-w, vj[u], a[sl][u]);
+      for (int u = 0; u < kRpl; ++u)
+        if ((umask >> u) & 1u) a[sl][u] = fma(-w, vj[u], a[sl][u]);
     }
   }
+}
+
+// 2^-e for the exponent e of x > 0 (x 2^-e in [1, 2)), or 0 when x is zero, subnormal, not finite
+// or 2^-e is not a normal double; from the exponent bits, without a division.
+__device__ __forceinline__ double pow2_inverse(double x) {
+  const int ex = (int)((__double_as_longlong(x) >> 52) & 0x7ff);
+  return (ex >= 1 && ex <= 2045) ? __longlong_as_double((long long)(2046 - ex) << 52) : 0.0;
+}
+
+// 1 / sqrt(z) and 1 / x for normal z, x > 0 in float64 by Newton's method from a float32 estimate:
+// the argument is scaled by a power of two into float32 range (an even power for the square root),
+// and each Newton step squares the relative error (2^-22 -> 2^-44 -> below float64 rounding).  Far
+// shorter dependent chains than a float64 division or square root, which matters where one thread's
+// result gates a whole block (a Householder reflector per column).
+__device__ __forceinline__ double rsqrt_newton(double z) {
+  const int ex = (int)((__double_as_longlong(z) >> 52) & 0x7ff) - 1023;
+  const int k = ex >> 1;                                     // z = z1 4^k, z1 in [1, 4)
+  const double down = __longlong_as_double((long long)(1023 - 2 * k) << 52);
+  const double up = __longlong_as_double((long long)(1023 - k) << 52);
+  const double z1 = z * down, h = 0.5 * z1;
+  double y = (double)rsqrtf((float)z1);
+  y = y * fma(-h * y, y, 1.5);
+  y = y * fma(-h * y, y, 1.5);
+  return y * up;
+}
+__device__ __forceinline__ double rcp_newton(double x) {
+  const double sc = pow2_inverse(x);
+  const double x1 = x * sc;                                  // in [1, 2)
+  double y = (double)(1.0f / (float)x1);
+  y = y * fma(-x1, y, 2.0);
+  y = y * fma(-x1, y, 2.0);
+  return y * sc;
 }
 
 // Forms the Householder reflector of column c (held by this warp: value a[u] at row lane + 32 u,
 // m rows) that zeroes the rows below c, and publishes v = (0, .., 0, 1, x / (alpha - beta)) into
-// v_out[0, vlen), tau = (beta - alpha) / beta and the diagonal entry beta of R.  A column whose
-// rows below c are already zero gets tau = 0 and keeps its diagonal entry.  Returns false when the
-// column norm is not finite.
+// v_out[0, vlen), tau = (beta - alpha) / beta and the diagonal entry beta of R.  With
+// beta = -sign(alpha) ||a||, tau = 1 + |alpha| / ||a|| and 1 / (alpha - beta) =
+// sign(alpha) / (|alpha| + ||a||), so one reciprocal square root and one reciprocal (rsqrt_newton,
+// rcp_newton) form the reflector.  A column whose rows below c are already zero gets tau = 0 and
+// keeps its diagonal entry.  Returns false when the column norm is not finite.
 template <int kRpl>
 __device__ __forceinline__ bool reflector_publish_d(const double (&a)[kRpl], int c, int m, double* v_out, int vlen,
                                                     double* tau_out, double* rdiag) {
   const int lane = threadIdx.x & 31;
-  double t2 = 0.0, alpha = 0.0;
+  double t0 = 0.0, t1 = 0.0, alpha = 0.0;
 #pragma unroll
   for (int u = 0; u < kRpl; ++u) {
     const int i = lane + 32 * u;
-    if (i > c && i < m) t2 = fma(a[u], a[u], t2);
+    if (i > c && i < m) {
+      if (u & 1) t1 = fma(a[u], a[u], t1);
+      else t0 = fma(a[u], a[u], t0);
+    }
     if (i == c) alpha = a[u];
   }
-  t2 = warp_sum_d(t2);
+  const double t2 = warp_sum_d(t0 + t1);
   alpha = __shfl_sync(0xffffffffu, alpha, c & 31);
-  const double nrm = sqrt(fma(alpha, alpha, t2));
-  const bool reflect = t2 > 0.0 && isfinite(nrm);
-  const double beta = alpha >= 0.0 ? -nrm : nrm;
-  const double tau = reflect ? (beta - alpha) / beta : 0.0;
-  const double sc = reflect ? 1.0 / (alpha - beta) : 0.0;
+  const double z = fma(alpha, alpha, t2);
+  const bool finite = isfinite(z);
+  const bool reflect = t2 > 0.0 && finite && pow2_inverse(z) > 0.0;
+  double tau = 0.0, sc = 0.0, beta = alpha;
+  if (reflect) {
+    const double inv_n = rsqrt_newton(z);
+    const double nrm = z * inv_n;
+    const double aa = fabs(alpha);
+    tau = fma(aa, inv_n, 1.0);
+    const double r = rcp_newton(aa + nrm);
+    sc = alpha >= 0.0 ? r : -r;
+    beta = alpha >= 0.0 ? -nrm : nrm;
+  }
 #pragma unroll
   for (int u = 0; u < kRpl; ++u) {
     const int i = lane + 32 * u;
@@ -99,29 +172,28 @@ __device__ __forceinline__ bool reflector_publish_d(const double (&a)[kRpl], int
   }
   if (lane == 0) {
     *tau_out = tau;
-    rdiag[c] = reflect ? beta : alpha;
+    rdiag[c] = beta;
   }
-  return isfinite(nrm);
+  return finite;
 }
 
 // ----------------------------------------------------------------------------- TSQR block (float64)
 // Householder QR of a rows x cols block of a float64 source read through a two-level row index
-// (rows <= 32 kRpl, cols <= 16 kSlots); only the triangular factor is kept.  The block is staged
+// (rows <= 32 kRpl, cols <= kWarps kSlots); only the triangular factor is kept.  The block is staged
 // through shared memory (coalesced along whichever index is contiguous in the source) and then
-// lives in registers: column l in warp l % 16 (slot l / 16), lane L holds rows L + 32 u.  Each step j
+// lives in registers: column l in warp l % kWarps (slot l / kWarps), lane L holds rows L + 32 u.  Each step j
 // reads the published reflector v_j and tau_j, every warp updates its columns l > j, and the warp
 // owning column j + 1 forms and publishes the next reflector: one barrier per column.
-constexpr int kT64Threads = 512;
-constexpr int kT64Warps = kT64Threads / 32;
 constexpr int kT64LoadBatch = 8;
 
-template <int kRpl, int kSlots>
-__global__ void __launch_bounds__(kT64Threads, 1) tsqr_f64_kernel(const TsqrJob* __restrict__ jobs, Bases bases) {
+template <int kRpl, int kSlots, int kWarps>
+__global__ void __launch_bounds__(32 * kWarps, 1) tsqr_f64_kernel(const TsqrJob* __restrict__ jobs, Bases bases) {
+  constexpr int kThreads = 32 * kWarps;
   constexpr int kBlockRows = 32 * kRpl;
   extern __shared__ double smem_t64[];
   __shared__ double vbuf[2][kBlockRows];
   __shared__ double sh_tau[2];
-  __shared__ double rdiag[kT64Warps * kSlots];
+  __shared__ double rdiag[kWarps * kSlots];
   __shared__ int64_t rowoff[kBlockRows];
   const TsqrJob& J = jobs[blockIdx.x];
   const int m = J.rows, b = J.cols;
@@ -137,12 +209,12 @@ __global__ void __launch_bounds__(kT64Threads, 1) tsqr_f64_kernel(const TsqrJob*
   const bool row_major = J.sc == 1;
   const int mb = m * b;   // <= 256 x 64 or 192 x 96, below 2^15
   const SmallDiv dq(row_major ? b : m);
-  for (int e0 = 0; e0 < mb; e0 += kT64LoadBatch * kT64Threads) {
+  for (int e0 = 0; e0 < mb; e0 += kT64LoadBatch * kThreads) {
     double v[kT64LoadBatch];
     int dst[kT64LoadBatch];
 #pragma unroll
     for (int u = 0; u < kT64LoadBatch; ++u) {
-      const int e = e0 + u * kT64Threads + threadIdx.x;
+      const int e = e0 + u * kThreads + threadIdx.x;
       v[u] = 0.0;
       dst[u] = -1;
       if (e < mb) {
@@ -161,7 +233,7 @@ __global__ void __launch_bounds__(kT64Threads, 1) tsqr_f64_kernel(const TsqrJob*
   double a[kSlots][kRpl];
 #pragma unroll
   for (int sl = 0; sl < kSlots; ++sl) {
-    const int l = warp + kT64Warps * sl;
+    const int l = warp + kWarps * sl;
 #pragma unroll
     for (int u = 0; u < kRpl; ++u) {
       const int i = lane + 32 * u;
@@ -176,10 +248,16 @@ __global__ void __launch_bounds__(kT64Threads, 1) tsqr_f64_kernel(const TsqrJob*
     double vj[kRpl];
 #pragma unroll
     for (int u = 0; u < kRpl; ++u) vj[u] = vbuf[j & 1][lane + 32 * u];
-    apply_reflector_d<kRpl, kSlots, kT64Warps>(a, vj, tau, j, b);
+    // row slots that can hold a nonzero of v_j: rows below the block's end, at or below row j, and
+    // for a stack of tri interleaved triangular factors (row i = factor + tri r) with r <= j
+    unsigned umask = 0;
+#pragma unroll
+    for (int u = 0; u < kRpl; ++u)
+      if (32 * u < m && 32 * u + 31 >= j && (J.tri == 0 || 32 * u < J.tri * (j + 1))) umask |= 1u << u;
+    apply_reflector_d<kRpl, kSlots, kWarps>(a, vj, tau, j, b, umask);
 #pragma unroll
     for (int sl = 0; sl < kSlots; ++sl) {
-      const int l = warp + kT64Warps * sl;
+      const int l = warp + kWarps * sl;
       if (l == j + 1 && l < kmax)
         reflector_publish_d(a[sl], l, m, vbuf[(j + 1) & 1], kBlockRows, &sh_tau[(j + 1) & 1], rdiag);
     }
@@ -190,7 +268,7 @@ __global__ void __launch_bounds__(kT64Threads, 1) tsqr_f64_kernel(const TsqrJob*
   double* dst = at<double>(bases, J.dst);
 #pragma unroll
   for (int sl = 0; sl < kSlots; ++sl) {
-    const int c = warp + kT64Warps * sl;
+    const int c = warp + kWarps * sl;
     if (c < b) {
 #pragma unroll
       for (int u = 0; u < kRpl; ++u) {
@@ -206,12 +284,13 @@ __global__ void __launch_bounds__(kT64Threads, 1) tsqr_f64_kernel(const TsqrJob*
 }
 
 // ----------------------------------------------------------------------------- Jacobi SVD (float64)
-// One-sided (Hestenes) Jacobi on the columns of the b x b factor A = R with the round-robin ordering:
-// each round rotates b/2 disjoint column pairs (kJ64Lanes lanes per pair, two rows per lane and
-// chunk) until they are orthogonal; V accumulates the rotations, so that at convergence
-// R V = U Sigma and the columns of V are the right singular vectors of R, i.e. the left singular
-// vectors of H_(n).  Then: singular values = column norms, sorted; the rank rule of Alg. 2; P = the
-// leading columns of V, sign-fixed (largest-magnitude entry positive), zero-padded to rmax.
+// One-sided (Hestenes) Jacobi with the round-robin ordering: each round rotates b/2 disjoint column
+// pairs (kJ64Lanes lanes per pair) until they are orthogonal.  It runs on the columns of X = R^T for
+// the b x b factor R of H_(n)^T: at convergence X J = U Sigma, and U (the normalized columns) holds the
+// right singular vectors of R, i.e. the left singular vectors of H_(n).  Then the singular values
+// (column norms) are sorted, the rank rule of Alg. 2 applied and P = the leading columns of U,
+// sign-fixed (largest-magnitude entry positive), zero-padded to rmax.
+
 constexpr int kJ64Sweeps = 40;
 constexpr int kJ64Lanes = 8;
 constexpr int kJ64Threads = kJ64Lanes * (TKS_MAX_BASIS / 2);   // 384
@@ -228,120 +307,239 @@ __device__ double block_sum_d(double v, double* red) {
   return s;
 }
 
-__global__ void __launch_bounds__(kJ64Threads) svd_jacobi_f64_kernel(const SvdJob* __restrict__ jobs, Bases bases,
-                                                                   Status* status) {
-  extern __shared__ double sm64[];
-  const SvdJob& J = jobs[blockIdx.x];
-  const int b = J.b;
-  const int m = b + (b & 1);
-  const int ld = (m + 1) & ~1;   // columns start 16-byte aligned; rows in [b, ld) stay zero
-  double* A = sm64;
-  double* V = A + m * ld;
-  double* nrm = V + m * ld;
-  int* order = reinterpret_cast<int*>(nrm + m);
-  __shared__ int sh_rot, sh_rank;
-  __shared__ double red[32];
-  __shared__ double sh_noise2;
-  const double* Rg = at<double>(bases, J.R);
-  for (int e = threadIdx.x; e < m * ld; e += blockDim.x) {
-    const int r = e % ld, c = e / ld;
-    A[e] = (r < b && c < b) ? Rg[r + c * b] : 0.0;
-    V[e] = (r == c) ? 1.0 : 0.0;
+// Column pair of group k in round `round` of the circle ordering over m (even) columns: pair 0 is
+// (round, m - 1), pair k > 0 is ((round + k) mod (m - 1), (round - k) mod (m - 1)); p < q.
+__device__ __forceinline__ void jacobi_pair(int k, int round, int m, int& p, int& q) {
+  if (k == 0) {
+    p = round;
+    q = m - 1;
+  } else {
+    p = round + k;
+    if (p >= m - 1) p -= m - 1;
+    q = round - k;
+    if (q < 0) q += m - 1;
   }
-  if (threadIdx.x == 0) sh_noise2 = 0.0;
-  __syncthreads();
+  if (p > q) { const int t = p; p = q; q = t; }
+}
+
+// tan(theta) of the Jacobi rotation, t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)) with zeta = num / den
+// (den != 0), evaluated in float32 after scaling num and den by the same power of two.  The angle only
+// steers convergence (a t off by float32 rounding leaves a float32-relative residual coupling that the
+// next sweep removes); the rotation built from t is exactly orthogonal in float64 in any case.  When a
+// rotation is taken, |zeta| < 1 / (16 eps thr), so the scaled values stay in float32 range.
+__device__ __forceinline__ double jacobi_tangent(double num, double den) {
+  const double sc = pow2_inverse(fabs(den));
+  float z;
+  if (sc > 0.0) {
+    z = (float)(num * sc) / (float)(den * sc);
+  } else {
+    z = (float)(num / den);
+  }
+  const float az = fabsf(z);
+  const float tm = az > 1e18f ? 0.5f / az : 1.f / (az + sqrtf(fmaf(az, az, 1.f)));
+  return (double)copysignf(tm, z);
+}
+
+// Float64 sweeps on the columns of A (ld doubles apart, 16-byte aligned) until no pair rotates or
+// max_sweeps; returns the sweeps run.  Rotates while |a_p . a_q| > b eps ||a_p|| ||a_q||, skipping
+// columns at the float64 noise floor (norm <= 8 eps max norm): their couplings are rounding noise.
+// The rotation angle is that of the symmetric 2 x 2 Schur decomposition of the pair's Gram block
+// (Golub & Van Loan), t = tan(theta) from zeta = (beta - alpha) / (2 gamma).
+//
+// Each column is kept as d_c a_c (a scale and a stored vector) with its squared norm n_c tracked
+// through the rotations: the rotation P' = c (P - t Q), Q' = c (Q + t P) becomes
+//   a_p <- a_p - (t d_q / d_p) a_q,  a_q <- a_q + (t d_p / d_q) a_p,  d_p, d_q <- c d_p, c d_q,
+//   n_p <- n_p - t gamma,  n_q <- n_q + t gamma,
+// so a pair costs one dot product (gamma) and one FMA per stored element, instead of three dot
+// products and two multiplies plus two FMAs (on GB300 the FP64 pipe, at 1/64 of the float32 rate,
+// is the bound).  At the start of every sweep the scales are folded into the vectors and the norms
+// recomputed, which bounds the drift of both.  The rotation is computed by the first lane of each
+// group and broadcast, with the tangent in float32 (jacobi_tangent) and c = 1 / sqrt(1 + t^2)
+// refined to float64 by two Newton steps, so the chain of dependent float64 operations that bounds
+// a round's latency is a small fraction of a float64 division-and-square-root evaluation.  A pair is
+// visited once per sweep; when neither of its columns has rotated since its previous visit (in the
+// previous sweep or earlier in this one) it is still orthogonal and is skipped without loading it.
+// dsc, dinv and nsq hold m doubles each, flags 2 m ints.
+__device__ int jacobi_sweeps_f64(double* A, int ld, int b, int m, int max_sweeps, double noise2, int* sh_rot,
+                                 double* dsc, double* dinv, double* nsq, int* flags) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  // rotate while |a_p . a_q| > b eps ||a_p|| ||a_q||, except for columns at the float64 noise floor
-  // (norm <= 8 eps times the largest column norm): their couplings are rounding noise
-  const double eps = 1.1102230246251565e-16;
-  const double thr = (double)b * eps;
-  for (int c = warp; c < b; c += nw) {
-    double s2 = 0.0;
-    for (int i = lane; i < b; i += 32) s2 = fma(A[i + c * ld], A[i + c * ld], s2);
-    s2 = warp_sum_d(s2);
-    // non-negative doubles order like their bit patterns
-    if (lane == 0) atomicMax(reinterpret_cast<unsigned long long*>(&sh_noise2), (unsigned long long)__double_as_longlong(s2));
-  }
-  __syncthreads();
-  const double noise2 = sh_noise2 * (8.0 * eps) * (8.0 * eps);
   const int sub = lane % kJ64Lanes;
+  const int lead = lane - sub;
   const int k = threadIdx.x / kJ64Lanes;
   const int pairs = m / 2;
+  const double thr = (double)b * 1.1102230246251565e-16, thr2 = thr * thr;
+  int* rot_prev = flags;       // column rotated during the previous sweep (all set before the first)
+  int* rot_cur = flags + m;    // column rotated so far in this sweep
+  for (int c = threadIdx.x; c < m; c += blockDim.x) {
+    rot_prev[c] = 1;
+    rot_cur[c] = 0;
+    dsc[c] = 1.0;
+    dinv[c] = 1.0;
+  }
+  __syncthreads();
   int sweep = 0;
-  for (; sweep < kJ64Sweeps; ++sweep) {
-    if (threadIdx.x == 0) sh_rot = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    // fold the scales into the vectors and recompute the squared norms
+    for (int c = warp; c < b; c += nw) {
+      const double dc = dsc[c];
+      double s2 = 0.0;
+      for (int i = lane; i < b; i += 32) {
+        const double v = dc * A[i + c * ld];
+        A[i + c * ld] = v;
+        s2 = fma(v, v, s2);
+      }
+      s2 = warp_sum_d(s2);
+      if (lane == 0) {
+        nsq[c] = s2;
+        dsc[c] = 1.0;
+        dinv[c] = 1.0;
+      }
+    }
+    if (threadIdx.x == 0) *sh_rot = 0;
     __syncthreads();
     int any = 0;
     for (int round = 0; round < m - 1; ++round) {
-      int p = 0, q = 0;
-      if (k == 0) {
-        p = round;
-        q = m - 1;
-      } else {
-        p = round + k;
-        if (p >= m - 1) p -= m - 1;
-        q = round - k;
-        if (q < 0) q += m - 1;
-      }
-      if (p > q) { const int t = p; p = q; q = t; }
-      const bool valid = k < pairs && q < b;
+      int p, q;
+      jacobi_pair(k, round, m, p, q);
+      bool valid = k < pairs && q < b;
+      if (valid) valid = (rot_prev[p] | rot_prev[q] | rot_cur[p] | rot_cur[q]) != 0;
       if (!valid) p = q = 0;
       double* ap = A + p * ld;
       double* aq = A + q * ld;
       double2 x[kJ64Chunks], y[kJ64Chunks];
-      double al = 0.0, be = 0.0, ga = 0.0;
+      double g0 = 0.0, g1 = 0.0;
 #pragma unroll
       for (int u = 0; u < kJ64Chunks; ++u) {
         const int i = 2 * (sub + kJ64Lanes * u);
         const bool in = valid && i < b;
         x[u] = in ? *reinterpret_cast<const double2*>(ap + i) : make_double2(0.0, 0.0);
         y[u] = in ? *reinterpret_cast<const double2*>(aq + i) : make_double2(0.0, 0.0);
+        g0 = fma(x[u].x, y[u].x, g0);
+        g1 = fma(x[u].y, y[u].y, g1);
       }
+      double g = g0 + g1;
 #pragma unroll
-      for (int u = 0; u < kJ64Chunks; ++u) {
-        al = fma(x[u].x, x[u].x, fma(x[u].y, x[u].y, al));
-        be = fma(y[u].x, y[u].x, fma(y[u].y, y[u].y, be));
-        ga = fma(x[u].x, y[u].x, fma(x[u].y, y[u].y, ga));
+      for (int o = kJ64Lanes / 2; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o, kJ64Lanes);
+      // the group's first lane decides and forms the rotation; every lane of the group follows
+      int act = 0;
+      double mp = 0.0, mq = 0.0;
+      if (valid && sub == 0) {
+        const double dp = dsc[p], dq = dsc[q];
+        const double al = nsq[p], be = nsq[q];
+        const double ga = dp * dq * g;
+        // |gamma| > thr sqrt(alpha beta), evaluated on values scaled by a power of two near
+        // 1 / max(alpha, beta) so that neither product under- or overflows
+        const double sc = pow2_inverse(fmax(al, be));
+        const double a1 = al * sc, b1 = be * sc, g1 = ga * sc;
+        if (sc > 0.0 && g1 * g1 > thr2 * a1 * b1 && fmin(al, be) > noise2) {
+          const double t = jacobi_tangent(be - al, 2.0 * ga);
+          // c = 1 / sqrt(w), w = 1 + t^2, from the float32 estimate and two Newton steps (float64
+          // accuracy: c^2 (1 + t^2) = 1 is what makes the rotation orthogonal)
+          const double w = fma(t, t, 1.0), hw = 0.5 * w;
+          double c = (double)rsqrtf((float)w);
+          c = c * fma(-hw * c, c, 1.5);
+          c = c * fma(-hw * c, c, 1.5);
+          const double c2 = c * c, wc = w * c;   // c^2 and sqrt(w)
+          const double ip = dinv[p], iq = dinv[q];
+          mp = t * dq * ip;
+          mq = t * dp * iq;
+          dsc[p] = c * dp;
+          dsc[q] = c * dq;
+          dinv[p] = ip * wc;
+          dinv[q] = iq * wc;
+          // the new squared norms for this t (exactly the rotated columns' norms, whatever t is)
+          nsq[p] = c2 * fma(t, fma(t, be, -2.0 * ga), al);
+          nsq[q] = c2 * fma(t, fma(t, al, 2.0 * ga), be);
+          rot_cur[p] = rot_cur[q] = 1;
+          act = 1;
+        }
       }
-#pragma unroll
-      for (int o = kJ64Lanes / 2; o > 0; o >>= 1) {
-        al += __shfl_xor_sync(0xffffffffu, al, o, kJ64Lanes);
-        be += __shfl_xor_sync(0xffffffffu, be, o, kJ64Lanes);
-        ga += __shfl_xor_sync(0xffffffffu, ga, o, kJ64Lanes);
-      }
-      if (valid && fabs(ga) > thr * sqrt(al * be) && ga != 0.0 && fmin(al, be) > noise2) {
-        // rotation that zeroes the (p, q) entry of A^T A (Golub & Van Loan, symmetric 2 x 2 Schur)
-        const double zeta = (be - al) / (2.0 * ga);
-        const double az = fabs(zeta);
-        const double tm = az > 1e150 ? 0.5 / az : 1.0 / (az + sqrt(fma(az, az, 1.0)));
-        const double t = copysign(tm, zeta);
-        const double c = 1.0 / sqrt(fma(t, t, 1.0));
-        const double s = c * t;
-        double* vp = V + p * ld;
-        double* vq = V + q * ld;
+      act = __shfl_sync(0xffffffffu, act, lead);
+      mp = __shfl_sync(0xffffffffu, mp, lead);
+      mq = __shfl_sync(0xffffffffu, mq, lead);
+      if (act) {
 #pragma unroll
         for (int u = 0; u < kJ64Chunks; ++u) {
           const int i = 2 * (sub + kJ64Lanes * u);
           if (i < b) {
             const double2 a0 = x[u], b0 = y[u];
-            *reinterpret_cast<double2*>(ap + i) = make_double2(c * a0.x - s * b0.x, c * a0.y - s * b0.y);
-            *reinterpret_cast<double2*>(aq + i) = make_double2(s * a0.x + c * b0.x, s * a0.y + c * b0.y);
-            const double2 vx = *reinterpret_cast<const double2*>(vp + i);
-            const double2 vy = *reinterpret_cast<const double2*>(vq + i);
-            *reinterpret_cast<double2*>(vp + i) = make_double2(c * vx.x - s * vy.x, c * vx.y - s * vy.y);
-            *reinterpret_cast<double2*>(vq + i) = make_double2(s * vx.x + c * vy.x, s * vx.y + c * vy.y);
+            *reinterpret_cast<double2*>(ap + i) = make_double2(fma(-mp, b0.x, a0.x), fma(-mp, b0.y, a0.y));
+            *reinterpret_cast<double2*>(aq + i) = make_double2(fma(mq, a0.x, b0.x), fma(mq, a0.y, b0.y));
           }
         }
         any = 1;
       }
       __syncthreads();
     }
-    if (any) sh_rot = 1;
+    if (any) *sh_rot = 1;
     __syncthreads();
-    const int rot = sh_rot;
+    const int rot = *sh_rot;
+    for (int c = threadIdx.x; c < m; c += blockDim.x) {
+      rot_prev[c] = rot_cur[c];
+      rot_cur[c] = 0;
+    }
     __syncthreads();
     if (!rot) break;
   }
+  // fold the last scales in: A holds the rotated columns
+  for (int c = warp; c < b; c += nw) {
+    const double dc = dsc[c];
+    for (int i = lane; i < b; i += 32) A[i + c * ld] *= dc;
+  }
+  __syncthreads();
+  return sweep;
+}
+
+// Largest squared column norm of the b x b matrix A (columns ld apart) over the CTA, as a double.
+__device__ double max_col_norm2(const double* A, int ld, int b, double* slot) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (threadIdx.x == 0) *slot = 0.0;
+  __syncthreads();
+  for (int c = warp; c < b; c += nw) {
+    double s2 = 0.0;
+    for (int i = lane; i < b; i += 32) s2 = fma(A[i + c * ld], A[i + c * ld], s2);
+    s2 = warp_sum_d(s2);
+    // non-negative doubles order like their bit patterns (a NaN sorts above them and stays)
+    if (lane == 0) atomicMax(reinterpret_cast<unsigned long long*>(slot), (unsigned long long)__double_as_longlong(s2));
+  }
+  __syncthreads();
+  const double v = *slot;
+  __syncthreads();
+  return v;
+}
+
+// The one-sided Jacobi runs on X = R^T: its left singular vectors are the right singular vectors of R,
+// i.e. the left singular vectors of H_(n), and at convergence they are the normalized columns of the
+// rotated X, so no rotation needs to be accumulated in float64.  (On a triangular factor from QR, the
+// sweeps on R^T also converge in about half the sweeps that R itself needs.)  Kept columns whose norm
+// is at the float64 noise floor carry no direction; they are replaced by an orthonormal completion.
+__global__ void __launch_bounds__(kJ64Threads, 1) svd_jacobi_f64_kernel(const SvdJob* __restrict__ jobs, Bases bases,
+                                                                   Status* status) {
+  extern __shared__ double sm64[];
+  const SvdJob& J = jobs[blockIdx.x];
+  const int b = J.b;
+  const int m = b + (b & 1);
+  const int ld = m;                 // even: columns start 16-byte aligned; rows in [b, ld) stay zero
+  double* A = sm64;                 // m x ld: X = R^T, rotated
+  double* nrm = A + m * ld;
+  double* dsc = nrm + m;            // column scales of the float64 sweeps
+  double* dinv = dsc + m;           // their inverses
+  double* nsq = dinv + m;           // tracked squared column norms
+  int* order = reinterpret_cast<int*>(nsq + m);
+  int* flags = order + m;           // 2 m
+  __shared__ int sh_rot, sh_rank, sh_fill;
+  __shared__ double red[32];
+  __shared__ double sh_max;
+  const double eps = 1.1102230246251565e-16;
+  const double* Rg = at<double>(bases, J.R);   // X[i, k] = R[k, i] = Rg[k + b i]
+  for (int e = threadIdx.x; e < m * ld; e += blockDim.x) {
+    const int r = e % ld, c = e / ld;
+    A[e] = (r < b && c < b) ? Rg[c + r * b] : 0.0;
+  }
+  __syncthreads();
+  const double noise2 = max_col_norm2(A, ld, b, &sh_max) * (8.0 * eps) * (8.0 * eps);
+  const int sweep = jacobi_sweeps_f64(A, ld, b, m, kJ64Sweeps, noise2, &sh_rot, dsc, dinv, nsq, flags);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   // squared singular values = squared column norms; order them by decreasing value
   for (int c = warp; c < b; c += nw) {
     double s = 0.0;
@@ -358,8 +556,7 @@ __global__ void __launch_bounds__(kJ64Threads) svd_jacobi_f64_kernel(const SvdJo
   }
   // thread i places column i at its rank (ties by index; a NaN counts as -1 so the ranks always
   // form a permutation)
-  if ((int)threadIdx.x < b) {
-    const int i = threadIdx.x;
+  for (int i = threadIdx.x; i < b; i += blockDim.x) {
     const double ni = nrm[i] == nrm[i] ? nrm[i] : -1.0;
     int rk = 0;
     for (int j = 0; j < b; ++j) {
@@ -387,22 +584,32 @@ __global__ void __launch_bounds__(kJ64Threads) svd_jacobi_f64_kernel(const SvdJo
       if (r > J.rmax) r = J.rmax;
     }
     sh_rank = r;
+    // kept columns from the first one at the noise floor on carry no direction
+    int fill = r;
+    for (int t = 0; t < r; ++t)
+      if (!(nrm[order[t]] > noise2)) {
+        fill = t;
+        break;
+      }
+    sh_fill = fill;
     *at<int32_t>(bases, J.rank) = r;
     if (!isfinite(tot)) record_status_64(status, TKS_ENONFINITE);
     if (sweep >= kJ64Sweeps) record_status_64(status, TKS_ENOCONV);
   }
   __syncthreads();
-  const int r = sh_rank;
+  const int r = sh_rank, fill = sh_fill;
   double* P = at<double>(bases, J.P);
+  // P[:, t] = the normalized column of rank t, sign-fixed (largest-magnitude entry positive)
   for (int t = warp; t < J.rmax; t += nw) {
-    if (t >= r) {
+    if (t >= fill) {
       for (int i = lane; i < b; i += 32) P[i + (int64_t)t * b] = 0.0;
       continue;
     }
     const int src = order[t];
+    const double inv = 1.0 / sqrt(nrm[src]);
     double best = 0.0;
     for (int i = lane; i < b; i += 32) {
-      const double v = V[i + src * ld];
+      const double v = A[i + src * ld];
       if (fabs(v) > fabs(best)) best = v;
     }
 #pragma unroll
@@ -410,49 +617,200 @@ __global__ void __launch_bounds__(kJ64Threads) svd_jacobi_f64_kernel(const SvdJo
       const double other = __shfl_xor_sync(0xffffffffu, best, o);
       if (fabs(other) > fabs(best) || (fabs(other) == fabs(best) && other > best)) best = other;
     }
-    const double sgn = (best < 0.0) ? -1.0 : 1.0;
-    for (int i = lane; i < b; i += 32) P[i + (int64_t)t * b] = sgn * V[i + src * ld];
+    const double sc = (best < 0.0) ? -inv : inv;
+    for (int i = lane; i < b; i += 32) P[i + (int64_t)t * b] = sc * A[i + src * ld];
+  }
+  if (fill >= r) return;
+  __syncthreads();
+  // orthonormal completion of columns [fill, r) (one warp; only rank-deficient H reaches this): for
+  // each, the unit vector e_j with the largest part orthogonal to the columns before it,
+  // 1 - sum_u P[j, u]^2 >= (b - t) / b, orthogonalized by two Gram-Schmidt passes and normalized
+  if (warp == 0) {
+    for (int t = fill; t < r; ++t) {
+      double* pt = P + (int64_t)t * b;
+      double best = -1.0;
+      int jbest = 0;
+      for (int j = lane; j < b; j += 32) {
+        double s2 = 0.0;
+        for (int u = 0; u < t; ++u) s2 = fma(P[j + (int64_t)u * b], P[j + (int64_t)u * b], s2);
+        if (1.0 - s2 > best) { best = 1.0 - s2; jbest = j; }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oj = __shfl_xor_sync(0xffffffffu, jbest, o);
+        if (ob > best || (ob == best && oj < jbest)) { best = ob; jbest = oj; }
+      }
+      for (int i = lane; i < b; i += 32) pt[i] = (i == jbest) ? 1.0 : 0.0;
+      __syncwarp();
+      for (int pass = 0; pass < 2; ++pass) {
+        for (int u = 0; u < t; ++u) {
+          const double* pu = P + (int64_t)u * b;
+          double d = 0.0;
+          for (int i = lane; i < b; i += 32) d = fma(pu[i], pt[i], d);
+          d = warp_sum_d(d);
+          for (int i = lane; i < b; i += 32) pt[i] = fma(-d, pu[i], pt[i]);
+          __syncwarp();
+        }
+      }
+      double n2 = 0.0;
+      for (int i = lane; i < b; i += 32) n2 = fma(pt[i], pt[i], n2);
+      n2 = warp_sum_d(n2);
+      const double inv = 1.0 / sqrt(n2);
+      for (int i = lane; i < b; i += 32) pt[i] *= inv;
+      __syncwarp();
+    }
   }
 }
 
 size_t svd64_smem(int bmax) {
-  const int m = bmax + (bmax & 1), ld = (m + 1) & ~1;
-  return (size_t)2 * m * ld * sizeof(double) + (size_t)m * sizeof(double) + (size_t)m * sizeof(int);
+  const int m = bmax + (bmax & 1);
+  return (size_t)m * m * sizeof(double) + (size_t)4 * m * sizeof(double) + (size_t)3 * m * sizeof(int);
 }
 
 size_t tsqr64_smem(int rows, int cols) { return (size_t)(rows + 1) * cols * sizeof(double); }
 
+// ----------------------------------------------------------------------------- mode products (float64)
+// Y[l + L (c + rmax r)] = sum_a X[l + L (a + b r)] P[a + b c] for l < L, r < Rr, c < rmax: the
+// ST-HOSVD truncation H <- H x_n P_n^T (X = H, fibres q = (l, r)) and the factors U~_n = Q_n P_n
+// (X = Q_n, L = n_n, Rr = 1).  A GEMM whose rows are the fibres, with K = b and N = rmax small: a
+// CTA takes kTtmF fibres and every column, stages the fibre tile (b x kTtmF) and P in shared memory
+// (coalesced along a when L = 1, along l otherwise), and each thread accumulates 4 fibres x
+// ceil(rmax / 16) columns over a in order.  Columns are tiled by 16, so at rmax = 48 no product is
+// wasted on padding (a general 64 x 64 tile computes 64 columns for 48); the FP64 pipe is the bound.
+constexpr int kTtmF = 64;                   // fibres per CTA
+constexpr int kTtmThreads = 256;            // 16 fibre lanes x 16 column lanes
+constexpr int kTtmXs = kTtmF + 1;           // padded row of the fibre tile
+
+// kCj = column groups of 16 (columns of the launch's widest job, rounded up); b is padded to a
+// multiple of 4 with zero rows so the reduction loop unrolls by four.
+template <int kCj>
+__global__ void __launch_bounds__(kTtmThreads) ttm_f64_kernel(const TtmJob* __restrict__ jobs, int njobs,
+                                                             Bases bases) {
+  constexpr int kCols = 16 * kCj;
+  extern __shared__ double tsm64[];
+  __shared__ int64_t fib_off[kTtmF];
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].tile_begin <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+  }
+  const TtmJob& J = jobs[lo];
+  const int b = J.b, rmax = J.rmax;
+  const int bp = (b + 3) & ~3;
+  const int64_t L = J.L, nfib = J.L * J.Rr;
+  const int64_t q0 = (int64_t)(blockIdx.x - J.tile_begin) * kTtmF;
+  const int nq = (int)(nfib - q0 < kTtmF ? nfib - q0 : kTtmF);
+  double* Ps = tsm64;                     // [a][c], zero for c >= rmax and a >= b
+  double* Xs = Ps + (size_t)bp * kCols;   // [a][q], row kTtmXs, zero for a >= b and q >= nq
+  const double* X = at<double>(bases, J.X);
+  const double* P = at<double>(bases, J.P);
+  double* Y = at<double>(bases, J.Y);
+  for (int e = threadIdx.x; e < bp * kCols; e += kTtmThreads) {
+    const int a = e % bp, c = e / bp;
+    Ps[a * kCols + c] = (c < rmax && a < b) ? P[a + (int64_t)b * c] : 0.0;
+  }
+  if (L == 1) {
+    // fibres are contiguous runs of b elements starting at (q0 + q) b
+    for (int e = threadIdx.x; e < bp * kTtmF; e += kTtmThreads) {
+      const int q = e / bp, a = e - q * bp;
+      Xs[a * kTtmXs + q] = (q < nq && a < b) ? X[(q0 + q) * b + a] : 0.0;
+    }
+  } else {
+    for (int q = threadIdx.x; q < kTtmF; q += kTtmThreads) {
+      const int64_t f = q0 + q, r = f / L, l = f - r * L;
+      fib_off[q] = l + L * (int64_t)b * r;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < bp * kTtmF; e += kTtmThreads) {
+      const int q = e % kTtmF, a = e / kTtmF;
+      Xs[a * kTtmXs + q] = (q < nq && a < b) ? X[fib_off[q] + L * a] : 0.0;
+    }
+  }
+  __syncthreads();
+  const int tq = threadIdx.x % 16, tc = threadIdx.x / 16;
+  double acc[4][kCj];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < kCj; ++j) acc[i][j] = 0.0;
+  for (int a0 = 0; a0 < bp; a0 += 4) {
+#pragma unroll
+    for (int da = 0; da < 4; ++da) {
+      const int a = a0 + da;
+      double xv[4], pv[kCj];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) xv[i] = Xs[a * kTtmXs + tq + 16 * i];
+#pragma unroll
+      for (int j = 0; j < kCj; ++j) pv[j] = Ps[a * kCols + tc + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < kCj; ++j) acc[i][j] = fma(xv[i], pv[j], acc[i][j]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int q = tq + 16 * i;
+    if (q >= nq) continue;
+    const int64_t f = q0 + q, r = f / L, l = f - r * L;
+    double* y = Y + l + L * (int64_t)rmax * r;
+#pragma unroll
+    for (int j = 0; j < kCj; ++j) {
+      const int c = tc + 16 * j;
+      if (c < rmax) y[L * c] = acc[i][j];
+    }
+  }
+}
+
+size_t ttm64_smem(int bmax) {
+  const int bp = (bmax + 3) & ~3, cols = 16 * ((bmax + 15) / 16);
+  return (size_t)bp * cols * sizeof(double) + (size_t)bp * kTtmXs * sizeof(double);
+}
+
 }  // namespace
 
 // At least twice the columns, so that every TSQR level shrinks the stack of factors.
-int tsqr64_block_rows(int max_cols) { return max_cols <= 4 * kT64Warps ? 256 : 192; }
+int tsqr64_block_rows(int max_cols) { return max_cols <= 72 ? 256 : 192; }
 
 cudaError_t prepare_la64(int bmax) {
   cudaError_t e = cudaFuncSetAttribute(svd_jacobi_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)svd64_smem(bmax));
   if (e != cudaSuccess) return e;
-  const void* kernels[] = {reinterpret_cast<const void*>(tsqr_f64_kernel<8, 2>),
-                           reinterpret_cast<const void*>(tsqr_f64_kernel<8, 3>),
-                           reinterpret_cast<const void*>(tsqr_f64_kernel<8, 4>),
-                           reinterpret_cast<const void*>(tsqr_f64_kernel<6, 6>)};
+  const void* ttm_kernels[] = {reinterpret_cast<const void*>(ttm_f64_kernel<1>),
+                               reinterpret_cast<const void*>(ttm_f64_kernel<2>),
+                               reinterpret_cast<const void*>(ttm_f64_kernel<3>),
+                               reinterpret_cast<const void*>(ttm_f64_kernel<4>),
+                               reinterpret_cast<const void*>(ttm_f64_kernel<5>),
+                               reinterpret_cast<const void*>(ttm_f64_kernel<6>)};
+  for (const void* k : ttm_kernels) {
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ttm64_smem(bmax));
+    if (e != cudaSuccess) return e;
+  }
+  const void* kernels[] = {reinterpret_cast<const void*>(tsqr_f64_kernel<8, 2, 16>),
+                           reinterpret_cast<const void*>(tsqr_f64_kernel<8, 2, 24>),
+                           reinterpret_cast<const void*>(tsqr_f64_kernel<8, 3, 24>),
+                           reinterpret_cast<const void*>(tsqr_f64_kernel<6, 4, 24>)};
+  // the largest staging tile of any instantiation: 256 x 72 or 192 x 96
+  const size_t tile = std::max(tsqr64_smem(256, 72), tsqr64_smem(192, 96));
   for (const void* k : kernels) {
-    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsqr64_smem(256, 64));
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
 
 void launch_tsqr_f64(const TsqrJob* jobs, int njobs, int max_cols, const Bases& bases, cudaStream_t stream) {
-  // columns per warp: the smallest instantiation that covers max_cols; 256-row blocks up to 64
-  // columns, 192-row blocks beyond (the register tile stays at 32 or 36 doubles per thread)
-  if (max_cols <= 2 * kT64Warps) {
-    tsqr_f64_kernel<8, 2><<<njobs, kT64Threads, tsqr64_smem(256, 2 * kT64Warps), stream>>>(jobs, bases);
-  } else if (max_cols <= 3 * kT64Warps) {
-    tsqr_f64_kernel<8, 3><<<njobs, kT64Threads, tsqr64_smem(256, 3 * kT64Warps), stream>>>(jobs, bases);
-  } else if (max_cols <= 4 * kT64Warps) {
-    tsqr_f64_kernel<8, 4><<<njobs, kT64Threads, tsqr64_smem(256, 4 * kT64Warps), stream>>>(jobs, bases);
+  // the smallest instantiation that covers max_cols: 24 warps (768 threads) hold up to 72 columns
+  // of a 256-row block (24 doubles per thread), 96 columns of a 192-row block
+  if (max_cols <= 32) {
+    tsqr_f64_kernel<8, 2, 16><<<njobs, 512, tsqr64_smem(256, 32), stream>>>(jobs, bases);
+  } else if (max_cols <= 48) {
+    tsqr_f64_kernel<8, 2, 24><<<njobs, 768, tsqr64_smem(256, 48), stream>>>(jobs, bases);
+  } else if (max_cols <= 72) {
+    tsqr_f64_kernel<8, 3, 24><<<njobs, 768, tsqr64_smem(256, 72), stream>>>(jobs, bases);
   } else {
-    tsqr_f64_kernel<6, 6><<<njobs, kT64Threads, tsqr64_smem(192, 6 * kT64Warps), stream>>>(jobs, bases);
+    tsqr_f64_kernel<6, 4, 24><<<njobs, 768, tsqr64_smem(192, 96), stream>>>(jobs, bases);
   }
 }
 
@@ -461,6 +819,22 @@ void launch_svd_f64(const SvdJob* jobs, int njobs, int bmax, const Bases& bases,
   const int pairs = (bmax + 1) / 2;
   const int threads = ((pairs * kJ64Lanes + 31) / 32) * 32;
   svd_jacobi_f64_kernel<<<njobs, threads, svd64_smem(bmax), stream>>>(jobs, bases, status);
+}
+
+int ttm64_tiles(int64_t fibres) { return (int)((fibres + kTtmF - 1) / kTtmF); }
+
+void launch_ttm_f64(const TtmJob* jobs, int njobs, int total_tiles, int max_cols, int bmax, const Bases& bases,
+                    cudaStream_t stream) {
+  // shared memory sized for the plan's widest basis (the kernel pads b and the columns it uses)
+  const size_t smem = ttm64_smem(bmax);
+  switch ((max_cols + 15) / 16) {
+    case 1: ttm_f64_kernel<1><<<total_tiles, kTtmThreads, smem, stream>>>(jobs, njobs, bases); break;
+    case 2: ttm_f64_kernel<2><<<total_tiles, kTtmThreads, smem, stream>>>(jobs, njobs, bases); break;
+    case 3: ttm_f64_kernel<3><<<total_tiles, kTtmThreads, smem, stream>>>(jobs, njobs, bases); break;
+    case 4: ttm_f64_kernel<4><<<total_tiles, kTtmThreads, smem, stream>>>(jobs, njobs, bases); break;
+    case 5: ttm_f64_kernel<5><<<total_tiles, kTtmThreads, smem, stream>>>(jobs, njobs, bases); break;
+    default: ttm_f64_kernel<6><<<total_tiles, kTtmThreads, smem, stream>>>(jobs, njobs, bases); break;
+  }
 }
 
 }  // namespace tks

@@ -120,10 +120,12 @@ struct CoreSketchF32Job {
   int64_t begin;
 };
 
-// Mode product with a small matrix (ST-HOSVD truncation and final factors, float32 arithmetic):
-// Y[l + L (c + rmax r)] = sum_a X[l + L (a + b r)] P[a + b c] for l < L, r < Rr, c < rmax <= 64.
+// Mode product with a small matrix (ST-HOSVD truncation and final factors):
+// Y[l + L (c + rmax r)] = sum_a X[l + L (a + b r)] P[a + b c] for l < L, r < Rr, c < rmax.
+// float32 kernel: X typed (T_F64 / T_F32), P float32, Y typed, rmax <= 64; float64 kernel: X, P
+// and Y float64.
 struct TtmJob {
-  Operand X, P, Y;       // X typed (T_F64 / T_F32), P float32, Y typed
+  Operand X, P, Y;
   int32_t x_type, y_type;
   int64_t L, Rr;
   int32_t b, rmax;
@@ -308,7 +310,9 @@ struct QrF32Job {
 // factoring again gives the triangular factor of the whole matrix.
 struct TsqrJob {
   Operand src, dst;
-  int32_t src_type, rows, cols, pad;
+  int32_t src_type, rows, cols;
+  int32_t tri;           // float64 kernel: 0 = dense rows; k = the rows interleave k stacked upper
+                         // triangular factors (row i = factor + k r), so column j is zero where r > j
   int64_t row_begin, L0, s0, s1, sc;
   int64_t dst_row0, dst_ld;
 };
