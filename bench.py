@@ -421,6 +421,7 @@ def extra_workload_leg(args, workload, device, stream, rank, world):
 
 FP32_PEAK_TFLOPS = 152 * 256 * 2.070e9 / 1e12   # 128 FP32 FMA per SM per clock
 FP64_KINDS = {"gemm", "reduce", "qr", "core_sketch", "tsqr64", "svd64", "ttm64"}
+TENSOR_FP64_KINDS = {"oz_gemm"}
 FP32_KINDS = {"simt", "core_sketch32", "qr32", "svd32", "tsqr32", "core_sketch3", "chain3", "qr_smem32",
               "project3", "sketch3", "qr_reg32", "ttm32", "fold4", "project4", "sketch3f", "sketch4"}
 

@@ -187,6 +187,16 @@ TKS_API tks_status tks_project_core(tks_plan* plan, void* workspace, const doubl
 TKS_API tks_status tucker_sum_recompress(tks_plan* plan, void* workspace, double* out, int32_t* ranks_out,
                                  void* stream);
 
+/* The final truncation alone: ST-HOSVD of given projected cores H (Alg. 2 phase 2; stage 4 of Algs. 3/4),
+ * with modes 1..d in order, the rank rule of the plan and U~_n = Q_n P_n.  Q_in (device, float64, the
+ * basis layout of tks_project_core) and H_in (device, float64, its core layout) are read; out and
+ * ranks_out (device) receive exactly what tucker_sum_recompress writes.  TKS_FP64 and TKS_MIXED plans
+ * run it in float64 (TSQR of each unfolding H_(n)^T, one-sided Jacobi SVD of its triangular factor;
+ * TKS_MIXED takes the mode products H x_n P_n^T and Q_n P_n float64-accurate on the tensor cores),
+ * TKS_MIXED_F32LA in float32. */
+TKS_API tks_status tks_truncate_core(tks_plan* plan, void* workspace, const double* Q_in, const double* H_in,
+                                     double* out, int32_t* ranks_out, void* stream);
+
 /* Backward of the core projection (Sec. 3.3) with the bases held fixed (stop-gradient through Q):
  * with A_kn = Q_n^T U_k^(n) and Hbar = dL/dH given (device, float64, the H layout of
  * tks_project_core), writes
@@ -200,6 +210,16 @@ TKS_API tks_status tucker_sum_recompress(tks_plan* plan, void* workspace, double
 TKS_API tks_status tks_project_core_backward(tks_plan* plan, void* workspace, const double* Q_in,
                                              const double* Hbar_in, double* dcores, double* dfactors,
                                              void* stream);
+
+/* Failure-path controls, for tests and diagnosis.  wait_cycles > 0 bounds every device-side wait of
+ * this plan's tensor-core kernels to that many SM clock cycles (0 restores the default, about 2 s at
+ * 2 GHz).  stall = 1 makes the copy-issuing thread of each tensor-core GEMM of the plan first wait
+ * for a device word that nothing sets, so that its wait runs out: the kernel records TKS_ETIMEOUT,
+ * drains its own copies and products (bounded), frees its tensor memory and returns; the launch
+ * sequence completes with undefined results and tks_sync_status reports TKS_ETIMEOUT.  stall = 0
+ * restores normal operation.  Host-only; applies to calls enqueued afterwards.  TKS_EINVAL for
+ * wait_cycles < 0 or stall outside {0, 1}. */
+TKS_API tks_status tks_plan_set_fault_test(tks_plan* plan, int64_t wait_cycles, int32_t stall);
 
 /* Synchronizes stream, then returns and clears the first error a kernel of this plan recorded
  * since the previous call (TKS_ENONFINITE, TKS_ENOCONV, TKS_ETIMEOUT), else TKS_OK. */
@@ -301,6 +321,16 @@ TKS_API tks_status tks_subrank_problem_info(const tks_subrank_plan* plan, int32_
  * workspace: workspace_bytes of device memory, 256-byte aligned. */
 TKS_API tks_status tks_effective_subrank(tks_subrank_plan* plan, void* workspace, int32_t* ranks_out,
                                          int32_t* ell_out, double* eigenvalues_out, void* stream);
+/* Failure-path controls, for tests and diagnosis.  wait_cycles > 0 bounds every device-side wait of
+ * this plan's tensor-core kernels to that many SM clock cycles (0 restores the default, about 2 s at
+ * 2 GHz).  stall = 1 makes the copy-issuing thread of each tensor-core GEMM of the plan first wait
+ * for a device word that nothing sets, so that its wait runs out: the kernel records TKS_ETIMEOUT,
+ * drains its own copies and products (bounded), frees its tensor memory and returns; the launch
+ * sequence completes with undefined results and tks_sync_status reports TKS_ETIMEOUT.  stall = 0
+ * restores normal operation.  Host-only; applies to calls enqueued afterwards.  TKS_EINVAL for
+ * wait_cycles < 0 or stall outside {0, 1}. */
+TKS_API tks_status tks_plan_set_fault_test(tks_plan* plan, int64_t wait_cycles, int32_t stall);
+
 /* Synchronizes stream, then returns and clears the first error a kernel of this plan recorded
  * (TKS_ENONFINITE for a NaN or Inf in a Gram matrix), else TKS_OK. */
 TKS_API tks_status tks_subrank_sync_status(tks_subrank_plan* plan, void* stream);

@@ -24,7 +24,7 @@ STEP_KINDS = {0: "omega", 1: "gemm", 2: "reduce", 3: "core_sketch", 4: "qr", 5: 
               8: "core_sketch32", 9: "split", 10: "transpose", 11: "qr32", 12: "svd32", 13: "tsqr32",
               14: "core_sketch3", 15: "chain3", 16: "qr_smem32", 17: "project3",
               18: "sketch3", 19: "qr_reg32", 20: "ttm32", 21: "fold4", 22: "project4",
-              23: "sketch3f", 24: "sketch4", 25: "svd64", 26: "ttm64"}
+              23: "sketch3f", 24: "sketch4", 25: "svd64", 26: "ttm64", 27: "oz_slice", 28: "oz_gemm"}
 
 
 class TksError(RuntimeError):
@@ -103,6 +103,8 @@ def load(path=None):
     lib.tucker_sum_sketch.argtypes = [P, P, P, P]
     lib.tks_project_core.argtypes = [P, P, P, P, P]
     lib.tucker_sum_recompress.argtypes = [P, P, P, P, P]
+    lib.tks_truncate_core.argtypes = [P, P, P, P, P, P, P]
+    lib.tks_plan_set_fault_test.argtypes = [P, ctypes.c_int64, ctypes.c_int32]
     lib.tks_project_core_backward.argtypes = [P, P, P, P, P, P, P]
     lib.tks_project_core_backward.restype = ctypes.c_int
     lib.tks_sync_status.argtypes = [P, P]
@@ -125,7 +127,8 @@ def load(path=None):
     lib.tks_subrank_sync_status.argtypes = [P, P]
     for name in ["tks_plan_create", "tks_plan_info", "tks_problem_info", "tks_generate_omega",
                  "tucker_sum_sketch", "tks_project_core", "tucker_sum_recompress", "tks_sync_status",
-                 "tks_profile_begin", "tks_profile_end", "tks_subrank_plan_create", "tks_subrank_info",
+                 "tks_profile_begin", "tks_profile_end", "tks_subrank_plan_create", "tks_truncate_core",
+                 "tks_plan_set_fault_test", "tks_subrank_info",
                  "tks_subrank_problem_info", "tks_effective_subrank", "tks_subrank_sync_status"]:
         getattr(lib, name).restype = ctypes.c_int
     _LIB = lib
@@ -248,9 +251,16 @@ class Plan:
         _check(self.lib.tks_project_core_backward(self.handle, _ptr(self.workspace), _ptr(Q), _ptr(Hbar),
                                                   _ptr(dcores), _ptr(dfactors), _stream_handle()))
 
+    def truncate_raw(self, Q, H, out, ranks):
+        _check(self.lib.tks_truncate_core(self.handle, _ptr(self.workspace), _ptr(Q), _ptr(H), _ptr(out), _ptr(ranks),
+                                          _stream_handle()))
+
     def recompress_raw(self, out, ranks):
         _check(self.lib.tucker_sum_recompress(self.handle, _ptr(self.workspace), _ptr(out), _ptr(ranks),
                                               _stream_handle()))
+
+    def set_fault_test(self, wait_cycles=0, stall=False):
+        _check(self.lib.tks_plan_set_fault_test(self.handle, int(wait_cycles), int(stall)))
 
     def sync(self):
         _check(self.lib.tks_sync_status(self.handle, _stream_handle()))
@@ -352,6 +362,16 @@ class Plan:
         self.sync()
         return self.unpack(out, ranks)
 
+    def truncate(self, Qs, Hs):
+        """The ST-HOSVD truncation alone of given bases Qs and projected cores Hs (lists per problem)."""
+        Q = self.pack_bases(Qs)
+        H = self.pack_core(Hs)
+        out = self._new(self.info.output_elems)
+        ranks = torch.zeros(len(self.problems) * MAX_ORDER, dtype=torch.int32, device=self.device)
+        self.truncate_raw(Q, H, out, ranks)
+        self.sync()
+        return self.unpack(out, ranks)
+
     def unpack(self, out, ranks):
         host = out.cpu().numpy()
         rk = ranks.cpu().numpy().reshape(-1, MAX_ORDER)
@@ -448,6 +468,9 @@ class SubrankPlan:
     def run_raw(self, ranks, ell, evals=None):
         _check(self.lib.tks_effective_subrank(self.handle, _ptr(self.workspace), _ptr(ranks), _ptr(ell),
                                               _ptr(evals) if evals is not None else None, _stream_handle()))
+
+    def set_fault_test(self, wait_cycles=0, stall=False):
+        _check(self.lib.tks_plan_set_fault_test(self.handle, int(wait_cycles), int(stall)))
 
     def sync(self):
         _check(self.lib.tks_subrank_sync_status(self.handle, _stream_handle()))

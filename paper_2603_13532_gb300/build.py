@@ -17,7 +17,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(HERE, "libtks.so")
 SOURCES = ["api.cu", "f64.cu", "tc_gemm.cu", "mixed.cu", "la32.cu", "proj3.cu", "sketch3.cu", "sketch4.cu", "ttm.cu",
-           "la64.cu", "subrank.cu", "subrank_api.cu"]
+           "la64.cu", "ozaki.cu", "subrank.cu", "subrank_api.cu"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",

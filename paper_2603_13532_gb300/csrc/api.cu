@@ -38,6 +38,7 @@ tks_status fail(tks_status st, const std::string& msg) {
   } while (0)
 
 constexpr size_t kAlign = 256;
+constexpr long long kDefaultWaitCycles = 4000000000LL;   // bound of a device-side wait: about 2 s at 2 GHz
 inline size_t align_up(size_t x, size_t a = kAlign) { return (x + a - 1) / a * a; }
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
@@ -48,7 +49,7 @@ Operand op_abs(const void* p, size_t off_bytes = 0) {
 
 enum StepKind { S_OMEGA, S_GEMM, S_REDUCE, S_CORESKETCH, S_QR, S_TSQR64, S_TC, S_SIMT, S_CS32, S_SPLIT,
                 S_TRANSPOSE, S_QR32, S_SVD32, S_TSQR, S_CS3, S_CHAIN3, S_QRSM, S_PROJ3, S_SK3, S_QRREG, S_TTM,
-                S_FOLD4, S_PROJ3F, S_SK3F, S_SK4, S_SVD64, S_TTM64 };
+                S_FOLD4, S_PROJ3F, S_SK3F, S_SK4, S_SVD64, S_TTM64, S_OZSLICE, S_OZGEMM };
 
 struct Step {
   StepKind kind;
@@ -92,6 +93,7 @@ struct ProbHost {
   size_t M[MAXD] = {}, V[MAXD] = {}, W[MAXD] = {}, tau[MAXD] = {}, A[MAXD] = {};
   size_t T = 0, P[MAXD] = {}, ev[MAXD] = {}, theta = 0, Hp[2] = {};
   size_t R64 = 0, stk64[2] = {};   // float64 ST-HOSVD: triangular factor and TSQR stacks
+  size_t ozA = 0, ozQ = 0, ozB = 0, ozEA = 0, ozEQ = 0, ozEB = 0;   // TKS_MIXED mode products: digit planes
   std::vector<size_t> chain;   // 2 ping-pong buffers per term
   // mixed-precision buffers (bytes): bf16 planes and float32 intermediates
   size_t om_plane[MAXD] = {}, UT[MAXD] = {}, M32[MAXD] = {}, Vp[MAXD][3] = {}, Qp[MAXD][3] = {};
@@ -171,6 +173,12 @@ struct tks_plan {
   int64_t grad_core_elems = 0, grad_factor_elems = 0;
   bool backward_ok = false;
   std::string build_error;   // set by a table builder that cannot plan a problem
+  size_t trunc_from = 0;     // first step of the ST-HOSVD truncation in st_recompress
+  // failure-path controls (tks_plan_set_fault_test): the bound of the tensor-core kernels' waits, and
+  // whether their copy-issuing thread first waits for a device word that nothing sets
+  long long wait_cycles = kDefaultWaitCycles;
+  int stall = 0;
+  const int* stall_word() const { return reinterpret_cast<const int*>(reinterpret_cast<const char*>(status) + 32); }
   double flops_low = 0.0, flops_f64 = 0.0;
 
   size_t add_table(const void* p, size_t bytes) {
@@ -1224,6 +1232,11 @@ static void build_hosvd_f64(tks_plan* plan) {
     std::vector<std::vector<TsqrJob>> tsqr;
     std::vector<SvdJob> svds;
     std::vector<TtmJob> ttm, fac;
+    std::vector<OzSliceJob> oz_slices;
+    std::vector<OzGemmJob> oz_gemms;
+    int oz_slice_total = 0, oz_gemm_total = 0;
+    // TKS_MIXED: the mode products run float64-accurate on the tensor cores (Ozaki scheme)
+    const bool emulate = plan->params.precision == TKS_MIXED;
     int ttm_tiles = 0, fac_tiles = 0;
     double qflops = 0.0, ttm_flops = 0.0, fac_flops = 0.0;
     for (int p = plan->lane_p0; p < plan->lane_p1; ++p) {
@@ -1337,6 +1350,54 @@ static void build_hosvd_f64(tks_plan* plan) {
       fac_tiles += fj.tiles;
       fac.push_back(fj);
       fac_flops += 2.0 * (double)h.n[n] * b * rmax;
+      if (emulate) {
+        // the same two products, float64-accurate on the tensor cores: digit planes of the fibres
+        // of H_(n), of the rows of Q_n and of the columns of P_n, then 128 x 64 tiles of Y
+        const int ldk = b <= 64 ? 64 : 128;
+        auto slice = [&](Operand src, size_t planes, size_t expo, int64_t rows, int64_t Ls) {
+          OzSliceJob sj2;
+          std::memset(&sj2, 0, sizeof(sj2));
+          sj2.src = src;
+          sj2.planes = op(B_WS, planes);
+          sj2.expo = op(B_WS, expo);
+          sj2.rows = rows;
+          sj2.L = Ls;
+          sj2.rows_pad = (rows + 7) / 8 * 8;
+          sj2.K = b;
+          sj2.ld = ldk;
+          sj2.tiles = oz_slice_tiles(rows);
+          sj2.tile_begin = oz_slice_total;
+          oz_slice_total += sj2.tiles;
+          oz_slices.push_back(sj2);
+          return sj2;
+        };
+        const OzSliceJob sx = slice(X, h.ozA, h.ozEA, L * Rr, L);
+        const OzSliceJob sp = slice(op(B_WS, h.P[n]), h.ozB, h.ozEB, rmax, 1);
+        const OzSliceJob sq = slice(op(B_Q, h.q_off[n] * 8), h.ozQ, h.ozEQ, (int64_t)h.n[n], (int64_t)h.n[n]);
+        auto gemm_job = [&](const OzSliceJob& a, Operand Yop, int64_t Ly) {
+          OzGemmJob g;
+          std::memset(&g, 0, sizeof(g));
+          g.M = (int)a.rows;
+          g.N = rmax;
+          g.K = b;
+          g.tiles_m = ceil_div(g.M, 128);
+          g.tiles_n = ceil_div(g.N, 64);
+          g.tile_begin = oz_gemm_total;
+          oz_gemm_total += g.tiles_m * g.tiles_n;
+          for (int sl = 0; sl < kOzSlices; ++sl) {
+            g.mapA[sl] = plan->map_of(B_WS, a.planes.off + (size_t)sl * a.rows_pad * ldk * 2, b, a.rows, ldk, 128);
+            g.mapB[sl] = plan->map_of(B_WS, sp.planes.off + (size_t)sl * sp.rows_pad * ldk * 2, b, rmax, ldk, 64);
+          }
+          g.expA = a.expo;
+          g.expB = sp.expo;
+          g.Y = Yop;
+          g.L = Ly;
+          g.rmax = rmax;
+          oz_gemms.push_back(g);
+        };
+        gemm_job(sx, tj.Y, L);
+        gemm_job(sq, fj.Y, (int64_t)h.n[n]);
+      }
     }
     char nm[32];
     for (size_t lvl = 0; lvl < tsqr.size(); ++lvl) {
@@ -1346,14 +1407,21 @@ static void build_hosvd_f64(tks_plan* plan) {
     }
     std::snprintf(nm, sizeof(nm), "a9:svd%d", n);
     plan->push(plan->st_recompress, S_SVD64, svds, (int64_t)svds.size(), nm);
-    int max_cols = 1;
-    for (const auto& t : ttm) max_cols = std::max(max_cols, t.rmax);
-    std::snprintf(nm, sizeof(nm), "a9:ttm%d", n);
-    plan->push(plan->st_recompress, S_TTM64, ttm, ttm_tiles, nm, ttm_flops, 0.0);
-    if (!ttm.empty()) plan->st_recompress.back().nb_max = max_cols;   // column groups of the kernel
-    std::snprintf(nm, sizeof(nm), "a9:factor%d", n);
-    plan->push(plan->st_recompress, S_TTM64, fac, fac_tiles, nm, fac_flops, 0.0);
-    if (!fac.empty()) plan->st_recompress.back().nb_max = max_cols;
+    if (emulate) {
+      std::snprintf(nm, sizeof(nm), "a9:slice%d[oz]", n);
+      plan->push(plan->st_recompress, S_OZSLICE, oz_slices, oz_slice_total, nm);
+      std::snprintf(nm, sizeof(nm), "a9:ttm+factor%d[oz]", n);
+      plan->push(plan->st_recompress, S_OZGEMM, oz_gemms, oz_gemm_total, nm, ttm_flops + fac_flops, 0.0);
+    } else {
+      int max_cols = 1;
+      for (const auto& t : ttm) max_cols = std::max(max_cols, t.rmax);
+      std::snprintf(nm, sizeof(nm), "a9:ttm%d", n);
+      plan->push(plan->st_recompress, S_TTM64, ttm, ttm_tiles, nm, ttm_flops, 0.0);
+      if (!ttm.empty()) plan->st_recompress.back().nb_max = max_cols;   // column groups of the kernel
+      std::snprintf(nm, sizeof(nm), "a9:factor%d", n);
+      plan->push(plan->st_recompress, S_TTM64, fac, fac_tiles, nm, fac_flops, 0.0);
+      if (!fac.empty()) plan->st_recompress.back().nb_max = max_cols;
+    }
   }
 }
 
@@ -1564,6 +1632,26 @@ tks_status tks_plan_create(tks_plan** out, const tks_problem* problems, int32_t 
       h.R64 = alloc((size_t)bm * bm * 8);
       h.stk64[0] = alloc((size_t)stack_rows * bm * 8);
       h.stk64[1] = alloc((size_t)stack_rows * bm * 8);
+      if (prm.precision == TKS_MIXED) {
+        // digit planes (kOzSlices bf16 planes, rows of 64 or 128 k) and row exponents of the mode
+        // products: the fibres of H_(n) (largest mode), the rows of Q_n, the columns of P_n
+        const int ldk = bm <= 64 ? 64 : 128;
+        int64_t fib = 0, nrow = 0, cols = 0;
+        for (int m = 0; m < d; ++m) {
+          int64_t L = 1, Rr = 1;
+          for (int j = 0; j < m; ++j) L *= h.rmax[j];
+          for (int j = m + 1; j < d; ++j) Rr *= h.b[j];
+          fib = std::max<int64_t>(fib, (L * Rr + 7) / 8 * 8);
+          nrow = std::max<int64_t>(nrow, (h.n[m] + 7) / 8 * 8);
+          cols = std::max<int64_t>(cols, (h.rmax[m] + 7) / 8 * 8);
+        }
+        h.ozA = alloc((size_t)kOzSlices * fib * ldk * 2);
+        h.ozQ = alloc((size_t)kOzSlices * nrow * ldk * 2);
+        h.ozB = alloc((size_t)kOzSlices * cols * ldk * 2);
+        h.ozEA = alloc((size_t)fib * 4);
+        h.ozEQ = alloc((size_t)nrow * 4);
+        h.ozEB = alloc((size_t)cols * 4);
+      }
     }
     if (f32la) {
       int64_t stack_rows = 0;
@@ -1727,6 +1815,7 @@ tks_status tks_plan_create(tks_plan** out, const tks_problem* problems, int32_t 
     build_backward3(plan);
   }
   }
+  plan->trunc_from = plan->st_recompress.size();
   if (f32la) build_hosvd_f32(plan);
   else build_hosvd_f64(plan);
 
@@ -1810,6 +1899,7 @@ tks_status tks_plan_create(tks_plan** out, const tks_problem* problems, int32_t 
     if (e == cudaSuccess) e = prepare_sketch4();
     if (e == cudaSuccess) e = prepare_qr_reg_f32();
     if (e == cudaSuccess) e = prepare_ttm_rows();
+    if (e == cudaSuccess) e = prepare_oz_gemm();
     if (e != cudaSuccess) {
       tks_plan_destroy(plan);
       return fail(TKS_ECUDA, std::string("tensor-core GEMM shared memory: ") + cudaGetErrorString(e));
@@ -1924,12 +2014,20 @@ tks_status run_steps(tks_plan* plan, const std::vector<Step>& steps, const Bases
       case S_SVD64:
         launch_svd_f64(static_cast<const SvdJob*>(table), s.njobs, plan->bmax, bases, plan->status, stream);
         break;
+      case S_OZSLICE:
+        launch_oz_slice(static_cast<const OzSliceJob*>(table), s.njobs, (int)s.work, bases, stream);
+        break;
+      case S_OZGEMM:
+        launch_oz_gemm(static_cast<const OzGemmJob*>(table), s.njobs, (int)s.work, plan->arena_dev + plan->maps_off,
+                       bases, plan->status, plan->wait_cycles, stream);
+        break;
       case S_TTM64:
         launch_ttm_f64(static_cast<const TtmJob*>(table), s.njobs, (int)s.work, s.nb_max, plan->bmax, bases, stream);
         break;
       case S_TC:
         launch_tc_gemm(static_cast<const TcJob*>(table), s.njobs, (int)s.work, plan->arena_dev + plan->maps_off,
-                       s.na_max, s.nb_max, bases, plan->status, stream);
+                       s.na_max, s.nb_max, bases, plan->status, plan->wait_cycles,
+                       plan->stall ? plan->stall_word() : nullptr, stream);
         break;
       case S_SIMT:
         launch_simt_gemm_f32(static_cast<const SimtJob*>(table), s.njobs, (int)s.work, bases, stream);
@@ -2119,6 +2217,26 @@ tks_status tucker_sum_recompress(tks_plan* plan, void* workspace, double* out, i
   return TKS_OK;
 }
 
+tks_status tks_truncate_core(tks_plan* plan, void* workspace, const double* Q_in, const double* H_in, double* out,
+                             int32_t* ranks_out, void* stream) {
+  tks_status st = check_ws(plan, workspace);
+  if (st != TKS_OK) return st;
+  if (!Q_in || !H_in || !out || !ranks_out) return fail(TKS_EINVAL, "null Q_in, H_in, out or ranks_out");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  st = ensure_maps(plan, workspace, s);
+  if (st != TKS_OK) return st;
+  TKS_CUDA_CHECK(cudaMemsetAsync(ranks_out, 0, (size_t)plan->nprob * TKS_MAX_ORDER * sizeof(int32_t), s));
+  TKS_CUDA_CHECK(cudaMemsetAsync(out, 0, (size_t)plan->output_elems * sizeof(double), s));
+  Bases b = bind(plan, workspace);
+  b.p[B_Q] = reinterpret_cast<char*>(const_cast<double*>(Q_in));
+  b.p[B_H] = reinterpret_cast<char*>(const_cast<double*>(H_in));
+  b.p[B_OUT] = reinterpret_cast<char*>(out);
+  b.p[B_RANKS] = reinterpret_cast<char*>(ranks_out);
+  const std::vector<Step> steps(plan->st_recompress.begin() + (std::ptrdiff_t)plan->trunc_from,
+                                plan->st_recompress.end());
+  return run_steps(plan, steps, b, s);
+}
+
 tks_status tks_profile_begin(tks_plan* plan, int32_t max_calls) {
   if (!plan || max_calls < 1) return fail(TKS_EINVAL, "bad plan or max_calls");
   plan->profile_clear();
@@ -2183,6 +2301,14 @@ tks_status tks_project_core_backward(tks_plan* plan, void* workspace, const doub
   b.p[B_DCORE] = reinterpret_cast<char*>(dcores);
   b.p[B_DFAC] = reinterpret_cast<char*>(dfactors);
   return run_steps(plan, plan->st_backward, b, static_cast<cudaStream_t>(stream));
+}
+
+tks_status tks_plan_set_fault_test(tks_plan* plan, int64_t wait_cycles, int32_t stall) {
+  if (!plan) return fail(TKS_EINVAL, "null plan");
+  if (wait_cycles < 0 || (stall != 0 && stall != 1)) return fail(TKS_EINVAL, "wait_cycles < 0 or stall not 0/1");
+  plan->wait_cycles = wait_cycles > 0 ? (long long)wait_cycles : kDefaultWaitCycles;
+  plan->stall = stall;
+  return TKS_OK;
 }
 
 tks_status tks_sync_status(tks_plan* plan, void* stream) {

@@ -36,8 +36,11 @@ void launch_ttm_f64(const TtmJob* jobs, int njobs, int total_tiles, int max_cols
 size_t tc_gemm_smem_bytes(int stages, int na_max, int nb_max, int bn);
 int tc_gemm_stages(int na_max, int nb_max, int bn);
 cudaError_t prepare_tc_gemm();
+// wait_cycles bounds every mbarrier wait; stall_word (tests of the timeout path) is a device word that
+// nothing sets, waited for by the copy-issuing thread before its first copy, or NULL.
 void launch_tc_gemm(const TcJob* jobs, int njobs, int total_tiles, const void* maps, int na_max, int nb_max,
-                    const Bases& bases, Status* status, cudaStream_t stream);
+                    const Bases& bases, Status* status, long long wait_cycles, const int* stall_word,
+                    cudaStream_t stream);
 
 // Float32 CUDA-core kernels of the mixed path.
 void launch_simt_gemm_f32(const SimtJob* jobs, int njobs, int total_tiles, const Bases& bases,
@@ -103,6 +106,14 @@ void launch_tsqr_f32(const TsqrJob* jobs, int njobs, int max_rows, int max_cols,
                      cudaStream_t stream);
 void launch_svd_f32(const SvdJob* jobs, int njobs, int bmax, const Bases& bases, Status* status,
                     cudaStream_t stream);
+
+// Float64-accurate mode products on the tensor cores (Ozaki scheme): digit planes of the rows of X
+// and of P^T (32 rows per CTA), then one 128 x 64 tile of Y per CTA.
+int oz_slice_tiles(int64_t rows);
+void launch_oz_slice(const OzSliceJob* jobs, int njobs, int total_tiles, const Bases& bases, cudaStream_t stream);
+cudaError_t prepare_oz_gemm();
+void launch_oz_gemm(const OzGemmJob* jobs, int njobs, int total_tiles, const void* maps, const Bases& bases,
+                    Status* status, long long wait_cycles, cudaStream_t stream);
 
 // Effective subrank heuristic (Alg. 5): term weights, weighted Gram tiles, tridiagonalization
 // (one CTA per matrix) and eigenvalues + rank rule (one CTA per matrix).

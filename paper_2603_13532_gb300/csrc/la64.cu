@@ -771,7 +771,7 @@ size_t ttm64_smem(int bmax) {
 }  // namespace
 
 // At least twice the columns, so that every TSQR level shrinks the stack of factors.
-int tsqr64_block_rows(int max_cols) { return max_cols <= 72 ? 256 : 192; }
+int tsqr64_block_rows(int max_cols) { return max_cols <= 64 ? 256 : 192; }
 
 cudaError_t prepare_la64(int bmax) {
   cudaError_t e = cudaFuncSetAttribute(svd_jacobi_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -788,11 +788,11 @@ cudaError_t prepare_la64(int bmax) {
     if (e != cudaSuccess) return e;
   }
   const void* kernels[] = {reinterpret_cast<const void*>(tsqr_f64_kernel<8, 2, 16>),
-                           reinterpret_cast<const void*>(tsqr_f64_kernel<8, 2, 24>),
-                           reinterpret_cast<const void*>(tsqr_f64_kernel<8, 3, 24>),
-                           reinterpret_cast<const void*>(tsqr_f64_kernel<6, 4, 24>)};
-  // the largest staging tile of any instantiation: 256 x 72 or 192 x 96
-  const size_t tile = std::max(tsqr64_smem(256, 72), tsqr64_smem(192, 96));
+                           reinterpret_cast<const void*>(tsqr_f64_kernel<8, 3, 16>),
+                           reinterpret_cast<const void*>(tsqr_f64_kernel<8, 4, 16>),
+                           reinterpret_cast<const void*>(tsqr_f64_kernel<6, 6, 16>)};
+  // the largest staging tile of any instantiation: 256 x 64 or 192 x 96
+  const size_t tile = std::max(tsqr64_smem(256, 64), tsqr64_smem(192, 96));
   for (const void* k : kernels) {
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile);
     if (e != cudaSuccess) return e;
@@ -801,16 +801,17 @@ cudaError_t prepare_la64(int bmax) {
 }
 
 void launch_tsqr_f64(const TsqrJob* jobs, int njobs, int max_cols, const Bases& bases, cudaStream_t stream) {
-  // the smallest instantiation that covers max_cols: 24 warps (768 threads) hold up to 72 columns
-  // of a 256-row block (24 doubles per thread), 96 columns of a 192-row block
+  // the smallest instantiation that covers max_cols: 16 warps hold up to 64 columns of a 256-row
+  // block (32 doubles per thread), 96 columns of a 192-row block (36); 768-thread variants with fewer
+  // columns per warp were measured slower (more instructions per column step)
   if (max_cols <= 32) {
     tsqr_f64_kernel<8, 2, 16><<<njobs, 512, tsqr64_smem(256, 32), stream>>>(jobs, bases);
   } else if (max_cols <= 48) {
-    tsqr_f64_kernel<8, 2, 24><<<njobs, 768, tsqr64_smem(256, 48), stream>>>(jobs, bases);
-  } else if (max_cols <= 72) {
-    tsqr_f64_kernel<8, 3, 24><<<njobs, 768, tsqr64_smem(256, 72), stream>>>(jobs, bases);
+    tsqr_f64_kernel<8, 3, 16><<<njobs, 512, tsqr64_smem(256, 48), stream>>>(jobs, bases);
+  } else if (max_cols <= 64) {
+    tsqr_f64_kernel<8, 4, 16><<<njobs, 512, tsqr64_smem(256, 64), stream>>>(jobs, bases);
   } else {
-    tsqr_f64_kernel<6, 4, 24><<<njobs, 768, tsqr64_smem(192, 96), stream>>>(jobs, bases);
+    tsqr_f64_kernel<6, 6, 16><<<njobs, 512, tsqr64_smem(192, 96), stream>>>(jobs, bases);
   }
 }
 

@@ -22,7 +22,6 @@ namespace {
 constexpr int kBM = 128;
 constexpr int kBK = 64;                       // bf16 elements = 128 bytes = one swizzle row
 constexpr int kATile = kBM * kBK * 2;         // 16 KB
-constexpr long long kWaitCycles = 4000000000LL;   // about 2 s at 2 GHz
 // Partial accumulators in TMEM: k-block kb goes to accumulator kb % kAcc and the epilogue adds
 // them, so each float32 accumulator takes 1/kAcc of the K-steps (the rounding error of a long
 // contraction whose products share a sign grows with the number of steps).
@@ -42,7 +41,8 @@ __device__ __forceinline__ float bf16_float(uint16_t h) {
 template <int BN>
 __global__ void __launch_bounds__(192, 1)
     tc_gemm_kernel(const TcJob* __restrict__ jobs, int njobs, const CUtensorMap* __restrict__ maps, Bases bases,
-                   Status* status, int stages, int na_max, int nb_max) {
+                   Status* status, int stages, int na_max, int nb_max, long long kWaitCycles,
+                   const volatile int* stall_word) {
   constexpr int kBTile = BN * kBK * 2;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -91,6 +91,18 @@ __global__ void __launch_bounds__(192, 1)
       for (int j = 0; j < J.nb; ++j) tc::prefetch_tmap(&maps[J.mapB[j]]);
       int issued = 0;
       const uint32_t bytes = (uint32_t)(J.na * kATile + J.nb * kBTile);
+      if (stall_word) {
+        // failure-path test: wait for a word that nothing sets, so that this wait and the MMA
+        // thread's run out and the kernel takes its timeout exit
+        const long long t0 = clock64();
+        while (*stall_word == 0) {
+          if (clock64() - t0 > kWaitCycles) {
+            *err = 1;
+            break;
+          }
+          __nanosleep(256);
+        }
+      }
       for (int kb = 0; kb < nk; ++kb) {
         const int s = kb % stages, round = kb / stages;
         if (*err || !tc::mbar_wait(&empty[s], (round & 1) ^ 1, kWaitCycles)) {
@@ -212,11 +224,12 @@ cudaError_t prepare_tc_gemm() {
 }
 
 void launch_tc_gemm(const TcJob* jobs, int njobs, int total_tiles, const void* maps, int na_max, int nb_max,
-                    const Bases& bases, Status* status, cudaStream_t stream) {
+                    const Bases& bases, Status* status, long long wait_cycles, const int* stall_word,
+                    cudaStream_t stream) {
   const int stages = tc_gemm_stages(na_max, nb_max, 64);
   const size_t smem = tc_gemm_smem_bytes(stages, na_max, nb_max, 64);
   tc_gemm_kernel<64><<<total_tiles, 192, smem, stream>>>(jobs, njobs, static_cast<const CUtensorMap*>(maps), bases,
-                                                         status, stages, na_max, nb_max);
+                                                         status, stages, na_max, nb_max, wait_cycles, stall_word);
 }
 
 }  // namespace tks

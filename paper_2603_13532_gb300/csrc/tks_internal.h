@@ -328,6 +328,38 @@ struct SvdJob {
   double tol;
 };
 
+// Float64-accurate mode product on the tensor cores (the ST-HOSVD truncation of TKS_MIXED):
+//   Y[l + L (c + rmax r)] = sum_a X[l + L (a + K r)] P[a + K c]
+// by exact integer slices (the Ozaki scheme).  Each row of X (fibre q = l + L r) and of P^T (column c)
+// is scaled by a power of two 2^e with |x| < 2^e over the row and cut into kOzSlices signed 7-bit
+// digits, x = 2^e sum_s d_s 2^(-7 s) up to 2^(e - 56); the digits are bfloat16 integers, their
+// products exact, and every sum over K <= TKS_MAX_BASIS of them an integer below 2^21, so the
+// tensor cores accumulate each level s + t of digit pairs exactly in float32.
+constexpr int kOzSlices = 8;     // 56 bits of every row
+constexpr int kOzLevels = 8;     // digit pairs with s + t <= 9 (1-based): levels 2..9
+
+// Cuts the rows of a float64 matrix into digit planes: row q (q < rows) holds element a (a < K) at
+// src[l + L a + L K r] with q = l + L r; plane s of row q goes to planes at element
+// (s * rows_pad + q) * ld + a, and the row's exponent e to expo[q].
+struct OzSliceJob {
+  Operand src, planes, expo;
+  int64_t rows, L, rows_pad;
+  int32_t K, ld;
+  int32_t tile_begin, tiles;
+};
+
+// One 128 x 64 output tile per CTA: A = digit planes of the X rows (TMA maps mapA[s]), B = digit
+// planes of the P columns (mapB[s]); the kOzLevels accumulators live in TMEM.
+struct OzGemmJob {
+  int32_t M, N, K;
+  int32_t tiles_m, tiles_n, tile_begin;
+  int32_t mapA[kOzSlices], mapB[kOzSlices];
+  Operand expA, expB;    // int32 row exponents of X and of P^T
+  Operand Y;             // float64: element (q, c) at Y[l + L (c + rmax r)], q = l + L r
+  int64_t L;
+  int32_t rmax, pad;
+};
+
 // Effective subrank heuristic (Alg. 5), float64 throughout.
 //
 // Term weight w_k = |alpha_k| ||G_k||_F, written as the weight of each of the term's columns of
