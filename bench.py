@@ -69,7 +69,8 @@ def parse_args():
     ap.add_argument("--measure-peaks", action="store_true", help="print FP64/FP32/TF32/BF16 GEMM rates")
     ap.add_argument("--lanes", type=int, default=None,
                     help="groups of problems whose recompressions run on concurrent streams (tks_params.lanes); "
-                         "default 2 for decay512 and batched, 1 for order4 (measured: +4% and -20%)")
+                         "default: 2 for mixed_f32la on decay512 and batched, else 1 (with the float64 "
+                         "ST-HOSVD every stage is throughput-bound and extra lanes measured slower)")
     ap.add_argument("--no-subrank", action="store_true", help="skip the effective subrank (Alg. 5) leg")
     ap.add_argument("--no-f32la", action="store_true", help="skip the float32-linear-algebra comparison leg")
     ap.add_argument("--oracle-problems", type=int, default=2,
@@ -386,7 +387,7 @@ def extra_workload_leg(args, workload, device, stream, rank, world):
     from paper_2603_13532_gb300 import binding
     P = EXTRA_PROBLEMS[workload]
     kind = workload_kind(workload)
-    lanes = 1 if workload.startswith("order4") else 2
+    lanes = 2 if (args.precision == "mixed_f32la" and not workload.startswith("order4")) else 1
     problems = make_problems(P, args.seed, rank, True, workload)
     plan = binding.Plan(problems, kind=kind, precision=args.precision, seed=args.seed, device=device, lanes=lanes)
     out = torch.zeros(plan.info.output_elems, dtype=torch.float64, device=device)
@@ -421,7 +422,7 @@ def extra_workload_leg(args, workload, device, stream, rank, world):
 
 FP32_PEAK_TFLOPS = 152 * 256 * 2.070e9 / 1e12   # 128 FP32 FMA per SM per clock
 FP64_KINDS = {"gemm", "reduce", "qr", "core_sketch", "tsqr64", "svd64", "ttm64"}
-TENSOR_FP64_KINDS = {"oz_gemm"}
+TENSOR_FP64_KINDS = {"oz_gemm", "oz_gram"}
 FP32_KINDS = {"simt", "core_sketch32", "qr32", "svd32", "tsqr32", "core_sketch3", "chain3", "qr_smem32",
               "project3", "sketch3", "qr_reg32", "ttm32", "fold4", "project4", "sketch3f", "sketch4"}
 
@@ -550,7 +551,7 @@ def main():
     if args.workload == "exact_recovery" and args.precision != "fp64":
         raise SystemExit("the exact_recovery workload is float64 only")
     if args.lanes is None:
-        args.lanes = 1 if args.workload.startswith("order4") else 2
+        args.lanes = 2 if (args.precision == "mixed_f32la" and not args.workload.startswith("order4")) else 1
     problems = make_problems(P, args.seed, rank, bf16, args.workload)
     plan = binding.Plan(problems, kind=kind, precision=args.precision, seed=args.seed, device=device,
                         lanes=args.lanes)
@@ -722,7 +723,7 @@ def main():
     f32la = None
     if args.precision == "mixed" and not args.no_f32la:
         plan32 = binding.Plan(problems, kind=kind, precision="mixed_f32la", seed=args.seed, device=device,
-                              lanes=args.lanes)
+                              lanes=1 if args.workload.startswith("order4") else 2)
         out32 = torch.zeros(plan32.info.output_elems, dtype=torch.float64, device=device)
         r32 = torch.zeros_like(ranks_t)
         timed32, graph32 = graph_step(plan32, out32, r32, stream, use_graph=not args.no_graph)

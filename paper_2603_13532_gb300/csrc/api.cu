@@ -49,7 +49,7 @@ Operand op_abs(const void* p, size_t off_bytes = 0) {
 
 enum StepKind { S_OMEGA, S_GEMM, S_REDUCE, S_CORESKETCH, S_QR, S_TSQR64, S_TC, S_SIMT, S_CS32, S_SPLIT,
                 S_TRANSPOSE, S_QR32, S_SVD32, S_TSQR, S_CS3, S_CHAIN3, S_QRSM, S_PROJ3, S_SK3, S_QRREG, S_TTM,
-                S_FOLD4, S_PROJ3F, S_SK3F, S_SK4, S_SVD64, S_TTM64, S_OZSLICE, S_OZGEMM };
+                S_FOLD4, S_PROJ3F, S_SK3F, S_SK4, S_SVD64, S_TTM64, S_OZSLICE, S_OZGEMM, S_OZCOLS, S_OZGRAM, S_CHOL };
 
 struct Step {
   StepKind kind;
@@ -94,6 +94,7 @@ struct ProbHost {
   size_t T = 0, P[MAXD] = {}, ev[MAXD] = {}, theta = 0, Hp[2] = {};
   size_t R64 = 0, stk64[2] = {};   // float64 ST-HOSVD: triangular factor and TSQR stacks
   size_t ozA = 0, ozQ = 0, ozB = 0, ozEA = 0, ozEQ = 0, ozEB = 0;   // TKS_MIXED mode products: digit planes
+  size_t cqX[2] = {}, cqCol = 0, cqColE = 0, cqG = 0, cqRinv = 0, cqRacc = 0, cqFlag = 0;   // CholeskyQR3
   std::vector<size_t> chain;   // 2 ping-pong buffers per term
   // mixed-precision buffers (bytes): bf16 planes and float32 intermediates
   size_t om_plane[MAXD] = {}, UT[MAXD] = {}, M32[MAXD] = {}, Vp[MAXD][3] = {}, Qp[MAXD][3] = {};
@@ -1239,6 +1240,16 @@ static void build_hosvd_f64(tks_plan* plan) {
     const bool emulate = plan->params.precision == TKS_MIXED;
     int ttm_tiles = 0, fac_tiles = 0;
     double qflops = 0.0, ttm_flops = 0.0, fac_flops = 0.0;
+    // TKS_MIXED with b <= 64: the triangular factor by shifted CholeskyQR3 with float64-accurate Gram
+    // matrices and products on the tensor cores; three passes of [column digits, Gram, Cholesky step,
+    // row digits of X and R^-1, X <- X R^-1] (the last pass stops after its Cholesky step)
+    std::vector<OzColSliceJob> cq_cols[3];
+    std::vector<OzGramJob> cq_gram[3];
+    std::vector<CholJob> cq_chol[3];
+    std::vector<OzSliceJob> cq_slice[2];
+    std::vector<OzGemmJob> cq_gemm[2];
+    int cq_cols_total[3] = {0, 0, 0}, cq_slice_total[2] = {0, 0}, cq_gemm_total[2] = {0, 0};
+    double cq_gram_flops = 0.0, cq_gemm_flops = 0.0;
     for (int p = plan->lane_p0; p < plan->lane_p1; ++p) {
       auto& h = plan->probs[p];
       const int d = h.d;
@@ -1248,6 +1259,91 @@ static void build_hosvd_f64(tks_plan* plan) {
       for (int j = n + 1; j < d; ++j) Rr *= h.b[j];
       const int b = h.b[n], rmax = h.rmax[n];
       const Operand X = (n == 0) ? op(B_H, h.h_off * 8) : op(B_WS, h.Hp[(n - 1) & 1]);
+      const bool cholqr = emulate && b <= 64;
+      Operand gate{B_NONE, 0, 0};
+      if (cholqr) {
+        const int64_t P = L * Rr;
+        const int64_t ldP = (P + 7) / 8 * 8;
+        const int ldk = 64;
+        gate = op(B_WS, h.cqFlag);
+        const Operand src[3] = {X, op(B_WS, h.cqX[0]), op(B_WS, h.cqX[1])};
+        for (int pass = 0; pass < 3; ++pass) {
+          OzColSliceJob cj;
+          std::memset(&cj, 0, sizeof(cj));
+          cj.src = src[pass];
+          cj.planes = op(B_WS, h.cqCol);
+          cj.expo = op(B_WS, h.cqColE);
+          cj.P = P;
+          cj.L = L;
+          cj.ldP = ldP;
+          cj.b = b;
+          cj.tile_begin = cq_cols_total[pass];
+          cq_cols_total[pass] += b;
+          cq_cols[pass].push_back(cj);
+          OzGramJob gj;
+          std::memset(&gj, 0, sizeof(gj));
+          for (int sl = 0; sl < kOzSlices; ++sl)
+            gj.map[sl] = plan->map_of(B_WS, h.cqCol + (size_t)sl * 64 * ldP * 2, P, b, ldP, 64);
+          gj.expo = cj.expo;
+          gj.G = op(B_WS, h.cqG);
+          gj.P = P;
+          gj.b = b;
+          cq_gram[pass].push_back(gj);
+          cq_gram_flops += 2.0 * (double)P * b * b;
+          CholJob ch;
+          std::memset(&ch, 0, sizeof(ch));
+          ch.G = gj.G;
+          ch.Rinv = op(B_WS, h.cqRinv);
+          ch.Racc = op(B_WS, h.cqRacc);
+          ch.Rout = op(B_WS, h.R64);
+          ch.fallback = gate;
+          ch.P = P;
+          ch.b = b;
+          ch.pass = pass + 1;
+          cq_chol[pass].push_back(ch);
+          if (pass == 2) break;
+          // X_next = X Rinv: digits of the rows of X and of the columns of Rinv, then 128 x 64 tiles
+          auto slice = [&](Operand s_src, size_t planes, size_t expo, int64_t rows, int64_t Ls) {
+            OzSliceJob sj2;
+            std::memset(&sj2, 0, sizeof(sj2));
+            sj2.src = s_src;
+            sj2.planes = op(B_WS, planes);
+            sj2.expo = op(B_WS, expo);
+            sj2.rows = rows;
+            sj2.L = Ls;
+            sj2.rows_pad = (rows + 7) / 8 * 8;
+            sj2.K = b;
+            sj2.ld = ldk;
+            sj2.tiles = oz_slice_tiles(rows);
+            sj2.tile_begin = cq_slice_total[pass];
+            cq_slice_total[pass] += sj2.tiles;
+            cq_slice[pass].push_back(sj2);
+            return sj2;
+          };
+          const OzSliceJob sx = slice(src[pass], h.ozA, h.ozEA, P, L);
+          const OzSliceJob sr = slice(ch.Rinv, h.ozB, h.ozEB, b, 1);
+          OzGemmJob g;
+          std::memset(&g, 0, sizeof(g));
+          g.M = (int)P;
+          g.N = b;
+          g.K = b;
+          g.tiles_m = ceil_div(g.M, 128);
+          g.tiles_n = 1;
+          g.tile_begin = cq_gemm_total[pass];
+          cq_gemm_total[pass] += g.tiles_m;
+          for (int sl = 0; sl < kOzSlices; ++sl) {
+            g.mapA[sl] = plan->map_of(B_WS, sx.planes.off + (size_t)sl * sx.rows_pad * ldk * 2, b, P, ldk, 128);
+            g.mapB[sl] = plan->map_of(B_WS, sr.planes.off + (size_t)sl * sr.rows_pad * ldk * 2, b, b, ldk, 64);
+          }
+          g.expA = sx.expo;
+          g.expB = sr.expo;
+          g.Y = src[pass + 1];
+          g.L = L;
+          g.rmax = b;
+          cq_gemm[pass].push_back(g);
+          cq_gemm_flops += 2.0 * (double)P * b * b;
+        }
+      }
       // TSQR of H_(n)^T: element (l + L rr, c) at l + L c + L b rr.  Level 0 factors blocks of dense
       // rows; every later level factors groups of the previous level's b x b triangular factors,
       // each group read with its factors' rows interleaved (row f + k r of a group of k is row r of
@@ -1276,6 +1372,7 @@ static void build_hosvd_f64(tks_plan* plan) {
           for (int i = 0; i < nblk; ++i) {
             TsqrJob t;
             std::memset(&t, 0, sizeof(t));
+            t.gate = gate;
             t.src_type = T_F64;
             t.cols = b;
             t.dst = dst;
@@ -1400,10 +1497,28 @@ static void build_hosvd_f64(tks_plan* plan) {
       }
     }
     char nm[32];
+    for (int pass = 0; pass < 3; ++pass) {
+      if (cq_gram[pass].empty()) break;
+      std::snprintf(nm, sizeof(nm), "a9:cq%d.cols%d[oz]", n, pass + 1);
+      plan->push(plan->st_recompress, S_OZCOLS, cq_cols[pass], cq_cols_total[pass], nm);
+      std::snprintf(nm, sizeof(nm), "a9:cq%d.gram%d[oz]", n, pass + 1);
+      plan->push(plan->st_recompress, S_OZGRAM, cq_gram[pass], (int64_t)cq_gram[pass].size(), nm,
+                 cq_gram_flops / 3.0, 0.0);
+      std::snprintf(nm, sizeof(nm), "a9:cq%d.chol%d", n, pass + 1);
+      plan->push(plan->st_recompress, S_CHOL, cq_chol[pass], (int64_t)cq_chol[pass].size(), nm);
+      if (pass == 2) break;
+      std::snprintf(nm, sizeof(nm), "a9:cq%d.slice%d[oz]", n, pass + 1);
+      plan->push(plan->st_recompress, S_OZSLICE, cq_slice[pass], cq_slice_total[pass], nm);
+      std::snprintf(nm, sizeof(nm), "a9:cq%d.XRinv%d[oz]", n, pass + 1);
+      plan->push(plan->st_recompress, S_OZGEMM, cq_gemm[pass], cq_gemm_total[pass], nm, cq_gemm_flops / 2.0, 0.0);
+    }
+    // the Householder TSQR: every problem on the TKS_FP64 path and those with b > 64; on the
+    // CholeskyQR3 path it is gated per problem and runs only where a Cholesky step broke down
+    const bool any_tsqr_work = !cq_gram[0].empty() ? false : true;
     for (size_t lvl = 0; lvl < tsqr.size(); ++lvl) {
       std::snprintf(nm, sizeof(nm), "a9:tsqr%d.%d", n, (int)lvl);
-      plan->push(plan->st_recompress, S_TSQR64, tsqr[lvl], (int64_t)tsqr[lvl].size(), nm, lvl == 0 ? qflops : 0.0,
-                 0.0);
+      plan->push(plan->st_recompress, S_TSQR64, tsqr[lvl], (int64_t)tsqr[lvl].size(), nm,
+                 lvl == 0 && any_tsqr_work ? qflops : 0.0, 0.0);
     }
     std::snprintf(nm, sizeof(nm), "a9:svd%d", n);
     plan->push(plan->st_recompress, S_SVD64, svds, (int64_t)svds.size(), nm);
@@ -1645,12 +1760,27 @@ tks_status tks_plan_create(tks_plan** out, const tks_problem* problems, int32_t 
           nrow = std::max<int64_t>(nrow, (h.n[m] + 7) / 8 * 8);
           cols = std::max<int64_t>(cols, (h.rmax[m] + 7) / 8 * 8);
         }
+        // with CholeskyQR3 (b <= 64) the b columns of R^-1 also go through the P digit planes
+        if (bm <= 64) cols = std::max<int64_t>(cols, (bm + 7) / 8 * 8);
         h.ozA = alloc((size_t)kOzSlices * fib * ldk * 2);
         h.ozQ = alloc((size_t)kOzSlices * nrow * ldk * 2);
         h.ozB = alloc((size_t)kOzSlices * cols * ldk * 2);
         h.ozEA = alloc((size_t)fib * 4);
         h.ozEQ = alloc((size_t)nrow * 4);
         h.ozEB = alloc((size_t)cols * 4);
+        // shifted CholeskyQR3 (b <= 64): two X buffers, column digit planes (64 rows of ldP), the Gram
+        // matrix, R^-1, the accumulated R, the fallback flag
+        if (bm <= 64) {
+          const int64_t ldP = fib;   // fib is a multiple of 8 and at least every mode's row count
+          h.cqX[0] = alloc((size_t)fib * bm * 8);
+          h.cqX[1] = alloc((size_t)fib * bm * 8);
+          h.cqCol = alloc((size_t)kOzSlices * 64 * ldP * 2);
+          h.cqColE = alloc(64 * 4);
+          h.cqG = alloc(64 * 64 * 8);
+          h.cqRinv = alloc(64 * 64 * 8);
+          h.cqRacc = alloc(64 * 64 * 8);
+          h.cqFlag = alloc(4);
+        }
       }
     }
     if (f32la) {
@@ -2020,6 +2150,16 @@ tks_status run_steps(tks_plan* plan, const std::vector<Step>& steps, const Bases
       case S_OZGEMM:
         launch_oz_gemm(static_cast<const OzGemmJob*>(table), s.njobs, (int)s.work, plan->arena_dev + plan->maps_off,
                        bases, plan->status, plan->wait_cycles, stream);
+        break;
+      case S_OZCOLS:
+        launch_oz_colslice(static_cast<const OzColSliceJob*>(table), s.njobs, (int)s.work, bases, stream);
+        break;
+      case S_OZGRAM:
+        launch_oz_gram(static_cast<const OzGramJob*>(table), s.njobs, plan->arena_dev + plan->maps_off, bases,
+                       plan->status, plan->wait_cycles, stream);
+        break;
+      case S_CHOL:
+        launch_chol_step(static_cast<const CholJob*>(table), s.njobs, bases, plan->status, stream);
         break;
       case S_TTM64:
         launch_ttm_f64(static_cast<const TtmJob*>(table), s.njobs, (int)s.work, s.nb_max, plan->bmax, bases, stream);

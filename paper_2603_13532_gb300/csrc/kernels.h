@@ -114,6 +114,13 @@ void launch_oz_slice(const OzSliceJob* jobs, int njobs, int total_tiles, const B
 cudaError_t prepare_oz_gemm();
 void launch_oz_gemm(const OzGemmJob* jobs, int njobs, int total_tiles, const void* maps, const Bases& bases,
                     Status* status, long long wait_cycles, cudaStream_t stream);
+// Shifted CholeskyQR3 with float64-accurate Gram matrices: column digit planes (one CTA per column),
+// G = X^T X (one CTA per job), and the small Cholesky steps (one CTA per job).
+void launch_oz_colslice(const OzColSliceJob* jobs, int njobs, int total_cols, const Bases& bases,
+                        cudaStream_t stream);
+void launch_oz_gram(const OzGramJob* jobs, int njobs, const void* maps, const Bases& bases, Status* status,
+                    long long wait_cycles, cudaStream_t stream);
+void launch_chol_step(const CholJob* jobs, int njobs, const Bases& bases, Status* status, cudaStream_t stream);
 
 // Effective subrank heuristic (Alg. 5): term weights, weighted Gram tiles, tridiagonalization
 // (one CTA per matrix) and eigenvalues + rank rule (one CTA per matrix).

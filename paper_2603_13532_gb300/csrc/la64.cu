@@ -196,6 +196,8 @@ __global__ void __launch_bounds__(32 * kWarps, 1) tsqr_f64_kernel(const TsqrJob*
   __shared__ double rdiag[kWarps * kSlots];
   __shared__ int64_t rowoff[kBlockRows];
   const TsqrJob& J = jobs[blockIdx.x];
+  // a gated block (the Householder fallback of CholeskyQR3) runs only when its job asked for it
+  if (J.gate.base != B_NONE && *at<const int32_t>(bases, J.gate) == 0) return;
   const int m = J.rows, b = J.cols;
   const int ld = m + 1;
   double* A = smem_t64;
@@ -768,12 +770,124 @@ size_t ttm64_smem(int bmax) {
   return (size_t)bp * cols * sizeof(double) + (size_t)bp * kTtmXs * sizeof(double);
 }
 
+// ----------------------------------------------------------------------------- CholeskyQR3 steps
+// One pass of shifted CholeskyQR3 (Fukaya, Kannan, Nakatsukasa, Yamamoto and Yanagisawa 2020) for
+// the triangular factor of X = H_(n)^T (P x b, b <= 64), one CTA per job, in float64:
+//   pass 1: R1 = chol(G + s I), s = 11 (P b + b (b + 1)) u ||X||_F^2 (||X||_F^2 = trace G): the shift
+//           keeps the factorization defined for any conditioning and leaves X R1^-1 with a condition
+//           number near u^-1/2;
+//   pass 2, 3: R = chol(G) of the re-formed X R^-1 (CholeskyQR2), which restores orthogonality to
+//           rounding;  R = R3 R2 R1 is then a backward-stable triangular factor of X.
+// Every pass writes Rinv = R^-1 (upper, column-major) for the next X <- X Rinv and accumulates
+// Racc <- R Racc; the last writes Racc to Rout.  A pivot that is not positive (pass 1) or below 1e-12
+// of its diagonal entry (passes 2, 3: X R^-1 is too ill-conditioned for CholeskyQR2, e.g. a rank-
+// deficient unfolding) sets *fallback, and the Householder TSQR factors X instead; later passes of a
+// failed job only write an identity Rinv.
+constexpr int kCholThreads = 256;
+
+__global__ void __launch_bounds__(kCholThreads) chol_step_kernel(const CholJob* __restrict__ jobs, Bases bases,
+                                                                Status* status) {
+  extern __shared__ double cs64[];
+  const CholJob& J = jobs[blockIdx.x];
+  const int b = J.b, ld = b + 1;
+  double* A = cs64;                 // G, then R in its upper triangle (row i, column c at i + ld c)
+  double* Ri = A + b * ld;          // R^-1
+  double* T = Ri + b * ld;          // R Racc
+  double* dg = T + b * ld;          // the diagonal of G
+  __shared__ int sh_fail;
+  __shared__ double sh_shift;
+  int32_t* fb = at<int32_t>(bases, J.fallback);
+  double* Rinv = at<double>(bases, J.Rinv);
+  const double* G = at<const double>(bases, J.G);
+  if (threadIdx.x == 0) sh_fail = J.pass == 1 ? 0 : *fb;
+  for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+    const int i = e % b, c = e / b;
+    A[i + ld * c] = G[e];
+    if (i == c) dg[i] = G[e];
+  }
+  __syncthreads();
+  if (!sh_fail) {
+    if (J.pass == 1) {
+      if (threadIdx.x == 0) {
+        double tr = 0.0;
+        for (int i = 0; i < b; ++i) tr += dg[i];
+        sh_shift = 11.0 * ((double)J.P * b + (double)b * (b + 1)) * 1.1102230246251565e-16 * tr;
+        if (!isfinite(tr)) sh_fail = 1;
+      }
+      __syncthreads();
+      for (int i = threadIdx.x; i < b; i += blockDim.x) A[i + ld * i] += sh_shift;
+      __syncthreads();
+    }
+    // right-looking Cholesky G = R^T R, R upper triangular (row j of R replaces row j of G)
+    for (int j = 0; j < b && !sh_fail; ++j) {
+      if (threadIdx.x == 0) {
+        const double d = A[j + ld * j];
+        const double bound = J.pass == 1 ? 0.0 : 1e-12 * dg[j];
+        if (!(d > bound) || !isfinite(d)) sh_fail = 1;
+        else A[j + ld * j] = sqrt(d);
+      }
+      __syncthreads();
+      if (sh_fail) break;
+      const double rjj = A[j + ld * j];
+      for (int c = j + 1 + threadIdx.x; c < b; c += blockDim.x) A[j + ld * c] /= rjj;
+      __syncthreads();
+      const int w = b - j - 1;   // trailing block rows/columns j+1..b-1, upper part
+      for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+        const int r = j + 1 + e % w, c = j + 1 + e / w;
+        if (r <= c) A[r + ld * c] = fma(-A[j + ld * r], A[j + ld * c], A[r + ld * c]);
+      }
+      __syncthreads();
+    }
+  }
+  __syncthreads();
+  if (sh_fail) {
+    // this job takes the Householder fallback: an identity Rinv keeps the following products harmless
+    for (int e = threadIdx.x; e < b * b; e += blockDim.x) Rinv[e] = (e % b == e / b) ? 1.0 : 0.0;
+    if (threadIdx.x == 0) *fb = 1;
+    return;
+  }
+  // R^-1 by rows from the bottom: Ri[i][c] = (delta_ic - sum_{i<k<=c} R[i][k] Ri[k][c]) / R[i][i],
+  // four threads per column of the row
+  for (int i = b - 1; i >= 0; --i) {
+    const int c = i + (int)(threadIdx.x >> 2), part = threadIdx.x & 3;
+    double acc = 0.0;
+    if (c < b)
+      for (int k = i + 1 + part; k <= c; k += 4) acc = fma(A[i + ld * k], Ri[k + ld * c], acc);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+    if (c < b && part == 0) Ri[i + ld * c] = ((c == i ? 1.0 : 0.0) - acc) / A[i + ld * i];
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+    const int i = e % b, c = e / b;
+    Rinv[e] = i <= c ? Ri[i + ld * c] : 0.0;
+  }
+  // Racc <- R Racc (both upper triangular)
+  double* Racc = at<double>(bases, J.Racc);
+  for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+    const int i = e % b, c = e / b;
+    double acc = 0.0;
+    if (J.pass == 1) acc = i <= c ? A[i + ld * c] : 0.0;
+    else
+      for (int k = i; k <= c; ++k) acc = fma(A[i + ld * k], Racc[k + b * c], acc);
+    T[i + ld * c] = i <= c ? acc : 0.0;
+  }
+  __syncthreads();
+  double* out = J.pass == 3 ? at<double>(bases, J.Rout) : Racc;
+  for (int e = threadIdx.x; e < b * b; e += blockDim.x) out[e] = T[(e % b) + ld * (e / b)];
+  if (J.pass == 1 && threadIdx.x == 0) *fb = 0;
+  (void)status;
+}
+
 }  // namespace
 
 // At least twice the columns, so that every TSQR level shrinks the stack of factors.
 int tsqr64_block_rows(int max_cols) { return max_cols <= 64 ? 256 : 192; }
 
 cudaError_t prepare_la64(int bmax) {
+  cudaError_t e0 = cudaFuncSetAttribute(chol_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)((3 * 64 * 65 + 64) * sizeof(double)));
+  if (e0 != cudaSuccess) return e0;
   cudaError_t e = cudaFuncSetAttribute(svd_jacobi_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)svd64_smem(bmax));
   if (e != cudaSuccess) return e;
@@ -836,6 +950,11 @@ void launch_ttm_f64(const TtmJob* jobs, int njobs, int total_tiles, int max_cols
     case 5: ttm_f64_kernel<5><<<total_tiles, kTtmThreads, smem, stream>>>(jobs, njobs, bases); break;
     default: ttm_f64_kernel<6><<<total_tiles, kTtmThreads, smem, stream>>>(jobs, njobs, bases); break;
   }
+}
+
+void launch_chol_step(const CholJob* jobs, int njobs, const Bases& bases, Status* status, cudaStream_t stream) {
+  const size_t smem = (size_t)(3 * 64 * 65 + 64) * sizeof(double);
+  chol_step_kernel<<<njobs, kCholThreads, smem, stream>>>(jobs, bases, status);
 }
 
 }  // namespace tks

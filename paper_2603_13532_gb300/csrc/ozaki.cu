@@ -101,6 +101,71 @@ __global__ void __launch_bounds__(kOzSliceThreads) oz_slice_kernel(const OzSlice
   }
 }
 
+// Digits of one float64 value against a row exponent e (|x| < 2^e): M = floor(|x| 2^(56 - e)) < 2^56
+// from the exponent and significand bits, digit s = bits [49 - 7 s, 55 - 7 s] of M, signed as x.
+__device__ __forceinline__ unsigned long long oz_magnitude(double x, int e, bool& neg) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((u >> 52) & 0x7ff);
+  const unsigned long long S = (u & 0xfffffffffffffull) | (E ? (1ull << 52) : 0ull);
+  const int sh = (E ? E : 1) - 1019 - e;
+  neg = (u >> 63) != 0;
+  if (sh >= 0) return S << sh;
+  return sh > -64 ? S >> (-sh) : 0ull;
+}
+
+__device__ __forceinline__ uint16_t oz_digit(unsigned long long M, int s, bool neg) {
+  const int d = (int)((M >> (49 - 7 * s)) & 127ull);
+  return __bfloat16_as_ushort(__float2bfloat16_rn((float)(neg ? -d : d)));
+}
+
+// Column slicing for the Gram matrices of shifted CholeskyQR3: one CTA per column a of X (P rows),
+// the column's exponent by a block reduction, then its digits along the row of each plane.
+constexpr int kOzColThreads = 256;
+
+__global__ void __launch_bounds__(kOzColThreads) oz_colslice_kernel(const OzColSliceJob* __restrict__ jobs,
+                                                                   int njobs, Bases bases) {
+  __shared__ int wmax[kOzColThreads / 32];
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].tile_begin <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+  }
+  const OzColSliceJob& J = jobs[lo];
+  const int a = blockIdx.x - J.tile_begin;
+  const int64_t P = J.P, L = J.L;
+  const double* src = at<double>(bases, J.src);
+  // element i = l + L r of column a at l + L a + L b r
+  auto elem = [&](int64_t i) {
+    const int64_t r = L == 1 ? i : i / L, l = i - r * L;
+    return src[l + L * (int64_t)a + L * (int64_t)J.b * r];
+  };
+  int emax = 0;
+  for (int64_t i = threadIdx.x; i < P; i += kOzColThreads) {
+    const int E = (int)((__double_as_longlong(elem(i)) >> 52) & 0x7ff);
+    emax = E > emax ? E : emax;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const int other = __shfl_xor_sync(0xffffffffu, emax, o);
+    emax = other > emax ? other : emax;
+  }
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = emax;
+  __syncthreads();
+  emax = 0;
+  for (int w = 0; w < kOzColThreads / 32; ++w) emax = wmax[w] > emax ? wmax[w] : emax;
+  const int e = emax == 0 ? 0 : emax - 1022;
+  if (threadIdx.x == 0) at<int32_t>(bases, J.expo)[a] = e;
+  uint16_t* planes = at<uint16_t>(bases, J.planes);
+  const int64_t pstride = 64 * J.ldP;
+  uint16_t* row = planes + (int64_t)a * J.ldP;
+  for (int64_t i = threadIdx.x; i < P; i += kOzColThreads) {
+    bool neg;
+    const unsigned long long M = oz_magnitude(elem(i), e, neg);
+#pragma unroll
+    for (int sl = 0; sl < kOzSlices; ++sl) row[sl * pstride + i] = oz_digit(M, sl, neg);
+  }
+}
+
 // ----------------------------------------------------------------------------- digit products
 // One 128 x 64 tile of Y per CTA.  Warp 0 (one thread) loads the eight digit planes of the tile's X
 // rows and of its P columns with TMA (one k-block of 64 at a time; K <= 96 takes two); warp 1 owns
@@ -246,6 +311,162 @@ __global__ void __launch_bounds__(192, 1) oz_gemm_kernel(const OzGemmJob* __rest
   if (threadIdx.x == 0 && *err) atomicCAS(&status->code, 0, (int)TKS_ETIMEOUT);
 }
 
+// ----------------------------------------------------------------------------- Gram matrices
+// G = X^T X (b x b, b <= 64) from the column digit planes, one CTA per job.  Warp 0 (one thread) loads
+// one k-block (64 rows of X) of all eight planes per stage, two stages; warp 1 owns the kOzLevels TMEM
+// accumulators and issues the 36 digit-pair products per k-block with A and B the same 64-column tiles
+// (an M = 128 product also reads the 64 rows after a tile, whose results land in TMEM lanes 64..127
+// and are ignored).  Every kOzGramGroup k-blocks the level sums, exact integers (8 pairs x 128 x
+// 127^2 < 2^24), are drained by warps 4 and 5 (TMEM lanes 0..63), combined in 64-bit integers and
+// added in float64 into a shared-memory accumulator; the scale 2^(e_i + e_j) is applied once at the
+// end.  Waits are bounded as in the other tensor-core kernels.
+constexpr int kOzGramGroup = 2;
+constexpr int kOzPlaneTile = 64 * kOzBK * 2;                          // 8 KB: 64 columns x 64 k
+constexpr int kOzStageBytes = (kOzSlices + 1) * kOzPlaneTile;         // + the 8 KB an M = 128 read passes
+constexpr size_t kOzGramSmem = 1024 + 2 * (size_t)kOzStageBytes + 64 * 64 * 8 + 128;
+
+__global__ void __launch_bounds__(192, 1) oz_gram_kernel(const OzGramJob* __restrict__ jobs,
+                                                       const CUtensorMap* __restrict__ maps, Bases bases,
+                                                       Status* status, long long wait_cycles) {
+  extern __shared__ uint8_t og_smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(og_smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* stage[2] = {smem, smem + kOzStageBytes};
+  double* acc64 = reinterpret_cast<double*>(smem + 2 * kOzStageBytes);   // [row][col], 64 x 64
+  uint64_t* full = reinterpret_cast<uint64_t*>(acc64 + 64 * 64);
+  uint64_t* empty = full + 2;
+  uint64_t* tmem_full = empty + 2;
+  uint64_t* tmem_empty = tmem_full + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tmem_empty + 1);
+  volatile int* err = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  const OzGramJob& J = jobs[blockIdx.x];
+  const int nk = (int)((J.P + kOzBK - 1) / kOzBK);
+  const int ngroups = (nk + kOzGramGroup - 1) / kOzGramGroup;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < 2; ++st) {
+      tc::mbar_init(&full[st], 1);
+      tc::mbar_init(&empty[st], 1);
+    }
+    tc::mbar_init(tmem_full, 1);
+    tc::mbar_init(tmem_empty, 2);
+    *err = 0;
+    tc::fence_barrier_init();
+  }
+  for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) acc64[e] = 0.0;
+  if (warp == 1) tc::tmem_alloc(tmem_slot, kOzLevels * kOzBN);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int sl = 0; sl < kOzSlices; ++sl) tc::prefetch_tmap(&maps[J.map[sl]]);
+      int issued = 0;
+      for (int kb = 0; kb < nk; ++kb) {
+        const int st = kb & 1, round = kb >> 1;
+        if (*err || !tc::mbar_wait(&empty[st], (round & 1) ^ 1, wait_cycles)) {
+          *err = 1;
+          break;
+        }
+        tc::mbar_expect_tx(&full[st], (uint32_t)(kOzSlices * kOzPlaneTile));
+        for (int sl = 0; sl < kOzSlices; ++sl)
+          tc::tma_load_2d(stage[st] + sl * kOzPlaneTile, &maps[J.map[sl]], &full[st], kb * kOzBK, 0);
+        issued = kb + 1;
+      }
+      // drain: every copy issued has landed before the CTA tears down
+      for (int kb = (issued > 2 ? issued - 2 : 0); kb < issued; ++kb)
+        if (!tc::mbar_wait(&full[kb & 1], (kb >> 1) & 1, wait_cycles)) *err = 1;
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = tc::idesc_bf16_f32(kOzBM, kOzBN);
+      for (int kb = 0; kb < nk; ++kb) {
+        const int st = kb & 1, round = kb >> 1;
+        const int g = kb / kOzGramGroup;
+        const bool first = kb % kOzGramGroup == 0;
+        const bool last = kb % kOzGramGroup == kOzGramGroup - 1 || kb == nk - 1;
+        // a group starts once the previous group's sums have been drained
+        if (first && g > 0 && (*err || !tc::mbar_wait(tmem_empty, (g - 1) & 1, wait_cycles))) {
+          *err = 1;
+          break;
+        }
+        if (*err || !tc::mbar_wait(&full[st], round & 1, wait_cycles)) {
+          *err = 1;
+          break;
+        }
+        tc::fence_after_sync();
+        for (int acc = 0; acc < kOzLevels; ++acc) {
+          const uint32_t d = tmem + (uint32_t)(acc * kOzBN);
+          for (int sa = 0; sa <= acc; ++sa) {
+            const uint32_t a0 = tc::smem_u32(stage[st] + sa * kOzPlaneTile);
+            const uint32_t b0 = tc::smem_u32(stage[st] + (acc - sa) * kOzPlaneTile);
+#pragma unroll
+            for (int k = 0; k < kOzBK / 16; ++k) {
+              const uint32_t accumulate = (!first || sa > 0 || k > 0) ? 1u : 0u;
+              tc::mma_bf16(d, tc::sw128_kmajor_desc(a0 + 32 * k), tc::sw128_kmajor_desc(b0 + 32 * k), idesc,
+                           accumulate);
+            }
+          }
+        }
+        tc::mma_commit(&empty[st]);
+        if (last) tc::mma_commit(tmem_full);
+      }
+      // the last group's products have completed before teardown
+      if (!*err && !tc::mbar_wait(tmem_full, (ngroups - 1) & 1, wait_cycles)) *err = 1;
+    }
+  } else if ((warp & 3) < 2) {
+    // warps 4 and 5: TMEM lanes 0..63 (the rows of G)
+    const int q = warp & 3;
+    const int row = 32 * q + lane;
+    for (int g = 0; g < ngroups; ++g) {
+      bool ok = tc::mbar_wait(tmem_full, g & 1, wait_cycles);
+      ok = __all_sync(0xffffffffu, ok) && !*err;
+      if (!ok) {
+        if (lane == 0) *err = 1;
+        break;
+      }
+      tc::fence_after_sync();
+      for (int c0 = 0; c0 < kOzBN; c0 += 8) {
+        uint32_t v[kOzLevels][8];
+#pragma unroll
+        for (int acc = 0; acc < kOzLevels; ++acc)
+          tc::tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * kOzBN + c0), v[acc]);
+        tc::tmem_ld_wait();
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          long long hi64 = 0, lo64 = 0;
+#pragma unroll
+          for (int acc = 0; acc < 4; ++acc)
+            hi64 = (hi64 << 7) + (long long)__float2int_rn(__uint_as_float(v[acc][j]));
+#pragma unroll
+          for (int acc = 4; acc < kOzLevels; ++acc)
+            lo64 = (lo64 << 7) + (long long)__float2int_rn(__uint_as_float(v[acc][j]));
+          acc64[row * 64 + c0 + j] += fma((double)lo64, 3.7252902984619140625e-09, (double)hi64);
+        }
+      }
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(tmem_empty);
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 1) tc::tmem_dealloc(tmem, kOzLevels * kOzBN);
+  if (!*err) {
+    // G[i + b j] = 2^(e_i + e_j - 35) acc[i][j]
+    const int32_t* expo = at<const int32_t>(bases, J.expo);
+    double* G = at<double>(bases, J.G);
+    const int b = J.b;
+    for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+      const int i = e % b, j = e / b;
+      G[e] = scalbn(acc64[i * 64 + j], expo[i] + expo[j] - 35);
+    }
+  } else if (threadIdx.x == 0) {
+    atomicCAS(&status->code, 0, (int)TKS_ETIMEOUT);
+  }
+}
+
 }  // namespace
 
 int oz_slice_tiles(int64_t rows) { return (int)((rows + kOzRowsPerCta - 1) / kOzRowsPerCta); }
@@ -255,7 +476,20 @@ void launch_oz_slice(const OzSliceJob* jobs, int njobs, int total_tiles, const B
 }
 
 cudaError_t prepare_oz_gemm() {
-  return cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOzSmem);
+  cudaError_t e = cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOzSmem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(oz_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOzGramSmem);
+}
+
+void launch_oz_colslice(const OzColSliceJob* jobs, int njobs, int total_cols, const Bases& bases,
+                        cudaStream_t stream) {
+  oz_colslice_kernel<<<total_cols, kOzColThreads, 0, stream>>>(jobs, njobs, bases);
+}
+
+void launch_oz_gram(const OzGramJob* jobs, int njobs, const void* maps, const Bases& bases, Status* status,
+                    long long wait_cycles, cudaStream_t stream) {
+  oz_gram_kernel<<<njobs, 192, kOzGramSmem, stream>>>(jobs, static_cast<const CUtensorMap*>(maps), bases, status,
+                                                      wait_cycles);
 }
 
 void launch_oz_gemm(const OzGemmJob* jobs, int njobs, int total_tiles, const void* maps, const Bases& bases,

@@ -20,6 +20,7 @@ namespace tks {
 constexpr int MAXD = TKS_MAX_ORDER;
 
 enum BaseId : int32_t {
+  B_NONE = -2,   // no operand
   B_ABS = -1,    // offset is an absolute device address
   B_WS = 0,      // workspace
   B_OMEGA = 1,   // Omega buffer (caller's for tks_generate_omega, else workspace)
@@ -310,6 +311,8 @@ struct QrF32Job {
 // factoring again gives the triangular factor of the whole matrix.
 struct TsqrJob {
   Operand src, dst;
+  Operand gate;          // float64 kernel: when gate.base != B_NONE, the block runs only if the int32
+                         // there is nonzero (the CholeskyQR path asked for the Householder fallback)
   int32_t src_type, rows, cols;
   int32_t tri;           // float64 kernel: 0 = dense rows; k = the rows interleave k stacked upper
                          // triangular factors (row i = factor + k r), so column j is zero where r > j
@@ -358,6 +361,35 @@ struct OzGemmJob {
   Operand Y;             // float64: element (q, c) at Y[l + L (c + rmax r)], q = l + L r
   int64_t L;
   int32_t rmax, pad;
+};
+
+// Shifted CholeskyQR3 of X = H_(n)^T (P x b, element (i = l + L r, a) at src[l + L a + L b r]) with
+// float64-accurate Gram matrices on the tensor cores (TKS_MIXED):
+// column slicing: the b columns of X as rows of digit planes (K = P along the row), one CTA per column;
+// plane s of column a at planes + (s * 64 + a) * ldP elements, its exponent at expo[a].
+struct OzColSliceJob {
+  Operand src, planes, expo;
+  int64_t P, L, ldP;
+  int32_t b, tile_begin;
+};
+
+// G = X^T X (b x b, b <= 64) from the column digit planes (TMA maps map[s], box 64 k x 64 rows),
+// one CTA per job, K = P in blocks of 64; G float64 at G[i + b j].
+struct OzGramJob {
+  int32_t map[kOzSlices];
+  Operand expo, G;
+  int64_t P;
+  int32_t b, pad;
+};
+
+// One Cholesky step of shifted CholeskyQR3 (pass 1..3) on G (b x b, float64), one CTA per job:
+// R = chol(G + shift I) (shift only in pass 1), Rinv = R^-1 for the next X <- X Rinv, Racc <- R Racc;
+// the last pass writes Racc (the triangular factor of X) to Rout and clears *fallback, a pivot below
+// the pass's bound sets *fallback (the Householder TSQR then factors X instead).
+struct CholJob {
+  Operand G, Rinv, Racc, Rout, fallback;
+  int64_t P;
+  int32_t b, pass;
 };
 
 // Effective subrank heuristic (Alg. 5), float64 throughout.
