@@ -75,6 +75,13 @@ Step make_step(StepKind kind, size_t off, int njobs, int64_t work, const char* n
   return s;
 }
 
+// Workspace of shifted CholeskyQR3 of one tall matrix (byte offsets): the two re-formed X, the column
+// digit planes and exponents, the Gram matrix, R^-1, the accumulated R, the fallback flag, and the row
+// digit planes and exponents of X and of R^-1.
+struct CqBuffers {
+  size_t X[2], col, colE, G, Rinv, Racc, flag, rowA, rowAE, rowB, rowBE;
+};
+
 struct ProbHost {
   int d = 0, K = 0;
   int64_t n[MAXD] = {};
@@ -95,6 +102,7 @@ struct ProbHost {
   size_t R64 = 0, stk64[2] = {};   // float64 ST-HOSVD: triangular factor and TSQR stacks
   size_t ozA = 0, ozQ = 0, ozB = 0, ozEA = 0, ozEQ = 0, ozEB = 0;   // TKS_MIXED mode products: digit planes
   size_t cqX[2] = {}, cqCol = 0, cqColE = 0, cqG = 0, cqRinv = 0, cqRacc = 0, cqFlag = 0;   // CholeskyQR3
+  CqBuffers qcq[MAXD] = {};   // TKS_MIXED: CholeskyQR3 of the sketches Y_n (flag == 0: Householder QR)
   std::vector<size_t> chain;   // 2 ping-pong buffers per term
   // mixed-precision buffers (bytes): bf16 planes and float32 intermediates
   size_t om_plane[MAXD] = {}, UT[MAXD] = {}, M32[MAXD] = {}, Vp[MAXD][3] = {}, Qp[MAXD][3] = {};
@@ -416,6 +424,126 @@ void count_flops(ProbHost& h, int kron) {
 
 namespace {
 
+// Launch lists of shifted CholeskyQR3 for a set of tall matrices X (P x b, b <= 64, element (i = l + L r,
+// a) at src[l + L a + L b r]), all run by the same grouped launches: three passes of [column digit
+// planes, Gram matrix, Cholesky step, row digit planes of X and R^-1, X <- X R^-1]; the third pass
+// ends after its Cholesky step, or with Q = X R^-1 when the caller wants the orthonormal factor.
+struct CqLists {
+  std::vector<OzColSliceJob> cols[3];
+  std::vector<OzGramJob> gram[3];
+  std::vector<CholJob> chol[3];
+  std::vector<OzSliceJob> slice[3];
+  std::vector<OzGemmJob> gemm[3];
+  int cols_total[3] = {0, 0, 0}, slice_total[3] = {0, 0, 0}, gemm_total[3] = {0, 0, 0};
+  double gram_flops = 0.0, gemm_flops[3] = {0.0, 0.0, 0.0};
+
+  // Rout: where the last pass writes R (B_NONE: not wanted); Qout: where X R^-1 of the last pass goes
+  // (B_NONE: no third product).  Returns the fallback flag operand (nonzero: a Cholesky step broke
+  // down and the Householder factorization must run for this matrix).
+  Operand add(tks_plan* plan, Operand src, int64_t P, int64_t L, int b, const CqBuffers& B, Operand Rout,
+              Operand Qout) {
+    const int64_t ldP = (P + 7) / 8 * 8;
+    const int ldk = 64;
+    const Operand flag = op(B_WS, B.flag);
+    const Operand X[3] = {src, op(B_WS, B.X[0]), op(B_WS, B.X[1])};
+    for (int pass = 0; pass < 3; ++pass) {
+      OzColSliceJob cj;
+      std::memset(&cj, 0, sizeof(cj));
+      cj.src = X[pass];
+      cj.planes = op(B_WS, B.col);
+      cj.expo = op(B_WS, B.colE);
+      cj.P = P;
+      cj.L = L;
+      cj.ldP = ldP;
+      cj.b = b;
+      cj.tile_begin = cols_total[pass];
+      cols_total[pass] += b;
+      cols[pass].push_back(cj);
+      OzGramJob gj;
+      std::memset(&gj, 0, sizeof(gj));
+      for (int sl = 0; sl < kOzSlices; ++sl)
+        gj.map[sl] = plan->map_of(B_WS, B.col + (size_t)sl * 64 * ldP * 2, P, b, ldP, 64);
+      gj.expo = cj.expo;
+      gj.G = op(B_WS, B.G);
+      gj.P = P;
+      gj.b = b;
+      gram[pass].push_back(gj);
+      gram_flops += 2.0 * (double)P * b * b;
+      CholJob ch;
+      std::memset(&ch, 0, sizeof(ch));
+      ch.G = gj.G;
+      ch.Rinv = op(B_WS, B.Rinv);
+      ch.Racc = op(B_WS, B.Racc);
+      ch.Rout = Rout;
+      ch.fallback = flag;
+      ch.P = P;
+      ch.b = b;
+      ch.pass = pass + 1;
+      chol[pass].push_back(ch);
+      if (pass == 2 && Qout.base == B_NONE) break;
+      // the next X (or Q) = X Rinv: digits of the rows of X and of the columns of Rinv
+      auto slice_job = [&](Operand s_src, size_t planes, size_t expo, int64_t rows, int64_t Ls) {
+        OzSliceJob sj;
+        std::memset(&sj, 0, sizeof(sj));
+        sj.src = s_src;
+        sj.planes = op(B_WS, planes);
+        sj.expo = op(B_WS, expo);
+        sj.rows = rows;
+        sj.L = Ls;
+        sj.rows_pad = (rows + 7) / 8 * 8;
+        sj.K = b;
+        sj.ld = ldk;
+        sj.tiles = oz_slice_tiles(rows);
+        sj.tile_begin = slice_total[pass];
+        slice_total[pass] += sj.tiles;
+        slice[pass].push_back(sj);
+        return sj;
+      };
+      const OzSliceJob sx = slice_job(X[pass], B.rowA, B.rowAE, P, L);
+      const OzSliceJob sr = slice_job(ch.Rinv, B.rowB, B.rowBE, b, 1);
+      OzGemmJob g;
+      std::memset(&g, 0, sizeof(g));
+      g.M = (int)P;
+      g.N = b;
+      g.K = b;
+      g.tiles_m = ceil_div(g.M, 128);
+      g.tiles_n = 1;
+      g.tile_begin = gemm_total[pass];
+      gemm_total[pass] += g.tiles_m;
+      for (int sl = 0; sl < kOzSlices; ++sl) {
+        g.mapA[sl] = plan->map_of(B_WS, sx.planes.off + (size_t)sl * sx.rows_pad * ldk * 2, b, P, ldk, 128);
+        g.mapB[sl] = plan->map_of(B_WS, sr.planes.off + (size_t)sl * sr.rows_pad * ldk * 2, b, b, ldk, 64);
+      }
+      g.expA = sx.expo;
+      g.expB = sr.expo;
+      g.Y = pass == 2 ? Qout : X[pass + 1];
+      g.L = L;
+      g.rmax = b;
+      gemm[pass].push_back(g);
+      gemm_flops[pass] += 2.0 * (double)P * b * b;
+    }
+    return flag;
+  }
+
+  void push(tks_plan* plan, std::vector<Step>& steps, const char* tag) const {
+    char nm[32];
+    for (int pass = 0; pass < 3; ++pass) {
+      if (gram[pass].empty()) break;
+      std::snprintf(nm, sizeof(nm), "%s.cols%d[oz]", tag, pass + 1);
+      plan->push(steps, S_OZCOLS, cols[pass], cols_total[pass], nm);
+      std::snprintf(nm, sizeof(nm), "%s.gram%d[oz]", tag, pass + 1);
+      plan->push(steps, S_OZGRAM, gram[pass], (int64_t)gram[pass].size(), nm, gram_flops / 3.0, 0.0);
+      std::snprintf(nm, sizeof(nm), "%s.chol%d", tag, pass + 1);
+      plan->push(steps, S_CHOL, chol[pass], (int64_t)chol[pass].size(), nm);
+      if (gemm[pass].empty()) continue;
+      std::snprintf(nm, sizeof(nm), "%s.slice%d[oz]", tag, pass + 1);
+      plan->push(steps, S_OZSLICE, slice[pass], slice_total[pass], nm);
+      std::snprintf(nm, sizeof(nm), "%s.XRinv%d[oz]", tag, pass + 1);
+      plan->push(steps, S_OZGEMM, gemm[pass], gemm_total[pass], nm, gemm_flops[pass], 0.0);
+    }
+  }
+};
+
 // Stages (a)-(c) of the mixed-precision path.  bf16 operand planes are laid out K-major for the
 // tensor-core GEMMs (TMA tiles of 64 k x 128 rows for A, 64 k x 64 rows for B):
 //   a1  Omega_m rounded to bf16 (a plane besides the float64 copy)
@@ -427,6 +555,7 @@ namespace {
 //   a7  per-term chains in float32, last step written as planes of Tcat (element (r, J) at r + ldT J)
 //   a8  H_(d)^T = Tcat^T A_d^T            A = Tcat planes (rows J)      B = A_d^T planes (rows a)
 static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
+  CqLists qcq;   // TKS_MIXED: Q_n = qr(Y_n) by shifted CholeskyQR3 where n_n >= S_n <= 64
   std::vector<QrF32Job> qr32, qrsm, qrreg;
   bool planes_in_qr = false;   // the register QR of this mode also writes the bf16 planes of Q
   size_t qrsm_smem = 0, qrreg_smem = 0;
@@ -661,9 +790,16 @@ static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
         q.W = op(B_WS, h.W[n]);
         q.Q = op(B_Q, h.q_off[n] * 8);
         q.tau = op(B_WS, h.tau[n]);
+        q.gate = Operand{B_NONE, 0, 0};
         q.n = (int)nn;
         q.S = h.S[n];
         q.b = h.b[n];
+        if (h.qcq[n].flag) {
+          // Q_n by shifted CholeskyQR3 (float64-accurate Grams and products on the tensor cores);
+          // the Householder QR runs only if a Cholesky step breaks down (a rank-deficient sketch)
+          q.gate = qcq.add(plan, op(B_Y, h.y_off[n] * 8), (int64_t)nn, (int64_t)nn, h.S[n], h.qcq[n], Operand{B_NONE, 0, 0},
+                           op(B_Q, h.q_off[n] * 8));
+        }
         qr.push_back(q);
       }
       qr_flops += 4.0 * (double)nn * h.b[n] * h.b[n];
@@ -958,7 +1094,9 @@ static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
   }
   push_proj(S_PROJ3F, p3f, p3fterms, "a7:project4[f32]", p3f_flops, p3f_bytes);
   plan->st_recompress = plan->st_sketch;
-  plan->push(plan->st_recompress, S_QR, qr, (int64_t)qr.size(), "a5:qr", qr_flops, qr_bytes);
+  qcq.push(plan, plan->st_recompress, "a5:cq");
+  plan->push(plan->st_recompress, S_QR, qr, (int64_t)qr.size(), "a5:qr", qcq.gram[0].empty() ? qr_flops : 0.0,
+             qr_bytes);
   plan->push(plan->st_recompress, S_QR32, qr32, (int64_t)qr32.size(), "a5:qr[f32]", qr_flops, qr_bytes);
   if (!qrreg.empty()) {
     // work = the largest row count (selects the kernel's rows per lane)
@@ -1241,15 +1379,8 @@ static void build_hosvd_f64(tks_plan* plan) {
     int ttm_tiles = 0, fac_tiles = 0;
     double qflops = 0.0, ttm_flops = 0.0, fac_flops = 0.0;
     // TKS_MIXED with b <= 64: the triangular factor by shifted CholeskyQR3 with float64-accurate Gram
-    // matrices and products on the tensor cores; three passes of [column digits, Gram, Cholesky step,
-    // row digits of X and R^-1, X <- X R^-1] (the last pass stops after its Cholesky step)
-    std::vector<OzColSliceJob> cq_cols[3];
-    std::vector<OzGramJob> cq_gram[3];
-    std::vector<CholJob> cq_chol[3];
-    std::vector<OzSliceJob> cq_slice[2];
-    std::vector<OzGemmJob> cq_gemm[2];
-    int cq_cols_total[3] = {0, 0, 0}, cq_slice_total[2] = {0, 0}, cq_gemm_total[2] = {0, 0};
-    double cq_gram_flops = 0.0, cq_gemm_flops = 0.0;
+    // matrices and products on the tensor cores (the Householder TSQR below runs only where it fails)
+    CqLists cq;
     for (int p = plan->lane_p0; p < plan->lane_p1; ++p) {
       auto& h = plan->probs[p];
       const int d = h.d;
@@ -1262,87 +1393,9 @@ static void build_hosvd_f64(tks_plan* plan) {
       const bool cholqr = emulate && b <= 64;
       Operand gate{B_NONE, 0, 0};
       if (cholqr) {
-        const int64_t P = L * Rr;
-        const int64_t ldP = (P + 7) / 8 * 8;
-        const int ldk = 64;
-        gate = op(B_WS, h.cqFlag);
-        const Operand src[3] = {X, op(B_WS, h.cqX[0]), op(B_WS, h.cqX[1])};
-        for (int pass = 0; pass < 3; ++pass) {
-          OzColSliceJob cj;
-          std::memset(&cj, 0, sizeof(cj));
-          cj.src = src[pass];
-          cj.planes = op(B_WS, h.cqCol);
-          cj.expo = op(B_WS, h.cqColE);
-          cj.P = P;
-          cj.L = L;
-          cj.ldP = ldP;
-          cj.b = b;
-          cj.tile_begin = cq_cols_total[pass];
-          cq_cols_total[pass] += b;
-          cq_cols[pass].push_back(cj);
-          OzGramJob gj;
-          std::memset(&gj, 0, sizeof(gj));
-          for (int sl = 0; sl < kOzSlices; ++sl)
-            gj.map[sl] = plan->map_of(B_WS, h.cqCol + (size_t)sl * 64 * ldP * 2, P, b, ldP, 64);
-          gj.expo = cj.expo;
-          gj.G = op(B_WS, h.cqG);
-          gj.P = P;
-          gj.b = b;
-          cq_gram[pass].push_back(gj);
-          cq_gram_flops += 2.0 * (double)P * b * b;
-          CholJob ch;
-          std::memset(&ch, 0, sizeof(ch));
-          ch.G = gj.G;
-          ch.Rinv = op(B_WS, h.cqRinv);
-          ch.Racc = op(B_WS, h.cqRacc);
-          ch.Rout = op(B_WS, h.R64);
-          ch.fallback = gate;
-          ch.P = P;
-          ch.b = b;
-          ch.pass = pass + 1;
-          cq_chol[pass].push_back(ch);
-          if (pass == 2) break;
-          // X_next = X Rinv: digits of the rows of X and of the columns of Rinv, then 128 x 64 tiles
-          auto slice = [&](Operand s_src, size_t planes, size_t expo, int64_t rows, int64_t Ls) {
-            OzSliceJob sj2;
-            std::memset(&sj2, 0, sizeof(sj2));
-            sj2.src = s_src;
-            sj2.planes = op(B_WS, planes);
-            sj2.expo = op(B_WS, expo);
-            sj2.rows = rows;
-            sj2.L = Ls;
-            sj2.rows_pad = (rows + 7) / 8 * 8;
-            sj2.K = b;
-            sj2.ld = ldk;
-            sj2.tiles = oz_slice_tiles(rows);
-            sj2.tile_begin = cq_slice_total[pass];
-            cq_slice_total[pass] += sj2.tiles;
-            cq_slice[pass].push_back(sj2);
-            return sj2;
-          };
-          const OzSliceJob sx = slice(src[pass], h.ozA, h.ozEA, P, L);
-          const OzSliceJob sr = slice(ch.Rinv, h.ozB, h.ozEB, b, 1);
-          OzGemmJob g;
-          std::memset(&g, 0, sizeof(g));
-          g.M = (int)P;
-          g.N = b;
-          g.K = b;
-          g.tiles_m = ceil_div(g.M, 128);
-          g.tiles_n = 1;
-          g.tile_begin = cq_gemm_total[pass];
-          cq_gemm_total[pass] += g.tiles_m;
-          for (int sl = 0; sl < kOzSlices; ++sl) {
-            g.mapA[sl] = plan->map_of(B_WS, sx.planes.off + (size_t)sl * sx.rows_pad * ldk * 2, b, P, ldk, 128);
-            g.mapB[sl] = plan->map_of(B_WS, sr.planes.off + (size_t)sl * sr.rows_pad * ldk * 2, b, b, ldk, 64);
-          }
-          g.expA = sx.expo;
-          g.expB = sr.expo;
-          g.Y = src[pass + 1];
-          g.L = L;
-          g.rmax = b;
-          cq_gemm[pass].push_back(g);
-          cq_gemm_flops += 2.0 * (double)P * b * b;
-        }
+        const CqBuffers B{{h.cqX[0], h.cqX[1]}, h.cqCol, h.cqColE, h.cqG, h.cqRinv, h.cqRacc, h.cqFlag,
+                          h.ozA, h.ozEA, h.ozB, h.ozEB};
+        gate = cq.add(plan, X, L * Rr, L, b, B, op(B_WS, h.R64), Operand{B_NONE, 0, 0});
       }
       // TSQR of H_(n)^T: element (l + L rr, c) at l + L c + L b rr.  Level 0 factors blocks of dense
       // rows; every later level factors groups of the previous level's b x b triangular factors,
@@ -1497,24 +1550,14 @@ static void build_hosvd_f64(tks_plan* plan) {
       }
     }
     char nm[32];
-    for (int pass = 0; pass < 3; ++pass) {
-      if (cq_gram[pass].empty()) break;
-      std::snprintf(nm, sizeof(nm), "a9:cq%d.cols%d[oz]", n, pass + 1);
-      plan->push(plan->st_recompress, S_OZCOLS, cq_cols[pass], cq_cols_total[pass], nm);
-      std::snprintf(nm, sizeof(nm), "a9:cq%d.gram%d[oz]", n, pass + 1);
-      plan->push(plan->st_recompress, S_OZGRAM, cq_gram[pass], (int64_t)cq_gram[pass].size(), nm,
-                 cq_gram_flops / 3.0, 0.0);
-      std::snprintf(nm, sizeof(nm), "a9:cq%d.chol%d", n, pass + 1);
-      plan->push(plan->st_recompress, S_CHOL, cq_chol[pass], (int64_t)cq_chol[pass].size(), nm);
-      if (pass == 2) break;
-      std::snprintf(nm, sizeof(nm), "a9:cq%d.slice%d[oz]", n, pass + 1);
-      plan->push(plan->st_recompress, S_OZSLICE, cq_slice[pass], cq_slice_total[pass], nm);
-      std::snprintf(nm, sizeof(nm), "a9:cq%d.XRinv%d[oz]", n, pass + 1);
-      plan->push(plan->st_recompress, S_OZGEMM, cq_gemm[pass], cq_gemm_total[pass], nm, cq_gemm_flops / 2.0, 0.0);
+    {
+      char tag[24];
+      std::snprintf(tag, sizeof(tag), "a9:cq%d", n);
+      cq.push(plan, plan->st_recompress, tag);
     }
     // the Householder TSQR: every problem on the TKS_FP64 path and those with b > 64; on the
     // CholeskyQR3 path it is gated per problem and runs only where a Cholesky step broke down
-    const bool any_tsqr_work = !cq_gram[0].empty() ? false : true;
+    const bool any_tsqr_work = cq.gram[0].empty();
     for (size_t lvl = 0; lvl < tsqr.size(); ++lvl) {
       std::snprintf(nm, sizeof(nm), "a9:tsqr%d.%d", n, (int)lvl);
       plan->push(plan->st_recompress, S_TSQR64, tsqr[lvl], (int64_t)tsqr[lvl].size(), nm,
@@ -1679,6 +1722,23 @@ tks_status tks_plan_create(tks_plan** out, const tks_problem* problems, int32_t 
         for (int t = 0; t < 3; ++t) h.Vp[m][t] = alloc((size_t)h.ldV[m] * h.S[m] * 2);
         for (int t = 0; t < 3; ++t) h.Qp[m][t] = alloc((size_t)h.n[m] * h.b[m] * 2);
         h.AT32[m] = alloc((size_t)h.R[m] * h.b[m] * 4);
+        if (prm.precision == TKS_MIXED && h.n[m] >= h.S[m] && h.S[m] <= 64) {
+          // CholeskyQR3 of Y_n (n_m x S_m): see CqBuffers
+          const int64_t rows8 = (h.n[m] + 7) / 8 * 8;
+          CqBuffers& B = h.qcq[m];
+          B.X[0] = alloc((size_t)h.n[m] * h.S[m] * 8);
+          B.X[1] = alloc((size_t)h.n[m] * h.S[m] * 8);
+          B.col = alloc((size_t)kOzSlices * 64 * rows8 * 2);
+          B.colE = alloc(64 * 4);
+          B.G = alloc(64 * 64 * 8);
+          B.Rinv = alloc(64 * 64 * 8);
+          B.Racc = alloc(64 * 64 * 8);
+          B.flag = alloc(4);
+          B.rowA = alloc((size_t)kOzSlices * rows8 * 64 * 2);
+          B.rowAE = alloc((size_t)rows8 * 4);
+          B.rowB = alloc((size_t)kOzSlices * 64 * 64 * 2);
+          B.rowBE = alloc(64 * 4);
+        }
       }
     }
     if (!mixed) {
@@ -1876,6 +1936,7 @@ tks_status tks_plan_create(tks_plan** out, const tks_problem* problems, int32_t 
       q.W = op(B_WS, h.W[n]);
       q.Q = op(B_Q, h.q_off[n] * 8);
       q.tau = op(B_WS, h.tau[n]);
+      q.gate = Operand{B_NONE, 0, 0};
       q.n = (int)h.n[n];
       q.S = h.S[n];
       q.b = h.b[n];

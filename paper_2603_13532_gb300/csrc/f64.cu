@@ -279,6 +279,7 @@ __global__ void __launch_bounds__(256) qr_f64_kernel(const QrJob* __restrict__ j
   __shared__ double sh_tau, sh_scale;
   __shared__ int sh_bad;
   const QrJob& J = jobs[blockIdx.x];
+  if (J.gate.base != B_NONE && *at<const int32_t>(bases, J.gate) == 0) return;
   const int n = J.n, S = J.S, b = J.b;
   const double* Y = at<double>(bases, J.Y);
   double* W = at<double>(bases, J.W);

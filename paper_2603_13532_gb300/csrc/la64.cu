@@ -873,7 +873,7 @@ __global__ void __launch_bounds__(kCholThreads) chol_step_kernel(const CholJob* 
     T[i + ld * c] = i <= c ? acc : 0.0;
   }
   __syncthreads();
-  double* out = J.pass == 3 ? at<double>(bases, J.Rout) : Racc;
+  double* out = (J.pass == 3 && J.Rout.base != B_NONE) ? at<double>(bases, J.Rout) : Racc;
   for (int e = threadIdx.x; e < b * b; e += blockDim.x) out[e] = T[(e % b) + ld * (e / b)];
   if (J.pass == 1 && threadIdx.x == 0) *fb = 0;
   (void)status;

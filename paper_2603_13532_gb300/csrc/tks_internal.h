@@ -264,6 +264,8 @@ struct CoreSketchJob {
 // Householder QR of Y (n x S) giving Q (n x b), b = min(n, S), diag(R) >= 0.
 struct QrJob {
   Operand Y, W, Q, tau;         // W: n x S work copy, tau: S doubles
+  Operand gate;                 // when gate.base != B_NONE, the job runs only if the int32 there is
+                                // nonzero (the CholeskyQR path asked for the Householder fallback)
   int32_t n, S, b, pad;
 };
 

@@ -38,6 +38,20 @@ def _rel(a, b):
     return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300)
 
 
+def _per_slice(a, b, tol):
+    """Elementwise check beside the normwise one: along every axis, each slice (a column of Y, a
+    mode-n slice of H) has max |a - b| within tol times the largest |b| of that slice, so an error
+    confined to small entries or trailing rows cannot hide in the Frobenius norm."""
+    a, b = np.asarray(a), np.asarray(b)
+    for axis in range(b.ndim):
+        for k in range(b.shape[axis]):
+            sa, sb = np.take(a, k, axis=axis), np.take(b, k, axis=axis)
+            m = float(np.max(np.abs(sb)))
+            if m > 0:
+                err = float(np.max(np.abs(sa - sb)))
+                assert err <= tol * m, (axis, k, err / m)
+
+
 def _ragged_problems(d, kind_seed=0):
     g = np.random.default_rng(100 + d + kind_seed)
     probs = []
@@ -92,6 +106,7 @@ def test_sketch_matches_oracle(cuda_lib, kind, d):
                             alpha=prob.alpha)
         for m in range(d):
             assert _rel(Ys[p][m], ref["Y"][m]) <= 1e-12, (kind, d, p, m)
+            _per_slice(Ys[p][m], ref["Y"][m], 1e-12)
 
 
 @pytest.mark.parametrize("kind", ["krp", "kron"])
@@ -105,6 +120,7 @@ def test_projection_matches_oracle_given_q(cuda_lib, kind, d):
     for H, r in zip(Hs, refs):
         assert H.shape == r["H"].shape
         assert _rel(H, r["H"]) <= 1e-12
+        _per_slice(H, r["H"], 1e-12)
 
 
 @pytest.mark.parametrize("kind", ["kron", "krp"])

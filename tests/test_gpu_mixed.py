@@ -35,6 +35,20 @@ def _rel(a, b):
     return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300)
 
 
+def _per_slice(a, b, tol):
+    """Elementwise check beside the normwise one: along every axis, each slice (a column of Y, a
+    mode-n slice of H) has max |a - b| within tol times the largest |b| of that slice, so an error
+    confined to small entries or trailing rows cannot hide in the Frobenius norm."""
+    a, b = np.asarray(a), np.asarray(b)
+    for axis in range(b.ndim):
+        for k in range(b.shape[axis]):
+            sa, sb = np.take(a, k, axis=axis), np.take(b, k, axis=axis)
+            m = float(np.max(np.abs(sb)))
+            if m > 0:
+                err = float(np.max(np.abs(sa - sb)))
+                assert err <= tol * m, (axis, k, err / m)
+
+
 def _bf16_problems(d, seed=0):
     """Ragged sizes: n a multiple of 8 (TMA row alignment) but not of the 128/64 tiles."""
     g = np.random.default_rng(200 + d + seed)
@@ -105,6 +119,7 @@ def test_mixed_sketch_matches_oracle(cuda_lib, kind, d):
         ref = _oracle(prob, kind, 5, i)
         for m in range(d):
             assert _rel(Ys[i][m], ref["Y"][m]) <= 1e-5, (kind, d, i, m, _rel(Ys[i][m], ref["Y"][m]))
+            _per_slice(Ys[i][m], ref["Y"][m], 1e-5)
 
 
 @pytest.mark.parametrize("kind", ["krp", "kron"])
@@ -115,6 +130,7 @@ def test_mixed_projection_matches_oracle_given_q(cuda_lib, kind, d):
     Hs = _plan(probs, kind, 6).project([r["Q"] for r in refs])
     for H, r in zip(Hs, refs):
         assert _rel(H, r["H"]) <= 1e-5
+        _per_slice(H, r["H"], 1e-5)
 
 
 def test_mixed_krp_sketch_order3_term_kernel_edges(cuda_lib):
@@ -137,6 +153,7 @@ def test_mixed_krp_sketch_order3_term_kernel_edges(cuda_lib):
         ref = _oracle(prob, "krp", 9, i)
         for m in range(3):
             assert _rel(Ys[i][m], ref["Y"][m]) <= 1e-5, (i, m, _rel(Ys[i][m], ref["Y"][m]))
+            _per_slice(Ys[i][m], ref["Y"][m], 1e-5)
 
 
 @pytest.mark.parametrize("kind", ["krp", "kron"])
@@ -159,6 +176,7 @@ def test_mixed_projection_order3_tile_edges(cuda_lib, kind):
     for H, r in zip(Hs, refs):
         assert H.shape == r["H"].shape
         assert _rel(H, r["H"]) <= 1e-5, _rel(H, r["H"])
+        _per_slice(H, r["H"], 1e-5)
 
 
 @pytest.mark.parametrize("precision", MODES)
