@@ -24,6 +24,9 @@ Also reported on the same JSON line:
                 Kronecker): rate, FP64-path rate, speedup, error against the oracle
   subrank       the effective subrank heuristic (Alg. 5, float64) on the same batch: problems/s,
                 its float64 roofline, and the oracle's rate on a sample
+  backward      config 5: the backward of the sketch-and-project stage (Q fixed) over 152 grad384
+                problems, mixed and float64 paths, their difference and the error against the
+                oracle's gradient
   clocks        nvidia-smi SM clocks and throttle reasons sampled during the timed region
 
 ``--impl reference`` times the FP64 CPU oracle (the reference arm) instead.
@@ -81,6 +84,9 @@ def parse_args():
     ap.add_argument("--extra-steps", type=int, default=5, help="timed steps of each extra workload (mixed)")
     ap.add_argument("--subrank-eps", type=float, default=1e-6, help="tolerance of the Alg. 5 leg")
     ap.add_argument("--subrank-steps", type=int, default=3, help="timed calls of the Alg. 5 leg")
+    ap.add_argument("--no-backward", action="store_true", help="skip the backward (config 5) leg")
+    ap.add_argument("--backward-problems", type=int, default=152, help="grad384 problems per backward call")
+    ap.add_argument("--backward-steps", type=int, default=20, help="timed calls of the mixed backward")
     return ap.parse_args()
 
 
@@ -417,6 +423,70 @@ def extra_workload_leg(args, workload, device, stream, rank, world):
     if rank == 0:
         leg["vs_oracle"] = oracle_errors(res, problems, kind, args.seed, "bf16",
                                          1 if workload.startswith("order4") else 2)
+    return leg
+
+
+def backward_leg(args, device, stream, rank, world):
+    """Config 5 (grad384: d=3, n=384, K=16 terms of rank 16, bf16 inputs, target 32 + 8): the backward
+    of the sketch-and-project stage with Q fixed over a batch of P such problems, on the mixed path
+    (tensor-core products, float32 accumulation) and on the float64 path, with Q and Hbar resident on
+    the device; plus the difference between the two and the error of the first problem against the
+    oracle's float64 gradient."""
+    import torch
+    from paper_2603_13532_gb300 import binding, workloads as wl
+    from oracle import sketch_sum as ss
+    P = args.backward_problems
+    problems = [wl.grad384(seed=20260318 + 1000 * rank + i).problems[0] for i in range(P)]
+    g = np.random.default_rng(args.seed + 7 * rank)
+    Qs = [[np.linalg.qr(g.standard_normal((p.dims[m], p.target[m] + p.oversampling[m])))[0] for m in range(3)]
+          for p in problems]
+    Hbars = [g.standard_normal([p.target[m] + p.oversampling[m] for m in range(3)]) for p in problems]
+    res = {}
+    grads = {}
+    for prec in ("mixed", "fp64"):
+        plan = binding.Plan(problems, kind="krp", precision=prec, seed=args.seed, device=device)
+        Q = plan.pack_bases(Qs)
+        Hb = plan.pack_core(Hbars)
+        dc = torch.zeros(max(1, plan.info.grad_core_elems), dtype=torch.float64, device=device)
+        df = torch.zeros(max(1, plan.info.grad_factor_elems), dtype=torch.float64, device=device)
+        call = lambda: plan.backward_raw(Q, Hb, dc, df)
+        for _ in range(args.warmup):
+            call()
+        plan.sync()
+        steps = args.backward_steps if prec == "mixed" else max(1, args.backward_steps // 5)
+        el = max_over_ranks(time_steps(call, steps, stream), device)
+        plan.sync()
+        res[prec] = {"value": weak_scaling_rate(P, world, steps, el), "unit": "gradients/s",
+                     "ms_per_call": 1e3 * el / steps, "steps": steps}
+        grads[prec] = (dc.clone(), df.clone())
+        res[prec]["gpu_launches_per_call"] = int(plan.info.launches_backward)
+        del plan
+    def rel(a, b):
+        return float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+    leg = {"workload": f"grad384 x{P} (d=3, n=384, K=16, rank 16, bf16 inputs, b=40)",
+           "value": res["mixed"]["value"], "unit": "gradients/s", "ms_per_call": res["mixed"]["ms_per_call"],
+           "steps": res["mixed"]["steps"], "gpu_launches_per_call": res["mixed"]["gpu_launches_per_call"],
+           "fp64_path": res["fp64"], "speedup": res["mixed"]["value"] / res["fp64"]["value"],
+           "rel_diff_vs_fp64": {"dcores": rel(grads["mixed"][0], grads["fp64"][0]),
+                                "dfactors": rel(grads["mixed"][1], grads["fp64"][1])},
+           "timing": "eager launches of tks_project_core_backward with Q, Hbar and the outputs on the device"}
+    if rank == 0:
+        p = problems[0]
+        rG, rU = ss.project_core_vjp(p.terms(), Qs[0], Hbars[0])
+        dc = grads["mixed"][0].cpu().numpy()
+        df = grads["mixed"][1].cpu().numpy()
+        nc = sum(G.size for G in p.cores)
+        ref_c = np.concatenate([G.ravel(order="F") for G in rG])
+        R = [sum(G.shape[m] for G in p.cores) for m in range(3)]
+        off, errs = 0, []
+        for m in range(3):
+            ref_f = np.hstack([rU[k][m] for k in range(p.num_terms)]).ravel(order="F")
+            errs.append(np.linalg.norm(df[off: off + ref_f.size] - ref_f) / np.linalg.norm(ref_f))
+            off += p.dims[m] * R[m]
+        leg["vs_oracle"] = {"dcores": float(np.linalg.norm(dc[:nc] - ref_c) / np.linalg.norm(ref_c)),
+                            "dfactors": float(max(errs)), "problems": 1,
+                            "note": "relative Frobenius error of the first problem's mixed gradients against "
+                                    "the oracle's float64 vector-Jacobian product"}
     return leg
 
 
@@ -782,6 +852,10 @@ def main():
                                                  f"the R x R Gram matrices, LAPACK on all host cores)"}
         del sp
 
+    backward = None
+    if not args.no_backward and args.precision != "fp64":
+        backward = backward_leg(args, device, stream, rank, world)
+
     extra = {}
     for wk in [w for w in args.extra_workloads.split(",") if w]:
         if wk == args.workload or args.precision == "fp64":
@@ -818,6 +892,7 @@ def main():
                 "mixed_f32la": f32la, "workloads": extra or None,
                 "projection_tensor_roofline": projection_tensor_roofline(prof, args.steps, peaks),
                 "subrank": subrank,
+                "backward": backward,
                 "gpu_launches": int(plan.info.launches_recompress) * args.steps,
                 "timing": ("CUDA-graph replays of the whole recompression" if graph is not None
                            else "eager launches") + "; stage times from an eager pass with events (one "

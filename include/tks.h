@@ -131,6 +131,8 @@ typedef struct {
   double flops_fp64;            /* algorithmic flops of QR and ST-HOSVD, all problems */
   int64_t grad_core_elems;      /* float64 elements of the core-gradient buffer (backward) */
   int64_t grad_factor_elems;    /* float64 elements of the factor-gradient buffer (backward) */
+  int32_t launches_backward;    /* kernel launches one tks_project_core_backward enqueues (0: none) */
+  int32_t pad;
 } tks_plan_info_t;
 
 typedef struct {
@@ -206,7 +208,11 @@ TKS_API tks_status tks_truncate_core(tks_plan* plan, void* workspace, const doub
  *            Ucat layout n_n x R_n, term k's columns holding
  *            dL/dU_k^(n) = alpha_k Q_n [ (Hbar x_{j != n} A_kj^T)_(n) G_k,(n)^T ].
  * The A_kn are recomputed from Q_in and the factors (nothing is kept from a forward call).
- * TKS_FP64 plans only (TKS_EUNSUPPORTED otherwise). */
+ * Plans whose problems are all of order 3 (TKS_EUNSUPPORTED otherwise): TKS_FP64 computes in float64
+ * on the CUDA cores; the mixed modes run A_n^T = Ucat_n^T Q_n, Hbar x_1 A_0cat^T, Hbar x_3 A_2cat^T and
+ * dUcat_n^T = Bcat_n^T Q_n^T as bf16 plane products on the tensor cores (hi/mid/lo splits of the float64
+ * and float32 operands, float32 accumulation) and the per-term contractions in float32, writing the
+ * same float64 layouts. */
 TKS_API tks_status tks_project_core_backward(tks_plan* plan, void* workspace, const double* Q_in,
                                              const double* Hbar_in, double* dcores, double* dfactors,
                                              void* stream);

@@ -24,7 +24,8 @@ STEP_KINDS = {0: "omega", 1: "gemm", 2: "reduce", 3: "core_sketch", 4: "qr", 5: 
               8: "core_sketch32", 9: "split", 10: "transpose", 11: "qr32", 12: "svd32", 13: "tsqr32",
               14: "core_sketch3", 15: "chain3", 16: "qr_smem32", 17: "project3",
               18: "sketch3", 19: "qr_reg32", 20: "ttm32", 21: "fold4", 22: "project4",
-              23: "sketch3f", 24: "sketch4", 25: "svd64", 26: "ttm64", 27: "oz_slice", 28: "oz_gemm", 29: "oz_cols", 30: "oz_gram", 31: "chol"}
+              23: "sketch3f", 24: "sketch4", 25: "svd64", 26: "ttm64", 27: "oz_slice", 28: "oz_gemm", 29: "oz_xmax", 30: "oz_gram", 31: "chol",
+              32: "oz_xdig"}
 
 
 class TksError(RuntimeError):
@@ -54,7 +55,8 @@ class PlanInfo_t(ctypes.Structure):
                 ("core_elems", ctypes.c_int64), ("output_elems", ctypes.c_int64),
                 ("num_problems", ctypes.c_int32), ("launches_recompress", ctypes.c_int32),
                 ("flops_lowprec", ctypes.c_double), ("flops_fp64", ctypes.c_double),
-                ("grad_core_elems", ctypes.c_int64), ("grad_factor_elems", ctypes.c_int64)]
+                ("grad_core_elems", ctypes.c_int64), ("grad_factor_elems", ctypes.c_int64),
+                ("launches_backward", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 I32x6 = ctypes.c_int32 * MAX_ORDER

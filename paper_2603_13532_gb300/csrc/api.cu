@@ -49,7 +49,8 @@ Operand op_abs(const void* p, size_t off_bytes = 0) {
 
 enum StepKind { S_OMEGA, S_GEMM, S_REDUCE, S_CORESKETCH, S_QR, S_TSQR64, S_TC, S_SIMT, S_CS32, S_SPLIT,
                 S_TRANSPOSE, S_QR32, S_SVD32, S_TSQR, S_CS3, S_CHAIN3, S_QRSM, S_PROJ3, S_SK3, S_QRREG, S_TTM,
-                S_FOLD4, S_PROJ3F, S_SK3F, S_SK4, S_SVD64, S_TTM64, S_OZSLICE, S_OZGEMM, S_OZCOLS, S_OZGRAM, S_CHOL };
+                S_FOLD4, S_PROJ3F, S_SK3F, S_SK4, S_SVD64, S_TTM64, S_OZSLICE, S_OZGEMM, S_OZXMAX, S_OZGRAM, S_CHOL,
+                S_OZXDIG };
 
 struct Step {
   StepKind kind;
@@ -79,7 +80,7 @@ Step make_step(StepKind kind, size_t off, int njobs, int64_t work, const char* n
 // digit planes and exponents, the Gram matrix, R^-1, the accumulated R, the fallback flag, and the row
 // digit planes and exponents of X and of R^-1.
 struct CqBuffers {
-  size_t X[2], col, colE, G, Rinv, Racc, flag, rowA, rowAE, rowB, rowBE;
+  size_t X[2], col, colE, G, Rinv, Racc, flag, rowA, rowAE, rowB, rowBE, part;
 };
 
 struct ProbHost {
@@ -101,7 +102,7 @@ struct ProbHost {
   size_t T = 0, P[MAXD] = {}, ev[MAXD] = {}, theta = 0, Hp[2] = {};
   size_t R64 = 0, stk64[2] = {};   // float64 ST-HOSVD: triangular factor and TSQR stacks
   size_t ozA = 0, ozQ = 0, ozB = 0, ozEA = 0, ozEQ = 0, ozEB = 0;   // TKS_MIXED mode products: digit planes
-  size_t cqX[2] = {}, cqCol = 0, cqColE = 0, cqG = 0, cqRinv = 0, cqRacc = 0, cqFlag = 0;   // CholeskyQR3
+  size_t cqX[2] = {}, cqCol = 0, cqColE = 0, cqG = 0, cqRinv = 0, cqRacc = 0, cqFlag = 0, cqPart = 0;   // CholeskyQR3
   CqBuffers qcq[MAXD] = {};   // TKS_MIXED: CholeskyQR3 of the sketches Y_n (flag == 0: Householder QR)
   std::vector<size_t> chain;   // 2 ping-pong buffers per term
   // mixed-precision buffers (bytes): bf16 planes and float32 intermediates
@@ -117,6 +118,11 @@ struct ProbHost {
   // backward of the core projection (order 3, float64)
   size_t bZ0 = 0, bZ2 = 0, bB[MAXD] = {};
   std::vector<size_t> bterm;   // per term: Z01, W1, W0
+  // mixed backward: bf16 planes (3 each) of A_n (element (r, a) at a + ldb r), of Hbar with mode 1
+  // (resp. mode 3) index fastest, of Bcat_n (element (a, col) at a + ldb col) and of Q_n transposed
+  // (element (i, a) at a + ldb i); ldb_n = b_n rounded up to 8
+  size_t bAp[MAXD][3] = {}, bHA[3] = {}, bHC[3] = {}, bBp[MAXD][3] = {}, bQT[MAXD][3] = {};
+  int ldb[MAXD] = {};
   int64_t gcore_off = 0, gfac_off[MAXD] = {};
   double flops_low = 0.0, flops_f64 = 0.0;
 };
@@ -429,12 +435,12 @@ namespace {
 // planes, Gram matrix, Cholesky step, row digit planes of X and R^-1, X <- X R^-1]; the third pass
 // ends after its Cholesky step, or with Q = X R^-1 when the caller wants the orthonormal factor.
 struct CqLists {
-  std::vector<OzColSliceJob> cols[3];
+  std::vector<OzXSliceJob> xsl[3];
   std::vector<OzGramJob> gram[3];
   std::vector<CholJob> chol[3];
   std::vector<OzSliceJob> slice[3];
   std::vector<OzGemmJob> gemm[3];
-  int cols_total[3] = {0, 0, 0}, slice_total[3] = {0, 0, 0}, gemm_total[3] = {0, 0, 0};
+  int xsl_total[3] = {0, 0, 0}, slice_total[3] = {0, 0, 0}, gemm_total[3] = {0, 0, 0};
   double gram_flops = 0.0, gemm_flops[3] = {0.0, 0.0, 0.0};
 
   // Rout: where the last pass writes R (B_NONE: not wanted); Qout: where X R^-1 of the last pass goes
@@ -447,23 +453,27 @@ struct CqLists {
     const Operand flag = op(B_WS, B.flag);
     const Operand X[3] = {src, op(B_WS, B.X[0]), op(B_WS, B.X[1])};
     for (int pass = 0; pass < 3; ++pass) {
-      OzColSliceJob cj;
-      std::memset(&cj, 0, sizeof(cj));
-      cj.src = X[pass];
-      cj.planes = op(B_WS, B.col);
-      cj.expo = op(B_WS, B.colE);
-      cj.P = P;
-      cj.L = L;
-      cj.ldP = ldP;
-      cj.b = b;
-      cj.tile_begin = cols_total[pass];
-      cols_total[pass] += b;
-      cols[pass].push_back(cj);
+      OzXSliceJob xj;
+      std::memset(&xj, 0, sizeof(xj));
+      xj.src = X[pass];
+      xj.part = op(B_WS, B.part);
+      xj.expo = op(B_WS, B.colE);
+      xj.colP = op(B_WS, B.col);
+      xj.rowP = op(B_WS, B.rowA);
+      xj.P = P;
+      xj.L = L;
+      xj.ldP = ldP;
+      xj.rows_pad = (P + 7) / 8 * 8;
+      xj.b = b;
+      xj.tiles = oz_xslice_tiles(P);
+      xj.tile_begin = xsl_total[pass];
+      xsl_total[pass] += xj.tiles;
+      xsl[pass].push_back(xj);
       OzGramJob gj;
       std::memset(&gj, 0, sizeof(gj));
       for (int sl = 0; sl < kOzSlices; ++sl)
         gj.map[sl] = plan->map_of(B_WS, B.col + (size_t)sl * 64 * ldP * 2, P, b, ldP, 64);
-      gj.expo = cj.expo;
+      gj.expo = xj.expo;
       gj.G = op(B_WS, B.G);
       gj.P = P;
       gj.b = b;
@@ -476,12 +486,14 @@ struct CqLists {
       ch.Racc = op(B_WS, B.Racc);
       ch.Rout = Rout;
       ch.fallback = flag;
+      ch.xexp = xj.expo;
       ch.P = P;
       ch.b = b;
       ch.pass = pass + 1;
       chol[pass].push_back(ch);
       if (pass == 2 && Qout.base == B_NONE) break;
-      // the next X (or Q) = X Rinv: digits of the rows of X and of the columns of Rinv
+      // the next X (or Q) = X Rinv: X's digits (column exponents, folded into Rinv's rows) and the
+      // digits of the columns of Rinv
       auto slice_job = [&](Operand s_src, size_t planes, size_t expo, int64_t rows, int64_t Ls) {
         OzSliceJob sj;
         std::memset(&sj, 0, sizeof(sj));
@@ -499,7 +511,6 @@ struct CqLists {
         slice[pass].push_back(sj);
         return sj;
       };
-      const OzSliceJob sx = slice_job(X[pass], B.rowA, B.rowAE, P, L);
       const OzSliceJob sr = slice_job(ch.Rinv, B.rowB, B.rowBE, b, 1);
       OzGemmJob g;
       std::memset(&g, 0, sizeof(g));
@@ -511,10 +522,10 @@ struct CqLists {
       g.tile_begin = gemm_total[pass];
       gemm_total[pass] += g.tiles_m;
       for (int sl = 0; sl < kOzSlices; ++sl) {
-        g.mapA[sl] = plan->map_of(B_WS, sx.planes.off + (size_t)sl * sx.rows_pad * ldk * 2, b, P, ldk, 128);
+        g.mapA[sl] = plan->map_of(B_WS, xj.rowP.off + (size_t)sl * xj.rows_pad * ldk * 2, b, P, ldk, 128);
         g.mapB[sl] = plan->map_of(B_WS, sr.planes.off + (size_t)sl * sr.rows_pad * ldk * 2, b, b, ldk, 64);
       }
-      g.expA = sx.expo;
+      g.expA = Operand{B_NONE, 0, 0};
       g.expB = sr.expo;
       g.Y = pass == 2 ? Qout : X[pass + 1];
       g.L = L;
@@ -529,8 +540,10 @@ struct CqLists {
     char nm[32];
     for (int pass = 0; pass < 3; ++pass) {
       if (gram[pass].empty()) break;
-      std::snprintf(nm, sizeof(nm), "%s.cols%d[oz]", tag, pass + 1);
-      plan->push(steps, S_OZCOLS, cols[pass], cols_total[pass], nm);
+      std::snprintf(nm, sizeof(nm), "%s.xmax%d[oz]", tag, pass + 1);
+      plan->push(steps, S_OZXMAX, xsl[pass], xsl_total[pass], nm);
+      std::snprintf(nm, sizeof(nm), "%s.xdig%d[oz]", tag, pass + 1);
+      plan->push(steps, S_OZXDIG, xsl[pass], xsl_total[pass], nm);
       std::snprintf(nm, sizeof(nm), "%s.gram%d[oz]", tag, pass + 1);
       plan->push(steps, S_OZGRAM, gram[pass], (int64_t)gram[pass].size(), nm, gram_flops / 3.0, 0.0);
       std::snprintf(nm, sizeof(nm), "%s.chol%d", tag, pass + 1);
@@ -1360,6 +1373,208 @@ static void build_backward3(tks_plan* plan) {
   plan->push_gemm(plan->st_backward, du, "bwd:dU=Q.B");
 }
 
+// The same backward for mixed-precision plans (order 3): the contractions over a basis index with a
+// large partner dimension run on the tensor cores as bf16 plane products (hi/mid/lo splits of float64
+// and float32 operands, six products up to second order, float32 accumulation in TMEM), the small
+// per-term ones in float32 on the CUDA cores:
+//   [tc]   A_n^T = Ucat_n^T Q_n (float32, and A_n as planes with the basis index fastest)
+//   [tc]   Z0 = Hbar x_1 A_0cat^T,  Z2^T = (Hbar x_3 A_2cat^T)^T
+//   [f32]  Z01, W1, W0, then dG_k (float64 out) and B_kn (written as planes of Bcat_n)
+//   [tc]   dUcat_n^T = Bcat_n^T Q_n^T (float64 out)
+static void simt_set(SimtJob& j, int M, int N, int K, Operand A, int32_t at, int64_t a_m, int64_t a_k0, Operand B,
+                     int32_t bt, int64_t b_n, int64_t b_k0, int64_t c_m, int64_t c_n, float alpha) {
+  std::memset(&j, 0, sizeof(j));
+  j.M = M; j.N = N; j.K = K; j.K1 = K; j.batch = 1;
+  j.A = A; j.a_type = at; j.a_m = a_m; j.a_k0 = a_k0;
+  j.B = B; j.b_type = bt; j.b_n = b_n; j.b_k0 = b_k0;
+  j.c_m = c_m; j.c_n = c_n;
+  j.alpha = alpha;
+}
+
+static void build_backward3_mixed(tks_plan* plan) {
+  std::vector<SplitJob> sp;
+  int64_t sp_total = 0;
+  std::vector<TcJob> tcA, tcZ, tcU;
+  std::vector<SimtJob> step1, step2;
+  auto split = [&](Operand src, const size_t* dst, int64_t rows, int64_t cols, int64_t ld_src, int64_t ld_dst,
+                   int trans) {
+    SplitJob sj;
+    std::memset(&sj, 0, sizeof(sj));
+    sj.src = src;
+    for (int t = 0; t < 3; ++t) sj.dst[t] = op(B_WS, dst[t]);
+    sj.rows = rows;
+    sj.cols = cols;
+    sj.ld_src = ld_src;
+    sj.ld_dst = ld_dst;
+    sj.trans = trans;
+    sj.count = rows * cols;
+    sj.begin = sp_total;
+    sp_total += sj.count;
+    sp.push_back(sj);
+  };
+  auto tc6 = [](TcJob& j) {
+    const uint8_t pa[6] = {0, 0, 1, 0, 2, 1}, pb[6] = {0, 1, 0, 2, 0, 1};
+    j.na = j.nb = 3;
+    j.npairs = 6;
+    for (int t = 0; t < 6; ++t) {
+      j.pa[t] = pa[t];
+      j.pb[t] = pb[t];
+    }
+  };
+  for (auto& h : plan->probs) {
+    const int b0 = h.b[0], b1 = h.b[1], b2 = h.b[2];
+    const int R0 = h.R[0], R2 = h.R[2];
+    const Operand Hbar = op(B_HBAR, h.h_off * 8);
+    // planes of Q_n (row i fastest, for A_n^T) and of Q_n^T (basis index fastest, for dU), of Hbar
+    // with the mode-1 index fastest (Z0) and with the mode-3 index fastest (Z2)
+    for (int n = 0; n < 3; ++n) {
+      const int64_t nn = h.n[n];
+      split(op(B_Q, h.q_off[n] * 8), h.Qp[n], nn, h.b[n], nn, nn, 0);
+      split(op(B_Q, h.q_off[n] * 8), h.bQT[n], nn, h.b[n], nn, h.ldb[n], 1);
+    }
+    split(Hbar, h.bHA, b0, (int64_t)b1 * b2, b0, h.ldb[0], 0);
+    split(Hbar, h.bHC, (int64_t)b0 * b1, b2, (int64_t)b0 * b1, h.ldb[2], 1);
+    // A_n^T = Ucat_n^T Q_n: exact bf16 factors times the three planes of Q_n
+    for (int n = 0; n < 3; ++n) {
+      const int64_t nn = h.n[n];
+      TcJob j;
+      std::memset(&j, 0, sizeof(j));
+      j.M = h.R[n]; j.N = h.b[n]; j.K = (int)nn;
+      j.epi.alpha = 1.0f;
+      j.na = 1; j.nb = 3; j.npairs = 3;
+      j.mapA[0] = plan->map_of(B_ABS, reinterpret_cast<uintptr_t>(h.factors[n]), nn, h.R[n], nn, 128);
+      for (int t = 0; t < 3; ++t) {
+        j.mapB[t] = plan->map_of(B_WS, h.Qp[n][t], nn, h.b[n], nn, 64);
+        j.pa[t] = 0;
+        j.pb[t] = (uint8_t)t;
+      }
+      j.epi.has_f32 = 1;
+      j.epi.f32 = op(B_WS, h.AT32[n]);
+      j.epi.f32_m = 1;
+      j.epi.f32_n = h.R[n];
+      j.epi.nbf = 3;
+      for (int t = 0; t < 3; ++t) j.epi.bf[t] = op(B_WS, h.bAp[n][t]);
+      j.epi.bf_m = h.ldb[n];
+      j.epi.bf_n = 1;
+      tcA.push_back(j);
+    }
+    // Z0[i + R0 J] = sum_a A_0[a, i] Hbar[a + b0 J]   (M = R0, N = b1 b2, K = b0)
+    {
+      TcJob j;
+      std::memset(&j, 0, sizeof(j));
+      j.M = R0; j.N = b1 * b2; j.K = b0;
+      j.epi.alpha = 1.0f;
+      tc6(j);
+      for (int t = 0; t < 3; ++t) {
+        j.mapA[t] = plan->map_of(B_WS, h.bAp[0][t], b0, R0, h.ldb[0], 128);
+        j.mapB[t] = plan->map_of(B_WS, h.bHA[t], b0, (uint64_t)b1 * b2, h.ldb[0], 64);
+      }
+      j.epi.has_f32 = 1;
+      j.epi.f32 = op(B_WS, h.bZ0);
+      j.epi.f32_m = 1;
+      j.epi.f32_n = R0;
+      tcZ.push_back(j);
+    }
+    // Z2[J01 + b0 b1 i] = sum_a Hbar[J01 + b0 b1 a] A_2[a, i]   (as Z2^T: M = R2, N = b0 b1, K = b2)
+    {
+      TcJob j;
+      std::memset(&j, 0, sizeof(j));
+      j.M = R2; j.N = b0 * b1; j.K = b2;
+      j.epi.alpha = 1.0f;
+      tc6(j);
+      for (int t = 0; t < 3; ++t) {
+        j.mapA[t] = plan->map_of(B_WS, h.bAp[2][t], b2, R2, h.ldb[2], 128);
+        j.mapB[t] = plan->map_of(B_WS, h.bHC[t], b2, (uint64_t)b0 * b1, h.ldb[2], 64);
+      }
+      j.epi.has_f32 = 1;
+      j.epi.f32 = op(B_WS, h.bZ2);
+      j.epi.f32_m = (int64_t)b0 * b1;
+      j.epi.f32_n = 1;
+      tcZ.push_back(j);
+    }
+    // per term (rank offsets o_n); A_n[a, r] = AT32_n[r + R_n a]
+    for (int k = 0; k < h.K; ++k) {
+      const int* r = &h.ranks[(size_t)k * 3];
+      const int o0 = h.roff[(size_t)k * 3], o1 = h.roff[(size_t)k * 3 + 1], o2 = h.roff[(size_t)k * 3 + 2];
+      const float al = (float)h.alpha[k];
+      const Operand Z0k = op(B_WS, h.bZ0 + (size_t)o0 * 4);
+      const Operand Z2k = op(B_WS, h.bZ2 + (size_t)b0 * b1 * o2 * 4);
+      const Operand A0k = op(B_WS, h.AT32[0] + (size_t)o0 * 4);
+      const Operand A1k = op(B_WS, h.AT32[1] + (size_t)o1 * 4);
+      const Operand A2k = op(B_WS, h.AT32[2] + (size_t)o2 * 4);
+      const int64_t R1 = h.R[1];
+      const Operand Gk = op_abs(h.cores, (size_t)h.core_off[k] * 2);
+      const Operand Z01 = op(B_WS, h.bterm[3 * k]), W1 = op(B_WS, h.bterm[3 * k + 1]);
+      const Operand W0 = op(B_WS, h.bterm[3 * k + 2]);
+      SimtJob g;
+      // Z01[i0 + r0 i1 + r0 r1 j2] = sum_j1 Z0k[i0 + R0 j1 + R0 b1 j2] A_1[j1, o1 + i1]
+      simt_set(g, r[0], r[1], b1, Z0k, T_F32, 1, R0, A1k, T_F32, 1, R1, 1, r[0], 1.0f);
+      g.batch = b2; g.a_b = (int64_t)R0 * b1; g.c_b = (int64_t)r[0] * r[1];
+      g.has_c32 = 1; g.c32 = Z01;
+      step1.push_back(g);
+      // W1[i0 + r0 j1 + r0 b1 i2] = sum_j2 Z0k[i0 + R0 j1 + R0 b1 j2] A_2[j2, o2 + i2]
+      simt_set(g, r[0], r[2], b2, Z0k, T_F32, 1, (int64_t)R0 * b1, A2k, T_F32, 1, R2, 1, (int64_t)r[0] * b1, 1.0f);
+      g.batch = b1; g.a_b = R0; g.c_b = r[0];
+      g.has_c32 = 1; g.c32 = W1;
+      step1.push_back(g);
+      // W0[j0 + b0 i1 + b0 r1 i2] = sum_j1 Z2k[j0 + b0 j1 + b0 b1 i2] A_1[j1, o1 + i1]
+      simt_set(g, b0, r[1], b1, Z2k, T_F32, 1, b0, A1k, T_F32, 1, R1, 1, b0, 1.0f);
+      g.batch = r[2]; g.a_b = (int64_t)b0 * b1; g.c_b = (int64_t)b0 * r[1];
+      g.has_c32 = 1; g.c32 = W0;
+      step1.push_back(g);
+      // dG_k[J + r0 r1 i2] = alpha sum_j2 Z01[J + r0 r1 j2] A_2[j2, o2 + i2]
+      simt_set(g, r[0] * r[1], r[2], b2, Z01, T_F32, 1, (int64_t)r[0] * r[1], A2k, T_F32, 1, R2, 1,
+               (int64_t)r[0] * r[1], al);
+      g.has_c64 = 1; g.c64 = op(B_DCORE, (size_t)(h.gcore_off + h.core_off[k]) * 8);
+      step2.push_back(g);
+      // Bcat_2[j2, o2 + i2] = alpha sum_J Z01[J + r0 r1 j2] G[J + r0 r1 i2]
+      simt_set(g, b2, r[2], r[0] * r[1], Z01, T_F32, (int64_t)r[0] * r[1], 1, Gk, T_BF16, (int64_t)r[0] * r[1], 1, 1,
+               h.ldb[2], al);
+      g.nbf = 3;
+      for (int t = 0; t < 3; ++t) g.cb[t] = op(B_WS, h.bBp[2][t] + (size_t)h.ldb[2] * o2 * 2);
+      step2.push_back(g);
+      // Bcat_1[j1, o1 + i1] = alpha sum_{i0, i2} W1[i0 + r0 j1 + r0 b1 i2] G[i0 + r0 i1 + r0 r1 i2]
+      simt_set(g, b1, r[1], r[0] * r[2], W1, T_F32, r[0], 1, Gk, T_BF16, r[0], 1, 1, h.ldb[1], al);
+      g.K1 = r[0];
+      g.a_k1 = (int64_t)r[0] * b1;
+      g.b_k1 = (int64_t)r[0] * r[1];
+      g.nbf = 3;
+      for (int t = 0; t < 3; ++t) g.cb[t] = op(B_WS, h.bBp[1][t] + (size_t)h.ldb[1] * o1 * 2);
+      step2.push_back(g);
+      // Bcat_0[j0, o0 + i0] = alpha sum_{i1, i2} W0[j0 + b0 (i1 + r1 i2)] G[i0 + r0 (i1 + r1 i2)]
+      simt_set(g, b0, r[0], r[1] * r[2], W0, T_F32, 1, b0, Gk, T_BF16, 1, r[0], 1, h.ldb[0], al);
+      g.nbf = 3;
+      for (int t = 0; t < 3; ++t) g.cb[t] = op(B_WS, h.bBp[0][t] + (size_t)h.ldb[0] * o0 * 2);
+      step2.push_back(g);
+      (void)A0k;
+    }
+    // dUcat_n^T = Bcat_n^T Q_n^T: dfac[i + n col] (M = R_n, N = n_n, K = b_n)
+    for (int n = 0; n < 3; ++n) {
+      const int64_t nn = h.n[n];
+      TcJob j;
+      std::memset(&j, 0, sizeof(j));
+      j.M = h.R[n]; j.N = (int)nn; j.K = h.b[n];
+      j.epi.alpha = 1.0f;
+      tc6(j);
+      for (int t = 0; t < 3; ++t) {
+        j.mapA[t] = plan->map_of(B_WS, h.bBp[n][t], h.b[n], h.R[n], h.ldb[n], 128);
+        j.mapB[t] = plan->map_of(B_WS, h.bQT[n][t], h.b[n], nn, h.ldb[n], 64);
+      }
+      j.epi.has_f64 = 1;
+      j.epi.f64 = op(B_DFAC, (size_t)h.gfac_off[n] * 8);
+      j.epi.f64_m = nn;
+      j.epi.f64_n = 1;
+      tcU.push_back(j);
+    }
+  }
+  plan->push(plan->st_backward, S_SPLIT, sp, sp_total, "bwd:Q,Hbar->planes", 0.0, 14.0 * sp_total);
+  plan->push_tc(plan->st_backward, tcA, "bwd:AT=UcatT.Q[tc]");
+  plan->push_tc(plan->st_backward, tcZ, "bwd:Z=Hbar.Acat[tc]");
+  plan->push_simt(plan->st_backward, step1, "bwd:per-term1[f32]");
+  plan->push_simt(plan->st_backward, step2, "bwd:per-term2[f32]");
+  plan->push_tc(plan->st_backward, tcU, "bwd:dUT=BT.QT[tc]");
+}
+
 }  // namespace
 
 // ST-HOSVD of H in float64 (TKS_FP64 and TKS_MIXED; Alg. 2 phase 2, modes 1..d in order): per mode,
@@ -1394,7 +1609,7 @@ static void build_hosvd_f64(tks_plan* plan) {
       Operand gate{B_NONE, 0, 0};
       if (cholqr) {
         const CqBuffers B{{h.cqX[0], h.cqX[1]}, h.cqCol, h.cqColE, h.cqG, h.cqRinv, h.cqRacc, h.cqFlag,
-                          h.ozA, h.ozEA, h.ozB, h.ozEB};
+                          h.ozA, h.ozEA, h.ozB, h.ozEB, h.cqPart};
         gate = cq.add(plan, X, L * Rr, L, b, B, op(B_WS, h.R64), Operand{B_NONE, 0, 0});
       }
       // TSQR of H_(n)^T: element (l + L rr, c) at l + L c + L b rr.  Level 0 factors blocks of dense
@@ -1693,7 +1908,7 @@ tks_status tks_plan_create(tks_plan** out, const tks_problem* problems, int32_t 
       plan->grad_factor_elems += h.n[m] * h.R[m];
     }
   }
-  plan->backward_ok = !mixed;
+  plan->backward_ok = true;
   for (auto& h : plan->probs)
     if (h.d != 3) plan->backward_ok = false;
   plan->ws_omega = alloc(plan->omega_elems * 8);
@@ -1738,6 +1953,7 @@ tks_status tks_plan_create(tks_plan** out, const tks_problem* problems, int32_t 
           B.rowAE = alloc((size_t)rows8 * 4);
           B.rowB = alloc((size_t)kOzSlices * 64 * 64 * 2);
           B.rowBE = alloc(64 * 4);
+          B.part = alloc((size_t)ceil_div(h.n[m], 64) * 64 * 4);
         }
       }
     }
@@ -1796,6 +2012,20 @@ tks_status tks_plan_create(tks_plan** out, const tks_problem* problems, int32_t 
         h.bterm[3 * k + 1] = alloc((size_t)r[0] * h.b[1] * r[2] * 8);
         h.bterm[3 * k + 2] = alloc((size_t)h.b[0] * r[1] * r[2] * 8);
       }
+      if (mixed) {
+        for (int m = 0; m < 3; ++m) {
+          h.ldb[m] = (h.b[m] + 7) / 8 * 8;
+          for (int t = 0; t < 3; ++t) {
+            h.bAp[m][t] = alloc((size_t)h.R[m] * h.ldb[m] * 2);
+            h.bBp[m][t] = alloc((size_t)h.R[m] * h.ldb[m] * 2);
+            h.bQT[m][t] = alloc((size_t)h.n[m] * h.ldb[m] * 2);
+          }
+        }
+        for (int t = 0; t < 3; ++t) {
+          h.bHA[t] = alloc((size_t)h.b[1] * h.b[2] * h.ldb[0] * 2);
+          h.bHC[t] = alloc((size_t)h.b[0] * h.b[1] * h.ldb[2] * 2);
+        }
+      }
     }
     if (!f32la) {
       // float64 TSQR stacks: at most ceil(rows / block) factors of b rows per level
@@ -1840,6 +2070,7 @@ tks_status tks_plan_create(tks_plan** out, const tks_problem* problems, int32_t 
           h.cqRinv = alloc(64 * 64 * 8);
           h.cqRacc = alloc(64 * 64 * 8);
           h.cqFlag = alloc(4);
+          h.cqPart = alloc((size_t)ceil_div(fib, 64) * 64 * 4);
         }
       }
     }
@@ -1867,6 +2098,7 @@ tks_status tks_plan_create(tks_plan** out, const tks_problem* problems, int32_t 
   plan->lane_p1 = num_problems;
   if (mixed) {
     build_mixed_stages(plan, kron, f32la);
+    if (plan->backward_ok) build_backward3_mixed(plan);
   } else {
   std::vector<OmegaJob> om_ext, om_int;
   int64_t om_blocks = 0;
@@ -2141,6 +2373,7 @@ tks_status tks_plan_info(const tks_plan* plan, tks_plan_info_t* info) {
   info->flops_lowprec = plan->flops_low;
   info->flops_fp64 = plan->flops_f64;
   info->grad_core_elems = plan->grad_core_elems;
+  info->launches_backward = plan->backward_ok ? (int32_t)plan->st_backward.size() : 0;
   info->grad_factor_elems = plan->grad_factor_elems;
   return TKS_OK;
 }
@@ -2212,8 +2445,11 @@ tks_status run_steps(tks_plan* plan, const std::vector<Step>& steps, const Bases
         launch_oz_gemm(static_cast<const OzGemmJob*>(table), s.njobs, (int)s.work, plan->arena_dev + plan->maps_off,
                        bases, plan->status, plan->wait_cycles, stream);
         break;
-      case S_OZCOLS:
-        launch_oz_colslice(static_cast<const OzColSliceJob*>(table), s.njobs, (int)s.work, bases, stream);
+      case S_OZXMAX:
+        launch_oz_xmax(static_cast<const OzXSliceJob*>(table), s.njobs, (int)s.work, bases, stream);
+        break;
+      case S_OZXDIG:
+        launch_oz_xdig(static_cast<const OzXSliceJob*>(table), s.njobs, (int)s.work, bases, stream);
         break;
       case S_OZGRAM:
         launch_oz_gram(static_cast<const OzGramJob*>(table), s.njobs, plan->arena_dev + plan->maps_off, bases,
@@ -2494,7 +2730,7 @@ tks_status tks_project_core_backward(tks_plan* plan, void* workspace, const doub
   tks_status st = check_ws(plan, workspace);
   if (st != TKS_OK) return st;
   if (!plan->backward_ok)
-    return fail(TKS_EUNSUPPORTED, "tks_project_core_backward needs a TKS_FP64 plan of order-3 problems");
+    return fail(TKS_EUNSUPPORTED, "tks_project_core_backward needs a plan of order-3 problems");
   if (!Q_in || !Hbar_in || !dcores || !dfactors) return fail(TKS_EINVAL, "null Q_in, Hbar_in, dcores or dfactors");
   Bases b = bind(plan, workspace);
   b.p[B_Q] = reinterpret_cast<char*>(const_cast<double*>(Q_in));

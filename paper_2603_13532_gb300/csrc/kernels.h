@@ -114,10 +114,11 @@ void launch_oz_slice(const OzSliceJob* jobs, int njobs, int total_tiles, const B
 cudaError_t prepare_oz_gemm();
 void launch_oz_gemm(const OzGemmJob* jobs, int njobs, int total_tiles, const void* maps, const Bases& bases,
                     Status* status, long long wait_cycles, cudaStream_t stream);
-// Shifted CholeskyQR3 with float64-accurate Gram matrices: column digit planes (one CTA per column),
-// G = X^T X (one CTA per job), and the small Cholesky steps (one CTA per job).
-void launch_oz_colslice(const OzColSliceJob* jobs, int njobs, int total_cols, const Bases& bases,
-                        cudaStream_t stream);
+// Shifted CholeskyQR3 with float64-accurate Gram matrices: column exponents and digit planes of X
+// (64-row tiles), G = X^T X (one CTA per job), and the small Cholesky steps (one CTA per job).
+int oz_xslice_tiles(int64_t rows);
+void launch_oz_xmax(const OzXSliceJob* jobs, int njobs, int total_tiles, const Bases& bases, cudaStream_t stream);
+void launch_oz_xdig(const OzXSliceJob* jobs, int njobs, int total_tiles, const Bases& bases, cudaStream_t stream);
 void launch_oz_gram(const OzGramJob* jobs, int njobs, const void* maps, const Bases& bases, Status* status,
                     long long wait_cycles, cudaStream_t stream);
 void launch_chol_step(const CholJob* jobs, int njobs, const Bases& bases, Status* status, cudaStream_t stream);

@@ -783,98 +783,120 @@ size_t ttm64_smem(int bmax) {
 // of its diagonal entry (passes 2, 3: X R^-1 is too ill-conditioned for CholeskyQR2, e.g. a rank-
 // deficient unfolding) sets *fallback, and the Householder TSQR factors X instead; later passes of a
 // failed job only write an identity Rinv.
+//
+// Layout: thread (r, ty) = (threadIdx % 64, threadIdx / 64) owns row r of every triangle and the
+// columns c = ty (mod 4), so a warp reads one column of the pivot row (a broadcast) and 32 consecutive
+// rows of the matrix it updates (no bank conflicts), and every elimination step costs one barrier.
+// The factor is kept as G = U^T D^-1 U with U's rows unscaled (d_j = U[j][j], the pivots), so a step
+// needs no square root:  R = D^-1/2 U,  R^-1 = Z D^-1/2 with Z the inverse of the unit triangle D^-1 U.
 constexpr int kCholThreads = 256;
+constexpr size_t kCholSmem = (3 * 64 * 65 + 2 * 64) * sizeof(double);
 
 __global__ void __launch_bounds__(kCholThreads) chol_step_kernel(const CholJob* __restrict__ jobs, Bases bases,
                                                                 Status* status) {
   extern __shared__ double cs64[];
   const CholJob& J = jobs[blockIdx.x];
   const int b = J.b, ld = b + 1;
-  double* A = cs64;                 // G, then R in its upper triangle (row i, column c at i + ld c)
-  double* Ri = A + b * ld;          // R^-1
-  double* T = Ri + b * ld;          // R Racc
-  double* dg = T + b * ld;          // the diagonal of G
+  double* A = cs64;                 // G, then U (upper triangle), then R (zero below the diagonal)
+  double* Z = A + b * ld;           // (D^-1 U)^-1, unit upper triangular
+  double* Ra = Z + b * ld;          // Racc of the previous passes
+  double* dv = Ra + b * ld;         // pivots d_j
+  double* dg = dv + 64;             // the diagonal of G
+  __shared__ double rdv[64];        // 1 / d_j
   __shared__ int sh_fail;
-  __shared__ double sh_shift;
+  const int r = threadIdx.x & 63, ty = threadIdx.x >> 6;
   int32_t* fb = at<int32_t>(bases, J.fallback);
   double* Rinv = at<double>(bases, J.Rinv);
+  double* Racc = at<double>(bases, J.Racc);
   const double* G = at<const double>(bases, J.G);
   if (threadIdx.x == 0) sh_fail = J.pass == 1 ? 0 : *fb;
-  for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+  for (int e = threadIdx.x; e < b * b; e += kCholThreads) {
     const int i = e % b, c = e / b;
     A[i + ld * c] = G[e];
+    Z[i + ld * c] = i == c ? 1.0 : 0.0;
+    if (J.pass > 1) Ra[i + ld * c] = Racc[e];
     if (i == c) dg[i] = G[e];
   }
   __syncthreads();
-  if (!sh_fail) {
-    if (J.pass == 1) {
-      if (threadIdx.x == 0) {
-        double tr = 0.0;
-        for (int i = 0; i < b; ++i) tr += dg[i];
-        sh_shift = 11.0 * ((double)J.P * b + (double)b * (b + 1)) * 1.1102230246251565e-16 * tr;
-        if (!isfinite(tr)) sh_fail = 1;
-      }
-      __syncthreads();
-      for (int i = threadIdx.x; i < b; i += blockDim.x) A[i + ld * i] += sh_shift;
-      __syncthreads();
-    }
-    // right-looking Cholesky G = R^T R, R upper triangular (row j of R replaces row j of G)
-    for (int j = 0; j < b && !sh_fail; ++j) {
-      if (threadIdx.x == 0) {
-        const double d = A[j + ld * j];
-        const double bound = J.pass == 1 ? 0.0 : 1e-12 * dg[j];
-        if (!(d > bound) || !isfinite(d)) sh_fail = 1;
-        else A[j + ld * j] = sqrt(d);
-      }
-      __syncthreads();
-      if (sh_fail) break;
-      const double rjj = A[j + ld * j];
-      for (int c = j + 1 + threadIdx.x; c < b; c += blockDim.x) A[j + ld * c] /= rjj;
-      __syncthreads();
-      const int w = b - j - 1;   // trailing block rows/columns j+1..b-1, upper part
-      for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
-        const int r = j + 1 + e % w, c = j + 1 + e / w;
-        if (r <= c) A[r + ld * c] = fma(-A[j + ld * r], A[j + ld * c], A[r + ld * c]);
-      }
-      __syncthreads();
-    }
+  bool fail = sh_fail != 0;         // the same value in every thread from here on
+  if (!fail && J.pass == 1) {
+    double tr = 0.0;
+    for (int i = 0; i < b; ++i) tr += dg[i];
+    const double shift = 11.0 * ((double)J.P * b + (double)b * (b + 1)) * 1.1102230246251565e-16 * tr;
+    fail = !isfinite(tr);
+    if (!fail && ty == 0 && r < b) A[r + ld * r] += shift;
+    __syncthreads();
   }
-  __syncthreads();
-  if (sh_fail) {
+  // right-looking elimination: step j takes the pivot d = U[j][j] and updates rows r > j,
+  // A[r][c] -= (A[j][r] / d) A[j][c] for r <= c; every thread reads the same pivot, so all leave together.
+  // The float64 pipe is the scarce unit here, so each step's one division is taken by the thread that
+  // finished the next pivot in the step before (1 / A[0][0] up front), and the rows use its reciprocal.
+  if (!fail && threadIdx.x == 0) rdv[0] = 1.0 / A[0];
+  if (!fail) __syncthreads();
+  for (int j = 0; j < b && !fail; ++j) {
+    const double d = A[j + ld * j];
+    const double bound = J.pass == 1 ? 0.0 : 1e-12 * dg[j];
+    if (!(d > bound) || !isfinite(d)) {
+      fail = true;
+      break;
+    }
+    if (threadIdx.x == 0) dv[j] = d;
+    if (r > j && r < b) {
+      const double f = A[j + ld * r] * rdv[j];
+      // c runs over one residue mod 4 from j + 1 for the whole warp: A[j][c] is a broadcast and the
+      // warp's rows r are consecutive words
+      for (int c = j + 1 + ((ty - j - 1) & 3); c < b; c += 4) {
+        if (c < r) continue;
+        const double v = fma(-f, A[j + ld * c], A[r + ld * c]);
+        A[r + ld * c] = v;
+        if (c == r && r == j + 1) rdv[r] = 1.0 / v;
+      }
+    }
+    __syncthreads();
+  }
+  if (fail) {
     // this job takes the Householder fallback: an identity Rinv keeps the following products harmless
-    for (int e = threadIdx.x; e < b * b; e += blockDim.x) Rinv[e] = (e % b == e / b) ? 1.0 : 0.0;
+    for (int e = threadIdx.x; e < b * b; e += kCholThreads) Rinv[e] = (e % b == e / b) ? 1.0 : 0.0;
     if (threadIdx.x == 0) *fb = 1;
     return;
   }
-  // R^-1 by rows from the bottom: Ri[i][c] = (delta_ic - sum_{i<k<=c} R[i][k] Ri[k][c]) / R[i][i],
-  // four threads per column of the row
-  for (int i = b - 1; i >= 0; --i) {
-    const int c = i + (int)(threadIdx.x >> 2), part = threadIdx.x & 3;
-    double acc = 0.0;
-    if (c < b)
-      for (int k = i + 1 + part; k <= c; k += 4) acc = fma(A[i + ld * k], Ri[k + ld * c], acc);
-    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-    if (c < b && part == 0) Ri[i + ld * c] = ((c == i ? 1.0 : 0.0) - acc) / A[i + ld * i];
+  // Z from the bottom: step k subtracts (U[i][k] / d_i) Z[k][:] from the rows i < k (row k is final)
+  const double inv_d = r < b ? rdv[r] : 0.0;
+  for (int k = b - 1; k > 0; --k) {
+    if (r < k) {
+      const double u = A[r + ld * k] * inv_d;
+      for (int c = k + ((ty - k) & 3); c < b; c += 4) Z[r + ld * c] = fma(-u, Z[k + ld * c], Z[r + ld * c]);
+    }
     __syncthreads();
   }
-  for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
-    const int i = e % b, c = e / b;
-    Rinv[e] = i <= c ? Ri[i + ld * c] : 0.0;
-  }
-  // Racc <- R Racc (both upper triangular)
-  double* Racc = at<double>(bases, J.Racc);
-  for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
-    const int i = e % b, c = e / b;
-    double acc = 0.0;
-    if (J.pass == 1) acc = i <= c ? A[i + ld * c] : 0.0;
-    else
-      for (int k = i; k <= c; ++k) acc = fma(A[i + ld * k], Racc[k + b * c], acc);
-    T[i + ld * c] = i <= c ? acc : 0.0;
+  // R = D^-1/2 U in place, Rinv = Z D^-1/2 (row a times 2^xexp[a] when X's digits carry column exponents)
+  __shared__ int xe[64];
+  if (threadIdx.x < b) {
+    dg[threadIdx.x] = sqrt(rdv[threadIdx.x]);
+    xe[threadIdx.x] = J.xexp.base != B_NONE ? at<const int32_t>(bases, J.xexp)[threadIdx.x] : 0;
   }
   __syncthreads();
+  for (int e = threadIdx.x; e < b * b; e += kCholThreads) {
+    const int i = e % b, c = e / b;
+    A[i + ld * c] = i <= c ? A[i + ld * c] * dg[i] : 0.0;
+    Rinv[e] = i <= c ? scalbn(Z[i + ld * c] * dg[c], xe[i]) : 0.0;
+  }
+  __syncthreads();
+  // Racc <- R Racc (pass 1: Racc = R); the last pass writes it to Rout when one is given
   double* out = (J.pass == 3 && J.Rout.base != B_NONE) ? at<double>(bases, J.Rout) : Racc;
-  for (int e = threadIdx.x; e < b * b; e += blockDim.x) out[e] = T[(e % b) + ld * (e / b)];
+  if (r < b) {
+    for (int c = ty; c < b; c += 4) {
+      double acc;
+      if (J.pass == 1) {
+        acc = A[r + ld * c];
+      } else {
+        // R and Racc are upper triangular: k runs over r..c
+        acc = 0.0;
+        for (int k = r; k <= c; ++k) acc = fma(A[r + ld * k], Ra[k + ld * c], acc);
+      }
+      out[r + b * c] = acc;
+    }
+  }
   if (J.pass == 1 && threadIdx.x == 0) *fb = 0;
   (void)status;
 }
@@ -886,7 +908,7 @@ int tsqr64_block_rows(int max_cols) { return max_cols <= 64 ? 256 : 192; }
 
 cudaError_t prepare_la64(int bmax) {
   cudaError_t e0 = cudaFuncSetAttribute(chol_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)((3 * 64 * 65 + 64) * sizeof(double)));
+                                        (int)kCholSmem);
   if (e0 != cudaSuccess) return e0;
   cudaError_t e = cudaFuncSetAttribute(svd_jacobi_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)svd64_smem(bmax));
@@ -953,8 +975,7 @@ void launch_ttm_f64(const TtmJob* jobs, int njobs, int total_tiles, int max_cols
 }
 
 void launch_chol_step(const CholJob* jobs, int njobs, const Bases& bases, Status* status, cudaStream_t stream) {
-  const size_t smem = (size_t)(3 * 64 * 65 + 64) * sizeof(double);
-  chol_step_kernel<<<njobs, kCholThreads, smem, stream>>>(jobs, bases, status);
+  chol_step_kernel<<<njobs, kCholThreads, kCholSmem, stream>>>(jobs, bases, status);
 }
 
 }  // namespace tks

@@ -379,7 +379,7 @@ __global__ void split_f64_kernel(const SplitJob* __restrict__ jobs, int njobs, i
     const double v = at<double>(bases, J.src)[i + J.ld_src * j];
     uint16_t h0, h1, h2;
     split3(v, h0, h1, h2);
-    const int64_t off = i + J.ld_dst * j;
+    const int64_t off = J.trans ? j + J.ld_dst * i : i + J.ld_dst * j;
     at<uint16_t>(bases, J.dst[0])[off] = h0;
     at<uint16_t>(bases, J.dst[1])[off] = h1;
     at<uint16_t>(bases, J.dst[2])[off] = h2;

@@ -29,6 +29,14 @@ constexpr int kOzSliceThreads = 256;
 constexpr int kOzMaxK = TKS_MAX_BASIS;
 
 // ----------------------------------------------------------------------------- slicing
+// bfloat16 bits of a digit d in [0, 127] carrying the sign of x, by full-rate integer and float32
+// operations (the int -> float -> bfloat16 conversions run at a quarter of that rate): 2^23 + d is
+// exact in float32, subtracting 2^23 leaves d, and d's float32 bits end in sixteen zeros.  Zero is +0.
+__device__ __forceinline__ uint16_t oz_bf16_digit(int d, bool neg) {
+  const float f = __int_as_float(0x4B000000 | d) - 8388608.0f;
+  return (uint16_t)((__float_as_uint(f) >> 16) | ((neg && d) ? 0x8000u : 0u));
+}
+
 __global__ void __launch_bounds__(kOzSliceThreads) oz_slice_kernel(const OzSliceJob* __restrict__ jobs, int njobs,
                                                                   Bases bases) {
   __shared__ double xs[kOzRowsPerCta][kOzMaxK + 1];
@@ -96,7 +104,7 @@ __global__ void __launch_bounds__(kOzSliceThreads) oz_slice_kernel(const OzSlice
 #pragma unroll
     for (int s = 0; s < kOzSlices; ++s) {
       const int d = (int)((M >> (49 - 7 * s)) & 127ull);
-      out[s * pstride] = __bfloat16_as_ushort(__float2bfloat16_rn((float)(neg ? -d : d)));
+      out[s * pstride] = oz_bf16_digit(d, neg);
     }
   }
 }
@@ -115,73 +123,231 @@ __device__ __forceinline__ unsigned long long oz_magnitude(double x, int e, bool
 
 __device__ __forceinline__ uint16_t oz_digit(unsigned long long M, int s, bool neg) {
   const int d = (int)((M >> (49 - 7 * s)) & 127ull);
-  return __bfloat16_as_ushort(__float2bfloat16_rn((float)(neg ? -d : d)));
+  return oz_bf16_digit(d, neg);
 }
 
-// Column slicing for the Gram matrices of shifted CholeskyQR3: one CTA per column a of X (P rows),
-// the column's exponent by a block reduction, then its digits along the row of each plane.
-constexpr int kOzColThreads = 256;
+// X of one CholeskyQR pass in 64-row tiles (one CTA per tile).  The tile is staged in shared memory
+// with coalesced reads: rows are contiguous runs of b when L = 1, and for L > 1 each column of the
+// tile is a run along l (crossing an r boundary at most where l wraps).
+constexpr int kOzXRows = 64;
+constexpr int kOzXThreads = 256;
+constexpr int kOzXMaxB = 64;           // CholeskyQR3 runs for b <= 64
 
-__global__ void __launch_bounds__(kOzColThreads) oz_colslice_kernel(const OzColSliceJob* __restrict__ jobs,
-                                                                   int njobs, Bases bases) {
-  __shared__ int wmax[kOzColThreads / 32];
+__device__ __forceinline__ const OzXSliceJob& oz_xjob(const OzXSliceJob* __restrict__ jobs, int njobs) {
   int lo = 0, hi = njobs - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
     if (jobs[mid].tile_begin <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
   }
-  const OzColSliceJob& J = jobs[lo];
-  const int a = blockIdx.x - J.tile_begin;
-  const int64_t P = J.P, L = J.L;
-  const double* src = at<double>(bases, J.src);
-  // element i = l + L r of column a at l + L a + L b r
-  auto elem = [&](int64_t i) {
-    const int64_t r = L == 1 ? i : i / L, l = i - r * L;
-    return src[l + L * (int64_t)a + L * (int64_t)J.b * r];
-  };
-  int emax = 0;
-  for (int64_t i = threadIdx.x; i < P; i += kOzColThreads) {
-    const int E = (int)((__double_as_longlong(elem(i)) >> 52) & 0x7ff);
-    emax = E > emax ? E : emax;
+  return jobs[lo];
+}
+
+__device__ __forceinline__ int oz_stage_xtile(const OzXSliceJob& J, const double* __restrict__ src, int64_t i0,
+                                              double (*xs)[kOzXMaxB + 1], int64_t* roff) {
+  const int b = J.b;
+  const int nq = (int)(J.P - i0 < kOzXRows ? J.P - i0 : kOzXRows);
+  if (J.L == 1) {
+    const double* base = src + i0 * b;
+    for (int e = threadIdx.x; e < nq * b; e += kOzXThreads) {
+      const int q = e / b;
+      xs[q][e - q * b] = base[e];
+    }
+  } else {
+    if (threadIdx.x < kOzXRows) {
+      const int64_t i = i0 + threadIdx.x, r = i / J.L, l = i - r * J.L;
+      roff[threadIdx.x] = l + J.L * (int64_t)b * r;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < kOzXRows * b; e += kOzXThreads) {
+      const int a = e / kOzXRows, q = e - a * kOzXRows;
+      if (q < nq) xs[q][a] = src[roff[q] + J.L * a];
+    }
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const int other = __shfl_xor_sync(0xffffffffu, emax, o);
-    emax = other > emax ? other : emax;
-  }
-  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = emax;
+  return nq;
+}
+
+__global__ void __launch_bounds__(kOzXThreads) oz_xmax_kernel(const OzXSliceJob* __restrict__ jobs, int njobs,
+                                                             Bases bases) {
+  __shared__ double xs[kOzXRows][kOzXMaxB + 1];
+  __shared__ int64_t roff[kOzXRows];
+  __shared__ int red[kOzXThreads / 64][64];
+  const OzXSliceJob& J = oz_xjob(jobs, njobs);
+  const int tile = blockIdx.x - J.tile_begin;
+  const int nq = oz_stage_xtile(J, at<const double>(bases, J.src), (int64_t)tile * kOzXRows, xs, roff);
   __syncthreads();
-  emax = 0;
-  for (int w = 0; w < kOzColThreads / 32; ++w) emax = wmax[w] > emax ? wmax[w] : emax;
-  const int e = emax == 0 ? 0 : emax - 1022;
-  if (threadIdx.x == 0) at<int32_t>(bases, J.expo)[a] = e;
-  uint16_t* planes = at<uint16_t>(bases, J.planes);
-  const int64_t pstride = 64 * J.ldP;
-  uint16_t* row = planes + (int64_t)a * J.ldP;
-  for (int64_t i = threadIdx.x; i < P; i += kOzColThreads) {
-    bool neg;
-    const unsigned long long M = oz_magnitude(elem(i), e, neg);
-#pragma unroll
-    for (int sl = 0; sl < kOzSlices; ++sl) row[sl * pstride + i] = oz_digit(M, sl, neg);
+  const int a = threadIdx.x & 63, g = threadIdx.x >> 6;
+  int emax = 0;
+  if (a < J.b)
+    for (int q = g; q < nq; q += kOzXThreads / 64) {
+      const int E = (int)((__double_as_longlong(xs[q][a]) >> 52) & 0x7ff);
+      emax = E > emax ? E : emax;
+    }
+  red[g][a] = emax;
+  __syncthreads();
+  if (threadIdx.x < J.b) {
+    int m = red[0][threadIdx.x];
+    for (int k = 1; k < kOzXThreads / 64; ++k) m = red[k][threadIdx.x] > m ? red[k][threadIdx.x] : m;
+    at<int32_t>(bases, J.part)[(int64_t)tile * 64 + threadIdx.x] = m;
   }
 }
 
+__global__ void __launch_bounds__(kOzXThreads) oz_xdig_kernel(const OzXSliceJob* __restrict__ jobs, int njobs,
+                                                             Bases bases) {
+  __shared__ double xs[kOzXRows][kOzXMaxB + 1];
+  __shared__ int64_t roff[kOzXRows];
+  __shared__ int red[kOzXThreads / 64][64];
+  __shared__ int es[64];
+  const OzXSliceJob& J = oz_xjob(jobs, njobs);
+  const int tile = blockIdx.x - J.tile_begin;
+  const int b = J.b;
+  const int64_t i0 = (int64_t)tile * kOzXRows;
+  // e_a = (largest biased exponent field of column a) - 1022, so |X[i][a]| < 2^e_a (0 for a zero column)
+  {
+    const int a = threadIdx.x & 63, g = threadIdx.x >> 6;
+    const int32_t* part = at<const int32_t>(bases, J.part);
+    int m = 0;
+    if (a < b)
+      for (int t = g; t < J.tiles; t += kOzXThreads / 64) {
+        const int v = part[(int64_t)t * 64 + a];
+        m = v > m ? v : m;
+      }
+    red[g][a] = m;
+  }
+  const int nq = oz_stage_xtile(J, at<const double>(bases, J.src), i0, xs, roff);
+  __syncthreads();
+  if (threadIdx.x < b) {
+    int m = red[0][threadIdx.x];
+    for (int k = 1; k < kOzXThreads / 64; ++k) m = red[k][threadIdx.x] > m ? red[k][threadIdx.x] : m;
+    const int e = m == 0 ? 0 : m - 1022;
+    es[threadIdx.x] = e;
+    if (tile == 0) at<int32_t>(bases, J.expo)[threadIdx.x] = e;
+  }
+  __syncthreads();
+  uint16_t* colP = at<uint16_t>(bases, J.colP);
+  uint16_t* rowP = at<uint16_t>(bases, J.rowP);
+  const int64_t cstride = 64 * J.ldP, rstride = J.rows_pad * 64;
+  // column planes: a warp writes 32 consecutive rows i of one plane row a
+  {
+    const int q = threadIdx.x & 63;
+    if (q < nq)
+      for (int a = threadIdx.x >> 6; a < b; a += kOzXThreads / 64) {
+        bool neg;
+        const unsigned long long M = oz_magnitude(xs[q][a], es[a], neg);
+        uint16_t* out = colP + (int64_t)a * J.ldP + i0 + q;
+#pragma unroll
+        for (int sl = 0; sl < kOzSlices; ++sl) out[sl * cstride] = oz_digit(M, sl, neg);
+      }
+  }
+  // row planes: a warp writes 32 consecutive columns a of one plane row i
+  {
+    const int a = threadIdx.x & 63;
+    if (a < b)
+      for (int q = threadIdx.x >> 6; q < nq; q += kOzXThreads / 64) {
+        bool neg;
+        const unsigned long long M = oz_magnitude(xs[q][a], es[a], neg);
+        uint16_t* out = rowP + (i0 + q) * 64 + a;
+#pragma unroll
+        for (int sl = 0; sl < kOzSlices; ++sl) out[sl * rstride] = oz_digit(M, sl, neg);
+      }
+  }
+}
+
+// ----------------------------------------------------------------------------- composing a float64
+// The level sums combine into the integer N = hi 2^28 + lo (hi, lo in 64 bits, |N| < 2^127), and the
+// result is N 2^scale rounded once to nearest-even.  GB300's float64 pipe issues about 1.6 lanes per
+// clock per SM against 64 or more for the integer pipes, so the epilogues build the float64 from the
+// integer bits (leading-zero count, a 53-bit window with round/sticky bits, the exponent field)
+// instead of converting and scaling in float64; results outside the normal range (never met by the
+// products here) take a float64 path.
+__host__ __device__ __forceinline__ int oz_clz64(unsigned long long x) {
+#ifdef __CUDA_ARCH__
+  return __clzll((long long)x);
+#else
+  return x ? __builtin_clzll(x) : 64;
+#endif
+}
+
+__host__ __device__ __forceinline__ double oz_compose(long long hi, long long lo, int scale) {
+  // 128-bit two's complement (nh, nl) of hi 2^28 + lo
+  const unsigned long long h0 = (unsigned long long)hi << 28;
+  const unsigned long long nl = h0 + (unsigned long long)lo;
+  long long nh = (hi >> 36) + (lo < 0 ? -1 : 0) + (nl < h0 ? 1 : 0);
+  const bool neg = nh < 0;
+  unsigned long long ml = nl, mh = (unsigned long long)nh;
+  if (neg) {
+    ml = ~nl + 1ull;
+    mh = ~mh + (ml == 0ull ? 1ull : 0ull);
+  }
+  if ((mh | ml) == 0ull) return 0.0;
+  const int bitlen = mh ? 128 - oz_clz64(mh) : 64 - oz_clz64(ml);
+  unsigned long long mant;
+  int e2 = bitlen - 53;                       // |N| ~ mant 2^e2 with mant in [2^52, 2^53)
+  if (e2 <= 0) {
+    mant = ml << (-e2);
+  } else {
+    bool half, sticky;
+    if (e2 < 64) {
+      mant = (ml >> e2) | (e2 ? (mh << (64 - e2)) : 0ull);
+      half = (ml >> (e2 - 1)) & 1ull;
+      sticky = e2 > 1 ? (ml & ((1ull << (e2 - 1)) - 1ull)) != 0ull : false;
+    } else {
+      const int t = e2 - 64;
+      mant = mh >> t;
+      half = t ? ((mh >> (t - 1)) & 1ull) : (ml >> 63);
+      sticky = t ? ((mh & ((1ull << (t - 1)) - 1ull)) != 0ull || ml != 0ull) : (ml << 1) != 0ull;
+    }
+    if (half && (sticky || (mant & 1ull))) ++mant;
+    if (mant >> 53) {
+      mant >>= 1;
+      ++e2;
+    }
+  }
+  const int field = e2 + 52 + scale + 1023;
+  if (field >= 1 && field <= 2046) {
+    const unsigned long long bits = (neg ? (1ull << 63) : 0ull) | ((unsigned long long)field << 52) |
+                                    (mant & 0xfffffffffffffull);
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double((long long)bits);
+#else
+    double d;
+    memcpy(&d, &bits, sizeof(d));
+    return d;
+#endif
+  }
+  const double m = neg ? -(double)mant : (double)mant;
+  return scalbn(m, e2 + scale);
+}
+
 // ----------------------------------------------------------------------------- digit products
-// One 128 x 64 tile of Y per CTA.  Warp 0 (one thread) loads the eight digit planes of the tile's X
-// rows and of its P columns with TMA (one k-block of 64 at a time; K <= 96 takes two); warp 1 owns
-// the kOzLevels TMEM accumulators (64 columns each, the whole 512) and one thread issues the 36
-// digit-pair products of every k-block, pair (s, t) into accumulator s + t; warps 2-5 read the
-// accumulators (TMEM lane quadrant warp % 4), combine the levels in 64-bit integers and write Y.
-// Every wait is bounded: on a timeout the kernel records TKS_ETIMEOUT, drains its own copies and
-// products (bounded), frees TMEM and returns.
+// Persistent: CTA c takes the contiguous tile range [c T / G, (c + 1) T / G) of the T tiles (G CTAs,
+// at most one per SM), so consecutive tiles mostly belong to one job and share its P digits.  Warp 0
+// (one thread) loads the eight digit planes of a tile's X rows (and of its P columns when they change)
+// with TMA, one k-block of 64 at a time (K <= 96 takes two); warp 1 owns the kOzLevels TMEM
+// accumulators (64 columns each, the whole 512) and one thread issues the 36 digit-pair products of
+// every k-block, pair (s, t) into accumulator s + t; warps 2-9 read the accumulators (TMEM lane
+// quadrant warp % 4, columns 32 (warp - 2) / 4 ...), combine the levels in 64-bit integers and write Y.
+// The next tile's planes load while the epilogue of the last one runs.  Every wait is bounded: on a
+// timeout the kernel records TKS_ETIMEOUT, drains its own copies and products (bounded), frees TMEM
+// and returns.
 constexpr int kOzBM = 128, kOzBN = 64, kOzBK = 64;
 constexpr int kOzATile = kOzBM * kOzBK * 2;     // 16 KB per plane
 constexpr int kOzBTile = kOzBN * kOzBK * 2;     // 8 KB per plane
+constexpr int kOzGemmThreads = 320;             // TMA, MMA and 8 epilogue warps
 constexpr size_t kOzSmem = 1024 + (size_t)kOzSlices * (kOzATile + kOzBTile) + 64;
 
-__global__ void __launch_bounds__(192, 1) oz_gemm_kernel(const OzGemmJob* __restrict__ jobs, int njobs,
-                                                       const CUtensorMap* __restrict__ maps, Bases bases,
-                                                       Status* status, long long kOzWait) {
+__device__ __forceinline__ int oz_tile_job(const OzGemmJob* __restrict__ jobs, int njobs, int t) {
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(kOzGemmThreads, 1) oz_gemm_kernel(const OzGemmJob* __restrict__ jobs, int njobs,
+                                                                  int total_tiles,
+                                                                  const CUtensorMap* __restrict__ maps, Bases bases,
+                                                                  Status* status, long long kOzWait) {
   extern __shared__ uint8_t oz_smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(oz_smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* At = smem;
@@ -189,23 +355,17 @@ __global__ void __launch_bounds__(192, 1) oz_gemm_kernel(const OzGemmJob* __rest
   uint64_t* full = reinterpret_cast<uint64_t*>(Bt + kOzSlices * kOzBTile);
   uint64_t* empty = full + 1;
   uint64_t* tmem_full = empty + 1;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tmem_full + 1);
+  uint64_t* tmem_empty = tmem_full + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tmem_empty + 1);
   volatile int* err = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  int lo = 0, hi = njobs - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (jobs[mid].tile_begin <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
-  }
-  const OzGemmJob& J = jobs[lo];
-  const int local = blockIdx.x - J.tile_begin;
-  const int tn = local % J.tiles_n, tm = local / J.tiles_n;
-  const int m0 = tm * kOzBM, n0 = tn * kOzBN;
-  const int nk = (J.K + kOzBK - 1) / kOzBK;
+  const int t_begin = (int)(((long long)blockIdx.x * total_tiles) / gridDim.x);
+  const int t_end = (int)(((long long)(blockIdx.x + 1) * total_tiles) / gridDim.x);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     tc::mbar_init(full, 1);
     tc::mbar_init(empty, 1);
     tc::mbar_init(tmem_full, 1);
+    tc::mbar_init(tmem_empty, (kOzGemmThreads - 64) / 32);
     *err = 0;
     tc::fence_barrier_init();
   }
@@ -217,23 +377,35 @@ __global__ void __launch_bounds__(192, 1) oz_gemm_kernel(const OzGemmJob* __rest
 
   if (warp == 0) {
     if (lane == 0) {
-      for (int s = 0; s < kOzSlices; ++s) {
-        tc::prefetch_tmap(&maps[J.mapA[s]]);
-        tc::prefetch_tmap(&maps[J.mapB[s]]);
-      }
       int issued = 0;
-      for (int kb = 0; kb < nk; ++kb) {
-        // the single stage is refilled once the previous k-block's products have completed
-        if (*err || !tc::mbar_wait(empty, (kb & 1) ^ 1, kOzWait)) {
-          *err = 1;
-          break;
+      long long bkey = -1;   // (job, tile column, k-block) whose P planes are in shared memory
+      for (int t = t_begin; t < t_end && !*err; ++t) {
+        const int ji = oz_tile_job(jobs, njobs, t);
+        const OzGemmJob& J = jobs[ji];
+        const int local = t - J.tile_begin;
+        const int tn = local % J.tiles_n, tm = local / J.tiles_n;
+        const int nk = (J.K + kOzBK - 1) / kOzBK;
+        if (t == t_begin || local == 0)
+          for (int s = 0; s < kOzSlices; ++s) {
+            tc::prefetch_tmap(&maps[J.mapA[s]]);
+            tc::prefetch_tmap(&maps[J.mapB[s]]);
+          }
+        for (int kb = 0; kb < nk; ++kb) {
+          // the single stage is refilled once the previous k-block's products have completed
+          if (*err || !tc::mbar_wait(empty, (issued & 1) ^ 1, kOzWait)) {
+            *err = 1;
+            break;
+          }
+          const long long key = ((long long)ji << 24) | ((long long)tn << 4) | kb;
+          const bool loadB = key != bkey;
+          bkey = key;
+          tc::mbar_expect_tx(full, (uint32_t)(kOzSlices * (kOzATile + (loadB ? kOzBTile : 0))));
+          for (int s = 0; s < kOzSlices; ++s) {
+            tc::tma_load_2d(At + s * kOzATile, &maps[J.mapA[s]], full, kb * kOzBK, tm * kOzBM);
+            if (loadB) tc::tma_load_2d(Bt + s * kOzBTile, &maps[J.mapB[s]], full, kb * kOzBK, tn * kOzBN);
+          }
+          ++issued;
         }
-        tc::mbar_expect_tx(full, (uint32_t)(kOzSlices * (kOzATile + kOzBTile)));
-        for (int s = 0; s < kOzSlices; ++s) {
-          tc::tma_load_2d(At + s * kOzATile, &maps[J.mapA[s]], full, kb * kOzBK, m0);
-          tc::tma_load_2d(Bt + s * kOzBTile, &maps[J.mapB[s]], full, kb * kOzBK, n0);
-        }
-        issued = kb + 1;
       }
       // drain: the last copies issued have landed before the CTA tears down
       if (issued > 0 && !tc::mbar_wait(full, (issued - 1) & 1, kOzWait)) *err = 1;
@@ -241,50 +413,80 @@ __global__ void __launch_bounds__(192, 1) oz_gemm_kernel(const OzGemmJob* __rest
   } else if (warp == 1) {
     if (lane == 0) {
       constexpr uint32_t idesc = tc::idesc_bf16_f32(kOzBM, kOzBN);
-      for (int kb = 0; kb < nk; ++kb) {
-        if (*err || !tc::mbar_wait(full, kb & 1, kOzWait)) {
+      int used = 0, tiles = 0;
+      for (int t = t_begin; t < t_end && !*err; ++t) {
+        const OzGemmJob& J = jobs[oz_tile_job(jobs, njobs, t)];
+        const int nk = (J.K + kOzBK - 1) / kOzBK;
+        // the accumulators are free once the epilogue has read the previous tile
+        if (!tc::mbar_wait(tmem_empty, (tiles & 1) ^ 1, kOzWait)) {
           *err = 1;
           break;
         }
         tc::fence_after_sync();
-        // level acc = s + t collects the digit pairs (s, t); its first product starts it at zero
-        for (int acc = 0; acc < kOzLevels; ++acc) {
-          const uint32_t d = tmem + (uint32_t)(acc * kOzBN);
-          for (int s = 0; s <= acc; ++s) {
-            const int t = acc - s;
-            const uint32_t a0 = tc::smem_u32(At + s * kOzATile);
-            const uint32_t b0 = tc::smem_u32(Bt + t * kOzBTile);
+        bool ok = true;
+        for (int kb = 0; kb < nk; ++kb) {
+          if (*err || !tc::mbar_wait(full, used & 1, kOzWait)) {
+            ok = false;
+            break;
+          }
+          tc::fence_after_sync();
+          // level acc = s + t collects the digit pairs (s, t); its first product starts it at zero
+          for (int acc = 0; acc < kOzLevels; ++acc) {
+            const uint32_t d = tmem + (uint32_t)(acc * kOzBN);
+            for (int s = 0; s <= acc; ++s) {
+              const int tt = acc - s;
+              const uint32_t a0 = tc::smem_u32(At + s * kOzATile);
+              const uint32_t b0 = tc::smem_u32(Bt + tt * kOzBTile);
 #pragma unroll
-            for (int k = 0; k < kOzBK / 16; ++k) {
-              const uint32_t accumulate = (kb > 0 || s > 0 || k > 0) ? 1u : 0u;
-              tc::mma_bf16(d, tc::sw128_kmajor_desc(a0 + 32 * k), tc::sw128_kmajor_desc(b0 + 32 * k), idesc,
-                           accumulate);
+              for (int k = 0; k < kOzBK / 16; ++k) {
+                const uint32_t accumulate = (kb > 0 || s > 0 || k > 0) ? 1u : 0u;
+                tc::mma_bf16(d, tc::sw128_kmajor_desc(a0 + 32 * k), tc::sw128_kmajor_desc(b0 + 32 * k), idesc,
+                             accumulate);
+              }
             }
           }
+          tc::mma_commit(empty);
+          ++used;
         }
-        tc::mma_commit(empty);
+        if (!ok) {
+          *err = 1;
+          break;
+        }
+        tc::mma_commit(tmem_full);
+        ++tiles;
       }
-      tc::mma_commit(tmem_full);
-      if (!tc::mbar_wait(tmem_full, 0, kOzWait)) *err = 1;
+      // the last products have completed before TMEM is freed
+      if (tiles > 0 && !tc::mbar_wait(tmem_full, (tiles - 1) & 1, kOzWait)) *err = 1;
     }
   } else {
-    bool ok = tc::mbar_wait(tmem_full, 0, kOzWait);
-    ok = __all_sync(0xffffffffu, ok) && !*err;
-    tc::fence_after_sync();
-    if (ok) {
-      const int q = warp & 3;
-      const int row = m0 + 32 * q + lane;
+    const int q = warp & 3;
+    const int cbase = 32 * ((warp - 2) >> 2);
+    int tiles = 0;
+    for (int t = t_begin; t < t_end; ++t) {
+      bool ok = tc::mbar_wait(tmem_full, tiles & 1, kOzWait);
+      ok = __all_sync(0xffffffffu, ok) && !*err;
+      if (!ok) {
+        if (lane == 0) *err = 1;
+        break;
+      }
+      tc::fence_after_sync();
+      const OzGemmJob& J = jobs[oz_tile_job(jobs, njobs, t)];
+      const int local = t - J.tile_begin;
+      const int tn = local % J.tiles_n, tm = local / J.tiles_n;
+      const int row = tm * kOzBM + 32 * q + lane;
       const bool live = row < J.M;
-      const int eA = live ? at<const int32_t>(bases, J.expA)[row] : 0;
+      const int eA = (live && J.expA.base != B_NONE) ? at<const int32_t>(bases, J.expA)[row] : 0;
       const int32_t* expB = at<const int32_t>(bases, J.expB);
       double* Y = at<double>(bases, J.Y);
       const int64_t r = live ? (int64_t)row / J.L : 0, l = (int64_t)row - r * J.L;
       double* y = Y + l + J.L * (int64_t)J.rmax * r;
-      for (int c0 = 0; c0 < kOzBN; c0 += 8) {
+      const int n0 = tn * kOzBN + cbase;
+      for (int c0 = 0; c0 < 32; c0 += 8) {
+        if (n0 + c0 >= J.N) break;   // warp-uniform
         uint32_t v[kOzLevels][8];
 #pragma unroll
         for (int acc = 0; acc < kOzLevels; ++acc)
-          tc::tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * kOzBN + c0), v[acc]);
+          tc::tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * kOzBN + cbase + c0), v[acc]);
         tc::tmem_ld_wait();
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
@@ -298,11 +500,15 @@ __global__ void __launch_bounds__(192, 1) oz_gemm_kernel(const OzGemmJob* __rest
 #pragma unroll
           for (int acc = 4; acc < kOzLevels; ++acc)
             lo64 = (lo64 << 7) + (long long)__float2int_rn(__uint_as_float(v[acc][j]));
-          // value = 2^-35 (hi + 2^-28 lo), times 2^(eA + eB)
-          const double val = fma((double)lo64, 3.7252902984619140625e-09, (double)hi64);
-          y[J.L * (int64_t)col] = scalbn(val, eA + expB[col] - 35);
+          // value = 2^-35 (hi + 2^-28 lo) 2^(eA + eB) = (hi 2^28 + lo) 2^(eA + eB - 63)
+          y[J.L * (int64_t)col] = oz_compose(hi64, lo64, eA + expB[col] - 63);
         }
       }
+      // every TMEM read of this tile has completed: the next tile's products may start
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(tmem_empty);
+      ++tiles;
     }
   }
   tc::fence_before_sync();
@@ -318,12 +524,12 @@ __global__ void __launch_bounds__(192, 1) oz_gemm_kernel(const OzGemmJob* __rest
 // (an M = 128 product also reads the 64 rows after a tile, whose results land in TMEM lanes 64..127
 // and are ignored).  Every kOzGramGroup k-blocks the level sums, exact integers (8 pairs x 128 x
 // 127^2 < 2^24), are drained by warps 4 and 5 (TMEM lanes 0..63), combined in 64-bit integers and
-// added in float64 into a shared-memory accumulator; the scale 2^(e_i + e_j) is applied once at the
-// end.  Waits are bounded as in the other tensor-core kernels.
+// added into two 64-bit integer accumulators per entry in shared memory, so G is the exact sum rounded
+// once at the end, with the scale 2^(e_i + e_j).  Waits are bounded as in the other tensor-core kernels.
 constexpr int kOzGramGroup = 2;
 constexpr int kOzPlaneTile = 64 * kOzBK * 2;                          // 8 KB: 64 columns x 64 k
 constexpr int kOzStageBytes = (kOzSlices + 1) * kOzPlaneTile;         // + the 8 KB an M = 128 read passes
-constexpr size_t kOzGramSmem = 1024 + 2 * (size_t)kOzStageBytes + 64 * 64 * 8 + 128;
+constexpr size_t kOzGramSmem = 1024 + 2 * (size_t)kOzStageBytes + 2 * 64 * 64 * 8 + 128;
 
 __global__ void __launch_bounds__(192, 1) oz_gram_kernel(const OzGramJob* __restrict__ jobs,
                                                        const CUtensorMap* __restrict__ maps, Bases bases,
@@ -331,8 +537,10 @@ __global__ void __launch_bounds__(192, 1) oz_gram_kernel(const OzGramJob* __rest
   extern __shared__ uint8_t og_smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(og_smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* stage[2] = {smem, smem + kOzStageBytes};
-  double* acc64 = reinterpret_cast<double*>(smem + 2 * kOzStageBytes);   // [row][col], 64 x 64
-  uint64_t* full = reinterpret_cast<uint64_t*>(acc64 + 64 * 64);
+  // the level sums of every drain, combined exactly in two 64-bit integers per entry, [col][row]
+  long long* acc_hi = reinterpret_cast<long long*>(smem + 2 * kOzStageBytes);
+  long long* acc_lo = acc_hi + 64 * 64;
+  uint64_t* full = reinterpret_cast<uint64_t*>(acc_lo + 64 * 64);
   uint64_t* empty = full + 2;
   uint64_t* tmem_full = empty + 2;
   uint64_t* tmem_empty = tmem_full + 1;
@@ -352,7 +560,10 @@ __global__ void __launch_bounds__(192, 1) oz_gram_kernel(const OzGramJob* __rest
     *err = 0;
     tc::fence_barrier_init();
   }
-  for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) acc64[e] = 0.0;
+  for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) {
+    acc_hi[e] = 0;
+    acc_lo[e] = 0;
+  }
   if (warp == 1) tc::tmem_alloc(tmem_slot, kOzLevels * kOzBN);
   tc::fence_before_sync();
   __syncthreads();
@@ -442,7 +653,8 @@ __global__ void __launch_bounds__(192, 1) oz_gram_kernel(const OzGramJob* __rest
 #pragma unroll
           for (int acc = 4; acc < kOzLevels; ++acc)
             lo64 = (lo64 << 7) + (long long)__float2int_rn(__uint_as_float(v[acc][j]));
-          acc64[row * 64 + c0 + j] += fma((double)lo64, 3.7252902984619140625e-09, (double)hi64);
+          acc_hi[(c0 + j) * 64 + row] += hi64;
+          acc_lo[(c0 + j) * 64 + row] += lo64;
         }
       }
       tc::fence_before_sync();
@@ -454,13 +666,13 @@ __global__ void __launch_bounds__(192, 1) oz_gram_kernel(const OzGramJob* __rest
   __syncthreads();
   if (warp == 1) tc::tmem_dealloc(tmem, kOzLevels * kOzBN);
   if (!*err) {
-    // G[i + b j] = 2^(e_i + e_j - 35) acc[i][j]
+    // G[i + b j] = (hi 2^28 + lo) 2^(e_i + e_j - 63), rounded once
     const int32_t* expo = at<const int32_t>(bases, J.expo);
     double* G = at<double>(bases, J.G);
     const int b = J.b;
     for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
       const int i = e % b, j = e / b;
-      G[e] = scalbn(acc64[i * 64 + j], expo[i] + expo[j] - 35);
+      G[e] = oz_compose(acc_hi[j * 64 + i], acc_lo[j * 64 + i], expo[i] + expo[j] - 63);
     }
   } else if (threadIdx.x == 0) {
     atomicCAS(&status->code, 0, (int)TKS_ETIMEOUT);
@@ -481,9 +693,14 @@ cudaError_t prepare_oz_gemm() {
   return cudaFuncSetAttribute(oz_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOzGramSmem);
 }
 
-void launch_oz_colslice(const OzColSliceJob* jobs, int njobs, int total_cols, const Bases& bases,
-                        cudaStream_t stream) {
-  oz_colslice_kernel<<<total_cols, kOzColThreads, 0, stream>>>(jobs, njobs, bases);
+int oz_xslice_tiles(int64_t rows) { return (int)((rows + kOzXRows - 1) / kOzXRows); }
+
+void launch_oz_xmax(const OzXSliceJob* jobs, int njobs, int total_tiles, const Bases& bases, cudaStream_t stream) {
+  oz_xmax_kernel<<<total_tiles, kOzXThreads, 0, stream>>>(jobs, njobs, bases);
+}
+
+void launch_oz_xdig(const OzXSliceJob* jobs, int njobs, int total_tiles, const Bases& bases, cudaStream_t stream) {
+  oz_xdig_kernel<<<total_tiles, kOzXThreads, 0, stream>>>(jobs, njobs, bases);
 }
 
 void launch_oz_gram(const OzGramJob* jobs, int njobs, const void* maps, const Bases& bases, Status* status,
@@ -494,8 +711,18 @@ void launch_oz_gram(const OzGramJob* jobs, int njobs, const void* maps, const Ba
 
 void launch_oz_gemm(const OzGemmJob* jobs, int njobs, int total_tiles, const void* maps, const Bases& bases,
                     Status* status, long long wait_cycles, cudaStream_t stream) {
-  oz_gemm_kernel<<<total_tiles, 192, kOzSmem, stream>>>(jobs, njobs, static_cast<const CUtensorMap*>(maps), bases,
-                                                         status, wait_cycles);
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess || sms <= 0)
+      sms = 148;
+  }
+  const int grid = total_tiles < sms ? total_tiles : sms;
+  if (grid <= 0) return;
+  oz_gemm_kernel<<<grid, kOzGemmThreads, kOzSmem, stream>>>(jobs, njobs, total_tiles,
+                                                             static_cast<const CUtensorMap*>(maps), bases, status,
+                                                             wait_cycles);
 }
 
 }  // namespace tks

@@ -9,6 +9,8 @@
 // Every wait is bounded: on a timeout the kernel records TKS_ETIMEOUT,
 // drains its own copies and MMAs (again bounded), frees TMEM and returns.
 #include <cuda.h>
+
+#include <algorithm>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -24,8 +26,9 @@ constexpr int kBK = 64;                       // bf16 elements = 128 bytes = one
 constexpr int kATile = kBM * kBK * 2;         // 16 KB
 // Partial accumulators in TMEM: k-block kb goes to accumulator kb % kAcc and the epilogue adds
 // them, so each float32 accumulator takes 1/kAcc of the K-steps (the rounding error of a long
-// contraction whose products share a sign grows with the number of steps).
-constexpr int kAcc = 4;
+// contraction whose products share a sign grows with the number of steps).  Eight accumulators of
+// 64 columns fill the 512 TMEM columns of the SM (one CTA per SM: its shared memory is 227 KB).
+constexpr int kAcc = 8;
 
 __device__ __forceinline__ void record_status_tc(Status* st, int code) {
   if (st) atomicCAS(&st->code, 0, code);
@@ -227,7 +230,8 @@ void launch_tc_gemm(const TcJob* jobs, int njobs, int total_tiles, const void* m
                     const Bases& bases, Status* status, long long wait_cycles, const int* stall_word,
                     cudaStream_t stream) {
   const int stages = tc_gemm_stages(na_max, nb_max, 64);
-  const size_t smem = tc_gemm_smem_bytes(stages, na_max, nb_max, 64);
+  // at least 116 KB of shared memory keeps one CTA per SM, which owns all 512 TMEM columns
+  const size_t smem = std::max<size_t>(tc_gemm_smem_bytes(stages, na_max, nb_max, 64), 116 * 1024);
   tc_gemm_kernel<64><<<total_tiles, 192, smem, stream>>>(jobs, njobs, static_cast<const CUtensorMap*>(maps), bases,
                                                          status, stages, na_max, nb_max, wait_cycles, stall_word);
 }

@@ -233,6 +233,7 @@ struct SplitJob {
   Operand dst[3];
   int64_t rows, cols, ld_src, ld_dst;
   int64_t count, begin;
+  int32_t trans, pad;   // trans: element (i, j) goes to j + ld_dst i (else i + ld_dst j)
 };
 
 // Transpose a bf16 matrix: dst[j + ld_dst i] = src[i + ld_src j] (src rows x cols).
@@ -359,20 +360,25 @@ struct OzGemmJob {
   int32_t M, N, K;
   int32_t tiles_m, tiles_n, tile_begin;
   int32_t mapA[kOzSlices], mapB[kOzSlices];
-  Operand expA, expB;    // int32 row exponents of X and of P^T
+  Operand expA, expB;    // int32 row exponents of X and of P^T (expA.base == B_NONE: X's are all 0)
   Operand Y;             // float64: element (q, c) at Y[l + L (c + rmax r)], q = l + L r
   int64_t L;
   int32_t rmax, pad;
 };
 
 // Shifted CholeskyQR3 of X = H_(n)^T (P x b, element (i = l + L r, a) at src[l + L a + L b r]) with
-// float64-accurate Gram matrices on the tensor cores (TKS_MIXED):
-// column slicing: the b columns of X as rows of digit planes (K = P along the row), one CTA per column;
-// plane s of column a at planes + (s * 64 + a) * ldP elements, its exponent at expo[a].
-struct OzColSliceJob {
-  Operand src, planes, expo;
-  int64_t P, L, ldP;
-  int32_t b, tile_begin;
+// float64-accurate Gram matrices on the tensor cores (TKS_MIXED).  X is cut into digits against one
+// exponent per COLUMN, e_a with |X[i][a]| < 2^e_a, in 64-row tiles (one CTA per tile, two launches):
+//   oz_xmax:  the largest biased exponent field of each column over the tile -> part[tile][a];
+//   oz_xdig:  e_a from the partials of the matrix's tiles (the first tile stores them at expo[a]),
+//             then the same digits twice: plane s of column a at colP + (s * 64 + a) * ldP (element i:
+//             the Gram's operand, K = P) and of row i at rowP + (s * rows_pad + i) * 64 (element a:
+//             the A operand of X Rinv, K = b).  With column exponents X Rinv needs no row exponents:
+//             the Cholesky step writes Rinv with row a scaled by 2^e_a.
+struct OzXSliceJob {
+  Operand src, part, expo, colP, rowP;
+  int64_t P, L, ldP, rows_pad;
+  int32_t b, tiles, tile_begin, pad;
 };
 
 // G = X^T X (b x b, b <= 64) from the column digit planes (TMA maps map[s], box 64 k x 64 rows),
@@ -390,6 +396,7 @@ struct OzGramJob {
 // the pass's bound sets *fallback (the Householder TSQR then factors X instead).
 struct CholJob {
   Operand G, Rinv, Racc, Rout, fallback;
+  Operand xexp;          // int32 column exponents of X: Rinv row a is written times 2^xexp[a] (B_NONE: none)
   int64_t P;
   int32_t b, pass;
 };

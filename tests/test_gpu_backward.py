@@ -153,12 +153,12 @@ def test_backward_grad384_workload(cuda_lib):
             assert np.linalg.norm(dU[k][n] - rU[k][n]) <= 1e-12 * np.linalg.norm(rU[k][n])
 
 
-def test_backward_rejects_mixed_plans(cuda_lib):
+def test_backward_rejects_order4_plans(cuda_lib):
     from paper_2603_13532_gb300 import binding
     g = np.random.default_rng(9)
-    dims = [16, 24, 32]
-    prob = wl._finish([wl.Problem(dims, [g.standard_normal((2, 2, 2))],
-                                  [[g.standard_normal((n, 2)) for n in dims]], [3, 3, 3], [1, 1, 1])], True)
+    dims = [16, 24, 32, 8]
+    prob = wl._finish([wl.Problem(dims, [g.standard_normal((2, 2, 2, 2))],
+                                  [[g.standard_normal((n, 2)) for n in dims]], [3, 3, 3, 3], [1, 1, 1, 1])], True)
     plan = binding.Plan(prob, kind="krp", precision="mixed", seed=1)
     Q = torch.zeros(plan.info.basis_elems, dtype=torch.float64, device="cuda")
     Hb = torch.zeros(plan.info.core_elems, dtype=torch.float64, device="cuda")
@@ -167,3 +167,118 @@ def test_backward_rejects_mixed_plans(cuda_lib):
     with pytest.raises(binding.TksError) as e:
         plan.backward_raw(Q, Hb, dc, df)
     assert e.value.code == 7
+
+
+# ---------------------------------------------------------------------------------------------------
+# Mixed precision (config 5: bf16 factors and cores, float32 accumulation).  The tensor-core products
+# take float64 Q and Hbar as three bf16 planes each (about 2^-24 relative) and accumulate in float32
+# over K <= 64; the per-term contractions run in float32 over at most r^2 = 256 terms.  Each step adds
+# a few units of 2^-24 of its operands' scale, so 1e-5 of each gradient tensor's norm is a bound with
+# an order of magnitude to spare, and a dropped term, a wrong offset or a transposed operand fails it
+# by orders of magnitude.
+def _mixed_problems(seed=0):
+    g = np.random.default_rng(500 + seed)
+    probs = []
+    for dims, K in ([[40, 56, 24], 3], [[64, 16, 48], 2]):
+        cores, facs = [], []
+        for _ in range(K):
+            r = [int(x) for x in g.integers(1, 9, size=3)]
+            cores.append(g.standard_normal(r))
+            facs.append([g.standard_normal((n, ri)) for n, ri in zip(dims, r)])
+        probs.append(wl.Problem(dims, cores, facs, [5, 7, 6], [2, 1, 3], alpha=list(g.standard_normal(K))))
+    return wl._finish(probs, True)
+
+
+def _rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300)
+
+
+def test_backward_mixed_matches_oracle_vjp(cuda_lib):
+    from paper_2603_13532_gb300 import binding
+    probs = _mixed_problems()
+    plan = binding.Plan(probs, kind="krp", precision="mixed", seed=3)
+    Qs, Ts = _qs_and_targets(plan, probs)
+    Hbars = [2.0 * (ss.project_core(ss.scaled_terms(p.terms(), p.alpha), Q) - T)
+             for p, Q, T in zip(probs, Qs, Ts)]
+    got = plan.backward(Qs, Hbars)
+    for p, Q, Hb, (dG, dU) in zip(probs, Qs, Hbars, got):
+        terms = ss.scaled_terms(p.terms(), p.alpha)
+        rG, rU = ss.project_core_vjp(terms, Q, Hb)
+        for k, a in enumerate(p.alpha):
+            assert _rel(dG[k], a * rG[k]) <= 1e-5, (k, _rel(dG[k], a * rG[k]))
+            for n in range(3):
+                assert _rel(dU[k][n], rU[k][n]) <= 1e-5, (k, n, _rel(dU[k][n], rU[k][n]))
+
+
+def test_backward_mixed_grad384_matches_oracle_and_central_differences(cuda_lib):
+    """Config 5 at full size on the mixed path: against the oracle's float64 gradient (1e-5 of each
+    tensor's norm), and entries against float64 central differences of L = ||H - T||^2 evaluated by the
+    float64 GPU forward (exact for a quadratic up to rounding; h = 1e-3)."""
+    from paper_2603_13532_gb300 import binding
+    w = wl.grad384()
+    p = w.problems[0]
+    ref = ss.recompress(p.terms(), "krp", p.target, p.oversampling, seed=w.seed)
+    T = w.notes["target_tensor"]
+    Hbar = 2.0 * (ref["H"] - T)
+    mixed = binding.Plan(w.problems, kind="krp", precision="mixed", seed=w.seed)
+    (dG, dU), = mixed.backward([ref["Q"]], [Hbar])
+    rG, rU = ss.project_core_vjp(p.terms(), ref["Q"], Hbar)
+    for k in range(p.num_terms):
+        assert _rel(dG[k], rG[k]) <= 1e-5, (k, _rel(dG[k], rG[k]))
+        for n in range(3):
+            assert _rel(dU[k][n], rU[k][n]) <= 1e-5, (k, n, _rel(dU[k][n], rU[k][n]))
+    plan = _plan(w.problems, w.seed)
+    Q = plan.pack_bases([ref["Q"]])
+    Tt = plan.pack_core([T])
+
+    def loss():
+        H = torch.zeros(plan.info.core_elems, dtype=torch.float64, device=plan.device)
+        plan.project_raw(Q, H)
+        torch.cuda.synchronize()
+        return float(((H - Tt) ** 2).sum())
+
+    core_v, fac_v = plan.inputs[0]
+    h = 1e-3
+    scale = max(max(np.abs(x).max() for x in dG), max(np.abs(u).max() for row in dU for u in row))
+    G0 = p.cores[0]
+    for flat_idx in [0, 7, G0.size - 1]:
+        idx = np.unravel_index(flat_idx, G0.shape, order="F")
+        old = float(core_v[flat_idx])
+        core_v[flat_idx] = old + h
+        lp = loss()
+        core_v[flat_idx] = old - h
+        lm = loss()
+        core_v[flat_idx] = old
+        assert abs((lp - lm) / (2 * h) - dG[0][idx]) <= 1e-5 * scale
+    for n in range(3):
+        for (i, j) in [(0, 0), (p.dims[n] - 1, 3)]:
+            old = float(fac_v[n][i + p.dims[n] * j])
+            fac_v[n][i + p.dims[n] * j] = old + h
+            lp = loss()
+            fac_v[n][i + p.dims[n] * j] = old - h
+            lm = loss()
+            fac_v[n][i + p.dims[n] * j] = old
+            assert abs((lp - lm) / (2 * h) - dU[0][n][i, j]) <= 1e-5 * scale
+
+
+def test_backward_mixed_autograd_function(cuda_lib):
+    from paper_2603_13532_gb300 import binding
+    probs = _mixed_problems(1)
+    plan = binding.Plan(probs, kind="krp", precision="mixed", seed=5)
+    Qs, Ts = _qs_and_targets(plan, probs, 5)
+    Q = plan.pack_bases(Qs)
+    T = plan.pack_core(Ts)
+    x = plan.flat_inputs
+    x.requires_grad_(True)
+    H = binding.ProjectCore.apply(x, Q, plan)
+    L = ((H - T) ** 2).sum()
+    (gx,) = torch.autograd.grad(L, [x])
+    x.requires_grad_(False)
+    direct = plan.backward(Qs, [2.0 * (h - t) for h, t in zip(plan.project(Qs), Ts)])
+    # the autograd gradient lands in the inputs' dtype (bfloat16): compare at bf16 resolution
+    g = gx.detach().to(torch.float64).cpu().numpy()
+    base = x.storage_offset()
+    for p, (core_v, fac_v), (dG, dU) in zip(probs, plan.inputs, direct):
+        o = core_v.storage_offset() - base
+        flat_dG = np.concatenate([a.ravel(order="F") for a in dG])
+        assert np.allclose(g[o: o + flat_dG.size], flat_dG, rtol=1e-2, atol=1e-2 * np.abs(flat_dG).max())

@@ -38,15 +38,18 @@ def _rel(a, b):
     return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300)
 
 
-def _per_slice(a, b, tol):
+def _per_slice(a, b, tol, floor=1e-2):
     """Elementwise check beside the normwise one: along every axis, each slice (a column of Y, a
-    mode-n slice of H) has max |a - b| within tol times the largest |b| of that slice, so an error
-    confined to small entries or trailing rows cannot hide in the Frobenius norm."""
+    mode-n slice of H) has max |a - b| within tol times its largest |b|, so an error confined to small
+    entries or trailing rows cannot hide in the Frobenius norm.  A slice below floor times the largest
+    |b| overall (a direction at the noise floor, e.g. beyond the sum's true rank, whose entries come
+    from cancellation) is held to tol times that floor instead."""
     a, b = np.asarray(a), np.asarray(b)
+    g = float(np.max(np.abs(b)))
     for axis in range(b.ndim):
         for k in range(b.shape[axis]):
             sa, sb = np.take(a, k, axis=axis), np.take(b, k, axis=axis)
-            m = float(np.max(np.abs(sb)))
+            m = max(float(np.max(np.abs(sb))), floor * g)
             if m > 0:
                 err = float(np.max(np.abs(sa - sb)))
                 assert err <= tol * m, (axis, k, err / m)
