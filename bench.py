@@ -85,6 +85,7 @@ def parse_args():
     ap.add_argument("--subrank-eps", type=float, default=1e-6, help="tolerance of the Alg. 5 leg")
     ap.add_argument("--subrank-steps", type=int, default=3, help="timed calls of the Alg. 5 leg")
     ap.add_argument("--no-backward", action="store_true", help="skip the backward (config 5) leg")
+    ap.add_argument("--no-autotune", action="store_true", help="run the built-in schedule rules untuned")
     ap.add_argument("--backward-problems", type=int, default=152, help="grad384 problems per backward call")
     ap.add_argument("--backward-steps", type=int, default=20, help="timed calls of the mixed backward")
     return ap.parse_args()
@@ -395,7 +396,9 @@ def extra_workload_leg(args, workload, device, stream, rank, world):
     kind = workload_kind(workload)
     lanes = 2 if (args.precision == "mixed_f32la" and not workload.startswith("order4")) else 1
     problems = make_problems(P, args.seed, rank, True, workload)
-    plan = binding.Plan(problems, kind=kind, precision=args.precision, seed=args.seed, device=device, lanes=lanes)
+    plan = binding.Plan(problems, kind=kind, precision=args.precision, seed=args.seed, device=device, lanes=lanes,
+                        autotune=not args.no_autotune)
+    tuning = plan.tuning()
     out = torch.zeros(plan.info.output_elems, dtype=torch.float64, device=device)
     ranks_t = torch.zeros(P * binding.MAX_ORDER, dtype=torch.int32, device=device)
     timed, graph = graph_step(plan, out, ranks_t, stream)
@@ -404,7 +407,9 @@ def extra_workload_leg(args, workload, device, stream, rank, world):
     value = weak_scaling_rate(P, world, args.extra_steps, el)
     res = plan.unpack(out, ranks_t)
     leg = {"workload": workload_label(P, workload), "precision": args.precision, "value": value, "unit": UNIT,
-           "ms_per_step": 1e3 * el / args.extra_steps, "steps": args.extra_steps, "lanes": lanes,
+           "ms_per_step": 1e3 * el / args.extra_steps, "steps": args.extra_steps, "lanes": tuning["picked"]["lanes"],
+           "schedule": {"knobs": tuning["picked"], "autotuned": bool(tuning["autotuned"]),
+                        "gain": (tuning["rule_ms"] / tuning["picked_ms"]) if tuning["autotuned"] else None},
            "tflops": (plan.info.flops_lowprec + plan.info.flops_fp64) * world * args.extra_steps / el / 1e12}
     del graph, plan
     plan64 = binding.Plan(problems, kind=kind, precision="fp64", seed=args.seed, device=device, omega_lowprec=True)
@@ -432,6 +437,7 @@ def backward_leg(args, device, stream, rank, world):
     (tensor-core products, float32 accumulation) and on the float64 path, with Q and Hbar resident on
     the device; plus the difference between the two and the error of the first problem against the
     oracle's float64 gradient."""
+    import numpy as np
     import torch
     from paper_2603_13532_gb300 import binding, workloads as wl
     from oracle import sketch_sum as ss
@@ -623,8 +629,20 @@ def main():
     if args.lanes is None:
         args.lanes = 2 if (args.precision == "mixed_f32la" and not args.workload.startswith("order4")) else 1
     problems = make_problems(P, args.seed, rank, bf16, args.workload)
+    autotune = args.precision != "fp64" and not args.no_autotune
+    t_tune = time.perf_counter()
     plan = binding.Plan(problems, kind=kind, precision=args.precision, seed=args.seed, device=device,
-                        lanes=args.lanes)
+                        lanes=args.lanes, autotune=autotune)
+    t_tune = time.perf_counter() - t_tune
+    tuning = plan.tuning()
+    schedule = {"knobs": tuning["picked"], "rule": tuning["rule"], "autotuned": bool(tuning["autotuned"])}
+    if tuning["autotuned"]:
+        schedule.update({"rule_ms": tuning["rule_ms"], "picked_ms": tuning["picked_ms"],
+                         "gain": tuning["rule_ms"] / tuning["picked_ms"], "candidates": len(tuning["candidates"]),
+                         "plan_create_s": t_tune,
+                         "note": "greedy search in tks_plan_create from the built-in rules (lanes, sketch QR, "
+                                 "ST-HOSVD factor, projection chunk, tensor-core stages), median of 3 eager "
+                                 "recompressions per candidate"})
     out = torch.zeros(plan.info.output_elems, dtype=torch.float64, device=device)
     ranks_t = torch.zeros(P * binding.MAX_ORDER, dtype=torch.int32, device=device)
     stream = torch.cuda.current_stream()
@@ -673,7 +691,7 @@ def main():
         host_in, _ = binding.pack_inputs(problems, plan.dtype, "cpu", pin=True)
         lanes = [(plan, out, ranks_t, timed)]
         plan_b = binding.Plan(problems, kind=kind, precision=args.precision, seed=args.seed, device=device,
-                              lanes=args.lanes)
+                              schedule=tuning["picked"])
         out_b = torch.zeros_like(out)
         ranks_b = torch.zeros_like(ranks_t)
         plan_b.recompress_raw(out_b, ranks_b)
@@ -793,7 +811,7 @@ def main():
     f32la = None
     if args.precision == "mixed" and not args.no_f32la:
         plan32 = binding.Plan(problems, kind=kind, precision="mixed_f32la", seed=args.seed, device=device,
-                              lanes=1 if args.workload.startswith("order4") else 2)
+                              lanes=1 if args.workload.startswith("order4") else 2, autotune=not args.no_autotune)
         out32 = torch.zeros(plan32.info.output_elems, dtype=torch.float64, device=device)
         r32 = torch.zeros_like(ranks_t)
         timed32, graph32 = graph_step(plan32, out32, r32, stream, use_graph=not args.no_graph)
@@ -801,7 +819,7 @@ def main():
         plan32.sync()
         v32 = weak_scaling_rate(P, world, args.steps, el32)
         f32la = {"value": v32, "unit": UNIT, "ms_per_step": 1e3 * el32 / args.steps, "steps": args.steps,
-                 "precision": "mixed_f32la",
+                 "precision": "mixed_f32la", "schedule": plan32.tuning()["picked"],
                  "note": "the same tensor-core contractions with the QR of Y_n and the ST-HOSVD in float32 "
                          "(Householder QR, TSQR and one-sided Jacobi SVD; no Gram matrices)"}
         if fp64_path is not None:
@@ -887,7 +905,8 @@ def main():
                            "flops_per_step": plan.info.flops_lowprec + plan.info.flops_fp64,
                            "l2": f"inputs {in_bytes / 1e6:.0f} MB per GPU > L2 129 MB, no flush",
                            "parallelism": f"replicas x{world}",
-                           "lanes": args.lanes if args.precision != "fp64" else 1},
+                           "lanes": tuning["picked"]["lanes"] if args.precision != "fp64" else 1,
+                           "schedule": schedule},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fp64_path": fp64_path, "vs_oracle": vs_oracle,
                 "mixed_f32la": f32la, "workloads": extra or None,
                 "projection_tensor_roofline": projection_tensor_roofline(prof, args.steps, peaks),

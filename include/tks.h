@@ -114,6 +114,24 @@ typedef struct {
                                    latency-bound stages of one group overlap the others' work);
                                    results are identical.  Ignored by TKS_FP64 and by the other
                                    entry points. */
+  /* Schedule knobs (0 = the built-in rule for every one).  None changes what is computed; the
+   * linear-algebra choices change the rounding only (float64-accurate either way). */
+  int32_t autotune;             /* 1 (mixed modes): tks_plan_create times candidate schedules on the
+                                   plan's own inputs before returning (lanes, then each knob below,
+                                   one at a time from the rule, keeping a candidate only when it is
+                                   at least 2% faster), using a scratch workspace and outputs it
+                                   allocates and frees; the plan keeps the fastest and reports the
+                                   candidates and times through tks_plan_tuning.  Autotuning runs
+                                   the recompression several times on a stream of its own and
+                                   synchronizes the device. */
+  int32_t sketch_qr;            /* TKS_MIXED QR of Y_n: 0 rule (shifted CholeskyQR3 where S_n <= 64
+                                   and n_n >= S_n, else Householder), 1 the same, 2 Householder always */
+  int32_t hosvd_r;              /* TKS_MIXED triangular factor of H_(n)^T: 0 rule (shifted CholeskyQR3
+                                   for b_n <= 64, else Householder TSQR), 1 the same, 2 TSQR always */
+  int32_t proj_chunk;           /* fused order-3 projection: 0 rule (16), else 8 or 16 mode-3
+                                   indices per staged chunk at most */
+  int32_t tc_stages;            /* tensor-core GEMM shared-memory ring: 0 rule (up to 4 stages as the
+                                   operand planes fit), else 2..4 at most */
 } tks_params;
 
 typedef struct tks_plan tks_plan;
@@ -158,6 +176,15 @@ typedef struct {
  * allocations and copies; synchronous.  On error *plan is set to NULL. */
 TKS_API tks_status tks_plan_create(tks_plan** plan, const tks_problem* problems, int32_t num_problems,
                            const tks_params* params);
+
+/* The schedule the plan runs, as one JSON object written to buf (host, cap bytes, NUL-terminated,
+ * truncated to fit; *len receives the full length without the NUL):
+ *   {"autotuned": 0|1, "picked": {knobs}, "rule": {knobs}, "rule_ms": t, "picked_ms": t,
+ *    "candidates": [{"knobs": {...}, "ms": t}, ...]}
+ * with knobs {"lanes", "sketch_qr", "hosvd_r", "proj_chunk", "tc_stages"} as tks_params takes them
+ * (so a caller can create later plans with the picks and autotune = 0).  Times are milliseconds per
+ * tucker_sum_recompress measured during tks_plan_create (0 when the plan was not autotuned). */
+TKS_API tks_status tks_plan_tuning(const tks_plan* plan, char* buf, int64_t cap, int64_t* len);
 TKS_API void tks_plan_destroy(tks_plan* plan);
 TKS_API tks_status tks_plan_info(const tks_plan* plan, tks_plan_info_t* info);
 TKS_API tks_status tks_problem_info(const tks_plan* plan, int32_t problem, tks_problem_info_t* info);

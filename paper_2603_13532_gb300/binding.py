@@ -46,7 +46,10 @@ class Problem_t(ctypes.Structure):
 class Params_t(ctypes.Structure):
     _fields_ = [("sketch", ctypes.c_int), ("precision", ctypes.c_int), ("dtype", ctypes.c_int),
                 ("seed", ctypes.c_uint64), ("trunc_tol", ctypes.c_double), ("omega_lowprec", ctypes.c_int32),
-                ("lanes", ctypes.c_int32)]
+                ("lanes", ctypes.c_int32), ("autotune", ctypes.c_int32), ("sketch_qr", ctypes.c_int32),
+                ("hosvd_r", ctypes.c_int32), ("proj_chunk", ctypes.c_int32), ("tc_stages", ctypes.c_int32)]
+
+SCHEDULE_KNOBS = ("lanes", "sketch_qr", "hosvd_r", "proj_chunk", "tc_stages")
 
 
 class PlanInfo_t(ctypes.Structure):
@@ -110,6 +113,7 @@ def load(path=None):
     lib.tks_project_core_backward.argtypes = [P, P, P, P, P, P, P]
     lib.tks_project_core_backward.restype = ctypes.c_int
     lib.tks_sync_status.argtypes = [P, P]
+    lib.tks_plan_tuning.argtypes = [P, ctypes.c_char_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
     lib.tks_last_error.restype = ctypes.c_char_p
     lib.tks_status_string.restype = ctypes.c_char_p
     lib.tks_status_string.argtypes = [ctypes.c_int]
@@ -130,7 +134,7 @@ def load(path=None):
     for name in ["tks_plan_create", "tks_plan_info", "tks_problem_info", "tks_generate_omega",
                  "tucker_sum_sketch", "tks_project_core", "tucker_sum_recompress", "tks_sync_status",
                  "tks_profile_begin", "tks_profile_end", "tks_subrank_plan_create", "tks_truncate_core",
-                 "tks_plan_set_fault_test", "tks_subrank_info",
+                 "tks_plan_set_fault_test", "tks_subrank_info", "tks_plan_tuning",
                  "tks_subrank_problem_info", "tks_effective_subrank", "tks_subrank_sync_status"]:
         getattr(lib, name).restype = ctypes.c_int
     _LIB = lib
@@ -210,7 +214,9 @@ class Plan:
     """A plan over a list of ``workloads.Problem`` with their device inputs."""
 
     def __init__(self, problems, kind="krp", precision="fp64", seed=0, tol=0.0, device="cuda", omega_lowprec=False,
-                 lanes=0):
+                 lanes=0, autotune=False, schedule=None):
+        """``schedule``: a dict of tks_params schedule knobs (the "picked" object of tuning()), which
+        overrides ``lanes``; ``autotune``: let tks_plan_create search them on these inputs."""
         self.lib = load()
         self.problems = list(problems)
         self.kind, self.precision, self.seed, self.tol = kind, precision, seed, tol
@@ -220,6 +226,11 @@ class Plan:
         self._keep = []
         arr = _problem_structs(self.problems, self.inputs, self._keep)
         prm = Params_t(SKETCH[kind], PRECISION[precision], DTYPE[self.dtype], seed, tol, int(omega_lowprec), int(lanes))
+        for k, v in (schedule or {}).items():
+            if k not in SCHEDULE_KNOBS:
+                raise ValueError(f"unknown schedule knob {k}")
+            setattr(prm, k, int(v))
+        prm.autotune = int(bool(autotune))
         handle = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             _check(self.lib.tks_plan_create(ctypes.byref(handle), arr, len(self.problems), ctypes.byref(prm)))
@@ -238,6 +249,15 @@ class Plan:
         if h is not None and h.value:
             self.lib.tks_plan_destroy(h)
             self.handle = None
+
+    def tuning(self):
+        """The schedule the plan runs and, when autotuned, the candidates timed (tks_plan_tuning)."""
+        import json
+        n = ctypes.c_int64()
+        _check(self.lib.tks_plan_tuning(self.handle, None, 0, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value + 1)
+        _check(self.lib.tks_plan_tuning(self.handle, buf, n.value + 1, ctypes.byref(n)))
+        return json.loads(buf.value.decode())
 
     # ---- raw entry points (device buffers in, nothing synchronised)
     def omega_raw(self, out):

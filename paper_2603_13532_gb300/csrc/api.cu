@@ -187,6 +187,11 @@ struct tks_plan {
   cudaEvent_t lane_fork = nullptr;
   int64_t grad_core_elems = 0, grad_factor_elems = 0;
   bool backward_ok = false;
+  // the schedule: knobs as run, and the autotuner's measurements (empty when not autotuned)
+  std::string tuning_candidates;
+  double tuning_rule_ms = 0.0, tuning_picked_ms = 0.0;
+  tks_params tuning_rule{};
+  bool autotuned = false;
   std::string build_error;   // set by a table builder that cannot plan a problem
   size_t trunc_from = 0;     // first step of the ST-HOSVD truncation in st_recompress
   // failure-path controls (tks_plan_set_fault_test): the bound of the tensor-core kernels' waits, and
@@ -872,6 +877,7 @@ static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
         }
         t.alpha = (float)h.alpha[k];
         t.chunk = proj3_chunk(t.r, 2);
+        if (plan->params.proj_chunk > 0) t.chunk = std::min(t.chunk, plan->params.proj_chunk);
         p3terms.push_back(t);
         p3_flops += 2.0 * h.b[0] * ((double)r[0] * r[1] * r[2] + (double)h.b[1] * r[1] * r[2] +
                                     (double)h.b[1] * h.b[2] * r[2]);
@@ -934,6 +940,7 @@ static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
           }
           t.alpha = 1.0f;
           t.chunk = proj3_chunk(t.r, 4);
+          if (plan->params.proj_chunk > 0) t.chunk = std::min(t.chunk, plan->params.proj_chunk);
           p3fterms.push_back(t);
           p3f_flops += 2.0 * b0 * ((double)r[0] * r[2] * r[3] + (double)b2 * r[2] * r[3] + (double)b2 * b3 * r[3]);
         }
@@ -1605,7 +1612,7 @@ static void build_hosvd_f64(tks_plan* plan) {
       for (int j = n + 1; j < d; ++j) Rr *= h.b[j];
       const int b = h.b[n], rmax = h.rmax[n];
       const Operand X = (n == 0) ? op(B_H, h.h_off * 8) : op(B_WS, h.Hp[(n - 1) & 1]);
-      const bool cholqr = emulate && b <= 64;
+      const bool cholqr = emulate && b <= 64 && plan->params.hosvd_r != 2;
       Operand gate{B_NONE, 0, 0};
       if (cholqr) {
         const CqBuffers B{{h.cqX[0], h.cqX[1]}, h.cqCol, h.cqColE, h.cqG, h.cqRinv, h.cqRacc, h.cqFlag,
@@ -1827,8 +1834,8 @@ void tks_plan_destroy(tks_plan* plan) {
   delete plan;
 }
 
-tks_status tks_plan_create(tks_plan** out, const tks_problem* problems, int32_t num_problems,
-                           const tks_params* params) {
+static tks_status create_plan(tks_plan** out, const tks_problem* problems, int32_t num_problems,
+                              const tks_params* params) {
   if (!out) return fail(TKS_EINVAL, "plan output pointer is NULL");
   *out = nullptr;
   if (!problems || !params || num_problems < 1) return fail(TKS_EINVAL, "no problems or params");
@@ -1837,6 +1844,12 @@ tks_status tks_plan_create(tks_plan** out, const tks_problem* problems, int32_t 
   if (!(prm.trunc_tol >= 0.0) || !std::isfinite(prm.trunc_tol)) return fail(TKS_EINVAL, "bad trunc_tol");
   if (prm.omega_lowprec != 0 && prm.omega_lowprec != 1) return fail(TKS_EINVAL, "omega_lowprec must be 0 or 1");
   if (prm.lanes < 0 || prm.lanes > 8) return fail(TKS_EINVAL, "lanes must be 0..8");
+  if (prm.autotune != 0 && prm.autotune != 1) return fail(TKS_EINVAL, "autotune must be 0 or 1");
+  if (prm.sketch_qr < 0 || prm.sketch_qr > 2) return fail(TKS_EINVAL, "sketch_qr must be 0..2");
+  if (prm.hosvd_r < 0 || prm.hosvd_r > 2) return fail(TKS_EINVAL, "hosvd_r must be 0..2");
+  if (prm.proj_chunk != 0 && prm.proj_chunk != 8 && prm.proj_chunk != 16)
+    return fail(TKS_EINVAL, "proj_chunk must be 0, 8 or 16");
+  if (prm.tc_stages != 0 && (prm.tc_stages < 2 || prm.tc_stages > 4)) return fail(TKS_EINVAL, "tc_stages must be 0 or 2..4");
   if (prm.precision == TKS_FP64) {
     if (prm.dtype != TKS_DT_F64) return fail(TKS_EINVAL, "TKS_FP64 needs float64 cores and factors");
   } else if (prm.precision == TKS_MIXED || prm.precision == TKS_MIXED_F32LA) {
@@ -1937,7 +1950,7 @@ tks_status tks_plan_create(tks_plan** out, const tks_problem* problems, int32_t 
         for (int t = 0; t < 3; ++t) h.Vp[m][t] = alloc((size_t)h.ldV[m] * h.S[m] * 2);
         for (int t = 0; t < 3; ++t) h.Qp[m][t] = alloc((size_t)h.n[m] * h.b[m] * 2);
         h.AT32[m] = alloc((size_t)h.R[m] * h.b[m] * 4);
-        if (prm.precision == TKS_MIXED && h.n[m] >= h.S[m] && h.S[m] <= 64) {
+        if (prm.precision == TKS_MIXED && h.n[m] >= h.S[m] && h.S[m] <= 64 && prm.sketch_qr != 2) {
           // CholeskyQR3 of Y_n (n_m x S_m): see CqBuffers
           const int64_t rows8 = (h.n[m] + 7) / 8 * 8;
           CqBuffers& B = h.qcq[m];
@@ -2407,6 +2420,11 @@ namespace {
 
 tks_status run_steps(tks_plan* plan, const std::vector<Step>& steps, const Bases& bases, cudaStream_t stream,
                      bool profile = false) {
+  // the tensor-core kernels read TMA tensor maps encoded for one workspace address: refuse to launch
+  // them against maps of another workspace (or none), which would hand the TMA unit a stale descriptor
+  for (const Step& s : steps)
+    if ((s.kind == S_TC || s.kind == S_OZGEMM || s.kind == S_OZGRAM) && plan->maps_ws != bases.p[B_WS])
+      return fail(TKS_EINVAL, "internal: tensor maps not encoded for this workspace");
   cudaEvent_t* ev = nullptr;
   if (profile && plan->prof_calls < plan->prof_max_calls) {
     ev = plan->prof_events.data() + (size_t)plan->prof_calls * (steps.size() + 1);
@@ -2464,7 +2482,7 @@ tks_status run_steps(tks_plan* plan, const std::vector<Step>& steps, const Bases
       case S_TC:
         launch_tc_gemm(static_cast<const TcJob*>(table), s.njobs, (int)s.work, plan->arena_dev + plan->maps_off,
                        s.na_max, s.nb_max, bases, plan->status, plan->wait_cycles,
-                       plan->stall ? plan->stall_word() : nullptr, stream);
+                       plan->stall ? plan->stall_word() : nullptr, plan->params.tc_stages, stream);
         break;
       case S_SIMT:
         launch_simt_gemm_f32(static_cast<const SimtJob*>(table), s.njobs, (int)s.work, bases, stream);
@@ -2725,6 +2743,166 @@ tks_status tks_profile_end(tks_plan* plan, tks_step_profile_t* out, int32_t cap,
   return TKS_OK;
 }
 
+namespace {
+
+std::string knobs_json(const tks_params& p) {
+  char b[160];
+  std::snprintf(b, sizeof(b), "{\"lanes\": %d, \"sketch_qr\": %d, \"hosvd_r\": %d, \"proj_chunk\": %d, \"tc_stages\": %d}",
+                p.lanes, p.sketch_qr, p.hosvd_r, p.proj_chunk, p.tc_stages);
+  return b;
+}
+
+// Median of three timed recompressions after one untimed call (ms), or a negative value when the
+// schedule failed (an error status, a device fault report or a CUDA error).
+double time_schedule(tks_plan* plan, void* ws, double* out, int32_t* ranks, cudaStream_t st) {
+  if (tucker_sum_recompress(plan, ws, out, ranks, st) != TKS_OK) return -1.0;
+  if (tks_sync_status(plan, st) != TKS_OK) return -1.0;
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+    if (a) cudaEventDestroy(a);
+    return -1.0;
+  }
+  float t[3] = {0.f, 0.f, 0.f};
+  bool ok = true;
+  for (int i = 0; i < 3 && ok; ++i) {
+    ok = cudaEventRecord(a, st) == cudaSuccess && tucker_sum_recompress(plan, ws, out, ranks, st) == TKS_OK &&
+         cudaEventRecord(b, st) == cudaSuccess && cudaEventSynchronize(b) == cudaSuccess &&
+         cudaEventElapsedTime(&t[i], a, b) == cudaSuccess;
+  }
+  ok = ok && tks_sync_status(plan, st) == TKS_OK;
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (!ok) return -1.0;
+  std::sort(t, t + 3);
+  return t[1];
+}
+
+// Greedy search from the rule: lanes first, then each schedule knob in turn; a candidate replaces the
+// current pick only when it is at least 2% faster.  Scratch buffers grow with the largest workspace.
+tks_status autotune_plan(tks_plan** out, const tks_problem* problems, int32_t num_problems, const tks_params& prm) {
+  tks_params cur = prm;
+  cur.autotune = 0;
+  tks_plan* best = nullptr;
+  tks_status st = create_plan(&best, problems, num_problems, &cur);
+  if (st != TKS_OK) return st;
+  if (prm.precision == TKS_FP64) {
+    best->tuning_rule = cur;
+    *out = best;
+    return TKS_OK;
+  }
+  void* ws = nullptr;
+  double* o = nullptr;
+  int32_t* rk = nullptr;
+  size_t ws_cap = 0;
+  cudaStream_t stream = nullptr;
+  auto cleanup = [&]() {
+    if (ws) cudaFree(ws);
+    if (o) cudaFree(o);
+    if (rk) cudaFree(rk);
+    if (stream) cudaStreamDestroy(stream);
+  };
+  auto ensure_ws = [&](size_t bytes) {
+    if (bytes <= ws_cap) return true;
+    if (ws) cudaFree(ws);
+    ws = nullptr;
+    ws_cap = 0;
+    if (cudaMalloc(&ws, bytes) != cudaSuccess) return false;
+    ws_cap = bytes;
+    return true;
+  };
+  if (cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaMalloc(reinterpret_cast<void**>(&o), (size_t)std::max<int64_t>(1, best->output_elems) * 8) != cudaSuccess ||
+      cudaMalloc(reinterpret_cast<void**>(&rk), (size_t)num_problems * TKS_MAX_ORDER * 4) != cudaSuccess ||
+      !ensure_ws(std::max<size_t>(best->ws_bytes, 256))) {
+    cleanup();
+    tks_plan_destroy(best);
+    return fail(TKS_ENOMEM, "autotune scratch buffers");
+  }
+  double best_ms = time_schedule(best, ws, o, rk, stream);
+  if (best_ms < 0.0) {
+    cleanup();
+    tks_plan_destroy(best);
+    return fail(TKS_ECUDA, "autotune: the rule schedule failed");
+  }
+  const double rule_ms = best_ms;
+  const tks_params rule = cur;
+  std::string cand = "[{\"knobs\": " + knobs_json(cur) + ", \"ms\": " + std::to_string(best_ms) + "}";
+  const bool f32la = prm.precision == TKS_MIXED_F32LA;
+  std::vector<std::pair<int32_t tks_params::*, std::vector<int32_t>>> knobs;
+  std::vector<int32_t> lane_opts;
+  for (int l = 1; l <= 4 && l <= num_problems; ++l) lane_opts.push_back(l);
+  knobs.push_back({&tks_params::lanes, lane_opts});
+  if (!f32la) {
+    knobs.push_back({&tks_params::sketch_qr, {0, 2}});
+    knobs.push_back({&tks_params::hosvd_r, {0, 2}});
+  }
+  knobs.push_back({&tks_params::proj_chunk, {0, 8}});
+  knobs.push_back({&tks_params::tc_stages, {0, 3, 2}});
+  for (const auto& kv : knobs) {
+    const int32_t picked = cur.*(kv.first);
+    for (int32_t v : kv.second) {
+      if (v == picked || (kv.first == &tks_params::lanes && v <= 1 && picked <= 1)) continue;
+      tks_params c = cur;
+      c.*(kv.first) = v;
+      tks_plan* cp = nullptr;
+      if (create_plan(&cp, problems, num_problems, &c) != TKS_OK) continue;
+      double ms = -1.0;
+      if (ensure_ws(std::max<size_t>(cp->ws_bytes, 256))) ms = time_schedule(cp, ws, o, rk, stream);
+      cand += ", {\"knobs\": " + knobs_json(c) + ", \"ms\": " + std::to_string(ms) + "}";
+      if (ms > 0.0 && ms < 0.98 * best_ms) {
+        tks_plan_destroy(best);
+        best = cp;
+        best_ms = ms;
+        cur = c;
+      } else {
+        tks_plan_destroy(cp);
+      }
+    }
+  }
+  cleanup();
+  cand += "]";
+  best->autotuned = true;
+  best->tuning_candidates = cand;
+  best->tuning_rule = rule;
+  best->tuning_rule_ms = rule_ms;
+  best->tuning_picked_ms = best_ms;
+  *out = best;
+  return TKS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+tks_status tks_plan_create(tks_plan** out, const tks_problem* problems, int32_t num_problems,
+                           const tks_params* params) {
+  if (!out) return fail(TKS_EINVAL, "plan output pointer is NULL");
+  *out = nullptr;
+  if (!params) return fail(TKS_EINVAL, "no params");
+  if (params->autotune == 1) return autotune_plan(out, problems, num_problems, *params);
+  tks_status st = create_plan(out, problems, num_problems, params);
+  if (st == TKS_OK) (*out)->tuning_rule = *params;
+  return st;
+}
+
+tks_status tks_plan_tuning(const tks_plan* plan, char* buf, int64_t cap, int64_t* len) {
+  if (!plan || !len || (cap > 0 && !buf)) return fail(TKS_EINVAL, "null plan, len or buf");
+  std::string j = std::string("{\"autotuned\": ") + (plan->autotuned ? "1" : "0") +
+                  ", \"picked\": " + knobs_json(plan->params) + ", \"rule\": " + knobs_json(plan->tuning_rule) +
+                  ", \"rule_ms\": " + std::to_string(plan->tuning_rule_ms) +
+                  ", \"picked_ms\": " + std::to_string(plan->tuning_picked_ms) +
+                  ", \"candidates\": " + (plan->tuning_candidates.empty() ? "[]" : plan->tuning_candidates) + "}";
+  *len = (int64_t)j.size();
+  if (cap > 0) {
+    const size_t n = std::min<size_t>((size_t)cap - 1, j.size());
+    std::memcpy(buf, j.data(), n);
+    buf[n] = '\0';
+  }
+  return TKS_OK;
+}
+
+}  // extern "C"
+
 tks_status tks_project_core_backward(tks_plan* plan, void* workspace, const double* Q_in, const double* Hbar_in,
                                      double* dcores, double* dfactors, void* stream) {
   tks_status st = check_ws(plan, workspace);
@@ -2732,6 +2910,8 @@ tks_status tks_project_core_backward(tks_plan* plan, void* workspace, const doub
   if (!plan->backward_ok)
     return fail(TKS_EUNSUPPORTED, "tks_project_core_backward needs a plan of order-3 problems");
   if (!Q_in || !Hbar_in || !dcores || !dfactors) return fail(TKS_EINVAL, "null Q_in, Hbar_in, dcores or dfactors");
+  st = ensure_maps(plan, workspace, static_cast<cudaStream_t>(stream));
+  if (st != TKS_OK) return st;
   Bases b = bind(plan, workspace);
   b.p[B_Q] = reinterpret_cast<char*>(const_cast<double*>(Q_in));
   b.p[B_HBAR] = reinterpret_cast<char*>(const_cast<double*>(Hbar_in));

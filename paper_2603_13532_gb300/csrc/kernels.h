@@ -40,6 +40,7 @@ cudaError_t prepare_tc_gemm();
 // nothing sets, waited for by the copy-issuing thread before its first copy, or NULL.
 void launch_tc_gemm(const TcJob* jobs, int njobs, int total_tiles, const void* maps, int na_max, int nb_max,
                     const Bases& bases, Status* status, long long wait_cycles, const int* stall_word,
+                    int max_stages,
                     cudaStream_t stream);
 
 // Float32 CUDA-core kernels of the mixed path.

@@ -228,8 +228,9 @@ cudaError_t prepare_tc_gemm() {
 
 void launch_tc_gemm(const TcJob* jobs, int njobs, int total_tiles, const void* maps, int na_max, int nb_max,
                     const Bases& bases, Status* status, long long wait_cycles, const int* stall_word,
-                    cudaStream_t stream) {
-  const int stages = tc_gemm_stages(na_max, nb_max, 64);
+                    int max_stages, cudaStream_t stream) {
+  int stages = tc_gemm_stages(na_max, nb_max, 64);
+  if (max_stages > 0 && stages > max_stages) stages = max_stages;
   // at least 116 KB of shared memory keeps one CTA per SM, which owns all 512 TMEM columns
   const size_t smem = std::max<size_t>(tc_gemm_smem_bytes(stages, na_max, nb_max, 64), 116 * 1024);
   tc_gemm_kernel<64><<<total_tiles, 192, smem, stream>>>(jobs, njobs, static_cast<const CUtensorMap*>(maps), bases,
