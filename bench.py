@@ -497,7 +497,7 @@ def backward_leg(args, device, stream, rank, world):
 
 
 FP32_PEAK_TFLOPS = 152 * 256 * 2.070e9 / 1e12   # 128 FP32 FMA per SM per clock
-FP64_KINDS = {"gemm", "reduce", "qr", "core_sketch", "tsqr64", "svd64", "ttm64"}
+FP64_KINDS = {"gemm", "reduce", "qr", "core_sketch", "tsqr64", "svd64", "ttm64", "chol"}
 TENSOR_FP64_KINDS = {"oz_gemm", "oz_gram"}
 FP32_KINDS = {"simt", "core_sketch32", "qr32", "svd32", "tsqr32", "core_sketch3", "chain3", "qr_smem32",
               "project3", "sketch3", "qr_reg32", "ttm32", "fold4", "project4", "sketch3f", "sketch4"}
@@ -506,7 +506,7 @@ FP32_KINDS = {"simt", "core_sketch32", "qr32", "svd32", "tsqr32", "core_sketch3"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch per problem, from an ncu
 # capture of the same kernel binary on 16 decay512 problems (15.594 MB read + 0.274 MB written),
 # used to scale the measured traffic to the bench launch; only valid for that kernel and workload.
-NCU_TRAFFIC_PER_PROBLEM = {("decay512", "a7:project3[f32]"): (15.593984e6 + 0.273920e6) / 16}
+NCU_TRAFFIC_PER_PROBLEM = {("decay512", "project3"): (15.593984e6 + 0.273920e6) / 16}
 
 
 def project3_tensor_flops(plan, problems):
@@ -533,10 +533,28 @@ def roofline_from_profile(prof, calls, peaks, workload=None, problems=0, tensor_
     finish the launch's algorithmic flops.
     """
     total_ms = sum(s["ms"] for s in prof)
-    counted = [s for s in prof if s["flops"] > 0 or s["bytes"] > 0]
-    top = max(counted or prof, key=lambda s: s["ms"])
-    overall_top = max(prof, key=lambda s: s["ms"])
-    avg_s = top["ms"] / 1e3 / max(1, calls)
+    # the dominant kernel: the launch kind with the largest share of the step among those with an
+    # algorithmic count, its launches taken together (flops and time summed)
+    groups = {}
+    for s_ in prof:
+        if s_["flops"] > 0 or s_["bytes"] > 0:
+            g = groups.setdefault(s_["kind"], {"kind": s_["kind"], "ms": 0.0, "flops": 0.0, "bytes": 0.0,
+                                               "launches": 0, "names": []})
+            g["ms"] += s_["ms"]
+            g["flops"] += s_["flops"]
+            g["bytes"] += s_["bytes"]
+            g["launches"] += 1
+            g["names"].append(s_["name"])
+    top = max(groups.values(), key=lambda g: g["ms"]) if groups else dict(max(prof, key=lambda s_: s_["ms"]),
+                                                                          launches=1, names=[])
+    if not top["names"]:
+        top["names"] = [top.get("name", "")]
+    top["name"] = top["names"][0] if top["launches"] == 1 else f'{top["kind"]} ({top["launches"]} launches)'
+    overall_top = max(prof, key=lambda s_: s_["ms"])
+    # per launch: the group's flops and time divided by its launches
+    top["flops"] /= top["launches"]
+    top["bytes"] /= top["launches"]
+    avg_s = top["ms"] / 1e3 / max(1, calls) / top["launches"]
     kind = top["kind"]
     if kind == "project3" and top["flops"] > 0 and tensor_flops:
         f_tc = min(tensor_flops, top["flops"])
@@ -566,16 +584,17 @@ def roofline_from_profile(prof, calls, peaks, workload=None, problems=0, tensor_
                     "unit": "GB/s", "peak_source": "measured hbm_gbs"}
         roof["arithmetic_intensity"] = ai
     roof["frac"] = roof["achieved"] / roof["peak"]
-    per_problem = NCU_TRAFFIC_PER_PROBLEM.get((workload, top["name"]))
+    per_problem = NCU_TRAFFIC_PER_PROBLEM.get((workload, kind))
     roof["traffic"] = per_problem * problems if per_problem is not None else None
     if per_problem is not None:
         roof["traffic_note"] = "ncu DRAM bytes of the kernel on 16 problems, scaled to this launch's problems"
     roof["kernel"] = top["name"]
+    roof["launches_per_step"] = top["launches"]
     roof["kernel_share"] = top["ms"] / total_ms if total_ms > 0 else None
     roof["avg_launch_ms"] = avg_s * 1e3
     roof["algorithmic_flops_per_launch"] = top["flops"]
     roof["algorithmic_bytes_per_launch"] = top["bytes"]
-    if overall_top is not top:
+    if overall_top["name"] not in top["names"]:
         roof["longest_launch"] = {"name": overall_top["name"],
                                   "share": overall_top["ms"] / total_ms if total_ms > 0 else None}
     return roof

@@ -125,9 +125,13 @@ typedef struct {
                                    the recompression several times on a stream of its own and
                                    synchronizes the device. */
   int32_t sketch_qr;            /* TKS_MIXED QR of Y_n: 0 rule (shifted CholeskyQR3 where S_n <= 64
-                                   and n_n >= S_n, else Householder), 1 the same, 2 Householder always */
+                                   and n_n >= S_n, else Householder), 1 the same, 2 Householder always,
+                                   3 CholeskyQR2 where the rule takes CholeskyQR3 (a matrix whose
+                                   second pass finds X R^-1 far from orthonormal, any pivot below 1/4
+                                   of its diagonal entry, falls back to Householder) */
   int32_t hosvd_r;              /* TKS_MIXED triangular factor of H_(n)^T: 0 rule (shifted CholeskyQR3
-                                   for b_n <= 64, else Householder TSQR), 1 the same, 2 TSQR always */
+                                   for b_n <= 64, else Householder TSQR), 1 the same, 2 TSQR always,
+                                   3 CholeskyQR2 as for sketch_qr */
   int32_t proj_chunk;           /* fused order-3 projection: 0 rule (16), else 8 or 16 mode-3
                                    indices per staged chunk at most */
   int32_t tc_stages;            /* tensor-core GEMM shared-memory ring: 0 rule (up to 4 stages as the

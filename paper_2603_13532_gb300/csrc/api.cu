@@ -446,18 +446,20 @@ struct CqLists {
   std::vector<OzSliceJob> slice[3];
   std::vector<OzGemmJob> gemm[3];
   int xsl_total[3] = {0, 0, 0}, slice_total[3] = {0, 0, 0}, gemm_total[3] = {0, 0, 0};
-  double gram_flops = 0.0, gemm_flops[3] = {0.0, 0.0, 0.0};
+  double gram_flops = 0.0, gemm_flops[3] = {0.0, 0.0, 0.0}, chol_flops[3] = {0.0, 0.0, 0.0};
 
   // Rout: where the last pass writes R (B_NONE: not wanted); Qout: where X R^-1 of the last pass goes
-  // (B_NONE: no third product).  Returns the fallback flag operand (nonzero: a Cholesky step broke
-  // down and the Householder factorization must run for this matrix).
+  // (B_NONE: no product after the last Cholesky step).  passes = 3: shifted CholeskyQR3; passes = 2:
+  // CholeskyQR2 (no shift; for condition numbers below about u^-1/2, a breakdown otherwise).  Returns
+  // the fallback flag operand (nonzero: a Cholesky step broke down and the Householder factorization
+  // must run for this matrix).
   Operand add(tks_plan* plan, Operand src, int64_t P, int64_t L, int b, const CqBuffers& B, Operand Rout,
-              Operand Qout) {
+              Operand Qout, int passes = 3) {
     const int64_t ldP = (P + 7) / 8 * 8;
     const int ldk = 64;
     const Operand flag = op(B_WS, B.flag);
     const Operand X[3] = {src, op(B_WS, B.X[0]), op(B_WS, B.X[1])};
-    for (int pass = 0; pass < 3; ++pass) {
+    for (int pass = 0; pass < passes; ++pass) {
       OzXSliceJob xj;
       std::memset(&xj, 0, sizeof(xj));
       xj.src = X[pass];
@@ -495,8 +497,17 @@ struct CqLists {
       ch.P = P;
       ch.b = b;
       ch.pass = pass + 1;
+      ch.shift = passes == 3 && pass == 0;
+      ch.last = pass == passes - 1;
+      // pass 1: any positive pivot.  CholeskyQR3 passes 2, 3: X R1^-1 may have a condition number
+      // near u^-1/2, so only near-singular pivots fail.  CholeskyQR2 pass 2: X R1^-1 must already be
+      // close to orthonormal (||Q1^T Q1 - I|| <= 0.6 keeps every pivot above 1/4 of its diagonal
+      // entry), else one more pass would not restore orthogonality to rounding and the matrix goes to
+      // Householder.
+      ch.pivot_tol = pass == 0 ? 0.0 : (passes == 3 ? 1e-12 : 0.25);
+      chol_flops[pass] += (double)b * b * b;
       chol[pass].push_back(ch);
-      if (pass == 2 && Qout.base == B_NONE) break;
+      if (ch.last && Qout.base == B_NONE) break;
       // the next X (or Q) = X Rinv: X's digits (column exponents, folded into Rinv's rows) and the
       // digits of the columns of Rinv
       auto slice_job = [&](Operand s_src, size_t planes, size_t expo, int64_t rows, int64_t Ls) {
@@ -532,7 +543,7 @@ struct CqLists {
       }
       g.expA = Operand{B_NONE, 0, 0};
       g.expB = sr.expo;
-      g.Y = pass == 2 ? Qout : X[pass + 1];
+      g.Y = pass == passes - 1 ? Qout : X[pass + 1];
       g.L = L;
       g.rmax = b;
       gemm[pass].push_back(g);
@@ -552,7 +563,7 @@ struct CqLists {
       std::snprintf(nm, sizeof(nm), "%s.gram%d[oz]", tag, pass + 1);
       plan->push(steps, S_OZGRAM, gram[pass], (int64_t)gram[pass].size(), nm, gram_flops / 3.0, 0.0);
       std::snprintf(nm, sizeof(nm), "%s.chol%d", tag, pass + 1);
-      plan->push(steps, S_CHOL, chol[pass], (int64_t)chol[pass].size(), nm);
+      plan->push(steps, S_CHOL, chol[pass], (int64_t)chol[pass].size(), nm, chol_flops[pass], 0.0);
       if (gemm[pass].empty()) continue;
       std::snprintf(nm, sizeof(nm), "%s.slice%d[oz]", tag, pass + 1);
       plan->push(steps, S_OZSLICE, slice[pass], slice_total[pass], nm);
@@ -816,7 +827,7 @@ static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
           // Q_n by shifted CholeskyQR3 (float64-accurate Grams and products on the tensor cores);
           // the Householder QR runs only if a Cholesky step breaks down (a rank-deficient sketch)
           q.gate = qcq.add(plan, op(B_Y, h.y_off[n] * 8), (int64_t)nn, (int64_t)nn, h.S[n], h.qcq[n], Operand{B_NONE, 0, 0},
-                           op(B_Q, h.q_off[n] * 8));
+                           op(B_Q, h.q_off[n] * 8), plan->params.sketch_qr == 3 ? 2 : 3);
         }
         qr.push_back(q);
       }
@@ -1592,6 +1603,7 @@ static void build_hosvd_f64(tks_plan* plan) {
   for (int n = 0; n < plan->dmax; ++n) {
     std::vector<std::vector<TsqrJob>> tsqr;
     std::vector<SvdJob> svds;
+    double svd_flops = 0.0;
     std::vector<TtmJob> ttm, fac;
     std::vector<OzSliceJob> oz_slices;
     std::vector<OzGemmJob> oz_gemms;
@@ -1617,7 +1629,8 @@ static void build_hosvd_f64(tks_plan* plan) {
       if (cholqr) {
         const CqBuffers B{{h.cqX[0], h.cqX[1]}, h.cqCol, h.cqColE, h.cqG, h.cqRinv, h.cqRacc, h.cqFlag,
                           h.ozA, h.ozEA, h.ozB, h.ozEB, h.cqPart};
-        gate = cq.add(plan, X, L * Rr, L, b, B, op(B_WS, h.R64), Operand{B_NONE, 0, 0});
+        gate = cq.add(plan, X, L * Rr, L, b, B, op(B_WS, h.R64), Operand{B_NONE, 0, 0},
+                      plan->params.hosvd_r == 3 ? 2 : 3);
       }
       // TSQR of H_(n)^T: element (l + L rr, c) at l + L c + L b rr.  Level 0 factors blocks of dense
       // rows; every later level factors groups of the previous level's b x b triangular factors,
@@ -1695,6 +1708,9 @@ static void build_hosvd_f64(tks_plan* plan) {
       sj.order = d;
       sj.tol = plan->params.trunc_tol;
       svds.push_back(sj);
+      // algorithmic count of an SVD giving the singular values and left vectors of a b x b matrix:
+      // Golub and Van Loan's R-SVD, 4 m^2 n + 22 n^3 with m = n = b (Jacobi executes its own count)
+      svd_flops += 26.0 * (double)b * b * b;
       // H x_n P_n^T (fibres (l, rr) of H_(n)) and U~_n = Q_n P_n (fibres = rows of Q_n)
       TtmJob tj;
       std::memset(&tj, 0, sizeof(tj));
@@ -1786,7 +1802,7 @@ static void build_hosvd_f64(tks_plan* plan) {
                  lvl == 0 && any_tsqr_work ? qflops : 0.0, 0.0);
     }
     std::snprintf(nm, sizeof(nm), "a9:svd%d", n);
-    plan->push(plan->st_recompress, S_SVD64, svds, (int64_t)svds.size(), nm);
+    plan->push(plan->st_recompress, S_SVD64, svds, (int64_t)svds.size(), nm, svd_flops, 0.0);
     if (emulate) {
       std::snprintf(nm, sizeof(nm), "a9:slice%d[oz]", n);
       plan->push(plan->st_recompress, S_OZSLICE, oz_slices, oz_slice_total, nm);
@@ -1845,8 +1861,8 @@ static tks_status create_plan(tks_plan** out, const tks_problem* problems, int32
   if (prm.omega_lowprec != 0 && prm.omega_lowprec != 1) return fail(TKS_EINVAL, "omega_lowprec must be 0 or 1");
   if (prm.lanes < 0 || prm.lanes > 8) return fail(TKS_EINVAL, "lanes must be 0..8");
   if (prm.autotune != 0 && prm.autotune != 1) return fail(TKS_EINVAL, "autotune must be 0 or 1");
-  if (prm.sketch_qr < 0 || prm.sketch_qr > 2) return fail(TKS_EINVAL, "sketch_qr must be 0..2");
-  if (prm.hosvd_r < 0 || prm.hosvd_r > 2) return fail(TKS_EINVAL, "hosvd_r must be 0..2");
+  if (prm.sketch_qr < 0 || prm.sketch_qr > 3) return fail(TKS_EINVAL, "sketch_qr must be 0..3");
+  if (prm.hosvd_r < 0 || prm.hosvd_r > 3) return fail(TKS_EINVAL, "hosvd_r must be 0..3");
   if (prm.proj_chunk != 0 && prm.proj_chunk != 8 && prm.proj_chunk != 16)
     return fail(TKS_EINVAL, "proj_chunk must be 0, 8 or 16");
   if (prm.tc_stages != 0 && (prm.tc_stages < 2 || prm.tc_stages > 4)) return fail(TKS_EINVAL, "tc_stages must be 0 or 2..4");
@@ -2833,8 +2849,8 @@ tks_status autotune_plan(tks_plan** out, const tks_problem* problems, int32_t nu
   for (int l = 1; l <= 4 && l <= num_problems; ++l) lane_opts.push_back(l);
   knobs.push_back({&tks_params::lanes, lane_opts});
   if (!f32la) {
-    knobs.push_back({&tks_params::sketch_qr, {0, 2}});
-    knobs.push_back({&tks_params::hosvd_r, {0, 2}});
+    knobs.push_back({&tks_params::sketch_qr, {0, 3, 2}});
+    knobs.push_back({&tks_params::hosvd_r, {0, 3, 2}});
   }
   knobs.push_back({&tks_params::proj_chunk, {0, 8}});
   knobs.push_back({&tks_params::tc_stages, {0, 3, 2}});

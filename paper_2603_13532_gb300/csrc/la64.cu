@@ -819,7 +819,7 @@ __global__ void __launch_bounds__(kCholThreads) chol_step_kernel(const CholJob* 
   }
   __syncthreads();
   bool fail = sh_fail != 0;         // the same value in every thread from here on
-  if (!fail && J.pass == 1) {
+  if (!fail && J.shift) {
     double tr = 0.0;
     for (int i = 0; i < b; ++i) tr += dg[i];
     const double shift = 11.0 * ((double)J.P * b + (double)b * (b + 1)) * 1.1102230246251565e-16 * tr;
@@ -835,7 +835,7 @@ __global__ void __launch_bounds__(kCholThreads) chol_step_kernel(const CholJob* 
   if (!fail) __syncthreads();
   for (int j = 0; j < b && !fail; ++j) {
     const double d = A[j + ld * j];
-    const double bound = J.pass == 1 ? 0.0 : 1e-12 * dg[j];
+    const double bound = J.pivot_tol * dg[j];
     if (!(d > bound) || !isfinite(d)) {
       fail = true;
       break;
@@ -883,7 +883,7 @@ __global__ void __launch_bounds__(kCholThreads) chol_step_kernel(const CholJob* 
   }
   __syncthreads();
   // Racc <- R Racc (pass 1: Racc = R); the last pass writes it to Rout when one is given
-  double* out = (J.pass == 3 && J.Rout.base != B_NONE) ? at<double>(bases, J.Rout) : Racc;
+  double* out = (J.last && J.Rout.base != B_NONE) ? at<double>(bases, J.Rout) : Racc;
   if (r < b) {
     for (int c = ty; c < b; c += 4) {
       double acc;

@@ -226,28 +226,41 @@ __global__ void __launch_bounds__(kOzXThreads) oz_xdig_kernel(const OzXSliceJob*
   uint16_t* colP = at<uint16_t>(bases, J.colP);
   uint16_t* rowP = at<uint16_t>(bases, J.rowP);
   const int64_t cstride = 64 * J.ldP, rstride = J.rows_pad * 64;
-  // column planes: a warp writes 32 consecutive rows i of one plane row a
+  // each element's magnitude once (M < 2^56, the sign in bit 63), kept as bits in place of the value
+  for (int e = threadIdx.x; e < kOzXRows * 64; e += kOzXThreads) {
+    const int q = e >> 6, a = e & 63;
+    if (q < nq && a < b) {
+      bool neg;
+      const unsigned long long M = oz_magnitude(xs[q][a], es[a], neg);
+      xs[q][a] = __longlong_as_double((long long)(M | (neg ? (1ull << 63) : 0ull)));
+    }
+  }
+  __syncthreads();
+  auto digit = [&](int q, int a, int sl) -> uint32_t {
+    if (q >= nq || a >= b) return 0u;
+    const unsigned long long v = (unsigned long long)__double_as_longlong(xs[q][a]);
+    return oz_digit(v & ~(1ull << 63), sl, (v >> 63) != 0);
+  };
+  // column planes: thread (row pair, column); a warp stores 32 x 4 contiguous bytes per plane row
   {
-    const int q = threadIdx.x & 63;
-    if (q < nq)
-      for (int a = threadIdx.x >> 6; a < b; a += kOzXThreads / 64) {
-        bool neg;
-        const unsigned long long M = oz_magnitude(xs[q][a], es[a], neg);
-        uint16_t* out = colP + (int64_t)a * J.ldP + i0 + q;
+    const int q0 = 2 * (threadIdx.x & 31);
+    if (q0 < nq)
+      for (int a = threadIdx.x >> 5; a < b; a += kOzXThreads / 32) {
+        uint32_t* out = reinterpret_cast<uint32_t*>(colP + (int64_t)a * J.ldP + i0 + q0);
 #pragma unroll
-        for (int sl = 0; sl < kOzSlices; ++sl) out[sl * cstride] = oz_digit(M, sl, neg);
+        for (int sl = 0; sl < kOzSlices; ++sl)
+          out[sl * (cstride / 2)] = digit(q0, a, sl) | (digit(q0 + 1, a, sl) << 16);
       }
   }
-  // row planes: a warp writes 32 consecutive columns a of one plane row i
+  // row planes: thread (column pair, row); a warp stores one 128-byte plane row
   {
-    const int a = threadIdx.x & 63;
-    if (a < b)
-      for (int q = threadIdx.x >> 6; q < nq; q += kOzXThreads / 64) {
-        bool neg;
-        const unsigned long long M = oz_magnitude(xs[q][a], es[a], neg);
-        uint16_t* out = rowP + (i0 + q) * 64 + a;
+    const int a0 = 2 * (threadIdx.x & 31);
+    if (a0 < b)
+      for (int q = threadIdx.x >> 5; q < nq; q += kOzXThreads / 32) {
+        uint32_t* out = reinterpret_cast<uint32_t*>(rowP + (i0 + q) * 64 + a0);
 #pragma unroll
-        for (int sl = 0; sl < kOzSlices; ++sl) out[sl * rstride] = oz_digit(M, sl, neg);
+        for (int sl = 0; sl < kOzSlices; ++sl)
+          out[sl * (rstride / 2)] = digit(q, a0, sl) | (digit(q, a0 + 1, sl) << 16);
       }
   }
 }

@@ -30,6 +30,20 @@ constexpr int kATile = kBM * kBK * 2;         // 16 KB
 // 64 columns fill the 512 TMEM columns of the SM (one CTA per SM: its shared memory is 227 KB).
 constexpr int kAcc = 8;
 
+// float32 -> float64 by the bits (exact): the conversion instruction runs on GB300's float64 pipe,
+// about 1/64 of the integer rate.  Normal numbers and zeros take the bit path; subnormals, infinities
+// and NaN the conversion.
+__device__ __forceinline__ double f32_to_f64_exact(float v) {
+  const uint32_t u = __float_as_uint(v);
+  const uint32_t e = (u >> 23) & 0xffu;
+  const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+  if (e != 0u && e != 0xffu)
+    return __longlong_as_double((long long)(sign | ((unsigned long long)(e + 896u) << 52) |
+                                            ((unsigned long long)(u & 0x7fffffu) << 29)));
+  if ((u & 0x7fffffffu) == 0u) return __longlong_as_double((long long)sign);
+  return (double)v;
+}
+
 __device__ __forceinline__ void record_status_tc(Status* st, int code) {
   if (st) atomicCAS(&st->code, 0, code);
 }
@@ -184,9 +198,8 @@ __global__ void __launch_bounds__(192, 1)
             const int col = n0 + c0 + j;
             if (col >= J.N) continue;
             const float v = E.alpha * sum[j];
-            const double vd = (double)v;
             if (o32) o32[row * E.f32_m + col * E.f32_n] = v;
-            if (o64) o64[row * E.f64_m + col * E.f64_n] = vd;
+            if (o64) o64[row * E.f64_m + col * E.f64_n] = f32_to_f64_exact(v);
             if (ob0) {
               const int64_t off = row * E.bf_m + col * E.bf_n;
               const uint16_t h0 = bf16_bits(v);

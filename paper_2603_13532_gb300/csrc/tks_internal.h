@@ -398,7 +398,9 @@ struct CholJob {
   Operand G, Rinv, Racc, Rout, fallback;
   Operand xexp;          // int32 column exponents of X: Rinv row a is written times 2^xexp[a] (B_NONE: none)
   int64_t P;
-  int32_t b, pass;
+  int32_t b, pass;       // pass 1 starts Racc; later passes read *fallback
+  int32_t shift, last;   // shift: add s I first (shifted CholeskyQR3); last: write Racc to Rout
+  double pivot_tol;      // a pivot d_j <= pivot_tol G_jj (or not positive) sets *fallback
 };
 
 // Effective subrank heuristic (Alg. 5), float64 throughout.

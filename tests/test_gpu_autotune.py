@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 from oracle import sketch_sum as ss
-from oracle.tensor import tucker_full
+from oracle.tensor import tucker_entries, tucker_full
 from paper_2603_13532_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
@@ -40,7 +40,8 @@ def _check_against_oracle(probs, outs, seed):
         assert got["ranks"] == ref["ranks"]
 
 
-@pytest.mark.parametrize("schedule", [{"sketch_qr": 2}, {"hosvd_r": 2}, {"proj_chunk": 8}, {"tc_stages": 2},
+@pytest.mark.parametrize("schedule", [{"sketch_qr": 2}, {"hosvd_r": 2}, {"sketch_qr": 3, "hosvd_r": 3},
+                                      {"proj_chunk": 8}, {"tc_stages": 2},
                                       {"lanes": 3, "sketch_qr": 2, "hosvd_r": 2, "proj_chunk": 8, "tc_stages": 3}])
 def test_every_schedule_meets_the_oracle(cuda_lib, schedule):
     from paper_2603_13532_gb300 import binding
@@ -73,10 +74,30 @@ def test_autotuned_plan_reports_and_replays_its_schedule(cuda_lib):
             assert np.array_equal(fa, fb)
 
 
-@pytest.mark.parametrize("schedule", [{"proj_chunk": 5}, {"tc_stages": 1}, {"sketch_qr": 3}, {"hosvd_r": -1},
+@pytest.mark.parametrize("schedule", [{"proj_chunk": 5}, {"tc_stages": 1}, {"sketch_qr": 4}, {"hosvd_r": -1},
                                       {"lanes": 9}])
 def test_bad_knobs_are_rejected(cuda_lib, schedule):
     from paper_2603_13532_gb300 import binding
     with pytest.raises(binding.TksError) as e:
         binding.Plan(_problems()[:1], kind="krp", precision="mixed", seed=1, schedule=schedule)
     assert e.value.code == 1
+
+
+@pytest.mark.parametrize("schedule", [{"sketch_qr": 3, "hosvd_r": 3}, {"sketch_qr": 2, "hosvd_r": 2}])
+def test_decay512_schedules_meet_the_oracle(cuda_lib, schedule):
+    """The ill-conditioned workload (mode spectra decaying like 10^(-i/8): unfoldings with condition
+    numbers near 1e7): two-pass CholeskyQR, or Householder throughout, still matches the oracle."""
+    from paper_2603_13532_gb300 import binding
+    w = wl.decay512()
+    p = w.problems[0]
+    plan = binding.Plan(w.problems, kind="krp", precision="mixed", seed=w.seed, schedule=schedule)
+    ref = ss.recompress(p.terms(), "krp", p.target, p.oversampling, seed=w.seed, problem=0, alpha=p.alpha,
+                        rounding="bf16")
+    got = plan.recompress()[0]
+    assert got["ranks"] == ref["ranks"] == [48, 48, 48]
+    idx = np.random.default_rng(1).integers(0, 512, size=(400, 3))
+    eg = tucker_entries(got["core"], got["factors"], idx)
+    eo = tucker_entries(ref["core"], ref["factors"], idx)
+    ex = sum(tucker_entries(G, Us, idx) for G, Us in p.terms())
+    scale = np.sqrt(np.mean(ex ** 2))
+    assert np.sqrt(np.mean((eg - eo) ** 2)) <= 1e-5 * scale
