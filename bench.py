@@ -489,6 +489,17 @@ def backward_leg(args, device, stream, rank, world):
             ref_f = np.hstack([rU[k][m] for k in range(p.num_terms)]).ravel(order="F")
             errs.append(np.linalg.norm(df[off: off + ref_f.size] - ref_f) / np.linalg.norm(ref_f))
             off += p.dims[m] * R[m]
+        if not args.no_cpu:
+            t0, done = time.perf_counter(), 0
+            while done < P and time.perf_counter() - t0 < args.cpu_seconds / 2:
+                q = problems[done]
+                ss.project_core_vjp(q.terms(), Qs[done], Hbars[done])
+                done += 1
+            dt = time.perf_counter() - t0
+            leg["cpu_baseline"] = {"value": done / dt, "unit": "gradients/s", "cores": os.cpu_count(),
+                                   "kind": "oracle",
+                                   "sample": f"{done} of the {P} problems in {dt:.1f} s (numpy float64 "
+                                             f"vector-Jacobian product, BLAS on all host cores)"}
         leg["vs_oracle"] = {"dcores": float(np.linalg.norm(dc[:nc] - ref_c) / np.linalg.norm(ref_c)),
                             "dfactors": float(max(errs)), "problems": 1,
                             "note": "relative Frobenius error of the first problem's mixed gradients against "
@@ -866,6 +877,8 @@ def main():
         got = sr_rank.cpu().numpy().reshape(-1, binding.MAX_ORDER)
         got = np.concatenate([got[i, :p.order] for i, p in enumerate(problems)])
         achieved = sp.info.flops * args.subrank_steps / el_sr / 1e12
+        executed = sp.executed_flops()
+        achieved_exec = executed * args.subrank_steps / el_sr / 1e12
         subrank = {"value": weak_scaling_rate(P, world, args.subrank_steps, el_sr), "unit": "problems/s",
                    "ms_per_call": 1e3 * el_sr / args.subrank_steps, "steps": args.subrank_steps,
                    "eps": args.subrank_eps, "launches_per_call": int(sp.info.launches),
@@ -880,7 +893,13 @@ def main():
                                               "ends early on numerically rank-deficient Gram matrices "
                                               "(decay512: after ~130 of 512 steps), so the count exceeds "
                                               "the executed work there",
-                                "traffic": None}}
+                                "traffic": None,
+                                "executed_flops_per_call": executed,
+                                "achieved_executed": achieved_exec,
+                                "frac_executed": achieved_exec / FP64_PEAK_TFLOPS,
+                                "executed_note": "the Gram matrices plus 4 (m - k)^2 per reduction step the "
+                                                 "tridiagonalization ran before its early end (read back from "
+                                                 "the device after the calls)"}}
         if rank == 0 and not args.no_cpu:
             rate, done, dt = oracle_subrank_rate(problems, args.subrank_eps, args.cpu_seconds / 2)
             subrank["cpu_baseline"] = {"value": rate, "unit": "problems/s", "cores": os.cpu_count(),

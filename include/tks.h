@@ -118,8 +118,9 @@ typedef struct {
    * linear-algebra choices change the rounding only (float64-accurate either way). */
   int32_t autotune;             /* 1 (mixed modes): tks_plan_create times candidate schedules on the
                                    plan's own inputs before returning (lanes, then each knob below,
-                                   one at a time from the rule, keeping a candidate only when it is
-                                   at least 2% faster), using a scratch workspace and outputs it
+                                   one at a time from the rule, a second round when the first changed
+                                   anything, keeping a candidate only when it is at least 2% faster),
+                                   using a scratch workspace and outputs it
                                    allocates and frees; the plan keeps the fastest and reports the
                                    candidates and times through tks_plan_tuning.  Autotuning runs
                                    the recompression several times on a stream of its own and
@@ -371,6 +372,14 @@ TKS_API tks_status tks_plan_set_fault_test(tks_plan* plan, int64_t wait_cycles, 
 /* Synchronizes stream, then returns and clears the first error a kernel of this plan recorded
  * (TKS_ENONFINITE for a NaN or Inf in a Gram matrix), else TKS_OK. */
 TKS_API tks_status tks_subrank_sync_status(tks_subrank_plan* plan, void* stream);
+
+/* Flops the last tks_effective_subrank call executed (Alg. 5 phase 1, float64): the Gram matrices'
+ * 2 c m(m+1)/2 plus, for each matrix, sum_{k < K} 4 (m - k)^2 over the K reduction steps the
+ * tridiagonalization ran before its trailing block was numerically zero (K = m - 1 without an early
+ * end), so that achieved rates can be stated on the work done rather than the 4/3 m^3 of a full
+ * reduction.  Reads a small device array synchronously: call it after tks_subrank_sync_status.
+ * *flops (host) receives the count. */
+TKS_API tks_status tks_subrank_executed_flops(const tks_subrank_plan* plan, double* flops);
 
 TKS_API const char* tks_last_error(void);
 TKS_API const char* tks_status_string(tks_status status);

@@ -131,10 +131,11 @@ def load(path=None):
                                              ctypes.POINTER(ctypes.c_int64)]
     lib.tks_effective_subrank.argtypes = [P, P, P, P, P, P]
     lib.tks_subrank_sync_status.argtypes = [P, P]
+    lib.tks_subrank_executed_flops.argtypes = [P, ctypes.POINTER(ctypes.c_double)]
     for name in ["tks_plan_create", "tks_plan_info", "tks_problem_info", "tks_generate_omega",
                  "tucker_sum_sketch", "tks_project_core", "tucker_sum_recompress", "tks_sync_status",
                  "tks_profile_begin", "tks_profile_end", "tks_subrank_plan_create", "tks_truncate_core",
-                 "tks_plan_set_fault_test", "tks_subrank_info", "tks_plan_tuning",
+                 "tks_plan_set_fault_test", "tks_subrank_info", "tks_plan_tuning", "tks_subrank_executed_flops",
                  "tks_subrank_problem_info", "tks_effective_subrank", "tks_subrank_sync_status"]:
         getattr(lib, name).restype = ctypes.c_int
     _LIB = lib
@@ -496,6 +497,12 @@ class SubrankPlan:
 
     def sync(self):
         _check(self.lib.tks_subrank_sync_status(self.handle, _stream_handle()))
+
+    def executed_flops(self):
+        """Flops the last run executed (Gram matrices plus the reduction steps before the early end)."""
+        f = ctypes.c_double()
+        _check(self.lib.tks_subrank_executed_flops(self.handle, ctypes.byref(f)))
+        return f.value
 
     def run(self, eigenvalues=False):
         """Per problem: dict(rank=[rank_n], ell=[ell_n], lam=[descending eigenvalues] or None)."""

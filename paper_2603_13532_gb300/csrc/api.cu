@@ -2793,8 +2793,9 @@ double time_schedule(tks_plan* plan, void* ws, double* out, int32_t* ranks, cuda
   return t[1];
 }
 
-// Greedy search from the rule: lanes first, then each schedule knob in turn; a candidate replaces the
-// current pick only when it is at least 2% faster.  Scratch buffers grow with the largest workspace.
+// Greedy search from the rule: lanes first, then each schedule knob in turn, a second round when the
+// first changed anything; a candidate replaces the current pick only when it is at least 2% faster.
+// Scratch buffers grow with the largest workspace.
 tks_status autotune_plan(tks_plan** out, const tks_problem* problems, int32_t num_problems, const tks_params& prm) {
   tks_params cur = prm;
   cur.autotune = 0;
@@ -2854,6 +2855,9 @@ tks_status autotune_plan(tks_plan** out, const tks_problem* problems, int32_t nu
   }
   knobs.push_back({&tks_params::proj_chunk, {0, 8}});
   knobs.push_back({&tks_params::tc_stages, {0, 3, 2}});
+  // coordinate descent: a second round revisits every knob once the first changed any
+  for (int round = 0; round < 2; ++round) {
+  const tks_params before = cur;
   for (const auto& kv : knobs) {
     const int32_t picked = cur.*(kv.first);
     for (int32_t v : kv.second) {
@@ -2874,6 +2878,8 @@ tks_status autotune_plan(tks_plan** out, const tks_problem* problems, int32_t nu
         tks_plan_destroy(cp);
       }
     }
+  }
+  if (std::memcmp(&before, &cur, sizeof(cur)) == 0) break;
   }
   cleanup();
   cand += "]";

@@ -346,7 +346,7 @@ constexpr int kOzBM = 128, kOzBN = 64, kOzBK = 64;
 constexpr int kOzATile = kOzBM * kOzBK * 2;     // 16 KB per plane
 constexpr int kOzBTile = kOzBN * kOzBK * 2;     // 8 KB per plane
 constexpr int kOzGemmThreads = 320;             // TMA, MMA and 8 epilogue warps
-constexpr size_t kOzSmem = 1024 + (size_t)kOzSlices * (kOzATile + kOzBTile) + 64;
+constexpr size_t kOzSmem = 1024 + (size_t)kOzSlices * (kOzATile + kOzBTile) + 64 + 8 * 32 * 9 * sizeof(double);
 
 __device__ __forceinline__ int oz_tile_job(const OzGemmJob* __restrict__ jobs, int njobs, int t) {
   int lo = 0, hi = njobs - 1;
@@ -371,6 +371,7 @@ __global__ void __launch_bounds__(kOzGemmThreads, 1) oz_gemm_kernel(const OzGemm
   uint64_t* tmem_empty = tmem_full + 1;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tmem_empty + 1);
   volatile int* err = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  double* ostage = reinterpret_cast<double*>(smem + kOzSlices * (kOzATile + kOzBTile) + 64);   // 8 warps x 32 x 9
   const int t_begin = (int)(((long long)blockIdx.x * total_tiles) / gridDim.x);
   const int t_end = (int)(((long long)(blockIdx.x + 1) * total_tiles) / gridDim.x);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -494,33 +495,61 @@ __global__ void __launch_bounds__(kOzGemmThreads, 1) oz_gemm_kernel(const OzGemm
       const int64_t r = live ? (int64_t)row / J.L : 0, l = (int64_t)row - r * J.L;
       double* y = Y + l + J.L * (int64_t)J.rmax * r;
       const int n0 = tn * kOzBN + cbase;
+      // this thread's row, columns n0 .. n0 + 31, composed before TMEM is released
+      double outv[32];
+#pragma unroll
       for (int c0 = 0; c0 < 32; c0 += 8) {
-        if (n0 + c0 >= J.N) break;   // warp-uniform
-        uint32_t v[kOzLevels][8];
+        if (n0 + c0 < J.N) {   // warp-uniform
+          uint32_t v[kOzLevels][8];
 #pragma unroll
-        for (int acc = 0; acc < kOzLevels; ++acc)
-          tc::tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * kOzBN + cbase + c0), v[acc]);
-        tc::tmem_ld_wait();
+          for (int acc = 0; acc < kOzLevels; ++acc)
+            tc::tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * kOzBN + cbase + c0), v[acc]);
+          tc::tmem_ld_wait();
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int col = n0 + c0 + j;
-          if (!live || col >= J.N) continue;
-          // exact integers below 2^24: sum_acc A_acc 2^(21 - 7 acc) in two 64-bit halves
-          long long hi64 = 0, lo64 = 0;
+          for (int j = 0; j < 8; ++j) {
+            const int col = n0 + c0 + j;
+            // exact integers below 2^24: sum_acc A_acc 2^(21 - 7 acc) in two 64-bit halves
+            long long hi64 = 0, lo64 = 0;
 #pragma unroll
-          for (int acc = 0; acc < 4; ++acc)
-            hi64 = (hi64 << 7) + (long long)__float2int_rn(__uint_as_float(v[acc][j]));
+            for (int acc = 0; acc < 4; ++acc)
+              hi64 = (hi64 << 7) + (long long)__float2int_rn(__uint_as_float(v[acc][j]));
 #pragma unroll
-          for (int acc = 4; acc < kOzLevels; ++acc)
-            lo64 = (lo64 << 7) + (long long)__float2int_rn(__uint_as_float(v[acc][j]));
-          // value = 2^-35 (hi + 2^-28 lo) 2^(eA + eB) = (hi 2^28 + lo) 2^(eA + eB - 63)
-          y[J.L * (int64_t)col] = oz_compose(hi64, lo64, eA + expB[col] - 63);
+            for (int acc = 4; acc < kOzLevels; ++acc)
+              lo64 = (lo64 << 7) + (long long)__float2int_rn(__uint_as_float(v[acc][j]));
+            // value = 2^-35 (hi + 2^-28 lo) 2^(eA + eB) = (hi 2^28 + lo) 2^(eA + eB - 63)
+            outv[c0 + j] = (live && col < J.N) ? oz_compose(hi64, lo64, eA + expB[col] - 63) : 0.0;
+          }
         }
       }
       // every TMEM read of this tile has completed: the next tile's products may start
       tc::fence_before_sync();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(tmem_empty);
+      if (J.L == 1) {
+        // rows are contiguous runs of rmax: transpose 32 rows x 8 columns through shared memory so
+        // that each store covers four rows' 64-byte segments instead of 32 scattered words
+        double* st = ostage + (warp - 2) * (32 * 9);
+        const int row0 = tm * kOzBM + 32 * q;
+#pragma unroll
+        for (int c0 = 0; c0 < 32; c0 += 8) {
+          if (n0 + c0 < J.N) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) st[lane * 9 + j] = outv[c0 + j];
+            __syncwarp();
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const int r = 4 * i + (lane >> 3), c = lane & 7;
+              const int rw = row0 + r, col = n0 + c0 + c;
+              if (rw < J.M && col < J.N) Y[(int64_t)J.rmax * rw + col] = st[r * 9 + c];
+            }
+            __syncwarp();
+          }
+        }
+      } else if (live) {
+#pragma unroll
+        for (int c = 0; c < 32; ++c)
+          if (n0 + c < J.N) y[J.L * (int64_t)(n0 + c)] = outv[c];
+      }
       ++tiles;
     }
   }
@@ -536,15 +565,17 @@ __global__ void __launch_bounds__(kOzGemmThreads, 1) oz_gemm_kernel(const OzGemm
 // accumulators and issues the 36 digit-pair products per k-block with A and B the same 64-column tiles
 // (an M = 128 product also reads the 64 rows after a tile, whose results land in TMEM lanes 64..127
 // and are ignored).  Every kOzGramGroup k-blocks the level sums, exact integers (8 pairs x 128 x
-// 127^2 < 2^24), are drained by warps 4 and 5 (TMEM lanes 0..63), combined in 64-bit integers and
-// added into two 64-bit integer accumulators per entry in shared memory, so G is the exact sum rounded
-// once at the end, with the scale 2^(e_i + e_j).  Waits are bounded as in the other tensor-core kernels.
+// 127^2 < 2^24), are drained by warps 4, 5, 8 and 9 (TMEM lanes 0..63, half the columns each),
+// combined in 64-bit integers and added into two 64-bit integer accumulators per entry in shared
+// memory, so G is the exact sum rounded once at the end, with the scale 2^(e_i + e_j).  Waits are
+// bounded as in the other tensor-core kernels.
 constexpr int kOzGramGroup = 2;
+constexpr int kOzGramThreads = 320;   // TMA, MMA, and drain warps 4, 5, 8, 9 (two per TMEM lane quadrant)
 constexpr int kOzPlaneTile = 64 * kOzBK * 2;                          // 8 KB: 64 columns x 64 k
 constexpr int kOzStageBytes = (kOzSlices + 1) * kOzPlaneTile;         // + the 8 KB an M = 128 read passes
 constexpr size_t kOzGramSmem = 1024 + 2 * (size_t)kOzStageBytes + 2 * 64 * 64 * 8 + 128;
 
-__global__ void __launch_bounds__(192, 1) oz_gram_kernel(const OzGramJob* __restrict__ jobs,
+__global__ void __launch_bounds__(kOzGramThreads, 1) oz_gram_kernel(const OzGramJob* __restrict__ jobs,
                                                        const CUtensorMap* __restrict__ maps, Bases bases,
                                                        Status* status, long long wait_cycles) {
   extern __shared__ uint8_t og_smem_raw[];
@@ -569,7 +600,7 @@ __global__ void __launch_bounds__(192, 1) oz_gram_kernel(const OzGramJob* __rest
       tc::mbar_init(&empty[st], 1);
     }
     tc::mbar_init(tmem_full, 1);
-    tc::mbar_init(tmem_empty, 2);
+    tc::mbar_init(tmem_empty, 4);
     *err = 0;
     tc::fence_barrier_init();
   }
@@ -639,10 +670,11 @@ __global__ void __launch_bounds__(192, 1) oz_gram_kernel(const OzGramJob* __rest
       // the last group's products have completed before teardown
       if (!*err && !tc::mbar_wait(tmem_full, (ngroups - 1) & 1, wait_cycles)) *err = 1;
     }
-  } else if ((warp & 3) < 2) {
-    // warps 4 and 5: TMEM lanes 0..63 (the rows of G)
+  } else if (warp >= 4 && (warp & 3) < 2) {
+    // warps 4, 5 (columns 0..31) and 8, 9 (columns 32..63): TMEM lanes 0..63 (the rows of G)
     const int q = warp & 3;
     const int row = 32 * q + lane;
+    const int cb = warp >= 8 ? 32 : 0;
     for (int g = 0; g < ngroups; ++g) {
       bool ok = tc::mbar_wait(tmem_full, g & 1, wait_cycles);
       ok = __all_sync(0xffffffffu, ok) && !*err;
@@ -651,7 +683,7 @@ __global__ void __launch_bounds__(192, 1) oz_gram_kernel(const OzGramJob* __rest
         break;
       }
       tc::fence_after_sync();
-      for (int c0 = 0; c0 < kOzBN; c0 += 8) {
+      for (int c0 = cb; c0 < cb + 32 && c0 < J.b; c0 += 8) {
         uint32_t v[kOzLevels][8];
 #pragma unroll
         for (int acc = 0; acc < kOzLevels; ++acc)
@@ -718,7 +750,7 @@ void launch_oz_xdig(const OzXSliceJob* jobs, int njobs, int total_tiles, const B
 
 void launch_oz_gram(const OzGramJob* jobs, int njobs, const void* maps, const Bases& bases, Status* status,
                     long long wait_cycles, cudaStream_t stream) {
-  oz_gram_kernel<<<njobs, 192, kOzGramSmem, stream>>>(jobs, static_cast<const CUtensorMap*>(maps), bases, status,
+  oz_gram_kernel<<<njobs, kOzGramThreads, kOzGramSmem, stream>>>(jobs, static_cast<const CUtensorMap*>(maps), bases, status,
                                                       wait_cycles);
 }
 

@@ -202,6 +202,7 @@ __global__ void __launch_bounds__(kTriThreads, 1) tridiag_f64_kernel(const Subra
   bool have_prev = false;
   bool bad = false;
   bool stopped = false;
+  int executed = m > 1 ? m - 1 : 0;
   double delta = 0.0;
   for (int k = 0; k + 1 < m; ++k) {
     double* colk = A + (int64_t)m * k;
@@ -234,6 +235,7 @@ __global__ void __launch_bounds__(kTriThreads, 1) tridiag_f64_kernel(const Subra
           eg[i] = 0.0;
         }
         stopped = true;
+        executed = k;
         break;
       }
     }
@@ -358,6 +360,7 @@ __global__ void __launch_bounds__(kTriThreads, 1) tridiag_f64_kernel(const Subra
     eg[m - 1] = 0.0;
     if (!isfinite(dg[m - 1])) bad = true;
   }
+  if (tid == 0 && J.steps) *J.steps = executed;
   if (bad) record_status(status, TKS_ENONFINITE);
 }
 

@@ -59,7 +59,9 @@ struct tks_subrank_plan {
   Status* status = nullptr;
   size_t ws_bytes = 0, ws_ev = 0;
   int64_t eval_elems = 0;
-  double flops = 0.0;
+  double flops = 0.0, gram_flops = 0.0;
+  std::vector<int> job_m;                  // order of each tridiagonalization job's matrix
+  int32_t* steps = nullptr;                // device: executed reduction steps per job (in the arena)
 };
 
 extern "C" {
@@ -174,6 +176,7 @@ tks_status tks_subrank_plan_create(tks_subrank_plan** out, const tks_problem* pr
       gjobs.push_back(g);
       const double kc = h.aat ? (double)h.R : (double)h.n;
       plan->flops += 2.0 * kc * 0.5 * h.m * (h.m + 1.0) + 4.0 / 3.0 * std::pow((double)h.m, 3.0);
+      plan->gram_flops += 2.0 * kc * 0.5 * h.m * (h.m + 1.0);
       plan->mats.push_back(h);
     }
     plan->order.push_back(d);
@@ -201,6 +204,7 @@ tks_status tks_subrank_plan_create(tks_subrank_plan** out, const tks_problem* pr
     s.p = problems[h.p].oversampling[h.mode];
     s.eps = prm.trunc_tol;
     sjobs.push_back(s);
+    plan->job_m.push_back(h.m);
   }
   plan->nw = (int)wjobs.size();
   plan->ng = (int)gjobs.size();
@@ -217,8 +221,14 @@ tks_status tks_subrank_plan_create(tks_subrank_plan** out, const tks_problem* pr
   plan->off_s = add(sjobs.data(), sizeof(SubrankJob) * sjobs.size());
   const Status zero{0, 0};
   const size_t off_status = add(&zero, sizeof(zero));
+  const std::vector<int32_t> zsteps(std::max<size_t>(1, sjobs.size()), 0);
+  const size_t off_steps = add(zsteps.data(), sizeof(int32_t) * zsteps.size());
   cudaError_t e = cudaMalloc(&plan->arena, host.size());
   if (e != cudaSuccess) return reject(TKS_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  // every tridiagonalization job records its executed steps in the arena
+  plan->steps = reinterpret_cast<int32_t*>(plan->arena + off_steps);
+  for (size_t i = 0; i < sjobs.size(); ++i)
+    reinterpret_cast<SubrankJob*>(host.data() + plan->off_s)[i].steps = plan->steps + i;
   e = cudaMemcpy(plan->arena, host.data(), host.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = prepare_subrank();
   if (e != cudaSuccess) {
@@ -246,6 +256,20 @@ tks_status tks_subrank_info(const tks_subrank_plan* plan, tks_subrank_info_t* in
   info->launches = 4;
   info->max_dim = plan->max_m;
   info->flops = plan->flops;
+  return TKS_OK;
+}
+
+tks_status tks_subrank_executed_flops(const tks_subrank_plan* plan, double* flops) {
+  if (!plan || !flops) return fail(TKS_EINVAL, "null plan or flops");
+  std::vector<int32_t> st(plan->job_m.size(), 0);
+  if (!st.empty())
+    SR_CUDA_CHECK(cudaMemcpy(st.data(), plan->steps, sizeof(int32_t) * st.size(), cudaMemcpyDeviceToHost));
+  double f = plan->gram_flops;
+  for (size_t i = 0; i < st.size(); ++i) {
+    const double m = plan->job_m[i];
+    for (int k = 0; k < st[i]; ++k) f += 4.0 * (m - k) * (m - k);
+  }
+  *flops = f;
   return TKS_OK;
 }
 

@@ -437,6 +437,7 @@ struct SubrankJob {
   Operand rank, ell;      // int32 outputs
   int32_t m, order, p, pad;
   double eps;
+  int32_t* steps;         // device: reduction steps the tridiagonalization executed (its early end)
 };
 
 struct Status {
