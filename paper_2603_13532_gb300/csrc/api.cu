@@ -2857,29 +2857,29 @@ tks_status autotune_plan(tks_plan** out, const tks_problem* problems, int32_t nu
   knobs.push_back({&tks_params::tc_stages, {0, 3, 2}});
   // coordinate descent: a second round revisits every knob once the first changed any
   for (int round = 0; round < 2; ++round) {
-  const tks_params before = cur;
-  for (const auto& kv : knobs) {
-    const int32_t picked = cur.*(kv.first);
-    for (int32_t v : kv.second) {
-      if (v == picked || (kv.first == &tks_params::lanes && v <= 1 && picked <= 1)) continue;
-      tks_params c = cur;
-      c.*(kv.first) = v;
-      tks_plan* cp = nullptr;
-      if (create_plan(&cp, problems, num_problems, &c) != TKS_OK) continue;
-      double ms = -1.0;
-      if (ensure_ws(std::max<size_t>(cp->ws_bytes, 256))) ms = time_schedule(cp, ws, o, rk, stream);
-      cand += ", {\"knobs\": " + knobs_json(c) + ", \"ms\": " + std::to_string(ms) + "}";
-      if (ms > 0.0 && ms < 0.98 * best_ms) {
-        tks_plan_destroy(best);
-        best = cp;
-        best_ms = ms;
-        cur = c;
-      } else {
-        tks_plan_destroy(cp);
+    const tks_params before = cur;
+    for (const auto& kv : knobs) {
+      const int32_t picked = cur.*(kv.first);
+      for (int32_t v : kv.second) {
+        if (v == picked || (kv.first == &tks_params::lanes && v <= 1 && picked <= 1)) continue;
+        tks_params c = cur;
+        c.*(kv.first) = v;
+        tks_plan* cp = nullptr;
+        if (create_plan(&cp, problems, num_problems, &c) != TKS_OK) continue;
+        double ms = -1.0;
+        if (ensure_ws(std::max<size_t>(cp->ws_bytes, 256))) ms = time_schedule(cp, ws, o, rk, stream);
+        cand += ", {\"knobs\": " + knobs_json(c) + ", \"ms\": " + std::to_string(ms) + "}";
+        if (ms > 0.0 && ms < 0.98 * best_ms) {
+          tks_plan_destroy(best);
+          best = cp;
+          best_ms = ms;
+          cur = c;
+        } else {
+          tks_plan_destroy(cp);
+        }
       }
     }
-  }
-  if (std::memcmp(&before, &cur, sizeof(cur)) == 0) break;
+    if (std::memcmp(&before, &cur, sizeof(cur)) == 0) break;
   }
   cleanup();
   cand += "]";
