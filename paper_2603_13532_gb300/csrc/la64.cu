@@ -370,6 +370,8 @@ __device__ int jacobi_sweeps_f64(double* A, int ld, int b, int m, int max_sweeps
   const int k = threadIdx.x / kJ64Lanes;
   const int pairs = m / 2;
   const double thr = (double)b * 1.1102230246251565e-16, thr2 = thr * thr;
+  __shared__ double sh_g[TKS_MAX_BASIS / 2], sh_mp[TKS_MAX_BASIS / 2], sh_mq[TKS_MAX_BASIS / 2];
+  __shared__ int sh_act[TKS_MAX_BASIS / 2];
   int* rot_prev = flags;       // column rotated during the previous sweep (all set before the first)
   int* rot_cur = flags + m;    // column rotated so far in this sweep
   for (int c = threadIdx.x; c < m; c += blockDim.x) {
@@ -409,57 +411,71 @@ __device__ int jacobi_sweeps_f64(double* A, int ld, int b, int m, int max_sweeps
       double* ap = A + p * ld;
       double* aq = A + q * ld;
       double2 x[kJ64Chunks], y[kJ64Chunks];
-      double g0 = 0.0, g1 = 0.0;
+      double g = 0.0;
+      if (__any_sync(0xffffffffu, valid)) {
+        double g0 = 0.0, g1 = 0.0;
 #pragma unroll
-      for (int u = 0; u < kJ64Chunks; ++u) {
-        const int i = 2 * (sub + kJ64Lanes * u);
-        const bool in = valid && i < b;
-        x[u] = in ? *reinterpret_cast<const double2*>(ap + i) : make_double2(0.0, 0.0);
-        y[u] = in ? *reinterpret_cast<const double2*>(aq + i) : make_double2(0.0, 0.0);
-        g0 = fma(x[u].x, y[u].x, g0);
-        g1 = fma(x[u].y, y[u].y, g1);
+        for (int u = 0; u < kJ64Chunks; ++u) {
+          const int i = 2 * (sub + kJ64Lanes * u);
+          const bool in = valid && i < b;
+          x[u] = in ? *reinterpret_cast<const double2*>(ap + i) : make_double2(0.0, 0.0);
+          y[u] = in ? *reinterpret_cast<const double2*>(aq + i) : make_double2(0.0, 0.0);
+          g0 = fma(x[u].x, y[u].x, g0);
+          g1 = fma(x[u].y, y[u].y, g1);
+        }
+        g = g0 + g1;
+#pragma unroll
+        for (int o = kJ64Lanes / 2; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o, kJ64Lanes);
       }
-      double g = g0 + g1;
-#pragma unroll
-      for (int o = kJ64Lanes / 2; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o, kJ64Lanes);
-      // the group's first lane decides and forms the rotation; every lane of the group follows
-      int act = 0;
-      double mp = 0.0, mq = 0.0;
-      if (valid && sub == 0) {
-        const double dp = dsc[p], dq = dsc[q];
-        const double al = nsq[p], be = nsq[q];
-        const double ga = dp * dq * g;
-        // |gamma| > thr sqrt(alpha beta), evaluated on values scaled by a power of two near
-        // 1 / max(alpha, beta) so that neither product under- or overflows
-        const double sc = pow2_inverse(fmax(al, be));
-        const double a1 = al * sc, b1 = be * sc, g1 = ga * sc;
-        if (sc > 0.0 && g1 * g1 > thr2 * a1 * b1 && fmin(al, be) > noise2) {
-          const double t = jacobi_tangent(be - al, 2.0 * ga);
-          // c = 1 / sqrt(w), w = 1 + t^2, from the float32 estimate and two Newton steps (float64
-          // accuracy: c^2 (1 + t^2) = 1 is what makes the rotation orthogonal)
-          const double w = fma(t, t, 1.0), hw = 0.5 * w;
-          double c = (double)rsqrtf((float)w);
-          c = c * fma(-hw * c, c, 1.5);
-          c = c * fma(-hw * c, c, 1.5);
-          const double c2 = c * c, wc = w * c;   // c^2 and sqrt(w)
-          const double ip = dinv[p], iq = dinv[q];
-          mp = t * dq * ip;
-          mq = t * dp * iq;
-          dsc[p] = c * dp;
-          dsc[q] = c * dq;
-          dinv[p] = ip * wc;
-          dinv[q] = iq * wc;
-          // the new squared norms for this t (exactly the rotated columns' norms, whatever t is)
-          nsq[p] = c2 * fma(t, fma(t, be, -2.0 * ga), al);
-          nsq[q] = c2 * fma(t, fma(t, al, 2.0 * ga), be);
-          rot_cur[p] = rot_cur[q] = 1;
-          act = 1;
+      if (sub == 0 && k < pairs) {
+        sh_g[k] = g;
+        sh_act[k] = valid ? 1 : 0;
+      }
+      __syncthreads();
+      // one warp forms every pair's rotation, lane = pair: the scalar float64 work of a round then
+      // issues as full warps instead of one lane in eight (the float64 pipe counts issued warps)
+      if (warp == 0) {
+        for (int pk = lane; pk < pairs; pk += 32) {
+          if (!sh_act[pk]) continue;
+          int pp, qq;
+          jacobi_pair(pk, round, m, pp, qq);
+          int act = 0;
+          const double dp = dsc[pp], dq = dsc[qq];
+          const double al = nsq[pp], be = nsq[qq];
+          const double ga = dp * dq * sh_g[pk];
+          // |gamma| > thr sqrt(alpha beta), evaluated on values scaled by a power of two near
+          // 1 / max(alpha, beta) so that neither product under- or overflows
+          const double sc = pow2_inverse(fmax(al, be));
+          const double a1 = al * sc, b1 = be * sc, g1 = ga * sc;
+          if (sc > 0.0 && g1 * g1 > thr2 * a1 * b1 && fmin(al, be) > noise2) {
+            const double t = jacobi_tangent(be - al, 2.0 * ga);
+            // c = 1 / sqrt(w), w = 1 + t^2, from the float32 estimate and two Newton steps (float64
+            // accuracy: c^2 (1 + t^2) = 1 is what makes the rotation orthogonal)
+            const double w = fma(t, t, 1.0), hw = 0.5 * w;
+            double c = (double)rsqrtf((float)w);
+            c = c * fma(-hw * c, c, 1.5);
+            c = c * fma(-hw * c, c, 1.5);
+            const double c2 = c * c, wc = w * c;   // c^2 and sqrt(w)
+            const double ip = dinv[pp], iq = dinv[qq];
+            sh_mp[pk] = t * dq * ip;
+            sh_mq[pk] = t * dp * iq;
+            dsc[pp] = c * dp;
+            dsc[qq] = c * dq;
+            dinv[pp] = ip * wc;
+            dinv[qq] = iq * wc;
+            // the new squared norms for this t (exactly the rotated columns' norms, whatever t is)
+            nsq[pp] = c2 * fma(t, fma(t, be, -2.0 * ga), al);
+            nsq[qq] = c2 * fma(t, fma(t, al, 2.0 * ga), be);
+            rot_cur[pp] = rot_cur[qq] = 1;
+            act = 1;
+          }
+          sh_act[pk] = act;
         }
       }
-      act = __shfl_sync(0xffffffffu, act, lead);
-      mp = __shfl_sync(0xffffffffu, mp, lead);
-      mq = __shfl_sync(0xffffffffu, mq, lead);
+      __syncthreads();
+      const int act = (k < pairs) ? sh_act[k] : 0;
       if (act) {
+        const double mp = sh_mp[k], mq = sh_mq[k];
 #pragma unroll
         for (int u = 0; u < kJ64Chunks; ++u) {
           const int i = 2 * (sub + kJ64Lanes * u);
@@ -790,9 +806,25 @@ size_t ttm64_smem(int bmax) {
 // The factor is kept as G = U^T D^-1 U with U's rows unscaled (d_j = U[j][j], the pivots), so a step
 // needs no square root:  R = D^-1/2 U,  R^-1 = Z D^-1/2 with Z the inverse of the unit triangle D^-1 U.
 constexpr int kCholThreads = 256;
+constexpr int kCholTri = 64 * 65 / 2;   // entries of a 64 x 64 upper triangle
 constexpr size_t kCholSmem = (3 * 64 * 65 + 2 * 64) * sizeof(double);
 
-__global__ void __launch_bounds__(kCholThreads) chol_step_kernel(const CholJob* __restrict__ jobs, Bases bases,
+// Upper-triangle index tables (r | c << 8): by row, rows from the last up (the trailing triangle
+// of elimination step j is the prefix of (b - 1 - j)(b - j) / 2 entries), and by diagonal c - r
+// (entries of one diagonal have dot products of equal length).  The float64 pipe issues per warp,
+// so the loops run over these flat lists with every lane busy rather than over predicated rows.
+__device__ __forceinline__ void chol_tables(int b, uint16_t* tri_r, uint16_t* tri_d) {
+  const int t = threadIdx.x;
+  if (t < b) {
+    const int w = b - 1 - t;                       // rows after t
+    const int off_r = w * (w + 1) / 2;
+    for (int c = t; c < b; ++c) tri_r[off_r + (c - t)] = (uint16_t)(t | (c << 8));
+    const int d = t, off_d = d * b - d * (d - 1) / 2;
+    for (int r = 0; r + d < b; ++r) tri_d[off_d + r] = (uint16_t)(r | ((r + d) << 8));
+  }
+}
+
+__global__ void __launch_bounds__(kCholThreads, 1) chol_step_kernel(const CholJob* __restrict__ jobs, Bases bases,
                                                                 Status* status) {
   extern __shared__ double cs64[];
   const CholJob& J = jobs[blockIdx.x];
@@ -803,20 +835,23 @@ __global__ void __launch_bounds__(kCholThreads) chol_step_kernel(const CholJob* 
   double* dv = Ra + b * ld;         // pivots d_j
   double* dg = dv + 64;             // the diagonal of G
   __shared__ double rdv[64];        // 1 / d_j
+  __shared__ double fr[64];         // the multipliers of one step
+  __shared__ uint16_t tri_r[kCholTri], tri_d[kCholTri];
   __shared__ int sh_fail;
-  const int r = threadIdx.x & 63, ty = threadIdx.x >> 6;
+  const int tid = threadIdx.x;
   int32_t* fb = at<int32_t>(bases, J.fallback);
   double* Rinv = at<double>(bases, J.Rinv);
   double* Racc = at<double>(bases, J.Racc);
   const double* G = at<const double>(bases, J.G);
-  if (threadIdx.x == 0) sh_fail = J.pass == 1 ? 0 : *fb;
-  for (int e = threadIdx.x; e < b * b; e += kCholThreads) {
+  if (tid == 0) sh_fail = J.pass == 1 ? 0 : *fb;
+  for (int e = tid; e < b * b; e += kCholThreads) {
     const int i = e % b, c = e / b;
     A[i + ld * c] = G[e];
     Z[i + ld * c] = i == c ? 1.0 : 0.0;
     if (J.pass > 1) Ra[i + ld * c] = Racc[e];
     if (i == c) dg[i] = G[e];
   }
+  chol_tables(b, tri_r, tri_d);
   __syncthreads();
   bool fail = sh_fail != 0;         // the same value in every thread from here on
   if (!fail && J.shift) {
@@ -824,14 +859,13 @@ __global__ void __launch_bounds__(kCholThreads) chol_step_kernel(const CholJob* 
     for (int i = 0; i < b; ++i) tr += dg[i];
     const double shift = 11.0 * ((double)J.P * b + (double)b * (b + 1)) * 1.1102230246251565e-16 * tr;
     fail = !isfinite(tr);
-    if (!fail && ty == 0 && r < b) A[r + ld * r] += shift;
+    if (!fail && tid < b) A[tid + ld * tid] += shift;
     __syncthreads();
   }
-  // right-looking elimination: step j takes the pivot d = U[j][j] and updates rows r > j,
-  // A[r][c] -= (A[j][r] / d) A[j][c] for r <= c; every thread reads the same pivot, so all leave together.
-  // The float64 pipe is the scarce unit here, so each step's one division is taken by the thread that
-  // finished the next pivot in the step before (1 / A[0][0] up front), and the rows use its reciprocal.
-  if (!fail && threadIdx.x == 0) rdv[0] = 1.0 / A[0];
+  // right-looking elimination: step j takes the pivot d = U[j][j] and updates the trailing triangle,
+  // A[r][c] -= (A[j][r] / d) A[j][c] for j < r <= c; every thread reads the same pivot, so all leave
+  // together.  Each step's one division is taken by the thread that finishes the next pivot.
+  if (!fail && tid == 0) rdv[0] = 1.0 / A[0];
   if (!fail) __syncthreads();
   for (int j = 0; j < b && !fail; ++j) {
     const double d = A[j + ld * j];
@@ -840,64 +874,68 @@ __global__ void __launch_bounds__(kCholThreads) chol_step_kernel(const CholJob* 
       fail = true;
       break;
     }
-    if (threadIdx.x == 0) dv[j] = d;
-    if (r > j && r < b) {
-      const double f = A[j + ld * r] * rdv[j];
-      // c runs over one residue mod 4 from j + 1 for the whole warp: A[j][c] is a broadcast and the
-      // warp's rows r are consecutive words
-      for (int c = j + 1 + ((ty - j - 1) & 3); c < b; c += 4) {
-        if (c < r) continue;
-        const double v = fma(-f, A[j + ld * c], A[r + ld * c]);
-        A[r + ld * c] = v;
-        if (c == r && r == j + 1) rdv[r] = 1.0 / v;
-      }
+    if (tid == 0) dv[j] = d;
+    if (tid > j && tid < b) fr[tid] = A[j + ld * tid] * rdv[j];
+    __syncthreads();
+    const int w = b - 1 - j, n = w * (w + 1) / 2;
+    for (int e = tid; e < n; e += kCholThreads) {
+      const int r = tri_r[e] & 255, c = tri_r[e] >> 8;
+      const double v = fma(-fr[r], A[j + ld * c], A[r + ld * c]);
+      A[r + ld * c] = v;
+      if (c == r && r == j + 1) rdv[r] = 1.0 / v;
     }
     __syncthreads();
   }
   if (fail) {
     // this job takes the Householder fallback: an identity Rinv keeps the following products harmless
-    for (int e = threadIdx.x; e < b * b; e += kCholThreads) Rinv[e] = (e % b == e / b) ? 1.0 : 0.0;
-    if (threadIdx.x == 0) *fb = 1;
+    for (int e = tid; e < b * b; e += kCholThreads) Rinv[e] = (e % b == e / b) ? 1.0 : 0.0;
+    if (tid == 0) *fb = 1;
     return;
   }
-  // Z from the bottom: step k subtracts (U[i][k] / d_i) Z[k][:] from the rows i < k (row k is final)
-  const double inv_d = r < b ? rdv[r] : 0.0;
+  // Z from the bottom: step k subtracts (U[i][k] / d_i) Z[k][:] from the rows i < k (row k is final);
+  // the k x (b - k) block is one flat list, e -> (e mod k, k + e div k) with the quotient from a float32
+  // reciprocal (exact here: e < 4096 and k <= 64 keep the product 2^-22 away from the next integer)
   for (int k = b - 1; k > 0; --k) {
-    if (r < k) {
-      const double u = A[r + ld * k] * inv_d;
-      for (int c = k + ((ty - k) & 3); c < b; c += 4) Z[r + ld * c] = fma(-u, Z[k + ld * c], Z[r + ld * c]);
+    if (tid < k) fr[tid] = A[tid + ld * k] * rdv[tid];
+    __syncthreads();
+    const float rk = 1.0f / (float)k;
+    const int n = k * (b - k);
+    for (int e = tid; e < n; e += kCholThreads) {
+      const int qd = (int)(((float)e + 0.5f) * rk), i = e - qd * k, c = k + qd;
+      Z[i + ld * c] = fma(-fr[i], Z[k + ld * c], Z[i + ld * c]);
     }
     __syncthreads();
   }
   // R = D^-1/2 U in place, Rinv = Z D^-1/2 (row a times 2^xexp[a] when X's digits carry column exponents)
   __shared__ int xe[64];
-  if (threadIdx.x < b) {
-    dg[threadIdx.x] = sqrt(rdv[threadIdx.x]);
-    xe[threadIdx.x] = J.xexp.base != B_NONE ? at<const int32_t>(bases, J.xexp)[threadIdx.x] : 0;
+  if (tid < b) {
+    dg[tid] = sqrt(rdv[tid]);
+    xe[tid] = J.xexp.base != B_NONE ? at<const int32_t>(bases, J.xexp)[tid] : 0;
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < b * b; e += kCholThreads) {
+  for (int e = tid; e < b * b; e += kCholThreads) {
     const int i = e % b, c = e / b;
     A[i + ld * c] = i <= c ? A[i + ld * c] * dg[i] : 0.0;
     Rinv[e] = i <= c ? scalbn(Z[i + ld * c] * dg[c], xe[i]) : 0.0;
   }
   __syncthreads();
-  // Racc <- R Racc (pass 1: Racc = R); the last pass writes it to Rout when one is given
+  // Racc <- R Racc (pass 1: Racc = R); the last pass writes it to Rout when one is given.  Both are
+  // upper triangular, so T[r][c] = sum_{k = r..c} R[r][k] Racc[k][c], taken diagonal by diagonal.
   double* out = (J.last && J.Rout.base != B_NONE) ? at<double>(bases, J.Rout) : Racc;
-  if (r < b) {
-    for (int c = ty; c < b; c += 4) {
-      double acc;
-      if (J.pass == 1) {
-        acc = A[r + ld * c];
-      } else {
-        // R and Racc are upper triangular: k runs over r..c
-        acc = 0.0;
-        for (int k = r; k <= c; ++k) acc = fma(A[r + ld * k], Ra[k + ld * c], acc);
-      }
+  if (J.pass == 1) {
+    for (int e = tid; e < b * b; e += kCholThreads) out[e] = A[(e % b) + ld * (e / b)];
+  } else {
+    const int n = b * (b + 1) / 2;
+    for (int e = tid; e < n; e += kCholThreads) {
+      const int r = tri_d[e] & 255, c = tri_d[e] >> 8;
+      double acc = 0.0;
+      for (int k = r; k <= c; ++k) acc = fma(A[r + ld * k], Ra[k + ld * c], acc);
       out[r + b * c] = acc;
     }
+    for (int e = tid; e < b * b; e += kCholThreads)
+      if (e % b > e / b) out[e] = 0.0;
   }
-  if (J.pass == 1 && threadIdx.x == 0) *fb = 0;
+  if (J.pass == 1 && tid == 0) *fb = 0;
   (void)status;
 }
 

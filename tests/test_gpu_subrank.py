@@ -177,25 +177,27 @@ def test_decay512_bf16(cuda_lib):
 
 def test_executed_flops_count_the_early_end(cuda_lib):
     """decay512's Gram matrices (n = 512, rank ~128) end their reduction early: the executed count lies
-    between the Gram flops alone and the algorithmic count, well below the latter; a full-rank matrix
-    runs every step, so its executed count is the full reduction (sum_k 4 (m - k)^2, k < m - 1)."""
+    between the Gram flops alone and the algorithmic count (stopping after ~130 of 511 steps still runs
+    the costliest steps, about 60% of a full reduction's flops); a full-rank matrix runs every step, so
+    its executed count is the full reduction (sum_k 4 (m - k)^2, k < m - 1)."""
     from paper_2603_13532_gb300 import binding
     w = wl.decay512(num_problems=2)
     plan = binding.SubrankPlan(w.problems, 1e-6, dtype="bf16")
     plan.run()
     ex = plan.executed_flops()
-    gram = plan.info.flops - 6 * 4.0 / 3.0 * 512.0 ** 3   # the algorithmic count less the full reductions
-    assert gram < ex < 0.6 * plan.info.flops
+    full = 6 * 4.0 / 3.0 * 512.0 ** 3
+    gram = plan.info.flops - full   # the algorithmic count less the full reductions
+    assert gram < ex < gram + 0.8 * full
     g = np.random.default_rng(6)
     dims, r = [40, 40, 40], 12
     p = wl.Problem(dims, [g.standard_normal((r, r, r)) for _ in range(5)],
                    [[g.standard_normal((n, r)) for n in dims] for _ in range(5)], [4, 4, 4], [2, 2, 2])
-    full = binding.SubrankPlan([p], 1e-6, dtype="fp64")
-    full.run()
+    whole = binding.SubrankPlan([p], 1e-6, dtype="fp64")
+    whole.run()
     m = 40   # R = 60 > n = 40: the n x n form, full rank
     red = sum(4.0 * (m - k) ** 2 for k in range(m - 1))
     gram_f = 3 * 2.0 * 60 * 0.5 * m * (m + 1)
-    assert abs(full.executed_flops() - (gram_f + 3 * red)) <= 1e-9 * full.executed_flops()
+    assert abs(whole.executed_flops() - (gram_f + 3 * red)) <= 1e-9 * whole.executed_flops()
 
 
 # ------------------------------------------------------------------ edges
