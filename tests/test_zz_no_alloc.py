@@ -116,29 +116,6 @@ def test_noalloc_two_calls_back_to_back_on_one_stream(cuda_lib, kind):
         _assert_close(_unpack(Y, prob, pinfo), ref, kind)
 
 
-def test_noalloc_refuses_a_capturing_stream(cuda_lib):
-    """While the stream is being captured the call enqueues nothing and says why."""
-    from paper_2603_13532_gb300 import binding
-    lib = binding.load()
-    prob = _problems(44)[0]
-    prm = binding.Params_t(1, 0, 0, 5, 0.0, 0, 0)
-    flat, views = binding.pack_inputs([prob], "fp64", torch.device("cuda"))
-    keep = []
-    pt = _problem_t(binding, prob, views[0], keep)
-    Y = torch.zeros(1 << 16, dtype=torch.float64, device="cuda")
-    torch.cuda.synchronize()
-    side = torch.cuda.Stream()
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.stream(side):
-        with torch.cuda.graph(graph, stream=side):
-            Y.add_(1.0)
-            rc = lib.tucker_sum_sketch_noalloc(ctypes.byref(pt), ctypes.byref(prm), ctypes.c_void_p(Y.data_ptr()),
-                                               ctypes.c_void_p(side.cuda_stream))
-    torch.cuda.synchronize()
-    assert rc == 7, lib.tks_last_error()
-    assert b"captured" in lib.tks_last_error()
-
-
 def test_noalloc_rejects_problems_beyond_the_static_scratch(cuda_lib):
     from paper_2603_13532_gb300 import binding
     lib = binding.load()
