@@ -79,8 +79,10 @@ Step make_step(StepKind kind, size_t off, int njobs, int64_t work, const char* n
 // Workspace of shifted CholeskyQR3 of one tall matrix (byte offsets): the two re-formed X, the column
 // digit planes and exponents, the Gram matrix, R^-1, the accumulated R, the fallback flag, and the row
 // digit planes and exponents of X and of R^-1.
+// rowA, colE: X's row digit planes and column exponents in pass 1; rowA2, colE2: those of the later
+// passes (the same buffers when pass 1's digits need not outlive the factorization)
 struct CqBuffers {
-  size_t X[2], col, colE, G, Rinv, Racc, flag, rowA, rowAE, rowB, rowBE, part;
+  size_t X[2], col, colE, G, Rinv, Racc, flag, rowA, rowAE, rowB, rowBE, part, rowA2, colE2;
 };
 
 struct ProbHost {
@@ -103,6 +105,7 @@ struct ProbHost {
   size_t R64 = 0, stk64[2] = {};   // float64 ST-HOSVD: triangular factor and TSQR stacks
   size_t ozA = 0, ozQ = 0, ozB = 0, ozEA = 0, ozEQ = 0, ozEB = 0;   // TKS_MIXED mode products: digit planes
   size_t cqX[2] = {}, cqCol = 0, cqColE = 0, cqG = 0, cqRinv = 0, cqRacc = 0, cqFlag = 0, cqPart = 0;   // CholeskyQR3
+  size_t cqRowA2 = 0, cqColE2 = 0, ozB2 = 0, ozEB2 = 0;   // later passes; unscaled P digits for Q_n P_n
   CqBuffers qcq[MAXD] = {};   // TKS_MIXED: CholeskyQR3 of the sketches Y_n (flag == 0: Householder QR)
   std::vector<size_t> chain;   // 2 ping-pong buffers per term
   // mixed-precision buffers (bytes): bf16 planes and float32 intermediates
@@ -464,15 +467,16 @@ struct CqLists {
       std::memset(&xj, 0, sizeof(xj));
       xj.src = X[pass];
       xj.part = op(B_WS, B.part);
-      xj.expo = op(B_WS, B.colE);
+      xj.expo = op(B_WS, pass == 0 ? B.colE : B.colE2);
       xj.colP = op(B_WS, B.col);
-      xj.rowP = op(B_WS, B.rowA);
+      xj.rowP = op(B_WS, pass == 0 ? B.rowA : B.rowA2);
       xj.P = P;
       xj.L = L;
       xj.ldP = ldP;
       xj.rows_pad = (P + 7) / 8 * 8;
       xj.b = b;
       xj.tiles = oz_xslice_tiles(P);
+      xj.want_rows = (pass < passes - 1 || Qout.base != B_NONE) ? 1 : 0;
       xj.tile_begin = xsl_total[pass];
       xsl_total[pass] += xj.tiles;
       xsl[pass].push_back(xj);
@@ -513,6 +517,7 @@ struct CqLists {
       auto slice_job = [&](Operand s_src, size_t planes, size_t expo, int64_t rows, int64_t Ls) {
         OzSliceJob sj;
         std::memset(&sj, 0, sizeof(sj));
+        sj.kexp = Operand{B_NONE, 0, 0};
         sj.src = s_src;
         sj.planes = op(B_WS, planes);
         sj.expo = op(B_WS, expo);
@@ -1628,7 +1633,7 @@ static void build_hosvd_f64(tks_plan* plan) {
       Operand gate{B_NONE, 0, 0};
       if (cholqr) {
         const CqBuffers B{{h.cqX[0], h.cqX[1]}, h.cqCol, h.cqColE, h.cqG, h.cqRinv, h.cqRacc, h.cqFlag,
-                          h.ozA, h.ozEA, h.ozB, h.ozEB, h.cqPart};
+                          h.ozA, h.ozEA, h.ozB, h.ozEB, h.cqPart, h.cqRowA2, h.cqColE2};
         gate = cq.add(plan, X, L * Rr, L, b, B, op(B_WS, h.R64), Operand{B_NONE, 0, 0},
                       plan->params.hosvd_r == 3 ? 2 : 3);
       }
@@ -1742,9 +1747,11 @@ static void build_hosvd_f64(tks_plan* plan) {
         // the same two products, float64-accurate on the tensor cores: digit planes of the fibres
         // of H_(n), of the rows of Q_n and of the columns of P_n, then 128 x 64 tiles of Y
         const int ldk = b <= 64 ? 64 : 128;
-        auto slice = [&](Operand src, size_t planes, size_t expo, int64_t rows, int64_t Ls) {
+        auto slice = [&](Operand src, size_t planes, size_t expo, int64_t rows, int64_t Ls,
+                         Operand kexp = Operand{B_NONE, 0, 0}) {
           OzSliceJob sj2;
           std::memset(&sj2, 0, sizeof(sj2));
+          sj2.kexp = kexp;
           sj2.src = src;
           sj2.planes = op(B_WS, planes);
           sj2.expo = op(B_WS, expo);
@@ -1759,10 +1766,24 @@ static void build_hosvd_f64(tks_plan* plan) {
           oz_slices.push_back(sj2);
           return sj2;
         };
-        const OzSliceJob sx = slice(X, h.ozA, h.ozEA, L * Rr, L);
-        const OzSliceJob sp = slice(op(B_WS, h.P[n]), h.ozB, h.ozEB, rmax, 1);
+        // with CholeskyQR, pass 1 already cut H_(n)^T into digits against its column exponents (in ozA):
+        // the mode product reuses them with those exponents folded into the rows of P_n (no row
+        // exponents of X); Q_n P_n takes P_n's own digits
+        OzSliceJob sx;
+        if (cholqr) {
+          std::memset(&sx, 0, sizeof(sx));
+          sx.planes = op(B_WS, h.ozA);
+          sx.expo = Operand{B_NONE, 0, 0};
+          sx.rows = L * Rr;
+          sx.rows_pad = (sx.rows + 7) / 8 * 8;
+        } else {
+          sx = slice(X, h.ozA, h.ozEA, L * Rr, L);
+        }
+        const OzSliceJob sp = cholqr ? slice(op(B_WS, h.P[n]), h.ozB, h.ozEB, rmax, 1, op(B_WS, h.cqColE))
+                                     : slice(op(B_WS, h.P[n]), h.ozB, h.ozEB, rmax, 1);
+        const OzSliceJob spq = cholqr ? slice(op(B_WS, h.P[n]), h.ozB2, h.ozEB2, rmax, 1) : sp;
         const OzSliceJob sq = slice(op(B_Q, h.q_off[n] * 8), h.ozQ, h.ozEQ, (int64_t)h.n[n], (int64_t)h.n[n]);
-        auto gemm_job = [&](const OzSliceJob& a, Operand Yop, int64_t Ly) {
+        auto gemm_job = [&](const OzSliceJob& a, const OzSliceJob& sp, Operand Yop, int64_t Ly) {
           OzGemmJob g;
           std::memset(&g, 0, sizeof(g));
           g.M = (int)a.rows;
@@ -1783,8 +1804,8 @@ static void build_hosvd_f64(tks_plan* plan) {
           g.rmax = rmax;
           oz_gemms.push_back(g);
         };
-        gemm_job(sx, tj.Y, L);
-        gemm_job(sq, fj.Y, (int64_t)h.n[n]);
+        gemm_job(sx, sp, tj.Y, L);
+        gemm_job(sq, spq, fj.Y, (int64_t)h.n[n]);
       }
     }
     char nm[32];
@@ -1983,6 +2004,8 @@ static tks_status create_plan(tks_plan** out, const tks_problem* problems, int32
           B.rowB = alloc((size_t)kOzSlices * 64 * 64 * 2);
           B.rowBE = alloc(64 * 4);
           B.part = alloc((size_t)ceil_div(h.n[m], 64) * 64 * 4);
+          B.rowA2 = B.rowA;
+          B.colE2 = B.colE;
         }
       }
     }
@@ -2100,6 +2123,12 @@ static tks_status create_plan(tks_plan** out, const tks_problem* problems, int32
           h.cqRacc = alloc(64 * 64 * 8);
           h.cqFlag = alloc(4);
           h.cqPart = alloc((size_t)ceil_div(fib, 64) * 64 * 4);
+          // pass 1's row digits of H_(n)^T (in ozA) serve the mode product H x_n P_n^T afterwards, so
+          // the later passes slice into buffers of their own
+          h.cqRowA2 = alloc((size_t)kOzSlices * fib * ldk * 2);
+          h.cqColE2 = alloc(64 * 4);
+          h.ozB2 = alloc((size_t)kOzSlices * cols * ldk * 2);
+          h.ozEB2 = alloc((size_t)cols * 4);
         }
       }
     }

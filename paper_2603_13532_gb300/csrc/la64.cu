@@ -362,6 +362,9 @@ __device__ __forceinline__ double jacobi_tangent(double num, double den) {
 // visited once per sweep; when neither of its columns has rotated since its previous visit (in the
 // previous sweep or earlier in this one) it is still orthogonal and is skipped without loading it.
 // dsc, dinv and nsq hold m doubles each, flags 2 m ints.
+// kChunks: 2-row chunks per lane (8 lanes per pair), enough for b rows; a smaller count than the
+// largest basis keeps the float64 pipe off padding rows (b <= 64 needs 4 of 6).
+template <int kChunks>
 __device__ int jacobi_sweeps_f64(double* A, int ld, int b, int m, int max_sweeps, double noise2, int* sh_rot,
                                  double* dsc, double* dinv, double* nsq, int* flags) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -410,12 +413,12 @@ __device__ int jacobi_sweeps_f64(double* A, int ld, int b, int m, int max_sweeps
       if (!valid) p = q = 0;
       double* ap = A + p * ld;
       double* aq = A + q * ld;
-      double2 x[kJ64Chunks], y[kJ64Chunks];
+      double2 x[kChunks], y[kChunks];
       double g = 0.0;
       if (__any_sync(0xffffffffu, valid)) {
         double g0 = 0.0, g1 = 0.0;
 #pragma unroll
-        for (int u = 0; u < kJ64Chunks; ++u) {
+        for (int u = 0; u < kChunks; ++u) {
           const int i = 2 * (sub + kJ64Lanes * u);
           const bool in = valid && i < b;
           x[u] = in ? *reinterpret_cast<const double2*>(ap + i) : make_double2(0.0, 0.0);
@@ -477,7 +480,7 @@ __device__ int jacobi_sweeps_f64(double* A, int ld, int b, int m, int max_sweeps
       if (act) {
         const double mp = sh_mp[k], mq = sh_mq[k];
 #pragma unroll
-        for (int u = 0; u < kJ64Chunks; ++u) {
+        for (int u = 0; u < kChunks; ++u) {
           const int i = 2 * (sub + kJ64Lanes * u);
           if (i < b) {
             const double2 a0 = x[u], b0 = y[u];
@@ -531,6 +534,7 @@ __device__ double max_col_norm2(const double* A, int ld, int b, double* slot) {
 // rotated X, so no rotation needs to be accumulated in float64.  (On a triangular factor from QR, the
 // sweeps on R^T also converge in about half the sweeps that R itself needs.)  Kept columns whose norm
 // is at the float64 noise floor carry no direction; they are replaced by an orthonormal completion.
+template <int kChunks>
 __global__ void __launch_bounds__(kJ64Threads, 1) svd_jacobi_f64_kernel(const SvdJob* __restrict__ jobs, Bases bases,
                                                                    Status* status) {
   extern __shared__ double sm64[];
@@ -556,7 +560,7 @@ __global__ void __launch_bounds__(kJ64Threads, 1) svd_jacobi_f64_kernel(const Sv
   }
   __syncthreads();
   const double noise2 = max_col_norm2(A, ld, b, &sh_max) * (8.0 * eps) * (8.0 * eps);
-  const int sweep = jacobi_sweeps_f64(A, ld, b, m, kJ64Sweeps, noise2, &sh_rot, dsc, dinv, nsq, flags);
+  const int sweep = jacobi_sweeps_f64<kChunks>(A, ld, b, m, kJ64Sweeps, noise2, &sh_rot, dsc, dinv, nsq, flags);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   // squared singular values = squared column norms; order them by decreasing value
   for (int c = warp; c < b; c += nw) {
@@ -948,8 +952,11 @@ cudaError_t prepare_la64(int bmax) {
   cudaError_t e0 = cudaFuncSetAttribute(chol_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)kCholSmem);
   if (e0 != cudaSuccess) return e0;
-  cudaError_t e = cudaFuncSetAttribute(svd_jacobi_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(svd_jacobi_f64_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)svd64_smem(bmax));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(svd_jacobi_f64_kernel<kJ64Chunks>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)svd64_smem(bmax));
   if (e != cudaSuccess) return e;
   const void* ttm_kernels[] = {reinterpret_cast<const void*>(ttm_f64_kernel<1>),
                                reinterpret_cast<const void*>(ttm_f64_kernel<2>),
@@ -993,7 +1000,10 @@ void launch_svd_f64(const SvdJob* jobs, int njobs, int bmax, const Bases& bases,
                     cudaStream_t stream) {
   const int pairs = (bmax + 1) / 2;
   const int threads = ((pairs * kJ64Lanes + 31) / 32) * 32;
-  svd_jacobi_f64_kernel<<<njobs, threads, svd64_smem(bmax), stream>>>(jobs, bases, status);
+  if (bmax <= 64)
+    svd_jacobi_f64_kernel<4><<<njobs, threads, svd64_smem(bmax), stream>>>(jobs, bases, status);
+  else
+    svd_jacobi_f64_kernel<kJ64Chunks><<<njobs, threads, svd64_smem(bmax), stream>>>(jobs, bases, status);
 }
 
 int ttm64_tiles(int64_t fibres) { return (int)((fibres + kTtmF - 1) / kTtmF); }

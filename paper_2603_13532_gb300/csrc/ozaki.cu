@@ -42,6 +42,7 @@ __global__ void __launch_bounds__(kOzSliceThreads) oz_slice_kernel(const OzSlice
   __shared__ double xs[kOzRowsPerCta][kOzMaxK + 1];
   __shared__ int64_t roff[kOzRowsPerCta];
   __shared__ int rexp[kOzRowsPerCta];
+  __shared__ int kx[kOzMaxK];      // per-column exponent offsets: element (q, a) is sliced as x 2^kx[a]
   int lo = 0, hi = njobs - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
@@ -57,6 +58,8 @@ __global__ void __launch_bounds__(kOzSliceThreads) oz_slice_kernel(const OzSlice
     const int64_t q = q0 + threadIdx.x, r = q / L, l = q - r * L;
     roff[threadIdx.x] = l + L * (int64_t)K * r;
   }
+  for (int a = threadIdx.x; a < K; a += kOzSliceThreads)
+    kx[a] = J.kexp.base != B_NONE ? at<const int32_t>(bases, J.kexp)[a] : 0;
   __syncthreads();
   // stage the rows, coalesced along a when L = 1 (rows contiguous), along the fibre index otherwise
   for (int e = threadIdx.x; e < kOzRowsPerCta * K; e += kOzSliceThreads) {
@@ -66,13 +69,15 @@ __global__ void __launch_bounds__(kOzSliceThreads) oz_slice_kernel(const OzSlice
     xs[q][a] = q < nq ? src[roff[q] + L * a] : 0.0;
   }
   __syncthreads();
-  // row exponent e: |x| < 2^e for every entry (from the largest biased exponent field); 0 for a zero row
+  // row exponent e: |x 2^kx| < 2^e for every entry (from the largest biased exponent field plus the
+  // offset); 0 for a row without a normal entry
   {
+    constexpr int kNone = -(1 << 20);
     const int q = threadIdx.x >> 3, t8 = threadIdx.x & 7;
-    int emax = 0;
+    int emax = kNone;
     for (int a = t8; a < K; a += 8) {
       const int E = (int)((__double_as_longlong(xs[q][a]) >> 52) & 0x7ff);
-      emax = E > emax ? E : emax;
+      if (E) emax = E + kx[a] > emax ? E + kx[a] : emax;
     }
 #pragma unroll
     for (int o = 4; o > 0; o >>= 1) {
@@ -80,7 +85,7 @@ __global__ void __launch_bounds__(kOzSliceThreads) oz_slice_kernel(const OzSlice
       emax = other > emax ? other : emax;
     }
     if (t8 == 0) {
-      const int e = emax == 0 ? 0 : (emax < 1 ? 1 : emax) - 1022;
+      const int e = emax == kNone ? 0 : emax - 1022;
       rexp[q] = e;
       if (q < nq) at<int32_t>(bases, J.expo)[q0 + q] = e;
     }
@@ -94,8 +99,8 @@ __global__ void __launch_bounds__(kOzSliceThreads) oz_slice_kernel(const OzSlice
     const unsigned long long u = (unsigned long long)__double_as_longlong(xs[q][a]);
     const int E = (int)((u >> 52) & 0x7ff);
     const unsigned long long S = (u & 0xfffffffffffffull) | (E ? (1ull << 52) : 0ull);
-    // M = floor(|x| 2^(56 - e)) = S 2^(Eeff - 1019 - e) < 2^56
-    const int sh = (E ? E : 1) - 1019 - rexp[q];
+    // M = floor(|x| 2^(kx + 56 - e)) = S 2^(Eeff + kx - 1019 - e) < 2^56
+    const int sh = (E ? E : 1) - 1019 - (rexp[q] - kx[a]);
     unsigned long long M = 0;
     if (sh >= 0) M = S << sh;
     else if (sh > -64) M = S >> (-sh);
@@ -132,6 +137,7 @@ __device__ __forceinline__ uint16_t oz_digit(unsigned long long M, int s, bool n
 constexpr int kOzXRows = 64;
 constexpr int kOzXThreads = 256;
 constexpr int kOzXMaxB = 64;           // CholeskyQR3 runs for b <= 64
+constexpr int kOzXPitch = 66;          // doubles per staged row; the same bytes hold 4 digit planes later
 
 __device__ __forceinline__ const OzXSliceJob& oz_xjob(const OzXSliceJob* __restrict__ jobs, int njobs) {
   int lo = 0, hi = njobs - 1;
@@ -143,7 +149,7 @@ __device__ __forceinline__ const OzXSliceJob& oz_xjob(const OzXSliceJob* __restr
 }
 
 __device__ __forceinline__ int oz_stage_xtile(const OzXSliceJob& J, const double* __restrict__ src, int64_t i0,
-                                              double (*xs)[kOzXMaxB + 1], int64_t* roff) {
+                                              double (*xs)[kOzXPitch], int64_t* roff) {
   const int b = J.b;
   const int nq = (int)(J.P - i0 < kOzXRows ? J.P - i0 : kOzXRows);
   if (J.L == 1) {
@@ -168,7 +174,7 @@ __device__ __forceinline__ int oz_stage_xtile(const OzXSliceJob& J, const double
 
 __global__ void __launch_bounds__(kOzXThreads) oz_xmax_kernel(const OzXSliceJob* __restrict__ jobs, int njobs,
                                                              Bases bases) {
-  __shared__ double xs[kOzXRows][kOzXMaxB + 1];
+  __shared__ __align__(16) double xs[kOzXRows][kOzXPitch];
   __shared__ int64_t roff[kOzXRows];
   __shared__ int red[kOzXThreads / 64][64];
   const OzXSliceJob& J = oz_xjob(jobs, njobs);
@@ -193,7 +199,7 @@ __global__ void __launch_bounds__(kOzXThreads) oz_xmax_kernel(const OzXSliceJob*
 
 __global__ void __launch_bounds__(kOzXThreads) oz_xdig_kernel(const OzXSliceJob* __restrict__ jobs, int njobs,
                                                              Bases bases) {
-  __shared__ double xs[kOzXRows][kOzXMaxB + 1];
+  __shared__ __align__(16) double xs[kOzXRows][kOzXPitch];
   __shared__ int64_t roff[kOzXRows];
   __shared__ int red[kOzXThreads / 64][64];
   __shared__ int es[64];
@@ -226,42 +232,62 @@ __global__ void __launch_bounds__(kOzXThreads) oz_xdig_kernel(const OzXSliceJob*
   uint16_t* colP = at<uint16_t>(bases, J.colP);
   uint16_t* rowP = at<uint16_t>(bases, J.rowP);
   const int64_t cstride = 64 * J.ldP, rstride = J.rows_pad * 64;
-  // each element's magnitude once (M < 2^56, the sign in bit 63), kept as bits in place of the value
-  for (int e = threadIdx.x; e < kOzXRows * 64; e += kOzXThreads) {
-    const int q = e >> 6, a = e & 63;
+  // each element's magnitude once, in registers (M < 2^56, the sign in bit 63; 0 outside the tile)
+  constexpr int kPer = kOzXRows * 64 / kOzXThreads;
+  unsigned long long mg[kPer];
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    const int e = threadIdx.x + kOzXThreads * k, q = e >> 6, a = e & 63;
+    mg[k] = 0ull;
     if (q < nq && a < b) {
       bool neg;
       const unsigned long long M = oz_magnitude(xs[q][a], es[a], neg);
-      xs[q][a] = __longlong_as_double((long long)(M | (neg ? (1ull << 63) : 0ull)));
+      mg[k] = M | (neg ? (1ull << 63) : 0ull);
     }
   }
   __syncthreads();
-  auto digit = [&](int q, int a, int sl) -> uint32_t {
-    if (q >= nq || a >= b) return 0u;
-    const unsigned long long v = (unsigned long long)__double_as_longlong(xs[q][a]);
-    return oz_digit(v & ~(1ull << 63), sl, (v >> 63) != 0);
-  };
-  // column planes: thread (row pair, column); a warp stores 32 x 4 contiguous bytes per plane row
-  {
-    const int q0 = 2 * (threadIdx.x & 31);
-    if (q0 < nq)
-      for (int a = threadIdx.x >> 5; a < b; a += kOzXThreads / 32) {
-        uint32_t* out = reinterpret_cast<uint32_t*>(colP + (int64_t)a * J.ldP + i0 + q0);
+  // the staged tile's bytes now hold four digit planes at a time: dg[s][q][a], rows of kOzXPitch
+  // bf16 (a 4-byte aligned row pitch, rows on distinct banks for a column read); each digit is
+  // formed once and written to both layouts with 16-byte stores
+  constexpr int kDPitch = kOzXPitch;   // bf16 per digit row: 4 planes x 64 rows fill the staged tile's bytes
+  uint16_t* dg = reinterpret_cast<uint16_t*>(&xs[0][0]);
+  constexpr int kDPlane = kOzXRows * kDPitch;
+  static_assert(4 * kDPlane * sizeof(uint16_t) <= sizeof(xs), "four digit planes must fit the staged tile");
 #pragma unroll
-        for (int sl = 0; sl < kOzSlices; ++sl)
-          out[sl * (cstride / 2)] = digit(q0, a, sl) | (digit(q0 + 1, a, sl) << 16);
-      }
-  }
-  // row planes: thread (column pair, row); a warp stores one 128-byte plane row
-  {
-    const int a0 = 2 * (threadIdx.x & 31);
-    if (a0 < b)
-      for (int q = threadIdx.x >> 5; q < nq; q += kOzXThreads / 32) {
-        uint32_t* out = reinterpret_cast<uint32_t*>(rowP + (i0 + q) * 64 + a0);
+  for (int half = 0; half < 2; ++half) {
 #pragma unroll
-        for (int sl = 0; sl < kOzSlices; ++sl)
-          out[sl * (rstride / 2)] = digit(q, a0, sl) | (digit(q, a0 + 1, sl) << 16);
+    for (int k = 0; k < kPer; ++k) {
+      const int e = threadIdx.x + kOzXThreads * k, q = e >> 6, a = e & 63;
+      const unsigned long long v = mg[k];
+#pragma unroll
+      for (int s4 = 0; s4 < 4; ++s4)
+        dg[s4 * kDPlane + q * kDPitch + a] = oz_digit(v & ~(1ull << 63), 4 * half + s4, (v >> 63) != 0);
+    }
+    __syncthreads();
+    // row planes: (slice, row q, 8 columns) -> one 16-byte store of plane row i0 + q
+    for (int it = threadIdx.x; J.want_rows && it < 4 * kOzXRows * 8; it += kOzXThreads) {
+      const int s4 = it >> 9, q = (it >> 3) & 63, c = it & 7;
+      if (q < nq && 8 * c < b) {
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(dg + s4 * kDPlane + q * kDPitch + 8 * c);
+        uint4 w;
+        w.x = src[0]; w.y = src[1]; w.z = src[2]; w.w = src[3];
+        *reinterpret_cast<uint4*>(rowP + (4 * half + s4) * rstride + (i0 + q) * 64 + 8 * c) = w;
       }
+    }
+    // column planes: (slice, column a, 8 rows) -> one 16-byte store of plane row a
+    for (int it = threadIdx.x; it < 4 * 64 * 8; it += kOzXThreads) {
+      const int s4 = it >> 9, a = (it >> 3) & 63, c = it & 7;
+      if (a < b && 8 * c < nq) {
+        const uint16_t* src = dg + s4 * kDPlane + 8 * c * kDPitch + a;
+        uint4 w;
+        w.x = (uint32_t)src[0] | ((uint32_t)src[kDPitch] << 16);
+        w.y = (uint32_t)src[2 * kDPitch] | ((uint32_t)src[3 * kDPitch] << 16);
+        w.z = (uint32_t)src[4 * kDPitch] | ((uint32_t)src[5 * kDPitch] << 16);
+        w.w = (uint32_t)src[6 * kDPitch] | ((uint32_t)src[7 * kDPitch] << 16);
+        *reinterpret_cast<uint4*>(colP + (4 * half + s4) * cstride + (int64_t)a * J.ldP + i0 + 8 * c) = w;
+      }
+    }
+    __syncthreads();
   }
 }
 

@@ -349,6 +349,7 @@ constexpr int kOzLevels = 8;     // digit pairs with s + t <= 9 (1-based): level
 // (s * rows_pad + q) * ld + a, and the row's exponent e to expo[q].
 struct OzSliceJob {
   Operand src, planes, expo;
+  Operand kexp;          // int32 per K index a (B_NONE: none): row q is sliced as x[q][a] 2^kexp[a]
   int64_t rows, L, rows_pad;
   int32_t K, ld;
   int32_t tile_begin, tiles;
@@ -378,7 +379,8 @@ struct OzGemmJob {
 struct OzXSliceJob {
   Operand src, part, expo, colP, rowP;
   int64_t P, L, ldP, rows_pad;
-  int32_t b, tiles, tile_begin, pad;
+  int32_t b, tiles, tile_begin;
+  int32_t want_rows;     // 0: no X Rinv follows this pass (its Gram is all it needs): skip the row planes
 };
 
 // G = X^T X (b x b, b <= 64) from the column digit planes (TMA maps map[s], box 64 k x 64 rows),
