@@ -189,6 +189,15 @@ def st_hosvd(H, target=None, tol=0.0):
     return H, Ps, ranks, svs
 
 
+def truncation_error_estimate(H, svs, ranks):
+    """||H - H~||_F / ||H||_F of the ST-HOSVD truncation (Alg. 2, phase 2) from the singular values of
+    each processed unfolding: the parts discarded at the successive modes are orthogonal, so the
+    squared error is the sum over modes of the discarded squared singular values."""
+    tail = sum(float(np.sum(np.asarray(sv, dtype=np.float64)[r:] ** 2)) for sv, r in zip(svs, ranks))
+    nh = float(np.sum(np.asarray(H, dtype=np.float64) ** 2))
+    return float(np.sqrt(tail / nh)) if nh > 0 else 0.0
+
+
 # ---------------------------------------------------------------- full method
 def scaled_terms(terms, alpha=None):
     """Fold term weights into the cores, as TuckerAxby (Alg. 1) scales them."""

@@ -136,6 +136,27 @@ def test_st_hosvd_rank_rule_closed_form():
     assert ranks == [4, 2, 5]
 
 
+def test_truncation_error_estimate_is_the_truncation_error():
+    """The discarded parts of the successive ST-HOSVD modes are orthogonal: the estimate from the
+    singular values equals ||H - core x_n P_n||_F / ||H||_F computed directly; the superdiagonal
+    closed form gives sqrt(sum over modes of the discarded squared diagonal) / ||H||."""
+    g = np.random.default_rng(12)
+    H = g.standard_normal((9, 7, 8)) * np.logspace(0, -3, 9)[:, None, None]
+    for target in ([4, 3, 5], [9, 7, 8], [1, 1, 1]):
+        core, Ps, ranks, svs = ss.st_hosvd(H, target=target)
+        direct = np.linalg.norm(H - tucker_full(core, Ps)) / np.linalg.norm(H)
+        assert abs(ss.truncation_error_estimate(H, svs, ranks) - direct) <= 1e-12 * max(direct, 1.0)
+    vals = 10.0 ** -np.arange(6)
+    D = np.zeros((6, 6, 6))
+    for i, v in enumerate(vals):
+        D[i, i, i] = v
+    core, Ps, ranks, svs = ss.st_hosvd(D, target=[2, 4, 3])
+    # mode 1 drops entries 2..5; after that the core is 2 x 6 x 6 with entries 1, 0.1, so modes 2, 3
+    # drop nothing more
+    expect = np.sqrt(np.sum(vals[2:] ** 2)) / np.linalg.norm(vals)
+    assert abs(ss.truncation_error_estimate(D, svs, ranks) - expect) <= 1e-14
+
+
 # ------------------------------------------------------------------ T3
 def _recon(res):
     return tucker_full(res["core"], res["factors"])
