@@ -231,6 +231,14 @@ TKS_API tks_status tucker_sum_recompress(tks_plan* plan, void* workspace, double
 TKS_API tks_status tks_truncate_core(tks_plan* plan, void* workspace, const double* Q_in, const double* H_in,
                                      double* out, int32_t* ranks_out, void* stream);
 
+/* Relative truncation error of the ST-HOSVD of the last tucker_sum_recompress (or tks_truncate_core)
+ * run with this workspace (Alg. 2, phase 2): per problem, err_out[p] = ||H - H~||_F / ||H||_F with
+ * H the projected core and H~ its truncation, from the singular values each mode discarded (the
+ * discarded parts of successive modes are orthogonal, so their squared norms add up).  It does not
+ * include the sketching error of the bases Q_n.  err_out: device, float64, num_problems entries.
+ * Enqueued on `stream` after the recompression; TKS_EINVAL for a null argument. */
+TKS_API tks_status tks_truncation_error(tks_plan* plan, void* workspace, double* err_out, void* stream);
+
 /* Backward of the core projection (Sec. 3.3) with the bases held fixed (stop-gradient through Q):
  * with A_kn = Q_n^T U_k^(n) and Hbar = dL/dH given (device, float64, the H layout of
  * tks_project_core), writes

@@ -114,6 +114,7 @@ def load(path=None):
     lib.tks_project_core_backward.restype = ctypes.c_int
     lib.tks_sync_status.argtypes = [P, P]
     lib.tks_plan_tuning.argtypes = [P, ctypes.c_char_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
+    lib.tks_truncation_error.argtypes = [P, P, P, P]
     lib.tks_last_error.restype = ctypes.c_char_p
     lib.tks_status_string.restype = ctypes.c_char_p
     lib.tks_status_string.argtypes = [ctypes.c_int]
@@ -135,7 +136,7 @@ def load(path=None):
     for name in ["tks_plan_create", "tks_plan_info", "tks_problem_info", "tks_generate_omega",
                  "tucker_sum_sketch", "tks_project_core", "tucker_sum_recompress", "tks_sync_status",
                  "tks_profile_begin", "tks_profile_end", "tks_subrank_plan_create", "tks_truncate_core",
-                 "tks_plan_set_fault_test", "tks_subrank_info", "tks_plan_tuning", "tks_subrank_executed_flops",
+                 "tks_plan_set_fault_test", "tks_subrank_info", "tks_plan_tuning", "tks_subrank_executed_flops", "tks_truncation_error",
                  "tks_subrank_problem_info", "tks_effective_subrank", "tks_subrank_sync_status"]:
         getattr(lib, name).restype = ctypes.c_int
     _LIB = lib
@@ -250,6 +251,13 @@ class Plan:
         if h is not None and h.value:
             self.lib.tks_plan_destroy(h)
             self.handle = None
+
+    def truncation_error(self):
+        """||H - H~|| / ||H|| of every problem's last ST-HOSVD (tks_truncation_error), as a numpy array."""
+        out = torch.zeros(max(1, len(self.problems)), dtype=torch.float64, device=self.device)
+        _check(self.lib.tks_truncation_error(self.handle, _ptr(self.workspace), _ptr(out), _stream_handle()))
+        self.sync()
+        return out[: len(self.problems)].cpu().numpy()
 
     def tuning(self):
         """The schedule the plan runs and, when autotuned, the candidates timed (tks_plan_tuning)."""

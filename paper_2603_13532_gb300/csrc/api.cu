@@ -50,7 +50,7 @@ Operand op_abs(const void* p, size_t off_bytes = 0) {
 enum StepKind { S_OMEGA, S_GEMM, S_REDUCE, S_CORESKETCH, S_QR, S_TSQR64, S_TC, S_SIMT, S_CS32, S_SPLIT,
                 S_TRANSPOSE, S_QR32, S_SVD32, S_TSQR, S_CS3, S_CHAIN3, S_QRSM, S_PROJ3, S_SK3, S_QRREG, S_TTM,
                 S_FOLD4, S_PROJ3F, S_SK3F, S_SK4, S_SVD64, S_TTM64, S_OZSLICE, S_OZGEMM, S_OZXMAX, S_OZGRAM, S_CHOL,
-                S_OZXDIG };
+                S_OZXDIG, S_TRUNCERR };
 
 struct Step {
   StepKind kind;
@@ -106,6 +106,7 @@ struct ProbHost {
   size_t ozA = 0, ozQ = 0, ozB = 0, ozEA = 0, ozEQ = 0, ozEB = 0;   // TKS_MIXED mode products: digit planes
   size_t cqX[2] = {}, cqCol = 0, cqColE = 0, cqG = 0, cqRinv = 0, cqRacc = 0, cqFlag = 0, cqPart = 0;   // CholeskyQR3
   size_t cqRowA2 = 0, cqColE2 = 0, ozB2 = 0, ozEB2 = 0;   // later passes; unscaled P digits for Q_n P_n
+  size_t errw = 0;   // ||H||^2 and the discarded energy of every mode (the truncation error estimate)
   CqBuffers qcq[MAXD] = {};   // TKS_MIXED: CholeskyQR3 of the sketches Y_n (flag == 0: Householder QR)
   std::vector<size_t> chain;   // 2 ping-pong buffers per term
   // mixed-precision buffers (bytes): bf16 planes and float32 intermediates
@@ -180,7 +181,7 @@ struct tks_plan {
   size_t ws_bytes = 0;
   size_t ws_omega = 0, ws_Y = 0, ws_Q = 0, ws_H = 0;
   int64_t omega_elems = 0, sketch_elems = 0, basis_elems = 0, core_elems = 0, output_elems = 0;
-  std::vector<Step> st_omega, st_sketch, st_project, st_recompress, st_backward;
+  std::vector<Step> st_omega, st_sketch, st_project, st_recompress, st_backward, st_truncerr;
   // problems [lane_p0, lane_p1) go into the launch tables being built; with lanes > 1 the
   // recompression has one step list per contiguous group of problems, run on its own stream
   int lane_p0 = 0, lane_p1 = 0;
@@ -1227,6 +1228,8 @@ static void build_hosvd_f32(tks_plan* plan) {
       sj.b = b;
       sj.rmax = rmax;
       sj.first_mode = (n == 0);
+      sj.mode = n;
+      sj.err = op(B_WS, h.errw);
       sj.order = d;
       sj.tol = plan->params.trunc_tol;
       svds.push_back(sj);
@@ -1710,6 +1713,8 @@ static void build_hosvd_f64(tks_plan* plan) {
       sj.b = b;
       sj.rmax = rmax;
       sj.first_mode = (n == 0);
+      sj.mode = n;
+      sj.err = op(B_WS, h.errw);
       sj.order = d;
       sj.tol = plan->params.trunc_tol;
       svds.push_back(sj);
@@ -1965,6 +1970,7 @@ static tks_status create_plan(tks_plan** out, const tks_problem* problems, int32
   plan->ws_Y = alloc(plan->sketch_elems * 8);
   plan->ws_Q = alloc(plan->basis_elems * 8);
   plan->ws_H = alloc(plan->core_elems * 8);
+  for (auto& h : plan->probs) h.errw = alloc((1 + TKS_MAX_ORDER) * sizeof(double));
   for (auto& h : plan->probs) {
     const int d = h.d;
     auto r8 = [](int x) { return (x + 7) / 8 * 8; };
@@ -2297,6 +2303,18 @@ static tks_status create_plan(tks_plan** out, const tks_problem* problems, int32
   }
   }
   plan->trunc_from = plan->st_recompress.size();
+  {
+    std::vector<TruncErrJob> te;
+    for (size_t p = 0; p < plan->probs.size(); ++p) {
+      TruncErrJob j;
+      std::memset(&j, 0, sizeof(j));
+      j.err = op(B_WS, plan->probs[p].errw);
+      j.out = op(B_OUT, p * sizeof(double));
+      j.d = plan->probs[p].d;
+      te.push_back(j);
+    }
+    plan->push(plan->st_truncerr, S_TRUNCERR, te, (int64_t)te.size(), "truncation_error");
+  }
   if (f32la) build_hosvd_f32(plan);
   else build_hosvd_f64(plan);
 
@@ -2520,6 +2538,9 @@ tks_status run_steps(tks_plan* plan, const std::vector<Step>& steps, const Bases
         break;
       case S_CHOL:
         launch_chol_step(static_cast<const CholJob*>(table), s.njobs, bases, plan->status, stream);
+        break;
+      case S_TRUNCERR:
+        launch_trunc_err(static_cast<const TruncErrJob*>(table), s.njobs, bases, stream);
         break;
       case S_TTM64:
         launch_ttm_f64(static_cast<const TtmJob*>(table), s.njobs, (int)s.work, s.nb_max, plan->bmax, bases, stream);
@@ -2953,6 +2974,15 @@ tks_status tks_plan_tuning(const tks_plan* plan, char* buf, int64_t cap, int64_t
 }
 
 }  // extern "C"
+
+tks_status tks_truncation_error(tks_plan* plan, void* workspace, double* err_out, void* stream) {
+  tks_status st = check_ws(plan, workspace);
+  if (st != TKS_OK) return st;
+  if (!err_out) return fail(TKS_EINVAL, "null err_out");
+  Bases b = bind(plan, workspace);
+  b.p[B_OUT] = reinterpret_cast<char*>(err_out);
+  return run_steps(plan, plan->st_truncerr, b, static_cast<cudaStream_t>(stream));
+}
 
 tks_status tks_project_core_backward(tks_plan* plan, void* workspace, const double* Q_in, const double* Hbar_in,
                                      double* dcores, double* dfactors, void* stream) {

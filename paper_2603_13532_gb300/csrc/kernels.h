@@ -123,6 +123,8 @@ void launch_oz_xdig(const OzXSliceJob* jobs, int njobs, int total_tiles, const B
 void launch_oz_gram(const OzGramJob* jobs, int njobs, const void* maps, const Bases& bases, Status* status,
                     long long wait_cycles, cudaStream_t stream);
 void launch_chol_step(const CholJob* jobs, int njobs, const Bases& bases, Status* status, cudaStream_t stream);
+// sqrt(sum of the discarded energies / ||H||^2) per problem (one thread each)
+void launch_trunc_err(const TruncErrJob* jobs, int njobs, const Bases& bases, cudaStream_t stream);
 
 // Effective subrank heuristic (Alg. 5): term weights, weighted Gram tiles, tridiagonalization
 // (one CTA per matrix) and eigenvalues + rank rule (one CTA per matrix).

@@ -748,6 +748,15 @@ __global__ void __launch_bounds__(kSvdThreads) svd_jacobi_f32_kernel(const SvdJo
       if (r > J.rmax) r = J.rmax;
     }
     sh_rank = r;
+    if (J.err.base != B_NONE) {
+      // the energy this mode's truncation discards; with the first mode's total, the ST-HOSVD's
+      // relative error (the discarded parts of successive modes are orthogonal)
+      double* er = at<double>(bases, J.err);
+      double dis = 0.0;
+      for (int i = r; i < b; ++i) dis += (double)nrm[order[i]];
+      if (J.first_mode) er[0] = (double)tot;
+      er[1 + J.mode] = dis;
+    }
     *at<int32_t>(bases, J.rank) = r;
     if (!isfinite(tot)) record_status_la(status, TKS_ENONFINITE);
     if (sweep >= kSvdSweeps) record_status_la(status, TKS_ENOCONV);

@@ -606,6 +606,15 @@ __global__ void __launch_bounds__(kJ64Threads, 1) svd_jacobi_f64_kernel(const Sv
       if (r > J.rmax) r = J.rmax;
     }
     sh_rank = r;
+    if (J.err.base != B_NONE) {
+      // the energy this mode's truncation discards; with the first mode's total, the ST-HOSVD's
+      // relative error (the discarded parts of successive modes are orthogonal)
+      double* er = at<double>(bases, J.err);
+      double dis = 0.0;
+      for (int i = r; i < b; ++i) dis += (double)nrm[order[i]];
+      if (J.first_mode) er[0] = (double)tot;
+      er[1 + J.mode] = dis;
+    }
     // kept columns from the first one at the noise floor on carry no direction
     int fill = r;
     for (int t = 0; t < r; ++t)
@@ -944,6 +953,22 @@ __global__ void __launch_bounds__(kCholThreads, 1) chol_step_kernel(const CholJo
 }
 
 }  // namespace
+
+namespace {
+__global__ void trunc_err_kernel(const TruncErrJob* __restrict__ jobs, int njobs, Bases bases) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= njobs) return;
+  const TruncErrJob& J = jobs[j];
+  const double* er = at<const double>(bases, J.err);
+  double dis = 0.0;
+  for (int n = 0; n < J.d; ++n) dis += er[1 + n];
+  *at<double>(bases, J.out) = er[0] > 0.0 ? sqrt(dis / er[0]) : 0.0;
+}
+}  // namespace
+
+void launch_trunc_err(const TruncErrJob* jobs, int njobs, const Bases& bases, cudaStream_t stream) {
+  trunc_err_kernel<<<(njobs + 127) / 128, 128, 0, stream>>>(jobs, njobs, bases);
+}
 
 // At least twice the columns, so that every TSQR level shrinks the stack of factors.
 int tsqr64_block_rows(int max_cols) { return max_cols <= 64 ? 256 : 192; }

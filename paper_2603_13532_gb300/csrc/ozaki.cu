@@ -153,9 +153,12 @@ __device__ __forceinline__ int oz_stage_xtile(const OzXSliceJob& J, const double
   const int b = J.b;
   const int nq = (int)(J.P - i0 < kOzXRows ? J.P - i0 : kOzXRows);
   if (J.L == 1) {
+    // the tile is nq * b contiguous values; the row index from a float32 reciprocal, exact for
+    // e < 4096 and b <= 64 (the product stays 2^-22 away from the next integer)
     const double* base = src + i0 * b;
+    const float rb = 1.0f / (float)b;
     for (int e = threadIdx.x; e < nq * b; e += kOzXThreads) {
-      const int q = e / b;
+      const int q = (int)(((float)e + 0.5f) * rb);
       xs[q][e - q * b] = base[e];
     }
   } else {
@@ -259,9 +262,16 @@ __global__ void __launch_bounds__(kOzXThreads) oz_xdig_kernel(const OzXSliceJob*
     for (int k = 0; k < kPer; ++k) {
       const int e = threadIdx.x + kOzXThreads * k, q = e >> 6, a = e & 63;
       const unsigned long long v = mg[k];
+      // digits 0-3 are bits 28..55 of M and digits 4-7 bits 0..27: one 32-bit word per half; a zero
+      // digit of a negative value becomes -0, which adds nothing to an exact sum
+      const uint32_t w = half == 0 ? (uint32_t)(v >> 28) & 0x0fffffffu : (uint32_t)v & 0x0fffffffu;
+      const uint32_t sg = (uint32_t)(v >> 63) << 15;
 #pragma unroll
-      for (int s4 = 0; s4 < 4; ++s4)
-        dg[s4 * kDPlane + q * kDPitch + a] = oz_digit(v & ~(1ull << 63), 4 * half + s4, (v >> 63) != 0);
+      for (int s4 = 0; s4 < 4; ++s4) {
+        const uint32_t d = (w >> (21 - 7 * s4)) & 127u;
+        const float f = __int_as_float(0x4B000000 | (int)d) - 8388608.0f;
+        dg[s4 * kDPlane + q * kDPitch + a] = (uint16_t)((__float_as_uint(f) >> 16) | sg);
+      }
     }
     __syncthreads();
     // row planes: (slice, row q, 8 columns) -> one 16-byte store of plane row i0 + q
@@ -471,17 +481,23 @@ __global__ void __launch_bounds__(kOzGemmThreads, 1) oz_gemm_kernel(const OzGemm
           }
           tc::fence_after_sync();
           // level acc = s + t collects the digit pairs (s, t); its first product starts it at zero
+          // plane descriptors once per k-block; a 16-deep k step advances the start address by 32
+          // bytes, i.e. the descriptor's address field by 2
+          uint64_t dA[kOzSlices], dB[kOzSlices];
+#pragma unroll
+          for (int p = 0; p < kOzSlices; ++p) {
+            dA[p] = tc::sw128_kmajor_desc(tc::smem_u32(At + p * kOzATile));
+            dB[p] = tc::sw128_kmajor_desc(tc::smem_u32(Bt + p * kOzBTile));
+          }
+#pragma unroll
           for (int acc = 0; acc < kOzLevels; ++acc) {
             const uint32_t d = tmem + (uint32_t)(acc * kOzBN);
+#pragma unroll
             for (int s = 0; s <= acc; ++s) {
-              const int tt = acc - s;
-              const uint32_t a0 = tc::smem_u32(At + s * kOzATile);
-              const uint32_t b0 = tc::smem_u32(Bt + tt * kOzBTile);
 #pragma unroll
               for (int k = 0; k < kOzBK / 16; ++k) {
                 const uint32_t accumulate = (kb > 0 || s > 0 || k > 0) ? 1u : 0u;
-                tc::mma_bf16(d, tc::sw128_kmajor_desc(a0 + 32 * k), tc::sw128_kmajor_desc(b0 + 32 * k), idesc,
-                             accumulate);
+                tc::mma_bf16(d, dA[s] + 2 * k, dB[acc - s] + 2 * k, idesc, accumulate);
               }
             }
           }
@@ -677,16 +693,19 @@ __global__ void __launch_bounds__(kOzGramThreads, 1) oz_gram_kernel(const OzGram
           break;
         }
         tc::fence_after_sync();
+        // plane descriptors once per k-block (a 16-deep k step adds 2 to the address field)
+        uint64_t dP[kOzSlices];
+#pragma unroll
+        for (int p = 0; p < kOzSlices; ++p) dP[p] = tc::sw128_kmajor_desc(tc::smem_u32(stage[st] + p * kOzPlaneTile));
+#pragma unroll
         for (int acc = 0; acc < kOzLevels; ++acc) {
           const uint32_t d = tmem + (uint32_t)(acc * kOzBN);
+#pragma unroll
           for (int sa = 0; sa <= acc; ++sa) {
-            const uint32_t a0 = tc::smem_u32(stage[st] + sa * kOzPlaneTile);
-            const uint32_t b0 = tc::smem_u32(stage[st] + (acc - sa) * kOzPlaneTile);
 #pragma unroll
             for (int k = 0; k < kOzBK / 16; ++k) {
               const uint32_t accumulate = (!first || sa > 0 || k > 0) ? 1u : 0u;
-              tc::mma_bf16(d, tc::sw128_kmajor_desc(a0 + 32 * k), tc::sw128_kmajor_desc(b0 + 32 * k), idesc,
-                           accumulate);
+              tc::mma_bf16(d, dP[sa] + 2 * k, dP[acc - sa] + 2 * k, idesc, accumulate);
             }
           }
         }

@@ -330,8 +330,17 @@ struct TsqrJob {
 // float32 for the float32 kernel and float64 for the float64 kernel (theta is float64 in both).
 struct SvdJob {
   Operand R, P, sv, theta, rank;
-  int32_t b, rmax, first_mode, order;
+  Operand err;           // float64 [1 + TKS_MAX_ORDER]: ||H||^2 (first mode) and each mode's discarded
+                         // squared singular values, at index 1 + mode (B_NONE: not recorded)
+  int32_t b, rmax, first_mode, order, mode, pad;
   double tol;
+};
+
+// Relative truncation error of one problem's ST-HOSVD from the energies its SVD jobs recorded.
+struct TruncErrJob {
+  Operand err;           // float64 [1 + TKS_MAX_ORDER] as in SvdJob
+  Operand out;           // float64: sqrt(sum of the discarded energies / ||H||^2)
+  int32_t d, pad;
 };
 
 // Float64-accurate mode product on the tensor cores (the ST-HOSVD truncation of TKS_MIXED):

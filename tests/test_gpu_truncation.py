@@ -78,3 +78,28 @@ def test_truncation_decay512_float64_bound(cuda_lib, precision):
     Ho = tucker_full(ref["core"], ref["P"])
     err = np.linalg.norm(Hg - Ho) / np.linalg.norm(ref["H"])
     assert err <= 1e-12, err
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_f32la"])
+@pytest.mark.parametrize("d", [3, 4])
+def test_truncation_error_estimate(cuda_lib, precision, d):
+    """tks_truncation_error after tks_truncate_core on the oracle's H: the relative error of the
+    ST-HOSVD from the discarded singular values, against the oracle's (1e-12 absolute in float64,
+    1e-5 with float32 linear algebra), and against ||H - H~|| / ||H|| of the returned truncation."""
+    from paper_2603_13532_gb300 import binding
+    bf16 = precision != "fp64"
+    probs = _problems(d, 60 + d, bf16)
+    plan = binding.Plan(probs, kind="krp", precision=precision, seed=9)
+    refs = [ss.recompress(p.terms(), "krp", p.target, p.oversampling, seed=9, problem=i, alpha=p.alpha,
+                          rounding="bf16" if bf16 else None) for i, p in enumerate(probs)]
+    outs = plan.truncate([r["Q"] for r in refs], [r["H"] for r in refs])
+    est = plan.truncation_error()
+    tol = 1e-5 if precision == "mixed_f32la" else 1e-12
+    for i, (got, ref) in enumerate(zip(outs, refs)):
+        e_ref = ss.truncation_error_estimate(ref["H"], ref["svs"], ref["ranks"])
+        assert abs(est[i] - e_ref) <= tol, (i, est[i], e_ref)
+        # the same quantity measured: H~ = H x_n (P_n P_n^T) with P_n = Q_n^T U~_n
+        Ps = [Q.T @ U for Q, U in zip(ref["Q"], got["factors"])]
+        Ht = tucker_full(got["core"], Ps)
+        direct = np.linalg.norm(ref["H"] - Ht) / np.linalg.norm(ref["H"])
+        assert abs(est[i] - direct) <= 10 * tol, (i, est[i], direct)
