@@ -79,10 +79,10 @@ Step make_step(StepKind kind, size_t off, int njobs, int64_t work, const char* n
 // Workspace of shifted CholeskyQR3 of one tall matrix (byte offsets): the two re-formed X, the column
 // digit planes and exponents, the Gram matrix, R^-1, the accumulated R, the fallback flag, and the row
 // digit planes and exponents of X and of R^-1.
-// rowA, colE: X's row digit planes and column exponents in pass 1; rowA2, colE2: those of the later
+// col, colE: X's column digit planes and column exponents in pass 1; col2, colE2: those of the later
 // passes (the same buffers when pass 1's digits need not outlive the factorization)
 struct CqBuffers {
-  size_t X[2], col, colE, G, Rinv, Racc, flag, rowA, rowAE, rowB, rowBE, part, rowA2, colE2;
+  size_t X[2], col, colE, G, Rinv, Racc, flag, rowA, rowAE, rowB, rowBE, part, col2, colE2;
 };
 
 struct ProbHost {
@@ -105,7 +105,7 @@ struct ProbHost {
   size_t R64 = 0, stk64[2] = {};   // float64 ST-HOSVD: triangular factor and TSQR stacks
   size_t ozA = 0, ozQ = 0, ozB = 0, ozEA = 0, ozEQ = 0, ozEB = 0;   // TKS_MIXED mode products: digit planes
   size_t cqX[2] = {}, cqCol = 0, cqColE = 0, cqG = 0, cqRinv = 0, cqRacc = 0, cqFlag = 0, cqPart = 0;   // CholeskyQR3
-  size_t cqRowA2 = 0, cqColE2 = 0, ozB2 = 0, ozEB2 = 0;   // later passes; unscaled P digits for Q_n P_n
+  size_t cqCol2 = 0, cqColE2 = 0, ozB2 = 0, ozEB2 = 0;   // later passes; unscaled P digits for Q_n P_n
   size_t errw = 0;   // ||H||^2 and the discarded energy of every mode (the truncation error estimate)
   CqBuffers qcq[MAXD] = {};   // TKS_MIXED: CholeskyQR3 of the sketches Y_n (flag == 0: Householder QR)
   std::vector<size_t> chain;   // 2 ping-pong buffers per term
@@ -469,22 +469,22 @@ struct CqLists {
       xj.src = X[pass];
       xj.part = op(B_WS, B.part);
       xj.expo = op(B_WS, pass == 0 ? B.colE : B.colE2);
-      xj.colP = op(B_WS, B.col);
-      xj.rowP = op(B_WS, pass == 0 ? B.rowA : B.rowA2);
+      xj.colP = op(B_WS, pass == 0 ? B.col : B.col2);
+      xj.rowP = op(B_WS, B.rowA);
       xj.P = P;
       xj.L = L;
       xj.ldP = ldP;
       xj.rows_pad = (P + 7) / 8 * 8;
       xj.b = b;
       xj.tiles = oz_xslice_tiles(P);
-      xj.want_rows = (pass < passes - 1 || Qout.base != B_NONE) ? 1 : 0;
+      xj.want_rows = 0;   // X R^-1 reads the column planes MN-major
       xj.tile_begin = xsl_total[pass];
       xsl_total[pass] += xj.tiles;
       xsl[pass].push_back(xj);
       OzGramJob gj;
       std::memset(&gj, 0, sizeof(gj));
       for (int sl = 0; sl < kOzSlices; ++sl)
-        gj.map[sl] = plan->map_of(B_WS, B.col + (size_t)sl * 64 * ldP * 2, P, b, ldP, 64);
+        gj.map[sl] = plan->map_of(B_WS, xj.colP.off + (size_t)sl * 64 * ldP * 2, P, b, ldP, 64);
       gj.expo = xj.expo;
       gj.G = op(B_WS, B.G);
       gj.P = P;
@@ -544,10 +544,11 @@ struct CqLists {
       g.tile_begin = gemm_total[pass];
       gemm_total[pass] += g.tiles_m;
       for (int sl = 0; sl < kOzSlices; ++sl) {
-        g.mapA[sl] = plan->map_of(B_WS, xj.rowP.off + (size_t)sl * xj.rows_pad * ldk * 2, b, P, ldk, 128);
+        g.mapA[sl] = gj.map[sl];   // the Gram's column planes, read MN-major
         g.mapB[sl] = plan->map_of(B_WS, sr.planes.off + (size_t)sl * sr.rows_pad * ldk * 2, b, b, ldk, 64);
       }
       g.expA = Operand{B_NONE, 0, 0};
+      g.a_mn = 1;
       g.expB = sr.expo;
       g.Y = pass == passes - 1 ? Qout : X[pass + 1];
       g.L = L;
@@ -1636,7 +1637,7 @@ static void build_hosvd_f64(tks_plan* plan) {
       Operand gate{B_NONE, 0, 0};
       if (cholqr) {
         const CqBuffers B{{h.cqX[0], h.cqX[1]}, h.cqCol, h.cqColE, h.cqG, h.cqRinv, h.cqRacc, h.cqFlag,
-                          h.ozA, h.ozEA, h.ozB, h.ozEB, h.cqPart, h.cqRowA2, h.cqColE2};
+                          h.ozA, h.ozEA, h.ozB, h.ozEB, h.cqPart, h.cqCol2, h.cqColE2};
         gate = cq.add(plan, X, L * Rr, L, b, B, op(B_WS, h.R64), Operand{B_NONE, 0, 0},
                       plan->params.hosvd_r == 3 ? 2 : 3);
       }
@@ -1771,13 +1772,13 @@ static void build_hosvd_f64(tks_plan* plan) {
           oz_slices.push_back(sj2);
           return sj2;
         };
-        // with CholeskyQR, pass 1 already cut H_(n)^T into digits against its column exponents (in ozA):
-        // the mode product reuses them with those exponents folded into the rows of P_n (no row
-        // exponents of X); Q_n P_n takes P_n's own digits
+        // with CholeskyQR, pass 1 already cut H_(n)^T into digits against its column exponents (the
+        // column planes in cqCol): the mode product reads them MN-major, with those exponents folded
+        // into the rows of P_n (no row exponents of X); Q_n P_n takes P_n's own digits
         OzSliceJob sx;
         if (cholqr) {
           std::memset(&sx, 0, sizeof(sx));
-          sx.planes = op(B_WS, h.ozA);
+          sx.planes = op(B_WS, h.cqCol);
           sx.expo = Operand{B_NONE, 0, 0};
           sx.rows = L * Rr;
           sx.rows_pad = (sx.rows + 7) / 8 * 8;
@@ -1788,7 +1789,7 @@ static void build_hosvd_f64(tks_plan* plan) {
                                      : slice(op(B_WS, h.P[n]), h.ozB, h.ozEB, rmax, 1);
         const OzSliceJob spq = cholqr ? slice(op(B_WS, h.P[n]), h.ozB2, h.ozEB2, rmax, 1) : sp;
         const OzSliceJob sq = slice(op(B_Q, h.q_off[n] * 8), h.ozQ, h.ozEQ, (int64_t)h.n[n], (int64_t)h.n[n]);
-        auto gemm_job = [&](const OzSliceJob& a, const OzSliceJob& sp, Operand Yop, int64_t Ly) {
+        auto gemm_job = [&](const OzSliceJob& a, const OzSliceJob& sp, Operand Yop, int64_t Ly, bool a_mn) {
           OzGemmJob g;
           std::memset(&g, 0, sizeof(g));
           g.M = (int)a.rows;
@@ -1799,9 +1800,13 @@ static void build_hosvd_f64(tks_plan* plan) {
           g.tile_begin = oz_gemm_total;
           oz_gemm_total += g.tiles_m * g.tiles_n;
           for (int sl = 0; sl < kOzSlices; ++sl) {
-            g.mapA[sl] = plan->map_of(B_WS, a.planes.off + (size_t)sl * a.rows_pad * ldk * 2, b, a.rows, ldk, 128);
+            // column planes (a_mn): 64 rows of rows_pad digits per plane, boxes of 64 rows x 64 k
+            g.mapA[sl] = a_mn ? plan->map_of(B_WS, a.planes.off + (size_t)sl * 64 * a.rows_pad * 2, a.rows, b,
+                                             a.rows_pad, 64)
+                              : plan->map_of(B_WS, a.planes.off + (size_t)sl * a.rows_pad * ldk * 2, b, a.rows, ldk, 128);
             g.mapB[sl] = plan->map_of(B_WS, sp.planes.off + (size_t)sl * sp.rows_pad * ldk * 2, b, rmax, ldk, 64);
           }
+          g.a_mn = a_mn ? 1 : 0;
           g.expA = a.expo;
           g.expB = sp.expo;
           g.Y = Yop;
@@ -1809,8 +1814,8 @@ static void build_hosvd_f64(tks_plan* plan) {
           g.rmax = rmax;
           oz_gemms.push_back(g);
         };
-        gemm_job(sx, sp, tj.Y, L);
-        gemm_job(sq, spq, fj.Y, (int64_t)h.n[n]);
+        gemm_job(sx, sp, tj.Y, L, cholqr);
+        gemm_job(sq, spq, fj.Y, (int64_t)h.n[n], false);
       }
     }
     char nm[32];
@@ -2010,7 +2015,7 @@ static tks_status create_plan(tks_plan** out, const tks_problem* problems, int32
           B.rowB = alloc((size_t)kOzSlices * 64 * 64 * 2);
           B.rowBE = alloc(64 * 4);
           B.part = alloc((size_t)ceil_div(h.n[m], 64) * 64 * 4);
-          B.rowA2 = B.rowA;
+          B.col2 = B.col;
           B.colE2 = B.colE;
         }
       }
@@ -2129,9 +2134,9 @@ static tks_status create_plan(tks_plan** out, const tks_problem* problems, int32
           h.cqRacc = alloc(64 * 64 * 8);
           h.cqFlag = alloc(4);
           h.cqPart = alloc((size_t)ceil_div(fib, 64) * 64 * 4);
-          // pass 1's row digits of H_(n)^T (in ozA) serve the mode product H x_n P_n^T afterwards, so
-          // the later passes slice into buffers of their own
-          h.cqRowA2 = alloc((size_t)kOzSlices * fib * ldk * 2);
+          // pass 1's column digits of H_(n)^T (in cqCol) serve the mode product H x_n P_n^T afterwards,
+          // so the later passes slice into buffers of their own
+          h.cqCol2 = alloc((size_t)kOzSlices * 64 * ldP * 2);
           h.cqColE2 = alloc(64 * 4);
           h.ozB2 = alloc((size_t)kOzSlices * cols * ldk * 2);
           h.ozEB2 = alloc((size_t)cols * 4);

@@ -451,7 +451,14 @@ __global__ void __launch_bounds__(kOzGemmThreads, 1) oz_gemm_kernel(const OzGemm
           bkey = key;
           tc::mbar_expect_tx(full, (uint32_t)(kOzSlices * (kOzATile + (loadB ? kOzBTile : 0))));
           for (int s = 0; s < kOzSlices; ++s) {
-            tc::tma_load_2d(At + s * kOzATile, &maps[J.mapA[s]], full, kb * kOzBK, tm * kOzBM);
+            if (J.a_mn) {
+              // column planes: two 64-row boxes (rows fastest) per plane, K = 64 digit columns each
+              tc::tma_load_2d(At + s * kOzATile, &maps[J.mapA[s]], full, tm * kOzBM, kb * kOzBK);
+              tc::tma_load_2d(At + s * kOzATile + kOzATile / 2, &maps[J.mapA[s]], full, tm * kOzBM + kOzBM / 2,
+                              kb * kOzBK);
+            } else {
+              tc::tma_load_2d(At + s * kOzATile, &maps[J.mapA[s]], full, kb * kOzBK, tm * kOzBM);
+            }
             if (loadB) tc::tma_load_2d(Bt + s * kOzBTile, &maps[J.mapB[s]], full, kb * kOzBK, tn * kOzBN);
           }
           ++issued;
@@ -462,7 +469,8 @@ __global__ void __launch_bounds__(kOzGemmThreads, 1) oz_gemm_kernel(const OzGemm
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      constexpr uint32_t idesc = tc::idesc_bf16_f32(kOzBM, kOzBN);
+      constexpr uint32_t idesc_k = tc::idesc_bf16_f32(kOzBM, kOzBN);
+      constexpr uint32_t idesc_mn = tc::idesc_bf16_f32_amn(kOzBM, kOzBN);
       int used = 0, tiles = 0;
       for (int t = t_begin; t < t_end && !*err; ++t) {
         const OzGemmJob& J = jobs[oz_tile_job(jobs, njobs, t)];
@@ -481,12 +489,18 @@ __global__ void __launch_bounds__(kOzGemmThreads, 1) oz_gemm_kernel(const OzGemm
           }
           tc::fence_after_sync();
           // level acc = s + t collects the digit pairs (s, t); its first product starts it at zero
-          // plane descriptors once per k-block; a 16-deep k step advances the start address by 32
-          // bytes, i.e. the descriptor's address field by 2
+          // plane descriptors once per k-block.  A 16-deep k step advances the start address by 32
+          // bytes in a K-major tile (address field + 2) and by two 8-row groups, 2048 bytes, in an
+          // MN-major one (+ 128); an MN-major A tile is two 64-row boxes 8 KB apart (LBO), 8-row
+          // groups 1024 bytes apart (SBO).
+          const bool amn = J.a_mn != 0;
+          const uint32_t idesc = amn ? idesc_mn : idesc_k;
+          const uint64_t astep = amn ? 128u : 2u;
           uint64_t dA[kOzSlices], dB[kOzSlices];
 #pragma unroll
           for (int p = 0; p < kOzSlices; ++p) {
-            dA[p] = tc::sw128_kmajor_desc(tc::smem_u32(At + p * kOzATile));
+            const uint32_t sa = tc::smem_u32(At + p * kOzATile);
+            dA[p] = amn ? tc::sw128_mnmajor_desc(sa, kOzATile / 2, 1024) : tc::sw128_kmajor_desc(sa);
             dB[p] = tc::sw128_kmajor_desc(tc::smem_u32(Bt + p * kOzBTile));
           }
 #pragma unroll
@@ -497,7 +511,7 @@ __global__ void __launch_bounds__(kOzGemmThreads, 1) oz_gemm_kernel(const OzGemm
 #pragma unroll
               for (int k = 0; k < kOzBK / 16; ++k) {
                 const uint32_t accumulate = (kb > 0 || s > 0 || k > 0) ? 1u : 0u;
-                tc::mma_bf16(d, dA[s] + 2 * k, dB[acc - s] + 2 * k, idesc, accumulate);
+                tc::mma_bf16(d, dA[s] + astep * k, dB[acc - s] + 2 * k, idesc, accumulate);
               }
             }
           }

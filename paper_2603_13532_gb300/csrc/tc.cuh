@@ -152,5 +152,23 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
          (static_cast<uint32_t>(M >> 4) << 24);
 }
 
+// The same with the A operand MN-major (its M index contiguous in shared memory; bit 15 of the
+// instruction descriptor).
+__host__ __device__ constexpr uint32_t idesc_bf16_f32_amn(int M, int N) { return idesc_bf16_f32(M, N) | (1u << 15); }
+
+// Shared-memory matrix descriptor of an MN-major tile in the 128-byte swizzled layout a TMA load with
+// CU_TENSOR_MAP_SWIZZLE_128B produces when the box's inner dimension runs along M (or N): K-rows of
+// 64 bf16 (128 bytes), 8-row atoms of 1024 bytes.  lbo: bytes between consecutive 64-element blocks
+// along M; sbo: bytes between consecutive 8-row groups along K.
+__device__ __forceinline__ uint64_t sw128_mnmajor_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);
+  d |= static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16;
+  d |= static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32;
+  d |= static_cast<uint64_t>(1) << 46;
+  d |= static_cast<uint64_t>(2) << 61;
+  return d;
+}
+
 }  // namespace tc
 }  // namespace tks

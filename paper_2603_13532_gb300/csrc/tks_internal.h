@@ -373,7 +373,9 @@ struct OzGemmJob {
   Operand expA, expB;    // int32 row exponents of X and of P^T (expA.base == B_NONE: X's are all 0)
   Operand Y;             // float64: element (q, c) at Y[l + L (c + rmax r)], q = l + L r
   int64_t L;
-  int32_t rmax, pad;
+  int32_t rmax;
+  int32_t a_mn;          // 1: mapA[s] are column digit planes (box 64 rows x 64 k, row index fastest),
+                         // read MN-major as two boxes per 128-row tile; 0: row planes, K-major
 };
 
 // Shifted CholeskyQR3 of X = H_(n)^T (P x b, element (i = l + L r, a) at src[l + L a + L b r]) with
