@@ -110,7 +110,7 @@ struct ProbHost {
   CqBuffers qcq[MAXD] = {};   // TKS_MIXED: CholeskyQR3 of the sketches Y_n (flag == 0: Householder QR)
   std::vector<size_t> chain;   // 2 ping-pong buffers per term
   // mixed-precision buffers (bytes): bf16 planes and float32 intermediates
-  size_t om_plane[MAXD] = {}, UT[MAXD] = {}, M32[MAXD] = {}, Vp[MAXD][3] = {}, Qp[MAXD][3] = {};
+  size_t om_plane[MAXD] = {}, M32[MAXD] = {}, Vp[MAXD][3] = {}, Qp[MAXD][3] = {};
   size_t AT32[MAXD] = {}, ATp[MAXD][3] = {}, Tp[3] = {};
   int ldU[MAXD] = {}, ldV[MAXD] = {}, ldA[MAXD] = {}, ldT = 0;
   bool fused3 = false;   // mixed path: order 3 with b_2, b_3 <= 64 -> fused projection kernel
@@ -470,14 +470,12 @@ struct CqLists {
       xj.part = op(B_WS, B.part);
       xj.expo = op(B_WS, pass == 0 ? B.colE : B.colE2);
       xj.colP = op(B_WS, pass == 0 ? B.col : B.col2);
-      xj.rowP = op(B_WS, B.rowA);
       xj.P = P;
       xj.L = L;
       xj.ldP = ldP;
       xj.rows_pad = (P + 7) / 8 * 8;
       xj.b = b;
       xj.tiles = oz_xslice_tiles(P);
-      xj.want_rows = 0;   // X R^-1 reads the column planes MN-major
       xj.tile_begin = xsl_total[pass];
       xsl_total[pass] += xj.tiles;
       xsl[pass].push_back(xj);
@@ -617,8 +615,6 @@ static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
   constexpr int kChainRows = 8;
   std::vector<OmegaJob> om;
   int64_t om_blocks = 0;
-  std::vector<TransposeJob> tr;
-  int tr_tiles = 0;
   std::vector<TcJob> tcM, tcY, tcA, tcH;
   std::vector<CoreSketchF32Job> cs;
   int64_t cs_total = 0;
@@ -652,19 +648,6 @@ static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
       oj.bf16 = 1;
       om_blocks += (oj.count + 3) / 4;
       om.push_back(oj);
-      TransposeJob t;
-      std::memset(&t, 0, sizeof(t));
-      t.src = op_abs(h.factors[m]);
-      t.dst = op(B_WS, h.UT[m]);
-      t.rows = (int)n;
-      t.cols = h.R[m];
-      t.ld_src = (int64_t)n;
-      t.ld_dst = h.ldU[m];
-      t.tiles_r = ceil_div(n, 64);
-      t.tiles_c = ceil_div(h.R[m], 64);
-      t.tile_begin = tr_tiles;
-      tr_tiles += t.tiles_r * t.tiles_c;
-      tr.push_back(t);
       TcJob a2 = tc_job(h.R[m], h.s[m], (int)n);
       a2.na = a2.nb = a2.npairs = 1;
       a2.mapA[0] = plan->map_of(B_ABS, reinterpret_cast<uintptr_t>(h.factors[m]), n, h.R[m], n, 128);
@@ -777,7 +760,9 @@ static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
       a4.na = 1;
       a4.nb = 3;
       a4.npairs = 3;
-      a4.mapA[0] = plan->map_of(B_WS, h.UT[n], h.R[n], nn, h.ldU[n], 128);
+      // A = Ucat_n as the caller stores it (row index fastest), read MN-major: no transposed copy
+      a4.mapA[0] = plan->map_of(B_ABS, reinterpret_cast<uintptr_t>(h.factors[n]), nn, h.R[n], nn, 64);
+      a4.a_mn = 1;
       for (int t = 0; t < 3; ++t) {
         a4.mapB[t] = plan->map_of(B_WS, h.Vp[n][t], h.R[n], h.S[n], h.ldV[n], 64);
         a4.pa[t] = 0;
@@ -1080,7 +1065,7 @@ static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
   }
   plan->push(plan->st_omega, S_OMEGA, om, om_blocks, "a1:omega", 0.0, 10.0 * plan->omega_elems);
   plan->push(plan->st_sketch, S_OMEGA, om, om_blocks, "a1:omega", 0.0, 10.0 * plan->omega_elems);
-  plan->push(plan->st_sketch, S_TRANSPOSE, tr, tr_tiles, "a4:UcatT", 0.0, 0.0);
+
   plan->push_tc(plan->st_sketch, tcM, "a2:M=UcatT.Omega[tc]");
   plan->push(plan->st_sketch, S_CS32, cs, cs_total, "a3:core_sketch[f32]", cs_flops, 0.0);
   if (!cs3.empty()) {
@@ -1993,7 +1978,6 @@ static tks_status create_plan(tks_plan** out, const tks_problem* problems, int32
       } else {
         h.ldU[m] = h.ldV[m] = h.ldA[m] = r8(h.R[m]);
         h.om_plane[m] = alloc((size_t)h.n[m] * h.s[m] * 2);
-        h.UT[m] = alloc((size_t)h.ldU[m] * h.n[m] * 2);
         h.M32[m] = alloc((size_t)h.R[m] * h.s[m] * 4);
         for (int t = 0; t < 3; ++t) h.Vp[m][t] = alloc((size_t)h.ldV[m] * h.S[m] * 2);
         for (int t = 0; t < 3; ++t) h.Qp[m][t] = alloc((size_t)h.n[m] * h.b[m] * 2);
@@ -2010,8 +1994,6 @@ static tks_status create_plan(tks_plan** out, const tks_problem* problems, int32
           B.Rinv = alloc(64 * 64 * 8);
           B.Racc = alloc(64 * 64 * 8);
           B.flag = alloc(4);
-          B.rowA = alloc((size_t)kOzSlices * rows8 * 64 * 2);
-          B.rowAE = alloc((size_t)rows8 * 4);
           B.rowB = alloc((size_t)kOzSlices * 64 * 64 * 2);
           B.rowBE = alloc(64 * 4);
           B.part = alloc((size_t)ceil_div(h.n[m], 64) * 64 * 4);

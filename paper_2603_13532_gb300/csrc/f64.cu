@@ -69,11 +69,7 @@ constexpr int GT = 64;   // tile edge
 constexpr int GK = 16;   // k step
 
 __device__ __forceinline__ int find_tile_job(const GemmJob* jobs, int njobs, int tile) {
-  int lo = 0, hi = njobs - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (jobs[mid].tile_begin <= tile) lo = mid; else hi = mid - 1;
-  }
+  const int lo = tile_job(jobs, njobs, tile);
   return lo;
 }
 

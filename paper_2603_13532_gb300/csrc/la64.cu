@@ -721,11 +721,7 @@ __global__ void __launch_bounds__(kTtmThreads) ttm_f64_kernel(const TtmJob* __re
   constexpr int kCols = 16 * kCj;
   extern __shared__ double tsm64[];
   __shared__ int64_t fib_off[kTtmF];
-  int lo = 0, hi = njobs - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (jobs[mid].tile_begin <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
-  }
+  const int lo = tile_job(jobs, njobs, (int)blockIdx.x);
   const TtmJob& J = jobs[lo];
   const int b = J.b, rmax = J.rmax;
   const int bp = (b + 3) & ~3;

@@ -36,11 +36,7 @@ __global__ void __launch_bounds__(256) simt_gemm_f32_kernel(const SimtJob* __res
                                                             Bases bases) {
   __shared__ float As[SK][ST + 1];
   __shared__ float Bs[SK][ST + 1];
-  int lo = 0, hi = njobs - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (jobs[mid].tile_begin <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
-  }
+  const int lo = tile_job(jobs, njobs, (int)blockIdx.x);
   const SimtJob& J = jobs[lo];
   int local = blockIdx.x - J.tile_begin;
   const int tn = local % J.tiles_n;
@@ -394,11 +390,7 @@ __global__ void __launch_bounds__(256) transpose_bf16_kernel(const TransposeJob*
   // 16-byte store of the destination hit distinct banks; each destination row gets 128 contiguous
   // bytes from 8 lanes.
   __shared__ __align__(16) uint16_t tile[64][66];
-  int lo = 0, hi = njobs - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (jobs[mid].tile_begin <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
-  }
+  const int lo = tile_job(jobs, njobs, (int)blockIdx.x);
   const TransposeJob& J = jobs[lo];
   const int local = blockIdx.x - J.tile_begin;
   const int tr = local % J.tiles_r, tcol = local / J.tiles_r;

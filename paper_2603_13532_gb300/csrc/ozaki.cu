@@ -43,11 +43,7 @@ __global__ void __launch_bounds__(kOzSliceThreads) oz_slice_kernel(const OzSlice
   __shared__ int64_t roff[kOzRowsPerCta];
   __shared__ int rexp[kOzRowsPerCta];
   __shared__ int kx[kOzMaxK];      // per-column exponent offsets: element (q, a) is sliced as x 2^kx[a]
-  int lo = 0, hi = njobs - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (jobs[mid].tile_begin <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
-  }
+  const int lo = tile_job(jobs, njobs, (int)blockIdx.x);
   const OzSliceJob& J = jobs[lo];
   const int K = J.K;
   const int64_t L = J.L;
@@ -140,11 +136,7 @@ constexpr int kOzXMaxB = 64;           // CholeskyQR3 runs for b <= 64
 constexpr int kOzXPitch = 66;          // doubles per staged row; the same bytes hold 4 digit planes later
 
 __device__ __forceinline__ const OzXSliceJob& oz_xjob(const OzXSliceJob* __restrict__ jobs, int njobs) {
-  int lo = 0, hi = njobs - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (jobs[mid].tile_begin <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
-  }
+  const int lo = tile_job(jobs, njobs, (int)blockIdx.x);
   return jobs[lo];
 }
 
@@ -233,8 +225,7 @@ __global__ void __launch_bounds__(kOzXThreads) oz_xdig_kernel(const OzXSliceJob*
   }
   __syncthreads();
   uint16_t* colP = at<uint16_t>(bases, J.colP);
-  uint16_t* rowP = at<uint16_t>(bases, J.rowP);
-  const int64_t cstride = 64 * J.ldP, rstride = J.rows_pad * 64;
+  const int64_t cstride = 64 * J.ldP;
   // each element's magnitude once, in registers (M < 2^56, the sign in bit 63; 0 outside the tile)
   constexpr int kPer = kOzXRows * 64 / kOzXThreads;
   unsigned long long mg[kPer];
@@ -250,8 +241,8 @@ __global__ void __launch_bounds__(kOzXThreads) oz_xdig_kernel(const OzXSliceJob*
   }
   __syncthreads();
   // the staged tile's bytes now hold four digit planes at a time: dg[s][q][a], rows of kOzXPitch
-  // bf16 (a 4-byte aligned row pitch, rows on distinct banks for a column read); each digit is
-  // formed once and written to both layouts with 16-byte stores
+  // bf16 (rows on distinct banks for a column read); each digit is formed once and leaves in
+  // 16-byte stores of 8 rows of one column
   constexpr int kDPitch = kOzXPitch;   // bf16 per digit row: 4 planes x 64 rows fill the staged tile's bytes
   uint16_t* dg = reinterpret_cast<uint16_t*>(&xs[0][0]);
   constexpr int kDPlane = kOzXRows * kDPitch;
@@ -274,16 +265,6 @@ __global__ void __launch_bounds__(kOzXThreads) oz_xdig_kernel(const OzXSliceJob*
       }
     }
     __syncthreads();
-    // row planes: (slice, row q, 8 columns) -> one 16-byte store of plane row i0 + q
-    for (int it = threadIdx.x; J.want_rows && it < 4 * kOzXRows * 8; it += kOzXThreads) {
-      const int s4 = it >> 9, q = (it >> 3) & 63, c = it & 7;
-      if (q < nq && 8 * c < b) {
-        const uint32_t* src = reinterpret_cast<const uint32_t*>(dg + s4 * kDPlane + q * kDPitch + 8 * c);
-        uint4 w;
-        w.x = src[0]; w.y = src[1]; w.z = src[2]; w.w = src[3];
-        *reinterpret_cast<uint4*>(rowP + (4 * half + s4) * rstride + (i0 + q) * 64 + 8 * c) = w;
-      }
-    }
     // column planes: (slice, column a, 8 rows) -> one 16-byte store of plane row a
     for (int it = threadIdx.x; it < 4 * 64 * 8; it += kOzXThreads) {
       const int s4 = it >> 9, a = (it >> 3) & 63, c = it & 7;
@@ -385,11 +366,7 @@ constexpr int kOzGemmThreads = 320;             // TMA, MMA and 8 epilogue warps
 constexpr size_t kOzSmem = 1024 + (size_t)kOzSlices * (kOzATile + kOzBTile) + 64 + 8 * 32 * 9 * sizeof(double);
 
 __device__ __forceinline__ int oz_tile_job(const OzGemmJob* __restrict__ jobs, int njobs, int t) {
-  int lo = 0, hi = njobs - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (jobs[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
-  }
+  const int lo = tile_job(jobs, njobs, t);
   return lo;
 }
 

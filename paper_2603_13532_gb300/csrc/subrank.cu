@@ -101,11 +101,7 @@ __global__ void __launch_bounds__(kGThreads) gram_f64_kernel(const GramJob* __re
                                                              Bases bases) {
   __shared__ double As[kGK][kGPad];
   __shared__ double Bs[kGK][kGPad];
-  int lo = 0, hi = njobs - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (jobs[mid].tile_begin <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
-  }
+  const int lo = tile_job(jobs, njobs, (int)blockIdx.x);
   const GramJob& J = jobs[lo];
   const int t = (int)blockIdx.x - J.tile_begin;
   int ti = 0;

@@ -70,11 +70,7 @@ __global__ void __launch_bounds__(192, 1)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tmem_full + 1);
   volatile int* err = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
-  int lo = 0, hi = njobs - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (jobs[mid].tile_begin <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
-  }
+  const int lo = tile_job(jobs, njobs, (int)blockIdx.x);
   const TcJob& J = jobs[lo];
   const int local = blockIdx.x - J.tile_begin;
   const int tn = local % J.tiles_n, tm = local / J.tiles_n;
@@ -127,7 +123,15 @@ __global__ void __launch_bounds__(192, 1)
           break;
         }
         tc::mbar_expect_tx(&full[s], bytes);
-        for (int i = 0; i < J.na; ++i) tc::tma_load_2d(a_tile(s, i), &maps[J.mapA[i]], &full[s], kb * kBK, m0);
+        for (int i = 0; i < J.na; ++i) {
+          if (J.a_mn) {
+            // A stored with its row index fastest (e.g. Ucat itself): two 64-row boxes per plane
+            tc::tma_load_2d(a_tile(s, i), &maps[J.mapA[i]], &full[s], m0, kb * kBK);
+            tc::tma_load_2d(a_tile(s, i) + kATile / 2, &maps[J.mapA[i]], &full[s], m0 + kBM / 2, kb * kBK);
+          } else {
+            tc::tma_load_2d(a_tile(s, i), &maps[J.mapA[i]], &full[s], kb * kBK, m0);
+          }
+        }
         for (int j = 0; j < J.nb; ++j) tc::tma_load_2d(b_tile(s, j), &maps[J.mapB[j]], &full[s], kb * kBK, n0);
         issued = kb + 1;
       }
@@ -137,7 +141,11 @@ __global__ void __launch_bounds__(192, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      constexpr uint32_t idesc = tc::idesc_bf16_f32(kBM, BN);
+      // an MN-major A (a_mn): two 64-row boxes 8 KB apart (LBO), 8-row k groups 1024 bytes apart
+      // (SBO); a 16-deep k step moves its start by 2048 bytes (address field + 128), a K-major
+      // tile's by 32 bytes (+ 2)
+      const uint32_t idesc = J.a_mn ? tc::idesc_bf16_f32_amn(kBM, BN) : tc::idesc_bf16_f32(kBM, BN);
+      const uint64_t astep = J.a_mn ? 128u : 2u;
       for (int kb = 0; kb < nk; ++kb) {
         const int s = kb % stages, round = kb / stages;
         if (*err || !tc::mbar_wait(&full[s], round & 1, kWaitCycles)) {
@@ -151,9 +159,11 @@ __global__ void __launch_bounds__(192, 1)
         for (int p = 0; p < J.npairs; ++p) {
           const uint32_t a0 = tc::smem_u32(a_tile(s, J.pa[p]));
           const uint32_t b0 = tc::smem_u32(b_tile(s, J.pb[p]));
+          const uint64_t da = J.a_mn ? tc::sw128_mnmajor_desc(a0, kATile / 2, 1024) : tc::sw128_kmajor_desc(a0);
+          const uint64_t db = tc::sw128_kmajor_desc(b0);
 #pragma unroll
           for (int k = 0; k < kBK / 16; ++k) {
-            tc::mma_bf16(d, tc::sw128_kmajor_desc(a0 + 32 * k), tc::sw128_kmajor_desc(b0 + 32 * k), idesc, acc);
+            tc::mma_bf16(d, da + astep * k, db + 2 * k, idesc, acc);
             acc = 1;
           }
         }

@@ -288,7 +288,8 @@ struct TcEpi {
 struct TcJob {
   int32_t M, N, K;
   int32_t tiles_m, tiles_n, tile_begin;
-  int32_t na, nb, npairs, pad;
+  int32_t na, nb, npairs;
+  int32_t a_mn;          // 1: the A maps have the row index innermost (box 64 rows x 64 k), read MN-major
   int32_t mapA[3], mapB[3];
   uint8_t pa[8], pb[8];
   TcEpi epi;
@@ -383,15 +384,14 @@ struct OzGemmJob {
 // exponent per COLUMN, e_a with |X[i][a]| < 2^e_a, in 64-row tiles (one CTA per tile, two launches):
 //   oz_xmax:  the largest biased exponent field of each column over the tile -> part[tile][a];
 //   oz_xdig:  e_a from the partials of the matrix's tiles (the first tile stores them at expo[a]),
-//             then the same digits twice: plane s of column a at colP + (s * 64 + a) * ldP (element i:
-//             the Gram's operand, K = P) and of row i at rowP + (s * rows_pad + i) * 64 (element a:
-//             the A operand of X Rinv, K = b).  With column exponents X Rinv needs no row exponents:
-//             the Cholesky step writes Rinv with row a scaled by 2^e_a.
+//             then the digits: plane s of column a at colP + (s * 64 + a) * ldP (element i).  The
+//             Gram reads these planes K-major (K = rows) and X Rinv reads them MN-major (K = columns);
+//             with column exponents X Rinv needs no row exponents: the Cholesky step writes Rinv with
+//             row a scaled by 2^e_a.
 struct OzXSliceJob {
-  Operand src, part, expo, colP, rowP;
+  Operand src, part, expo, colP;
   int64_t P, L, ldP, rows_pad;
-  int32_t b, tiles, tile_begin;
-  int32_t want_rows;     // 0: no X Rinv follows this pass (its Gram is all it needs): skip the row planes
+  int32_t b, tiles, tile_begin, pad;
 };
 
 // G = X^T X (b x b, b <= 64) from the column digit planes (TMA maps map[s], box 64 k x 64 rows),
@@ -457,6 +457,28 @@ struct Status {
   int32_t code;                 // first tks_status recorded by a kernel
   int32_t pad;
 };
+
+#ifdef __CUDACC__
+// The job that owns tile t of a grouped launch (jobs in tile order, job j covering tiles
+// [jobs[j].tile_begin, jobs[j + 1].tile_begin)).  A batch of equal problems gives every job the same
+// tile count, so the guess from the first job's count is checked first: two rounds of loads from the
+// job table instead of the log2(njobs) dependent rounds of a binary search, which remains the fallback.
+template <class Job>
+__device__ __forceinline__ int tile_job(const Job* __restrict__ jobs, int njobs, int t) {
+  if (njobs <= 1) return 0;
+  const int t0 = jobs[0].tile_begin, per = jobs[1].tile_begin - t0;
+  if (per > 0) {
+    const int j = (t - t0) / per;
+    if (j >= 0 && j < njobs && jobs[j].tile_begin <= t && (j + 1 == njobs || jobs[j + 1].tile_begin > t)) return j;
+  }
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+#endif
 
 // Sets the thread-local message returned by tks_last_error (host code of every entry point).
 void set_last_error(const std::string& msg);

@@ -28,11 +28,7 @@ __device__ __forceinline__ float load_elem(const char* base, int32_t type, int64
 
 __global__ void __launch_bounds__(kThreads) ttm_rows_kernel(const TtmJob* __restrict__ jobs, int njobs, Bases bases) {
   extern __shared__ __align__(16) float tsm[];
-  int lo = 0, hi = njobs - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (jobs[mid].tile_begin <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
-  }
+  const int lo = tile_job(jobs, njobs, (int)blockIdx.x);
   const TtmJob& J = jobs[lo];
   const int b = J.b, rmax = J.rmax;
   const int64_t L = J.L, rows = J.L * J.Rr;
