@@ -348,22 +348,66 @@ __host__ __device__ __forceinline__ double oz_compose(long long hi, long long lo
   return scalbn(m, e2 + scale);
 }
 
+// The same rounding for |hi|, |lo| < 2^60 (the digit products' level sums), without 128-bit
+// arithmetic or branches: N = s 2^28 + r with s = hi + floor(lo / 2^28) and 0 <= r < 2^28, its
+// magnitude m_hi 2^28 + m_lo (m_lo < 2^28), shifted right by k = max(bitlen(m_hi) - 36, 0) bits
+// into one 64-bit word (the k bits shifted out only feed the sticky bit), then rounded to 53 bits.
+__host__ __device__ __forceinline__ double oz_compose_b(long long hi, long long lo, int scale) {
+  constexpr unsigned long long kMask28 = (1ull << 28) - 1ull;
+  const long long sv = hi + (lo >> 28);
+  const unsigned long long r = (unsigned long long)lo & kMask28;
+  const bool neg = sv < 0;
+  const unsigned long long mh = neg ? ~(unsigned long long)sv + (r == 0ull ? 1ull : 0ull) : (unsigned long long)sv;
+  const unsigned long long ml = neg ? (0ull - r) & kMask28 : r;
+  const int lh = 64 - oz_clz64(mh);
+  const int k = lh > 36 ? lh - 36 : 0;
+  const unsigned long long w = (mh << (28 - k)) | (ml >> k);
+  const bool lost = (ml & ((1ull << k) - 1ull)) != 0ull;
+  if (w == 0ull) return 0.0;
+  const int lz = oz_clz64(w);
+  const unsigned long long top = w << lz;               // leading one at bit 63
+  unsigned long long mant = top >> 11;
+  const bool half = (top >> 10) & 1ull;
+  const bool sticky = lost || (top & 0x3ffull) != 0ull;
+  mant += (half && (sticky || (mant & 1ull))) ? 1ull : 0ull;
+  const int e_lead = 63 - lz + k + scale;               // exponent of N's leading bit, scaled
+  const int field = e_lead + 1023;
+  if (field >= 1 && field <= 2045) {
+    // mant in [2^52, 2^53]: the implicit bit carries into the exponent field, so a mantissa that
+    // rounded up to 2^53 gives the next binade with a zero fraction
+    const unsigned long long bits = (neg ? (1ull << 63) : 0ull) + ((unsigned long long)(field - 1) << 52) + mant;
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double((long long)bits);
+#else
+    double d;
+    memcpy(&d, &bits, sizeof(d));
+    return d;
+#endif
+  }
+  const double m = neg ? -(double)mant : (double)mant;
+  return scalbn(m, e_lead - 52);
+}
+
 // ----------------------------------------------------------------------------- digit products
 // Persistent: CTA c takes the contiguous tile range [c T / G, (c + 1) T / G) of the T tiles (G CTAs,
 // at most one per SM), so consecutive tiles mostly belong to one job and share its P digits.  Warp 0
 // (one thread) loads the eight digit planes of a tile's X rows (and of its P columns when they change)
 // with TMA, one k-block of 64 at a time (K <= 96 takes two); warp 1 owns the kOzLevels TMEM
 // accumulators (64 columns each, the whole 512) and one thread issues the 36 digit-pair products of
-// every k-block, pair (s, t) into accumulator s + t; warps 2-9 read the accumulators (TMEM lane
-// quadrant warp % 4, columns 32 (warp - 2) / 4 ...), combine the levels in 64-bit integers and write Y.
+// every k-block, pair (s, t) into accumulator s + t; warps 2-17 read the accumulators (TMEM lane
+// quadrant warp % 4, columns 16 (warp - 2) / 4 ...), combine the levels in integers and write Y.
+// Four epilogue warps per quadrant keep the integer pipes busy while one warp waits on a TMEM load.
 // The next tile's planes load while the epilogue of the last one runs.  Every wait is bounded: on a
 // timeout the kernel records TKS_ETIMEOUT, drains its own copies and products (bounded), frees TMEM
 // and returns.
 constexpr int kOzBM = 128, kOzBN = 64, kOzBK = 64;
 constexpr int kOzATile = kOzBM * kOzBK * 2;     // 16 KB per plane
 constexpr int kOzBTile = kOzBN * kOzBK * 2;     // 8 KB per plane
-constexpr int kOzGemmThreads = 320;             // TMA, MMA and 8 epilogue warps
-constexpr size_t kOzSmem = 1024 + (size_t)kOzSlices * (kOzATile + kOzBTile) + 64 + 8 * 32 * 9 * sizeof(double);
+constexpr int kOzGemmThreads = 576;             // TMA, MMA and 16 epilogue warps
+constexpr int kOzEpiCols = 16;                  // columns per epilogue warp
+constexpr int kOzStagePitch = 5;                // staged stores: 32 rows x 4 columns (+1) per warp
+constexpr size_t kOzSmem = 1024 + (size_t)kOzSlices * (kOzATile + kOzBTile) + 64 +
+                           16 * 32 * kOzStagePitch * sizeof(double);
 
 __device__ __forceinline__ int oz_tile_job(const OzGemmJob* __restrict__ jobs, int njobs, int t) {
   const int lo = tile_job(jobs, njobs, t);
@@ -378,19 +422,23 @@ __global__ void __launch_bounds__(kOzGemmThreads, 1) oz_gemm_kernel(const OzGemm
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(oz_smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* At = smem;
   uint8_t* Bt = smem + kOzSlices * kOzATile;
+  // full/empty[h]: A planes 4h .. 4h + 3 of a k-block (half 0 also carries P's planes when they
+  // change), so that the next tile's first half loads while the products of the second half run
   uint64_t* full = reinterpret_cast<uint64_t*>(Bt + kOzSlices * kOzBTile);
-  uint64_t* empty = full + 1;
-  uint64_t* tmem_full = empty + 1;
+  uint64_t* empty = full + 2;
+  uint64_t* tmem_full = empty + 2;
   uint64_t* tmem_empty = tmem_full + 1;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tmem_empty + 1);
   volatile int* err = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  double* ostage = reinterpret_cast<double*>(smem + kOzSlices * (kOzATile + kOzBTile) + 64);   // 8 warps x 32 x 9
+  double* ostage = reinterpret_cast<double*>(smem + kOzSlices * (kOzATile + kOzBTile) + 64);   // 16 x 32 x 5
   const int t_begin = (int)(((long long)blockIdx.x * total_tiles) / gridDim.x);
   const int t_end = (int)(((long long)(blockIdx.x + 1) * total_tiles) / gridDim.x);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    tc::mbar_init(full, 1);
-    tc::mbar_init(empty, 1);
+    for (int h = 0; h < 2; ++h) {
+      tc::mbar_init(&full[h], 1);
+      tc::mbar_init(&empty[h], 1);
+    }
     tc::mbar_init(tmem_full, 1);
     tc::mbar_init(tmem_empty, (kOzGemmThreads - 64) / 32);
     *err = 0;
@@ -404,7 +452,8 @@ __global__ void __launch_bounds__(kOzGemmThreads, 1) oz_gemm_kernel(const OzGemm
 
   if (warp == 0) {
     if (lane == 0) {
-      int issued = 0;
+      int issued = 0;        // k-blocks whose two halves were both issued
+      int issued_h[2] = {0, 0};
       long long bkey = -1;   // (job, tile column, k-block) whose P planes are in shared memory
       for (int t = t_begin; t < t_end && !*err; ++t) {
         const int ji = oz_tile_job(jobs, njobs, t);
@@ -417,32 +466,42 @@ __global__ void __launch_bounds__(kOzGemmThreads, 1) oz_gemm_kernel(const OzGemm
             tc::prefetch_tmap(&maps[J.mapA[s]]);
             tc::prefetch_tmap(&maps[J.mapB[s]]);
           }
-        for (int kb = 0; kb < nk; ++kb) {
-          // the single stage is refilled once the previous k-block's products have completed
-          if (*err || !tc::mbar_wait(empty, (issued & 1) ^ 1, kOzWait)) {
-            *err = 1;
-            break;
-          }
+        for (int kb = 0; kb < nk && !*err; ++kb) {
           const long long key = ((long long)ji << 24) | ((long long)tn << 4) | kb;
           const bool loadB = key != bkey;
           bkey = key;
-          tc::mbar_expect_tx(full, (uint32_t)(kOzSlices * (kOzATile + (loadB ? kOzBTile : 0))));
-          for (int s = 0; s < kOzSlices; ++s) {
-            if (J.a_mn) {
-              // column planes: two 64-row boxes (rows fastest) per plane, K = 64 digit columns each
-              tc::tma_load_2d(At + s * kOzATile, &maps[J.mapA[s]], full, tm * kOzBM, kb * kOzBK);
-              tc::tma_load_2d(At + s * kOzATile + kOzATile / 2, &maps[J.mapA[s]], full, tm * kOzBM + kOzBM / 2,
-                              kb * kOzBK);
-            } else {
-              tc::tma_load_2d(At + s * kOzATile, &maps[J.mapA[s]], full, kb * kOzBK, tm * kOzBM);
+          for (int h = 0; h < 2; ++h) {
+            // half h is refilled once the previous k-block's products that read it have completed;
+            // new P planes also wait for the second half (both halves' products read P)
+            bool ok = tc::mbar_wait(&empty[h], (issued & 1) ^ 1, kOzWait);
+            if (ok && h == 0 && loadB) ok = tc::mbar_wait(&empty[1], (issued & 1) ^ 1, kOzWait);
+            if (*err || !ok) {
+              *err = 1;
+              break;
             }
-            if (loadB) tc::tma_load_2d(Bt + s * kOzBTile, &maps[J.mapB[s]], full, kb * kOzBK, tn * kOzBN);
+            const bool withB = h == 0 && loadB;
+            tc::mbar_expect_tx(&full[h], (uint32_t)(kOzSlices / 2 * kOzATile + (withB ? kOzSlices * kOzBTile : 0)));
+            for (int s = 4 * h; s < 4 * h + 4; ++s) {
+              if (J.a_mn) {
+                // column planes: two 64-row boxes (rows fastest) per plane, K = 64 digit columns each
+                tc::tma_load_2d(At + s * kOzATile, &maps[J.mapA[s]], &full[h], tm * kOzBM, kb * kOzBK);
+                tc::tma_load_2d(At + s * kOzATile + kOzATile / 2, &maps[J.mapA[s]], &full[h], tm * kOzBM + kOzBM / 2,
+                                kb * kOzBK);
+              } else {
+                tc::tma_load_2d(At + s * kOzATile, &maps[J.mapA[s]], &full[h], kb * kOzBK, tm * kOzBM);
+              }
+            }
+            if (withB)
+              for (int s = 0; s < kOzSlices; ++s)
+                tc::tma_load_2d(Bt + s * kOzBTile, &maps[J.mapB[s]], &full[0], kb * kOzBK, tn * kOzBN);
+            ++issued_h[h];
           }
-          ++issued;
+          if (!*err) ++issued;
         }
       }
-      // drain: the last copies issued have landed before the CTA tears down
-      if (issued > 0 && !tc::mbar_wait(full, (issued - 1) & 1, kOzWait)) *err = 1;
+      // drain: the last copies issued into each half have landed before the CTA tears down
+      for (int h = 0; h < 2; ++h)
+        if (issued_h[h] > 0 && !tc::mbar_wait(&full[h], (issued_h[h] - 1) & 1, kOzWait)) *err = 1;
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -459,14 +518,9 @@ __global__ void __launch_bounds__(kOzGemmThreads, 1) oz_gemm_kernel(const OzGemm
         }
         tc::fence_after_sync();
         bool ok = true;
-        for (int kb = 0; kb < nk; ++kb) {
-          if (*err || !tc::mbar_wait(full, used & 1, kOzWait)) {
-            ok = false;
-            break;
-          }
-          tc::fence_after_sync();
-          // level acc = s + t collects the digit pairs (s, t); its first product starts it at zero
-          // plane descriptors once per k-block.  A 16-deep k step advances the start address by 32
+        for (int kb = 0; kb < nk && ok; ++kb) {
+          // level acc = s + t collects the digit pairs (s, t); its first product starts it at zero.
+          // Plane descriptors once per k-block.  A 16-deep k step advances the start address by 32
           // bytes in a K-major tile (address field + 2) and by two 8-row groups, 2048 bytes, in an
           // MN-major one (+ 128); an MN-major A tile is two 64-row boxes 8 KB apart (LBO), 8-row
           // groups 1024 bytes apart (SBO).
@@ -480,20 +534,29 @@ __global__ void __launch_bounds__(kOzGemmThreads, 1) oz_gemm_kernel(const OzGemm
             dA[p] = amn ? tc::sw128_mnmajor_desc(sa, kOzATile / 2, 1024) : tc::sw128_kmajor_desc(sa);
             dB[p] = tc::sw128_kmajor_desc(tc::smem_u32(Bt + p * kOzBTile));
           }
+          // first half: the pairs with s <= 3 (they start every level); second half: s >= 4
 #pragma unroll
-          for (int acc = 0; acc < kOzLevels; ++acc) {
-            const uint32_t d = tmem + (uint32_t)(acc * kOzBN);
+          for (int h = 0; h < 2; ++h) {
+            if (*err || !tc::mbar_wait(&full[h], used & 1, kOzWait)) {
+              ok = false;
+              break;
+            }
+            tc::fence_after_sync();
 #pragma unroll
-            for (int s = 0; s <= acc; ++s) {
+            for (int acc = 0; acc < kOzLevels; ++acc) {
+              const uint32_t d = tmem + (uint32_t)(acc * kOzBN);
 #pragma unroll
-              for (int k = 0; k < kOzBK / 16; ++k) {
-                const uint32_t accumulate = (kb > 0 || s > 0 || k > 0) ? 1u : 0u;
-                tc::mma_bf16(d, dA[s] + astep * k, dB[acc - s] + 2 * k, idesc, accumulate);
+              for (int s = 4 * h; s <= acc && s < 4 * h + 4; ++s) {
+#pragma unroll
+                for (int k = 0; k < kOzBK / 16; ++k) {
+                  const uint32_t accumulate = (kb > 0 || s > 0 || k > 0) ? 1u : 0u;
+                  tc::mma_bf16(d, dA[s] + astep * k, dB[acc - s] + 2 * k, idesc, accumulate);
+                }
               }
             }
+            tc::mma_commit(&empty[h]);
           }
-          tc::mma_commit(empty);
-          ++used;
+          if (ok) ++used;
         }
         if (!ok) {
           *err = 1;
@@ -507,9 +570,20 @@ __global__ void __launch_bounds__(kOzGemmThreads, 1) oz_gemm_kernel(const OzGemm
     }
   } else {
     const int q = warp & 3;
-    const int cbase = 32 * ((warp - 2) >> 2);
+    const int cbase = kOzEpiCols * ((warp - 2) >> 2);
     int tiles = 0;
     for (int t = t_begin; t < t_end; ++t) {
+      // this tile's row and column exponents are read while the products run
+      const OzGemmJob& J = jobs[oz_tile_job(jobs, njobs, t)];
+      const int local = t - J.tile_begin;
+      const int tn = local % J.tiles_n, tm = local / J.tiles_n;
+      const int row = tm * kOzBM + 32 * q + lane;
+      const bool live = row < J.M;
+      const int n0 = tn * kOzBN + cbase;
+      const int eA = (live && J.expA.base != B_NONE) ? at<const int32_t>(bases, J.expA)[row] : 0;
+      const int ecol = n0 + (lane & (kOzEpiCols - 1));
+      const int eB = ecol < J.N ? at<const int32_t>(bases, J.expB)[ecol] : 0;   // lane c: column n0 + c
+      double* Y = at<double>(bases, J.Y);
       bool ok = tc::mbar_wait(tmem_full, tiles & 1, kOzWait);
       ok = __all_sync(0xffffffffu, ok) && !*err;
       if (!ok) {
@@ -517,40 +591,30 @@ __global__ void __launch_bounds__(kOzGemmThreads, 1) oz_gemm_kernel(const OzGemm
         break;
       }
       tc::fence_after_sync();
-      const OzGemmJob& J = jobs[oz_tile_job(jobs, njobs, t)];
-      const int local = t - J.tile_begin;
-      const int tn = local % J.tiles_n, tm = local / J.tiles_n;
-      const int row = tm * kOzBM + 32 * q + lane;
-      const bool live = row < J.M;
-      const int eA = (live && J.expA.base != B_NONE) ? at<const int32_t>(bases, J.expA)[row] : 0;
-      const int32_t* expB = at<const int32_t>(bases, J.expB);
-      double* Y = at<double>(bases, J.Y);
-      const int64_t r = live ? (int64_t)row / J.L : 0, l = (int64_t)row - r * J.L;
-      double* y = Y + l + J.L * (int64_t)J.rmax * r;
-      const int n0 = tn * kOzBN + cbase;
-      // this thread's row, columns n0 .. n0 + 31, composed before TMEM is released
-      double outv[32];
+      // this thread's row, columns n0 .. n0 + 15, composed before TMEM is released
+      double outv[kOzEpiCols];
 #pragma unroll
-      for (int c0 = 0; c0 < 32; c0 += 8) {
+      for (int c0 = 0; c0 < kOzEpiCols; c0 += 4) {
         if (n0 + c0 < J.N) {   // warp-uniform
-          uint32_t v[kOzLevels][8];
+          uint32_t v[kOzLevels][4];
 #pragma unroll
           for (int acc = 0; acc < kOzLevels; ++acc)
-            tc::tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * kOzBN + cbase + c0), v[acc]);
+            tc::tmem_ld4(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * kOzBN + cbase + c0), v[acc]);
           tc::tmem_ld_wait();
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const int col = n0 + c0 + j;
-            // exact integers below 2^24: sum_acc A_acc 2^(21 - 7 acc) in two 64-bit halves
-            long long hi64 = 0, lo64 = 0;
+          for (int j = 0; j < 4; ++j) {
+            // level sums are exact integers below 2^24, so adjacent levels pair exactly in 32 bits
+            // (A_2i 2^7 + A_2i+1), and sum_acc A_acc 2^(49 - 7 acc) = hi 2^28 + lo with
+            // hi = p0 2^14 + p1, lo = p2 2^14 + p3
+            int p[4];
 #pragma unroll
-            for (int acc = 0; acc < 4; ++acc)
-              hi64 = (hi64 << 7) + (long long)__float2int_rn(__uint_as_float(v[acc][j]));
-#pragma unroll
-            for (int acc = 4; acc < kOzLevels; ++acc)
-              lo64 = (lo64 << 7) + (long long)__float2int_rn(__uint_as_float(v[acc][j]));
+            for (int i = 0; i < 4; ++i)
+              p[i] = __float2int_rn(__uint_as_float(v[2 * i][j])) * 128 + __float2int_rn(__uint_as_float(v[2 * i + 1][j]));
+            const long long hi64 = (long long)p[0] * 16384 + p[1];
+            const long long lo64 = (long long)p[2] * 16384 + p[3];
+            const int scale = eA + __shfl_sync(0xffffffffu, eB, c0 + j) - 63;
             // value = 2^-35 (hi + 2^-28 lo) 2^(eA + eB) = (hi 2^28 + lo) 2^(eA + eB - 63)
-            outv[c0 + j] = (live && col < J.N) ? oz_compose(hi64, lo64, eA + expB[col] - 63) : 0.0;
+            outv[c0 + j] = (live && n0 + c0 + j < J.N) ? oz_compose_b(hi64, lo64, scale) : 0.0;
           }
         }
       }
@@ -559,28 +623,30 @@ __global__ void __launch_bounds__(kOzGemmThreads, 1) oz_gemm_kernel(const OzGemm
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(tmem_empty);
       if (J.L == 1) {
-        // rows are contiguous runs of rmax: transpose 32 rows x 8 columns through shared memory so
-        // that each store covers four rows' 64-byte segments instead of 32 scattered words
-        double* st = ostage + (warp - 2) * (32 * 9);
+        // rows are contiguous runs of rmax: transpose 32 rows x 4 columns through shared memory so
+        // that each store covers eight rows' 32-byte segments instead of 32 scattered words
+        double* st = ostage + (warp - 2) * (32 * kOzStagePitch);
         const int row0 = tm * kOzBM + 32 * q;
 #pragma unroll
-        for (int c0 = 0; c0 < 32; c0 += 8) {
+        for (int c0 = 0; c0 < kOzEpiCols; c0 += 4) {
           if (n0 + c0 < J.N) {
 #pragma unroll
-            for (int j = 0; j < 8; ++j) st[lane * 9 + j] = outv[c0 + j];
+            for (int j = 0; j < 4; ++j) st[lane * kOzStagePitch + j] = outv[c0 + j];
             __syncwarp();
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              const int r = 4 * i + (lane >> 3), c = lane & 7;
+            for (int i = 0; i < 4; ++i) {
+              const int r = 8 * i + (lane >> 2), c = lane & 3;
               const int rw = row0 + r, col = n0 + c0 + c;
-              if (rw < J.M && col < J.N) Y[(int64_t)J.rmax * rw + col] = st[r * 9 + c];
+              if (rw < J.M && col < J.N) Y[(int64_t)J.rmax * rw + col] = st[r * kOzStagePitch + c];
             }
             __syncwarp();
           }
         }
       } else if (live) {
+        const int64_t r = (int64_t)row / J.L, l = (int64_t)row - r * J.L;
+        double* y = Y + l + J.L * (int64_t)J.rmax * r;
 #pragma unroll
-        for (int c = 0; c < 32; ++c)
+        for (int c = 0; c < kOzEpiCols; ++c)
           if (n0 + c < J.N) y[J.L * (int64_t)(n0 + c)] = outv[c];
       }
       ++tiles;
