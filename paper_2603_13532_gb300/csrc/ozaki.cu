@@ -660,19 +660,25 @@ __global__ void __launch_bounds__(kOzGemmThreads, 1) oz_gemm_kernel(const OzGemm
 
 // ----------------------------------------------------------------------------- Gram matrices
 // G = X^T X (b x b, b <= 64) from the column digit planes, one CTA per job.  Warp 0 (one thread) loads
-// one k-block (64 rows of X) of all eight planes per stage, two stages; warp 1 owns the kOzLevels TMEM
-// accumulators and issues the 36 digit-pair products per k-block with A and B the same 64-column tiles
-// (an M = 128 product also reads the 64 rows after a tile, whose results land in TMEM lanes 64..127
-// and are ignored).  Every kOzGramGroup k-blocks the level sums, exact integers (8 pairs x 128 x
-// 127^2 < 2^24), are drained by warps 4, 5, 8 and 9 (TMEM lanes 0..63, half the columns each),
-// combined in 64-bit integers and added into two 64-bit integer accumulators per entry in shared
-// memory, so G is the exact sum rounded once at the end, with the scale 2^(e_i + e_j).  Waits are
-// bounded as in the other tensor-core kernels.
-constexpr int kOzGramGroup = 2;
-constexpr int kOzGramThreads = 320;   // TMA, MMA, and drain warps 4, 5, 8, 9 (two per TMEM lane quadrant)
+// one k-block (64 rows of X) of all eight planes per stage, two stages, each plane a 64-column tile,
+// stored in the order 0, 4, 1, 5, 2, 6, 3, 7 so that planes s and s + 4 form one 128-row operand.
+// Warp 1 issues, per k-block, the 26 products [X_s; X_(s+4)]^T X_t (s <= 3, s + t <= 7) into TMEM
+// block s + t: lanes 0..63 collect the digit pair (s, t) at level s + t, lanes 64..127 the pair
+// (s + 4, t) at level s + t + 4 (used for blocks 0..3, where s + t + 4 <= 7; the rest is ignored), so
+// the 36 pairs of levels 0..7 take 26 M = 128 products.  A level sum holds at most 4 pairs per block,
+// so kOzGramGroup = 4 k-blocks stay exact integers in float32 (4 pairs x 256 x 127^2 < 2^24); after
+// each group warps 4, 5, 8, 9 (TMEM lanes 0..63: levels 0..7 of the pairs s <= 3) and warps 2, 3, 6, 7
+// (lanes 64..127: levels 4..7 of the pairs s >= 4) combine the levels in integers and add them into
+// 64-bit integer accumulators in shared memory (hi, lo and the upper lanes' lo), so G is the exact
+// sum rounded once at the end, with the scale 2^(e_i + e_j).  Waits are bounded as in the other
+// tensor-core kernels.
+constexpr int kOzGramGroup = 4;
+constexpr int kOzGramThreads = 320;   // TMA, MMA, and drain warps 2..9 (two per TMEM lane quadrant)
 constexpr int kOzPlaneTile = 64 * kOzBK * 2;                          // 8 KB: 64 columns x 64 k
-constexpr int kOzStageBytes = (kOzSlices + 1) * kOzPlaneTile;         // + the 8 KB an M = 128 read passes
-constexpr size_t kOzGramSmem = 1024 + 2 * (size_t)kOzStageBytes + 2 * 64 * 64 * 8 + 128;
+constexpr int kOzStageBytes = kOzSlices * kOzPlaneTile;
+constexpr size_t kOzGramSmem = 1024 + 2 * (size_t)kOzStageBytes + 3 * 64 * 64 * 8 + 128;
+
+__device__ __forceinline__ int oz_gram_pos(int plane) { return plane < 4 ? 2 * plane : 2 * (plane - 4) + 1; }
 
 __global__ void __launch_bounds__(kOzGramThreads, 1) oz_gram_kernel(const OzGramJob* __restrict__ jobs,
                                                        const CUtensorMap* __restrict__ maps, Bases bases,
@@ -680,10 +686,12 @@ __global__ void __launch_bounds__(kOzGramThreads, 1) oz_gram_kernel(const OzGram
   extern __shared__ uint8_t og_smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(og_smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* stage[2] = {smem, smem + kOzStageBytes};
-  // the level sums of every drain, combined exactly in two 64-bit integers per entry, [col][row]
+  // the level sums of every drain, combined exactly in 64-bit integers per entry, [col][row]:
+  // hi (levels 0..3) and lo (levels 4..7) of the pairs s <= 3, lo2 (levels 4..7) of the pairs s >= 4
   long long* acc_hi = reinterpret_cast<long long*>(smem + 2 * kOzStageBytes);
   long long* acc_lo = acc_hi + 64 * 64;
-  uint64_t* full = reinterpret_cast<uint64_t*>(acc_lo + 64 * 64);
+  long long* acc_lo2 = acc_lo + 64 * 64;
+  uint64_t* full = reinterpret_cast<uint64_t*>(acc_lo2 + 64 * 64);
   uint64_t* empty = full + 2;
   uint64_t* tmem_full = empty + 2;
   uint64_t* tmem_empty = tmem_full + 1;
@@ -699,14 +707,11 @@ __global__ void __launch_bounds__(kOzGramThreads, 1) oz_gram_kernel(const OzGram
       tc::mbar_init(&empty[st], 1);
     }
     tc::mbar_init(tmem_full, 1);
-    tc::mbar_init(tmem_empty, 4);
+    tc::mbar_init(tmem_empty, 8);
     *err = 0;
     tc::fence_barrier_init();
   }
-  for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) {
-    acc_hi[e] = 0;
-    acc_lo[e] = 0;
-  }
+  for (int e = threadIdx.x; e < 3 * 64 * 64; e += blockDim.x) acc_hi[e] = 0;
   if (warp == 1) tc::tmem_alloc(tmem_slot, kOzLevels * kOzBN);
   tc::fence_before_sync();
   __syncthreads();
@@ -725,7 +730,7 @@ __global__ void __launch_bounds__(kOzGramThreads, 1) oz_gram_kernel(const OzGram
         }
         tc::mbar_expect_tx(&full[st], (uint32_t)(kOzSlices * kOzPlaneTile));
         for (int sl = 0; sl < kOzSlices; ++sl)
-          tc::tma_load_2d(stage[st] + sl * kOzPlaneTile, &maps[J.map[sl]], &full[st], kb * kOzBK, 0);
+          tc::tma_load_2d(stage[st] + oz_gram_pos(sl) * kOzPlaneTile, &maps[J.map[sl]], &full[st], kb * kOzBK, 0);
         issued = kb + 1;
       }
       // drain: every copy issued has landed before the CTA tears down
@@ -750,19 +755,21 @@ __global__ void __launch_bounds__(kOzGramThreads, 1) oz_gram_kernel(const OzGram
           break;
         }
         tc::fence_after_sync();
-        // plane descriptors once per k-block (a 16-deep k step adds 2 to the address field)
+        // plane descriptors once per k-block (a 16-deep k step adds 2 to the address field); the
+        // 128-row operand of plane s <= 3 starts at its tile and runs on into plane s + 4's
         uint64_t dP[kOzSlices];
 #pragma unroll
-        for (int p = 0; p < kOzSlices; ++p) dP[p] = tc::sw128_kmajor_desc(tc::smem_u32(stage[st] + p * kOzPlaneTile));
+        for (int p = 0; p < kOzSlices; ++p)
+          dP[p] = tc::sw128_kmajor_desc(tc::smem_u32(stage[st] + oz_gram_pos(p) * kOzPlaneTile));
 #pragma unroll
-        for (int acc = 0; acc < kOzLevels; ++acc) {
-          const uint32_t d = tmem + (uint32_t)(acc * kOzBN);
+        for (int blk = 0; blk < kOzLevels; ++blk) {
+          const uint32_t d = tmem + (uint32_t)(blk * kOzBN);
 #pragma unroll
-          for (int sa = 0; sa <= acc; ++sa) {
+          for (int sa = 0; sa <= blk && sa < 4; ++sa) {
 #pragma unroll
             for (int k = 0; k < kOzBK / 16; ++k) {
               const uint32_t accumulate = (!first || sa > 0 || k > 0) ? 1u : 0u;
-              tc::mma_bf16(d, dP[sa] + 2 * k, dP[acc - sa] + 2 * k, idesc, accumulate);
+              tc::mma_bf16(d, dP[sa] + 2 * k, dP[blk - sa] + 2 * k, idesc, accumulate);
             }
           }
         }
@@ -772,11 +779,13 @@ __global__ void __launch_bounds__(kOzGramThreads, 1) oz_gram_kernel(const OzGram
       // the last group's products have completed before teardown
       if (!*err && !tc::mbar_wait(tmem_full, (ngroups - 1) & 1, wait_cycles)) *err = 1;
     }
-  } else if (warp >= 4 && (warp & 3) < 2) {
-    // warps 4, 5 (columns 0..31) and 8, 9 (columns 32..63): TMEM lanes 0..63 (the rows of G)
+  } else {
+    // warps 4, 5, 8, 9: TMEM lanes 0..63, blocks 0..7; warps 2, 3, 6, 7: lanes 64..127, blocks 0..3.
+    // Warps 2..5 take columns 0..31, warps 6..9 columns 32..63.
     const int q = warp & 3;
-    const int row = 32 * q + lane;
-    const int cb = warp >= 8 ? 32 : 0;
+    const bool upper = q >= 2;
+    const int row = 32 * (q & 1) + lane;   // the row of G (column of X) this lane holds
+    const int cb = warp >= 6 ? 32 : 0;
     for (int g = 0; g < ngroups; ++g) {
       bool ok = tc::mbar_wait(tmem_full, g & 1, wait_cycles);
       ok = __all_sync(0xffffffffu, ok) && !*err;
@@ -785,23 +794,36 @@ __global__ void __launch_bounds__(kOzGramThreads, 1) oz_gram_kernel(const OzGram
         break;
       }
       tc::fence_after_sync();
+      const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16);
       for (int c0 = cb; c0 < cb + 32 && c0 < J.b; c0 += 8) {
-        uint32_t v[kOzLevels][8];
+        if (!upper) {
+          uint32_t v[kOzLevels][8];
 #pragma unroll
-        for (int acc = 0; acc < kOzLevels; ++acc)
-          tc::tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * kOzBN + c0), v[acc]);
-        tc::tmem_ld_wait();
+          for (int blk = 0; blk < kOzLevels; ++blk) tc::tmem_ld8(tl + (uint32_t)(blk * kOzBN + c0), v[blk]);
+          tc::tmem_ld_wait();
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          long long hi64 = 0, lo64 = 0;
+          for (int j = 0; j < 8; ++j) {
+            // exact integers below 2^24: adjacent levels pair in 32 bits, then hi = p0 2^14 + p1,
+            // lo = p2 2^14 + p3 (sum_L A_L 2^(49 - 7 L) = hi 2^28 + lo)
+            int p[4];
 #pragma unroll
-          for (int acc = 0; acc < 4; ++acc)
-            hi64 = (hi64 << 7) + (long long)__float2int_rn(__uint_as_float(v[acc][j]));
+            for (int i = 0; i < 4; ++i)
+              p[i] = __float2int_rn(__uint_as_float(v[2 * i][j])) * 128 + __float2int_rn(__uint_as_float(v[2 * i + 1][j]));
+            acc_hi[(c0 + j) * 64 + row] += (long long)p[0] * 16384 + p[1];
+            acc_lo[(c0 + j) * 64 + row] += (long long)p[2] * 16384 + p[3];
+          }
+        } else {
+          // block L - 4 of these lanes holds level L = 4..7 of the pairs s >= 4
+          uint32_t v[4][8];
 #pragma unroll
-          for (int acc = 4; acc < kOzLevels; ++acc)
-            lo64 = (lo64 << 7) + (long long)__float2int_rn(__uint_as_float(v[acc][j]));
-          acc_hi[(c0 + j) * 64 + row] += hi64;
-          acc_lo[(c0 + j) * 64 + row] += lo64;
+          for (int blk = 0; blk < 4; ++blk) tc::tmem_ld8(tl + (uint32_t)(blk * kOzBN + c0), v[blk]);
+          tc::tmem_ld_wait();
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int p2 = __float2int_rn(__uint_as_float(v[0][j])) * 128 + __float2int_rn(__uint_as_float(v[1][j]));
+            const int p3 = __float2int_rn(__uint_as_float(v[2][j])) * 128 + __float2int_rn(__uint_as_float(v[3][j]));
+            acc_lo2[(c0 + j) * 64 + row] += (long long)p2 * 16384 + p3;
+          }
         }
       }
       tc::fence_before_sync();
@@ -813,13 +835,13 @@ __global__ void __launch_bounds__(kOzGramThreads, 1) oz_gram_kernel(const OzGram
   __syncthreads();
   if (warp == 1) tc::tmem_dealloc(tmem, kOzLevels * kOzBN);
   if (!*err) {
-    // G[i + b j] = (hi 2^28 + lo) 2^(e_i + e_j - 63), rounded once
+    // G[i + b j] = (hi 2^28 + lo + lo2) 2^(e_i + e_j - 63), rounded once
     const int32_t* expo = at<const int32_t>(bases, J.expo);
     double* G = at<double>(bases, J.G);
     const int b = J.b;
     for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
       const int i = e % b, j = e / b;
-      G[e] = oz_compose(acc_hi[j * 64 + i], acc_lo[j * 64 + i], expo[i] + expo[j] - 63);
+      G[e] = oz_compose(acc_hi[j * 64 + i], acc_lo[j * 64 + i] + acc_lo2[j * 64 + i], expo[i] + expo[j] - 63);
     }
   } else if (threadIdx.x == 0) {
     atomicCAS(&status->code, 0, (int)TKS_ETIMEOUT);
