@@ -597,7 +597,7 @@ static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
   int64_t qrreg_rows = 0;
   std::vector<CoreSketchF32Job> cs3;
   std::vector<Chain3Job> ch3;
-  std::vector<Sketch3Job> sk3, sk3f;   // bf16 / float32 core copies in shared memory
+  std::vector<Sketch3Job> sk3, sk3f;   // terms whose CTAs fit one / two per SM
   std::vector<Sketch4Job> sk4;         // order-4 Khatri-Rao terms, one CTA each
   size_t sk4_smem = 0;
   double sk4_flops = 0.0;
@@ -675,17 +675,17 @@ static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
           }
           j.s = h.s[0];
           j.alpha = (float)h.alpha[k];
-          const double fl = 2.0 * h.s[0] * (2.0 * r[0] * r[1] * r[2] + 2.0 * r[0] * r[1] + (double)r[1] * r[2]);
-          // float32 core copies when two CTAs per SM still fit, else bf16 copies
-          const bool f32_copy = sketch3_fits_f32(r);
-          j.r2p = sketch3_stride(r, f32_copy);
-          if (f32_copy) {
+          // three contractions of the core with a Khatri-Rao factor, and the factors' entries
+          const double fl = 2.0 * h.s[0] * (3.0 * r[0] * r[1] * r[2]) +
+                            (double)h.s[0] * ((double)r[0] * r[1] + (double)r[0] * r[2] + (double)r[1] * r[2]);
+          // two launches: the terms whose CTAs fit two per SM, and the rest
+          if (sketch3_two_per_sm(r)) {
             sk3f.push_back(j);
-            sk3f_smem = std::max(sk3f_smem, sketch3_smem_bytes(r, true));
+            sk3f_smem = std::max(sk3f_smem, sketch3_smem_bytes(r));
             sk3f_flops += fl;
           } else {
             sk3.push_back(j);
-            sk3_smem = std::max(sk3_smem, sketch3_smem_bytes(r, false));
+            sk3_smem = std::max(sk3_smem, sketch3_smem_bytes(r));
             sk3_flops += fl;
           }
           continue;
@@ -1077,11 +1077,11 @@ static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
     plan->st_sketch.back().smem = sk4_smem;
   }
   if (!sk3f.empty()) {
-    plan->push(plan->st_sketch, S_SK3F, sk3f, (int64_t)sk3f.size(), "a3:sketch3[f32]", sk3f_flops, 0.0);
+    plan->push(plan->st_sketch, S_SK3F, sk3f, (int64_t)sk3f.size(), "a3:sketch3[tc]", sk3f_flops, 0.0);
     plan->st_sketch.back().smem = sk3f_smem;
   }
   if (!sk3.empty()) {
-    plan->push(plan->st_sketch, S_SK3, sk3, (int64_t)sk3.size(), "a3:sketch3b[f32]", sk3_flops, 0.0);
+    plan->push(plan->st_sketch, S_SK3, sk3, (int64_t)sk3.size(), "a3:sketch3b[tc]", sk3_flops, 0.0);
     plan->st_sketch.back().smem = sk3_smem;
   }
   plan->push_tc(plan->st_sketch, tcY, "a4:Y=Ucat.Vcat[tc]");
@@ -2576,13 +2576,13 @@ tks_status run_steps(tks_plan* plan, const std::vector<Step>& steps, const Bases
         launch_chain3(static_cast<const Chain3Job*>(table), s.njobs, s.smem, bases, stream);
         break;
       case S_SK3:
-        launch_sketch3(static_cast<const Sketch3Job*>(table), s.njobs, s.smem, false, bases, stream);
+        launch_sketch3(static_cast<const Sketch3Job*>(table), s.njobs, s.smem, bases, plan->status, stream);
         break;
       case S_SK4:
         launch_sketch4(static_cast<const Sketch4Job*>(table), s.njobs, s.smem, bases, stream);
         break;
       case S_SK3F:
-        launch_sketch3(static_cast<const Sketch3Job*>(table), s.njobs, s.smem, true, bases, stream);
+        launch_sketch3(static_cast<const Sketch3Job*>(table), s.njobs, s.smem, bases, plan->status, stream);
         break;
       case S_PROJ3:
         launch_proj3(static_cast<const Proj3Job*>(table), s.njobs, false, bases, plan->status, stream);

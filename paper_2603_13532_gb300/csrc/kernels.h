@@ -58,13 +58,12 @@ int ttm_rows_tiles(int64_t rows);
 bool ttm_rows_fits(int b, int rmax);
 cudaError_t prepare_ttm_rows();
 void launch_ttm_rows(const TtmJob* jobs, int njobs, int total_tiles, const Bases& bases, cudaStream_t stream);
-// Khatri-Rao core sketches of order-3 terms, one CTA per term.
-// f32_core: the core copies in shared memory are float32 (faster, twice the shared memory).
-size_t sketch3_smem_bytes(const int r[3], bool f32_core);
-bool sketch3_fits_f32(const int r[3]);   // float32 core copies with two CTAs per SM
-int sketch3_stride(const int r[3], bool f32_core);   // Sketch3Job::r2p
+// Khatri-Rao core sketches of order-3 terms on the tensor cores, one CTA per term: the dynamic
+// shared memory of a term, and whether two such CTAs fit one SM.
+size_t sketch3_smem_bytes(const int r[3]);
+bool sketch3_two_per_sm(const int r[3]);
 cudaError_t prepare_sketch3();
-void launch_sketch3(const Sketch3Job* jobs, int njobs, size_t smem, bool f32_core, const Bases& bases,
+void launch_sketch3(const Sketch3Job* jobs, int njobs, size_t smem, const Bases& bases, Status* status,
                     cudaStream_t stream);
 // Khatri-Rao core sketches of order-4 terms, one CTA per term: the core slice kc (mode-1 indices per
 // pass) that fits budget_bytes of shared memory, and the dynamic shared memory of a job.

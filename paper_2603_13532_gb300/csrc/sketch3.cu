@@ -1,253 +1,298 @@
-// Khatri-Rao core sketches of an order-3 term, all three modes in one CTA (mixed-precision path).
+// Khatri-Rao core sketches of an order-3 term with the tcgen05 tensor cores (mixed-precision path).
 //
-// Alg. 4 (KRPSum-Tucker), Sec. 3.1.1: with M_m = U_k^(m)T Omega_m (r_m x s) the sketch of mode n
-// is V_kn = G_k,(n) (M_j2 (.) M_j1) (r_n x s), i.e. column c is G_k contracted with column c of
-// the two other M's.  One CTA per term loads the core once and forms
-//   Z[i0, i1, c]  = sum_i2 G[i0, i1, i2] M_2[i2, c]
-//   V_0[i0, c]    = sum_i1 Z[i0, i1, c] M_1[i1, c]          V_1[i1, c] = sum_i0 Z[i0, i1, c] M_0[i0, c]
-//   V_2[i2, c]    = sum_i1 M_1[i1, c] sum_i0 G[i0, i1, i2] M_0[i0, c]
-// so modes 0 and 1 share the contraction over i2 (4 r0 r1 r2 s flops per term instead of 6).
-// Thread (group g, column c): c < s <= 64 owns one sketch column; the four groups split i1 (first
-// pass) and i2 (second pass).  Contractions run along the contiguous index of a zero-padded copy
-// of the core in shared memory (i2 fastest for the first pass, i0 fastest for the second), four
-// bf16 values per 8-byte load, against the thread's column of M_2 or M_0 held in registers.
+// Alg. 4 (KRPSum-Tucker), Sec. 3.1.1: with M_m = U_k^(m)T Omega_m (r_m x s) the sketch of mode n is
+// V_kn = G_k,(n) (M_l (.) M_j) (r_n x s), {j, l} the other two modes: column c of V_kn is the core
+// contracted with column c of M_j and of M_l.  One CTA per term computes it in two stages per mode:
+//   Z[(i_n, i_j), c] = sum_{i_l} G[i_n, i_j, i_l] M_l[i_l, c]        (tensor cores)
+//   V_kn[i_n, c]     = sum_{i_j} Z[(i_n, i_j), c] M_j[i_j, c]         (CUDA cores, per column c)
+// with (j, l) = (1, 2), (0, 2), (0, 1) for n = 0, 1, 2.  The first stage is a product with M = 128
+// rows (i_n, i_j) per tile (i_n padded to a power of two P, row = i_n + P (i_j - i_j0)), N = 64
+// columns c and K = r_l (padded to 16 or 32): A is the core, exact in bfloat16, gathered from a copy
+// of the core in shared memory ordered (i_n, i_j, i_l); B is M_l^T split exactly into three bf16
+// planes (hi + mid + lo = the float32 value), so the three plane products reproduce the float32
+// contraction to float32 rounding.  One elected thread issues them into one of two TMEM
+// accumulators of 64 columns; while the next tile's A is gathered, all eight warps read the last
+// accumulator back (warp w: TMEM lanes 32 (w % 4) .., columns 32 (w / 4) ..) and add Z M_j into
+// per-thread sums for their row's i_n, which are reduced across rows through shared memory at the
+// end of the mode and written, scaled by alpha_k, as the three bf16 planes of V_kn.  Every wait is
+// bounded: on a timeout the kernel records TKS_ETIMEOUT, waits (bounded) for its products in flight,
+// frees TMEM and returns.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
-#include "bf16.cuh"
 #include "fastdiv.cuh"
 #include "kernels.h"
+#include "tc.cuh"
 
 namespace tks {
 
 namespace {
 
-constexpr int kCols = 64;       // sketch columns per CTA (s <= 64)
-constexpr int kGroups = 4;      // thread groups splitting i1 / i2
-constexpr int kMaxR = kSketch3MaxRank;
-constexpr int kQuads = kMaxR / 4;
-constexpr int kThreads = kCols * kGroups;
-constexpr int kBatch = 8;       // core elements loaded per thread before they are stored
+constexpr int kThreads = 256;
+constexpr int kCols = 64;                   // sketch columns (s <= 64): N of the products
+constexpr int kMaxR = kSketch3MaxRank;      // 32
+constexpr int kRows = 128;                  // M of the products
+// K-major operand tiles without swizzle: 8-row x 16-byte core matrices; the k blocks of a row group
+// kLbo bytes apart, row groups kp / 8 * kLbo bytes apart (kp = 16 or 32).
+constexpr int kLbo = 128;
+constexpr int kATile = kRows * kMaxR * 2;   // 8 KB: 128 rows x 32 k
+constexpr int kBPlane = kCols * kMaxR * 2;  // 4 KB: 64 rows x 32 k
+constexpr int kRedLd = kCols + 1;           // row stride (floats) of the reduction buffer
+// Layout: M_0..M_2 ([m][i][c] float32, zero outside i < r_m, c < s), two A stages, three B planes,
+// then the core copy of the current mode, which the end-of-mode reduction ([row][c]) overwrites.
+constexpr int kMOff = 0;
+constexpr int kAOff = kMOff + 3 * kMaxR * kCols * (int)sizeof(float);
+constexpr int kBOff = kAOff + 2 * kATile;
+constexpr int kGOff = kBOff + 3 * kBPlane;
+constexpr int kRedBytes = kRows * kRedLd * (int)sizeof(float);
+constexpr int kTmemCols = 128;
+constexpr long long kWaitCycles = 4000000000LL;   // about 2 s at 2 GHz
 
-__device__ __forceinline__ float lo_bf16(uint32_t w) { return __uint_as_float(w << 16); }
-__device__ __forceinline__ float hi_bf16(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
-
-// four consecutive core values starting at a 4-aligned index
-__device__ __forceinline__ float4 load4(const uint16_t* p) {
-  const uint2 pk = *reinterpret_cast<const uint2*>(p);
-  return make_float4(lo_bf16(pk.x), hi_bf16(pk.x), lo_bf16(pk.y), hi_bf16(pk.y));
-}
-__device__ __forceinline__ float4 load4(const float* p) { return *reinterpret_cast<const float4*>(p); }
-__device__ __forceinline__ uint16_t to_core(uint16_t h, uint16_t) { return h; }
-__device__ __forceinline__ float to_core(uint16_t h, float) { return __uint_as_float((uint32_t)h << 16); }
-
-constexpr size_t kF32Smem = 110 * 1024;   // largest float32-core CTA (two per SM)
-
-size_t smem_for(int r0, int r1, int r2, int r2p, bool f32) {
-  const size_t r0p = (r0 + 3) & ~3;
-  const size_t g = (size_t)r2p * r0 * r1 > r0p * r1 * r2 ? (size_t)r2p * r0 * r1 : r0p * r1 * r2;
-  return sizeof(float) * (2 + kGroups) * kMaxR * kCols + (f32 ? 4 : 2) * g;
+__device__ __forceinline__ int tile_offset(int row, int k, int kp) {
+  return (row >> 3) * (kp / 8) * kLbo + (k >> 3) * kLbo + (row & 7) * 16 + (k & 7) * 2;
 }
 
-// Row stride of the first-pass core copy (i2 fastest): a multiple of 4 for the 16-byte reads.
-// Float32 copies take 4 mod 8 where that still fits two CTAs per SM, so that the staging stores
-// of consecutive i0 (r2p floats apart) are 4-way bank conflicts instead of up to 32-way (r2p = 32);
-// the bf16 launch keeps the plain stride (its shared memory is that of its largest term).
-int pass1_stride(int r0, int r1, int r2, bool f32) {
-  const int p = (r2 + 3) & ~3;
-  if (!f32 || (p & 7) != 0) return p;
-  return smem_for(r0, r1, r2, p + 4, true) <= kF32Smem ? p + 4 : p;
+__device__ __forceinline__ uint32_t pack2(uint16_t lo, uint16_t hi) { return (uint32_t)lo | ((uint32_t)hi << 16); }
+
+// v = hi + mid + lo exactly, each part a bfloat16 (returned in the upper 16 bits): hi is v truncated
+// to its leading 8 significant bits, mid the same of the remainder, lo the rest (at most 8
+// significant bits).  Masks and exact float32 subtractions: no conversion instructions.
+__device__ __forceinline__ void split3_exact(float v, uint32_t& u0, uint32_t& u1, uint32_t& u2) {
+  u0 = __float_as_uint(v) & 0xffff0000u;
+  const float r1 = v - __uint_as_float(u0);
+  u1 = __float_as_uint(r1) & 0xffff0000u;
+  u2 = __float_as_uint(r1 - __uint_as_float(u1));
 }
 
-__device__ __forceinline__ void store_planes(const Bases& bases, const Operand* planes, int64_t off, float v) {
-  uint16_t h0, h1, h2;
-  split3(v, h0, h1, h2);
-  at<uint16_t>(bases, planes[0])[off] = h0;
-  at<uint16_t>(bases, planes[1])[off] = h1;
-  at<uint16_t>(bases, planes[2])[off] = h2;
-}
-
-// CoreT: the element type of the core copies in shared memory (float: converted once while
-// staging, so the contractions load 16 bytes per four values; bf16: half the shared memory).
-template <typename CoreT>
-__global__ void __launch_bounds__(kThreads) sketch3_term_kernel(const Sketch3Job* __restrict__ jobs, Bases bases) {
-  extern __shared__ __align__(16) float s3s[];
+__global__ void __launch_bounds__(kThreads) sketch3_tc_kernel(const Sketch3Job* __restrict__ jobs, Bases bases,
+                                                              Status* status) {
+  extern __shared__ __align__(16) unsigned char sk_smem[];
+  __shared__ uint64_t full[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int err;
   const Sketch3Job& J = jobs[blockIdx.x];
-  const int r0 = J.r[0], r1 = J.r[1], r2 = J.r[2], s = J.s;
-  const int r0p = (r0 + 3) & ~3, r2p = J.r2p;
-  const int tid = threadIdx.x, c = tid % kCols, grp = tid / kCols;
-  const bool live = c < s;
-  float* M0s = s3s;                                   // [i0][c]
-  float* M1s = M0s + kMaxR * kCols;                   // [i1][c]
-  float* V0p = M1s + kMaxR * kCols;                   // [grp][i0][c], partial sums of V_0
-  CoreT* Gb = reinterpret_cast<CoreT*>(V0p + kGroups * kMaxR * kCols);
+  const int r0 = J.r[0], r1 = J.r[1], r2 = J.r[2];
+  const int s = J.s;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  float* Ms = reinterpret_cast<float*>(sk_smem + kMOff);
+  unsigned char* Ast = sk_smem + kAOff;
+  unsigned char* Bp = sk_smem + kBOff;
+  uint16_t* Gt = reinterpret_cast<uint16_t*>(sk_smem + kGOff);
+  float* red = reinterpret_cast<float*>(sk_smem + kGOff);
   const uint16_t* G = at<uint16_t>(bases, J.core);
-  const float* Mg0 = at<float>(bases, J.M[0]) + J.roff[0];
-  const float* Mg1 = at<float>(bases, J.M[1]) + J.roff[1];
-  const float* Mg2 = at<float>(bases, J.M[2]) + J.roff[2];
-  const int tot = r0 * r1 * r2;   // <= 2^15: the index quotients below are SmallDiv's
-  const SmallDiv dr0(r0), dr1(r1);
 
-  for (int e = tid; e < r0 * kCols; e += kThreads) {
-    const int cc = dr0.quo(e), i = e - cc * r0;
-    M0s[i * kCols + cc] = cc < s ? Mg0[i + (int64_t)J.R[0] * cc] : 0.f;
+  if (tid == 0) {
+    tc::mbar_init(&full[0], 1);
+    tc::mbar_init(&full[1], 1);
+    err = 0;
+    tc::fence_barrier_init();
   }
-  for (int e = tid; e < r1 * kCols; e += kThreads) {
-    const int cc = dr1.quo(e), i = e - cc * r1;
-    M1s[i * kCols + cc] = cc < s ? Mg1[i + (int64_t)J.R[1] * cc] : 0.f;
-  }
-  // first-pass copy of the core: Gb[i2 + r2p (i0 + r0 i1)], zero for i2 in [r2, r2p)
-  if (r2p > r2) {
-    const SmallDiv dp(r2p - r2);
-    for (int e = tid; e < r0 * r1 * (r2p - r2); e += kThreads) {
-      const int rest = dp.quo(e), pad = e - rest * (r2p - r2);
-      Gb[r2 + pad + r2p * rest] = CoreT(0);
+  if (warp == 0) tc::tmem_alloc(&tmem_slot, kTmemCols);
+  for (int m = 0; m < 3; ++m) {
+    const float* Mg = at<float>(bases, J.M[m]) + J.roff[m];
+    const int rm = m == 0 ? r0 : (m == 1 ? r1 : r2);
+    for (int e = tid; e < kMaxR * kCols; e += kThreads) {
+      const int i = e >> 6, c = e & (kCols - 1);
+      Ms[m * kMaxR * kCols + e] = (i < rm && c < s) ? Mg[i + (int64_t)J.R[m] * c] : 0.f;
     }
   }
-  for (int e0 = 0; e0 < tot; e0 += kBatch * kThreads) {
-    // kBatch independent loads in flight per thread before the scattered shared-memory stores
-    uint16_t v[kBatch];
-#pragma unroll
-    for (int u = 0; u < kBatch; ++u) {
-      const int e = e0 + u * kThreads + tid;
-      v[u] = e < tot ? G[e] : 0;
-    }
-#pragma unroll
-    for (int u = 0; u < kBatch; ++u) {
-      const int e = e0 + u * kThreads + tid;
-      if (e < tot) {
-        const int q = dr0.quo(e), i0 = e - q * r0, i2 = dr1.quo(q), i1 = q - i2 * r1;
-        Gb[i2 + r2p * (i0 + r0 * i1)] = to_core(v[u], CoreT());
-      }
-    }
-  }
-  float m2[kMaxR];
-#pragma unroll
-  for (int i = 0; i < kMaxR; ++i) m2[i] = (i < r2 && live) ? Mg2[i + (int64_t)J.R[2] * c] : 0.f;
+  tc::fence_before_sync();
   __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tmem_slot;
 
-  // pass 1: modes 0 and 1
-  float v0[kMaxR];
+  int g = 0;   // products issued so far (tiles over all modes): buffer g & 1, phase (g >> 1) & 1
+  for (int n = 0; n < 3 && !err; ++n) {
+    const int j = n == 0 ? 1 : 0, l = n == 2 ? 1 : 2;
+    const int rn = n == 0 ? r0 : (n == 1 ? r1 : r2);
+    const int rj = j == 0 ? r0 : r1;
+    const int rl = l == 1 ? r1 : r2;
+    int pb = 0;
+    while ((1 << pb) < rn) ++pb;                 // P = 2^pb >= r_n
+    const int per = kRows >> pb;                 // i_j per tile
+    const int tiles = (rj + per - 1) / per;
+    const int kp = rl <= 16 ? 16 : 32;
+    const float* Mj = Ms + j * kMaxR * kCols;
+    const float* Ml = Ms + l * kMaxR * kCols;
+    const SmallDiv drn(rn), drj(rj);
+    // the core ordered (i_n, i_j, i_l), i_n fastest: Gt[i_n + r_n (i_j + r_j i_l)]
+    {
+      const int tot = r0 * r1 * r2;
+      for (int e0 = 0; e0 < tot; e0 += 4 * kThreads) {
+        uint16_t v[4];
 #pragma unroll
-  for (int i = 0; i < kMaxR; ++i) v0[i] = 0.f;
-  for (int i1 = grp; i1 < r1; i1 += kGroups) {
-    const float m1 = M1s[i1 * kCols + c];
-    float v1 = 0.f;
-#pragma unroll
-    for (int q0 = 0; q0 < kQuads; ++q0) {
-      if (4 * q0 >= r0) continue;
-      float z[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-      for (int q2 = 0; q2 < kQuads; ++q2) {
-        if (4 * q2 >= r2) continue;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          // rows i0 >= r0 of the last quad read the next core fibre (or the padding); their z is unused
-          const int i0 = min(4 * q0 + j, r0 - 1);
-          const float4 gv = load4(Gb + r2p * (i0 + r0 * i1) + 4 * q2);
-          z[j] = fmaf(gv.x, m2[4 * q2], z[j]);
-          z[j] = fmaf(gv.y, m2[4 * q2 + 1], z[j]);
-          z[j] = fmaf(gv.z, m2[4 * q2 + 2], z[j]);
-          z[j] = fmaf(gv.w, m2[4 * q2 + 3], z[j]);
+        for (int u = 0; u < 4; ++u) {
+          const int e = e0 + u * kThreads + tid;
+          v[u] = 0;
+          if (e < tot) {
+            const int rest = drn.quo(e), a = e - rest * rn, c = drj.quo(rest), b = rest - c * rj;   // (i_n, i_j, i_l)
+            int i0, i1, i2;
+            if (n == 0) {
+              i0 = a; i1 = b; i2 = c;
+            } else if (n == 1) {
+              i1 = a; i0 = b; i2 = c;
+            } else {
+              i2 = a; i0 = b; i1 = c;
+            }
+            v[u] = G[i0 + r0 * (i1 + r1 * i2)];
+          }
         }
-      }
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int i0 = 4 * q0 + j;
-        if (i0 < r0) {
-          v0[i0] = fmaf(z[j], m1, v0[i0]);
-          v1 = fmaf(z[j], M0s[i0 * kCols + c], v1);
+        for (int u = 0; u < 4; ++u) {
+          const int e = e0 + u * kThreads + tid;
+          if (e < tot) Gt[e] = v[u];
         }
       }
     }
-    if (live) store_planes(bases, J.V[1], (J.roff[1] + i1) + (int64_t)J.ldv[1] * c, J.alpha * v1);
-  }
+    // B: planes of M_l^T (rows c, k = i_l < kp; zero for k >= r_l), one 8-k block per thread
+    for (int item = tid; item < kCols * (kp / 8); item += kThreads) {
+      const int c = item & (kCols - 1), kb = item >> 6;
+      uint32_t p0[4], p1[4], p2[4];
 #pragma unroll
-  for (int i = 0; i < kMaxR; ++i)
-    if (i < r0) V0p[(grp * kMaxR + i) * kCols + c] = v0[i];
-  __syncthreads();   // pass 1 is done with Gb; the V_0 partials are in place
-  for (int e = tid; e < r0 * kCols; e += kThreads) {
-    const int cc = dr0.quo(e), i = e - cc * r0;   // runs of consecutive rows of one column
-    if (cc < s) {
-      float v = 0.f;
-#pragma unroll
-      for (int g = 0; g < kGroups; ++g) v += V0p[(g * kMaxR + i) * kCols + cc];
-      store_planes(bases, J.V[0], (J.roff[0] + i) + (int64_t)J.ldv[0] * cc, J.alpha * v);
-    }
-  }
-  // second-pass copy: Gb[i0 + r0p (i1 + r1 i2)], zero for i0 in [r0, r0p)
-  if (r0p > r0) {
-    const SmallDiv dp(r0p - r0);
-    for (int e = tid; e < r1 * r2 * (r0p - r0); e += kThreads) {
-      const int rest = dp.quo(e), pad = e - rest * (r0p - r0);
-      Gb[r0 + pad + r0p * rest] = CoreT(0);
-    }
-  }
-  for (int e0 = 0; e0 < tot; e0 += kBatch * kThreads) {
-    uint16_t v[kBatch];
-#pragma unroll
-    for (int u = 0; u < kBatch; ++u) {
-      const int e = e0 + u * kThreads + tid;
-      v[u] = e < tot ? G[e] : 0;
-    }
-#pragma unroll
-    for (int u = 0; u < kBatch; ++u) {
-      const int e = e0 + u * kThreads + tid;
-      if (e < tot) {
-        const int q = dr0.quo(e);
-        Gb[e - q * r0 + r0p * q] = to_core(v[u], CoreT());
+      for (int e = 0; e < 4; ++e) {
+        uint32_t a0, a1, a2, b0, b1, b2;
+        split3_exact(Ml[(8 * kb + 2 * e) * kCols + c], a0, a1, a2);
+        split3_exact(Ml[(8 * kb + 2 * e + 1) * kCols + c], b0, b1, b2);
+        p0[e] = __byte_perm(a0, b0, 0x7632);
+        p1[e] = __byte_perm(a1, b1, 0x7632);
+        p2[e] = __byte_perm(a2, b2, 0x7632);
       }
+      const int off = tile_offset(c, 8 * kb, kp);
+      *reinterpret_cast<uint4*>(Bp + off) = make_uint4(p0[0], p0[1], p0[2], p0[3]);
+      *reinterpret_cast<uint4*>(Bp + kBPlane + off) = make_uint4(p1[0], p1[1], p1[2], p1[3]);
+      *reinterpret_cast<uint4*>(Bp + 2 * kBPlane + off) = make_uint4(p2[0], p2[1], p2[2], p2[3]);
     }
-  }
-  float m0[kMaxR];
+    __syncthreads();   // the core copy is complete before any thread gathers from it
+    // this thread's row of every tile and its 32 columns of the read-back
+    const int q = warp & 3, h = warp >> 2;
+    const int rho = 32 * q + lane;
+    const int jr = rho >> pb;
+    float acc[32];
 #pragma unroll
-  for (int i = 0; i < kMaxR; ++i) m0[i] = (i < r0) ? M0s[i * kCols + c] : 0.f;
-  __syncthreads();
+    for (int cc = 0; cc < 32; ++cc) acc[cc] = 0.f;
 
-  // pass 2: mode 2
-  for (int i2 = grp; i2 < r2; i2 += kGroups) {
-    float acc = 0.f;
-    for (int i1 = 0; i1 < r1; ++i1) {
-      const CoreT* g = Gb + r0p * (i1 + r1 * i2);
-      float y[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int t = 0; t <= tiles; ++t) {
+      if (t < tiles) {
+        // A(t): rows = i_n + P (i_j - per t), k = i_l; zero outside the core
+        unsigned char* A = Ast + (g & 1) * kATile;
+        for (int item = tid; item < kRows * (kp / 8); item += kThreads) {
+          const int row = item & (kRows - 1), kb = item >> 7;
+          const int in = row & ((1 << pb) - 1), ij = per * t + (row >> pb);
+          const bool live = in < rn && ij < rj;
+          const int base = in + rn * ij;
+          uint16_t v[8];
 #pragma unroll
-      for (int q0 = 0; q0 < kQuads; ++q0) {
-        if (4 * q0 >= r0) continue;
-        const float4 gv = load4(g + 4 * q0);
-        y[0] = fmaf(gv.x, m0[4 * q0], y[0]);
-        y[1] = fmaf(gv.y, m0[4 * q0 + 1], y[1]);
-        y[2] = fmaf(gv.z, m0[4 * q0 + 2], y[2]);
-        y[3] = fmaf(gv.w, m0[4 * q0 + 3], y[3]);
+          for (int e = 0; e < 8; ++e) {
+            const int il = 8 * kb + e;
+            const bool ok = live && il < rl;
+            const uint16_t gv = Gt[ok ? base + rn * rj * il : 0];
+            v[e] = ok ? gv : (uint16_t)0;
+          }
+          *reinterpret_cast<uint4*>(A + tile_offset(row, 8 * kb, kp)) =
+              make_uint4(pack2(v[0], v[1]), pack2(v[2], v[3]), pack2(v[4], v[5]), pack2(v[6], v[7]));
+        }
+        tc::fence_proxy_async_smem();
       }
-      acc = fmaf((y[0] + y[1]) + (y[2] + y[3]), M1s[i1 * kCols + c], acc);
+      tc::fence_before_sync();
+      __syncthreads();   // A(t) is complete; every read of the accumulator MMA(t) reuses has finished
+      tc::fence_after_sync();
+      if (err) break;
+      if (t < tiles && tid == 0) {
+        const uint32_t idesc = tc::idesc_bf16_f32(kRows, kCols);
+        const uint32_t d = tmem + (uint32_t)(kCols * (g & 1));
+        const uint32_t a0 = tc::smem_u32(Ast + (g & 1) * kATile), b0 = tc::smem_u32(Bp);
+        const uint32_t sbo = (uint32_t)(kp / 8 * kLbo);
+        for (int ks = 0; ks < kp / 16; ++ks) {
+          const uint64_t da = tc::plain_kmajor_desc(a0 + 2 * kLbo * ks, kLbo, sbo);
+#pragma unroll
+          for (int p = 0; p < 3; ++p) {
+            const uint64_t db = tc::plain_kmajor_desc(b0 + p * kBPlane + 2 * kLbo * ks, kLbo, sbo);
+            tc::mma_bf16(d, da, db, idesc, (ks > 0 || p > 0) ? 1u : 0u);
+          }
+        }
+        tc::mma_commit(&full[g & 1]);
+      }
+      if (t >= 1) {
+        // read back Z(t - 1) and add Z M_j into this row's sums
+        const int gp = g - 1;
+        const bool ok = tc::mbar_wait(&full[gp & 1], (gp >> 1) & 1, kWaitCycles);
+        if (!__all_sync(0xffffffffu, ok)) {
+          if (lane == 0) err = 1;
+        } else {
+          tc::fence_after_sync();
+          uint32_t v[32];
+          tc::tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(kCols * (gp & 1) + 32 * h), v);
+          tc::tmem_ld_wait();
+          const int ij = per * (t - 1) + jr;
+          if (ij < rj) {
+            const float4* mj = reinterpret_cast<const float4*>(Mj + ij * kCols + 32 * h);
+#pragma unroll
+            for (int c4 = 0; c4 < 8; ++c4) {
+              const float4 w = mj[c4];
+              acc[4 * c4] = fmaf(__uint_as_float(v[4 * c4]), w.x, acc[4 * c4]);
+              acc[4 * c4 + 1] = fmaf(__uint_as_float(v[4 * c4 + 1]), w.y, acc[4 * c4 + 1]);
+              acc[4 * c4 + 2] = fmaf(__uint_as_float(v[4 * c4 + 2]), w.z, acc[4 * c4 + 2]);
+              acc[4 * c4 + 3] = fmaf(__uint_as_float(v[4 * c4 + 3]), w.w, acc[4 * c4 + 3]);
+            }
+          }
+        }
+      }
+      if (t < tiles) ++g;
     }
-    if (live) store_planes(bases, J.V[2], (J.roff[2] + i2) + (int64_t)J.ldv[2] * c, J.alpha * acc);
+    __syncthreads();   // a timeout recorded by the last read-back is seen by every thread
+    if (err) break;
+    // V_kn[i_n, c] = alpha sum over the rows i_n + P m of their sums (the core copy is no longer read)
+#pragma unroll
+    for (int cc = 0; cc < 32; ++cc) red[rho * kRedLd + 32 * h + cc] = acc[cc];
+    __syncthreads();
+    {
+      uint16_t* P0 = at<uint16_t>(bases, J.V[n][0]);
+      uint16_t* P1 = at<uint16_t>(bases, J.V[n][1]);
+      uint16_t* P2 = at<uint16_t>(bases, J.V[n][2]);
+      const int groups = kRows >> pb;
+      for (int e = tid; e < rn * kCols; e += kThreads) {
+        const int c = drn.quo(e), in = e - c * rn;   // consecutive threads: consecutive i_n of a column
+        if (c < s) {
+          float sum = 0.f;
+          for (int m = 0; m < groups; ++m) sum += red[(in + (m << pb)) * kRedLd + c];
+          uint32_t u0, u1, u2;
+          split3_exact(J.alpha * sum, u0, u1, u2);
+          const int64_t o = J.roff[n] + in + (int64_t)J.ldv[n] * c;
+          P0[o] = (uint16_t)(u0 >> 16);
+          P1[o] = (uint16_t)(u1 >> 16);
+          P2[o] = (uint16_t)(u2 >> 16);
+        }
+      }
+    }
+    __syncthreads();   // the reduction buffer is read before the next mode's core copy
   }
+
+  tc::fence_before_sync();
+  __syncthreads();
+  // after a timeout, the products issued last complete before TMEM is freed (bounded)
+  if (err && g > 0 && tid == 0) tc::mbar_wait(&full[(g - 1) & 1], ((g - 1) >> 1) & 1, kWaitCycles);
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
+  if (tid == 0 && err && status) atomicCAS(&status->code, 0, (int)TKS_ETIMEOUT);
 }
 
 }  // namespace
 
-size_t sketch3_smem_bytes(const int r[3], bool f32_core) {
-  return smem_for(r[0], r[1], r[2], pass1_stride(r[0], r[1], r[2], f32_core), f32_core);
+size_t sketch3_smem_bytes(const int r[3]) {
+  const size_t core = ((size_t)r[0] * r[1] * r[2] * 2 + 15) & ~(size_t)15;
+  return (size_t)kGOff + (core > (size_t)kRedBytes ? core : (size_t)kRedBytes);
 }
 
-int sketch3_stride(const int r[3], bool f32_core) { return pass1_stride(r[0], r[1], r[2], f32_core); }
-
-bool sketch3_fits_f32(const int r[3]) { return smem_for(r[0], r[1], r[2], (r[2] + 3) & ~3, true) <= kF32Smem; }
+bool sketch3_two_per_sm(const int r[3]) { return sketch3_smem_bytes(r) <= 110 * 1024; }
 
 cudaError_t prepare_sketch3() {
-  cudaError_t e =
-      cudaFuncSetAttribute(sketch3_term_kernel<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(sketch3_term_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  return cudaFuncSetAttribute(sketch3_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(kGOff + kMaxR * kMaxR * kMaxR * 2));
 }
 
-void launch_sketch3(const Sketch3Job* jobs, int njobs, size_t smem, bool f32_core, const Bases& bases,
+void launch_sketch3(const Sketch3Job* jobs, int njobs, size_t smem, const Bases& bases, Status* status,
                     cudaStream_t stream) {
-  if (f32_core)
-    sketch3_term_kernel<float><<<njobs, kThreads, smem, stream>>>(jobs, bases);
-  else
-    sketch3_term_kernel<uint16_t><<<njobs, kThreads, smem, stream>>>(jobs, bases);
+  sketch3_tc_kernel<<<njobs, kThreads, smem, stream>>>(jobs, bases, status);
 }
 
 }  // namespace tks

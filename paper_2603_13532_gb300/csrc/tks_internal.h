@@ -144,8 +144,7 @@ struct Sketch3Job {
   int32_t r[3], roff[3], R[3], ldv[3];
   int32_t s;
   float alpha;
-  int32_t r2p;           // row stride of the first-pass core copy (elements, a multiple of 4)
-  int32_t pad;
+  int32_t pad[2];
 };
 
 // Khatri-Rao core sketches of all four modes of one order-4 term (stage b, float32), one CTA per
