@@ -8,7 +8,8 @@
 // with (j, l) = (1, 2), (0, 2), (0, 1) for n = 0, 1, 2.  The first stage is a product with M = 128
 // rows (i_n, i_j) per tile (i_n padded to a power of two P, row = i_n + P (i_j - i_j0)), N = 64
 // columns c and K = r_l (padded to 16 or 32): A is the core, exact in bfloat16, gathered from a copy
-// of the core in shared memory ordered (i_n, i_j, i_l); B is M_l^T split exactly into three bf16
+// of the core in shared memory ordered (i_n, i_j, i_l) (the stored order for n = 0; for n = 1, 2 a
+// transposed copy with an odd row stride, made from the stored one); B is M_l^T split exactly into three bf16
 // planes (hi + mid + lo = the float32 value), so the three plane products reproduce the float32
 // contraction to float32 rounding.  One elected thread issues them into one of two TMEM
 // accumulators of 64 columns; while the next tile's A is gathered, all eight warps read the last
@@ -39,7 +40,8 @@ constexpr int kATile = kRows * kMaxR * 2;   // 8 KB: 128 rows x 32 k
 constexpr int kBPlane = kCols * kMaxR * 2;  // 4 KB: 64 rows x 32 k
 constexpr int kRedLd = kCols + 1;           // row stride (floats) of the reduction buffer
 // Layout: M_0..M_2 ([m][i][c] float32, zero outside i < r_m, c < s), two A stages, three B planes,
-// then the core copy of the current mode, which the end-of-mode reduction ([row][c]) overwrites.
+// the core as stored, then the transposed copy of the current mode, which the end-of-mode reduction
+// ([row][c]) overwrites.
 constexpr int kMOff = 0;
 constexpr int kAOff = kMOff + 3 * kMaxR * kCols * (int)sizeof(float);
 constexpr int kBOff = kAOff + 2 * kATile;
@@ -77,8 +79,11 @@ __global__ void __launch_bounds__(kThreads) sketch3_tc_kernel(const Sketch3Job* 
   float* Ms = reinterpret_cast<float*>(sk_smem + kMOff);
   unsigned char* Ast = sk_smem + kAOff;
   unsigned char* Bp = sk_smem + kBOff;
-  uint16_t* Gt = reinterpret_cast<uint16_t*>(sk_smem + kGOff);
-  float* red = reinterpret_cast<float*>(sk_smem + kGOff);
+  const int tot = r0 * r1 * r2;
+  const int tpad = (2 * tot + 15) & ~15;
+  uint16_t* Gs = reinterpret_cast<uint16_t*>(sk_smem + kGOff);
+  uint16_t* Gx = reinterpret_cast<uint16_t*>(sk_smem + kGOff + tpad);
+  float* red = reinterpret_cast<float*>(sk_smem + kGOff + tpad);
   const uint16_t* G = at<uint16_t>(bases, J.core);
 
   if (tid == 0) {
@@ -94,6 +99,19 @@ __global__ void __launch_bounds__(kThreads) sketch3_tc_kernel(const Sketch3Job* 
     for (int e = tid; e < kMaxR * kCols; e += kThreads) {
       const int i = e >> 6, c = e & (kCols - 1);
       Ms[m * kMaxR * kCols + e] = (i < rm && c < s) ? Mg[i + (int64_t)J.R[m] * c] : 0.f;
+    }
+  }
+  for (int e0 = 0; e0 < tot; e0 += 8 * kThreads) {
+    uint16_t v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * kThreads + tid;
+      v[u] = e < tot ? G[e] : (uint16_t)0;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * kThreads + tid;
+      if (e < tot) Gs[e] = v[u];
     }
   }
   tc::fence_before_sync();
@@ -114,35 +132,24 @@ __global__ void __launch_bounds__(kThreads) sketch3_tc_kernel(const Sketch3Job* 
     const int kp = rl <= 16 ? 16 : 32;
     const float* Mj = Ms + j * kMaxR * kCols;
     const float* Ml = Ms + l * kMaxR * kCols;
-    const SmallDiv drn(rn), drj(rj);
-    // the core ordered (i_n, i_j, i_l), i_n fastest: Gt[i_n + r_n (i_j + r_j i_l)]
-    {
-      const int tot = r0 * r1 * r2;
-      for (int e0 = 0; e0 < tot; e0 += 4 * kThreads) {
-        uint16_t v[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int e = e0 + u * kThreads + tid;
-          v[u] = 0;
-          if (e < tot) {
-            const int rest = drn.quo(e), a = e - rest * rn, c = drj.quo(rest), b = rest - c * rj;   // (i_n, i_j, i_l)
-            int i0, i1, i2;
-            if (n == 0) {
-              i0 = a; i1 = b; i2 = c;
-            } else if (n == 1) {
-              i1 = a; i0 = b; i2 = c;
-            } else {
-              i2 = a; i0 = b; i1 = c;
-            }
-            v[u] = G[i0 + r0 * (i1 + r1 * i2)];
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int e = e0 + u * kThreads + tid;
-          if (e < tot) Gt[e] = v[u];
-        }
+    const SmallDiv drn(rn);
+    // the core ordered (i_n, i_j, i_l), i_n fastest: Gt[i_n + ld (i_j + r_j i_l)] -- the stored core
+    // for n = 0 (ld = r_0); for n = 1, 2 a copy with ld = r_n | 1 (odd: the copy's strided stores fall
+    // on distinct banks), made with one thread per (i_j, i_l), whose reads of the stored core
+    // (i_j = i_0 fastest) are consecutive across a warp
+    const uint16_t* Gt = Gs;
+    int ld = r0;
+    if (n > 0) {
+      ld = rn | 1;
+      const int outer = rj * rl;           // o = i_0 + r_0 i_l
+      const int step = n == 1 ? r0 : r0 * r1;   // stored-core stride of i_n
+      for (int o = tid; o < outer; o += kThreads) {
+        const int il = o / r0, i0 = o - il * r0;
+        const uint16_t* src = Gs + i0 + (n == 1 ? r0 * r1 * il : r0 * il);
+        uint16_t* dst = Gx + ld * o;
+        for (int in = 0; in < rn; ++in) dst[in] = src[step * in];
       }
+      Gt = Gx;
     }
     // B: planes of M_l^T (rows c, k = i_l < kp; zero for k >= r_l), one 8-k block per thread
     for (int item = tid; item < kCols * (kp / 8); item += kThreads) {
@@ -162,7 +169,7 @@ __global__ void __launch_bounds__(kThreads) sketch3_tc_kernel(const Sketch3Job* 
       *reinterpret_cast<uint4*>(Bp + kBPlane + off) = make_uint4(p1[0], p1[1], p1[2], p1[3]);
       *reinterpret_cast<uint4*>(Bp + 2 * kBPlane + off) = make_uint4(p2[0], p2[1], p2[2], p2[3]);
     }
-    __syncthreads();   // the core copy is complete before any thread gathers from it
+    __syncthreads();   // the transposed copy is complete before any thread gathers from it
     // this thread's row of every tile and its 32 columns of the read-back
     const int q = warp & 3, h = warp >> 2;
     const int rho = 32 * q + lane;
@@ -179,13 +186,13 @@ __global__ void __launch_bounds__(kThreads) sketch3_tc_kernel(const Sketch3Job* 
           const int row = item & (kRows - 1), kb = item >> 7;
           const int in = row & ((1 << pb) - 1), ij = per * t + (row >> pb);
           const bool live = in < rn && ij < rj;
-          const int base = in + rn * ij;
+          const int base = in + ld * ij;
           uint16_t v[8];
 #pragma unroll
           for (int e = 0; e < 8; ++e) {
             const int il = 8 * kb + e;
             const bool ok = live && il < rl;
-            const uint16_t gv = Gt[ok ? base + rn * rj * il : 0];
+            const uint16_t gv = Gt[ok ? base + ld * rj * il : 0];
             v[e] = ok ? gv : (uint16_t)0;
           }
           *reinterpret_cast<uint4*>(A + tile_offset(row, 8 * kb, kp)) =
@@ -241,7 +248,8 @@ __global__ void __launch_bounds__(kThreads) sketch3_tc_kernel(const Sketch3Job* 
     }
     __syncthreads();   // a timeout recorded by the last read-back is seen by every thread
     if (err) break;
-    // V_kn[i_n, c] = alpha sum over the rows i_n + P m of their sums (the core copy is no longer read)
+    // V_kn[i_n, c] = alpha sum over the rows i_n + P m of their sums (the transposed copy is no
+    // longer read)
 #pragma unroll
     for (int cc = 0; cc < 32; ++cc) red[rho * kRedLd + 32 * h + cc] = acc[cc];
     __syncthreads();
@@ -264,7 +272,7 @@ __global__ void __launch_bounds__(kThreads) sketch3_tc_kernel(const Sketch3Job* 
         }
       }
     }
-    __syncthreads();   // the reduction buffer is read before the next mode's core copy
+    __syncthreads();   // the reduction buffer is read before the next mode's transposed copy
   }
 
   tc::fence_before_sync();
@@ -280,14 +288,22 @@ __global__ void __launch_bounds__(kThreads) sketch3_tc_kernel(const Sketch3Job* 
 
 size_t sketch3_smem_bytes(const int r[3]) {
   const size_t core = ((size_t)r[0] * r[1] * r[2] * 2 + 15) & ~(size_t)15;
-  return (size_t)kGOff + (core > (size_t)kRedBytes ? core : (size_t)kRedBytes);
+  // the transposed copies have rows of r_n | 1 elements
+  size_t copy = 0;
+  for (int n = 1; n < 3; ++n) {
+    const size_t c = (size_t)(r[n] | 1) * (n == 1 ? r[0] * r[2] : r[0] * r[1]) * 2;
+    copy = c > copy ? c : copy;
+  }
+  copy = (copy + 15) & ~(size_t)15;
+  return (size_t)kGOff + core + (copy > (size_t)kRedBytes ? copy : (size_t)kRedBytes);
 }
 
-bool sketch3_two_per_sm(const int r[3]) { return sketch3_smem_bytes(r) <= 110 * 1024; }
+bool sketch3_two_per_sm(const int r[3]) { return sketch3_smem_bytes(r) <= 112 * 1024; }
 
 cudaError_t prepare_sketch3() {
+  const int r[3] = {kMaxR, kMaxR, kMaxR};
   return cudaFuncSetAttribute(sketch3_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)(kGOff + kMaxR * kMaxR * kMaxR * 2));
+                              (int)sketch3_smem_bytes(r));
 }
 
 void launch_sketch3(const Sketch3Job* jobs, int njobs, size_t smem, const Bases& bases, Status* status,
