@@ -515,21 +515,20 @@ FP32_KINDS = {"simt", "core_sketch32", "qr32", "svd32", "tsqr32", "core_sketch3"
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch per problem, from an ncu
-# capture of the same kernel binary, keyed by (workload, launch kind); an entry is dropped when its
-# kernel changes (no current capture: none).
-NCU_TRAFFIC_PER_PROBLEM = {}
+# capture of the same kernel binary on 16 decay512 problems (15.594 MB read + 0.274 MB written),
+# used to scale the measured traffic to the bench launch; only valid for that kernel and workload.
+NCU_TRAFFIC_PER_PROBLEM = {("decay512", "project3"): (15.593984e6 + 0.273920e6) / 16}
 
 
 def project3_tensor_flops(plan, problems):
-    """Algorithmic flops of the fused projection's tensor-core contractions (s2: 2 b0 b1 r_k2 r_k3,
-    s3: 2 b0 b1 b2 r_k3 per term) over the problems that take that kernel (order 3, b2, b3 <= 64,
-    mixed precision)."""
+    """Algorithmic flops of the fused projection's tensor-core contraction (s3: 2 b0 b1 b2 r_k3 per
+    term) over the problems that take that kernel (order 3, b2, b3 <= 64, mixed precision)."""
     total = 0.0
     for p, pi in zip(problems, plan.pinfo):
         b = [pi.basis_cols[m] for m in range(p.order)]
         if p.order != 3 or b[1] > 64 or b[2] > 64:
             continue
-        total += sum(2.0 * b[0] * b[1] * r[1] * r[2] + 2.0 * b[0] * b[1] * b[2] * r[2] for r in p.ranks())
+        total += sum(2.0 * b[0] * b[1] * b[2] * r[2] for r in p.ranks())
     return total
 
 
@@ -539,10 +538,10 @@ def roofline_from_profile(prof, calls, peaks, workload=None, problems=0, tensor_
     FP64 CUDA-core launches are bound by the FP64 pipe, FP32 CUDA-core launches by the FP32 pipe
     (peaks from unit counts and the 2070 MHz clock); tensor-core launches by the tensor pipe or
     HBM, whichever the launch's algorithmic arithmetic intensity puts first (ridge = sustained
-    bf16 peak / HBM bandwidth).  The fused projection runs on two pipes at once: its first
-    contraction on the FP32 pipe and the second and third (`tensor_flops`) on the tensor pipe as six
-    bf16 products of split operands each; its peak is the rate at which the busier of the two pipes
-    would finish the launch's algorithmic flops.
+    bf16 peak / HBM bandwidth).  The fused projection runs on two pipes at once: its first two
+    contractions on the FP32 pipe and the third (`tensor_flops`) on the tensor pipe as six bf16
+    products of split operands; its peak is the rate at which the busier of the two pipes would
+    finish the launch's algorithmic flops.
     """
     total_ms = sum(s["ms"] for s in prof)
     # the dominant kernel: the launch kind with the largest share of the step among those with an
@@ -574,9 +573,9 @@ def roofline_from_profile(prof, calls, peaks, workload=None, problems=0, tensor_
         t_tc = 6.0 * f_tc / (peaks["bf16_tflops_sustained"] * 1e12)
         roof = {"bound": "alu" if t_alu >= t_tc else "tensor", "achieved": top["flops"] / avg_s / 1e12,
                 "peak": top["flops"] / max(t_alu, t_tc) / 1e12, "unit": "TFLOP/s",
-                "peak_source": "two pipes: s1 on the FP32 pipe (derived 152 SMs x 256 flop/clk x 2070 MHz), "
-                               "s2 and s3 as 6 bf16 products each on the tensor pipe (measured bf16 sustained / 6); "
-                               "peak = algorithmic flops / the longer of the two pipe times",
+                "peak_source": "two pipes: s1, s2 on the FP32 pipe (derived 152 SMs x 256 flop/clk x 2070 MHz), "
+                               "s3 as 6 bf16 products on the tensor pipe (measured bf16 sustained / 6); peak = "
+                               "algorithmic flops / the longer of the two pipe times",
                 "tensor_flops_per_launch": f_tc}
     elif kind in FP64_KINDS and top["flops"] > 0:
         roof = {"bound": "alu", "achieved": top["flops"] / avg_s / 1e12, "peak": FP64_PEAK_TFLOPS,

@@ -1099,26 +1099,23 @@ static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
   }
   plan->push_tc(plan->st_project, tcH, "a8:H=Tcat.AT[tc]");
   // fused projections: one table each, the jobs followed by the term records they index
-  auto push_proj = [&](StepKind kind, std::vector<Proj3Job> jobs, const std::vector<Proj3Term>& terms,
+  auto push_proj = [&](StepKind kind, const std::vector<Proj3Job>& jobs, const std::vector<Proj3Term>& terms,
                        const char* name, double flops, double bytes) {
     if (jobs.empty()) return;
-    int kp1max = 16;
-    for (const Proj3Term& t : terms) kp1max = std::max(kp1max, (t.r[1] + 15) & ~15);
-    for (Proj3Job& j : jobs) j.kp1max = kp1max;
     std::vector<char> blob(jobs.size() * sizeof(Proj3Job) + terms.size() * sizeof(Proj3Term));
     std::memcpy(blob.data(), jobs.data(), jobs.size() * sizeof(Proj3Job));
     if (!terms.empty())
       std::memcpy(blob.data() + jobs.size() * sizeof(Proj3Job), terms.data(), terms.size() * sizeof(Proj3Term));
     plan->st_project.push_back(make_step(kind, plan->add_table(blob.data(), blob.size()), (int)jobs.size(),
                                          (int64_t)jobs.size(), name, flops, bytes));
-    plan->st_project.back().smem = proj3_smem_bytes(kp1max);
+    plan->st_project.back().smem = proj3_smem_bytes();
   };
-  push_proj(S_PROJ3, p3, p3terms, "a7:project3[tc]", p3_flops, p3_bytes);
+  push_proj(S_PROJ3, p3, p3terms, "a7:project3[f32]", p3_flops, p3_bytes);
   if (!f4.empty()) {
     plan->push(plan->st_project, S_FOLD4, f4, (int64_t)f4.size(), "a7:fold4[f32]", f4_flops, 0.0);
     plan->st_project.back().smem = f4_smem;
   }
-  push_proj(S_PROJ3F, p3f, p3fterms, "a7:project4[tc]", p3f_flops, p3f_bytes);
+  push_proj(S_PROJ3F, p3f, p3fterms, "a7:project4[f32]", p3f_flops, p3f_bytes);
   plan->st_recompress = plan->st_sketch;
   qcq.push(plan, plan->st_recompress, "a5:cq");
   plan->push(plan->st_recompress, S_QR, qr, (int64_t)qr.size(), "a5:qr", qcq.gram[0].empty() ? qr_flops : 0.0,
@@ -2588,10 +2585,10 @@ tks_status run_steps(tks_plan* plan, const std::vector<Step>& steps, const Bases
         launch_sketch3(static_cast<const Sketch3Job*>(table), s.njobs, s.smem, bases, plan->status, stream);
         break;
       case S_PROJ3:
-        launch_proj3(static_cast<const Proj3Job*>(table), s.njobs, s.smem, false, bases, plan->status, stream);
+        launch_proj3(static_cast<const Proj3Job*>(table), s.njobs, false, bases, plan->status, stream);
         break;
       case S_PROJ3F:
-        launch_proj3(static_cast<const Proj3Job*>(table), s.njobs, s.smem, true, bases, plan->status, stream);
+        launch_proj3(static_cast<const Proj3Job*>(table), s.njobs, true, bases, plan->status, stream);
         break;
       case S_FOLD4:
         launch_fold4(static_cast<const Fold4Job*>(table), s.njobs, s.smem, bases, stream);

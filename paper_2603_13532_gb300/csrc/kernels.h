@@ -72,9 +72,9 @@ size_t sketch4_smem_bytes(const int r[4], int kc);
 cudaError_t prepare_sketch4();
 void launch_sketch4(const Sketch4Job* jobs, int njobs, size_t smem, const Bases& bases, cudaStream_t stream);
 // Fused order-3 projection; `jobs` is followed in memory by the Proj3Term records.
-size_t proj3_smem_bytes(int kp1max);
+size_t proj3_smem_bytes();
 cudaError_t prepare_proj3();
-void launch_proj3(const Proj3Job* jobs, int njobs, size_t smem, bool f32_cores, const Bases& bases, Status* status,
+void launch_proj3(const Proj3Job* jobs, int njobs, bool f32_cores, const Bases& bases, Status* status,
                   cudaStream_t stream);
 // Order-4 fold G'_k(a1) = alpha_k G_k x_2 A_2k[a1, :], one CTA per (term, i3); smem from fold4_smem_bytes.
 size_t fold4_smem_bytes(int r0, int r1, int r2, int b1);

@@ -162,19 +162,23 @@ struct Sketch4Job {
   int32_t pad;
 };
 
-// Fused order-3 projection (stage c; the first mode product in float32 on the CUDA cores, the other
-// two on the tensor cores with split bf16 operands): one CTA per (problem, kProj3Rows mode-1 rows
-// of H), requires b_2, b_3 <= 64.  The job table is followed by the Proj3Term records of all
-// problems; job j reads terms [term_begin, term_begin + nterms) of that array.  A chunk stages at
-// most kProj3SliceBytes of a core, and at least one mode-3 slice G[:, :, i3] must fit.
+// Fused order-3 projection (stage c; float32 on the CUDA cores, split bf16 on the tensor cores):
+// one CTA per (problem, kProj3Rows mode-1 rows of H), requires b_2, b_3 <= 64.  The job table is
+// followed by the Proj3Term records of all problems; job j reads terms [term_begin, term_begin +
+// nterms) of that array.  A chunk stages at most kProj3SliceBytes of a core, and at least one
+// mode-3 slice G[:, :, i3] must fit.
 constexpr int kProj3Rows = 4;
 constexpr int kProj3SliceBytes = 12288;
-constexpr int kProj3Chunk = 16;        // mode-3 indices of a chunk (at most): K of the last product
+constexpr int kProj3Chunk = 16;        // mode-3 indices of a chunk (at most): K of one MMA
+constexpr int kProj3W1Floats = 2048;   // first-stage products of a chunk (at most)
 
 // Mode-3 indices per chunk of a term with ranks r and core elements of `elem` bytes: the chunk's
-// core slice fits kProj3SliceBytes.
+// core slice fits kProj3SliceBytes and its first-stage products kProj3W1Floats (odd row stride).
 inline int proj3_chunk(const int32_t r[3], int elem) {
-  return std::min(kProj3Chunk, kProj3SliceBytes / elem / (r[0] * r[1]));
+  int c = kProj3Chunk;
+  c = std::min(c, kProj3SliceBytes / elem / (r[0] * r[1]));
+  c = std::min(c, kProj3W1Floats / (kProj3Rows * (r[1] | 1)));
+  return c;
 }
 
 struct Proj3Term {
@@ -192,8 +196,7 @@ struct Proj3Job {
   int32_t x0, rows;      // mode-1 rows [x0, x0 + rows), rows <= kProj3Rows
   int32_t term_begin, nterms;
   int64_t hs1, hs2;      // strides of a1 and a2 in H (b0 and b0 b1 for an order-3 core)
-  int32_t kp1max;        // the launch's largest r_2 rounded up to 16 (sizes its shared memory)
-  int32_t pad;
+  int32_t pad[2];
 };
 static_assert(sizeof(Proj3Job) % 16 == 0 && sizeof(Proj3Term) % 16 == 0, "term records follow the jobs");
 
