@@ -86,6 +86,9 @@ def parse_args():
     ap.add_argument("--subrank-steps", type=int, default=3, help="timed calls of the Alg. 5 leg")
     ap.add_argument("--no-backward", action="store_true", help="skip the backward (config 5) leg")
     ap.add_argument("--no-autotune", action="store_true", help="run the built-in schedule rules untuned")
+    ap.add_argument("--schedule", default=None,
+                    help='fixed schedule knobs for the main plan as JSON, e.g. \'{"sketch_qr": 3, "hosvd_r": 3}\' '
+                         "(no autotuning; for profiling the tuned launch sequence without the search)")
     ap.add_argument("--backward-problems", type=int, default=152, help="grad384 problems per backward call")
     ap.add_argument("--backward-steps", type=int, default=20, help="timed calls of the mixed backward")
     return ap.parse_args()
@@ -659,10 +662,11 @@ def main():
     if args.lanes is None:
         args.lanes = 2 if (args.precision == "mixed_f32la" and not args.workload.startswith("order4")) else 1
     problems = make_problems(P, args.seed, rank, bf16, args.workload)
-    autotune = args.precision != "fp64" and not args.no_autotune
+    fixed = json.loads(args.schedule) if args.schedule else None
+    autotune = args.precision != "fp64" and not args.no_autotune and fixed is None
     t_tune = time.perf_counter()
     plan = binding.Plan(problems, kind=kind, precision=args.precision, seed=args.seed, device=device,
-                        lanes=args.lanes, autotune=autotune)
+                        lanes=args.lanes, autotune=autotune, schedule=fixed)
     t_tune = time.perf_counter() - t_tune
     tuning = plan.tuning()
     schedule = {"knobs": tuning["picked"], "rule": tuning["rule"], "autotuned": bool(tuning["autotuned"])}
