@@ -227,56 +227,61 @@ __global__ void __launch_bounds__(kOzXThreads) oz_xdig_kernel(const OzXSliceJob*
   __syncthreads();
   uint16_t* colP = at<uint16_t>(bases, J.colP);
   const int64_t cstride = 64 * J.ldP;
-  // each element's magnitude once, in registers (M < 2^56, the sign in bit 63; 0 outside the tile)
-  constexpr int kPer = kOzXRows * 64 / kOzXThreads;
-  unsigned long long mg[kPer];
+  // each element's magnitude once, in registers (M < 2^56, the sign in bit 63; 0 outside the tile):
+  // thread t holds column a = t % 64 of the row pairs (2 j, 2 j + 1), j = t / 64 + 4 k
+  constexpr int kPairs = kOzXRows / 2 * 64 / kOzXThreads;   // 8 row pairs per thread
+  const int a = threadIdx.x & 63, j0 = threadIdx.x >> 6;
+  unsigned long long mg[kPairs][2];
 #pragma unroll
-  for (int k = 0; k < kPer; ++k) {
-    const int e = threadIdx.x + kOzXThreads * k, q = e >> 6, a = e & 63;
-    mg[k] = 0ull;
-    if (q < nq && a < b) {
-      bool neg;
-      const unsigned long long M = oz_magnitude(xs[q][a], es[a], neg);
-      mg[k] = M | (neg ? (1ull << 63) : 0ull);
+  for (int k = 0; k < kPairs; ++k) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int q = 2 * (j0 + 4 * k) + h;
+      mg[k][h] = 0ull;
+      if (q < nq && a < b) {
+        bool neg;
+        const unsigned long long M = oz_magnitude(xs[q][a], es[a], neg);
+        mg[k][h] = M | (neg ? (1ull << 63) : 0ull);
+      }
     }
   }
   __syncthreads();
-  // the staged tile's bytes now hold four digit planes at a time: dg[s][q][a], rows of kOzXPitch
-  // bf16 (rows on distinct banks for a column read); each digit is formed once and leaves in
+  // the staged tile's bytes now hold four digit planes at a time, as 32-bit words of two rows:
+  // dg[s][j][a] = (digit of row 2 j + 1) << 16 | digit of row 2 j, rows of kDPitch words (an odd
+  // count: the column reads below fall on distinct banks); each digit is formed once and leaves in
   // 16-byte stores of 8 rows of one column
-  constexpr int kDPitch = kOzXPitch;   // bf16 per digit row: 4 planes x 64 rows fill the staged tile's bytes
-  uint16_t* dg = reinterpret_cast<uint16_t*>(&xs[0][0]);
-  constexpr int kDPlane = kOzXRows * kDPitch;
-  static_assert(4 * kDPlane * sizeof(uint16_t) <= sizeof(xs), "four digit planes must fit the staged tile");
+  constexpr int kDPitch = 65;
+  constexpr int kDPlane = kOzXRows / 2 * kDPitch;
+  uint32_t* dg = reinterpret_cast<uint32_t*>(&xs[0][0]);
+  static_assert(4 * kDPlane * sizeof(uint32_t) <= sizeof(xs), "four digit planes must fit the staged tile");
 #pragma unroll
   for (int half = 0; half < 2; ++half) {
 #pragma unroll
-    for (int k = 0; k < kPer; ++k) {
-      const int e = threadIdx.x + kOzXThreads * k, q = e >> 6, a = e & 63;
-      const unsigned long long v = mg[k];
+    for (int k = 0; k < kPairs; ++k) {
+      const int j = j0 + 4 * k;
       // digits 0-3 are bits 28..55 of M and digits 4-7 bits 0..27: one 32-bit word per half; a zero
       // digit of a negative value becomes -0, which adds nothing to an exact sum
-      const uint32_t w = half == 0 ? (uint32_t)(v >> 28) & 0x0fffffffu : (uint32_t)v & 0x0fffffffu;
-      const uint32_t sg = (uint32_t)(v >> 63) << 15;
+      const unsigned long long v0 = mg[k][0], v1 = mg[k][1];
+      const uint32_t w0 = half == 0 ? (uint32_t)(v0 >> 28) & 0x0fffffffu : (uint32_t)v0 & 0x0fffffffu;
+      const uint32_t w1 = half == 0 ? (uint32_t)(v1 >> 28) & 0x0fffffffu : (uint32_t)v1 & 0x0fffffffu;
+      const uint32_t sg = ((uint32_t)(v0 >> 63) << 15) | ((uint32_t)(v1 >> 63) << 31);
 #pragma unroll
       for (int s4 = 0; s4 < 4; ++s4) {
-        const uint32_t d = (w >> (21 - 7 * s4)) & 127u;
-        const float f = __int_as_float(0x4B000000 | (int)d) - 8388608.0f;
-        dg[s4 * kDPlane + q * kDPitch + a] = (uint16_t)((__float_as_uint(f) >> 16) | sg);
+        const uint32_t d0 = (w0 >> (21 - 7 * s4)) & 127u, d1 = (w1 >> (21 - 7 * s4)) & 127u;
+        // bf16 of a digit: the upper half of the float32 (2^23 + d) - 2^23, exact
+        const float f0 = __int_as_float(0x4B000000 | (int)d0) - 8388608.0f;
+        const float f1 = __int_as_float(0x4B000000 | (int)d1) - 8388608.0f;
+        dg[s4 * kDPlane + j * kDPitch + a] = __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632) | sg;
       }
     }
     __syncthreads();
     // column planes: (slice, column a, 8 rows) -> one 16-byte store of plane row a
     for (int it = threadIdx.x; it < 4 * 64 * 8; it += kOzXThreads) {
-      const int s4 = it >> 9, a = (it >> 3) & 63, c = it & 7;
-      if (a < b && 8 * c < nq) {
-        const uint16_t* src = dg + s4 * kDPlane + 8 * c * kDPitch + a;
-        uint4 w;
-        w.x = (uint32_t)src[0] | ((uint32_t)src[kDPitch] << 16);
-        w.y = (uint32_t)src[2 * kDPitch] | ((uint32_t)src[3 * kDPitch] << 16);
-        w.z = (uint32_t)src[4 * kDPitch] | ((uint32_t)src[5 * kDPitch] << 16);
-        w.w = (uint32_t)src[6 * kDPitch] | ((uint32_t)src[7 * kDPitch] << 16);
-        *reinterpret_cast<uint4*>(colP + (4 * half + s4) * cstride + (int64_t)a * J.ldP + i0 + 8 * c) = w;
+      const int s4 = it >> 9, ac = (it >> 3) & 63, c = it & 7;
+      if (ac < b && 8 * c < nq) {
+        const uint32_t* src = dg + s4 * kDPlane + 4 * c * kDPitch + ac;
+        const uint4 w = make_uint4(src[0], src[kDPitch], src[2 * kDPitch], src[3 * kDPitch]);
+        *reinterpret_cast<uint4*>(colP + (4 * half + s4) * cstride + (int64_t)ac * J.ldP + i0 + 8 * c) = w;
       }
     }
     __syncthreads();
