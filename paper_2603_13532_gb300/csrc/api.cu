@@ -835,12 +835,13 @@ static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
       sj.cols = h.b[n];
       sj.ld_src = sj.ld_dst = (int64_t)nn;
       sj.count = sj.rows * sj.cols;
-      sj.begin = sp_all_total;
-      sp_all_total += sj.count;
+      sj.begin = 0;
+      sj.tile_begin = (int32_t)sp_all_total;
+      sp_all_total += (sj.count + kSplitTile - 1) / kSplitTile;
       sp_all.push_back(sj);
       if (!planes_in_qr) {
-        sj.begin = sp_total;
-        sp_total += sj.count;
+        sj.tile_begin = (int32_t)sp_total;
+        sp_total += (sj.count + kSplitTile - 1) / kSplitTile;
         sp.push_back(sj);
       }
       planes_in_qr = false;
@@ -1085,7 +1086,7 @@ static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
     plan->st_sketch.back().smem = sk3_smem;
   }
   plan->push_tc(plan->st_sketch, tcY, "a4:Y=Ucat.Vcat[tc]");
-  plan->push(plan->st_project, S_SPLIT, sp_all, sp_all_total, "a6:Q->planes", 0.0, 14.0 * sp_all_total);
+  plan->push(plan->st_project, S_SPLIT, sp_all, sp_all_total, "a6:Q->planes", 0.0, 14.0 * kSplitTile * sp_all_total);
   const size_t project_from = plan->st_project.size();   // the recompression takes its own split
   plan->push_tc(plan->st_project, tcA, "a6:AT=UcatT.Q[tc]");
   for (size_t t = 0; t < chain.size(); ++t) {
@@ -1131,7 +1132,7 @@ static void build_mixed_stages(tks_plan* plan, int kron, bool f32la) {
                0.0);
     plan->st_recompress.back().smem = qrsm_smem;
   }
-  plan->push(plan->st_recompress, S_SPLIT, sp, sp_total, "a6:Q->planes", 0.0, 14.0 * sp_total);
+  plan->push(plan->st_recompress, S_SPLIT, sp, sp_total, "a6:Q->planes", 0.0, 14.0 * kSplitTile * sp_total);
   for (size_t i = project_from; i < plan->st_project.size(); ++i) plan->st_recompress.push_back(plan->st_project[i]);
 }
 
@@ -1420,8 +1421,9 @@ static void build_backward3_mixed(tks_plan* plan) {
     sj.ld_dst = ld_dst;
     sj.trans = trans;
     sj.count = rows * cols;
-    sj.begin = sp_total;
-    sp_total += sj.count;
+    sj.begin = 0;
+    sj.tile_begin = (int32_t)sp_total;
+    sp_total += (sj.count + kSplitTile - 1) / kSplitTile;
     sp.push_back(sj);
   };
   auto tc6 = [](TcJob& j) {
@@ -1579,7 +1581,7 @@ static void build_backward3_mixed(tks_plan* plan) {
       tcU.push_back(j);
     }
   }
-  plan->push(plan->st_backward, S_SPLIT, sp, sp_total, "bwd:Q,Hbar->planes", 0.0, 14.0 * sp_total);
+  plan->push(plan->st_backward, S_SPLIT, sp, sp_total, "bwd:Q,Hbar->planes", 0.0, 14.0 * kSplitTile * sp_total);
   plan->push_tc(plan->st_backward, tcA, "bwd:AT=UcatT.Q[tc]");
   plan->push_tc(plan->st_backward, tcZ, "bwd:Z=Hbar.Acat[tc]");
   plan->push_simt(plan->st_backward, step1, "bwd:per-term1[f32]");

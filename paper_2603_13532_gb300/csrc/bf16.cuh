@@ -17,12 +17,35 @@ __device__ __forceinline__ void split3(float v, uint16_t& h0, uint16_t& h1, uint
   h1 = bf16_bits(r1);
   h2 = bf16_bits(r1 - bf16_float(h1));
 }
+// The same for a float64 value, without float64 instructions where it can (GB300's float64 pipe
+// would otherwise bound the kernels that split float64 matrices): v = f + e exactly, with f = v
+// rounded to float32 (nearest-even, from the float64 bits) and e = delta 2^(E - 1075) the dropped
+// bits (|delta| <= 2^28, as a float32 to 2^-24 of e); then the float32 split of f with e added to
+// the first remainder.  Values outside [2^-74, 2^126) take float64 arithmetic.
 __device__ __forceinline__ void split3(double v, uint16_t& h0, uint16_t& h1, uint16_t& h2) {
-  h0 = bf16_bits(__double2float_rn(v));
-  const double r1 = v - (double)bf16_float(h0);
-  h1 = bf16_bits(__double2float_rn(r1));
-  const double r2 = r1 - (double)bf16_float(h1);
-  h2 = bf16_bits(__double2float_rn(r2));
+  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  const int fe = (int)((u >> 52) & 0x7ff) - 1023 + 127;   // float32 exponent field of f
+  if (fe < 53 || fe > 253) {
+    h0 = bf16_bits(__double2float_rn(v));
+    const double r1 = v - (double)bf16_float(h0);
+    h1 = bf16_bits(__double2float_rn(r1));
+    const double r2 = r1 - (double)bf16_float(h1);
+    h2 = bf16_bits(__double2float_rn(r2));
+    return;
+  }
+  const unsigned long long m53 = (u & 0xfffffffffffffull) | (1ull << 52);
+  const int low = (int)(m53 & 0x1fffffffull);              // the 29 bits below float32's 24
+  unsigned int m24 = (unsigned int)(m53 >> 29);
+  const bool up = low > 0x10000000 || (low == 0x10000000 && (m24 & 1u));
+  m24 += up ? 1u : 0u;                                     // 2^24 carries into the exponent below
+  const int delta = low - (up ? 0x20000000 : 0);
+  const bool neg = (u >> 63) != 0;
+  const float f = __uint_as_float((neg ? 0x80000000u : 0u) | ((((unsigned int)fe - 1u) << 23) + m24));
+  const float e = (float)(neg ? -delta : delta) * __uint_as_float((unsigned int)(fe - 52) << 23);
+  h0 = bf16_bits(f);
+  const float r1 = (f - bf16_float(h0)) + e;
+  h1 = bf16_bits(r1);
+  h2 = bf16_bits(r1 - bf16_float(h1));
 }
 
 }  // namespace tks

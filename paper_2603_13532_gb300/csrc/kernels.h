@@ -80,7 +80,7 @@ void launch_proj3(const Proj3Job* jobs, int njobs, bool f32_cores, const Bases& 
 size_t fold4_smem_bytes(int r0, int r1, int r2, int b1);
 cudaError_t prepare_fold4();
 void launch_fold4(const Fold4Job* jobs, int njobs, size_t smem, const Bases& bases, cudaStream_t stream);
-void launch_split_f64(const SplitJob* jobs, int njobs, int64_t total, const Bases& bases, cudaStream_t stream);
+void launch_split_f64(const SplitJob* jobs, int njobs, int64_t tiles, const Bases& bases, cudaStream_t stream);
 void launch_transpose_bf16(const TransposeJob* jobs, int njobs, int total_tiles, const Bases& bases,
                            cudaStream_t stream);
 

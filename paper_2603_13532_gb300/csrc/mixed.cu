@@ -366,19 +366,32 @@ __global__ void __launch_bounds__(256) chain3_kernel(const Chain3Job* __restrict
 }
 
 // ----------------------------------------------------------------------------- split / transpose
-__global__ void split_f64_kernel(const SplitJob* __restrict__ jobs, int njobs, int64_t total, Bases bases) {
-  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total;
-       g += (int64_t)gridDim.x * blockDim.x) {
-    const SplitJob& J = jobs[find_begin(jobs, njobs, g)];
-    const int64_t e = g - J.begin;
-    const int64_t i = e % J.rows, j = e / J.rows;
-    const double v = at<double>(bases, J.src)[i + J.ld_src * j];
-    uint16_t h0, h1, h2;
-    split3(v, h0, h1, h2);
-    const int64_t off = J.trans ? j + J.ld_dst * i : i + J.ld_dst * j;
-    at<uint16_t>(bases, J.dst[0])[off] = h0;
-    at<uint16_t>(bases, J.dst[1])[off] = h1;
-    at<uint16_t>(bases, J.dst[2])[off] = h2;
+// One CTA per tile of kSplitTile elements of one job (column-major element order): the tile's first
+// element takes one 64-bit division, later ones step along the column.
+__global__ void __launch_bounds__(256) split_f64_kernel(const SplitJob* __restrict__ jobs, int njobs, Bases bases) {
+  const SplitJob& J = jobs[tile_job(jobs, njobs, (int)blockIdx.x)];
+  const int64_t e0 = (int64_t)(blockIdx.x - J.tile_begin) * kSplitTile + threadIdx.x;
+  int64_t j = e0 / J.rows, i = e0 - j * J.rows;
+  const double* src = at<double>(bases, J.src);
+  uint16_t* d0 = at<uint16_t>(bases, J.dst[0]);
+  uint16_t* d1 = at<uint16_t>(bases, J.dst[1]);
+  uint16_t* d2 = at<uint16_t>(bases, J.dst[2]);
+#pragma unroll
+  for (int k = 0; k < kSplitTile / 256; ++k) {
+    if (e0 + 256 * k < J.count) {
+      const double v = src[i + J.ld_src * j];
+      uint16_t h0, h1, h2;
+      split3(v, h0, h1, h2);
+      const int64_t off = J.trans ? j + J.ld_dst * i : i + J.ld_dst * j;
+      d0[off] = h0;
+      d1[off] = h1;
+      d2[off] = h2;
+    }
+    i += 256;
+    while (i >= J.rows) {   // rows >= 1: at most 256 steps, one when rows >= 256
+      i -= J.rows;
+      ++j;
+    }
   }
 }
 
@@ -472,8 +485,8 @@ void launch_chain3(const Chain3Job* jobs, int njobs, size_t smem, const Bases& b
   chain3_kernel<<<njobs, 256, smem, stream>>>(jobs, bases);
 }
 
-void launch_split_f64(const SplitJob* jobs, int njobs, int64_t total, const Bases& bases, cudaStream_t stream) {
-  split_f64_kernel<<<grid_for(total, 256), 256, 0, stream>>>(jobs, njobs, total, bases);
+void launch_split_f64(const SplitJob* jobs, int njobs, int64_t tiles, const Bases& bases, cudaStream_t stream) {
+  split_f64_kernel<<<(unsigned)tiles, 256, 0, stream>>>(jobs, njobs, bases);
 }
 
 void launch_transpose_bf16(const TransposeJob* jobs, int njobs, int total_tiles, const Bases& bases,

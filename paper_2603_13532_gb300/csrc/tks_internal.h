@@ -227,12 +227,16 @@ struct Chain3Job {
 
 // Split a float64 matrix (rows x cols, element (i, j) at i + ld_src j) into bf16 planes
 // hi + mid + lo (element (i, j) at i + ld_dst j).
+// Split a float64 matrix into three bf16 planes; the launch covers each job in tiles of
+// kSplitTile elements (column-major order), tiles [tile_begin, tile_begin + ceil(count / kSplitTile)).
+constexpr int kSplitTile = 1024;
 struct SplitJob {
   Operand src;
   Operand dst[3];
   int64_t rows, cols, ld_src, ld_dst;
   int64_t count, begin;
-  int32_t trans, pad;   // trans: element (i, j) goes to j + ld_dst i (else i + ld_dst j)
+  int32_t trans;        // trans: element (i, j) goes to j + ld_dst i (else i + ld_dst j)
+  int32_t tile_begin;
 };
 
 // Transpose a bf16 matrix: dst[j + ld_dst i] = src[i + ld_src j] (src rows x cols).
