@@ -308,7 +308,8 @@ TKS_API tks_status tks_profile_end(tks_plan* plan, tks_step_profile_t* out, int3
  * until the process exits; a problem needing more is rejected with TKS_EINVAL and a message giving
  * both sizes.  No cudaMalloc, cudaFree or other allocating call is made.  The first call on a
  * device (and the first call after that device's context was destroyed, e.g. by cudaDeviceReset)
- * looks up the array's device address (cudaGetSymbolAddress) for that device.  The descriptor
+ * looks up the array's device address (cudaGetSymbolAddress) for that device; make that first call
+ * before any stream capture on that device.  The descriptor
  * tables are copied to the array from host memory that lives only for the duration of the call.
  * Every call reuses the same array and leaves its
  * contents behind; nothing in it needs to start at zero (each element a call reads is written
