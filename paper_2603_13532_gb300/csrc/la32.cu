@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(1024) qr_smem_f32_kernel(const QrF32Job* __res
   for (int e = threadIdx.x; e < n * b; e += blockDim.x) {
     const int l = e / n;
     const float sgn = rdiag[l] < 0.f ? -1.f : 1.f;
-    Q[e] = (double)(sgn * W[e]);
+    Q[e] = f32_to_f64_exact(sgn * W[e]);
   }
   if (threadIdx.x == 0 && sh_bad) record_status_la(status, TKS_ENONFINITE);
 }
@@ -444,7 +444,7 @@ __global__ void __launch_bounds__(kQrRegThreads, 1) qr_reg_f32_kernel(const QrF3
         const int i = lane + 32 * u;
         if (i < n) {
           const float v = sgn * q[u];
-          Q[i + (int64_t)n * l] = (double)v;
+          Q[i + (int64_t)n * l] = f32_to_f64_exact(v);
           if (J.nplanes) {
             // the same planes the float64 -> bf16 split gives for this float32 value
             uint16_t h0, h1, h2;

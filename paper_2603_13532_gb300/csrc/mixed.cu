@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(256) simt_gemm_f32_kernel(const SimtJob* __res
         const int64_t off = bt * J.c_b + gi * J.c_m + gj * J.c_n;
         const float v = J.alpha * acc[i][j];
         if (c32) c32[off] = v;
-        if (c64) c64[off] = (double)v;
+        if (c64) c64[off] = f32_to_f64_exact(v);
         if (cb0) {
           uint16_t h0, h1, h2;
           split3(v, h0, h1, h2);

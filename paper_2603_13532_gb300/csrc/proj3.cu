@@ -387,7 +387,7 @@ __global__ void __launch_bounds__(kThreads, 2) project3_kernel(const Proj3Job* _
         const int ncol = min(32, b2 - cb);
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
-          if (j < ncol) *dst = (double)sum[j];
+          if (j < ncol) *dst = f32_to_f64_exact(sum[j]);
           dst += J.hs2;
         }
       }

@@ -14,6 +14,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include "bf16.cuh"
 #include "kernels.h"
 #include "tc.cuh"
 
@@ -30,29 +31,8 @@ constexpr int kATile = kBM * kBK * 2;         // 16 KB
 // 64 columns fill the 512 TMEM columns of the SM (one CTA per SM: its shared memory is 227 KB).
 constexpr int kAcc = 8;
 
-// float32 -> float64 by the bits (exact): the conversion instruction runs on GB300's float64 pipe,
-// about 1/64 of the integer rate.  Normal numbers and zeros take the bit path; subnormals, infinities
-// and NaN the conversion.
-__device__ __forceinline__ double f32_to_f64_exact(float v) {
-  const uint32_t u = __float_as_uint(v);
-  const uint32_t e = (u >> 23) & 0xffu;
-  const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
-  if (e != 0u && e != 0xffu)
-    return __longlong_as_double((long long)(sign | ((unsigned long long)(e + 896u) << 52) |
-                                            ((unsigned long long)(u & 0x7fffffu) << 29)));
-  if ((u & 0x7fffffffu) == 0u) return __longlong_as_double((long long)sign);
-  return (double)v;
-}
-
 __device__ __forceinline__ void record_status_tc(Status* st, int code) {
   if (st) atomicCAS(&st->code, 0, code);
-}
-
-__device__ __forceinline__ uint16_t bf16_bits(float x) {
-  return __bfloat16_as_ushort(__float2bfloat16_rn(x));
-}
-__device__ __forceinline__ float bf16_float(uint16_t h) {
-  return __bfloat162float(__ushort_as_bfloat16(h));
 }
 
 template <int BN>
