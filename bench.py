@@ -61,7 +61,8 @@ def parse_args():
                     help="mixed: tensor-core contractions with float64 QR and ST-HOSVD (TKS_MIXED); mixed_f32la: "
                          "the same contractions with float32 QR and ST-HOSVD")
     ap.add_argument("--fp64-steps", type=int, default=3, help="timed steps of the FP64 comparison")
-    ap.add_argument("--problems", type=int, default=152, help="independent sums per step and GPU")
+    ap.add_argument("--problems", type=int, default=None,
+                    help="independent sums per step and GPU (default: 152; 256 for batched, 38 for order4)")
     ap.add_argument("--workload", default="decay512",
                     choices=["decay512", "order4-krp", "order4-kron", "batched", "exact_recovery"])
     ap.add_argument("--no-graph", action="store_true", help="time eager launches instead of graph replays")
@@ -91,7 +92,10 @@ def parse_args():
                          "(no autotuning; for profiling the tuned launch sequence without the search)")
     ap.add_argument("--backward-problems", type=int, default=152, help="grad384 problems per backward call")
     ap.add_argument("--backward-steps", type=int, default=20, help="timed calls of the mixed backward")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.problems is None:
+        args.problems = EXTRA_PROBLEMS.get(args.workload, 152)
+    return args
 
 
 WORKLOAD_LABELS = {

@@ -60,6 +60,7 @@ struct Step {
   char name[32];
   double flops, bytes;
   int na_max = 0, nb_max = 0;   // tensor-core GEMM steps: planes per operand
+  int kmax = 0;                 // tensor-core GEMM steps: the longest contraction
   size_t smem = 0;              // dynamic shared memory of one-CTA-per-job steps
 };
 
@@ -262,7 +263,7 @@ struct tks_plan {
   }
   void push_tc(std::vector<Step>& steps, std::vector<TcJob>& jobs, const char* name) {
     if (jobs.empty()) return;
-    int tiles = 0, na = 1, nb = 1;
+    int tiles = 0, na = 1, nb = 1, kmax = 0;
     double flops = 0.0, bytes = 0.0;
     for (auto& j : jobs) {
       j.tiles_m = ceil_div(j.M, 128);
@@ -271,6 +272,7 @@ struct tks_plan {
       tiles += j.tiles_m * j.tiles_n;
       na = std::max(na, j.na);
       nb = std::max(nb, j.nb);
+      kmax = std::max(kmax, (int)j.K);
       flops += 2.0 * j.M * (double)j.N * j.K;
       bytes += 2.0 * ((double)j.M * j.K + (double)j.N * j.K) +
                (double)j.M * j.N * (4.0 * j.epi.has_f32 + 8.0 * j.epi.has_f64 + 2.0 * j.epi.nbf);
@@ -279,6 +281,7 @@ struct tks_plan {
                         flops, bytes);
     st.na_max = na;
     st.nb_max = nb;
+    st.kmax = kmax;
     steps.push_back(st);
   }
   void push_simt(std::vector<Step>& steps, std::vector<SimtJob>& jobs, const char* name) {
@@ -2537,7 +2540,7 @@ tks_status run_steps(tks_plan* plan, const std::vector<Step>& steps, const Bases
       case S_TC:
         launch_tc_gemm(static_cast<const TcJob*>(table), s.njobs, (int)s.work, plan->arena_dev + plan->maps_off,
                        s.na_max, s.nb_max, bases, plan->status, plan->wait_cycles,
-                       plan->stall ? plan->stall_word() : nullptr, plan->params.tc_stages, stream);
+                       plan->stall ? plan->stall_word() : nullptr, plan->params.tc_stages, s.kmax, stream);
         break;
       case S_SIMT:
         launch_simt_gemm_f32(static_cast<const SimtJob*>(table), s.njobs, (int)s.work, bases, stream);

@@ -37,11 +37,11 @@ size_t tc_gemm_smem_bytes(int stages, int na_max, int nb_max, int bn);
 int tc_gemm_stages(int na_max, int nb_max, int bn);
 cudaError_t prepare_tc_gemm();
 // wait_cycles bounds every mbarrier wait; stall_word (tests of the timeout path) is a device word that
-// nothing sets, waited for by the copy-issuing thread before its first copy, or NULL.
+// nothing sets, waited for by the copy-issuing thread before its first copy, or NULL.  kmax: the
+// launch's longest contraction (it sets the number of partial accumulators).
 void launch_tc_gemm(const TcJob* jobs, int njobs, int total_tiles, const void* maps, int na_max, int nb_max,
                     const Bases& bases, Status* status, long long wait_cycles, const int* stall_word,
-                    int max_stages,
-                    cudaStream_t stream);
+                    int max_stages, int kmax, cudaStream_t stream);
 
 // Float32 CUDA-core kernels of the mixed path.
 void launch_simt_gemm_f32(const SimtJob* jobs, int njobs, int total_tiles, const Bases& bases,

@@ -2,8 +2,8 @@
 //
 // One CTA computes one 128 x BN output tile of one job.  Warp 0 (one elected thread) streams
 // the bf16 planes of A and B through a ring of shared-memory stages with TMA (128-byte swizzle);
-// warp 1 allocates kAcc TMEM accumulators and (one elected thread) issues tcgen05.mma for every
-// selected plane pair, 16 deep in k per instruction, k-block kb into accumulator kb % kAcc,
+// warp 1 allocates acc TMEM accumulators (4 or 8) and (one elected thread) issues tcgen05.mma for
+// every selected plane pair, 16 deep in k per instruction, k-block kb into accumulator kb % acc,
 // releasing each stage with tcgen05.commit; warps 2-5 read the accumulators back with
 // tcgen05.ld (one TMEM lane quadrant each), add them and write the requested outputs.
 // Every wait is bounded: on a timeout the kernel records TKS_ETIMEOUT,
@@ -25,11 +25,14 @@ namespace {
 constexpr int kBM = 128;
 constexpr int kBK = 64;                       // bf16 elements = 128 bytes = one swizzle row
 constexpr int kATile = kBM * kBK * 2;         // 16 KB
-// Partial accumulators in TMEM: k-block kb goes to accumulator kb % kAcc and the epilogue adds
-// them, so each float32 accumulator takes 1/kAcc of the K-steps (the rounding error of a long
-// contraction whose products share a sign grows with the number of steps).  Eight accumulators of
-// 64 columns fill the 512 TMEM columns of the SM (one CTA per SM: its shared memory is 227 KB).
-constexpr int kAcc = 8;
+// Partial accumulators in TMEM: k-block kb goes to accumulator kb % acc and the epilogue adds
+// them, so each float32 accumulator takes 1/acc of the K-steps (the rounding error of a long
+// contraction whose products share a sign grows with the number of steps).  Contractions of up to
+// kShortK take four accumulators (at most four k-blocks, 16 steps, each): 256 TMEM columns, so two
+// CTAs share an SM and one's loads and epilogue overlap the other's products.  Longer ones take
+// eight accumulators of 64 columns, all 512 TMEM columns, one CTA per SM.
+constexpr int kAccLong = 8, kAccShort = 4;
+constexpr int kShortK = 16 * 64;
 
 __device__ __forceinline__ void record_status_tc(Status* st, int code) {
   if (st) atomicCAS(&st->code, 0, code);
@@ -38,7 +41,7 @@ __device__ __forceinline__ void record_status_tc(Status* st, int code) {
 template <int BN>
 __global__ void __launch_bounds__(192, 1)
     tc_gemm_kernel(const TcJob* __restrict__ jobs, int njobs, const CUtensorMap* __restrict__ maps, Bases bases,
-                   Status* status, int stages, int na_max, int nb_max, long long kWaitCycles,
+                   Status* status, int stages, int na_max, int nb_max, int acc, long long kWaitCycles,
                    const volatile int* stall_word) {
   constexpr int kBTile = BN * kBK * 2;
   extern __shared__ uint8_t smem_raw[];
@@ -67,7 +70,7 @@ __global__ void __launch_bounds__(192, 1)
     *err = 0;
     tc::fence_barrier_init();
   }
-  if (warp == 1) tc::tmem_alloc(tmem_slot, BN * kAcc);
+  if (warp == 1) tc::tmem_alloc(tmem_slot, BN * acc);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
@@ -133,9 +136,9 @@ __global__ void __launch_bounds__(192, 1)
           break;
         }
         tc::fence_after_sync();
-        // k-block kb accumulates into accumulator kb % kAcc; its first block starts it at zero
-        const uint32_t d = tmem + (uint32_t)((kb % kAcc) * BN);
-        uint32_t acc = kb >= kAcc ? 1u : 0u;
+        // k-block kb accumulates into accumulator kb % acc; its first block starts it at zero
+        const uint32_t d = tmem + (uint32_t)((kb % acc) * BN);
+        uint32_t accum = kb >= acc ? 1u : 0u;
         for (int p = 0; p < J.npairs; ++p) {
           const uint32_t a0 = tc::smem_u32(a_tile(s, J.pa[p]));
           const uint32_t b0 = tc::smem_u32(b_tile(s, J.pb[p]));
@@ -143,8 +146,8 @@ __global__ void __launch_bounds__(192, 1)
           const uint64_t db = tc::sw128_kmajor_desc(b0);
 #pragma unroll
           for (int k = 0; k < kBK / 16; ++k) {
-            tc::mma_bf16(d, da + astep * k, db + 2 * k, idesc, acc);
-            acc = 1;
+            tc::mma_bf16(d, da + astep * k, db + 2 * k, idesc, accum);
+            accum = 1;
           }
         }
         tc::mma_commit(&empty[s]);
@@ -166,11 +169,11 @@ __global__ void __launch_bounds__(192, 1)
       uint16_t* ob0 = E.nbf > 0 ? at<uint16_t>(bases, E.bf[0]) : nullptr;
       uint16_t* ob1 = E.nbf > 1 ? at<uint16_t>(bases, E.bf[1]) : nullptr;
       uint16_t* ob2 = E.nbf > 2 ? at<uint16_t>(bases, E.bf[2]) : nullptr;
-      const int nacc = nk < kAcc ? nk : kAcc;
+      const int nacc = nk < acc ? nk : acc;
 #pragma unroll
       for (int c0 = 0; c0 < BN; c0 += 32) {
-        // the partial accumulators of this column chunk (kAcc - 1 float32 additions: negligible
-        // next to the K / (16 kAcc) roundings inside each accumulator; float64 arithmetic here
+        // the partial accumulators of this column chunk (acc - 1 float32 additions: negligible
+        // next to the K / (16 acc) roundings inside each accumulator; float64 arithmetic here
         // would run at the FP64 rate)
         float sum[32];
 #pragma unroll
@@ -208,7 +211,7 @@ __global__ void __launch_bounds__(192, 1)
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (warp == 1) tc::tmem_dealloc(tmem, BN * kAcc);
+  if (warp == 1) tc::tmem_dealloc(tmem, BN * acc);
   if (threadIdx.x == 0 && *err) record_status_tc(status, TKS_ETIMEOUT);
 }
 
@@ -231,13 +234,29 @@ cudaError_t prepare_tc_gemm() {
 
 void launch_tc_gemm(const TcJob* jobs, int njobs, int total_tiles, const void* maps, int na_max, int nb_max,
                     const Bases& bases, Status* status, long long wait_cycles, const int* stall_word,
-                    int max_stages, cudaStream_t stream) {
-  int stages = tc_gemm_stages(na_max, nb_max, 64);
+                    int max_stages, int kmax, cudaStream_t stream) {
+  // two CTAs per SM for short contractions of at most kTwoTiles output tiles (few tiles an SM, whose
+  // TMA set-up, products and epilogue one CTA per SM would run in turn), and for those of at most
+  // four k-blocks (epilogue-heavy; four accumulators round them exactly as eight).  Longer
+  // contractions of more tiles keep one CTA per SM: no faster on two, and each float32 accumulator
+  // takes half the k-blocks.
+  constexpr int kTwoTiles = 32 * 152;
+  const bool two = kmax <= kShortK && (total_tiles <= kTwoTiles || kmax <= kAccShort * kBK);
+  // two CTAs per SM: the stages that fit half the shared memory, and at least 77 KB each so that no
+  // third CTA (and its TMEM columns) joins; one CTA per SM: at least 116 KB, all 512 TMEM columns
+  int stages = two ? 1 : tc_gemm_stages(na_max, nb_max, 64);
+  if (two)
+    for (int s = 4; s >= 2; --s)
+      if (tc_gemm_smem_bytes(s, na_max, nb_max, 64) <= 112 * 1024) {
+        stages = s;
+        break;
+      }
   if (max_stages > 0 && stages > max_stages) stages = max_stages;
-  // at least 116 KB of shared memory keeps one CTA per SM, which owns all 512 TMEM columns
-  const size_t smem = std::max<size_t>(tc_gemm_smem_bytes(stages, na_max, nb_max, 64), 116 * 1024);
+  const size_t floor = two ? 77 * 1024 : 116 * 1024;
+  const size_t smem = std::max<size_t>(tc_gemm_smem_bytes(stages, na_max, nb_max, 64), floor);
   tc_gemm_kernel<64><<<total_tiles, 192, smem, stream>>>(jobs, njobs, static_cast<const CUtensorMap*>(maps), bases,
-                                                         status, stages, na_max, nb_max, wait_cycles, stall_word);
+                                                         status, stages, na_max, nb_max, two ? kAccShort : kAccLong,
+                                                         wait_cycles, stall_word);
 }
 
 }  // namespace tks
