@@ -33,12 +33,11 @@ void launch_ttm_f64(const TtmJob* jobs, int njobs, int total_tiles, int max_cols
                     cudaStream_t stream);
 
 // Tensor-core (tcgen05) grouped GEMM over bf16 planes; maps = device array of CUtensorMap.
-size_t tc_gemm_smem_bytes(int stages, int na_max, int nb_max, int bn);
-int tc_gemm_stages(int na_max, int nb_max, int bn);
+// (launch shape: tc_gemm_shape in tc_shape.h)
 cudaError_t prepare_tc_gemm();
 // wait_cycles bounds every mbarrier wait; stall_word (tests of the timeout path) is a device word that
 // nothing sets, waited for by the copy-issuing thread before its first copy, or NULL.  kmax: the
-// launch's longest contraction (it sets the number of partial accumulators).
+// launch's longest contraction (with total_tiles it sets CTAs per SM and partial accumulators).
 void launch_tc_gemm(const TcJob* jobs, int njobs, int total_tiles, const void* maps, int na_max, int nb_max,
                     const Bases& bases, Status* status, long long wait_cycles, const int* stall_word,
                     int max_stages, int kmax, cudaStream_t stream);

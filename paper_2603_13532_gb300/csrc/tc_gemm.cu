@@ -17,6 +17,7 @@
 #include "bf16.cuh"
 #include "kernels.h"
 #include "tc.cuh"
+#include "tc_shape.h"
 
 namespace tks {
 
@@ -25,14 +26,12 @@ namespace {
 constexpr int kBM = 128;
 constexpr int kBK = 64;                       // bf16 elements = 128 bytes = one swizzle row
 constexpr int kATile = kBM * kBK * 2;         // 16 KB
+static_assert(kBM == kTcBM && kBK == kTcBK, "the launch shape's tile sizes are the kernel's");
 // Partial accumulators in TMEM: k-block kb goes to accumulator kb % acc and the epilogue adds
 // them, so each float32 accumulator takes 1/acc of the K-steps (the rounding error of a long
-// contraction whose products share a sign grows with the number of steps).  Contractions of up to
-// kShortK take four accumulators (at most four k-blocks, 16 steps, each): 256 TMEM columns, so two
-// CTAs share an SM and one's loads and epilogue overlap the other's products.  Longer ones take
-// eight accumulators of 64 columns, all 512 TMEM columns, one CTA per SM.
-constexpr int kAccLong = 8, kAccShort = 4;
-constexpr int kShortK = 16 * 64;
+// contraction whose products share a sign grows with the number of steps).  tc_gemm_shape picks
+// acc: four (256 TMEM columns, two CTAs per SM, one's loads and epilogue overlapping the other's
+// products) for short contractions, eight (all 512 columns, one CTA per SM) for the rest.
 
 __device__ __forceinline__ void record_status_tc(Status* st, int code) {
   if (st) atomicCAS(&st->code, 0, code);
@@ -217,46 +216,17 @@ __global__ void __launch_bounds__(192, 1)
 
 }  // namespace
 
-size_t tc_gemm_smem_bytes(int stages, int na_max, int nb_max, int bn) {
-  return 1024 + (size_t)stages * (na_max * kATile + nb_max * bn * kBK * 2) + 8 * (2 * stages + 1) + 16;
-}
-
-int tc_gemm_stages(int na_max, int nb_max, int bn) {
-  const size_t budget = 220 * 1024;
-  for (int s = 4; s >= 2; --s)
-    if (tc_gemm_smem_bytes(s, na_max, nb_max, bn) <= budget) return s;
-  return 1;
-}
-
 cudaError_t prepare_tc_gemm() {
-  return cudaFuncSetAttribute(tc_gemm_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  return cudaFuncSetAttribute(tc_gemm_kernel<kTcBN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
 }
 
 void launch_tc_gemm(const TcJob* jobs, int njobs, int total_tiles, const void* maps, int na_max, int nb_max,
                     const Bases& bases, Status* status, long long wait_cycles, const int* stall_word,
                     int max_stages, int kmax, cudaStream_t stream) {
-  // two CTAs per SM for short contractions of at most kTwoTiles output tiles (few tiles an SM, whose
-  // TMA set-up, products and epilogue one CTA per SM would run in turn), and for those of at most
-  // four k-blocks (epilogue-heavy; four accumulators round them exactly as eight).  Longer
-  // contractions of more tiles keep one CTA per SM: no faster on two, and each float32 accumulator
-  // takes half the k-blocks.
-  constexpr int kTwoTiles = 32 * 152;
-  const bool two = kmax <= kShortK && (total_tiles <= kTwoTiles || kmax <= kAccShort * kBK);
-  // two CTAs per SM: the stages that fit half the shared memory, and at least 77 KB each so that no
-  // third CTA (and its TMEM columns) joins; one CTA per SM: at least 116 KB, all 512 TMEM columns
-  int stages = two ? 1 : tc_gemm_stages(na_max, nb_max, 64);
-  if (two)
-    for (int s = 4; s >= 2; --s)
-      if (tc_gemm_smem_bytes(s, na_max, nb_max, 64) <= 112 * 1024) {
-        stages = s;
-        break;
-      }
-  if (max_stages > 0 && stages > max_stages) stages = max_stages;
-  const size_t floor = two ? 77 * 1024 : 116 * 1024;
-  const size_t smem = std::max<size_t>(tc_gemm_smem_bytes(stages, na_max, nb_max, 64), floor);
-  tc_gemm_kernel<64><<<total_tiles, 192, smem, stream>>>(jobs, njobs, static_cast<const CUtensorMap*>(maps), bases,
-                                                         status, stages, na_max, nb_max, two ? kAccShort : kAccLong,
-                                                         wait_cycles, stall_word);
+  const TcShape sh = tc_gemm_shape(kmax, total_tiles, na_max, nb_max, max_stages);
+  tc_gemm_kernel<kTcBN><<<total_tiles, 192, sh.smem, stream>>>(jobs, njobs, static_cast<const CUtensorMap*>(maps),
+                                                               bases, status, sh.stages, na_max, nb_max, sh.acc,
+                                                               wait_cycles, stall_word);
 }
 
 }  // namespace tks
