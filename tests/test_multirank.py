@@ -1,6 +1,6 @@
 """The multi-rank path of bench.py on CPU with gloo, world size 2: disjoint problem seeds per
 rank, the max-over-ranks time and the weak-scaling rate, and the reference arm launched under
-torchrun with two ranks printing exactly one line."""
+torchrun with two ranks printing exactly one line; also the batch size each workload defaults to."""
 import json
 import os
 import socket
@@ -59,3 +59,15 @@ def test_reference_arm_under_torchrun_two_ranks():
     assert len(lines) == 1
     line = json.loads(lines[0])
     assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
+
+
+@pytest.mark.parametrize("workload,problems", [("decay512", 152), ("batched", 256), ("order4-krp", 38),
+                                               ("order4-kron", 38), ("exact_recovery", 152)])
+def test_bench_problem_count_defaults_per_workload(monkeypatch, workload, problems):
+    """Without --problems each workload takes the batch its configuration names (order 4: 38 sums,
+    which fit one GPU with the autotuner's scratch; batched: 256); --problems overrides it."""
+    import bench
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--workload", workload])
+    assert bench.parse_args().problems == problems
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--workload", workload, "--problems", "7"])
+    assert bench.parse_args().problems == 7
