@@ -194,6 +194,19 @@ TKS_API void tks_plan_destroy(tks_plan* plan);
 TKS_API tks_status tks_plan_info(const tks_plan* plan, tks_plan_info_t* info);
 TKS_API tks_status tks_problem_info(const tks_plan* plan, int32_t problem, tks_problem_info_t* info);
 
+/* Sketch sizes of one problem without a plan or a device (host-only; the values tks_problem_info
+ * reports as omega_cols and sketch_cols for a problem with these targets and oversamplings, so a
+ * caller of tucker_sum_sketch_noalloc can size Y_out).  With ell_m = target_ranks[m] +
+ * oversampling[m]: Khatri-Rao (Sec. 3.2), s_m = S_m = max_j ell_j; Kronecker, s_m is the least s
+ * with (s ell_m)^(d-1) >= prod_j ell_j (the exact integer form of Eq. heuristic_formula, which meets
+ * Eq. sketch_condition) and S_m = prod_{j != m} s_j.  order = d; target_ranks, oversampling,
+ * omega_cols and sketch_cols are host arrays of d entries (the last two written only on success).
+ * TKS_EINVAL for an unknown sketch type, d outside 2..TKS_MAX_ORDER, a NULL pointer, a target below
+ * 1, a negative oversampling or an ell_m above 2^21; TKS_EUNSUPPORTED for a Kronecker S_m above
+ * 8192 (the limit tks_plan_create applies). */
+TKS_API tks_status tks_sketch_sizes(int32_t sketch, int32_t order, const int32_t* target_ranks,
+                                    const int32_t* oversampling, int32_t* omega_cols, int32_t* sketch_cols);
+
 /* Writes every Omega_m (n_m x s_m, float64, column-major) of every problem into the device
  * buffer omega_out at the offsets of tks_problem_info.  Draw e = i + n_m c of problem p, mode m
  * is Philox4x64-10 block e/4 under key (seed, 0) and counter (e/4, m, p, 0), turned into normals
@@ -302,8 +315,8 @@ TKS_API tks_status tks_profile_end(tks_plan* plan, tks_step_profile_t* out, int3
  * TKS_FP64 with dtype F64; omega_lowprec and lanes are checked as there, and omega_lowprec = 1
  * draws the mixed modes' Omega), Y_out a device buffer of sum_n n_n S_n float64 where Y_n
  * (n_n x S_n, column-major) starts at element sum_{m<n} n_m S_m, S_n being the sketch_cols that
- * tks_problem_info reports for the same problem (Khatri-Rao: max_m ell_m; Kronecker: the product
- * of the other modes' s_j).  The descriptor tables and the intermediates Omega_j, M_j, Vcat_n live
+ * tks_problem_info reports for the same problem, or tks_sketch_sizes without a plan (Khatri-Rao:
+ * max_m ell_m; Kronecker: the product of the other modes' s_j).  The descriptor tables and the intermediates Omega_j, M_j, Vcat_n live
  * in a static device array of TKS_NOALLOC_SCRATCH_BYTES that every GPU loading this library holds
  * until the process exits; a problem needing more is rejected with TKS_EINVAL and a message giving
  * both sizes.  No cudaMalloc, cudaFree or other allocating call is made.  The first call on a

@@ -104,6 +104,9 @@ def load(path=None):
     lib.tks_plan_destroy.restype = None
     lib.tks_plan_info.argtypes = [P, ctypes.POINTER(PlanInfo_t)]
     lib.tks_problem_info.argtypes = [P, ctypes.c_int32, ctypes.POINTER(ProblemInfo_t)]
+    I32P = ctypes.POINTER(ctypes.c_int32)
+    lib.tks_sketch_sizes.argtypes = [ctypes.c_int32, ctypes.c_int32, I32P, I32P, I32P, I32P]
+    lib.tks_sketch_sizes.restype = ctypes.c_int
     lib.tks_generate_omega.argtypes = [P, P, P, P]
     lib.tucker_sum_sketch.argtypes = [P, P, P, P]
     lib.tks_project_core.argtypes = [P, P, P, P, P]
@@ -540,3 +543,14 @@ def with_sketch_ranks(problems, ells):
     ST-HOSVD ranks capped at ell_n)."""
     import dataclasses
     return [dataclasses.replace(p, target=list(e), oversampling=[0] * p.order) for p, e in zip(problems, ells)]
+
+
+def sketch_sizes(kind, target, oversampling):
+    """(columns of Omega_m, columns S_m of Y_m) per mode, from tks_sketch_sizes (host-only: no plan
+    and no device)."""
+    lib = load()
+    d = len(target)
+    arr = ctypes.c_int32 * d
+    cols, S = arr(), arr()
+    _check(lib.tks_sketch_sizes(SKETCH[kind], d, arr(*target), arr(*oversampling), cols, S))
+    return list(cols), list(S)

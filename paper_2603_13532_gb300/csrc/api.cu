@@ -312,16 +312,70 @@ int64_t prod(const int* v, int n) {
   return p;
 }
 
+// Largest ell_n = target_n + oversampling_n accepted: it keeps prod_j ell_j of an order-6 problem
+// below 2^126, so the Kronecker sizes below are exact in 128-bit integers.
+constexpr int64_t kMaxEll = int64_t(1) << 21;
+
+using u128 = unsigned __int128;
+
+u128 mul_sat(u128 a, u128 b) {
+  const u128 top = ~(u128)0;
+  if (a != 0 && b > top / a) return top;
+  return a * b;
+}
+
 // Least s >= 1 with (s ell_i)^(d-1) >= prod_j ell_j: the exact integer form of
-// s_i = ceil((prod_j ell_j)^(1/(d-1)) / ell_i) (Eq. heuristic_formula).
+// s_i = ceil((prod_j ell_j)^(1/(d-1)) / ell_i) (Eq. heuristic_formula), by bisection on s in
+// [1, prod_j ell_j] with saturating products (the comparison stays exact: prod_j ell_j < 2^126).
+// s_i <= (prod_{j != i} ell_j)^(1/(d-1)) + 1 <= 2^21 + 1.
 int kron_size(const int* ell, int d, int i) {
-  long double P = 1;
-  for (int j = 0; j < d; ++j) P *= ell[j];
-  for (int s = 1;; ++s) {
-    long double v = 1;
-    for (int t = 0; t < d - 1; ++t) v *= (long double)s * ell[i];
-    if (v >= P) return s;
+  u128 P = 1;
+  for (int j = 0; j < d; ++j) P *= (u128)ell[j];
+  const u128 li = (u128)ell[i];
+  auto enough = [&](u128 sz) {
+    const u128 x = mul_sat(sz, li);
+    u128 v = 1;
+    for (int t = 0; t < d - 1; ++t) v = mul_sat(v, x);
+    return v >= P;
+  };
+  u128 lo = 1, hi = P;   // enough(P) holds: (P ell_i)^(d-1) >= P
+  while (lo < hi) {
+    const u128 mid = lo + (hi - lo) / 2;
+    if (enough(mid)) {
+      hi = mid;
+    } else {
+      lo = mid + 1;
+    }
   }
+  return (int)lo;
+}
+
+// Columns of Omega_m (s) and of Y_m (S) for one problem (Sec. 3.2: s = max_n ell_n for Khatri-Rao;
+// Eq. heuristic_formula per mode for Kronecker, S_n = prod_{j != n} s_j).  ell[m] in [1, kMaxEll].
+tks_status sketch_sizes(int sketch, int d, const int* ell, int* s, int* S, const std::string& where) {
+  for (int m = 0; m < d; ++m) {
+    if (sketch == TKS_SKETCH_KRP) {
+      int w = 0;
+      for (int j = 0; j < d; ++j) w = std::max(w, ell[j]);
+      s[m] = w;
+    } else {
+      s[m] = kron_size(ell, d, m);
+    }
+  }
+  for (int m = 0; m < d; ++m) {
+    if (sketch == TKS_SKETCH_KRP) {
+      S[m] = s[m];
+      continue;
+    }
+    int64_t w = 1;
+    for (int j = 0; j < d; ++j) {
+      if (j == m) continue;
+      w *= s[j];   // at most 8192 x (2^21 + 1) before the check below ends the loop
+      if (w > 8192) return fail(TKS_EUNSUPPORTED, where + "Kronecker sketch wider than 8192 columns");
+    }
+    S[m] = (int)w;
+  }
+  return TKS_OK;
 }
 
 tks_status validate_and_size(const tks_problem& pr, const tks_params& prm, ProbHost& h, int pidx) {
@@ -339,6 +393,8 @@ tks_status validate_and_size(const tks_problem& pr, const tks_params& prm, ProbH
     h.target[m] = pr.target_ranks[m];
     h.over[m] = pr.oversampling[m];
     if (h.target[m] < 1 || h.over[m] < 0) return fail(TKS_EINVAL, where + "bad target/oversampling");
+    if ((int64_t)h.target[m] + h.over[m] > kMaxEll)
+      return fail(TKS_EINVAL, where + "target + oversampling above 2^21");
     h.ell[m] = h.target[m] + h.over[m];
     if (!pr.factors[m]) return fail(TKS_EINVAL, where + "null factor pointer");
     h.factors[m] = pr.factors[m];
@@ -365,25 +421,9 @@ tks_status validate_and_size(const tks_problem& pr, const tks_params& prm, ProbH
     }
   }
   // sketch sizes (Sec. 3.2 / Eq. heuristic_formula)
+  const tks_status sst = sketch_sizes(prm.sketch, h.d, h.ell, h.s, h.S, where);
+  if (sst != TKS_OK) return sst;
   for (int m = 0; m < h.d; ++m) {
-    if (prm.sketch == TKS_SKETCH_KRP) {
-      int s = 0;
-      for (int j = 0; j < h.d; ++j) s = std::max(s, h.ell[j]);
-      h.s[m] = s;
-    } else {
-      h.s[m] = kron_size(h.ell, h.d, m);
-    }
-  }
-  for (int m = 0; m < h.d; ++m) {
-    if (prm.sketch == TKS_SKETCH_KRP) {
-      h.S[m] = h.s[m];
-    } else {
-      int64_t S = 1;
-      for (int j = 0; j < h.d; ++j)
-        if (j != m) S *= h.s[j];
-      if (S > 8192) return fail(TKS_EUNSUPPORTED, where + "Kronecker sketch wider than 8192 columns");
-      h.S[m] = (int)S;
-    }
     h.b[m] = (int)std::min<int64_t>(h.n[m], h.S[m]);
     if (h.b[m] > TKS_MAX_BASIS) return fail(TKS_EUNSUPPORTED, where + "basis wider than TKS_MAX_BASIS");
     h.rmax[m] = std::min(h.target[m], h.b[m]);
@@ -2443,6 +2483,26 @@ tks_status tks_plan_info(const tks_plan* plan, tks_plan_info_t* info) {
   info->grad_core_elems = plan->grad_core_elems;
   info->launches_backward = plan->backward_ok ? (int32_t)plan->st_backward.size() : 0;
   info->grad_factor_elems = plan->grad_factor_elems;
+  return TKS_OK;
+}
+
+tks_status tks_sketch_sizes(int32_t sketch, int32_t order, const int32_t* target_ranks, const int32_t* oversampling,
+                            int32_t* omega_cols, int32_t* sketch_cols) {
+  if (sketch != TKS_SKETCH_KRON && sketch != TKS_SKETCH_KRP) return fail(TKS_EINVAL, "unknown sketch type");
+  if (order < 2 || order > TKS_MAX_ORDER) return fail(TKS_EINVAL, "order out of range");
+  if (!target_ranks || !oversampling || !omega_cols || !sketch_cols) return fail(TKS_EINVAL, "null pointer");
+  int ell[TKS_MAX_ORDER] = {}, sz[TKS_MAX_ORDER] = {}, cols[TKS_MAX_ORDER] = {};
+  for (int m = 0; m < order; ++m) {
+    if (target_ranks[m] < 1 || oversampling[m] < 0) return fail(TKS_EINVAL, "bad target/oversampling");
+    if ((int64_t)target_ranks[m] + oversampling[m] > kMaxEll) return fail(TKS_EINVAL, "target + oversampling above 2^21");
+    ell[m] = target_ranks[m] + oversampling[m];
+  }
+  const tks_status st = sketch_sizes(sketch, order, ell, sz, cols, "");
+  if (st != TKS_OK) return st;
+  for (int m = 0; m < order; ++m) {
+    omega_cols[m] = sz[m];
+    sketch_cols[m] = cols[m];
+  }
   return TKS_OK;
 }
 

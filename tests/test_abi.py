@@ -73,6 +73,7 @@ def _problem(binding, dims=(5, 6, 7), ranks=((2, 2, 2),), target=(3, 3, 3), over
     (lambda p, k: k["ranks"].__setitem__(0, 6), 1),     # rank above n_1 = 5
     (lambda p, k: k["tgt"].__setitem__(2, 0), 1),
     (lambda p, k: k["ovs"].__setitem__(0, -1), 1),
+    (lambda p, k: k["ovs"].__setitem__(1, 2 ** 31 - 4), 1),   # ell above 2^21 (and above INT32_MAX)
     (lambda p, k: setattr(p, "cores", None), 1),
     (lambda p, k: k["tgt"].__setitem__(0, 200), 7),      # basis b = min(n, S) = 201 > TKS_MAX_BASIS
 ])
