@@ -313,34 +313,48 @@ int64_t prod(const int* v, int n) {
 }
 
 // Largest ell_n = target_n + oversampling_n accepted: it keeps prod_j ell_j of an order-6 problem
-// below 2^126, so the Kronecker sizes below are exact in 128-bit integers.
+// below 2^126 and every Kronecker s_i at most 2^21 + 1, so the sizes below are exact in the
+// fixed-width integers of Wide.
 constexpr int64_t kMaxEll = int64_t(1) << 21;
 
-using u128 = unsigned __int128;
-
-u128 mul_sat(u128 a, u128 b) {
-  const u128 top = ~(u128)0;
-  if (a != 0 && b > top / a) return top;
-  return a * b;
-}
+// Non-negative integers below 2^256 as eight 32-bit limbs, least significant first (portable: no
+// 128-bit or extended floating point types, whose width differs between hosts).  Room for
+// prod_j ell_j < 2^126 and for (s ell_i)^(d-1) < (2^22 2^21)^5 = 2^215.
+struct Wide {
+  uint32_t w[8] = {1, 0, 0, 0, 0, 0, 0, 0};
+  void mul(uint32_t m) {
+    uint64_t carry = 0;
+    for (int k = 0; k < 8; ++k) {
+      const uint64_t t = (uint64_t)w[k] * m + carry;
+      w[k] = (uint32_t)t;
+      carry = t >> 32;
+    }
+  }
+  bool at_least(const Wide& o) const {
+    for (int k = 7; k >= 0; --k)
+      if (w[k] != o.w[k]) return w[k] > o.w[k];
+    return true;
+  }
+};
 
 // Least s >= 1 with (s ell_i)^(d-1) >= prod_j ell_j: the exact integer form of
 // s_i = ceil((prod_j ell_j)^(1/(d-1)) / ell_i) (Eq. heuristic_formula), by bisection on s in
-// [1, prod_j ell_j] with saturating products (the comparison stays exact: prod_j ell_j < 2^126).
-// s_i <= (prod_{j != i} ell_j)^(1/(d-1)) + 1 <= 2^21 + 1.
+// [1, 2^22]: with every ell_j <= 2^21, s = 2^22 qualifies, since (2^22 ell_i)^(d-1) >=
+// ell_i 2^(21 (d-1)) >= prod_j ell_j.
 int kron_size(const int* ell, int d, int i) {
-  u128 P = 1;
-  for (int j = 0; j < d; ++j) P *= (u128)ell[j];
-  const u128 li = (u128)ell[i];
-  auto enough = [&](u128 sz) {
-    const u128 x = mul_sat(sz, li);
-    u128 v = 1;
-    for (int t = 0; t < d - 1; ++t) v = mul_sat(v, x);
-    return v >= P;
+  Wide P;
+  for (int j = 0; j < d; ++j) P.mul((uint32_t)ell[j]);
+  auto enough = [&](uint32_t sz) {
+    Wide v;
+    for (int t = 0; t < d - 1; ++t) {
+      v.mul(sz);
+      v.mul((uint32_t)ell[i]);
+    }
+    return v.at_least(P);
   };
-  u128 lo = 1, hi = P;   // enough(P) holds: (P ell_i)^(d-1) >= P
+  uint32_t lo = 1, hi = 1u << 22;
   while (lo < hi) {
-    const u128 mid = lo + (hi - lo) / 2;
+    const uint32_t mid = lo + (hi - lo) / 2;
     if (enough(mid)) {
       hi = mid;
     } else {

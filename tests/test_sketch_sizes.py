@@ -80,7 +80,7 @@ def test_exact_roots(binding):
 
 def test_large_ells_stay_exact(binding):
     """Values near the 2^21 limit, with one small mode so that the sketch stays within 8192 columns:
-    the 128-bit bisection gives the oracle's exact sizes."""
+    the integer bisection gives the oracle's exact sizes."""
     cases = [[2 ** 21, 2 ** 21, 1], [8191, 8192, 1], [2 ** 20 + 1, 2 ** 20 - 1, 3], [4096, 4096, 1, 1],
              [2 ** 21, 1, 1, 1, 1, 1], [3 ** 13, 3 ** 13, 1]]
     for ell in cases:
