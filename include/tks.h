@@ -80,10 +80,10 @@ typedef enum { TKS_DT_F64 = 0, TKS_DT_BF16 = 1 } tks_dtype;
 typedef struct {
   int32_t order;                /* d */
   const int64_t* dims;          /* host [d]: n_1..n_d, each >= 1 */
-  int32_t num_terms;            /* K >= 1 */
+  int32_t num_terms;            /* 1 <= K <= 2^20 */
   const int32_t* ranks;         /* host [K*d]: ranks[k*d + m] = r_km */
   const int32_t* target_ranks;  /* host [d]: target rank per mode, >= 1 */
-  const int32_t* oversampling;  /* host [d]: oversampling p_n >= 0; ell_n = target_n + p_n */
+  const int32_t* oversampling;  /* host [d]: oversampling p_n >= 0; ell_n = target_n + p_n <= 2^21 */
   const double* alpha;          /* host [K] term weights, or NULL for all ones */
   const void* cores;            /* device: the K cores packed back to back, term k's core
                                    (r_k1 x ... x r_kd, mode 1 fastest) starting at element
@@ -178,7 +178,9 @@ typedef struct {
 /* Validates the problems, computes sketch sizes (Sec. 3.2: s = max_n ell_n for Khatri-Rao,
  * Eq. heuristic_formula in exact integer form for Kronecker), workspace layout and launch
  * tables, and copies the tables to the current CUDA device.  Host-only apart from those
- * allocations and copies; synchronous.  On error *plan is set to NULL. */
+ * allocations and copies; synchronous.  At most 2^20 problems (TKS_EINVAL above); a plan one of
+ * whose launches would count more than 2^31 - 1 tiles or elements is refused with
+ * TKS_EUNSUPPORTED (split the batch over several plans).  On error *plan is set to NULL. */
 TKS_API tks_status tks_plan_create(tks_plan** plan, const tks_problem* problems, int32_t num_problems,
                            const tks_params* params);
 

@@ -134,7 +134,7 @@ struct ProbHost {
 
 struct GemmList {
   std::vector<GemmJob> jobs;
-  int tiles = 0;
+  int64_t tiles = 0;
   int64_t red = 0;
   void add(GemmJob j) {
     if (j.M <= 0 || j.N <= 0 || j.batch <= 0) return;
@@ -144,8 +144,8 @@ struct GemmList {
     j.ksplit = std::max(1, ceil_div(std::max(j.K, 1), j.kchunk));
     j.tiles_m = ceil_div(j.M, 64);
     j.tiles_n = ceil_div(j.N, 64);
-    j.tile_begin = tiles;
-    tiles += j.tiles_m * j.tiles_n * j.batch * j.ksplit;
+    j.tile_begin = (int)tiles;   // exact while the launch's total passes the 32-bit check at plan creation
+    tiles += (int64_t)j.tiles_m * j.tiles_n * j.batch * j.ksplit;
     j.red_begin = 0;
     if (j.ksplit > 1) {
       j.red_begin = red;
@@ -263,13 +263,14 @@ struct tks_plan {
   }
   void push_tc(std::vector<Step>& steps, std::vector<TcJob>& jobs, const char* name) {
     if (jobs.empty()) return;
-    int tiles = 0, na = 1, nb = 1, kmax = 0;
+    int64_t tiles = 0;
+    int na = 1, nb = 1, kmax = 0;
     double flops = 0.0, bytes = 0.0;
     for (auto& j : jobs) {
       j.tiles_m = ceil_div(j.M, 128);
       j.tiles_n = ceil_div(j.N, 64);
-      j.tile_begin = tiles;
-      tiles += j.tiles_m * j.tiles_n;
+      j.tile_begin = (int)tiles;
+      tiles += (int64_t)j.tiles_m * j.tiles_n;
       na = std::max(na, j.na);
       nb = std::max(nb, j.nb);
       kmax = std::max(kmax, (int)j.K);
@@ -286,13 +287,13 @@ struct tks_plan {
   }
   void push_simt(std::vector<Step>& steps, std::vector<SimtJob>& jobs, const char* name) {
     if (jobs.empty()) return;
-    int tiles = 0;
+    int64_t tiles = 0;
     double flops = 0.0;
     for (auto& j : jobs) {
       j.tiles_m = ceil_div(j.M, 64);
       j.tiles_n = ceil_div(j.N, 64);
-      j.tile_begin = tiles;
-      tiles += j.tiles_m * j.tiles_n * j.batch;
+      j.tile_begin = (int)tiles;
+      tiles += (int64_t)j.tiles_m * j.tiles_n * j.batch;
       flops += 2.0 * j.M * (double)j.N * j.K * j.batch;
     }
     push(steps, S_SIMT, jobs, tiles, name, flops, 0.0);
@@ -316,6 +317,10 @@ int64_t prod(const int* v, int n) {
 // below 2^126 and every Kronecker s_i at most 2^21 + 1, so the sizes below are exact in the
 // fixed-width integers of Wide.
 constexpr int64_t kMaxEll = int64_t(1) << 21;
+// Most terms in one sum and most sums in one plan: every per-mode rank sum, per-plan count and
+// byte offset then fits its integer type with room to spare.
+constexpr int kMaxTerms = 1 << 20;
+constexpr int kMaxProblems = 1 << 20;
 
 // Non-negative integers below 2^256 as eight 32-bit limbs, least significant first (portable: no
 // 128-bit or extended floating point types, whose width differs between hosts).  Room for
@@ -396,6 +401,7 @@ tks_status validate_and_size(const tks_problem& pr, const tks_params& prm, ProbH
   const std::string where = "problem " + std::to_string(pidx) + ": ";
   if (pr.order < 2 || pr.order > TKS_MAX_ORDER) return fail(TKS_EINVAL, where + "order out of range");
   if (pr.num_terms < 1) return fail(TKS_EINVAL, where + "num_terms < 1");
+  if (pr.num_terms > kMaxTerms) return fail(TKS_EINVAL, where + "num_terms above 2^20");
   if (!pr.dims || !pr.ranks || !pr.target_ranks || !pr.oversampling || !pr.cores || !pr.factors)
     return fail(TKS_EINVAL, where + "null pointer");
   h.d = pr.order;
@@ -506,7 +512,7 @@ struct CqLists {
   std::vector<CholJob> chol[3];
   std::vector<OzSliceJob> slice[3];
   std::vector<OzGemmJob> gemm[3];
-  int xsl_total[3] = {0, 0, 0}, slice_total[3] = {0, 0, 0}, gemm_total[3] = {0, 0, 0};
+  int64_t xsl_total[3] = {0, 0, 0}, slice_total[3] = {0, 0, 0}, gemm_total[3] = {0, 0, 0};
   double gram_flops = 0.0, gemm_flops[3] = {0.0, 0.0, 0.0}, chol_flops[3] = {0.0, 0.0, 0.0};
 
   // Rout: where the last pass writes R (B_NONE: not wanted); Qout: where X R^-1 of the last pass goes
@@ -533,7 +539,7 @@ struct CqLists {
       xj.rows_pad = (P + 7) / 8 * 8;
       xj.b = b;
       xj.tiles = oz_xslice_tiles(P);
-      xj.tile_begin = xsl_total[pass];
+      xj.tile_begin = (int)xsl_total[pass];
       xsl_total[pass] += xj.tiles;
       xsl[pass].push_back(xj);
       OzGramJob gj;
@@ -583,7 +589,7 @@ struct CqLists {
         sj.K = b;
         sj.ld = ldk;
         sj.tiles = oz_slice_tiles(rows);
-        sj.tile_begin = slice_total[pass];
+        sj.tile_begin = (int)slice_total[pass];
         slice_total[pass] += sj.tiles;
         slice[pass].push_back(sj);
         return sj;
@@ -596,7 +602,7 @@ struct CqLists {
       g.K = b;
       g.tiles_m = ceil_div(g.M, 128);
       g.tiles_n = 1;
-      g.tile_begin = gemm_total[pass];
+      g.tile_begin = (int)gemm_total[pass];
       gemm_total[pass] += g.tiles_m;
       for (int sl = 0; sl < kOzSlices; ++sl) {
         g.mapA[sl] = gj.map[sl];   // the Gram's column planes, read MN-major
@@ -1203,7 +1209,7 @@ static void build_hosvd_f32(tks_plan* plan) {
     std::vector<SvdJob> svds;
     std::vector<SimtJob> ttm, fac;
     std::vector<TtmJob> ttm2, fac2;
-    int ttm_tiles = 0, fac_tiles = 0;
+    int64_t ttm_tiles = 0, fac_tiles = 0;
     double ttm_flops = 0.0, fac_flops = 0.0;
     double qflops = 0.0;
     for (int p = plan->lane_p0; p < plan->lane_p1; ++p) {
@@ -1296,7 +1302,7 @@ static void build_hosvd_f32(tks_plan* plan) {
           tj.y_type = T_F32;
         }
         tj.tiles = ttm_rows_tiles(L * Rr);
-        tj.tile_begin = ttm_tiles;
+        tj.tile_begin = (int)ttm_tiles;
         ttm_tiles += tj.tiles;
         ttm2.push_back(tj);
         ttm_flops += 2.0 * (double)L * Rr * b * rmax;
@@ -1312,7 +1318,7 @@ static void build_hosvd_f32(tks_plan* plan) {
         fj.b = b;
         fj.rmax = rmax;
         fj.tiles = ttm_rows_tiles((int64_t)h.n[n]);
-        fj.tile_begin = fac_tiles;
+        fj.tile_begin = (int)fac_tiles;
         fac_tiles += fj.tiles;
         fac2.push_back(fj);
         fac_flops += 2.0 * (double)h.n[n] * b * rmax;
@@ -1660,10 +1666,10 @@ static void build_hosvd_f64(tks_plan* plan) {
     std::vector<TtmJob> ttm, fac;
     std::vector<OzSliceJob> oz_slices;
     std::vector<OzGemmJob> oz_gemms;
-    int oz_slice_total = 0, oz_gemm_total = 0;
+    int64_t oz_slice_total = 0, oz_gemm_total = 0;
     // TKS_MIXED: the mode products run float64-accurate on the tensor cores (Ozaki scheme)
     const bool emulate = plan->params.precision == TKS_MIXED;
-    int ttm_tiles = 0, fac_tiles = 0;
+    int64_t ttm_tiles = 0, fac_tiles = 0;
     double qflops = 0.0, ttm_flops = 0.0, fac_flops = 0.0;
     // TKS_MIXED with b <= 64: the triangular factor by shifted CholeskyQR3 with float64-accurate Gram
     // matrices and products on the tensor cores (the Householder TSQR below runs only where it fails)
@@ -1779,7 +1785,7 @@ static void build_hosvd_f64(tks_plan* plan) {
       tj.b = b;
       tj.rmax = rmax;
       tj.tiles = ttm64_tiles(L * Rr);
-      tj.tile_begin = ttm_tiles;
+      tj.tile_begin = (int)ttm_tiles;
       ttm_tiles += tj.tiles;
       ttm.push_back(tj);
       ttm_flops += 2.0 * (double)L * Rr * b * rmax;
@@ -1789,7 +1795,7 @@ static void build_hosvd_f64(tks_plan* plan) {
       fj.L = (int64_t)h.n[n];
       fj.Rr = 1;
       fj.tiles = ttm64_tiles((int64_t)h.n[n]);
-      fj.tile_begin = fac_tiles;
+      fj.tile_begin = (int)fac_tiles;
       fac_tiles += fj.tiles;
       fac.push_back(fj);
       fac_flops += 2.0 * (double)h.n[n] * b * rmax;
@@ -1811,7 +1817,7 @@ static void build_hosvd_f64(tks_plan* plan) {
           sj2.K = b;
           sj2.ld = ldk;
           sj2.tiles = oz_slice_tiles(rows);
-          sj2.tile_begin = oz_slice_total;
+          sj2.tile_begin = (int)oz_slice_total;
           oz_slice_total += sj2.tiles;
           oz_slices.push_back(sj2);
           return sj2;
@@ -1841,8 +1847,8 @@ static void build_hosvd_f64(tks_plan* plan) {
           g.K = b;
           g.tiles_m = ceil_div(g.M, 128);
           g.tiles_n = ceil_div(g.N, 64);
-          g.tile_begin = oz_gemm_total;
-          oz_gemm_total += g.tiles_m * g.tiles_n;
+          g.tile_begin = (int)oz_gemm_total;
+          oz_gemm_total += (int64_t)g.tiles_m * g.tiles_n;
           for (int sl = 0; sl < kOzSlices; ++sl) {
             // column planes (a_mn): 64 rows of rows_pad digits per plane, boxes of 64 rows x 64 k
             g.mapA[sl] = a_mn ? plan->map_of(B_WS, a.planes.off + (size_t)sl * 64 * a.rows_pad * 2, a.rows, b,
@@ -1930,6 +1936,7 @@ static tks_status create_plan(tks_plan** out, const tks_problem* problems, int32
   if (!out) return fail(TKS_EINVAL, "plan output pointer is NULL");
   *out = nullptr;
   if (!problems || !params || num_problems < 1) return fail(TKS_EINVAL, "no problems or params");
+  if (num_problems > kMaxProblems) return fail(TKS_EINVAL, "more than 2^20 problems in one plan");
   const tks_params prm = *params;
   if (prm.sketch != TKS_SKETCH_KRP && prm.sketch != TKS_SKETCH_KRON) return fail(TKS_EINVAL, "bad sketch");
   if (!(prm.trunc_tol >= 0.0) || !std::isfinite(prm.trunc_tol)) return fail(TKS_EINVAL, "bad trunc_tol");
@@ -2413,6 +2420,21 @@ static tks_status create_plan(tks_plan** out, const tks_problem* problems, int32
         return fail(TKS_ECUDA, "lane streams and events");
       }
     }
+  }
+
+  // every launch counts its tiles, blocks or elements in 32 bits
+  {
+    std::vector<const std::vector<Step>*> lists = {&plan->st_omega,    &plan->st_sketch,   &plan->st_project,
+                                                   &plan->st_recompress, &plan->st_backward, &plan->st_truncerr};
+    for (const auto& l : plan->lane_steps) lists.push_back(&l);
+    for (const auto* l : lists)
+      for (const Step& st : *l)
+        if (st.work > INT32_MAX) {
+          const std::string msg = std::string(st.name) +
+                                  ": more than 2^31 - 1 tiles or elements in one launch (split the batch over plans)";
+          tks_plan_destroy(plan);
+          return fail(TKS_EUNSUPPORTED, msg);
+        }
   }
 
   // ---- device copies
@@ -3262,9 +3284,9 @@ extern "C" tks_status tucker_sum_sketch_noalloc(const tks_problem* problem, cons
   b.p[B_WS] = base + tables;
   b.p[B_Y] = reinterpret_cast<char*>(Y_out);
   launch_omega(reinterpret_cast<const OmegaJob*>(base + t_om), (int)omj.size(), om_blocks, b, params->seed, s);
-  launch_gemm_f64(reinterpret_cast<const GemmJob*>(base + t_gM), (int)gM.jobs.size(), gM.tiles, b, s);
+  launch_gemm_f64(reinterpret_cast<const GemmJob*>(base + t_gM), (int)gM.jobs.size(), (int)gM.tiles, b, s);
   launch_core_sketch_f64(reinterpret_cast<const CoreSketchJob*>(base + t_cs), (int)cs.size(), cs_total, b, s);
-  launch_gemm_f64(reinterpret_cast<const GemmJob*>(base + t_gY), (int)gY.jobs.size(), gY.tiles, b, s);
+  launch_gemm_f64(reinterpret_cast<const GemmJob*>(base + t_gY), (int)gY.jobs.size(), (int)gY.tiles, b, s);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(TKS_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
   return TKS_OK;

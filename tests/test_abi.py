@@ -68,6 +68,7 @@ def _problem(binding, dims=(5, 6, 7), ranks=((2, 2, 2),), target=(3, 3, 3), over
 @pytest.mark.parametrize("mutate,code", [
     (lambda p, k: setattr(p, "order", 1), 1),
     (lambda p, k: setattr(p, "num_terms", 0), 1),
+    (lambda p, k: setattr(p, "num_terms", 2 ** 20 + 1), 1),   # rejected before the ranks are read
     (lambda p, k: k["ranks"].__setitem__(0, 0), 1),
     (lambda p, k: k["ranks"].__setitem__(1, 65), 1),
     (lambda p, k: k["ranks"].__setitem__(0, 6), 1),     # rank above n_1 = 5
@@ -100,6 +101,9 @@ def test_plan_create_rejects_bad_params(lib):
         assert lib.tks_plan_create(ctypes.byref(h), ctypes.byref(p), 1, ctypes.byref(prm)) == 1
     assert lib.tks_plan_create(None, ctypes.byref(p), 1, ctypes.byref(binding.Params_t(1, 0, 0, 1, 0.0))) == 1
     assert lib.tks_plan_create(ctypes.byref(h), ctypes.byref(p), 0, ctypes.byref(binding.Params_t(1, 0, 0, 1, 0.0))) == 1
+    # more than 2^20 problems: rejected before any problem is read
+    assert lib.tks_plan_create(ctypes.byref(h), ctypes.byref(p), 2 ** 20 + 1,
+                               ctypes.byref(binding.Params_t(1, 0, 0, 1, 0.0))) == 1
 
 
 def test_execute_rejects_null_plan(lib):
