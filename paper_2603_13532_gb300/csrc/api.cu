@@ -61,6 +61,7 @@ struct Step {
   double flops, bytes;
   int na_max = 0, nb_max = 0;   // tensor-core GEMM steps: planes per operand
   int kmax = 0;                 // tensor-core GEMM steps: the longest contraction
+  bool beside_lanes = false;    // runs while other lanes' kernels share the GPU (see launch_tc_gemm)
   size_t smem = 0;              // dynamic shared memory of one-CTA-per-job steps
 };
 
@@ -2400,6 +2401,11 @@ static tks_status create_plan(tks_plan** out, const tks_problem* problems, int32
         tks_plan_destroy(plan);
         return fail(TKS_EUNSUPPORTED, msg);
       }
+      // a lane's tensor-core GEMMs share the SMs with the other lanes' kernels, some of which hold
+      // all 512 TMEM columns of their SM (the persistent digit products, the Gram kernel): one CTA
+      // per SM keeps a GEMM CTA from landing beside one of them and waiting for columns
+      for (auto& l : plan->lane_steps)
+        for (auto& st : l) st.beside_lanes = true;
       plan->st_omega = std::move(om);
       plan->st_sketch = std::move(sk);
       plan->st_project = std::move(pr);
@@ -2636,7 +2642,8 @@ tks_status run_steps(tks_plan* plan, const std::vector<Step>& steps, const Bases
       case S_TC:
         launch_tc_gemm(static_cast<const TcJob*>(table), s.njobs, (int)s.work, plan->arena_dev + plan->maps_off,
                        s.na_max, s.nb_max, bases, plan->status, plan->wait_cycles,
-                       plan->stall ? plan->stall_word() : nullptr, plan->params.tc_stages, s.kmax, stream);
+                       plan->stall ? plan->stall_word() : nullptr, plan->params.tc_stages, s.kmax,
+                       !s.beside_lanes, stream);
         break;
       case S_SIMT:
         launch_simt_gemm_f32(static_cast<const SimtJob*>(table), s.njobs, (int)s.work, bases, stream);

@@ -37,10 +37,11 @@ void launch_ttm_f64(const TtmJob* jobs, int njobs, int total_tiles, int max_cols
 cudaError_t prepare_tc_gemm();
 // wait_cycles bounds every mbarrier wait; stall_word (tests of the timeout path) is a device word that
 // nothing sets, waited for by the copy-issuing thread before its first copy, or NULL.  kmax: the
-// launch's longest contraction (with total_tiles it sets CTAs per SM and partial accumulators).
+// launch's longest contraction (with total_tiles it sets CTAs per SM and partial accumulators);
+// allow_two = false keeps one CTA per SM (launches beside other streams' TMEM-holding kernels).
 void launch_tc_gemm(const TcJob* jobs, int njobs, int total_tiles, const void* maps, int na_max, int nb_max,
                     const Bases& bases, Status* status, long long wait_cycles, const int* stall_word,
-                    int max_stages, int kmax, cudaStream_t stream);
+                    int max_stages, int kmax, bool allow_two, cudaStream_t stream);
 
 // Float32 CUDA-core kernels of the mixed path.
 void launch_simt_gemm_f32(const SimtJob* jobs, int njobs, int total_tiles, const Bases& bases,

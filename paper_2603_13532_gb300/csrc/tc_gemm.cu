@@ -222,8 +222,8 @@ cudaError_t prepare_tc_gemm() {
 
 void launch_tc_gemm(const TcJob* jobs, int njobs, int total_tiles, const void* maps, int na_max, int nb_max,
                     const Bases& bases, Status* status, long long wait_cycles, const int* stall_word,
-                    int max_stages, int kmax, cudaStream_t stream) {
-  const TcShape sh = tc_gemm_shape(kmax, total_tiles, na_max, nb_max, max_stages);
+                    int max_stages, int kmax, bool allow_two, cudaStream_t stream) {
+  const TcShape sh = tc_gemm_shape(kmax, total_tiles, na_max, nb_max, max_stages, allow_two);
   tc_gemm_kernel<kTcBN><<<total_tiles, 192, sh.smem, stream>>>(jobs, njobs, static_cast<const CUtensorMap*>(maps),
                                                                bases, status, sh.stages, na_max, nb_max, sh.acc,
                                                                wait_cycles, stall_word);

@@ -43,16 +43,19 @@ struct TcShape {
 };
 
 // kmax: the launch's longest contraction; total_tiles: its 128 x 64 output tiles; na_max, nb_max:
-// the most bf16 planes of an A or B operand; max_stages: a cap on the ring (0 = none).
+// the most bf16 planes of an A or B operand; max_stages: a cap on the ring (0 = none); allow_two:
+// false when the launch runs beside other streams' kernels that may hold all of an SM's TMEM
+// columns (two CTAs of 77-113 KB could share an SM with one of them and wait for columns).
 //
 // Two CTAs per SM for short contractions (K <= kTcShortK) of at most kTcTwoTiles tiles (a few
 // tiles an SM, whose TMA set-up, products and epilogue one CTA per SM would run in turn) and for
 // those of at most four k-blocks (epilogue-heavy; four accumulators round them exactly as eight).
 // Longer contractions of more tiles keep one CTA per SM: no faster on two, and each float32
 // accumulator takes half the k-blocks.
-inline TcShape tc_gemm_shape(int kmax, int total_tiles, int na_max, int nb_max, int max_stages) {
+inline TcShape tc_gemm_shape(int kmax, int total_tiles, int na_max, int nb_max, int max_stages,
+                             bool allow_two = true) {
   TcShape sh;
-  sh.two = kmax <= kTcShortK && (total_tiles <= kTcTwoTiles || kmax <= kTcAccShort * kTcBK);
+  sh.two = allow_two && kmax <= kTcShortK && (total_tiles <= kTcTwoTiles || kmax <= kTcAccShort * kTcBK);
   sh.stages = tc_gemm_ring(na_max, nb_max, kTcBN, sh.two ? kTcHalfSmem : kTcOneBudget);
   if (max_stages > 0 && sh.stages > max_stages) sh.stages = max_stages;
   const size_t need = tc_gemm_smem_bytes(sh.stages, na_max, nb_max, kTcBN);

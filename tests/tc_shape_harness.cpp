@@ -1,5 +1,6 @@
 // Prints the tensor-core GEMM's launch shape (csrc/tc_shape.h) over a grid of launches, one line
-// each: kmax tiles na nb max_stages two stages smem acc need, where need is the ring's own bytes.
+// each: kmax tiles na nb max_stages allow_two two stages smem acc need, where need is the ring's own
+// bytes.
 #include <stdio.h>
 
 #include "tc_shape.h"
@@ -11,10 +12,11 @@ int main() {
     for (int t : tiles)
       for (int na = 1; na <= 3; ++na)
         for (int nb = 1; nb <= 3; ++nb)
-          for (int ms = 0; ms <= 4; ++ms) {
-            const tks::TcShape sh = tks::tc_gemm_shape(km, t, na, nb, ms);
-            printf("%d %d %d %d %d %d %d %zu %d %zu\n", km, t, na, nb, ms, sh.two ? 1 : 0, sh.stages, sh.smem,
-                   sh.acc, tks::tc_gemm_smem_bytes(sh.stages, na, nb, tks::kTcBN));
-          }
+          for (int ms = 0; ms <= 4; ++ms)
+            for (int al = 0; al <= 1; ++al) {
+              const tks::TcShape sh = tks::tc_gemm_shape(km, t, na, nb, ms, al != 0);
+              printf("%d %d %d %d %d %d %d %d %zu %d %zu\n", km, t, na, nb, ms, al, sh.two ? 1 : 0, sh.stages,
+                     sh.smem, sh.acc, tks::tc_gemm_smem_bytes(sh.stages, na, nb, tks::kTcBN));
+            }
   return 0;
 }

@@ -5,7 +5,8 @@ Every launch must fit the SM: at most 227 KB of dynamic shared memory per CTA, 2
 accumulators (256 columns) are only safe where exactly two CTAs fit an SM by shared memory, and
 eight (512 columns) only where one does; a third CTA, or a second beside eight accumulators, would
 wait for columns.  The rule itself: two CTAs per SM when K <= 1024 and either at most 4,864 tiles
-or K <= 256 (four k-blocks, which four accumulators round exactly as eight).
+or K <= 256 (four k-blocks, which four accumulators round exactly as eight), unless the launch runs
+beside other lanes' kernels (allow_two = 0), which always takes one CTA per SM.
 """
 import shutil
 import subprocess
@@ -32,7 +33,7 @@ def shapes(tmp_path_factory):
                     "-o", str(exe)], check=True)
     out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
     rows = [tuple(int(v) for v in line.split()) for line in out.splitlines()]
-    assert len(rows) == 15 * 8 * 3 * 3 * 5
+    assert len(rows) == 15 * 8 * 3 * 3 * 5 * 2
     return rows
 
 
@@ -41,7 +42,7 @@ def ctas_per_sm(smem):
 
 
 def test_every_shape_fits_the_sm(shapes):
-    for km, tiles, na, nb, ms, two, stages, smem, acc, need in shapes:
+    for km, tiles, na, nb, ms, allow, two, stages, smem, acc, need in shapes:
         case = (km, tiles, na, nb, ms)
         assert 1 <= stages <= 4, case
         assert smem >= need and smem <= CTA_MAX_DYN, case
@@ -55,8 +56,8 @@ def test_every_shape_fits_the_sm(shapes):
 
 
 def test_rule_and_rounding(shapes):
-    for km, tiles, na, nb, ms, two, stages, smem, acc, need in shapes:
-        expect = km <= 1024 and (tiles <= 4864 or km <= 256)
+    for km, tiles, na, nb, ms, allow, two, stages, smem, acc, need in shapes:
+        expect = bool(allow) and km <= 1024 and (tiles <= 4864 or km <= 256)
         assert bool(two) == expect, (km, tiles)
         nk = -(-km // 64)
         if two:
@@ -74,7 +75,7 @@ def test_deepest_ring_that_fits(shapes):
     def ring_bytes(s, na, nb):
         return 1024 + s * (na * 128 * 64 * 2 + nb * 64 * 64 * 2) + 8 * (2 * s + 1) + 16
 
-    for km, tiles, na, nb, ms, two, stages, smem, acc, need in shapes:
+    for km, tiles, na, nb, ms, allow, two, stages, smem, acc, need in shapes:
         assert need == ring_bytes(stages, na, nb)
         budget = 112 * 1024 if two else 220 * 1024
         deepest = next((s for s in (4, 3, 2) if ring_bytes(s, na, nb) <= budget), 1)
@@ -86,9 +87,11 @@ def test_measured_launches(shapes):
     tiles; a6: 1 x 3, K = 512, 760 tiles) run two CTAs per SM; the order-4 Kronecker Y = Ucat Vcat
     (K = 896, about 108,000 tiles) and H = Tcat A^T (3 x 3 planes, K = 896, about 19,000 tiles)
     one; the backward's K = 40 launches of 15,200 and 5,472 tiles two."""
-    by = {(r[0], r[1], r[2], r[3], r[4]): r for r in shapes}
-    assert by[(512, 760, 1, 1, 0)][5:7] == (1, 4)
-    assert by[(640, 760, 1, 3, 0)][5:7] == (1, 2)
-    assert by[(896, 108000, 1, 3, 0)][5] == 0
-    assert by[(896, 15200, 3, 3, 0)][5] == 0
-    assert by[(40, 15200, 3, 3, 0)][5:7] == (1, 1)
+    by = {(r[0], r[1], r[2], r[3], r[4], r[5]): r for r in shapes}
+    assert by[(512, 760, 1, 1, 0, 1)][6:8] == (1, 4)
+    assert by[(640, 760, 1, 3, 0, 1)][6:8] == (1, 2)
+    assert by[(896, 108000, 1, 3, 0, 1)][6] == 0
+    assert by[(896, 15200, 3, 3, 0, 1)][6] == 0
+    assert by[(40, 15200, 3, 3, 0, 1)][6:8] == (1, 1)
+    # a lane of a multi-lane plan: one CTA per SM whatever the shape
+    assert by[(512, 760, 1, 1, 0, 0)][6] == 0 and by[(40, 15200, 3, 3, 0, 0)][6] == 0
