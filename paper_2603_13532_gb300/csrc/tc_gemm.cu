@@ -3,7 +3,8 @@
 // One CTA computes one 128 x BN output tile of one job.  Warp 0 (one elected thread) streams
 // the bf16 planes of A and B through a ring of shared-memory stages with TMA (128-byte swizzle);
 // warp 1 allocates acc TMEM accumulators (4 or 8) and (one elected thread) issues tcgen05.mma for
-// every selected plane pair, 16 deep in k per instruction, k-block kb into accumulator kb % acc,
+// every selected plane pair, 16 deep in k per instruction, k-block kb into accumulator kb % accj
+// (accj: 4 for a job of K <= 1024, else 8, whatever the launch allocated),
 // releasing each stage with tcgen05.commit; warps 2-5 read the accumulators back with
 // tcgen05.ld (one TMEM lane quadrant each), add them and write the requested outputs.
 // Every wait is bounded: on a timeout the kernel records TKS_ETIMEOUT,
@@ -27,11 +28,12 @@ constexpr int kBM = 128;
 constexpr int kBK = 64;                       // bf16 elements = 128 bytes = one swizzle row
 constexpr int kATile = kBM * kBK * 2;         // 16 KB
 static_assert(kBM == kTcBM && kBK == kTcBK, "the launch shape's tile sizes are the kernel's");
-// Partial accumulators in TMEM: k-block kb goes to accumulator kb % acc and the epilogue adds
-// them, so each float32 accumulator takes 1/acc of the K-steps (the rounding error of a long
-// contraction whose products share a sign grows with the number of steps).  tc_gemm_shape picks
-// acc: four (256 TMEM columns, two CTAs per SM, one's loads and epilogue overlapping the other's
-// products) for short contractions, eight (all 512 columns, one CTA per SM) for the rest.
+// Partial accumulators in TMEM: k-block kb goes to accumulator kb % accj and the epilogue adds
+// them, so each float32 accumulator takes 1/accj of the K-steps (the rounding error of a long
+// contraction whose products share a sign grows with the number of steps).  A job of K <= 1024
+// takes four (at most four k-blocks each), a longer one eight.  tc_gemm_shape picks what a CTA
+// allocates: four (256 TMEM columns, two CTAs per SM, one's loads and epilogue overlapping the
+// other's products) when every job of the launch is short, else eight (all 512, one CTA per SM).
 
 __device__ __forceinline__ void record_status_tc(Status* st, int code) {
   if (st) atomicCAS(&st->code, 0, code);
@@ -58,6 +60,10 @@ __global__ void __launch_bounds__(192, 1)
   const int tn = local % J.tiles_n, tm = local / J.tiles_n;
   const int m0 = tm * kBM, n0 = tn * BN;
   const int nk = (J.K + kBK - 1) / kBK;
+  // the job's own partial accumulators: four for K <= kTcShortK, eight above (the launch allocates
+  // acc = 8 whenever one of its jobs is longer), so that a job rounds the same whatever launch it
+  // shares: one lane or several, one CTA per SM or two
+  const int accj = J.K <= kTcShortK ? kTcAccShort : acc;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
@@ -135,9 +141,9 @@ __global__ void __launch_bounds__(192, 1)
           break;
         }
         tc::fence_after_sync();
-        // k-block kb accumulates into accumulator kb % acc; its first block starts it at zero
-        const uint32_t d = tmem + (uint32_t)((kb % acc) * BN);
-        uint32_t accum = kb >= acc ? 1u : 0u;
+        // k-block kb accumulates into accumulator kb % accj; its first block starts it at zero
+        const uint32_t d = tmem + (uint32_t)((kb % accj) * BN);
+        uint32_t accum = kb >= accj ? 1u : 0u;
         for (int p = 0; p < J.npairs; ++p) {
           const uint32_t a0 = tc::smem_u32(a_tile(s, J.pa[p]));
           const uint32_t b0 = tc::smem_u32(b_tile(s, J.pb[p]));
@@ -168,11 +174,11 @@ __global__ void __launch_bounds__(192, 1)
       uint16_t* ob0 = E.nbf > 0 ? at<uint16_t>(bases, E.bf[0]) : nullptr;
       uint16_t* ob1 = E.nbf > 1 ? at<uint16_t>(bases, E.bf[1]) : nullptr;
       uint16_t* ob2 = E.nbf > 2 ? at<uint16_t>(bases, E.bf[2]) : nullptr;
-      const int nacc = nk < acc ? nk : acc;
+      const int nacc = nk < accj ? nk : accj;
 #pragma unroll
       for (int c0 = 0; c0 < BN; c0 += 32) {
-        // the partial accumulators of this column chunk (acc - 1 float32 additions: negligible
-        // next to the K / (16 acc) roundings inside each accumulator; float64 arithmetic here
+        // the partial accumulators of this column chunk (accj - 1 float32 additions: negligible
+        // next to the K / (16 accj) roundings inside each accumulator; float64 arithmetic here
         // would run at the FP64 rate)
         float sum[32];
 #pragma unroll

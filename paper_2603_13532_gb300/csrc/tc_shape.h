@@ -49,9 +49,10 @@ struct TcShape {
 //
 // Two CTAs per SM for short contractions (K <= kTcShortK) of at most kTcTwoTiles tiles (a few
 // tiles an SM, whose TMA set-up, products and epilogue one CTA per SM would run in turn) and for
-// those of at most four k-blocks (epilogue-heavy; four accumulators round them exactly as eight).
-// Longer contractions of more tiles keep one CTA per SM: no faster on two, and each float32
-// accumulator takes half the k-blocks.
+// those of at most four k-blocks (epilogue-heavy).  Short contractions of more tiles keep one CTA
+// per SM (measured no faster on two).  The shape changes no result: a job of K <= kTcShortK always
+// spreads its k-blocks over four accumulators and a longer one over eight (the kernel's per-job
+// count), so only what a CTA allocates differs.
 inline TcShape tc_gemm_shape(int kmax, int total_tiles, int na_max, int nb_max, int max_stages,
                              bool allow_two = true) {
   TcShape sh;

@@ -5,8 +5,9 @@ Every launch must fit the SM: at most 227 KB of dynamic shared memory per CTA, 2
 accumulators (256 columns) are only safe where exactly two CTAs fit an SM by shared memory, and
 eight (512 columns) only where one does; a third CTA, or a second beside eight accumulators, would
 wait for columns.  The rule itself: two CTAs per SM when K <= 1024 and either at most 4,864 tiles
-or K <= 256 (four k-blocks, which four accumulators round exactly as eight), unless the launch runs
-beside other lanes' kernels (allow_two = 0), which always takes one CTA per SM.
+or K <= 256 (four k-blocks), unless the launch runs beside other lanes' kernels (allow_two = 0),
+which always takes one CTA per SM.  The kernel gives each job four accumulators when its K <= 1024
+and eight above, so a two-CTA launch (K <= 1024 throughout) never needs more than it allocates.
 """
 import shutil
 import subprocess
@@ -63,10 +64,9 @@ def test_rule_and_rounding(shapes):
         if two:
             # at most four k-blocks per float32 accumulator
             assert -(-nk // acc) <= 4, (km, tiles)
-        if km <= 256:
-            # at most four k-blocks: one per accumulator with four accumulators or eight, so the
-            # two shapes round alike
-            assert nk <= 4 and min(nk, 4) == min(nk, 8)
+        # the kernel's per-job count: four accumulators up to K = 1024, eight above; a CTA
+        # allocates at least that many for every job it can be given
+        assert (4 if km <= 1024 else 8) <= acc, (km, tiles, two)
 
 
 def test_deepest_ring_that_fits(shapes):
